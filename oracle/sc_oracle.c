@@ -1,0 +1,1054 @@
+/*
+ * Plain FP64 CPU oracle of the quasiclassical Riccati sweep (SuperConga,
+ * arXiv 2205.15000).  TEST INFRASTRUCTURE ONLY: only tests/, the package's
+ * smoke() check and bench.py's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * The code is deliberately plain: loops in the order the method states them,
+ * C99 complex doubles, no blocking or fusion.  OpenMP only splits independent
+ * (angle, line) work and grid points.
+ *
+ * Discretisation (the paper leaves the details open; each reading is listed in
+ * the repository's design notes and repeated here where it is applied):
+ *   grid       point (i,j) at (x0+(i+1/2)h, y0+(j+1/2)h); mask = centre inside
+ *              the shape, with points on the boundary counted inside.
+ *   angles     phi_k = 2 pi k / N; pair p < N/2 owns a rotated square lattice
+ *              with spacing h (Sec. 3.1): line l is O + l h e_perp + s e_par,
+ *              samples at s = m h.  Angle p+N/2 uses the same lines, run in
+ *              the opposite direction (its direction vector is exactly -e_par).
+ *   chord      exact intersection with the disc / convex polygon; samples
+ *              ceil(smin/h) .. floor(smax/h).
+ *   segments   end segments take the nearest sample's value, interior segments
+ *              the mean of their two samples (App. C: linear interpolation to
+ *              the half step, nearest-neighbour extrapolation at the boundary).
+ *   step       exact solution of the Riccati equation with constant
+ *              coefficients over each segment (the stepping method, App. C).
+ *   boundary   specular: the entry value is the exit value of the reflected
+ *              incoming trajectory, bilinear in (angle, line coordinate)
+ *              (Sec. 3.1 and Fig. riccati_fig_A).
+ *   average    per-angle images are interpolated back to the grid (bilinear)
+ *              and summed with the quadrature weights (Sec. 3.1).
+ */
+#define _GNU_SOURCE
+#include "sc_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* Tolerance (units of h) for the robust geometric decisions of the
+   discretisation: inside test, chord existence, sample inclusion and the
+   choice of the active polygon edge. */
+#define TAU 1e-9
+
+static __thread char g_err[512];
+const char *or_last_error(void) { return g_err; }
+static int fail(const char *msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+    return -1;
+}
+
+struct or_geom {
+    or_params P;
+    double *vx, *vy;        /* copied polygon vertices */
+    double *nxe, *nye;      /* unit outward edge normals */
+    uint8_t *mask;
+    int32_t *ghost;         /* padded (nx+2)*(ny+2) */
+    int64_t n_in;
+    double area;
+    double Ox, Oy;
+    int npair, N;
+    double *w;              /* [N] quadrature weights */
+    double *vh;             /* [N][2] Fermi velocity directions */
+    double *eta;            /* [N] basis function */
+    /* per pair */
+    int *l_lo, *l_hi, *line_off, *samp_off; /* line_off/samp_off: [npair+1] */
+    /* per line (pair-major) */
+    double *smin, *smax;
+    int *m0, *m1, *ns, *edge_lo, *edge_hi, *soff; /* soff: sample offset within the pair */
+    int *nearest_line;       /* per line: nearest line of the pair with samples */
+    /* links per angle: [N][nl(p)][4] (pair line count); angle offsets = line_off of pair */
+    int *lk_g_angle, *lk_g_line;
+    double *lk_g_w;
+    int *lk_t_angle, *lk_t_line;
+    double *lk_t_w;
+    int64_t *ang_line_off;   /* [N+1] cumulative line counts over angles */
+    int64_t *ang_samp_off;   /* [N+1] cumulative sample counts over angles */
+};
+
+/* ---------------------------------------------------------------------- */
+/* Fermi surface: quadrature weights (Sec. 3.1: Boole, Simpson 3/8,       */
+/* Simpson 1/3 or trapezoid by divisibility of N by 4, 3, 2, else),       */
+/* composite rule closed on the periodic grid and normalised to sum 1.    */
+/* ---------------------------------------------------------------------- */
+double or_quad_weight(int k, int n) {
+    if (n % 4 == 0) {
+        static const double c[4] = {14.0, 32.0, 12.0, 32.0}; /* Boole 7,32,12,32,7 */
+        return 2.0 * c[k % 4] / (45.0 * n);
+    } else if (n % 3 == 0) {
+        static const double c[3] = {2.0, 3.0, 3.0};          /* Simpson 3/8: 1,3,3,1 */
+        return 3.0 * c[k % 3] / (8.0 * n);
+    } else if (n % 2 == 0) {
+        static const double c[2] = {2.0, 4.0};               /* Simpson 1/3: 1,4,1 */
+        return c[k % 2] / (3.0 * n);
+    }
+    return 1.0 / n;
+}
+
+/* Basis functions of Table basis_functions for a circular Fermi surface,
+   evaluated at the direction (c, s) rotated by -2 pi * crystal_rotation. */
+static double basis_eta(int pairing, double rot, double c, double s) {
+    double th = 2.0 * M_PI * rot;
+    double cr = c * cos(th) + s * sin(th);
+    double sr = -c * sin(th) + s * cos(th);
+    double c2 = cr * cr - sr * sr;  /* cos 2 phi */
+    double s2 = 2.0 * cr * sr;      /* sin 2 phi */
+    switch (pairing) {
+    case 0: return 1.0;
+    case 1: return sqrt(2.0) * c2;
+    case 2: return sqrt(2.0) * s2;
+    case 3: return sqrt(2.0) * 2.0 * s2 * c2; /* sin 4 phi */
+    }
+    return 0.0;
+}
+
+/* Normalisation of the fixed-point gap equation (Eq. gapeq_fixpoint), in
+   units of 2 pi kB Tc with eps_n = t (n + 1/2):  ln t + pi T sum_n 1/|eps_n|
+   = ln t + 2 sum_{n<Ne} 1/(2n+1). */
+double or_norm_D(double t, int n_e) {
+    double s = 0.0;
+    for (int n = 0; n < n_e; ++n) s += 1.0 / (2.0 * n + 1.0);
+    return log(t) + 2.0 * s;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Geometry                                                               */
+/* ---------------------------------------------------------------------- */
+/* signed distance outside the shape (negative inside) */
+static double sdist(const or_geom *g, double x, double y) {
+    if (g->P.shape_kind == 0) {
+        double dx = x - g->P.disc_cx, dy = y - g->P.disc_cy;
+        return sqrt(dx * dx + dy * dy) - g->P.disc_r;
+    }
+    double d = -INFINITY;
+    for (int e = 0; e < g->P.n_vert; ++e) {
+        double v = (x - g->vx[e]) * g->nxe[e] + (y - g->vy[e]) * g->nye[e];
+        if (v > d) d = v;
+    }
+    return d;
+}
+
+/* Intersection of the line B + s*e with the shape: returns 0 if empty. */
+static int chord(const or_geom *g, double bx, double by, double ex, double ey, double *smin,
+                 double *smax, int *elo, int *ehi) {
+    double h = g->P.h;
+    *elo = *ehi = -1;
+    if (g->P.shape_kind == 0) {
+        double dx = bx - g->P.disc_cx, dy = by - g->P.disc_cy;
+        double b = dx * ex + dy * ey;
+        double c = dx * dx + dy * dy - g->P.disc_r * g->P.disc_r;
+        double disc = b * b - c;
+        if (disc <= 0.0) return 0;
+        double r = sqrt(disc);
+        *smin = -b - r;
+        *smax = -b + r;
+    } else {
+        double lo = -INFINITY, hi = INFINITY;
+        int n = g->P.n_vert;
+        double *bound = malloc(sizeof(double) * n);
+        int *kind = malloc(sizeof(int) * n);
+        for (int e = 0; e < n; ++e) {
+            double f0 = (bx - g->vx[e]) * g->nxe[e] + (by - g->vy[e]) * g->nye[e];
+            double ge = ex * g->nxe[e] + ey * g->nye[e];
+            kind[e] = 0;
+            if (ge > 0.0) {           /* leaving through edge e at s = -f0/ge */
+                bound[e] = -f0 / ge;
+                kind[e] = 1;
+                if (bound[e] < hi) hi = bound[e];
+            } else if (ge < 0.0) {    /* entering through edge e */
+                bound[e] = -f0 / ge;
+                kind[e] = -1;
+                if (bound[e] > lo) lo = bound[e];
+            } else if (f0 > 0.0) {    /* parallel and outside */
+                free(bound);
+                free(kind);
+                return 0;
+            }
+        }
+        /* active edges: lowest index within the tolerance of the extremum */
+        for (int e = 0; e < n && *elo < 0; ++e)
+            if (kind[e] == -1 && bound[e] >= lo - TAU * h) *elo = e;
+        for (int e = 0; e < n && *ehi < 0; ++e)
+            if (kind[e] == 1 && bound[e] <= hi + TAU * h) *ehi = e;
+        free(bound);
+        free(kind);
+        *smin = lo;
+        *smax = hi;
+    }
+    return (*smax - *smin) > TAU * h;
+}
+
+static void normal_at(const or_geom *g, double px, double py, int edge, double *nx, double *ny) {
+    if (g->P.shape_kind == 0) {
+        double dx = px - g->P.disc_cx, dy = py - g->P.disc_cy;
+        double r = sqrt(dx * dx + dy * dy);
+        *nx = dx / r;
+        *ny = dy / r;
+    } else {
+        *nx = g->nxe[edge];
+        *ny = g->nye[edge];
+    }
+}
+
+/* line index of pair p: l in [l_lo, l_hi] -> global line index */
+static inline int gline(const or_geom *g, int p, int l) { return g->line_off[p] + (l - g->l_lo[p]); }
+
+/* Bilinear link: exit values of angles bracketing direction (ux,uy) on lines
+   bracketing point (px,py).  Writes 4 taps. */
+static void make_link(const or_geom *g, double px, double py, double ux, double uy, int *ta,
+                      int *tl, double *tw) {
+    int N = g->N;
+    double psi = atan2(uy, ux);
+    if (psi < 0.0) psi += 2.0 * M_PI;
+    double u = psi * N / (2.0 * M_PI);
+    int j0 = (int)floor(u);
+    double wa = u - j0;
+    if (j0 >= N) j0 -= N;
+    if (j0 < 0) j0 += N;
+    int js[2] = {j0, (j0 + 1) % N};
+    double was[2] = {1.0 - wa, wa};
+    for (int a = 0; a < 2; ++a) {
+        int j = js[a];
+        int p = j % g->npair;
+        double epx = -g->vh[2 * p + 1], epy = g->vh[2 * p]; /* e_perp of the pair */
+        double c = ((px - g->Ox) * epx + (py - g->Oy) * epy) / g->P.h;
+        int i0 = (int)floor(c);
+        double wl = c - i0;
+        int ls[2] = {i0, i0 + 1};
+        double wls[2] = {1.0 - wl, wl};
+        for (int b = 0; b < 2; ++b) {
+            int l = ls[b];
+            if (l < g->l_lo[p]) l = g->l_lo[p];
+            if (l > g->l_hi[p]) l = g->l_hi[p];
+            ta[2 * a + b] = j;
+            tl[2 * a + b] = l;
+            tw[2 * a + b] = was[a] * wls[b];
+        }
+    }
+}
+
+static double polygon_area(int n, const double *x, const double *y) {
+    double s = 0.0;
+    for (int e = 0; e < n; ++e) {
+        int f = (e + 1) % n;
+        s += x[e] * y[f] - x[f] * y[e];
+    }
+    return 0.5 * s;
+}
+
+void or_geom_free(or_geom *g) {
+    if (!g) return;
+    void *ptrs[] = {g->vx, g->vy, g->nxe, g->nye, g->mask, g->ghost, g->w, g->vh, g->eta,
+                    g->l_lo, g->l_hi, g->line_off, g->samp_off, g->smin, g->smax, g->m0,
+                    g->m1, g->ns, g->edge_lo, g->edge_hi, g->soff, g->nearest_line,
+                    g->lk_g_angle, g->lk_g_line, g->lk_g_w, g->lk_t_angle, g->lk_t_line,
+                    g->lk_t_w, g->ang_line_off, g->ang_samp_off};
+    for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
+    free(g);
+}
+
+or_geom *or_geom_create(const or_params *prm) {
+    if (!prm) { fail("null params"); return NULL; }
+    if (prm->nx < 2 || prm->ny < 2 || !(prm->h > 0)) { fail("bad grid"); return NULL; }
+    if (prm->n_angles < 2 || prm->n_angles % 2) { fail("n_angles must be even"); return NULL; }
+    if (prm->n_energies < 1) { fail("n_energies < 1"); return NULL; }
+    if (!(prm->t > 0 && prm->t <= 1)) { fail("t out of (0,1]"); return NULL; }
+    if (prm->shape_kind == 1 && (prm->n_vert < 3 || !prm->vx || !prm->vy)) {
+        fail("polygon needs >= 3 vertices");
+        return NULL;
+    }
+    or_geom *g = calloc(1, sizeof *g);
+    g->P = *prm;
+    int nx = prm->nx, ny = prm->ny;
+    double h = prm->h;
+    if (prm->shape_kind == 1) {
+        int n = prm->n_vert;
+        g->vx = malloc(sizeof(double) * n);
+        g->vy = malloc(sizeof(double) * n);
+        g->nxe = malloc(sizeof(double) * n);
+        g->nye = malloc(sizeof(double) * n);
+        memcpy(g->vx, prm->vx, sizeof(double) * n);
+        memcpy(g->vy, prm->vy, sizeof(double) * n);
+        for (int e = 0; e < n; ++e) {
+            int f = (e + 1) % n;
+            double dx = g->vx[f] - g->vx[e], dy = g->vy[f] - g->vy[e];
+            double len = sqrt(dx * dx + dy * dy);
+            g->nxe[e] = dy / len;   /* outward for counter-clockwise order */
+            g->nye[e] = -dx / len;
+        }
+        g->area = polygon_area(n, g->vx, g->vy);
+        if (!(g->area > 0)) { fail("polygon must be counter-clockwise"); or_geom_free(g); return NULL; }
+    } else {
+        if (!(prm->disc_r > 0)) { fail("disc radius"); or_geom_free(g); return NULL; }
+        g->area = M_PI * prm->disc_r * prm->disc_r;
+    }
+    g->P.vx = g->vx;
+    g->P.vy = g->vy;
+
+    /* mask: grid point centre inside (boundary counts as inside) */
+    g->mask = calloc((size_t)nx * ny, 1);
+    g->n_in = 0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double x = prm->x0 + (i + 0.5) * h, y = prm->y0 + (j + 0.5) * h;
+            if (sdist(g, x, y) <= TAU * h) {
+                g->mask[(size_t)j * nx + i] = 1;
+                g->n_in++;
+            }
+        }
+    if (g->n_in == 0) { fail("empty mask"); or_geom_free(g); return NULL; }
+
+    /* shape must lie inside the grid box */
+    {
+        double xlo = prm->x0, xhi = prm->x0 + nx * h, ylo = prm->y0, yhi = prm->y0 + ny * h;
+        int ok = 1;
+        if (prm->shape_kind == 0) {
+            ok = prm->disc_cx - prm->disc_r >= xlo && prm->disc_cx + prm->disc_r <= xhi &&
+                 prm->disc_cy - prm->disc_r >= ylo && prm->disc_cy + prm->disc_r <= yhi;
+        } else {
+            for (int e = 0; e < prm->n_vert; ++e)
+                ok = ok && g->vx[e] >= xlo && g->vx[e] <= xhi && g->vy[e] >= ylo && g->vy[e] <= yhi;
+        }
+        if (!ok) { fail("shape extends outside the grid box"); or_geom_free(g); return NULL; }
+    }
+
+    /* ghost map on the padded index range [-1,nx] x [-1,ny]: every index whose
+       centre is within 1.5 h of the shape maps to the nearest in-mask grid point
+       (integer squared distance; ties -> lowest row-major index). Brute force. */
+    int px = nx + 2, py = ny + 2;
+    g->ghost = malloc(sizeof(int32_t) * (size_t)px * py);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int jj = 0; jj < py; ++jj) {
+        for (int ii = 0; ii < px; ++ii) {
+            int i = ii - 1, j = jj - 1;
+            int32_t *out = &g->ghost[(size_t)jj * px + ii];
+            *out = -1;
+            if (i >= 0 && i < nx && j >= 0 && j < ny && g->mask[(size_t)j * nx + i]) {
+                *out = j * nx + i;
+                continue;
+            }
+            double x = prm->x0 + (i + 0.5) * h, y = prm->y0 + (j + 0.5) * h;
+            if (sdist(g, x, y) > 1.5 * h) continue;
+            long best = -1;
+            long bestd = 0;
+            for (int j2 = 0; j2 < ny; ++j2)
+                for (int i2 = 0; i2 < nx; ++i2) {
+                    if (!g->mask[(size_t)j2 * nx + i2]) continue;
+                    long d = (long)(i - i2) * (i - i2) + (long)(j - j2) * (j - j2);
+                    if (best < 0 || d < bestd) {
+                        best = (long)j2 * nx + i2;
+                        bestd = d;
+                    }
+                }
+            *out = (int32_t)best;
+        }
+    }
+
+    /* angles */
+    int N = prm->n_angles, np = N / 2;
+    g->N = N;
+    g->npair = np;
+    g->w = malloc(sizeof(double) * N);
+    g->vh = malloc(sizeof(double) * 2 * N);
+    g->eta = malloc(sizeof(double) * N);
+    for (int k = 0; k < np; ++k) {
+        double phi = 2.0 * M_PI * k / N;
+        g->vh[2 * k] = cos(phi);
+        g->vh[2 * k + 1] = sin(phi);
+        g->vh[2 * (k + np)] = -g->vh[2 * k];   /* exactly opposite */
+        g->vh[2 * (k + np) + 1] = -g->vh[2 * k + 1];
+    }
+    for (int k = 0; k < N; ++k) {
+        g->w[k] = or_quad_weight(k, N);
+        g->eta[k] = basis_eta(prm->pairing, prm->crystal_rotation, g->vh[2 * k], g->vh[2 * k + 1]);
+    }
+
+    /* lattice origin: grid-box centre plus the offset (units of h) */
+    g->Ox = prm->x0 + 0.5 * nx * h + prm->lattice_ox * h;
+    g->Oy = prm->y0 + 0.5 * ny * h + prm->lattice_oy * h;
+    double rext = 0.0;
+    if (prm->shape_kind == 0) {
+        rext = hypot(prm->disc_cx - g->Ox, prm->disc_cy - g->Oy) + prm->disc_r;
+    } else {
+        for (int e = 0; e < prm->n_vert; ++e) {
+            double d = hypot(g->vx[e] - g->Ox, g->vy[e] - g->Oy);
+            if (d > rext) rext = d;
+        }
+    }
+    int Lmax = (int)ceil(rext / h) + 1;
+
+    /* lines per pair (first pass: ranges) */
+    g->l_lo = malloc(sizeof(int) * np);
+    g->l_hi = malloc(sizeof(int) * np);
+    g->line_off = malloc(sizeof(int) * (np + 1));
+    g->samp_off = malloc(sizeof(int) * (np + 1));
+    for (int p = 0; p < np; ++p) {
+        double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
+        double qx = -ey, qy = ex;
+        int lo = 1 << 30, hi = -(1 << 30);
+        for (int l = -Lmax; l <= Lmax; ++l) {
+            double s0, s1;
+            int a, b;
+            if (chord(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, &s0, &s1, &a, &b)) {
+                if (l < lo) lo = l;
+                if (l > hi) hi = l;
+            }
+        }
+        if (lo > hi) { fail("pair without lines"); or_geom_free(g); return NULL; }
+        g->l_lo[p] = lo;
+        g->l_hi[p] = hi;
+    }
+    g->line_off[0] = 0;
+    for (int p = 0; p < np; ++p) g->line_off[p + 1] = g->line_off[p] + g->l_hi[p] - g->l_lo[p] + 1;
+    int nl = g->line_off[np];
+    g->smin = malloc(sizeof(double) * nl);
+    g->smax = malloc(sizeof(double) * nl);
+    g->m0 = malloc(sizeof(int) * nl);
+    g->m1 = malloc(sizeof(int) * nl);
+    g->ns = malloc(sizeof(int) * nl);
+    g->edge_lo = malloc(sizeof(int) * nl);
+    g->edge_hi = malloc(sizeof(int) * nl);
+    g->soff = malloc(sizeof(int) * nl);
+    g->nearest_line = malloc(sizeof(int) * nl);
+    g->samp_off[0] = 0;
+    for (int p = 0; p < np; ++p) {
+        double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
+        double qx = -ey, qy = ex;
+        int cnt = 0;
+        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
+            int L = gline(g, p, l);
+            double s0, s1;
+            int a, b;
+            if (!chord(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, &s0, &s1, &a, &b)) {
+                fail("line range of a pair is not contiguous (shape not convex?)");
+                or_geom_free(g);
+                return NULL;
+            }
+            g->smin[L] = s0;
+            g->smax[L] = s1;
+            g->edge_lo[L] = a;
+            g->edge_hi[L] = b;
+            g->m0[L] = (int)ceil(s0 / h - TAU);
+            g->m1[L] = (int)floor(s1 / h + TAU);
+            g->ns[L] = g->m1[L] - g->m0[L] + 1;
+            if (g->ns[L] < 0) g->ns[L] = 0;
+            g->soff[L] = cnt;
+            cnt += g->ns[L];
+        }
+        g->samp_off[p + 1] = g->samp_off[p] + cnt;
+        /* nearest line with samples (ties -> lower index) */
+        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
+            int best = -(1 << 30), bd = 1 << 30;
+            for (int l2 = g->l_lo[p]; l2 <= g->l_hi[p]; ++l2) {
+                if (g->ns[gline(g, p, l2)] < 1) continue;
+                int d = abs(l2 - l);
+                if (d < bd) { bd = d; best = l2; }
+            }
+            if (bd == (1 << 30)) { fail("pair without samples"); or_geom_free(g); return NULL; }
+            g->nearest_line[gline(g, p, l)] = best;
+        }
+    }
+
+    /* per-angle offsets */
+    g->ang_line_off = malloc(sizeof(int64_t) * (N + 1));
+    g->ang_samp_off = malloc(sizeof(int64_t) * (N + 1));
+    g->ang_line_off[0] = g->ang_samp_off[0] = 0;
+    for (int k = 0; k < N; ++k) {
+        int p = k % np;
+        g->ang_line_off[k + 1] = g->ang_line_off[k] + (g->l_hi[p] - g->l_lo[p] + 1);
+        g->ang_samp_off[k + 1] = g->ang_samp_off[k] + (g->samp_off[p + 1] - g->samp_off[p]);
+    }
+
+    /* boundary links, Sec. 3.1 and Fig. riccati_fig_A: entry of gamma for
+       angle k on line l takes the exit value of the specularly reflected
+       incoming direction; gamma~ starts from the gamma~ value that leaves
+       along the reflected outgoing direction. */
+    int64_t NL = g->ang_line_off[N];
+    g->lk_g_angle = malloc(sizeof(int) * 4 * NL);
+    g->lk_g_line = malloc(sizeof(int) * 4 * NL);
+    g->lk_g_w = malloc(sizeof(double) * 4 * NL);
+    g->lk_t_angle = malloc(sizeof(int) * 4 * NL);
+    g->lk_t_line = malloc(sizeof(int) * 4 * NL);
+    g->lk_t_w = malloc(sizeof(double) * 4 * NL);
+    for (int k = 0; k < N; ++k) {
+        int p = k % np;
+        int sg = k < np ? 1 : -1;
+        double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
+        double qx = -ey, qy = ex;
+        double vx = g->vh[2 * k], vy = g->vh[2 * k + 1];
+        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
+            int L = gline(g, p, l);
+            int64_t A = g->ang_line_off[k] + (l - g->l_lo[p]);
+            double bx = g->Ox + l * h * qx, by = g->Oy + l * h * qy;
+            /* entry end and exit end of the line in the direction of travel */
+            double s_in = sg > 0 ? g->smin[L] : g->smax[L];
+            double s_out = sg > 0 ? g->smax[L] : g->smin[L];
+            int e_in = sg > 0 ? g->edge_lo[L] : g->edge_hi[L];
+            int e_out = sg > 0 ? g->edge_hi[L] : g->edge_lo[L];
+            double pex = bx + s_in * ex, pey = by + s_in * ey;
+            double nnx, nny;
+            normal_at(g, pex, pey, e_in, &nnx, &nny);
+            double vn = vx * nnx + vy * nny;
+            double uix = vx - 2.0 * vn * nnx, uiy = vy - 2.0 * vn * nny;
+            make_link(g, pex, pey, uix, uiy, &g->lk_g_angle[4 * A], &g->lk_g_line[4 * A],
+                      &g->lk_g_w[4 * A]);
+            double pxx = bx + s_out * ex, pxy = by + s_out * ey;
+            normal_at(g, pxx, pxy, e_out, &nnx, &nny);
+            vn = vx * nnx + vy * nny;
+            double uox = vx - 2.0 * vn * nnx, uoy = vy - 2.0 * vn * nny;
+            make_link(g, pxx, pxy, uox, uoy, &g->lk_t_angle[4 * A], &g->lk_t_line[4 * A],
+                      &g->lk_t_w[4 * A]);
+        }
+    }
+    return g;
+}
+
+int or_geom_info(const or_geom *g, int64_t *info) {
+    info[0] = g->npair;
+    info[1] = g->line_off[g->npair];
+    info[2] = g->samp_off[g->npair];
+    info[3] = g->n_in;
+    info[4] = g->ang_line_off[g->N];
+    info[5] = g->ang_samp_off[g->N];
+    return 0;
+}
+double or_geom_area(const or_geom *g) { return g->area; }
+int or_geom_mask(const or_geom *g, uint8_t *m) {
+    memcpy(m, g->mask, (size_t)g->P.nx * g->P.ny);
+    return 0;
+}
+int or_geom_ghost(const or_geom *g, int32_t *o) {
+    memcpy(o, g->ghost, sizeof(int32_t) * (size_t)(g->P.nx + 2) * (g->P.ny + 2));
+    return 0;
+}
+int or_geom_lines(const or_geom *g, int32_t *l_lo, int32_t *l_hi, double *smin, double *smax,
+                  int32_t *m0, int32_t *m1) {
+    for (int p = 0; p < g->npair; ++p) {
+        l_lo[p] = g->l_lo[p];
+        l_hi[p] = g->l_hi[p];
+    }
+    int nl = g->line_off[g->npair];
+    for (int L = 0; L < nl; ++L) {
+        smin[L] = g->smin[L];
+        smax[L] = g->smax[L];
+        m0[L] = g->m0[L];
+        m1[L] = g->m1[L];
+    }
+    return 0;
+}
+int or_geom_links(const or_geom *g, int32_t *ta, int32_t *tl, double *tw) {
+    int64_t n = 4 * g->ang_line_off[g->N];
+    for (int64_t i = 0; i < n; ++i) {
+        ta[i] = g->lk_g_angle[i];
+        tl[i] = g->lk_g_line[i];
+        tw[i] = g->lk_g_w[i];
+    }
+    return 0;
+}
+int or_geom_quadrature(const or_geom *g, double *w, double *vh, double *eta) {
+    for (int k = 0; k < g->N; ++k) {
+        w[k] = g->w[k];
+        vh[2 * k] = g->vh[2 * k];
+        vh[2 * k + 1] = g->vh[2 * k + 1];
+        eta[k] = g->eta[k];
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Fields on the rotated lattice (Sec. 3.1: bilinear interpolation from   */
+/* the reference grid; grid points outside the grain take the value of    */
+/* the nearest grain point).                                              */
+/* ---------------------------------------------------------------------- */
+static int interp2(const or_geom *g, const double *f, double x, double y, double out[2]) {
+    int nx = g->P.nx, ny = g->P.ny;
+    double gx = (x - g->P.x0) / g->P.h - 0.5, gy = (y - g->P.y0) / g->P.h - 0.5;
+    int i0 = (int)floor(gx), j0 = (int)floor(gy);
+    double fx = gx - i0, fy = gy - j0;
+    out[0] = out[1] = 0.0;
+    if (i0 < -1 || i0 > nx - 1 || j0 < -1 || j0 > ny - 1) return -1;
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) {
+            double wgt = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+            int src = g->ghost[(size_t)(j0 + b + 1) * (nx + 2) + (i0 + a + 1)];
+            if (src < 0) {
+                if (wgt != 0.0) return -1;
+                continue;
+            }
+            out[0] += wgt * f[2 * (size_t)src];
+            out[1] += wgt * f[2 * (size_t)src + 1];
+        }
+    return 0;
+}
+
+/* total vector potential at a point: analytic symmetric-gauge external part
+   A_ext = B/2 (-(y-yg), x-xg) with B = pi alpha / area (units B0), plus the
+   interpolated induced part */
+static int a_total(const or_geom *g, const double *aind, double x, double y, double A[2]) {
+    double B = M_PI * g->P.flux_quanta / g->area;
+    A[0] = -0.5 * B * (y - g->P.gauge_cy);
+    A[1] = 0.5 * B * (x - g->P.gauge_cx);
+    if (aind) {
+        double ai[2];
+        if (interp2(g, aind, x, y, ai)) return -1;
+        A[0] += ai[0];
+        A[1] += ai[1];
+    }
+    return 0;
+}
+
+int or_sample_fields(const or_geom *g, const double *delta, const double *aind, int p,
+                     double *ds, double *as) {
+    double h = g->P.h;
+    double ex = g->vh[2 * p], ey = g->vh[2 * p + 1], qx = -ey, qy = ex;
+    for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
+        int L = gline(g, p, l);
+        for (int m = g->m0[L]; m <= g->m1[L]; ++m) {
+            int idx = g->soff[L] + (m - g->m0[L]);
+            double x = g->Ox + l * h * qx + m * h * ex, y = g->Oy + l * h * qy + m * h * ey;
+            if (interp2(g, delta, x, y, &ds[2 * idx])) return fail("sample outside grid");
+            if (a_total(g, aind, x, y, &as[2 * idx])) return fail("sample outside grid");
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Closed-form Riccati step.  For d gamma/ds = i (P g^2 + 2 Q g + R) with  */
+/* constant coefficients, gamma_h = -R/(Q + i Om), Om = sqrt(PR - Q^2)    */
+/* (principal branch), is the fixed point that is stable along s; with    */
+/* delta = gamma - gamma_h the equation is of Bernoulli type and          */
+/*   delta(ell) = delta E / (1 - i P delta (1-E)/(2 Om)),  E = e^{-2 Om ell}.*/
+/* ---------------------------------------------------------------------- */
+static cplx one_minus_exp_over(cplx Om, double ell) {
+    /* (1 - exp(-2 Om ell)) / (2 Om), with the series near Om ell = 0 */
+    cplx x = 2.0 * Om * ell;
+    if (cabs(x) < 1e-2) {
+        cplx s = 0.0, term = 1.0;
+        for (int k = 0; k < 8; ++k) { /* sum_k (-x)^k/(k+1)! */
+            double fact = 1.0;
+            for (int q = 2; q <= k + 1; ++q) fact *= q;
+            s += term / fact;
+            term *= -x;
+        }
+        return ell * s;
+    }
+    return (1.0 - cexp(-x)) / (2.0 * Om);
+}
+
+static cplx riccati_fixed_point(cplx P, cplx Q, cplx R) {
+    cplx Om = csqrt(P * R - Q * Q);
+    return -R / (Q + I * Om);
+}
+
+static cplx riccati_step(cplx P, cplx Q, cplx R, double ell, cplx ga) {
+    cplx Om = csqrt(P * R - Q * Q);
+    cplx gh = -R / (Q + I * Om);
+    cplx E = cexp(-2.0 * Om * ell);
+    cplx c = one_minus_exp_over(Om, ell);
+    cplx d = ga - gh;
+    return gh + d * E / (1.0 - I * P * d * c);
+}
+
+void or_step(const double *P, const double *Q, const double *R, double ell, const double *ga,
+             double *gb) {
+    cplx r = riccati_step(P[0] + I * P[1], Q[0] + I * Q[1], R[0] + I * R[1], ell, ga[0] + I * ga[1]);
+    gb[0] = creal(r);
+    gb[1] = cimag(r);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Sweep                                                                  */
+/* ---------------------------------------------------------------------- */
+int or_sweep(const or_geom *g, const double *delta, const double *aind, const double *z,
+             int n_e, int mode, const double *exit_in, double *exit_out, double *images,
+             double *gam_out) {
+    int N = g->N, np = g->npair;
+    double h = g->P.h;
+    int64_t NLA = g->ang_line_off[N];
+    int64_t NSA = g->ang_samp_off[N];
+    int sgc = g->P.charge_sign;
+    int err = 0;
+
+    /* sample fields of every pair */
+    double **dS = malloc(sizeof(double *) * np), **aS = malloc(sizeof(double *) * np);
+    for (int p = 0; p < np; ++p) {
+        int ns = g->samp_off[p + 1] - g->samp_off[p];
+        dS[p] = malloc(sizeof(double) * 2 * (ns > 0 ? ns : 1));
+        aS[p] = malloc(sizeof(double) * 2 * (ns > 0 ? ns : 1));
+        if (or_sample_fields(g, delta, aind, p, dS[p], aS[p])) err = 1;
+    }
+    if (err) goto done;
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t A = 0; A < NLA; ++A) {
+        {
+            int k = 0;
+            while (g->ang_line_off[k + 1] <= A) ++k;
+            int p = k % np;
+            int li = (int)(A - g->ang_line_off[k]);
+            int l = g->l_lo[p] + li;
+            int L = gline(g, p, l);
+            int sg = k < np ? 1 : -1;
+            double vx = g->vh[2 * k], vy = g->vh[2 * k + 1];
+            double eta = g->eta[k];
+            int ns = g->ns[L];
+            int m0 = g->m0[L], m1 = g->m1[L];
+            /* coefficient of each segment in travel order: Delta(p,R) and a = sigma v.A */
+            int nseg = ns + 1;
+            cplx *dseg = malloc(sizeof(cplx) * nseg);
+            double *aseg = malloc(sizeof(double) * nseg);
+            double *lseg = malloc(sizeof(double) * nseg);
+            cplx *dsm = malloc(sizeof(cplx) * (ns > 0 ? ns : 1)); /* sample values, travel order */
+            double *asm_ = malloc(sizeof(double) * (ns > 0 ? ns : 1));
+            int *sidx = malloc(sizeof(int) * (ns > 0 ? ns : 1));   /* canonical sample index */
+            for (int q = 0; q < ns; ++q) {
+                int m = sg > 0 ? m0 + q : m1 - q;
+                int idx = g->soff[L] + (m - m0);
+                sidx[q] = idx;
+                dsm[q] = eta * (dS[p][2 * idx] + I * dS[p][2 * idx + 1]);
+                asm_[q] = sgc * (vx * aS[p][2 * idx] + vy * aS[p][2 * idx + 1]);
+            }
+            if (ns == 0) {
+                double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
+                double smid = 0.5 * (g->smin[L] + g->smax[L]);
+                double x = g->Ox - l * h * ey + smid * ex, y = g->Oy + l * h * ex + smid * ey;
+                double dd[2] = {0.0, 0.0}, AA[2] = {0.0, 0.0};
+                if (interp2(g, delta, x, y, dd) || a_total(g, aind, x, y, AA)) {
+#pragma omp atomic write
+                    err = 1;
+                }
+                dseg[0] = eta * (dd[0] + I * dd[1]);
+                aseg[0] = sgc * (vx * AA[0] + vy * AA[1]);
+                lseg[0] = g->smax[L] - g->smin[L];
+            } else {
+                double lead = sg > 0 ? m0 * h - g->smin[L] : g->smax[L] - m1 * h;
+                double tail = sg > 0 ? g->smax[L] - m1 * h : m0 * h - g->smin[L];
+                dseg[0] = dsm[0];
+                aseg[0] = asm_[0];
+                lseg[0] = lead > 0.0 ? lead : 0.0;
+                for (int q = 1; q < ns; ++q) {
+                    dseg[q] = 0.5 * (dsm[q - 1] + dsm[q]);
+                    aseg[q] = 0.5 * (asm_[q - 1] + asm_[q]);
+                    lseg[q] = h;
+                }
+                dseg[ns] = dsm[ns - 1];
+                aseg[ns] = asm_[ns - 1];
+                lseg[ns] = tail > 0.0 ? tail : 0.0;
+            }
+            cplx *gam = malloc(sizeof(cplx) * (ns > 0 ? ns : 1));
+            cplx *gat = malloc(sizeof(cplx) * (ns > 0 ? ns : 1));
+            for (int n = 0; n < n_e; ++n) {
+                cplx zn = z[2 * n] + I * z[2 * n + 1];
+                /* gamma along the direction of travel (Eq. riccati):
+                   d gamma/ds = i (Delta* gamma^2 + 2 z gamma + Delta) */
+                cplx gm;
+                if (exit_in) {
+                    gm = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        int ja = g->lk_g_angle[4 * A + q];
+                        int jl = g->lk_g_line[4 * A + q];
+                        int jp = ja % np;
+                        int64_t B = g->ang_line_off[ja] + (jl - g->l_lo[jp]);
+                        gm += g->lk_g_w[4 * A + q] *
+                              (exit_in[2 * (B * n_e + n)] + I * exit_in[2 * (B * n_e + n) + 1]);
+                    }
+                } else {
+                    gm = riccati_fixed_point(conj(dseg[0]), zn + aseg[0], dseg[0]);
+                }
+                for (int q = 0; q < nseg; ++q) {
+                    gm = riccati_step(conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
+                    if (q < ns) gam[q] = gm;
+                }
+                int64_t oi = 2 * (A * n_e + n);
+                exit_out[oi] = creal(gm);
+                exit_out[oi + 1] = cimag(gm);
+                /* gamma~ against the direction of travel (Eq. riccati_tilde):
+                   d gamma~/ds = i (Delta gamma~^2 - 2 z gamma~ + Delta*); with u = -s
+                   d gamma~/du = i (-Delta gamma~^2 + 2 z gamma~ - Delta*) */
+                cplx gt;
+                if (exit_in) {
+                    gt = 0.0;
+                    for (int q = 0; q < 4; ++q) {
+                        int ja = g->lk_t_angle[4 * A + q];
+                        int jl = g->lk_t_line[4 * A + q];
+                        int jp = ja % np;
+                        int64_t B = g->ang_line_off[ja] + (jl - g->l_lo[jp]);
+                        int64_t ii = 2 * (NLA * n_e + B * n_e + n);
+                        gt += g->lk_t_w[4 * A + q] * (exit_in[ii] + I * exit_in[ii + 1]);
+                    }
+                } else {
+                    gt = riccati_fixed_point(-dseg[ns], zn + aseg[ns], -conj(dseg[ns]));
+                }
+                for (int q = ns; q >= 0; --q) {
+                    gt = riccati_step(-dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
+                    if (q > 0) gat[q - 1] = gt;
+                }
+                int64_t ti = 2 * (NLA * n_e + A * n_e + n);
+                exit_out[ti] = creal(gt);
+                exit_out[ti + 1] = cimag(gt);
+                /* propagator at each sample (Eq. riccati_parameterization) */
+                for (int q = 0; q < ns; ++q) {
+                    cplx ga = gam[q], gb = gat[q];
+                    cplx den = 1.0 + ga * gb;
+                    cplx gg = -I * M_PI * (1.0 - ga * gb) / den;
+                    cplx ff = -2.0 * I * M_PI * ga / den;
+                    cplx ft = 2.0 * I * M_PI * gb / den;
+                    int64_t si = g->ang_samp_off[k] + sidx[q];
+                    if (gam_out) {
+                        int64_t gi = 2 * (si * n_e + n);
+                        gam_out[gi] = creal(ga);
+                        gam_out[gi + 1] = cimag(ga);
+                        gam_out[2 * NSA * n_e + gi] = creal(gb);
+                        gam_out[2 * NSA * n_e + gi + 1] = cimag(gb);
+                    }
+                    if (mode == 0) {
+                        /* positive Matsubara energies; the negative ones follow from
+                           g(-e) = g(e)*, f(-e) = f~(e)* (Eq. symmetries) */
+                        cplx dl = dsm[q];
+                        cplx In = (conj(dl) * ff + dl * ft) / (M_PI + I * gg);
+                        double *im = &images[4 * si];
+                        if (n == 0) im[0] = im[1] = im[2] = im[3] = 0.0;
+                        cplx sf = ff + conj(ft);
+                        im[0] += creal(sf);
+                        im[1] += cimag(sf);
+                        im[2] += 2.0 * creal(gg);
+                        im[3] += 2.0 * creal(In);
+                    } else {
+                        images[si * n_e + n] = -cimag(gg) / M_PI;
+                    }
+                }
+            }
+            free(gam);
+            free(gat);
+            free(dseg);
+            free(aseg);
+            free(lseg);
+            free(dsm);
+            free(asm_);
+            free(sidx);
+        }
+    }
+done:
+    for (int p = 0; p < np; ++p) {
+        free(dS[p]);
+        free(aS[p]);
+    }
+    free(dS);
+    free(aS);
+    if (err) return fail("sample outside grid");
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Rotate back + FS average (Sec. 3.1).                                   */
+/* ---------------------------------------------------------------------- */
+int or_rotate_back(const or_geom *g, const double *images, int mode, int n_e, double *acc) {
+    int nx = g->P.nx, ny = g->P.ny, N = g->N, np = g->npair;
+    double h = g->P.h;
+    int nv = mode == 0 ? 4 : n_e;
+    int nout = mode == 0 ? 5 : n_e;
+    size_t npts = (size_t)nx * ny;
+    memset(acc, 0, sizeof(double) * nout * npts);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (size_t idx = 0; idx < npts; ++idx) {
+        if (!g->mask[idx]) continue;
+        int i = (int)(idx % nx), j = (int)(idx / nx);
+        double x = g->P.x0 + (i + 0.5) * h, y = g->P.y0 + (j + 0.5) * h;
+        double *X = malloc(sizeof(double) * nv);
+        for (int k = 0; k < N; ++k) {
+            int p = k % np;
+            double ex = g->vh[2 * p], ey = g->vh[2 * p + 1], qx = -ey, qy = ex;
+            double u = ((x - g->Ox) * qx + (y - g->Oy) * qy) / h;
+            double v = ((x - g->Ox) * ex + (y - g->Oy) * ey) / h;
+            int iu = (int)floor(u), iv = (int)floor(v);
+            double wu = u - iu, wv = v - iv;
+            for (int c = 0; c < nv; ++c) X[c] = 0.0;
+            for (int b = 0; b < 2; ++b) {
+                int l = iu + b;
+                if (l < g->l_lo[p]) l = g->l_lo[p];
+                if (l > g->l_hi[p]) l = g->l_hi[p];
+                int l2 = g->nearest_line[gline(g, p, l)];
+                int L = gline(g, p, l2);
+                for (int a = 0; a < 2; ++a) {
+                    int m = iv + a;
+                    if (m < g->m0[L]) m = g->m0[L];
+                    if (m > g->m1[L]) m = g->m1[L];
+                    int64_t si = g->ang_samp_off[k] + g->soff[L] + (m - g->m0[L]);
+                    double wgt = (b ? wu : 1.0 - wu) * (a ? wv : 1.0 - wv);
+                    for (int c = 0; c < nv; ++c) X[c] += wgt * images[si * nv + c];
+                }
+            }
+            double wk = g->w[k];
+            if (mode == 0) {
+                acc[0 * npts + idx] += wk * g->eta[k] * X[0];
+                acc[1 * npts + idx] += wk * g->eta[k] * X[1];
+                acc[2 * npts + idx] += wk * g->vh[2 * k] * X[2];
+                acc[3 * npts + idx] += wk * g->vh[2 * k + 1] * X[2];
+                acc[4 * npts + idx] += wk * X[3];
+            } else {
+                for (int c = 0; c < n_e; ++c) acc[c * npts + idx] += wk * X[c];
+            }
+        }
+        free(X);
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Outputs: gap equation (Eq. gapeq_fixpoint), current (Eq.               */
+/* current_density), Eilenberger free energy (Eq. qcLWFE with the         */
+/* Eilenberger form of I(R)), global error (Eq. global_error, p = 2).     */
+/* ---------------------------------------------------------------------- */
+int or_outputs(const or_geom *g, const double *acc, const double *delta, const double *aind,
+               double *delta_new, double *jout, double *F, double *scalars) {
+    int nx = g->P.nx, ny = g->P.ny;
+    double h = g->P.h, t = g->P.t;
+    size_t npts = (size_t)nx * ny;
+    double D = or_norm_D(t, g->P.n_energies);
+    double sgc = g->P.charge_sign;
+    int magn = g->P.kappa > 0 && isfinite(g->P.kappa) && aind;
+    double k2 = magn ? g->P.kappa * g->P.kappa : 0.0;
+    double Fsum = 0.0, num = 0.0, den = 0.0;
+    for (size_t idx = 0; idx < npts; ++idx) {
+        if (!g->mask[idx]) {
+            delta_new[2 * idx] = delta_new[2 * idx + 1] = 0.0;
+            jout[2 * idx] = jout[2 * idx + 1] = 0.0;
+            F[idx] = 0.0;
+            continue;
+        }
+        int i = (int)(idx % nx), j = (int)(idx / nx);
+        /* Delta = T sum_n <eta f> / D, T = t/(2 pi) in units of 2 pi kB Tc */
+        double dr = t / (2.0 * M_PI) * acc[idx] / D;
+        double di = t / (2.0 * M_PI) * acc[npts + idx] / D;
+        delta_new[2 * idx] = dr;
+        delta_new[2 * idx + 1] = di;
+        /* j = 2 e N_F T sum_n <v g>  ->  sigma (t/pi) <v Sg> in units of j0 */
+        jout[2 * idx] = sgc * t / M_PI * acc[2 * npts + idx];
+        jout[2 * idx + 1] = sgc * t / M_PI * acc[3 * npts + idx];
+        /* F(R) = |Delta|^2 D - (t/2) <SF> + (kappa^2/2) |B_ind|^2 */
+        double d2 = delta[2 * idx] * delta[2 * idx] + delta[2 * idx + 1] * delta[2 * idx + 1];
+        double f = d2 * D - 0.5 * t * acc[4 * npts + idx];
+        if (magn) {
+            /* B_ind = dAy/dx - dAx/dy, central differences (one-sided at the grid edge) */
+            int ia = i > 0 ? i - 1 : i, ib = i < nx - 1 ? i + 1 : i;
+            int ja = j > 0 ? j - 1 : j, jb = j < ny - 1 ? j + 1 : j;
+            double dAy = (aind[2 * ((size_t)j * nx + ib) + 1] - aind[2 * ((size_t)j * nx + ia) + 1]) /
+                         ((ib - ia) * h);
+            double dAx = (aind[2 * ((size_t)jb * nx + i)] - aind[2 * ((size_t)ja * nx + i)]) /
+                         ((jb - ja) * h);
+            double B = dAy - dAx;
+            f += 0.5 * k2 * B * B;
+        }
+        F[idx] = f;
+        Fsum += f;
+        double er = dr - delta[2 * idx], ei = di - delta[2 * idx + 1];
+        num += er * er + ei * ei;
+        den += d2;
+    }
+    scalars[0] = Fsum / (double)g->n_in;
+    scalars[1] = den > 0 ? sqrt(num / den) : 0.0;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* App. D: cell-integrated Green's function of the 2D Laplacian and the   */
+/* induced vector potential (full correlation, the tolerance-zero case).  */
+/* ---------------------------------------------------------------------- */
+static double gf_alpha(double m, double n) {
+    return (1.0 + 2.0 * m) * (1.0 + 2.0 * n) *
+           log(0.5 * (1.0 + 2.0 * m) * (1.0 + 2.0 * m) + 0.5 * (1.0 + 2.0 * n) * (1.0 + 2.0 * n));
+}
+static double gf_beta(double m, double n) {
+    return (-2.0 * m * m + 2.0 * n * n + 4.0 * n + 1.0) * atan((1.0 + 2.0 * m) / (1.0 + 2.0 * n));
+}
+static double gf_Gamma(double m, double n) { return gf_alpha(m, n) + gf_beta(m, n) + gf_beta(n, m); }
+
+double or_greens(int m, int n, double h) {
+    double s = 0.0;
+    for (int a = -1; a <= 1; a += 2)
+        for (int b = -1; b <= 1; b += 2) s += gf_Gamma(a * (double)m, b * (double)n);
+    return h * h / (4.0 * M_PI) * (2.0 * log(h) - log(2.0) - 3.0 + 0.25 * s);
+}
+
+int or_vector_potential(const or_geom *g, const double *j, double *aind) {
+    int nx = g->P.nx, ny = g->P.ny;
+    size_t npts = (size_t)nx * ny;
+    if (!(g->P.kappa > 0) || !isfinite(g->P.kappa)) {
+        memset(aind, 0, sizeof(double) * 2 * npts);
+        return 0;
+    }
+    double k2 = g->P.kappa * g->P.kappa;
+    /* subtract the mean current over the grain (App. D, last paragraph) */
+    double mx = 0.0, my = 0.0;
+    for (size_t i = 0; i < npts; ++i)
+        if (g->mask[i]) { mx += j[2 * i]; my += j[2 * i + 1]; }
+    mx /= g->n_in;
+    my /= g->n_in;
+    int W = nx > ny ? nx : ny;
+    double *G = malloc(sizeof(double) * (size_t)W * W);
+    for (int a = 0; a < W; ++a)
+        for (int b = 0; b < W; ++b) G[(size_t)a * W + b] = or_greens(a, b, g->P.h);
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < npts; ++i) {
+        int xi = (int)(i % nx), yi = (int)(i / nx);
+        double sx = 0.0, sy = 0.0;
+        for (size_t q = 0; q < npts; ++q) {
+            if (!g->mask[q]) continue;
+            int xq = (int)(q % nx), yq = (int)(q / nx);
+            double Gv = G[(size_t)abs(xq - xi) * W + abs(yq - yi)];
+            sx += Gv * (j[2 * q] - mx);
+            sy += Gv * (j[2 * q + 1] - my);
+        }
+        aind[2 * i] = -sx / k2;
+        aind[2 * i + 1] = -sy / k2;
+    }
+    free(G);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bulk gap: root of  D = t sum_{n<Ne} <eta^2 / sqrt(eta^2 Delta^2 + eps_n^2)> */
+/* (homogeneous limit of Eq. gapeq_fixpoint, f = pi Delta eta / Omega).   */
+/* ---------------------------------------------------------------------- */
+static double bulk_rhs(int pairing, double t, int n_e, int N, double d) {
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double phi = 2.0 * M_PI * k / N;
+        double eta = basis_eta(pairing, 0.0, cos(phi), sin(phi));
+        double w = or_quad_weight(k, N);
+        double sk = 0.0;
+        for (int n = 0; n < n_e; ++n) {
+            double e = t * (n + 0.5);
+            sk += eta * eta / sqrt(eta * eta * d * d + e * e);
+        }
+        s += w * sk;
+    }
+    return t * s;
+}
+
+double or_bulk_gap(int pairing, double t, int n_e, int N) {
+    double D = or_norm_D(t, n_e);
+    if (bulk_rhs(pairing, t, n_e, N, 0.0) <= D) return 0.0;
+    double lo = 0.0, hi = 2.0;
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (bulk_rhs(pairing, t, n_e, N, mid) > D) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
