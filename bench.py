@@ -1,0 +1,312 @@
+"""Benchmark of the Riccati sweep: trajectory-steps/s on one grain.
+
+One step = one pass of the whole hot path over the workload: rotate Delta and
+A onto the lattices, the Riccati sweep (all angle pairs, lines and Matsubara
+energies, propagator and energy sums fused), rotate-back with the
+Fermi-surface average, then gap update, current and free energy.  Boundary
+values carry over from step to step (Delta and A frozen: burn-in sweeps).
+
+Workload: d_{x2-y2} square rotated by 45 deg ([110] edges), side 50 xi0,
+256x256 grid over the bounding box, 128 Fermi angles, t = 0.1, Matsubara
+cutoff 16 pi kB Tc (80 energies), 0.5 flux quanta, kappa = 80; seeded
+synthetic Delta = 0.240792 (1 + 0.05 Z).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+    python bench.py --impl reference      # the FP64 CPU oracle on this host
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2205_15000_b300 import workloads as W  # noqa: E402
+
+METRIC = "Riccati trajectory-steps/s"
+WORKLOAD = "c2_diamond_dx2y2_256sq_128ang_80eps"
+# algorithmic FP32 lane-operations of the sweep kernel per (angle pair, sample,
+# energy): two closed-form steps (coefficients 58 + application 18 each) and one
+# propagator/energy-sum evaluation (22); MUFU operations counted separately (15)
+ALG_FP32_OPS_PER_PSE = 2 * (58 + 18) + 22
+ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
+SM_COUNT_B300 = 148
+FP32_LANES_PER_SM = 128
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _sample_clocks_start(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def _sample_clocks_stop(proc, f, path, device_index=0):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    f.close()
+    sm, smax, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    except Exception:
+        return None
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16):
+    """The FP64 oracle on this host: the same grain and energies with a subset
+    of the Fermi angles (a bounded sample); returns steps/s and details."""
+    import oracle
+    q = dict(p)
+    q["n_angles"] = angle_subset
+    g = oracle.OracleGeom(q)
+    # steps of the sample: n_e * sum over pairs and lines of 2 (n_samples + 1)
+    L = g.lines()
+    ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+    steps = q["n_energies"] * int(np.sum(2 * (ns + 1)))
+    ex = None
+    t0 = time.perf_counter()
+    for _ in range(n_sweeps):
+        o = g.full_sweep(delta, aind, ex)
+        ex = o["exit"]
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": steps * n_sweeps / dt, "unit": "trajectory-steps/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"{n_sweeps} FP64 sweep(s) of the same grain and 80 energies with "
+                      f"{angle_subset} of 128 Fermi angles ({steps} steps per sweep), {dt:.2f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p, delta, aind = W.c2_diamond_d()
+    vals = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(p, delta, aind, 1, 16)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            cb = r
+    v = float(statistics.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": "trajectory-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+            "cpu_baseline": {"value": v, "unit": "trajectory-steps/s", "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": "trajectory-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2205_15000_b300 import sc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    p, delta, aind = W.c2_diamond_d()
+    ctx = sc.Context(p, precision=args.precision)
+    info = ctx.info
+    stream = torch.cuda.current_stream()
+    d_delta = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128)).contiguous().to(dev)
+    sc.sc_set_fields(ctx.h, d_delta, None, True, stream)
+    dn = torch.empty((p["ny"], p["nx"], 2), dtype=torch.float64, device=dev)
+    jj = torch.empty_like(dn)
+    FF = torch.empty((p["ny"], p["nx"]), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        sc.sc_riccati_sweep(ctx.h, stream)
+        sc.sc_gap_update(ctx.h, dn, True, False, stream)
+        sc.sc_current(ctx.h, jj, True, stream)
+        sc.sc_free_energy(ctx.h, FF, True, False, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
+    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    cproc, cfile = _sample_clocks_start(clk_path) if rank == 0 else (None, None)
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+
+    # sweep kernel alone (dominant kernel), same stream, for the roofline
+    ksw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+    for a, b in ksw:
+        flush.fill_(0.0)
+        a.record(stream)
+        sc.sc_riccati_sweep(ctx.h, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = statistics.median([a.elapsed_time(b) for a, b in ksw])
+    clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
+
+    # end to end through the public API with host buffers
+    pin_delta = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128)).contiguous().pin_memory()
+    h_dn = torch.empty((p["ny"], p["nx"], 2), dtype=torch.float64).pin_memory()
+    h_j = torch.empty_like(h_dn).pin_memory()
+    h_F = torch.empty((p["ny"], p["nx"]), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(max(3, min(args.steps, 10))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sc.sc_set_fields(ctx.h, pin_delta, None, False, stream)
+        sc.sc_riccati_sweep(ctx.h, stream)
+        sc.sc_gap_update(ctx.h, h_dn, False, True, stream)
+        sc.sc_current(ctx.h, h_j, False, stream)
+        sc.sc_free_energy(ctx.h, h_F, False, True, stream)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = pin_delta.numel() * 8
+    d2h = (h_dn.numel() + h_j.numel() + h_F.numel()) * 8 + 2 * 8
+
+    steps_per_step = info.steps_per_sweep
+    local_val = steps_per_step * args.steps / (total_ms * 1e-3)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms_max = float(t.item())
+        dist.barrier()
+    else:
+        total_ms_max = total_ms
+    value = world * steps_per_step * args.steps / (total_ms_max * 1e-3)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    peaks = _measured_peaks()
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    # FP32 issue roofline: 148 SMs x 128 FP32 lanes x max SM clock
+    peak_gops = SM_COUNT_B300 * FP32_LANES_PER_SM * sm_max * 1e6 / 1e9
+    pse = info.points_per_sweep // 2  # (pair, sample, energy) combinations per sweep
+    ops = pse * (ALG_FP32_OPS_PER_PSE if args.precision == "fp32" else ALG_FP32_OPS_PER_PSE)
+    achieved = ops / (sweep_ms * 1e-3) / 1e9
+    prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    traffic = None
+    try:
+        with open(prof) as f:
+            tr = json.load(f)
+        if tr.get("precision") == args.precision and tr.get("workload") == WORKLOAD:
+            traffic = tr.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    line = {
+        "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [p["nx"], p["ny"]], "n_angles": p["n_angles"],
+                   "n_energies": p["n_energies"], "t": p["t"], "pairing": "dx2y2",
+                   "flux_quanta": p["flux_quanta"], "precision": args.precision,
+                   "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                     "frac": achieved / peak_gops, "traffic": traffic,
+                     "kernel": "sweep (sc_riccati_sweep: rotate + sweep + rotate_back)",
+                     "ms_per_launch": sweep_ms,
+                     "peak_note": "FP32 lane issue 148 SM x 128 x max SM clock (derived)"},
+        "e2e": {"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
+                "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clocks,
+        "wall_s": t_wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 1, 16)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

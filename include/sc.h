@@ -1,0 +1,184 @@
+/*
+ * sc.h -- C ABI of the B300-native Riccati sweep (quasiclassical Eilenberger
+ * method of Holmvall et al., "SuperConga", arXiv 2205.15000).
+ *
+ * One context = one 2D grain on the current CUDA device.  The context owns all
+ * of its device memory (allocated in sc_create, freed in sc_destroy).  Every
+ * pointer argument is owned by the caller and never retained after the call.
+ * Device pointers (on_device = 1) must live on the context's device; `stream`
+ * is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on
+ * `stream` unless they return a host scalar.  One context must not be used
+ * from two threads at once.
+ *
+ * Units (Table units): lengths xi0 = hbar vF / 2 pi kB Tc, energies
+ * 2 pi kB Tc, vector potential Phi0/(pi xi0), current j0, free energy
+ * Omega_A = (2 pi kB Tc)^2 N_F A.
+ *
+ * Layouts: grids are row-major [ny][nx]; grid point (i, j) sits at
+ * (x0 + (i + 1/2) h, y0 + (j + 1/2) h).  Complex grids interleave (re, im) as
+ * two doubles per point; vector grids interleave (x, y).
+ *
+ * Errors: every call returns an sc_status.  Nothing aborts or exits.  A CUDA
+ * error puts the context into a failed state; later calls return SC_ESTATE.
+ * sc_last_error(ctx) (or sc_last_error(NULL) for sc_create) gives the message.
+ */
+#ifndef SC_H
+#define SC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sc_ctx sc_ctx;
+
+typedef enum {
+    SC_OK = 0,
+    SC_EINVAL = 1,    /* invalid argument or parameter */
+    SC_ENOMEM = 2,    /* device or host allocation failed */
+    SC_ECUDA = 3,     /* CUDA runtime error */
+    SC_ETIMEOUT = 4,  /* a bounded device wait gave up */
+    SC_ENUMERIC = 5,  /* NaN / Inf detected in a result */
+    SC_ESTATE = 6,    /* context unusable after an earlier failure, or wrong call order */
+    SC_ENOTCONV = 7   /* iteration limit reached without convergence */
+} sc_status;
+
+typedef enum { SC_PAIR_S = 0, SC_PAIR_DX2Y2 = 1, SC_PAIR_DXY = 2, SC_PAIR_G = 3 } sc_pairing;
+typedef enum { SC_PREC_FP64 = 0, SC_PREC_FP32 = 1 } sc_precision;
+
+/*
+ * Problem statement of one grain (configuration appendix of the paper:
+ * physics, geometry, numerics).  Call sc_params_default() first.
+ */
+typedef struct {
+    int32_t nx, ny;          /* grid points */
+    double h, x0, y0;        /* spacing and lower-left corner of the grid box (xi0) */
+    int32_t shape_kind;      /* 0 = disc, 1 = convex polygon (counter-clockwise) */
+    double disc_cx, disc_cy, disc_r;
+    int32_t n_vert;          /* polygon vertex count (>= 3) */
+    const double *vx, *vy;   /* polygon vertices (copied by sc_create) */
+    int32_t pairing;         /* sc_pairing (Table basis_functions) */
+    double crystal_rotation; /* crystal a-axis rotation, units of 2 pi */
+    double t;                /* temperature T/Tc, 0 < t <= 1 */
+    double flux_quanta;      /* alpha = B_ext * area / Phi0, symmetric gauge */
+    double gauge_cx, gauge_cy; /* symmetric-gauge origin */
+    double kappa;            /* penetration depth lambda0/xi0; <= 0 or inf: no induced A */
+    int32_t charge_sign;     /* sign of the carrier charge, +1 or -1 */
+    int32_t n_angles;        /* Fermi-surface angles, even */
+    int32_t n_energies;      /* positive Matsubara energies eps_n = t (n + 1/2) */
+    double lattice_ox, lattice_oy; /* origin of the rotated lattices relative to the
+                                      grid-box centre, units of h (default 0.1, 0.2) */
+    int32_t precision;       /* sc_precision: FP64 plain sweep or FP32 production sweep */
+    int32_t lanes_per_line;  /* 0 = automatic; else 4, 8, 16 or 32 energy lanes per line */
+    int32_t host_only;       /* 1 = build the geometry tables only (no device memory); every
+                                call that computes then returns SC_ESTATE.  For inspecting
+                                the discretisation on a machine without a GPU. */
+} sc_params;
+
+typedef struct {
+    int32_t n_pairs;         /* angle pairs (phi, phi + pi) = n_angles / 2 */
+    int32_t n_lines;         /* trajectories (lines) summed over angle pairs */
+    int64_t n_samples;       /* lattice samples summed over angle pairs */
+    int64_t n_in;            /* grid points inside the grain */
+    int64_t steps_per_sweep; /* closed-form Riccati steps per sweep:
+                                n_energies * sum_pairs sum_lines 2 (n_samples + 1) */
+    int64_t points_per_sweep;/* (angle, energy, sample) points where g is formed */
+    double area;             /* exact grain area (xi0^2) */
+    double norm_D;           /* gap-equation normalisation ln t + 2 sum 1/(2n+1) */
+    int32_t lanes_per_line, energies_per_lane, lines_per_warp;
+    int64_t scratch_bytes;   /* device scratch used by the sweep */
+} sc_info;
+
+/* Fill defaults: 64x64 unit grid, s-wave disc, t = 0.5, 32 angles, 16 energies,
+   charge -1, lattice offset (0.1, 0.2), FP32. */
+sc_status sc_params_default(sc_params *p);
+
+/* Validate the parameters, build the geometry (mask, rotated lattices, chords,
+   specular boundary links; Sec. 3.1) and allocate device memory.
+   SC_EINVAL: odd n_angles, t outside (0,1], shape outside the grid box, empty
+   grain, non-convex polygon.  SC_ENOMEM / SC_ECUDA on device failures. */
+sc_status sc_create(const sc_params *p, sc_ctx **out);
+sc_status sc_destroy(sc_ctx *ctx);
+sc_status sc_get_info(const sc_ctx *ctx, sc_info *info);
+/* Grain mask (nx*ny bytes, 1 = inside), host pointer. */
+sc_status sc_get_mask(const sc_ctx *ctx, uint8_t *mask);
+
+/* Set the order-parameter amplitude Delta(R) (complex, nx*ny) and the induced
+   vector potential A_ind (vector, nx*ny; NULL = zero).  Eq. order_parameter:
+   Delta(p, R) = Delta(R) eta(p).  Values outside the grain are ignored. */
+sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, int on_device,
+                        void *stream);
+/* Forget the boundary coherence functions: the next sweep starts every
+   trajectory from the local homogeneous solution. */
+sc_status sc_reset_boundary(sc_ctx *ctx);
+
+/* One Riccati sweep (Alg. suprcon inner loop): for every angle pair, line and
+   positive Matsubara energy integrate gamma (Eq. riccati) along and gamma~
+   (Eq. riccati_tilde) against the Fermi velocity with the closed-form
+   constant-coefficient step, starting from the boundary values of the
+   previous sweep (specular condition, Fig. riccati_fig_A); form the propagator
+   (Eq. riccati_parameterization), sum over energies and Fermi-surface angles
+   and keep the sums for sc_gap_update / sc_current / sc_free_energy.  The
+   exit values become the next sweep's boundary values. */
+sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream);
+
+/* Sweeps with Delta and A frozen until the boundary values change by less
+   than tol (max abs) or max_sweeps is reached (burn-in, Sec. 3.1).  Returns
+   SC_ENOTCONV if tol was not met; the sweeps are done either way. */
+sc_status sc_burnin(sc_ctx *ctx, int32_t max_sweeps, double tol, void *stream);
+
+/* Gap equation in fixed-point form (Eq. gapeq_fixpoint):
+   Delta_new(R) = T sum_n <eta f> / (ln t + pi T sum_n 1/|eps_n|), complex nx*ny
+   (zero outside the grain).  eps_G (host, may be NULL) = ||Delta_new - Delta||_2 /
+   ||Delta||_2 over the grain (Eq. global_error, p = 2); asking for it
+   synchronises the stream.  Requires a preceding sc_riccati_sweep. */
+sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_device,
+                        void *stream);
+/* Charge-current density j(R) = 2 e N_F T sum_n <v_F g> (Eq. current_density),
+   vector nx*ny in units of j0. */
+sc_status sc_current(sc_ctx *ctx, double *j_out, int on_device, void *stream);
+/* Free energy (Eq. qcLWFE with the Eilenberger form of I(R)): density F(R)
+   (nx*ny, may be NULL) and F_total = mean over the grain in units of
+   Omega_A/area (host, may be NULL; synchronises).  Includes
+   (kappa^2/2)|B_ind|^2 when kappa > 0. */
+sc_status sc_free_energy(sc_ctx *ctx, double *F_total, double *density_out, int on_device,
+                         void *stream);
+/* Induced vector potential from the current of the last sweep (App. D):
+   A_ind = -(1/kappa^2) sum G (j - <j>), full correlation; becomes the
+   context's A_ind.  No-op when kappa <= 0. */
+sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream);
+/* One Picard step of Alg. suprcon (App. E, alpha = 1): Delta <- Delta_new,
+   A_ind <- from j (when kappa > 0). */
+sc_status sc_picard_step(sc_ctx *ctx, void *stream);
+
+/* Local density of states N(R, eps)/N_F = -<Im g^R(eps + i broadening)>/pi
+   (Sec. 2).  energies: host array of n_e real energies that must be symmetric
+   about zero (eps_k = -eps_{n_e-1-k}), because gamma~ at eps is taken from
+   gamma at -eps (Eq. symmetries).  Boundary values are burnt in with Delta, A
+   frozen for up to n_burnin sweeps.  ldos_out: n_e * nx * ny doubles. */
+sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening,
+                  int32_t n_burnin, double *ldos_out, int on_device, void *stream);
+
+/* ---- inspection (tests and tools) ------------------------------------- */
+/* per pair l_lo, l_hi (n_pairs each); per line smin, smax, m0, m1 (n_lines) */
+sc_status sc_debug_lines(const sc_ctx *ctx, int32_t *l_lo, int32_t *l_hi, double *smin,
+                         double *smax, int32_t *m0, int32_t *m1);
+/* padded (nx+2)*(ny+2) nearest-grain-point map, -1 where unused */
+sc_status sc_debug_ghost(const sc_ctx *ctx, int32_t *ghost);
+/* entry links of gamma for every angle k and line (k-major, lines of pair k mod
+   n_pairs): 4 taps of (angle, absolute line index, weight) */
+sc_status sc_debug_links(const sc_ctx *ctx, int32_t *tap_angle, int32_t *tap_line,
+                         double *tap_w);
+/* boundary exit values after the last sweep: complex [angle][line][energy] */
+sc_status sc_debug_exits(sc_ctx *ctx, double *exits);
+/* per-sample energy sums of the last sweep: [pair][sample][4] = (Re Sf, Im Sf,
+   Sg, SF) for angle p (angle p + N/2 follows by symmetry) */
+sc_status sc_debug_images(sc_ctx *ctx, double *images);
+
+const char *sc_last_error(const sc_ctx *ctx);
+const char *sc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,816 @@
+// C ABI of the Riccati sweep: context, device memory, launch plans.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "geometry.hpp"
+#include "kernels.cuh"
+#include "sc.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// How the sweep kernel maps (line, energy) work to lanes for one energy count.
+struct Plan {
+    int lanes = 0, ept = 0, lines_per_warp = 0;
+    int32_t *d_groups = nullptr;
+    int32_t n_groups = 0;
+    int grid_blocks = 0;
+    int64_t stride = 0;  // scratch elements (complex) per warp
+};
+
+}  // namespace
+
+struct sc_ctx {
+    scg::Geometry geo;
+    int device = 0;
+    bool fp64 = false;
+    int n_e = 0;
+    int forced_lanes = 0;
+    double normD = 0.0;
+    size_t real_bytes = 4;
+    scd::GridDev grid{};
+    // geometry on the device
+    uint8_t *d_mask = nullptr;
+    int32_t *d_ghost = nullptr;
+    scd::LineGeo *d_geo = nullptr;
+    int32_t *d_slot_line = nullptr;
+    scd::PairDev *d_pairs = nullptr;
+    scd::BackLine *d_back = nullptr;
+    scd::LineDev *d_lines = nullptr;
+    std::map<int, Plan> plans;  // key: lanes * 16 + ept
+    Plan *main_plan = nullptr;
+    // fields and results
+    double *d_delta = nullptr, *d_aind = nullptr, *d_acc = nullptr, *d_dnew = nullptr, *d_j = nullptr,
+           *d_F = nullptr, *d_sums = nullptr, *d_jsum = nullptr, *d_G = nullptr, *d_diff = nullptr;
+    int G_width = 0;
+    bool have_aind = false;
+    void *d_img_in = nullptr, *d_img_out = nullptr;
+    void *d_exit[2] = {nullptr, nullptr};
+    int cur = 0;  // d_exit[cur] holds the latest exit values
+    bool have_boundary = false;
+    bool have_sweep = false;
+    bool have_outputs = false;
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t *d_counter = nullptr;
+    int sm_count = 0;
+    bool failed = false;
+    bool host_only = false;
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg) {
+    c->err = msg;
+    if (st == SC_ECUDA || st == SC_ENOMEM) c->failed = true;
+    return st;
+}
+
+#define CK(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? SC_ENOMEM : SC_ECUDA, \
+                           std::string(#expr) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+#define CKS(expr)                            \
+    do {                                     \
+        sc_status s_ = (expr);               \
+        if (s_ != SC_OK) return s_;          \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(sc_ctx *ctx, P **p, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(v);
+        *p = (P *)v;
+    }
+    return e;
+}
+
+void dfree(sc_ctx *ctx, void *p) {
+    if (!p) return;
+    auto f = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+    if (f != ctx->allocs.end()) ctx->allocs.erase(f);
+    cudaFree(p);
+}
+
+// energy lanes per line and energies per lane: least padding, then EPT near 4
+void choose_lanes(int n_e, int forced, int &lanes, int &ept) {
+    if (forced) {
+        lanes = forced;
+        ept = (n_e + lanes - 1) / lanes;
+        return;
+    }
+    int best_pad = 1 << 30, best_l = 32, best_e = 8;
+    for (int l : {32, 16, 8, 4}) {
+        const int e = (n_e + l - 1) / l;
+        if (e > 8) continue;
+        const int pad = l * e;
+        if (pad < best_pad || (pad == best_pad && std::abs(e - 4) < std::abs(best_e - 4))) {
+            best_pad = pad;
+            best_l = l;
+            best_e = e;
+        }
+    }
+    lanes = best_l;
+    ept = best_e;
+}
+
+sc_status make_plan(sc_ctx *ctx, int n_e, Plan **out) {
+    int lanes, ept;
+    choose_lanes(n_e, ctx->forced_lanes, lanes, ept);
+    if (ept > 8 || lanes * ept < n_e)
+        return set_err(ctx, SC_EINVAL, "too many energies for the lane layout (at most 8 per lane)");
+    const int key = lanes * 16 + ept;
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        *out = &it->second;
+        return SC_OK;
+    }
+    Plan pl;
+    pl.lanes = lanes;
+    pl.ept = ept;
+    pl.lines_per_warp = 32 / lanes;
+    const int G = pl.lines_per_warp;
+    // groups of G neighbouring lines of one pair (similar lengths); longest first
+    std::vector<std::vector<int32_t>> groups;
+    std::vector<int> cost;
+    for (const auto &pp : ctx->geo.pairs) {
+        const int n = pp.l_hi - pp.l_lo + 1;
+        for (int i = 0; i < n; i += G) {
+            std::vector<int32_t> g(G, -1);
+            int c = 0;
+            for (int k = 0; k < G && i + k < n; ++k) {
+                g[k] = pp.line0 + i + k;
+                c = std::max(c, ctx->geo.lines[pp.line0 + i + k].ns + 1);
+            }
+            groups.push_back(g);
+            cost.push_back(c);
+        }
+    }
+    std::vector<int> order(groups.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<int32_t> flat;
+    flat.reserve(groups.size() * G);
+    for (int o : order) flat.insert(flat.end(), groups[o].begin(), groups[o].end());
+    pl.n_groups = (int32_t)groups.size();
+    CK(dalloc(ctx, &pl.d_groups, flat.size() * sizeof(int32_t)));
+    CK(cudaMemcpy(pl.d_groups, flat.data(), flat.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    const int bs = 128;
+    int occ = scd::sweep_occupancy(ctx->fp64, ept, bs);
+    if (occ < 1) occ = 1;
+    pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+    pl.stride = (int64_t)G * std::max(ctx->geo.max_ns, 1) * lanes * ept;
+    const size_t need = (size_t)pl.grid_blocks * 4 * (size_t)pl.stride * 2 * ctx->real_bytes;
+    if (need > ctx->scratch_bytes) {
+        dfree(ctx, ctx->d_scratch);
+        ctx->d_scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        CK(dalloc(ctx, &ctx->d_scratch, need));
+        ctx->scratch_bytes = need;
+    }
+    auto res = ctx->plans.emplace(key, pl);
+    *out = &res.first->second;
+    return SC_OK;
+}
+
+sc_status check_ctx(sc_ctx *ctx) {
+    if (!ctx) return SC_EINVAL;
+    if (ctx->host_only) return set_err(ctx, SC_ESTATE, "context was created with host_only = 1");
+    if (ctx->failed) return SC_ESTATE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+    return SC_OK;
+}
+
+// rotate the fields, then sweep; exits go from exit_prev to exit_cur
+sc_status run_sweep(sc_ctx *ctx, const Plan &pl, int n_e, bool retarded, const double *d_energies,
+                    double broadening, void *img_out, const void *exit_prev, void *exit_cur, bool first,
+                    cudaStream_t st) {
+    CK(scd::launch_rotate(ctx->fp64, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
+                          ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_img_in,
+                          st));
+    CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
+    scd::SweepLaunch a{};
+    a.lines = ctx->d_lines;
+    a.groups = pl.d_groups;
+    a.n_groups = pl.n_groups;
+    a.lines_per_warp = pl.lines_per_warp;
+    a.lanes_per_line = pl.lanes;
+    a.energies_per_lane = pl.ept;
+    a.n_e = n_e;
+    a.t = ctx->geo.prm.t;
+    a.h = ctx->geo.prm.h;
+    a.image_in = ctx->d_img_in;
+    a.image_out = img_out;
+    a.exit_prev = exit_prev;
+    a.exit_cur = exit_cur;
+    a.first_sweep = first ? 1 : 0;
+    a.scratch = ctx->d_scratch;
+    a.scratch_stride = pl.stride;
+    a.max_ns = std::max(ctx->geo.max_ns, 1);
+    a.ne_pad = pl.lanes * pl.ept;
+    a.counter = ctx->d_counter;
+    a.grid_blocks = pl.grid_blocks;
+    a.block_threads = 128;
+    a.retarded = retarded ? 1 : 0;
+    a.energies = d_energies;
+    a.broadening = broadening;
+    CK(scd::launch_sweep(ctx->fp64, a, st));
+    return SC_OK;
+}
+
+sc_status ensure_outputs(sc_ctx *ctx, cudaStream_t st) {
+    if (!ctx->have_sweep) return set_err(ctx, SC_ESTATE, "no sweep since the fields were last set");
+    if (ctx->have_outputs) return SC_OK;
+    const double kappa = ctx->geo.prm.kappa;
+    const bool magn = kappa > 0.0 && std::isfinite(kappa) && ctx->have_aind;
+    CK(scd::launch_outputs(ctx->grid, ctx->d_mask, ctx->d_acc, ctx->d_delta, magn ? ctx->d_aind : nullptr,
+                           ctx->geo.prm.t, ctx->normD, magn ? kappa : 0.0, ctx->d_dnew, ctx->d_j, ctx->d_F,
+                           ctx->d_sums, st));
+    ctx->have_outputs = true;
+    return SC_OK;
+}
+
+sc_status copy_out(sc_ctx *ctx, void *dst, const void *src, size_t bytes, int on_device, cudaStream_t st) {
+    if (!dst) return SC_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return SC_OK;
+}
+
+size_t npts(const sc_ctx *ctx) { return (size_t)ctx->geo.nx * ctx->geo.ny; }
+
+}  // namespace
+
+extern "C" {
+
+const char *sc_version(void) { return "sc-riccati 0.1 (sm_103a)"; }
+
+const char *sc_last_error(const sc_ctx *ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->err.c_str();
+}
+
+sc_status sc_params_default(sc_params *p) {
+    if (!p) return SC_EINVAL;
+    std::memset(p, 0, sizeof *p);
+    p->nx = p->ny = 64;
+    p->h = 1.0;
+    p->x0 = p->y0 = -32.0;
+    p->shape_kind = 0;
+    p->disc_r = 30.0;
+    p->pairing = SC_PAIR_S;
+    p->t = 0.5;
+    p->kappa = 0.0;
+    p->charge_sign = -1;
+    p->n_angles = 32;
+    p->n_energies = 16;
+    p->lattice_ox = 0.1;
+    p->lattice_oy = 0.2;
+    p->precision = SC_PREC_FP32;
+    return SC_OK;
+}
+
+sc_status sc_destroy(sc_ctx *ctx) {
+    if (!ctx) return SC_EINVAL;
+    if (!ctx->allocs.empty()) cudaSetDevice(ctx->device);
+    for (void *p : ctx->allocs) cudaFree(p);
+    delete ctx;
+    return SC_OK;
+}
+
+sc_status sc_create(const sc_params *p, sc_ctx **out) {
+    g_create_error.clear();
+    if (!p || !out) {
+        g_create_error = "null argument";
+        return SC_EINVAL;
+    }
+    *out = nullptr;
+    if (p->precision != SC_PREC_FP32 && p->precision != SC_PREC_FP64) {
+        g_create_error = "unknown precision";
+        return SC_EINVAL;
+    }
+    if (p->lanes_per_line != 0 && p->lanes_per_line != 4 && p->lanes_per_line != 8 && p->lanes_per_line != 16 &&
+        p->lanes_per_line != 32) {
+        g_create_error = "lanes_per_line must be 0, 4, 8, 16 or 32";
+        return SC_EINVAL;
+    }
+    sc_ctx *ctx = new (std::nothrow) sc_ctx();
+    if (!ctx) {
+        g_create_error = "host allocation failed";
+        return SC_ENOMEM;
+    }
+    std::string why = ctx->geo.build(*p);
+    if (!why.empty()) {
+        g_create_error = why;
+        delete ctx;
+        return SC_EINVAL;
+    }
+    const scg::Geometry &G = ctx->geo;
+    ctx->fp64 = p->precision == SC_PREC_FP64;
+    ctx->real_bytes = ctx->fp64 ? 8 : 4;
+    ctx->n_e = p->n_energies;
+    ctx->forced_lanes = p->lanes_per_line;
+    {
+        double s = 0.0;
+        for (int n = 0; n < ctx->n_e; ++n) s += 1.0 / (2.0 * n + 1.0);
+        ctx->normD = std::log(p->t) + 2.0 * s;
+    }
+    if (p->host_only) {
+        ctx->host_only = true;
+        *out = ctx;
+        return SC_OK;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        delete ctx;
+        return SC_ECUDA;
+    }
+    // grid description for the kernels
+    scd::GridDev &gd = ctx->grid;
+    gd.nx = G.nx;
+    gd.ny = G.ny;
+    gd.h = p->h;
+    gd.x0 = p->x0;
+    gd.y0 = p->y0;
+    gd.ox = G.ox;
+    gd.oy = G.oy;
+    gd.bfield = M_PI * p->flux_quanta / G.area;  // B = pi alpha / area in units of B0
+    gd.gx = p->gauge_cx;
+    gd.gy = p->gauge_cy;
+    gd.charge_sign = p->charge_sign;
+
+    // host tables
+    const int P = G.n_pairs;
+    const size_t nL = G.lines.size();
+    std::vector<scd::LineGeo> lgeo(nL);
+    std::vector<scd::LineDev> ldev(nL);
+    std::vector<scd::BackLine> lback(nL);
+    std::vector<int32_t> slot_line(G.n_slots);
+    for (size_t L = 0; L < nL; ++L) {
+        const scg::LineInfo &li = G.lines[L];
+        scd::LineGeo &lg = lgeo[L];
+        lg.pair = li.pair;
+        lg.l = li.l;
+        lg.m0 = li.m0;
+        lg.ns = li.ns;
+        lg.slot0 = li.slot0;
+        lg.pad = 0;
+        lg.smid = 0.5 * (li.smin + li.smax);
+        for (int q = 0; q < std::max(li.ns, 1); ++q) slot_line[li.slot0 + q] = (int32_t)L;
+        scd::LineDev &ld = ldev[L];
+        ld.ns = li.ns;
+        ld.slot0 = li.slot0;
+        ld.exit_f = (int32_t)L;
+        ld.exit_b = (int32_t)(nL + L);
+        if (li.ns > 0) {
+            ld.lead = std::max(0.0, li.m0 * p->h - li.smin);
+            ld.tail = std::max(0.0, li.smax - li.m1 * p->h);
+        } else {
+            ld.lead = ld.tail = li.smax - li.smin;
+        }
+        for (int q = 0; q < 4; ++q) {
+            ld.tap_f[q] = li.fwd[q].slot;
+            ld.w_f[q] = li.fwd[q].w;
+            ld.tap_b[q] = li.bwd[q].slot;
+            ld.w_b[q] = li.bwd[q].w;
+        }
+        const scg::LineInfo &nn = G.lines[li.nearest];
+        lback[L] = scd::BackLine{li.nearest, nn.m0, nn.ns, nn.slot0};
+    }
+    std::vector<scd::PairDev> pdev(P);
+    const double cx = 0.5 + (p->x0 - G.ox) / p->h, cy = 0.5 + (p->y0 - G.oy) / p->h;
+    for (int q = 0; q < P; ++q) {
+        const scg::PairInfo &pp = G.pairs[q];
+        scd::PairDev &d = pdev[q];
+        d.ex = pp.ex;
+        d.ey = pp.ey;
+        d.u0 = cx * (-pp.ey) + cy * pp.ex;  // (R - O).e_perp / h at grid point (0, 0)
+        d.v0 = cx * pp.ex + cy * pp.ey;
+        d.eta = pp.eta;
+        d.wa = G.weight[q];
+        d.wb = G.weight[q + P];
+        d.l_lo = pp.l_lo;
+        d.l_hi = pp.l_hi;
+        d.line0 = pp.line0;
+        d.pad = 0;
+    }
+
+    // device memory
+    const size_t np = npts(ctx);
+    const size_t t4 = ctx->fp64 ? 32 : 16;
+    const size_t cplx = 2 * ctx->real_bytes;
+    auto fail_cuda = [&](cudaError_t err, const char *what) {
+        g_create_error = std::string(what) + ": " + cudaGetErrorString(err);
+        sc_status st = err == cudaErrorMemoryAllocation ? SC_ENOMEM : SC_ECUDA;
+        sc_destroy(ctx);
+        return st;
+    };
+#define CA(ptr, bytes)                                      \
+    do {                                                    \
+        cudaError_t err_ = dalloc(ctx, &(ptr), (bytes));    \
+        if (err_ != cudaSuccess) return fail_cuda(err_, #ptr); \
+    } while (0)
+#define CP(dst, src, bytes)                                                      \
+    do {                                                                         \
+        cudaError_t err_ = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice); \
+        if (err_ != cudaSuccess) return fail_cuda(err_, "upload " #dst);        \
+    } while (0)
+    CA(ctx->d_mask, np);
+    CP(ctx->d_mask, G.mask.data(), np);
+    CA(ctx->d_ghost, G.ghost.size() * sizeof(int32_t));
+    CP(ctx->d_ghost, G.ghost.data(), G.ghost.size() * sizeof(int32_t));
+    CA(ctx->d_geo, nL * sizeof(scd::LineGeo));
+    CP(ctx->d_geo, lgeo.data(), nL * sizeof(scd::LineGeo));
+    CA(ctx->d_lines, nL * sizeof(scd::LineDev));
+    CP(ctx->d_lines, ldev.data(), nL * sizeof(scd::LineDev));
+    CA(ctx->d_back, nL * sizeof(scd::BackLine));
+    CP(ctx->d_back, lback.data(), nL * sizeof(scd::BackLine));
+    CA(ctx->d_slot_line, slot_line.size() * sizeof(int32_t));
+    CP(ctx->d_slot_line, slot_line.data(), slot_line.size() * sizeof(int32_t));
+    CA(ctx->d_pairs, P * sizeof(scd::PairDev));
+    CP(ctx->d_pairs, pdev.data(), P * sizeof(scd::PairDev));
+    CA(ctx->d_delta, 2 * np * sizeof(double));
+    CA(ctx->d_aind, 2 * np * sizeof(double));
+    CA(ctx->d_acc, 5 * np * sizeof(double));
+    CA(ctx->d_dnew, 2 * np * sizeof(double));
+    CA(ctx->d_j, 2 * np * sizeof(double));
+    CA(ctx->d_F, np * sizeof(double));
+    CA(ctx->d_sums, 8 * sizeof(double));
+    CA(ctx->d_jsum, 2 * sizeof(double));
+    CA(ctx->d_diff, sizeof(double));
+    CA(ctx->d_counter, sizeof(int32_t));
+    CA(ctx->d_img_in, G.n_slots * t4);
+    CA(ctx->d_img_out, G.n_slots * t4);
+    for (int b = 0; b < 2; ++b) CA(ctx->d_exit[b], 2 * nL * (size_t)ctx->n_e * cplx);
+    {
+        cudaError_t err = cudaMemset(ctx->d_delta, 0, 2 * np * sizeof(double));
+        if (err == cudaSuccess) err = cudaMemset(ctx->d_aind, 0, 2 * np * sizeof(double));
+        if (err == cudaSuccess) err = cudaMemset(ctx->d_img_out, 0, G.n_slots * t4);
+        if (err != cudaSuccess) return fail_cuda(err, "memset");
+    }
+    const double kappa = p->kappa;
+    if (kappa > 0.0 && std::isfinite(kappa)) {
+        // cell-integrated Green's function of the 2D Laplacian (App. D)
+        const int W = std::max(G.nx, G.ny);
+        ctx->G_width = W;
+        std::vector<double> Gt((size_t)W * W);
+        const double h = p->h;
+        auto alpha = [](double m, double n) {
+            return (1 + 2 * m) * (1 + 2 * n) * std::log(0.5 * (1 + 2 * m) * (1 + 2 * m) + 0.5 * (1 + 2 * n) * (1 + 2 * n));
+        };
+        auto beta = [](double m, double n) { return (-2 * m * m + 2 * n * n + 4 * n + 1) * std::atan((1 + 2 * m) / (1 + 2 * n)); };
+        for (int a = 0; a < W; ++a)
+            for (int b = 0; b < W; ++b) {
+                double s = 0.0;
+                for (int sa = -1; sa <= 1; sa += 2)
+                    for (int sb = -1; sb <= 1; sb += 2) {
+                        const double m = sa * (double)a, n = sb * (double)b;
+                        s += alpha(m, n) + beta(m, n) + beta(n, m);
+                    }
+                Gt[(size_t)a * W + b] = h * h / (4 * M_PI) * (2 * std::log(h) - std::log(2.0) - 3 + 0.25 * s);
+            }
+        CA(ctx->d_G, Gt.size() * sizeof(double));
+        CP(ctx->d_G, Gt.data(), Gt.size() * sizeof(double));
+    }
+#undef CA
+#undef CP
+    sc_status st = make_plan(ctx, ctx->n_e, &ctx->main_plan);
+    if (st != SC_OK) {
+        g_create_error = ctx->err;
+        sc_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return SC_OK;
+}
+
+sc_status sc_get_info(const sc_ctx *ctx, sc_info *info) {
+    if (!ctx || !info) return SC_EINVAL;
+    const scg::Geometry &G = ctx->geo;
+    std::memset(info, 0, sizeof *info);
+    info->n_pairs = G.n_pairs;
+    info->n_lines = (int32_t)G.lines.size();
+    info->n_samples = G.n_samples;
+    info->n_in = G.n_in;
+    int64_t steps = 0;
+    for (const auto &li : G.lines) steps += 2 * (int64_t)(li.ns + 1);
+    info->steps_per_sweep = steps * ctx->n_e;
+    info->points_per_sweep = 2 * G.n_samples * ctx->n_e;
+    info->area = G.area;
+    info->norm_D = ctx->normD;
+    if (ctx->main_plan) {
+        info->lanes_per_line = ctx->main_plan->lanes;
+        info->energies_per_lane = ctx->main_plan->ept;
+        info->lines_per_warp = ctx->main_plan->lines_per_warp;
+    }
+    info->scratch_bytes = (int64_t)ctx->scratch_bytes;
+    return SC_OK;
+}
+
+sc_status sc_get_mask(const sc_ctx *ctx, uint8_t *mask) {
+    if (!ctx || !mask) return SC_EINVAL;
+    std::memcpy(mask, ctx->geo.mask.data(), ctx->geo.mask.size());
+    return SC_OK;
+}
+
+sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!delta) return set_err(ctx, SC_EINVAL, "delta is required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 2 * npts(ctx) * sizeof(double);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->d_delta, delta, bytes, k, st));
+    if (a_ind) {
+        CK(cudaMemcpyAsync(ctx->d_aind, a_ind, bytes, k, st));
+        ctx->have_aind = true;
+    } else {
+        CK(cudaMemsetAsync(ctx->d_aind, 0, bytes, st));
+        ctx->have_aind = false;
+    }
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    ctx->have_sweep = false;
+    ctx->have_outputs = false;
+    return SC_OK;
+}
+
+sc_status sc_reset_boundary(sc_ctx *ctx) {
+    CKS(check_ctx(ctx));
+    ctx->have_boundary = false;
+    return SC_OK;
+}
+
+sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nxt = 1 - ctx->cur;
+    CKS(run_sweep(ctx, *ctx->main_plan, ctx->n_e, false, nullptr, 0.0, ctx->d_img_out, ctx->d_exit[ctx->cur],
+                  ctx->d_exit[nxt], !ctx->have_boundary, st));
+    CK(scd::launch_rotate_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                               ctx->d_img_out, ctx->d_acc, st));
+    ctx->cur = nxt;
+    ctx->have_boundary = true;
+    ctx->have_sweep = true;
+    ctx->have_outputs = false;
+    return SC_OK;
+}
+
+sc_status sc_burnin(sc_ctx *ctx, int32_t max_sweeps, double tol, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = 2 * (int64_t)ctx->geo.lines.size() * ctx->n_e;
+    for (int it = 0; it < max_sweeps; ++it) {
+        const bool had = ctx->have_boundary;
+        CKS(sc_riccati_sweep(ctx, stream));
+        if (!had) continue;
+        CK(scd::launch_max_diff(n, ctx->d_exit[ctx->cur], ctx->d_exit[1 - ctx->cur], ctx->fp64, ctx->d_diff, st));
+        double diff = 0.0;
+        CK(cudaMemcpyAsync(&diff, ctx->d_diff, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (diff <= tol) return SC_OK;
+    }
+    return max_sweeps > 0 ? SC_ENOTCONV : SC_OK;
+}
+
+sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_outputs(ctx, st));
+    CKS(copy_out(ctx, delta_out, ctx->d_dnew, 2 * npts(ctx) * sizeof(double), on_device, st));
+    if (eps_G) {
+        double s[4];
+        CK(cudaMemcpyAsync(s, ctx->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (s[3] != 0.0) return set_err(ctx, SC_ENUMERIC, "non-finite values in the sweep outputs");
+        *eps_G = s[1] > 0.0 ? std::sqrt(s[0] / s[1]) : 0.0;
+    }
+    return SC_OK;
+}
+
+sc_status sc_current(sc_ctx *ctx, double *j_out, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_outputs(ctx, st));
+    return copy_out(ctx, j_out, ctx->d_j, 2 * npts(ctx) * sizeof(double), on_device, st);
+}
+
+sc_status sc_free_energy(sc_ctx *ctx, double *F_total, double *density_out, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_outputs(ctx, st));
+    CKS(copy_out(ctx, density_out, ctx->d_F, npts(ctx) * sizeof(double), on_device, st));
+    if (F_total) {
+        double s[4];
+        CK(cudaMemcpyAsync(s, ctx->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (s[3] != 0.0) return set_err(ctx, SC_ENUMERIC, "non-finite values in the sweep outputs");
+        *F_total = s[2] / (double)ctx->geo.n_in;
+    }
+    return SC_OK;
+}
+
+sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!ctx->d_G) return SC_OK;  // kappa <= 0: no induced field
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_outputs(ctx, st));
+    CK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, st));
+    const double k = ctx->geo.prm.kappa;
+    CK(scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in, ctx->d_G,
+                                    ctx->G_width, 1.0 / (k * k), ctx->d_aind, st));
+    ctx->have_aind = true;
+    return SC_OK;
+}
+
+sc_status sc_picard_step(sc_ctx *ctx, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    CKS(ensure_outputs(ctx, st));
+    if (ctx->d_G) CKS(sc_update_vector_potential(ctx, stream));
+    CK(scd::launch_copy_delta(2 * (int64_t)npts(ctx), ctx->d_dnew, ctx->d_delta, st));
+    ctx->have_sweep = false;
+    ctx->have_outputs = false;
+    return SC_OK;
+}
+
+sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening, int32_t n_burnin,
+                  double *ldos_out, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!energies || n_e < 1 || !ldos_out) return set_err(ctx, SC_EINVAL, "energies and ldos_out are required");
+    if (!(broadening > 0.0)) return set_err(ctx, SC_EINVAL, "broadening must be > 0");
+    for (int k = 0; k < n_e; ++k)
+        if (std::fabs(energies[k] + energies[n_e - 1 - k]) > 1e-12 * (1.0 + std::fabs(energies[k])))
+            return set_err(ctx, SC_EINVAL, "energies must be symmetric about zero");
+    cudaStream_t st = (cudaStream_t)stream;
+    Plan *pl = nullptr;
+    CKS(make_plan(ctx, n_e, &pl));
+    const size_t nL = ctx->geo.lines.size();
+    const size_t cplx = 2 * ctx->real_bytes;
+    double *d_en = nullptr;
+    void *d_ex[2] = {nullptr, nullptr};
+    void *d_img = nullptr;
+    double *d_out = nullptr;
+    sc_status rc = SC_OK;
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(st);
+        dfree(ctx, d_en);
+        dfree(ctx, d_ex[0]);
+        dfree(ctx, d_ex[1]);
+        dfree(ctx, d_img);
+        if (d_out != ldos_out) dfree(ctx, d_out);
+    };
+    do {
+        cudaError_t e;
+        if ((e = dalloc(ctx, &d_en, n_e * sizeof(double))) != cudaSuccess ||
+            (e = dalloc(ctx, &d_ex[0], 2 * nL * n_e * cplx)) != cudaSuccess ||
+            (e = dalloc(ctx, &d_ex[1], 2 * nL * n_e * cplx)) != cudaSuccess ||
+            (e = dalloc(ctx, &d_img, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ENOMEM, std::string("ldos buffers: ") + cudaGetErrorString(e));
+            break;
+        }
+        if (on_device) d_out = ldos_out;
+        else if ((e = dalloc(ctx, &d_out, (size_t)n_e * npts(ctx) * sizeof(double))) != cudaSuccess) {
+            rc = set_err(ctx, SC_ENOMEM, "ldos output");
+            break;
+        }
+        if ((e = cudaMemcpyAsync(d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        int c = 0;
+        const int nb = std::max(1, n_burnin);
+        for (int it = 0; it < nb && rc == SC_OK; ++it) {
+            rc = run_sweep(ctx, *pl, n_e, true, d_en, broadening, d_img, d_ex[c], d_ex[1 - c], it == 0, st);
+            c = 1 - c;
+        }
+        if (rc != SC_OK) break;
+        if ((e = scd::launch_ldos_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                       d_img, n_e, d_out, st)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        if (!on_device) {
+            if ((e = cudaMemcpyAsync(ldos_out, d_out, (size_t)n_e * npts(ctx) * sizeof(double), cudaMemcpyDeviceToHost,
+                                     st)) != cudaSuccess) {
+                rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+                break;
+            }
+        }
+    } while (0);
+    cleanup();
+    return rc;
+}
+
+// ---- inspection ----------------------------------------------------------
+sc_status sc_debug_lines(const sc_ctx *ctx, int32_t *l_lo, int32_t *l_hi, double *smin, double *smax, int32_t *m0,
+                         int32_t *m1) {
+    if (!ctx) return SC_EINVAL;
+    const scg::Geometry &G = ctx->geo;
+    for (int q = 0; q < G.n_pairs; ++q) {
+        if (l_lo) l_lo[q] = G.pairs[q].l_lo;
+        if (l_hi) l_hi[q] = G.pairs[q].l_hi;
+    }
+    for (size_t L = 0; L < G.lines.size(); ++L) {
+        if (smin) smin[L] = G.lines[L].smin;
+        if (smax) smax[L] = G.lines[L].smax;
+        if (m0) m0[L] = G.lines[L].m0;
+        if (m1) m1[L] = G.lines[L].m1;
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_ghost(const sc_ctx *ctx, int32_t *ghost) {
+    if (!ctx || !ghost) return SC_EINVAL;
+    std::memcpy(ghost, ctx->geo.ghost.data(), ctx->geo.ghost.size() * sizeof(int32_t));
+    return SC_OK;
+}
+
+sc_status sc_debug_links(const sc_ctx *ctx, int32_t *ta, int32_t *tl, double *tw) {
+    if (!ctx) return SC_EINVAL;
+    const scg::Geometry &G = ctx->geo;
+    size_t o = 0;
+    for (int k = 0; k < G.n_angles; ++k) {
+        const scg::PairInfo &pp = G.pairs[k % G.n_pairs];
+        for (int l = pp.l_lo; l <= pp.l_hi; ++l) {
+            const scg::LineInfo &li = G.lines[pp.line0 + l - pp.l_lo];
+            for (int q = 0; q < 4; ++q, ++o) {
+                const bool f = k < G.n_pairs;
+                if (ta) ta[o] = f ? li.dbg_fwd_angle[q] : li.dbg_bwd_angle[q];
+                if (tl) tl[o] = f ? li.dbg_fwd_line[q] : li.dbg_bwd_line[q];
+                if (tw) tw[o] = f ? li.fwd[q].w : li.bwd[q].w;
+            }
+        }
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_exits(sc_ctx *ctx, double *exits) {
+    CKS(check_ctx(ctx));
+    if (!exits) return SC_EINVAL;
+    const size_t nL = ctx->geo.lines.size();
+    const size_t n = 2 * nL * ctx->n_e;  // complex values, [angle half][line][energy]
+    std::vector<char> buf(n * 2 * ctx->real_bytes);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(buf.data(), ctx->d_exit[ctx->cur], buf.size(), cudaMemcpyDeviceToHost));
+    // slots: [0, nL) = angle p (pair-major lines) ; [nL, 2nL) = angle p + P
+    const scg::Geometry &G = ctx->geo;
+    size_t o = 0;
+    for (int k = 0; k < G.n_angles; ++k) {
+        const scg::PairInfo &pp = G.pairs[k % G.n_pairs];
+        for (int l = pp.l_lo; l <= pp.l_hi; ++l) {
+            const size_t L = pp.line0 + l - pp.l_lo;
+            const size_t slot = k < G.n_pairs ? L : nL + L;
+            for (int n2 = 0; n2 < ctx->n_e; ++n2, ++o) {
+                const size_t i = slot * ctx->n_e + n2;
+                if (ctx->fp64) {
+                    exits[2 * o] = ((double *)buf.data())[2 * i];
+                    exits[2 * o + 1] = ((double *)buf.data())[2 * i + 1];
+                } else {
+                    exits[2 * o] = ((float *)buf.data())[2 * i];
+                    exits[2 * o + 1] = ((float *)buf.data())[2 * i + 1];
+                }
+            }
+        }
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_images(sc_ctx *ctx, double *images) {
+    CKS(check_ctx(ctx));
+    if (!images) return SC_EINVAL;
+    const scg::Geometry &G = ctx->geo;
+    std::vector<char> buf(G.n_slots * (ctx->fp64 ? 32 : 16));
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(buf.data(), ctx->d_img_out, buf.size(), cudaMemcpyDeviceToHost));
+    size_t o = 0;
+    for (const auto &li : G.lines) {
+        for (int q = 0; q < li.ns; ++q, ++o)
+            for (int c = 0; c < 4; ++c) {
+                const size_t i = 4 * (size_t)(li.slot0 + q) + c;
+                images[4 * o + c] = ctx->fp64 ? ((double *)buf.data())[i] : ((float *)buf.data())[i];
+            }
+    }
+    return SC_OK;
+}
+
+}  // extern "C"

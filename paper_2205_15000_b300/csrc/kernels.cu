@@ -1,0 +1,843 @@
+// CUDA kernels of the Riccati sweep (sm_103a).
+//
+//  rotate_fields  grid Delta(R), A(R) -> per-slot (Delta eta, sigma v.A) on the
+//                 rotated lattices (bilinear, nearest-grain-point fill)      [Sec. 3.1]
+//  sweep          per (line, energy): gamma along +e_par (angle p) and gamma along
+//                 -e_par (angle p+P, = conj gamma~ of angle p), closed-form steps,
+//                 propagator and energy sums fused into the backward pass   [Eqs. riccati,
+//                 riccati_tilde, riccati_parameterization, symmetries; App. C]
+//  rotate_back    per grid point: bilinear gather of every pair's image and the
+//                 Fermi-surface sum                                         [Sec. 3.1]
+//  outputs        gap equation, current, free energy, residual norms      [Eqs. gapeq_fixpoint,
+//                                                                            current_density, qcLWFE]
+//  vector_pot     A_ind = -(1/kappa^2) G * (j - <j>)                        [App. D]
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace scd {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Precision traits: FP32 uses the approximate PTX unit instructions, FP64 the
+// IEEE-accurate library functions (the plain FP64 sweep).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Mth;
+
+template <>
+struct Mth<float> {
+    static __device__ __forceinline__ float rcp(float v) {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    static __device__ __forceinline__ float rsqrt(float v) {
+        float r;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    static __device__ __forceinline__ float sqrt(float v) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    static __device__ __forceinline__ float expneg(float u) {  // exp(-u) = 2^(-u log2 e)
+        float r;
+        const float x = -u * 1.4426950408889634f;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ void sincos_(float x, float *s, float *c) {
+        asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+        asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+    }
+};
+
+template <>
+struct Mth<double> {
+    static __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+    static __device__ __forceinline__ double rsqrt(double v) { return 1.0 / ::sqrt(v); }
+    static __device__ __forceinline__ double sqrt(double v) { return ::sqrt(v); }
+    static __device__ __forceinline__ double expneg(double u) { return ::exp(-u); }
+    static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { ::sincos(x, s, c); }
+};
+
+template <typename T>
+struct Cx {
+    T x, y;
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    typedef float4 type;
+};
+template <>
+struct Vec4<double> {
+    typedef double4_32a type;
+};
+
+// Coefficients of one closed-form step over a segment with constant Delta and
+// z (stepping method, App. C).  For d gamma/ds = i (Delta* g^2 + 2 z g + Delta):
+//   Omega   = sqrt(|Delta|^2 - z^2)          principal branch, Re Omega >= 0
+//   gamma_h = -Delta / (z + i Omega)          fixed point that is stable along s
+//   E = exp(-2 Omega ell),  K = i Delta* (1 - E) / (2 Omega)
+//   gamma'  = gamma_h + (gamma - gamma_h) E / (1 - K (gamma - gamma_h))
+// (gamma - gamma_h obeys a Bernoulli equation whose solution is this Moebius map.)
+template <typename T>
+struct StepCoef {
+    Cx<T> gh, E, K;
+};
+
+template <typename T>
+__device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, StepCoef<T> &c) {
+    typedef Mth<T> M;
+    const T x = d2 - zr * zr + zi * zi;  // Re Omega^2
+    const T y = T(-2) * zr * zi;         // Im Omega^2
+    const T r = M::sqrt(x * x + y * y);
+    const T hs = T(0.5) * (r + fabs(x));
+    const T q = M::rsqrt(hs);            // 1/s
+    const T s = hs * q;                  // s = sqrt((r + |x|)/2)
+    const T yq = T(0.5) * y * q;         // y / (2 s)
+    T Or, Oi;
+    if (x >= T(0)) {
+        Or = s;
+        Oi = yq;
+    } else {
+        Or = fabs(yq);
+        Oi = copysign(s, y);
+    }
+    const T wr = zr - Oi, wi = zi + Or;  // w = z + i Omega
+    // a single reciprocal serves 1/w and 1/(2 Omega):  q = 1 / (2 Omega w)
+    const T mr = T(2) * (Or * wr - Oi * wi), mi = T(2) * (Or * wi + Oi * wr);
+    const T rm = M::rcp(mr * mr + mi * mi);
+    const T qr = mr * rm, qi = -mi * rm;
+    const T iwr = T(2) * (Or * qr - Oi * qi), iwi = T(2) * (Or * qi + Oi * qr);  // 1/w
+    const T i2r = wr * qr - wi * qi, i2i = wr * qi + wi * qr;                    // 1/(2 Omega)
+    c.gh.x = -(dr * iwr - di * iwi);
+    c.gh.y = -(dr * iwi + di * iwr);
+    const T eu = M::expneg(T(2) * ell * Or);
+    T sn, cs;
+    M::sincos_(T(2) * ell * Oi, &sn, &cs);
+    c.E.x = eu * cs;
+    c.E.y = -eu * sn;
+    const T omr = T(1) - c.E.x, omi = -c.E.y;  // 1 - E
+    const T ccr = omr * i2r - omi * i2i, cci = omr * i2i + omi * i2r;
+    c.K.x = -(dr * cci - di * ccr);  // K = i conj(Delta) (1 - E)/(2 Omega)
+    c.K.y = dr * ccr + di * cci;
+}
+
+template <typename T>
+__device__ __forceinline__ void step_apply(const StepCoef<T> &c, Cx<T> &g) {
+    const T dx = g.x - c.gh.x, dy = g.y - c.gh.y;
+    const T nr = dx * c.E.x - dy * c.E.y, ni = dx * c.E.y + dy * c.E.x;
+    const T dnr = T(1) - (c.K.x * dx - c.K.y * dy), dni = -(c.K.x * dy + c.K.y * dx);
+    const T rd = Mth<T>::rcp(dnr * dnr + dni * dni);
+    g.x = c.gh.x + (nr * dnr + ni * dni) * rd;
+    g.y = c.gh.y + (ni * dnr - nr * dni) * rd;
+}
+
+// ---------------------------------------------------------------------------
+// rotate_fields: one thread per image slot
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool bilinear(const GridDev &g, const int32_t *__restrict__ ghost,
+                                         const double *__restrict__ f, double x, double y,
+                                         double &o0, double &o1) {
+    const double gx = (x - g.x0) / g.h - 0.5, gy = (y - g.y0) / g.h - 0.5;
+    const double fi = floor(gx), fj = floor(gy);
+    const int i0 = (int)fi, j0 = (int)fj;
+    const double fx = gx - fi, fy = gy - fj;
+    o0 = o1 = 0.0;
+    if (i0 < -1 || i0 > g.nx - 1 || j0 < -1 || j0 > g.ny - 1) return false;
+    const int px = g.nx + 2;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const double w = (a ? fx : 1.0 - fx) * (b ? fy : 1.0 - fy);
+            const int src = ghost[(j0 + b + 1) * px + (i0 + a + 1)];
+            if (src < 0) {
+                if (w != 0.0) return false;
+                continue;
+            }
+            o0 += w * f[2 * (int64_t)src];
+            o1 += w * f[2 * (int64_t)src + 1];
+        }
+    return true;
+}
+
+template <typename T>
+__global__ void rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__restrict__ slot_line,
+                              int64_t n_slots, const PairDev *__restrict__ pairs, GridDev grid,
+                              const int32_t *__restrict__ ghost, const double *__restrict__ delta,
+                              const double *__restrict__ aind, typename Vec4<T>::type *out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    const LineGeo lg = geo[slot_line[s]];
+    const PairDev pp = pairs[lg.pair];
+    const double h = grid.h;
+    const double sc = lg.ns > 0 ? (double)(lg.m0 + (int)(s - lg.slot0)) * h : lg.smid;
+    const double lh = lg.l * h;
+    const double x = grid.ox + lh * (-pp.ey) + sc * pp.ex;
+    const double y = grid.oy + lh * pp.ex + sc * pp.ey;
+    double dr, di, ax = 0.0, ay = 0.0;
+    bool ok = bilinear(grid, ghost, delta, x, y, dr, di);
+    if (aind) ok = bilinear(grid, ghost, aind, x, y, ax, ay) && ok;
+    // external vector potential, symmetric gauge: A = B/2 (-(y - yg), x - xg)
+    ax += -0.5 * grid.bfield * (y - grid.gy);
+    ay += 0.5 * grid.bfield * (x - grid.gx);
+    const double a = grid.charge_sign * (pp.ex * ax + pp.ey * ay);
+    typename Vec4<T>::type o;
+    o.x = (T)(pp.eta * dr);
+    o.y = (T)(pp.eta * di);
+    o.z = (T)a;
+    o.w = ok ? T(0) : T(1);  // 1 flags a sample whose stencil left the grid
+    out[s] = o;
+}
+
+cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_line, int64_t n_slots,
+                          const PairDev *pairs, const GridDev &grid, const int32_t *ghost,
+                          const double *delta, const double *aind, void *image_in,
+                          cudaStream_t st) {
+    const int bs = 256;
+    const unsigned nb = (unsigned)((n_slots + bs - 1) / bs);
+    if (fp64)
+        rotate_kernel<double><<<nb, bs, 0, st>>>(geo, slot_line, n_slots, pairs, grid, ghost, delta,
+                                                 aind, (double4_32a *)image_in);
+    else
+        rotate_kernel<float><<<nb, bs, 0, st>>>(geo, slot_line, n_slots, pairs, grid, ghost, delta,
+                                                aind, (float4 *)image_in);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The sweep.  A warp owns G = 32 / Lw lines of one work item; each line gets Lw
+// lanes and each lane EPT energies (n = lane_in_line + Lw * e).  Persistent:
+// warps take items (longest lines first) from an atomic counter.
+//
+// Forward pass: gamma of angle p from smin to smax; gamma at every sample is
+// parked in the warp's scratch slab ([line][sample][energy]).
+// Backward pass: gamma of angle p + P from smax to smin; at each sample the
+// parked gamma and the new one give the propagator of both angles
+// (gamma~(p) = conj gamma(p + P), Eq. symmetries), summed over the lane's
+// energies and then over the line's lanes by shuffles.
+// ---------------------------------------------------------------------------
+template <typename T, int EPT, bool RET>
+__global__ void __launch_bounds__(128) sweep_kernel(SweepLaunch a) {
+    typedef typename Vec4<T>::type T4;
+    typedef Cx<T> C;
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int Lw = a.lanes_per_line, G = a.lines_per_warp;
+    const int gi = lane / Lw, r = lane - gi * Lw;
+    const T4 *__restrict__ img = (const T4 *)a.image_in;
+    const C *__restrict__ exit_prev = (const C *)a.exit_prev;
+    C *__restrict__ exit_cur = (C *)a.exit_cur;
+    C *slab = (C *)a.scratch + wid * a.scratch_stride + (int64_t)gi * a.max_ns * a.ne_pad;
+    const T h = (T)a.h;
+    const int n_e = a.n_e;
+
+    // the lane's energies: z = zr0 + i zi (+ a along the line)
+    T zr0[EPT], zi[EPT];
+    int nid[EPT], mir[EPT];
+    bool ev[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const int n = r + Lw * e;
+        ev[e] = n < n_e;
+        const int nn = ev[e] ? n : n_e - 1;
+        nid[e] = nn;
+        if (RET) {
+            zr0[e] = (T)a.energies[nn];
+            zi[e] = (T)a.broadening;
+            mir[e] = n_e - 1 - nn;
+        } else {
+            zr0[e] = T(0);
+            zi[e] = (T)(a.t * (nn + 0.5));
+            mir[e] = nn;
+        }
+    }
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(FULL_MASK, item, 0);
+        if (item >= a.n_groups) break;
+        const int L = a.groups[(int64_t)item * G + gi];
+        const bool lv = L >= 0;
+        const LineDev &ln = a.lines[lv ? L : 0];
+        const int ns = lv ? ln.ns : 0;
+        const int nsl = ns > 0 ? ns : 1;
+        const int nsteps = lv ? ns + 1 : 0;
+        int nmax = nsteps;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(FULL_MASK, nmax, off));
+        const T lead = (T)ln.lead, tail = (T)ln.tail;
+        const int slot0 = ln.slot0;
+        const T4 *li = img + slot0;
+
+        // ---------------- forward: angle p, along +e_par ----------------
+        C g[EPT];
+        T4 sp = li[0];
+        if (a.first_sweep) {
+            const T d2 = sp.x * sp.x + sp.y * sp.y;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                StepCoef<T> c;
+                step_coef<T>(sp.x, sp.y, d2, zr0[e] + sp.z, zi[e], lead, c);
+                g[e] = c.gh;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                T gx = 0, gy = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const C v = exit_prev[(int64_t)ln.tap_f[q] * n_e + nid[e]];
+                    const T w = (T)ln.w_f[q];
+                    gx += w * v.x;
+                    gy += w * v.y;
+                }
+                g[e].x = gx;
+                g[e].y = gy;
+            }
+        }
+        // segment i joins samples max(i-1, 0) and min(i, nsl-1); the end segments
+        // (i = 0 and i = ns) see a single sample
+        T4 sq = sp;                      // s[min(i, nsl-1)]
+        T4 sn = li[min(1, nsl - 1)];     // s[min(i+1, nsl-1)], prefetched
+        for (int i = 0; i < nsteps; ++i) {
+            const T dr = T(0.5) * (sp.x + sq.x), di = T(0.5) * (sp.y + sq.y);
+            const T av = T(0.5) * (sp.z + sq.z);
+            const T ell = (i == 0) ? lead : (i == ns ? tail : h);
+            const T d2 = dr * dr + di * di;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                StepCoef<T> c;
+                step_coef<T>(dr, di, d2, zr0[e] + av, zi[e], ell, c);
+                step_apply<T>(c, g[e]);
+            }
+            if (i < ns) {
+                C *dst = slab + (int64_t)i * a.ne_pad + r;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) dst[Lw * e] = g[e];
+            }
+            sp = sq;
+            sq = sn;
+            sn = li[min(i + 2, nsl - 1)];
+        }
+        if (lv) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (ev[e]) exit_cur[(int64_t)ln.exit_f * n_e + nid[e]] = g[e];
+        }
+
+        __syncwarp();  // parked gammas of other lanes are read in retarded mode
+
+        // ---------------- backward: angle p + P, along -e_par ----------------
+        // (a -> -a; samples visited nsl-1 ... 0)
+        T4 sh = li[nsl - 1];
+        if (a.first_sweep) {
+            const T d2 = sh.x * sh.x + sh.y * sh.y;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                StepCoef<T> c;
+                step_coef<T>(sh.x, sh.y, d2, zr0[e] - sh.z, zi[e], tail, c);
+                g[e] = c.gh;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                T gx = 0, gy = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const C v = exit_prev[(int64_t)ln.tap_b[q] * n_e + nid[e]];
+                    const T w = (T)ln.w_b[q];
+                    gx += w * v.x;
+                    gy += w * v.y;
+                }
+                g[e].x = gx;
+                g[e].y = gy;
+            }
+        }
+        // backward segment j joins samples min(nsl-j, nsl-1) and max(nsl-1-j, 0)
+        T4 slo = sh;                     // s[max(nsl-1-j, 0)] = sample reached (j < ns)
+        T4 snb = li[max(nsl - 2, 0)];    // prefetched s[max(nsl-2-j, 0)]
+        for (int j = 0; j < nmax; ++j) {
+            const bool act = j < nsteps;
+            const int qs = nsl - 1 - j;          // sample reached after this step
+            const bool comb = act && j < ns;     // a sample to combine at
+            C gf[EPT];
+            if (comb) {
+                const C *src = slab + (int64_t)qs * a.ne_pad;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) gf[e] = src[RET ? mir[e] : (r + Lw * e)];
+            }
+            if (act) {
+                const T dr = T(0.5) * (sh.x + slo.x), di = T(0.5) * (sh.y + slo.y);
+                const T av = T(0.5) * (sh.z + slo.z);
+                const T ell = (j == 0) ? tail : (j == ns ? lead : h);
+                const T d2 = dr * dr + di * di;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    StepCoef<T> c;
+                    step_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, c);
+                    step_apply<T>(c, g[e]);
+                }
+            }
+            if (!RET) {
+                // propagator of angle p from gamma = gf, gamma~ = conj(g):
+                //   D = 1 + gf conj(g);  f + conj f~ = -2 i pi (gf/D + g/conj D)
+                //   2 Re g = 4 pi Im(1/D);  2 Re I = 2 Im(conj(Delta)(gf + g))
+                T sfr = 0, sfi = 0, sg = 0, sFr = 0, sFi = 0;
+                if (comb) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        if (!ev[e]) continue;
+                        const C gb = g[e], ga = gf[e];
+                        const T pr = ga.x * gb.x + ga.y * gb.y;   // ga * conj(gb)
+                        const T pi_ = ga.y * gb.x - ga.x * gb.y;
+                        const T Dr = T(1) + pr, Di = pi_;
+                        const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
+                        const T ir = Dr * rD, ii = -Di * rD;      // 1/D
+                        sg += ii;
+                        // ga/D + gb conj(1/D)
+                        sfr += (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
+                        sfi += (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
+                        sFr += ga.x + gb.x;
+                        sFi += ga.y + gb.y;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    if (off >= Lw) continue;
+                    sfr += __shfl_xor_sync(FULL_MASK, sfr, off);
+                    sfi += __shfl_xor_sync(FULL_MASK, sfi, off);
+                    sg += __shfl_xor_sync(FULL_MASK, sg, off);
+                    sFr += __shfl_xor_sync(FULL_MASK, sFr, off);
+                    sFi += __shfl_xor_sync(FULL_MASK, sFi, off);
+                }
+                if (comb && r == 0) {
+                    const T twopi = T(6.283185307179586), fourpi = T(12.566370614359172);
+                    T4 o;
+                    o.x = twopi * sfi;                          // Re Sf
+                    o.y = -twopi * sfr;                         // Im Sf
+                    o.z = fourpi * sg;                          // Sg
+                    o.w = T(2) * (slo.x * sFi - slo.y * sFr);   // SF
+                    ((T4 *)a.image_out)[slot0 + qs] = o;
+                }
+            } else if (comb) {
+                // LDOS: -Im g / pi = Re[(1 - p)/(1 + p)] = 2 Re(1/D) - 1
+                T *outl = (T *)a.image_out + (int64_t)(slot0 + qs) * n_e;
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    if (!ev[e]) continue;
+                    const C gb = g[e], ga = gf[e];
+                    const T pr = ga.x * gb.x + ga.y * gb.y;
+                    const T pi_ = ga.y * gb.x - ga.x * gb.y;
+                    const T Dr = T(1) + pr, Di = pi_;
+                    const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
+                    outl[nid[e]] = T(2) * Dr * rD - T(1);
+                }
+            }
+            if (act) {
+                sh = slo;
+                slo = snb;
+                snb = li[max(nsl - 3 - j, 0)];
+            }
+        }
+        if (lv) {
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                if (ev[e]) exit_cur[(int64_t)ln.exit_b * n_e + nid[e]] = g[e];
+        }
+        __syncwarp();  // the slab is rewritten by the next item
+    }
+}
+
+template <typename T, bool RET>
+static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
+    dim3 grid(a.grid_blocks), block(a.block_threads);
+    switch (a.energies_per_lane) {
+#define SC_CASE(E) \
+    case E: sweep_kernel<T, E, RET><<<grid, block, 0, st>>>(a); break;
+        SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
+#undef SC_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t st) {
+    if (fp64) return a.retarded ? sweep_dispatch<double, true>(a, st) : sweep_dispatch<double, false>(a, st);
+    return a.retarded ? sweep_dispatch<float, true>(a, st) : sweep_dispatch<float, false>(a, st);
+}
+
+template <typename T, bool RET>
+static int occ_dispatch(int ept, int bs) {
+    int n = 0;
+    switch (ept) {
+#define SC_CASE(E) \
+    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET>, bs, 0); break;
+        SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
+#undef SC_CASE
+        default: n = 0;
+    }
+    return n;
+}
+
+int sweep_occupancy(bool fp64, int ept, int bs) {
+    // the larger of the Matsubara and retarded instantiations bounds both
+    const int a = fp64 ? occ_dispatch<double, false>(ept, bs) : occ_dispatch<float, false>(ept, bs);
+    const int b = fp64 ? occ_dispatch<double, true>(ept, bs) : occ_dispatch<float, true>(ept, bs);
+    return a < b ? a : b;
+}
+
+// ---------------------------------------------------------------------------
+// rotate_back: one thread per grid point.  For every pair the point's lattice
+// coordinates (u across lines, v along them) select two lines (clamped to the
+// pair's range, replaced by the nearest line with samples) and two samples on
+// each (clamped to the line); the bilinear mix of the four image slots enters
+// the Fermi-surface sums with the weights of both angles of the pair.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pairs,
+                                   const BackLine *__restrict__ bl, GridDev grid,
+                                   const uint8_t *__restrict__ mask,
+                                   const typename Vec4<T>::type *__restrict__ img,
+                                   double *__restrict__ acc) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npts) return;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    if (mask[idx]) {
+        const double fi = (double)(idx % grid.nx), fj = (double)(idx / grid.nx);
+        for (int p = 0; p < n_pairs; ++p) {
+            const PairDev pp = pairs[p];
+            const double u = fma(fi, -pp.ey, fma(fj, pp.ex, pp.u0));
+            const double v = fma(fi, pp.ex, fma(fj, pp.ey, pp.v0));
+            const double fu = floor(u), fv = floor(v);
+            const int iu = (int)fu, iv = (int)fv;
+            const double wu = u - fu, wv = v - fv;
+            double x0 = 0, x1 = 0, x2 = 0, x3 = 0;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
+                const BackLine L = bl[pp.line0 + (l - pp.l_lo)];
+                const double wl = b ? wu : 1.0 - wu;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int m = min(max(iv + c, L.m0), L.m0 + L.ns - 1);
+                    const typename Vec4<T>::type s = img[L.slot0 + (m - L.m0)];
+                    const double w = wl * (c ? wv : 1.0 - wv);
+                    x0 += w * (double)s.x;
+                    x1 += w * (double)s.y;
+                    x2 += w * (double)s.z;
+                    x3 += w * (double)s.w;
+                }
+            }
+            const double ws = pp.wa + pp.wb;
+            // S_f and S_F are the same at phi and phi + pi; S_g and v change sign
+            a0 += ws * pp.eta * x0;
+            a1 += ws * pp.eta * x1;
+            a2 += ws * pp.ex * x2;
+            a3 += ws * pp.ey * x2;
+            a4 += ws * x3;
+        }
+    }
+    acc[idx] = a0;
+    acc[npts + idx] = a1;
+    acc[2 * npts + idx] = a2;
+    acc[3 * npts + idx] = a3;
+    acc[4 * npts + idx] = a4;
+}
+
+cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
+                               const GridDev &grid, const uint8_t *mask, const void *image_out,
+                               double *acc, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int bs = 128;
+    const unsigned nb = (unsigned)((npts + bs - 1) / bs);
+    if (fp64)
+        rotate_back_kernel<double><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
+                                                      (const double4_32a *)image_out, acc);
+    else
+        rotate_back_kernel<float><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
+                                                     (const float4 *)image_out, acc);
+    return cudaGetLastError();
+}
+
+// LDOS rotate-back: N(R, eps_n) = sum_p [w_{p+P} X_p(n) + w_p X_p(mirror n)]
+template <typename T>
+__global__ void ldos_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pairs,
+                                 const BackLine *__restrict__ bl, GridDev grid,
+                                 const uint8_t *__restrict__ mask, const T *__restrict__ img,
+                                 int32_t n_e, double *__restrict__ out) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (idx >= npts) return;
+    double acc = 0.0;
+    if (mask[idx]) {
+        const double fi = (double)(idx % grid.nx), fj = (double)(idx / grid.nx);
+        const int nm = n_e - 1 - n;
+        for (int p = 0; p < n_pairs; ++p) {
+            const PairDev pp = pairs[p];
+            const double u = fma(fi, -pp.ey, fma(fj, pp.ex, pp.u0));
+            const double v = fma(fi, pp.ex, fma(fj, pp.ey, pp.v0));
+            const double fu = floor(u), fv = floor(v);
+            const int iu = (int)fu, iv = (int)fv;
+            const double wu = u - fu, wv = v - fv;
+            double xn = 0, xm = 0;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
+                const BackLine L = bl[pp.line0 + (l - pp.l_lo)];
+                const double wl = b ? wu : 1.0 - wu;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int m = min(max(iv + c, L.m0), L.m0 + L.ns - 1);
+                    const int64_t sl = (int64_t)(L.slot0 + (m - L.m0)) * n_e;
+                    const double w = wl * (c ? wv : 1.0 - wv);
+                    xn += w * (double)img[sl + n];
+                    xm += w * (double)img[sl + nm];
+                }
+            }
+            acc += pp.wb * xn + pp.wa * xm;
+        }
+    }
+    out[(int64_t)n * npts + idx] = acc;
+}
+
+cudaError_t launch_ldos_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
+                             const GridDev &grid, const uint8_t *mask, const void *img, int32_t n_e,
+                             double *out, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int bs = 128;
+    dim3 nb((unsigned)((npts + bs - 1) / bs), (unsigned)n_e);
+    if (fp64)
+        ldos_back_kernel<double><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, (const double *)img,
+                                                    n_e, out);
+    else
+        ldos_back_kernel<float><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, (const float *)img,
+                                                   n_e, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// outputs: Delta_new = (t/2pi) <eta Sf> / D, j = sigma (t/pi) <v Sg>,
+// F = |Delta|^2 D - (t/2) <SF> + (kappa^2/2) |curl A_ind|^2; block sums of the
+// residual, the norm, F and of non-finite values go to sums[0..3].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL_MASK, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    return s;
+}
+
+__global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
+                               const double *__restrict__ acc, const double *__restrict__ delta,
+                               const double *__restrict__ aind, double t, double normD, double kappa,
+                               double *__restrict__ dn, double *__restrict__ jo,
+                               double *__restrict__ F, double *__restrict__ sums) {
+    __shared__ double sh[32];
+    const int nx = grid.nx, ny = grid.ny;
+    const int64_t npts = (int64_t)nx * ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double num = 0, den = 0, fs = 0, bad = 0;
+    if (idx < npts) {
+        if (!mask[idx]) {
+            dn[2 * idx] = dn[2 * idx + 1] = 0.0;
+            jo[2 * idx] = jo[2 * idx + 1] = 0.0;
+            F[idx] = 0.0;
+        } else {
+            const double c = t / (2.0 * 3.141592653589793) / normD;
+            const double dr = c * acc[idx], di = c * acc[npts + idx];
+            dn[2 * idx] = dr;
+            dn[2 * idx + 1] = di;
+            const double cj = grid.charge_sign * t / 3.141592653589793;
+            jo[2 * idx] = cj * acc[2 * npts + idx];
+            jo[2 * idx + 1] = cj * acc[3 * npts + idx];
+            const double d0r = delta[2 * idx], d0i = delta[2 * idx + 1];
+            const double d2 = d0r * d0r + d0i * d0i;
+            double f = d2 * normD - 0.5 * t * acc[4 * npts + idx];
+            if (aind && kappa > 0.0) {
+                const int i = (int)(idx % nx), j = (int)(idx / nx);
+                const int ia = i > 0 ? i - 1 : i, ib = i < nx - 1 ? i + 1 : i;
+                const int ja = j > 0 ? j - 1 : j, jb = j < ny - 1 ? j + 1 : j;
+                const double dAy = (aind[2 * ((int64_t)j * nx + ib) + 1] - aind[2 * ((int64_t)j * nx + ia) + 1]) /
+                                   ((ib - ia) * grid.h);
+                const double dAx = (aind[2 * ((int64_t)jb * nx + i)] - aind[2 * ((int64_t)ja * nx + i)]) /
+                                   ((jb - ja) * grid.h);
+                const double B = dAy - dAx;
+                f += 0.5 * kappa * kappa * B * B;
+            }
+            F[idx] = f;
+            fs = f;
+            const double er = dr - d0r, ei = di - d0i;
+            num = er * er + ei * ei;
+            den = d2;
+            bad = (isfinite(dr) && isfinite(di) && isfinite(f) && isfinite(jo[2 * idx]) &&
+                   isfinite(jo[2 * idx + 1])) ? 0.0 : 1.0;
+        }
+    }
+    const double s0 = block_sum(num, sh);
+    const double s1 = block_sum(den, sh);
+    const double s2 = block_sum(fs, sh);
+    const double s3 = block_sum(bad, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[0], s0);
+        atomicAdd(&sums[1], s1);
+        atomicAdd(&sums[2], s2);
+        atomicAdd(&sums[3], s3);
+    }
+}
+
+cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
+                           const double *delta, const double *aind, double t, double normD,
+                           double kappa, double *delta_new, double *j, double *F, double *sums,
+                           cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    cudaError_t e = cudaMemsetAsync(sums, 0, 4 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int bs = 256;
+    outputs_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(grid, mask, acc, delta, aind, t,
+                                                                    normD, kappa, delta_new, j, F, sums);
+    return cudaGetLastError();
+}
+
+__global__ void mean_current_kernel(GridDev grid, const uint8_t *__restrict__ mask,
+                                    const double *__restrict__ j, double *sums) {
+    __shared__ double sh[32];
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double jx = 0, jy = 0;
+    if (idx < npts && mask[idx]) {
+        jx = j[2 * idx];
+        jy = j[2 * idx + 1];
+    }
+    const double sx = block_sum(jx, sh);
+    const double sy = block_sum(jy, sh);
+    if (threadIdx.x == 0) {
+        atomicAdd(&sums[0], sx);
+        atomicAdd(&sums[1], sy);
+    }
+}
+
+cudaError_t launch_mean_current(const GridDev &grid, const uint8_t *mask, const double *j,
+                                double *sums, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int bs = 256;
+    mean_current_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(grid, mask, j, sums);
+    return cudaGetLastError();
+}
+
+// A_ind(R) = -(1/kappa^2) sum_R' G(|dx|, |dy|) (j(R') - <j>)   (App. D, full correlation)
+// One thread per output point; sources staged through shared memory in tiles.
+__global__ void vector_potential_kernel(GridDev grid, const uint8_t *__restrict__ mask,
+                                        const double *__restrict__ j, const double *__restrict__ jsum,
+                                        double n_in, const double *__restrict__ G, int W,
+                                        double inv_k2, double *__restrict__ aind) {
+    __shared__ double sx[256], sy[256];
+    __shared__ int si[256], sj[256];
+    const int nx = grid.nx;
+    const int64_t npts = (int64_t)nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int xi = (int)(idx % nx), yi = (int)(idx / nx);
+    const double mx = jsum[0] / n_in, my = jsum[1] / n_in;
+    double ax = 0, ay = 0;
+    for (int64_t base = 0; base < npts; base += blockDim.x) {
+        const int64_t q = base + threadIdx.x;
+        __syncthreads();
+        if (q < npts && mask[q]) {
+            sx[threadIdx.x] = j[2 * q] - mx;
+            sy[threadIdx.x] = j[2 * q + 1] - my;
+        } else {
+            sx[threadIdx.x] = 0.0;
+            sy[threadIdx.x] = 0.0;
+        }
+        si[threadIdx.x] = (int)(q % nx);
+        sj[threadIdx.x] = (int)(q / nx);
+        __syncthreads();
+        const int cnt = (int)min((int64_t)blockDim.x, npts - base);
+        if (idx < npts) {
+            for (int k = 0; k < cnt; ++k) {
+                const double g = G[abs(si[k] - xi) * W + abs(sj[k] - yi)];
+                ax += g * sx[k];
+                ay += g * sy[k];
+            }
+        }
+    }
+    if (idx < npts) {
+        aind[2 * idx] = -inv_k2 * ax;
+        aind[2 * idx + 1] = -inv_k2 * ay;
+    }
+}
+
+cudaError_t launch_vector_potential(const GridDev &grid, const uint8_t *mask, const double *j,
+                                    const double *jsum, double n_in, const double *G, int W,
+                                    double inv_k2, double *aind, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int bs = 256;
+    vector_potential_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(grid, mask, j, jsum, n_in,
+                                                                             G, W, inv_k2, aind);
+    return cudaGetLastError();
+}
+
+__global__ void copy_kernel(int64_t n, const double *__restrict__ s, double *__restrict__ d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) d[i] = s[i];
+}
+
+cudaError_t launch_copy_delta(int64_t n, const double *src, double *dst, cudaStream_t st) {
+    const int bs = 256;
+    copy_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(n, src, dst);
+    return cudaGetLastError();
+}
+
+// max |a - b| over n complex values (boundary convergence of the burn-in)
+template <typename T>
+__global__ void max_diff_kernel(int64_t n, const T *__restrict__ a, const T *__restrict__ b,
+                                unsigned long long *out) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double m = 0.0;
+    for (int64_t i = i0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double dx = (double)a[2 * i] - (double)b[2 * i];
+        const double dy = (double)a[2 * i + 1] - (double)b[2 * i + 1];
+        const double d = sqrt(dx * dx + dy * dy);
+        m = (d > m || d != d) ? (d != d ? 1e300 : d) : m;
+    }
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(FULL_MASK, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_max_diff(int64_t n, const void *a, const void *b, bool fp64, double *out,
+                            cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const int bs = 256;
+    int nb = (int)((n + bs - 1) / bs);
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    if (fp64)
+        max_diff_kernel<double><<<nb, bs, 0, st>>>(n, (const double *)a, (const double *)b,
+                                                   (unsigned long long *)out);
+    else
+        max_diff_kernel<float><<<nb, bs, 0, st>>>(n, (const float *)a, (const float *)b,
+                                                  (unsigned long long *)out);
+    return cudaGetLastError();
+}
+
+}  // namespace scd

@@ -1,0 +1,103 @@
+// Device data layouts and kernel launchers of the Riccati sweep.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scd {
+
+// One trajectory line of an angle pair, as the sweep kernel reads it.
+struct LineDev {
+    int32_t ns;          // lattice samples on the line (0: one slot holds the chord midpoint)
+    int32_t slot0;       // first image slot of the line
+    int32_t exit_f;      // exit slot of angle p (at smax)
+    int32_t exit_b;      // exit slot of angle p + P (at smin)
+    double lead;         // smin -> first sample (chord length when ns == 0)
+    double tail;         // last sample -> smax (chord length when ns == 0)
+    int32_t tap_f[4];    // entry link of angle p: exit slots
+    int32_t tap_b[4];    // entry link of angle p + P
+    double w_f[4];
+    double w_b[4];
+};
+
+// Where the rotate kernel finds the position of every image slot.
+struct LineGeo {
+    int32_t pair, l, m0, ns, slot0, pad;
+    double smid;         // chord midpoint (position of the single slot when ns == 0)
+};
+
+// Per angle pair, for the rotate-back kernel.
+struct PairDev {
+    double ex, ey;       // e_par
+    double u0, v0;       // lattice coordinates (line, sample) of grid point (0, 0), units of h
+    double eta;          // basis function of the pair
+    double wa, wb;       // quadrature weights of angle p and of angle p + P
+    int32_t l_lo, l_hi, line0, pad;
+};
+
+// Per line, for the rotate-back kernel: nearest line with samples, its m0, ns, slot0.
+struct BackLine {
+    int32_t nearest, m0, ns, slot0;
+};
+
+struct GridDev {
+    int32_t nx, ny;
+    double h, x0, y0, ox, oy;
+    double bfield;       // external field, units of B0
+    double gx, gy;       // gauge origin
+    int32_t charge_sign;
+};
+
+struct SweepLaunch {
+    const LineDev *lines;
+    const int32_t *groups;     // [n_groups][lines_per_warp], -1 padded
+    int32_t n_groups;
+    int32_t lines_per_warp;    // G
+    int32_t lanes_per_line;    // Lw (G * Lw = 32)
+    int32_t energies_per_lane; // EPT (template)
+    int32_t n_e;
+    double t;                  // eps_n = t (n + 1/2)
+    double h;
+    const void *image_in;      // T4 per slot
+    void *image_out;           // T4 per slot
+    const void *exit_prev;     // complex T [2 n_lines][n_e]
+    void *exit_cur;
+    int32_t first_sweep;
+    void *scratch;             // per warp slab
+    int64_t scratch_stride;    // complex T elements per warp
+    int32_t max_ns;
+    int32_t ne_pad;            // Lw * EPT
+    int32_t *counter;
+    int32_t grid_blocks, block_threads;
+    // retarded (LDOS) mode: complex energies z_n = eps_n + i*delta, partner energy index
+    int32_t retarded;
+    const double *energies;    // n_e real energies (retarded mode)
+    double broadening;
+};
+
+// launchers (return cudaError_t)
+cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_line, int64_t n_slots,
+                          const PairDev *pairs, const GridDev &grid, const int32_t *ghost,
+                          const double *delta, const double *aind, void *image_in,
+                          cudaStream_t s);
+cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
+int sweep_occupancy(bool fp64, int ept, int block_threads);
+cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
+                               const BackLine *bl, const GridDev &grid, const uint8_t *mask,
+                               const void *image_out, double *acc, cudaStream_t s);
+cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
+                           const double *delta, const double *aind, double t, double normD,
+                           double kappa, double *delta_new, double *j, double *F,
+                           double *sums /* [4]: num, den, Fsum, nonfinite */, cudaStream_t s);
+cudaError_t launch_mean_current(const GridDev &grid, const uint8_t *mask, const double *j,
+                                double *sums /* [2] */, cudaStream_t s);
+cudaError_t launch_vector_potential(const GridDev &grid, const uint8_t *mask, const double *j,
+                                    const double *jsum, double n_in, const double *G, int W,
+                                    double inv_k2, double *aind, cudaStream_t s);
+cudaError_t launch_copy_delta(int64_t n, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_max_diff(int64_t n, const void *a, const void *b, bool fp64, double *out,
+                            cudaStream_t s);
+cudaError_t launch_ldos_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
+                             const BackLine *bl, const GridDev &grid, const uint8_t *mask,
+                             const void *ldos_img, int32_t n_e, double *out, cudaStream_t s);
+
+}  // namespace scd

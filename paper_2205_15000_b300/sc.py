@@ -1,0 +1,320 @@
+"""Thin Python binding of the C ABI in include/sc.h (libsc.so).
+
+Argument marshalling only: every step of the sweep runs in the library's CUDA
+kernels.  The functions keep the C names; ``Context`` bundles them for one
+grain.  Device buffers are torch tensors (plumbing: memory and streams).
+If the compiled library is missing this module raises on import -- there is
+no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsc.so")
+
+SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ETIMEOUT, SC_ENUMERIC, SC_ESTATE, SC_ENOTCONV = range(8)
+STATUS_NAMES = ["SC_OK", "SC_EINVAL", "SC_ENOMEM", "SC_ECUDA", "SC_ETIMEOUT", "SC_ENUMERIC",
+                "SC_ESTATE", "SC_ENOTCONV"]
+SC_PREC_FP64, SC_PREC_FP32 = 0, 1
+
+
+class ScError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class sc_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+        ("shape_kind", ctypes.c_int32),
+        ("disc_cx", ctypes.c_double), ("disc_cy", ctypes.c_double), ("disc_r", ctypes.c_double),
+        ("n_vert", ctypes.c_int32),
+        ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double)),
+        ("pairing", ctypes.c_int32), ("crystal_rotation", ctypes.c_double),
+        ("t", ctypes.c_double), ("flux_quanta", ctypes.c_double),
+        ("gauge_cx", ctypes.c_double), ("gauge_cy", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("charge_sign", ctypes.c_int32),
+        ("n_angles", ctypes.c_int32), ("n_energies", ctypes.c_int32),
+        ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
+        ("precision", ctypes.c_int32), ("lanes_per_line", ctypes.c_int32),
+        ("host_only", ctypes.c_int32),
+    ]
+
+
+class sc_info(ctypes.Structure):
+    _fields_ = [
+        ("n_pairs", ctypes.c_int32), ("n_lines", ctypes.c_int32),
+        ("n_samples", ctypes.c_int64), ("n_in", ctypes.c_int64),
+        ("steps_per_sweep", ctypes.c_int64), ("points_per_sweep", ctypes.c_int64),
+        ("area", ctypes.c_double), ("norm_D", ctypes.c_double),
+        ("lanes_per_line", ctypes.c_int32), ("energies_per_lane", ctypes.c_int32),
+        ("lines_per_warp", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
+    ]
+
+
+# every symbol include/sc.h declares
+EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_get_mask",
+            "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
+            "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
+            "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
+            "sc_debug_exits", "sc_debug_images", "sc_last_error", "sc_version"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsc.so not built ({LIB_PATH}); run python -m paper_2205_15000_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "sc_params_default": [P(sc_params)],
+        "sc_create": [P(sc_params), P(vp)],
+        "sc_destroy": [vp],
+        "sc_get_info": [vp, P(sc_info)],
+        "sc_get_mask": [vp, vp],
+        "sc_set_fields": [vp, vp, vp, ctypes.c_int, vp],
+        "sc_reset_boundary": [vp],
+        "sc_riccati_sweep": [vp, vp],
+        "sc_burnin": [vp, i32, f64, vp],
+        "sc_gap_update": [vp, vp, P(f64), ctypes.c_int, vp],
+        "sc_current": [vp, vp, ctypes.c_int, vp],
+        "sc_free_energy": [vp, P(f64), vp, ctypes.c_int, vp],
+        "sc_update_vector_potential": [vp, vp],
+        "sc_picard_step": [vp, vp],
+        "sc_ldos": [vp, vp, i32, f64, i32, vp, ctypes.c_int, vp],
+        "sc_debug_lines": [vp, vp, vp, vp, vp, vp, vp],
+        "sc_debug_ghost": [vp, vp],
+        "sc_debug_links": [vp, vp, vp, vp],
+        "sc_debug_exits": [vp, vp],
+        "sc_debug_images": [vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.sc_last_error.argtypes = [vp]
+    L.sc_last_error.restype = ctypes.c_char_p
+    L.sc_version.argtypes = []
+    L.sc_version.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(st, ctx=None):
+    if st != SC_OK:
+        raise ScError(st, lib.sc_last_error(ctx).decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def sc_version():
+    return lib.sc_version().decode()
+
+
+def sc_params_default():
+    p = sc_params()
+    _check(lib.sc_params_default(ctypes.byref(p)))
+    return p
+
+
+def make_params(d, precision="fp32", lanes_per_line=0, host_only=False):
+    """sc_params from a workload dict (keys of workloads.PARAM_KEYS).  The
+    vertex arrays are kept alive on the returned struct."""
+    p = sc_params_default()
+    for k in ("nx", "ny", "h", "x0", "y0", "shape_kind", "disc_cx", "disc_cy", "disc_r", "pairing",
+              "crystal_rotation", "t", "flux_quanta", "gauge_cx", "gauge_cy", "kappa", "charge_sign",
+              "n_angles", "n_energies", "lattice_ox", "lattice_oy"):
+        setattr(p, k, d[k])
+    vx = np.ascontiguousarray(d.get("vx", []) or [0.0], np.float64)
+    vy = np.ascontiguousarray(d.get("vy", []) or [0.0], np.float64)
+    p.n_vert = len(d.get("vx", [])) if d["shape_kind"] == 1 else 0
+    p.vx = vx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.vy = vy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p._keep = (vx, vy)
+    p.precision = SC_PREC_FP64 if precision == "fp64" else SC_PREC_FP32
+    p.lanes_per_line = lanes_per_line
+    p.host_only = 1 if host_only else 0
+    return p
+
+
+def sc_create(params):
+    h = ctypes.c_void_p()
+    _check(lib.sc_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def sc_destroy(ctx):
+    _check(lib.sc_destroy(ctx))
+
+
+def sc_get_info(ctx):
+    i = sc_info()
+    _check(lib.sc_get_info(ctx, ctypes.byref(i)), ctx)
+    return i
+
+
+def sc_set_fields(ctx, delta, a_ind=None, on_device=True, stream=None):
+    _check(lib.sc_set_fields(ctx, _ptr(delta), _ptr(a_ind), int(on_device), _stream(stream)), ctx)
+
+
+def sc_reset_boundary(ctx):
+    _check(lib.sc_reset_boundary(ctx), ctx)
+
+
+def sc_riccati_sweep(ctx, stream=None):
+    _check(lib.sc_riccati_sweep(ctx, _stream(stream)), ctx)
+
+
+def sc_burnin(ctx, max_sweeps, tol, stream=None):
+    st = lib.sc_burnin(ctx, int(max_sweeps), float(tol), _stream(stream))
+    if st not in (SC_OK, SC_ENOTCONV):
+        _check(st, ctx)
+    return st == SC_OK
+
+
+def sc_gap_update(ctx, delta_out, on_device=True, want_eps=False, stream=None):
+    eps = ctypes.c_double(0.0)
+    _check(lib.sc_gap_update(ctx, _ptr(delta_out), ctypes.byref(eps) if want_eps else None,
+                             int(on_device), _stream(stream)), ctx)
+    return eps.value if want_eps else None
+
+
+def sc_current(ctx, j_out, on_device=True, stream=None):
+    _check(lib.sc_current(ctx, _ptr(j_out), int(on_device), _stream(stream)), ctx)
+
+
+def sc_free_energy(ctx, density_out=None, on_device=True, want_total=True, stream=None):
+    F = ctypes.c_double(0.0)
+    _check(lib.sc_free_energy(ctx, ctypes.byref(F) if want_total else None, _ptr(density_out),
+                              int(on_device), _stream(stream)), ctx)
+    return F.value if want_total else None
+
+
+def sc_update_vector_potential(ctx, stream=None):
+    _check(lib.sc_update_vector_potential(ctx, _stream(stream)), ctx)
+
+
+def sc_picard_step(ctx, stream=None):
+    _check(lib.sc_picard_step(ctx, _stream(stream)), ctx)
+
+
+def sc_ldos(ctx, energies, broadening, n_burnin, ldos_out, on_device=True, stream=None):
+    e = np.ascontiguousarray(energies, np.float64)
+    _check(lib.sc_ldos(ctx, _ptr(e), len(e), float(broadening), int(n_burnin), _ptr(ldos_out),
+                       int(on_device), _stream(stream)), ctx)
+
+
+class Context:
+    """One grain: owns an sc_ctx.  Arrays in, arrays out (torch on the GPU)."""
+
+    def __init__(self, prm, precision="fp32", lanes_per_line=0, host_only=False):
+        self.prm = dict(prm)
+        self._p = make_params(prm, precision, lanes_per_line, host_only)
+        self.h = sc_create(self._p)
+        self.info = sc_get_info(self.h)
+        self.nx, self.ny = prm["nx"], prm["ny"]
+        self.n_e = prm["n_energies"]
+        self.N = prm["n_angles"]
+
+    def close(self):
+        if self.h:
+            sc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- geometry (host) --------------------------------------------------
+    def mask(self):
+        m = np.zeros((self.ny, self.nx), np.uint8)
+        _check(lib.sc_get_mask(self.h, _ptr(m)), self.h)
+        return m
+
+    def lines(self):
+        P, L = self.info.n_pairs, self.info.n_lines
+        lo, hi = np.zeros(P, np.int32), np.zeros(P, np.int32)
+        smin, smax = np.zeros(L), np.zeros(L)
+        m0, m1 = np.zeros(L, np.int32), np.zeros(L, np.int32)
+        _check(lib.sc_debug_lines(self.h, _ptr(lo), _ptr(hi), _ptr(smin), _ptr(smax), _ptr(m0),
+                                  _ptr(m1)), self.h)
+        return dict(l_lo=lo, l_hi=hi, smin=smin, smax=smax, m0=m0, m1=m1)
+
+    def ghost(self):
+        g = np.zeros((self.ny + 2, self.nx + 2), np.int32)
+        _check(lib.sc_debug_ghost(self.h, _ptr(g)), self.h)
+        return g
+
+    def links(self):
+        n = 4 * 2 * self.info.n_lines
+        ta, tl, tw = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
+        _check(lib.sc_debug_links(self.h, _ptr(ta), _ptr(tl), _ptr(tw)), self.h)
+        return dict(angle=ta.reshape(-1, 4), line=tl.reshape(-1, 4), w=tw.reshape(-1, 4))
+
+    # -- compute (device) -------------------------------------------------
+    def set_fields(self, delta, aind=None, stream=None):
+        import torch
+        d = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128, device="cuda").contiguous()).contiguous()
+        a = None
+        if aind is not None:
+            a = torch.as_tensor(aind, dtype=torch.float64, device="cuda").contiguous()
+        self._fields = (d, a)  # keep alive until the copy ran
+        sc_set_fields(self.h, d, a, True, stream)
+
+    def sweep(self, stream=None):
+        sc_riccati_sweep(self.h, stream)
+
+    def outputs(self, stream=None):
+        import torch
+        dn = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        j = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        F = torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
+        eps = sc_gap_update(self.h, dn, True, True, stream)
+        sc_current(self.h, j, True, stream)
+        Ft = sc_free_energy(self.h, F, True, True, stream)
+        return dict(delta_new=torch.view_as_complex(dn), j=j, F=F, F_total=Ft, eps_G=eps)
+
+    def exits(self):
+        out = np.zeros(2 * 2 * self.info.n_lines * self.n_e)
+        _check(lib.sc_debug_exits(self.h, _ptr(out)), self.h)
+        return out.view(np.complex128).reshape(2 * self.info.n_lines, self.n_e)
+
+    def images(self):
+        out = np.zeros(4 * self.info.n_samples)
+        _check(lib.sc_debug_images(self.h, _ptr(out)), self.h)
+        return out.reshape(-1, 4)
+
+    def ldos(self, energies, broadening, n_burnin=20, stream=None):
+        import torch
+        out = torch.empty((len(energies), self.ny, self.nx), dtype=torch.float64, device="cuda")
+        sc_ldos(self.h, energies, broadening, n_burnin, out, True, stream)
+        return out

@@ -1,0 +1,117 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol of
+include/sc.h, validates parameters, and its host-side discretisation (mask,
+nearest-grain-point map, rotated lattices, chords, specular links) equals the
+oracle's, decision for decision."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_15000_b300 import sc
+from paper_2205_15000_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "sc.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sc_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_symbols_exported():
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(sc.lib, n), n
+    assert sorted(sc.EXPORTED) == names
+
+
+def test_version_and_defaults():
+    assert "sm_103a" in sc.sc_version()
+    p = sc.sc_params_default()
+    assert p.n_angles == 32 and p.charge_sign == -1 and p.precision == sc.SC_PREC_FP32
+    assert abs(p.lattice_ox - 0.1) < 1e-15 and abs(p.lattice_oy - 0.2) < 1e-15
+
+
+@pytest.mark.parametrize("bad", [dict(n_angles=31), dict(t=0.0), dict(t=1.5), dict(n_energies=0),
+                                 dict(charge_sign=2), dict(disc_r=-1.0), dict(disc_r=40.0),
+                                 dict(h=-0.1)])
+def test_invalid_params_rejected(bad):
+    p = W.disc(5.0, 32, n_angles=8, n_energies=2)
+    p.update(bad)
+    with pytest.raises(sc.ScError) as ei:
+        sc.Context(p, host_only=True)
+    assert ei.value.status == sc.SC_EINVAL
+
+
+def test_nonconvex_polygon_rejected():
+    p = W.polygon([0.0, 4.0, 2.0, 4.0, 0.0], [0.0, 0.0, 1.0, 4.0, 4.0], 0.25, n_angles=8, n_energies=2)
+    with pytest.raises(sc.ScError) as ei:
+        sc.Context(p, host_only=True)
+    assert ei.value.status == sc.SC_EINVAL
+
+
+def test_clockwise_polygon_rejected():
+    p = W.polygon([0.0, 0.0, 4.0, 4.0], [0.0, 4.0, 4.0, 0.0], 0.25, n_angles=8, n_energies=2)
+    with pytest.raises(sc.ScError):
+        sc.Context(p, host_only=True)
+
+
+def test_compute_on_host_only_context_is_state_error():
+    c = sc.Context(W.disc(5.0, 32, n_angles=8, n_energies=2), host_only=True)
+    with pytest.raises(sc.ScError) as ei:
+        sc.sc_riccati_sweep(c.h)
+    assert ei.value.status == sc.SC_ESTATE
+
+
+GEOMS = {
+    "c1_square": lambda: W.c1_square_s()[0],
+    "c2_diamond": lambda: W.c2_diamond_d()[0],
+    "c4_disc": lambda: W.c4_disc_d()[0],
+    "disc_small": lambda: W.disc(1.6, 8, n_angles=4, n_energies=2),
+    "polygon": lambda: W.polygon([0.0, 7.0, 9.0, 2.0], [0.0, -1.0, 6.0, 8.0], 0.3, n_angles=12, n_energies=3),
+    "triangle": lambda: W.polygon([0.0, 5.0, 1.0], [0.0, 1.0, 4.0], 0.2, n_angles=18, n_energies=2),
+    "rotated": lambda: W.square(9.0, 50, rotation=0.3, n_angles=10, n_energies=2, crystal_rotation=0.1),
+}
+
+
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_geometry_matches_oracle(name):
+    p = GEOMS[name]()
+    c = sc.Context(p, host_only=True)
+    g = oracle.OracleGeom(p)
+    assert c.info.n_pairs == g.n_pairs and c.info.n_lines == g.n_lines
+    assert c.info.n_samples == g.n_samples and c.info.n_in == g.n_in
+    assert abs(c.info.area - g.area) < 1e-12 * g.area
+    np.testing.assert_array_equal(c.mask(), g.mask())
+    np.testing.assert_array_equal(c.ghost(), g.ghost())
+    a, b = c.lines(), g.lines()
+    for k in ("l_lo", "l_hi", "m0", "m1"):
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_allclose(a["smin"], b["smin"], atol=1e-12, rtol=0)
+    np.testing.assert_allclose(a["smax"], b["smax"], atol=1e-12, rtol=0)
+    la, lb = c.links(), g.links()
+    # taps with vanishing weight may differ by rounding of a floor(); compare weighted maps
+    assert la["w"].shape == lb["w"].shape
+    for A in range(la["w"].shape[0]):
+        da, db = {}, {}
+        for q in range(4):
+            ka = (la["angle"][A, q], la["line"][A, q])
+            kb = (lb["angle"][A, q], lb["line"][A, q])
+            da[ka] = da.get(ka, 0.0) + la["w"][A, q]
+            db[kb] = db.get(kb, 0.0) + lb["w"][A, q]
+        keys = set(da) | set(db)
+        for k in keys:
+            assert abs(da.get(k, 0.0) - db.get(k, 0.0)) < 1e-12, (A, k)
+
+
+def test_steps_per_sweep_count():
+    p = W.c1_square_s()[0]
+    c = sc.Context(p, host_only=True)
+    L = c.lines()
+    ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+    assert c.info.steps_per_sweep == p["n_energies"] * int(np.sum(2 * (ns + 1)))
+    assert c.info.points_per_sweep == 2 * p["n_energies"] * int(ns.sum())

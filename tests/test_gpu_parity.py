@@ -1,0 +1,197 @@
+"""Parity of the CUDA sweep (through the C ABI) with the FP64 oracle on the
+same seeded inputs.
+
+FP64 (plain sweep): every intermediate and output within 1e-10.
+FP32 (production sweep): relative error of Delta_new <= 1e-5, of j and F
+<= 1e-4 (max norm over the grain, relative to the oracle's max; j with an
+absolute floor of 1e-6 j0 for grains that carry almost no current).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_15000_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL_DELTA, TOL_J, TOL_F = 1e-5, 1e-4, 1e-4
+J_FLOOR = 1e-6
+
+
+def _sc():
+    from paper_2205_15000_b300 import sc
+    return sc
+
+
+def _smooth_a(p, amp, seed):
+    X, Y = W.grid_xy(p)
+    rng = np.random.default_rng(seed)
+    a = np.zeros((p["ny"], p["nx"], 2))
+    for c in range(2):
+        kx, ky, ph = rng.uniform(0.1, 0.4), rng.uniform(0.1, 0.4), rng.uniform(0, 6.28)
+        a[..., c] = amp * np.sin(kx * X + ky * Y + ph)
+    return a
+
+
+def case(name):
+    if name == "square_s":
+        p = W.square(10.0, 32, pairing=0, t=0.5, n_angles=16, n_energies=6)
+        return p, W.noisy_delta(p, 0.26, 0.1, seed=11), None
+    if name == "diamond_d_field":
+        p = W.diamond(12.0, 48, pairing=1, t=0.3, n_angles=16, n_energies=5, flux_quanta=0.5)
+        return p, W.noisy_delta(p, 0.23, 0.1, seed=12), None
+    if name == "disc_vortex_ragged":
+        p = W.disc(5.0, 40, pairing=1, t=0.25, n_angles=18, n_energies=13, flux_quanta=1.0)
+        d = W.vortex_delta(p, 0.22, [(1.0, -0.5)], [-1], seed=13, rel_noise=0.05)
+        return p, d, _smooth_a(p, 0.02, 13)
+    if name == "tiny_disc":
+        p = W.disc(1.6, 8, pairing=0, t=0.6, n_angles=4, n_energies=2, flux_quanta=0.3)
+        return p, W.noisy_delta(p, 0.2, 0.2, seed=14), None
+    if name == "polygon_dxy":
+        p = W.polygon([0.0, 7.0, 9.0, 2.0], [0.0, -1.0, 6.0, 8.0], 0.3, pairing=2, t=0.4,
+                      n_angles=10, n_energies=3, crystal_rotation=0.1, flux_quanta=0.8,
+                      charge_sign=1)
+        return p, W.noisy_delta(p, 0.2, 0.1, seed=15), _smooth_a(p, 0.03, 15)
+    raise KeyError(name)
+
+
+CASES = ["square_s", "diamond_d_field", "disc_vortex_ragged", "tiny_disc", "polygon_dxy"]
+
+
+def _rel(a, b, floor=0.0):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), floor, 1e-300))
+
+
+def _run_both(p, delta, aind, precision, n_sweeps=3, lanes=0):
+    sc = _sc()
+    g = oracle.OracleGeom(p)
+    ctx = sc.Context(p, precision=precision, lanes_per_line=lanes)
+    ctx.set_fields(delta, aind)
+    m = g.mask().astype(bool)
+    ex = None
+    res = []
+    for it in range(n_sweeps):
+        o = g.full_sweep(delta, aind, ex)
+        ex = o["exit"]
+        ctx.sweep()
+        r = ctx.outputs()
+        res.append(dict(
+            o=o, r={k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in r.items()},
+            exits=ctx.exits(), images=ctx.images()))
+    return g, ctx, m, res
+
+
+def _oracle_pair_images(g, o_images):
+    # the oracle images are per angle; the product keeps pair p = angle p
+    return o_images[: g.n_samples_all // 2]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp64_sweep_matches_oracle(name):
+    p, delta, aind = case(name)
+    g, ctx, m, res = _run_both(p, delta, aind, "fp64")
+    for it, R in enumerate(res):
+        o, r = R["o"], R["r"]
+        np.testing.assert_allclose(R["images"], _oracle_pair_images(g, o["images"]), atol=TOL64, rtol=0)
+        np.testing.assert_allclose(R["exits"], o["exit"][0], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["j"], o["j"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["F"], o["F"], atol=TOL64, rtol=0)
+        assert abs(r["F_total"] - o["F_total"]) < TOL64
+        assert abs(r["eps_G"] - o["eps_G"]) < 1e-9
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_fp32_sweep_within_tolerance(name):
+    p, delta, aind = case(name)
+    g, ctx, m, res = _run_both(p, delta, aind, "fp32")
+    for R in res:
+        o, r = R["o"], R["r"]
+        assert _rel(r["delta_new"][m], o["delta_new"][m]) < TOL_DELTA
+        assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
+        assert _rel(r["F"][m], o["F"][m]) < TOL_F
+        assert abs(r["F_total"] - o["F_total"]) <= TOL_F * abs(o["F_total"])
+        assert np.max(np.abs(R["exits"] - o["exit"][0])) < 2e-5
+
+
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+def test_lane_layouts_agree(lanes):
+    """Every lanes-per-line layout (with padded energies) gives the FP64 result."""
+    p, delta, aind = case("disc_vortex_ragged")
+    g, ctx, m, res = _run_both(p, delta, aind, "fp64", n_sweeps=2, lanes=lanes)
+    r, o = res[-1]["r"], res[-1]["o"]
+    np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=TOL64, rtol=0)
+    np.testing.assert_allclose(r["j"], o["j"], atol=TOL64, rtol=0)
+
+
+def test_picard_with_vector_potential_matches_oracle():
+    """Three iterations of Alg. suprcon with Picard steps and the App. D
+    vector-potential update, FP64, against the oracle's loop."""
+    sc = _sc()
+    import torch
+    p = W.disc(5.0, 32, pairing=0, t=0.5, n_angles=16, n_energies=6, flux_quanta=1.5, kappa=2.0)
+    d0 = W.vortex_delta(p, 0.25, [(0.5, 0.0)], [-1])
+    g = oracle.OracleGeom(p)
+    ref = g.picard(d0, 3)
+    ctx = sc.Context(p, precision="fp64")
+    ctx.set_fields(d0, np.zeros((p["ny"], p["nx"], 2)))
+    for _ in range(3):
+        ctx.sweep()
+        sc.sc_picard_step(ctx.h)
+    torch.cuda.synchronize()
+    # after the last Picard step, one more sweep on both sides gives comparable outputs
+    ctx.sweep()
+    r = ctx.outputs()
+    o = g.full_sweep(ref["delta"], ref["aind"], ref["exit"])
+    np.testing.assert_allclose(r["delta_new"].cpu().numpy(), o["delta_new"], atol=1e-10, rtol=0)
+    np.testing.assert_allclose(r["j"].cpu().numpy(), o["j"], atol=1e-10, rtol=0)
+    assert abs(r["F_total"] - o["F_total"]) < 1e-10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
+def test_ldos_matches_oracle(precision, tol):
+    sc = _sc()
+    p = W.diamond(8.0, 32, pairing=1, t=0.5, n_angles=16, n_energies=1)
+    d = W.noisy_delta(p, 0.22, 0.05, seed=21)
+    e = np.linspace(-0.3, 0.3, 8)
+    g = oracle.OracleGeom(p)
+    acc, _ = g.ldos(d, None, e, 0.03, n_burnin=6, tol=0.0)
+    ctx = sc.Context(p, precision=precision)
+    ctx.set_fields(d)
+    out = ctx.ldos(e, 0.03, n_burnin=6).cpu().numpy()
+    m = g.mask().astype(bool)
+    for c in range(len(e)):
+        assert _rel(out[c][m], acc[c][m]) < tol, c
+
+
+def test_burnin_converges_boundary():
+    sc = _sc()
+    p, delta, aind = case("diamond_d_field")
+    ctx = sc.Context(p, precision="fp64")
+    ctx.set_fields(delta, aind)
+    assert sc.sc_burnin(ctx.h, 200, 1e-11)
+    g = oracle.OracleGeom(p)
+    ex = None
+    for _ in range(200):
+        o = g.full_sweep(delta, aind, ex)
+        if ex is not None and np.max(np.abs(o["exit"] - ex)) < 1e-12:
+            break
+        ex = o["exit"]
+    np.testing.assert_allclose(ctx.exits(), o["exit"][0], atol=1e-9, rtol=0)
+
+
+def test_c2_full_size_fp32_against_oracle():
+    """The benchmark workload (d-wave 45-degree square, 256^2, 128 angles, 80
+    energies, 0.5 flux quanta): two FP32 sweeps against the oracle."""
+    sc = _sc()
+    p, delta, aind = W.c2_diamond_d()
+    g, ctx, m, res = _run_both(p, delta, aind, "fp32", n_sweeps=2)
+    for R in res:
+        o, r = R["o"], R["r"]
+        assert _rel(r["delta_new"][m], o["delta_new"][m]) < TOL_DELTA
+        assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
+        assert _rel(r["F"][m], o["F"][m]) < TOL_F
+        assert abs(r["F_total"] - o["F_total"]) <= TOL_F * abs(o["F_total"])
