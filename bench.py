@@ -161,7 +161,9 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    p, delta, aind = W.c2_diamond_d()
+    p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
+    workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
+        f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     ctx = sc.Context(p, precision=args.precision)
     info = ctx.info
     stream = torch.cuda.current_stream()
@@ -259,7 +261,7 @@ def run_ours(args):
     try:
         with open(prof) as f:
             tr = json.load(f)
-        if tr.get("precision") == args.precision and tr.get("workload") == WORKLOAD:
+        if tr.get("precision") == args.precision and tr.get("workload") == workload:
             traffic = tr.get("dram_bytes_per_launch")
     except Exception:
         pass
@@ -268,7 +270,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [p["nx"], p["ny"]], "n_angles": p["n_angles"],
+        "config": {"workload": workload, "grid": [p["nx"], p["ny"]], "n_angles": p["n_angles"],
                    "n_energies": p["n_energies"], "t": p["t"], "pairing": "dx2y2",
                    "flux_quanta": p["flux_quanta"], "precision": args.precision,
                    "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
@@ -285,7 +287,7 @@ def run_ours(args):
         "wall_s": t_wall,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 1, 16)
+        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"])
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -300,6 +302,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=256, help="grid side (reduced cases for profiling)")
+    ap.add_argument("--angles", type=int, default=128, help="Fermi angles (reduced cases for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
