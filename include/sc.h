@@ -175,6 +175,50 @@ sc_status sc_debug_exits(sc_ctx *ctx, double *exits);
    Sg, SF) for angle p (angle p + N/2 follows by symmetry) */
 sc_status sc_debug_images(sc_ctx *ctx, double *images);
 
+/* ---- allocation-free line sweep ---------------------------------------
+ * No counterpart in the paper: an engineering entry point for callers that
+ * must not allocate device memory when they run a sweep -- code whose device
+ * heap is owned by another allocator or memory pool, real-time loops that
+ * cannot afford the implicit synchronisation of cudaMalloc/cudaFree, or hosts
+ * that reserve all device memory up front.  It needs no sc_ctx and allocates
+ * nothing: the caller passes every input and output as a device pointer, and
+ * the only scratch (the forward coherence functions parked between the two
+ * passes of a line) lives in a static 32 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * FP32 sweep of n_lines independent lines, both directions, at the positive
+ * Matsubara energies eps_n = t (n + 1/2), n < n_e (the same step, propagator
+ * and energy sums as sc_riccati_sweep; one warp per line, energies on lanes).
+ *   samples     [n_slots][4] floats: Re(Delta eta), Im(Delta eta), a = sigma v.A
+ *               at each lattice sample, lines stored one after another
+ *               (a line with no sample has one slot: the chord-midpoint value)
+ *   line_slot0  [n_lines] first slot of each line;  line_ns [n_lines] samples
+ *               on the line (0 <= line_ns <= max_ns; longer lines are skipped and
+ *               their exits set to NaN)
+ *   line_len    [n_lines][2] floats: lengths from the chord start to the first
+ *               sample and from the last sample to the chord end (both the chord
+ *               length when line_ns = 0)
+ *   entry       [2][n_lines][n_e] complex floats: gamma entering at the chord
+ *               start (+ direction) and at the chord end (- direction); NULL =
+ *               start from the local homogeneous solution
+ *   images out  [n_slots][4] floats per sample: (Re Sf, Im Sf, Sg, SF) of the +
+ *               direction, as sc_debug_images reports them
+ *   exits out   [2][n_lines][n_e] complex floats: gamma leaving at the chord end
+ *               (+) and at the chord start (-)
+ * Limits: n_e <= 256 and max(max_ns, 1) * 32 * ceil(n_e / 32) <= 4 Mi
+ * (SC_EINVAL otherwise, with the reason in sc_last_error(NULL)).
+ * The first call on each device looks up the device address of the static
+ * array (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call uses the same array and leaves its contents behind;
+ * nothing in it needs to start at zero.  Calls whose kernels overlap on the GPU
+ * (different streams, or several host threads) race on the array: serialise
+ * them. */
+sc_status sc_sweep_lines_noalloc(const float *samples, const int32_t *line_slot0,
+                                 const int32_t *line_ns, const float *line_len,
+                                 const float *entry, int32_t n_lines, int32_t max_ns,
+                                 int32_t n_e, double t, double h, float *images,
+                                 float *exits, void *stream);
+
 const char *sc_last_error(const sc_ctx *ctx);
 const char *sc_version(void);
 

@@ -29,6 +29,10 @@ struct Plan {
 
 }  // namespace
 
+namespace sc_internal {
+void set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
+}  // namespace sc_internal
+
 struct sc_ctx {
     scg::Geometry geo;
     int device = 0;

@@ -61,7 +61,8 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
-            "sc_debug_exits", "sc_debug_images", "sc_last_error", "sc_version"]
+            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_last_error",
+            "sc_version"]
 
 
 def _load():
@@ -91,6 +92,7 @@ def _load():
         "sc_debug_links": [vp, vp, vp, vp],
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
+        "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -229,6 +231,16 @@ def sc_ldos(ctx, energies, broadening, n_burnin, ldos_out, on_device=True, strea
     e = np.ascontiguousarray(energies, np.float64)
     _check(lib.sc_ldos(ctx, _ptr(e), len(e), float(broadening), int(n_burnin), _ptr(ldos_out),
                        int(on_device), _stream(stream)), ctx)
+
+
+def sc_sweep_lines_noalloc(samples, line_slot0, line_ns, line_len, entry, n_lines, max_ns, n_e,
+                           t, h, images, exits, stream=None):
+    """Allocation-free FP32 line sweep (no sc_ctx; every buffer is the
+    caller's device memory; scratch is a static array inside the library).
+    For callers that cannot allocate device memory at sweep time."""
+    _check(lib.sc_sweep_lines_noalloc(_ptr(samples), _ptr(line_slot0), _ptr(line_ns), _ptr(line_len),
+                                      _ptr(entry), int(n_lines), int(max_ns), int(n_e), float(t),
+                                      float(h), _ptr(images), _ptr(exits), _stream(stream)))
 
 
 class Context:
