@@ -164,7 +164,7 @@ def run_ours(args):
     p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
     workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
         f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
-    ctx = sc.Context(p, precision=args.precision)
+    ctx = sc.Context(p, precision=args.precision, record_timings=True)
     info = ctx.info
     stream = torch.cuda.current_stream()
     d_delta = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128)).contiguous().to(dev)
@@ -192,26 +192,22 @@ def run_ours(args):
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
+    kern = []  # per timed step: (rotate, sweep, rotate_back) from the library's events
     t_wall = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
         step()
         ev[i][1].record(stream)
         flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+        ki = sc.sc_get_info(ctx.h)  # waits for this step's sweep kernels
+        kern.append((ki.ms_rotate, ki.ms_sweep, ki.ms_rotate_back))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = float(sum(step_ms))
-
-    # sweep kernel alone (dominant kernel), same stream, for the roofline
-    ksw = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-    for a, b in ksw:
-        flush.fill_(0.0)
-        a.record(stream)
-        sc.sc_riccati_sweep(ctx.h, stream)
-        b.record(stream)
-    torch.cuda.synchronize()
-    sweep_ms = statistics.median([a.elapsed_time(b) for a, b in ksw])
+    sweep_ms = statistics.mean(k[1] for k in kern)
+    kernels_ms = {"rotate": statistics.mean(k[0] for k in kern), "sweep": sweep_ms,
+                  "rotate_back": statistics.mean(k[2] for k in kern)}
     clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
 
     # end to end through the public API with host buffers
@@ -277,8 +273,8 @@ def run_ours(args):
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
-                     "kernel": "sweep (sc_riccati_sweep: rotate + sweep + rotate_back)",
-                     "ms_per_launch": sweep_ms,
+                     "kernel": "sweep_kernel", "ms_per_launch": sweep_ms,
+                     "kernels_ms_per_step": kernels_ms,
                      "peak_note": "FP32 lane issue 148 SM x 128 x max SM clock (derived)"},
         "e2e": {"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
                 "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

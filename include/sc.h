@@ -73,6 +73,8 @@ typedef struct {
     int32_t host_only;       /* 1 = build the geometry tables only (no device memory); every
                                 call that computes then returns SC_ESTATE.  For inspecting
                                 the discretisation on a machine without a GPU. */
+    int32_t record_timings;  /* 1 = time the three kernels of every sweep with CUDA events on
+                                the sweep's stream (reported by sc_get_info) */
 } sc_params;
 
 typedef struct {
@@ -87,6 +89,8 @@ typedef struct {
     double norm_D;           /* gap-equation normalisation ln t + 2 sum 1/(2n+1) */
     int32_t lanes_per_line, energies_per_lane, lines_per_warp;
     int64_t scratch_bytes;   /* device scratch used by the sweep */
+    double ms_rotate, ms_sweep, ms_rotate_back; /* last sweep's kernel times when
+                                record_timings = 1 (sc_get_info then waits for that sweep) */
 } sc_info;
 
 /* Fill defaults: 64x64 unit grid, s-wave disc, t = 0.5, 32 angles, 16 energies,

@@ -67,6 +67,14 @@ struct sc_ctx {
     size_t scratch_bytes = 0;
     int32_t *d_counter = nullptr;
     int sm_count = 0;
+    // FP32 production path tables and buffers
+    scd::LineF32 *d_line_f32 = nullptr;
+    scd::PairF32 *d_pair_f32 = nullptr;
+    float2 *d_delta_f = nullptr, *d_aind_f = nullptr;
+    // kernel timings
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
     bool failed = false;
     bool host_only = false;
     std::string err;
@@ -207,10 +215,20 @@ sc_status check_ctx(sc_ctx *ctx) {
 sc_status run_sweep(sc_ctx *ctx, const Plan &pl, int n_e, bool retarded, const double *d_energies,
                     double broadening, void *img_out, const void *exit_prev, void *exit_cur, bool first,
                     cudaStream_t st) {
-    CK(scd::launch_rotate(ctx->fp64, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
-                          ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_img_in,
-                          st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], st));
+    if (ctx->fp64) {
+        CK(scd::launch_rotate(true, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
+                              ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_img_in,
+                              st));
+    } else {
+        const int64_t np = (int64_t)ctx->geo.nx * ctx->geo.ny;
+        CK(scd::launch_fields_f32(np, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_delta_f,
+                                  ctx->d_aind_f, st));
+        CK(scd::launch_rotate_f32(ctx->d_line_f32, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pair_f32, ctx->grid,
+                                  ctx->d_ghost, ctx->d_delta_f, ctx->d_aind_f, (float4 *)ctx->d_img_in, st));
+    }
     CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], st));
     scd::SweepLaunch a{};
     a.lines = ctx->d_lines;
     a.groups = pl.d_groups;
@@ -237,6 +255,7 @@ sc_status run_sweep(sc_ctx *ctx, const Plan &pl, int n_e, bool retarded, const d
     a.energies = d_energies;
     a.broadening = broadening;
     CK(scd::launch_sweep(ctx->fp64, a, st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], st));
     return SC_OK;
 }
 
@@ -296,6 +315,8 @@ sc_status sc_destroy(sc_ctx *ctx) {
     if (!ctx) return SC_EINVAL;
     if (!ctx->allocs.empty()) cudaSetDevice(ctx->device);
     for (void *p : ctx->allocs) cudaFree(p);
+    for (cudaEvent_t e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
     return SC_OK;
 }
@@ -419,6 +440,56 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         d.pad = 0;
     }
 
+    // FP32 production path: fixed-point lattice coordinates (2^-40 grid units)
+    const double fix = std::ldexp(1.0, scd::kFixBits);
+    auto to_fix = [&](double v) { return (int64_t)std::llround(v * fix); };
+    std::vector<scd::LineF32> lf(nL);
+    std::vector<scd::PairF32> pf(P);
+    {
+        const double cxo = (G.ox - p->x0) / p->h - 0.5, cyo = (G.oy - p->y0) / p->h - 0.5;
+        const double half_b = 0.5 * gd.bfield;
+        for (size_t L = 0; L < nL; ++L) {
+            const scg::LineInfo &li = G.lines[L];
+            const scg::PairInfo &pp = G.pairs[li.pair];
+            const double sh = li.ns > 0 ? (double)li.m0 : 0.5 * (li.smin + li.smax) / p->h;  // along, units of h
+            lf[L].gx0 = to_fix(cxo + li.l * (-pp.ey) + sh * pp.ex);
+            lf[L].gy0 = to_fix(cyo + li.l * pp.ex + sh * pp.ey);
+            // v.A_ext is constant on a line: B/2 (e_y (Ox - gx) - e_x (Oy - gy) - l h)
+            lf[L].aext = (float)(p->charge_sign * half_b *
+                                 (pp.ey * (G.ox - p->gauge_cx) - pp.ex * (G.oy - p->gauge_cy) - li.l * p->h));
+            lf[L].pair = li.pair;
+            lf[L].ns = li.ns;
+            lf[L].slot0 = li.slot0;
+        }
+        const double cx = 0.5 + (p->x0 - G.ox) / p->h, cy = 0.5 + (p->y0 - G.oy) / p->h;
+        for (int q = 0; q < P; ++q) {
+            const scg::PairInfo &pp = G.pairs[q];
+            scd::PairF32 &d = pf[q];
+            d.dx = to_fix(pp.ex);
+            d.dy = to_fix(pp.ey);
+            d.ui = to_fix(-pp.ey);
+            d.uj = to_fix(pp.ex);
+            d.u0 = to_fix(cx * (-pp.ey) + cy * pp.ex);
+            d.vi = to_fix(pp.ex);
+            d.vj = to_fix(pp.ey);
+            d.v0 = to_fix(cx * pp.ex + cy * pp.ey);
+            const double ws = G.weight[q] + G.weight[q + P];
+            d.eta = (float)pp.eta;
+            d.w_eta = (float)(ws * pp.eta);
+            d.w_ex = (float)(ws * pp.ex);
+            d.w_ey = (float)(ws * pp.ey);
+            d.w_sum = (float)ws;
+            d.wa = (float)G.weight[q];
+            d.wb = (float)G.weight[q + P];
+            d.ex_f = (float)pp.ex;
+            d.ey_f = (float)pp.ey;
+            d.l_lo = pp.l_lo;
+            d.l_hi = pp.l_hi;
+            d.line0 = pp.line0;
+            d.pad = 0;
+        }
+    }
+
     // device memory
     const size_t np = npts(ctx);
     const size_t t4 = ctx->fp64 ? 32 : 16;
@@ -466,6 +537,21 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     CA(ctx->d_img_in, G.n_slots * t4);
     CA(ctx->d_img_out, G.n_slots * t4);
     for (int b = 0; b < 2; ++b) CA(ctx->d_exit[b], 2 * nL * (size_t)ctx->n_e * cplx);
+    if (!ctx->fp64) {
+        CA(ctx->d_line_f32, nL * sizeof(scd::LineF32));
+        CP(ctx->d_line_f32, lf.data(), nL * sizeof(scd::LineF32));
+        CA(ctx->d_pair_f32, P * sizeof(scd::PairF32));
+        CP(ctx->d_pair_f32, pf.data(), P * sizeof(scd::PairF32));
+        CA(ctx->d_delta_f, np * sizeof(float2));
+        CA(ctx->d_aind_f, np * sizeof(float2));
+    }
+    if (p->record_timings) {
+        ctx->timing = true;
+        for (auto &e : ctx->ev) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return fail_cuda(err, "cudaEventCreate");
+        }
+    }
     {
         cudaError_t err = cudaMemset(ctx->d_delta, 0, 2 * np * sizeof(double));
         if (err == cudaSuccess) err = cudaMemset(ctx->d_aind, 0, 2 * np * sizeof(double));
@@ -528,6 +614,16 @@ sc_status sc_get_info(const sc_ctx *ctx, sc_info *info) {
         info->lines_per_warp = ctx->main_plan->lines_per_warp;
     }
     info->scratch_bytes = (int64_t)ctx->scratch_bytes;
+    if (ctx->timing && ctx->timed) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (cudaEventSynchronize(ctx->ev[3]) == cudaSuccess && cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, ctx->ev[1], ctx->ev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&c, ctx->ev[2], ctx->ev[3]) == cudaSuccess) {
+            info->ms_rotate = a;
+            info->ms_sweep = b;
+            info->ms_rotate_back = c;
+        }
+    }
     return SC_OK;
 }
 
@@ -569,8 +665,16 @@ sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream) {
     const int nxt = 1 - ctx->cur;
     CKS(run_sweep(ctx, *ctx->main_plan, ctx->n_e, false, nullptr, 0.0, ctx->d_img_out, ctx->d_exit[ctx->cur],
                   ctx->d_exit[nxt], !ctx->have_boundary, st));
-    CK(scd::launch_rotate_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
-                               ctx->d_img_out, ctx->d_acc, st));
+    if (ctx->fp64)
+        CK(scd::launch_rotate_back(true, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                   ctx->d_img_out, ctx->d_acc, st));
+    else
+        CK(scd::launch_rotate_back_f32(ctx->d_pair_f32, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                       (const float4 *)ctx->d_img_out, ctx->d_acc, st));
+    if (ctx->timing) {
+        CK(cudaEventRecord(ctx->ev[3], st));
+        ctx->timed = true;
+    }
     ctx->cur = nxt;
     ctx->have_boundary = true;
     ctx->have_sweep = true;

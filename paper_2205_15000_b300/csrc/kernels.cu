@@ -107,7 +107,7 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
 // energies and then over the line's lanes by shuffles.
 // ---------------------------------------------------------------------------
 template <typename T, int EPT, bool RET>
-__global__ void __launch_bounds__(128) sweep_kernel(SweepLaunch a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(SweepLaunch a) {
     typedef typename Vec4<T>::type T4;
     typedef Cx<T> C;
     const int lane = threadIdx.x & 31;

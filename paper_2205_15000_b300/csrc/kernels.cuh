@@ -47,6 +47,26 @@ struct GridDev {
     int32_t charge_sign;
 };
 
+// FP32 production path: lattice coordinates in fixed point (2^-40 grid units),
+// so that floor and fraction are exact and no FP64 arithmetic is needed.
+constexpr int kFixBits = 40;
+
+struct LineF32 {
+    int64_t gx0, gy0;    // grid coordinates (x - x0)/h - 1/2 of the first slot's point
+    float aext;          // sigma v.A_ext: constant along a line in the symmetric gauge
+    int32_t pair, ns, slot0;
+};
+
+struct PairF32 {
+    int64_t dx, dy;                 // e_par in grid units per sample
+    int64_t ui, uj, u0, vi, vj, v0; // u = i ui + j uj + u0, v = i vi + j vj + v0
+    float eta;                      // basis function
+    float w_eta, w_ex, w_ey, w_sum; // (w_p + w_{p+P}) times eta, e_x, e_y, 1
+    float wa, wb;                   // w_p, w_{p+P}
+    float ex_f, ey_f;               // e_par in FP32
+    int32_t l_lo, l_hi, line0, pad;
+};
+
 struct SweepLaunch {
     const LineDev *lines;
     const int32_t *groups;     // [n_groups][lines_per_warp], -1 padded
@@ -80,6 +100,16 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
                           const double *delta, const double *aind, void *image_in,
                           cudaStream_t s);
 cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
+// FP32 production path
+cudaError_t launch_fields_f32(int64_t npts, const double *delta, const double *aind, float2 *delta_f,
+                              float2 *aind_f, cudaStream_t s);
+cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
+                              const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
+                              const float2 *delta_f, const float2 *aind_f, float4 *image_in,
+                              cudaStream_t s);
+cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
+                                   const GridDev &grid, const uint8_t *mask, const float4 *image_out,
+                                   double *acc, cudaStream_t s);
 int sweep_occupancy(bool fp64, int ept, int block_threads);
 cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
                                const BackLine *bl, const GridDev &grid, const uint8_t *mask,

@@ -1,0 +1,168 @@
+// FP32 production path of the lattice transfers (Sec. 3.1: bilinear
+// interpolation from the reference grid to each rotated lattice and back).
+//
+// Positions on the lattices are kept in 64-bit fixed point with 40 fractional
+// bits (grid units), so the cell index is an exact shift and the bilinear
+// weight an exact fraction; the interpolation itself runs in FP32 and the
+// Fermi-surface sums are accumulated in FP32 over blocks of 16 pairs and then
+// in FP64.  The FP64 sweep keeps the plain FP64 kernels in kernels.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace scd {
+
+namespace {
+
+__device__ __forceinline__ void split_fixed(int64_t v, int &cell, float &frac) {
+    cell = (int)(v >> kFixBits);
+    const uint32_t f32 = (uint32_t)((v >> (kFixBits - 32)) & 0xffffffffll);
+    frac = (float)f32 * 2.3283064365386963e-10f;  // 2^-32
+}
+
+}  // namespace
+
+__global__ void fields_f32_kernel(int64_t npts, const double2 *__restrict__ delta,
+                                  const double2 *__restrict__ aind, float2 *__restrict__ df,
+                                  float2 *__restrict__ af) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npts) return;
+    const double2 d = delta[i];
+    df[i] = make_float2((float)d.x, (float)d.y);
+    if (aind) {
+        const double2 a = aind[i];
+        af[i] = make_float2((float)a.x, (float)a.y);
+    } else {
+        af[i] = make_float2(0.f, 0.f);
+    }
+}
+
+cudaError_t launch_fields_f32(int64_t npts, const double *delta, const double *aind, float2 *delta_f,
+                              float2 *aind_f, cudaStream_t st) {
+    const int bs = 256;
+    fields_f32_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(
+        npts, (const double2 *)delta, (const double2 *)aind, delta_f, aind_f);
+    return cudaGetLastError();
+}
+
+// one thread per image slot: bilinear Delta and A_ind at the sample, nearest
+// grain point for stencil points outside the grain
+__global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32_t *__restrict__ slot_line,
+                                  int64_t n_slots, const PairF32 *__restrict__ pairs, GridDev grid,
+                                  const int32_t *__restrict__ ghost, const float2 *__restrict__ df,
+                                  const float2 *__restrict__ af, float4 *__restrict__ out) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n_slots) return;
+    const LineF32 ln = lines[slot_line[s]];
+    const PairF32 &pp = pairs[ln.pair];
+    const int q = (int)(s - ln.slot0);
+    int i0, j0;
+    float fx, fy;
+    split_fixed(ln.gx0 + (int64_t)q * pp.dx, i0, fx);
+    split_fixed(ln.gy0 + (int64_t)q * pp.dy, j0, fy);
+    float4 o = make_float4(0.f, 0.f, 0.f, 1.f);
+    if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
+        const int px = grid.nx + 2;
+        const int base = (j0 + 1) * px + (i0 + 1);
+        const int g00 = ghost[base], g10 = ghost[base + 1], g01 = ghost[base + px], g11 = ghost[base + px + 1];
+        const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+        // a stencil point without a grain neighbour only occurs with zero weight
+        const float2 z = make_float2(0.f, 0.f);
+        const float2 d00 = g00 >= 0 ? df[g00] : z, d10 = g10 >= 0 ? df[g10] : z;
+        const float2 d01 = g01 >= 0 ? df[g01] : z, d11 = g11 >= 0 ? df[g11] : z;
+        const float2 a00 = g00 >= 0 ? af[g00] : z, a10 = g10 >= 0 ? af[g10] : z;
+        const float2 a01 = g01 >= 0 ? af[g01] : z, a11 = g11 >= 0 ? af[g11] : z;
+        const float dr = w00 * d00.x + w10 * d10.x + w01 * d01.x + w11 * d11.x;
+        const float di = w00 * d00.y + w10 * d10.y + w01 * d01.y + w11 * d11.y;
+        const float ax = w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x;
+        const float ay = w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y;
+        o.x = pp.eta * dr;
+        o.y = pp.eta * di;
+        o.z = ln.aext + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
+        const bool ok = (g00 >= 0 || w00 == 0.f) && (g10 >= 0 || w10 == 0.f) && (g01 >= 0 || w01 == 0.f) &&
+                        (g11 >= 0 || w11 == 0.f);
+        o.w = ok ? 0.f : 1.f;
+    }
+    out[s] = o;
+}
+
+cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
+                              const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
+                              const float2 *delta_f, const float2 *aind_f, float4 *image_in,
+                              cudaStream_t st) {
+    const int bs = 256;
+    rotate_f32_kernel<<<(unsigned)((n_slots + bs - 1) / bs), bs, 0, st>>>(lines, slot_line, n_slots, pairs,
+                                                                          grid, ghost, delta_f, aind_f,
+                                                                          image_in);
+    return cudaGetLastError();
+}
+
+// one thread per grid point: for every pair, bilinear gather of the four image
+// slots around the point's lattice coordinates and the Fermi-surface sum
+__global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
+                                       const BackLine *__restrict__ bl, GridDev grid,
+                                       const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
+                                       double *__restrict__ acc) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npts) return;
+    double A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0;
+    if (mask[idx]) {
+        const int64_t i = idx % grid.nx, j = idx / grid.nx;
+        for (int p0 = 0; p0 < n_pairs; p0 += 16) {
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+            const int pe = min(p0 + 16, n_pairs);
+            for (int p = p0; p < pe; ++p) {
+                const PairF32 &pp = pairs[p];
+                int iu, iv;
+                float wu, wv;
+                split_fixed(i * pp.ui + j * pp.uj + pp.u0, iu, wu);
+                split_fixed(i * pp.vi + j * pp.vj + pp.v0, iv, wv);
+                const int la = min(max(iu, pp.l_lo), pp.l_hi), lb = min(max(iu + 1, pp.l_lo), pp.l_hi);
+                const BackLine La = bl[pp.line0 + (la - pp.l_lo)];
+                const BackLine Lb = bl[pp.line0 + (lb - pp.l_lo)];
+                const int ma0 = min(max(iv, La.m0), La.m0 + La.ns - 1);
+                const int ma1 = min(max(iv + 1, La.m0), La.m0 + La.ns - 1);
+                const int mb0 = min(max(iv, Lb.m0), Lb.m0 + Lb.ns - 1);
+                const int mb1 = min(max(iv + 1, Lb.m0), Lb.m0 + Lb.ns - 1);
+                const float4 sa0 = img[La.slot0 + (ma0 - La.m0)], sa1 = img[La.slot0 + (ma1 - La.m0)];
+                const float4 sb0 = img[Lb.slot0 + (mb0 - Lb.m0)], sb1 = img[Lb.slot0 + (mb1 - Lb.m0)];
+                const float wa0 = (1.f - wu) * (1.f - wv), wa1 = (1.f - wu) * wv;
+                const float wb0 = wu * (1.f - wv), wb1 = wu * wv;
+                const float x0 = wa0 * sa0.x + wa1 * sa1.x + wb0 * sb0.x + wb1 * sb1.x;
+                const float x1 = wa0 * sa0.y + wa1 * sa1.y + wb0 * sb0.y + wb1 * sb1.y;
+                const float x2 = wa0 * sa0.z + wa1 * sa1.z + wb0 * sb0.z + wb1 * sb1.z;
+                const float x3 = wa0 * sa0.w + wa1 * sa1.w + wb0 * sb0.w + wb1 * sb1.w;
+                // S_f, S_F are equal at phi and phi + pi; S_g and v change sign together
+                a0 += pp.w_eta * x0;
+                a1 += pp.w_eta * x1;
+                a2 += pp.w_ex * x2;
+                a3 += pp.w_ey * x2;
+                a4 += pp.w_sum * x3;
+            }
+            A0 += a0;
+            A1 += a1;
+            A2 += a2;
+            A3 += a3;
+            A4 += a4;
+        }
+    }
+    acc[idx] = A0;
+    acc[npts + idx] = A1;
+    acc[2 * npts + idx] = A2;
+    acc[3 * npts + idx] = A3;
+    acc[4 * npts + idx] = A4;
+}
+
+cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
+                                   const GridDev &grid, const uint8_t *mask, const float4 *image_out,
+                                   double *acc, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int bs = 128;
+    rotate_back_f32_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
+                                                                           image_out, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace scd

@@ -97,12 +97,12 @@ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, S
         Oi = copysign(s, y);
     }
     const T wr = zr - Oi, wi = zi + Or;  // w = z + i Omega
-    // a single reciprocal serves 1/w and 1/(2 Omega):  q = 1 / (2 Omega w)
-    const T mr = T(2) * (Or * wr - Oi * wi), mi = T(2) * (Or * wi + Oi * wr);
-    const T rm = M::rcp(mr * mr + mi * mi);
-    const T qr = mr * rm, qi = -mi * rm;
-    const T iwr = T(2) * (Or * qr - Oi * qi), iwi = T(2) * (Or * qi + Oi * qr);  // 1/w
-    const T i2r = wr * qr - wi * qi, i2i = wr * qi + wi * qr;                    // 1/(2 Omega)
+    // 1/w and 1/(2 Omega) from two reciprocals of squared moduli (the sweep is
+    // bound by FP32 issue, not by the reciprocal unit)
+    const T rw = M::rcp(wr * wr + wi * wi);
+    const T iwr = wr * rw, iwi = -wi * rw;                    // 1/w
+    const T ro = T(0.5) * M::rcp(Or * Or + Oi * Oi);
+    const T i2r = Or * ro, i2i = -Oi * ro;                    // 1/(2 Omega)
     c.gh.x = -(dr * iwr - di * iwi);
     c.gh.y = -(dr * iwi + di * iwr);
     const T eu = M::expneg(T(2) * ell * Or);

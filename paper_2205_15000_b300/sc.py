@@ -41,7 +41,7 @@ class sc_params(ctypes.Structure):
         ("n_angles", ctypes.c_int32), ("n_energies", ctypes.c_int32),
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
         ("precision", ctypes.c_int32), ("lanes_per_line", ctypes.c_int32),
-        ("host_only", ctypes.c_int32),
+        ("host_only", ctypes.c_int32), ("record_timings", ctypes.c_int32),
     ]
 
 
@@ -53,6 +53,8 @@ class sc_info(ctypes.Structure):
         ("area", ctypes.c_double), ("norm_D", ctypes.c_double),
         ("lanes_per_line", ctypes.c_int32), ("energies_per_lane", ctypes.c_int32),
         ("lines_per_warp", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
+        ("ms_rotate", ctypes.c_double), ("ms_sweep", ctypes.c_double),
+        ("ms_rotate_back", ctypes.c_double),
     ]
 
 
@@ -146,7 +148,7 @@ def sc_params_default():
     return p
 
 
-def make_params(d, precision="fp32", lanes_per_line=0, host_only=False):
+def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_timings=False):
     """sc_params from a workload dict (keys of workloads.PARAM_KEYS).  The
     vertex arrays are kept alive on the returned struct."""
     p = sc_params_default()
@@ -163,6 +165,7 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False):
     p.precision = SC_PREC_FP64 if precision == "fp64" else SC_PREC_FP32
     p.lanes_per_line = lanes_per_line
     p.host_only = 1 if host_only else 0
+    p.record_timings = 1 if record_timings else 0
     return p
 
 
@@ -246,9 +249,10 @@ def sc_sweep_lines_noalloc(samples, line_slot0, line_ns, line_len, entry, n_line
 class Context:
     """One grain: owns an sc_ctx.  Arrays in, arrays out (torch on the GPU)."""
 
-    def __init__(self, prm, precision="fp32", lanes_per_line=0, host_only=False):
+    def __init__(self, prm, precision="fp32", lanes_per_line=0, host_only=False,
+                 record_timings=False):
         self.prm = dict(prm)
-        self._p = make_params(prm, precision, lanes_per_line, host_only)
+        self._p = make_params(prm, precision, lanes_per_line, host_only, record_timings)
         self.h = sc_create(self._p)
         self.info = sc_get_info(self.h)
         self.nx, self.ny = prm["nx"], prm["ny"]
