@@ -163,6 +163,42 @@ sc_status sc_picard_step(sc_ctx *ctx, void *stream);
 sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening,
                   int32_t n_burnin, double *ldos_out, int on_device, void *stream);
 
+/* ---- batched form: many grains in one persistent launch ---------------- */
+typedef struct sc_batch sc_batch;
+typedef struct {
+    int32_t n_grains;
+    int32_t n_items;           /* (grain, line group) work items of one sweep */
+    int32_t energies_per_lane; /* kernel layout shared by all members */
+    int64_t steps_per_sweep;   /* closed-form steps of one batch sweep, all grains */
+    int64_t scratch_bytes;
+    double ms_sweep;           /* last batch sweep kernel (CUDA events on its stream) */
+} sc_batch_info;
+
+/* Create n member contexts (params[0..n-1], same precision; each validated as
+   in sc_create) and one work list over all their (line group) items, longest
+   first, for a single persistent sweep launch.  energies_per_lane = 0 picks a
+   default; sc_batch_autotune chooses by timing.  Each member keeps its own
+   lanes-per-line layout.  The members are owned by the batch. */
+sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,
+                          sc_batch **out);
+sc_status sc_batch_destroy(sc_batch *b);
+/* Member context i: set its fields and read its outputs with the sc_* calls
+   above; sweeping it alone returns SC_ESTATE (its boundary values are the
+   batch's). */
+sc_status sc_batch_member(sc_batch *b, int32_t i, sc_ctx **out);
+/* One sweep of every member (rotate per member, one persistent sweep launch,
+   rotate-back per member); equivalent to sc_riccati_sweep on each member. */
+sc_status sc_batch_sweep(sc_batch *b, void *stream);
+/* n_sweeps batch sweeps (with_outputs = 1: plus every member's gap update,
+   current and free energy on the device), replayed as captured CUDA graphs --
+   one graph per iteration parity -- on an internal stream ordered after and
+   before `stream`.  The first sweep from fresh boundary values runs uncaptured. */
+sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream);
+/* Time one sweep per candidate energies-per-lane (2..8) and keep the fastest.
+   The timing sweeps are real sweeps (boundary values advance). */
+sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *stream);
+sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info);
+
 /* ---- inspection (tests and tools) ------------------------------------- */
 /* per pair l_lo, l_hi (n_pairs each); per line smin, smax, m0, m1 (n_lines) */
 sc_status sc_debug_lines(const sc_ctx *ctx, int32_t *l_lo, int32_t *l_hi, double *smin,

@@ -10,78 +10,17 @@
 #include <string>
 #include <vector>
 
-#include "geometry.hpp"
-#include "kernels.cuh"
-#include "sc.h"
+#include "context.hpp"
 
 namespace {
-
 thread_local std::string g_create_error;
-
-// How the sweep kernel maps (line, energy) work to lanes for one energy count.
-struct Plan {
-    int lanes = 0, ept = 0, lines_per_warp = 0;
-    int32_t *d_groups = nullptr;
-    int32_t n_groups = 0;
-    int grid_blocks = 0;
-    int64_t stride = 0;  // scratch elements (complex) per warp
-};
-
 }  // namespace
 
 namespace sc_internal {
 void set_thread_error(const char *msg) { g_create_error = msg ? msg : ""; }
 }  // namespace sc_internal
 
-struct sc_ctx {
-    scg::Geometry geo;
-    int device = 0;
-    bool fp64 = false;
-    int n_e = 0;
-    int forced_lanes = 0;
-    double normD = 0.0;
-    size_t real_bytes = 4;
-    scd::GridDev grid{};
-    // geometry on the device
-    uint8_t *d_mask = nullptr;
-    int32_t *d_ghost = nullptr;
-    scd::LineGeo *d_geo = nullptr;
-    int32_t *d_slot_line = nullptr;
-    scd::PairDev *d_pairs = nullptr;
-    scd::BackLine *d_back = nullptr;
-    scd::LineDev *d_lines = nullptr;
-    std::map<int, Plan> plans;  // key: lanes * 16 + ept
-    Plan *main_plan = nullptr;
-    // fields and results
-    double *d_delta = nullptr, *d_aind = nullptr, *d_acc = nullptr, *d_dnew = nullptr, *d_j = nullptr,
-           *d_F = nullptr, *d_sums = nullptr, *d_jsum = nullptr, *d_G = nullptr, *d_diff = nullptr;
-    int G_width = 0;
-    bool have_aind = false;
-    void *d_img_in = nullptr, *d_img_out = nullptr;
-    void *d_exit[2] = {nullptr, nullptr};
-    int cur = 0;  // d_exit[cur] holds the latest exit values
-    bool have_boundary = false;
-    bool have_sweep = false;
-    bool have_outputs = false;
-    void *d_scratch = nullptr;
-    size_t scratch_bytes = 0;
-    int32_t *d_counter = nullptr;
-    int sm_count = 0;
-    // FP32 production path tables and buffers
-    scd::LineF32 *d_line_f32 = nullptr;
-    scd::PairF32 *d_pair_f32 = nullptr;
-    float2 *d_delta_f = nullptr, *d_aind_f = nullptr;
-    // kernel timings
-    bool timing = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    bool timed = false;
-    bool failed = false;
-    bool host_only = false;
-    std::string err;
-    std::vector<void *> allocs;
-};
-
-namespace {
+namespace sc_internal {
 
 sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg) {
     c->err = msg;
@@ -89,27 +28,12 @@ sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg) {
     return st;
 }
 
-#define CK(expr)                                                                        \
-    do {                                                                                \
-        cudaError_t e_ = (expr);                                                        \
-        if (e_ != cudaSuccess)                                                          \
-            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? SC_ENOMEM : SC_ECUDA, \
-                           std::string(#expr) + ": " + cudaGetErrorString(e_));          \
-    } while (0)
-
-#define CKS(expr)                            \
-    do {                                     \
-        sc_status s_ = (expr);               \
-        if (s_ != SC_OK) return s_;          \
-    } while (0)
-
-template <typename P>
-cudaError_t dalloc(sc_ctx *ctx, P **p, size_t bytes) {
+cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes) {
     void *v = nullptr;
     cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
     if (e == cudaSuccess) {
         ctx->allocs.push_back(v);
-        *p = (P *)v;
+        *p = v;
     }
     return e;
 }
@@ -121,10 +45,49 @@ void dfree(sc_ctx *ctx, void *p) {
     cudaFree(p);
 }
 
+}  // namespace sc_internal
+
+namespace {
+
+using sc_internal::dfree;
+using sc_internal::set_err;
+
+#define CK(expr)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? SC_ENOMEM : SC_ECUDA, \
+                           std::string(#expr) + ": " + cudaGetErrorString(e_));          \
+    } while (0)
+
+#define CKS(expr)                   \
+    do {                            \
+        sc_status s_ = (expr);      \
+        if (s_ != SC_OK) return s_; \
+    } while (0)
+
+template <typename P>
+cudaError_t dalloc(sc_ctx *ctx, P **p, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = sc_internal::dalloc_bytes(ctx, &v, bytes);
+    if (e == cudaSuccess) *p = (P *)v;
+    return e;
+}
+
 // energy lanes per line and energies per lane: least padding, then EPT near 4
-void choose_lanes(int n_e, int forced, int &lanes, int &ept) {
-    if (forced) {
-        lanes = forced;
+void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ept) {
+    if (forced_ept) {
+        ept = forced_ept;
+        lanes = 32;
+        for (int l : {4, 8, 16, 32})
+            if (l * ept >= n_e) {
+                lanes = l;
+                break;
+            }
+        return;
+    }
+    if (forced_lanes) {
+        lanes = forced_lanes;
         ept = (n_e + lanes - 1) / lanes;
         return;
     }
@@ -143,11 +106,36 @@ void choose_lanes(int n_e, int forced, int &lanes, int &ept) {
     ept = best_e;
 }
 
-sc_status make_plan(sc_ctx *ctx, int n_e, Plan **out) {
+sc_status ensure_scratch(sc_ctx *ctx, size_t need) {
+    if (need <= ctx->scratch_bytes) return SC_OK;
+    dfree(ctx, ctx->d_scratch);
+    ctx->d_scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    CK(dalloc(ctx, &ctx->d_scratch, need));
+    ctx->scratch_bytes = need;
+    return SC_OK;
+}
+
+size_t npts(const sc_ctx *ctx) { return (size_t)ctx->geo.nx * ctx->geo.ny; }
+
+}  // namespace
+
+namespace sc_internal {
+
+sc_status check_ctx(sc_ctx *ctx) {
+    if (!ctx) return SC_EINVAL;
+    if (ctx->host_only) return set_err(ctx, SC_ESTATE, "context was created with host_only = 1");
+    if (ctx->failed) return SC_ESTATE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+    return SC_OK;
+}
+
+sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out) {
     int lanes, ept;
-    choose_lanes(n_e, ctx->forced_lanes, lanes, ept);
-    if (ept > 8 || lanes * ept < n_e)
-        return set_err(ctx, SC_EINVAL, "too many energies for the lane layout (at most 8 per lane)");
+    choose_lanes(n_e, ctx->forced_lanes, forced_ept, lanes, ept);
+    if (ept < 1 || ept > 8 || lanes * ept < n_e)
+        return set_err(ctx, SC_EINVAL, "too many energies for the lane layout (at most 32 lanes x 8 per lane)");
     const int key = lanes * 16 + ept;
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
@@ -159,63 +147,64 @@ sc_status make_plan(sc_ctx *ctx, int n_e, Plan **out) {
     pl.ept = ept;
     pl.lines_per_warp = 32 / lanes;
     const int G = pl.lines_per_warp;
-    // groups of G neighbouring lines of one pair (similar lengths); longest first
-    std::vector<std::vector<int32_t>> groups;
-    std::vector<int> cost;
+    // groups of G neighbouring lines of one pair (similar lengths)
+    std::vector<int32_t> flat;
     for (const auto &pp : ctx->geo.pairs) {
         const int n = pp.l_hi - pp.l_lo + 1;
         for (int i = 0; i < n; i += G) {
-            std::vector<int32_t> g(G, -1);
             int c = 0;
-            for (int k = 0; k < G && i + k < n; ++k) {
-                g[k] = pp.line0 + i + k;
-                c = std::max(c, ctx->geo.lines[pp.line0 + i + k].ns + 1);
+            for (int k = 0; k < G; ++k) {
+                if (i + k < n) {
+                    flat.push_back(pp.line0 + i + k);
+                    c = std::max(c, ctx->geo.lines[pp.line0 + i + k].ns + 1);
+                } else {
+                    flat.push_back(-1);
+                }
             }
-            groups.push_back(g);
-            cost.push_back(c);
+            pl.group_cost.push_back(c);
         }
     }
-    std::vector<int> order(groups.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    std::vector<int32_t> flat;
-    flat.reserve(groups.size() * G);
-    for (int o : order) flat.insert(flat.end(), groups[o].begin(), groups[o].end());
-    pl.n_groups = (int32_t)groups.size();
+    pl.n_groups = (int32_t)pl.group_cost.size();
+    std::vector<int> order(pl.n_groups);
+    for (int i = 0; i < pl.n_groups; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return pl.group_cost[a] > pl.group_cost[b]; });
+    std::vector<int2> items(pl.n_groups);
+    for (int i = 0; i < pl.n_groups; ++i) items[i] = make_int2(0, order[i]);
     CK(dalloc(ctx, &pl.d_groups, flat.size() * sizeof(int32_t)));
     CK(cudaMemcpy(pl.d_groups, flat.data(), flat.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(dalloc(ctx, &pl.d_items, items.size() * sizeof(int2)));
+    CK(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     const int bs = 128;
     int occ = scd::sweep_occupancy(ctx->fp64, ept, bs);
     if (occ < 1) occ = 1;
     pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
     pl.stride = (int64_t)G * std::max(ctx->geo.max_ns, 1) * lanes * ept;
-    const size_t need = (size_t)pl.grid_blocks * 4 * (size_t)pl.stride * 2 * ctx->real_bytes;
-    if (need > ctx->scratch_bytes) {
-        dfree(ctx, ctx->d_scratch);
-        ctx->d_scratch = nullptr;
-        ctx->scratch_bytes = 0;
-        CK(dalloc(ctx, &ctx->d_scratch, need));
-        ctx->scratch_bytes = need;
-    }
-    auto res = ctx->plans.emplace(key, pl);
+    // descriptor of the context's own Matsubara sweep
+    scd::GrainSweep gs{};
+    gs.lines = ctx->d_lines;
+    gs.groups = pl.d_groups;
+    gs.image_in = ctx->d_img_in;
+    gs.image_out = ctx->d_img_out;
+    gs.exits[0] = ctx->d_exit[0];
+    gs.exits[1] = ctx->d_exit[1];
+    gs.energies = nullptr;
+    gs.t = ctx->geo.prm.t;
+    gs.h = ctx->geo.prm.h;
+    gs.broadening = 0.0;
+    gs.n_e = n_e;
+    gs.lanes = lanes;
+    gs.lines_per_warp = G;
+    gs.ne_pad = lanes * ept;
+    gs.max_ns = std::max(ctx->geo.max_ns, 1);
+    CK(dalloc(ctx, &pl.d_grain, sizeof(gs)));
+    CK(cudaMemcpy(pl.d_grain, &gs, sizeof(gs), cudaMemcpyHostToDevice));
+    auto res = ctx->plans.emplace(key, std::move(pl));
     *out = &res.first->second;
     return SC_OK;
 }
 
-sc_status check_ctx(sc_ctx *ctx) {
-    if (!ctx) return SC_EINVAL;
-    if (ctx->host_only) return set_err(ctx, SC_ESTATE, "context was created with host_only = 1");
-    if (ctx->failed) return SC_ESTATE;
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
-    return SC_OK;
-}
-
-// rotate the fields, then sweep; exits go from exit_prev to exit_cur
-sc_status run_sweep(sc_ctx *ctx, const Plan &pl, int n_e, bool retarded, const double *d_energies,
-                    double broadening, void *img_out, const void *exit_prev, void *exit_cur, bool first,
-                    cudaStream_t st) {
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], st));
+sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st) {
     if (ctx->fp64) {
         CK(scd::launch_rotate(true, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
                               ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_img_in,
@@ -227,35 +216,45 @@ sc_status run_sweep(sc_ctx *ctx, const Plan &pl, int n_e, bool retarded, const d
         CK(scd::launch_rotate_f32(ctx->d_line_f32, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pair_f32, ctx->grid,
                                   ctx->d_ghost, ctx->d_delta_f, ctx->d_aind_f, (float4 *)ctx->d_img_in, st));
     }
+    return SC_OK;
+}
+
+sc_status rotate_back(sc_ctx *ctx, cudaStream_t st) {
+    if (ctx->fp64)
+        CK(scd::launch_rotate_back(true, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                   ctx->d_img_out, ctx->d_acc, st));
+    else
+        CK(scd::launch_rotate_back_f32(ctx->d_pair_f32, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                       (const float4 *)ctx->d_img_out, ctx->d_acc, st));
+    return SC_OK;
+}
+
+}  // namespace sc_internal
+
+namespace {
+
+using sc_internal::check_ctx;
+using sc_internal::make_plan;
+
+// one persistent sweep launch over the plan's items for one grain descriptor
+sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *d_grain, bool retarded,
+                            bool first, int parity, cudaStream_t st) {
+    CKS(ensure_scratch(ctx, (size_t)pl.grid_blocks * 4 * (size_t)pl.stride * 2 * ctx->real_bytes));
     CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], st));
     scd::SweepLaunch a{};
-    a.lines = ctx->d_lines;
-    a.groups = pl.d_groups;
-    a.n_groups = pl.n_groups;
-    a.lines_per_warp = pl.lines_per_warp;
-    a.lanes_per_line = pl.lanes;
-    a.energies_per_lane = pl.ept;
-    a.n_e = n_e;
-    a.t = ctx->geo.prm.t;
-    a.h = ctx->geo.prm.h;
-    a.image_in = ctx->d_img_in;
-    a.image_out = img_out;
-    a.exit_prev = exit_prev;
-    a.exit_cur = exit_cur;
-    a.first_sweep = first ? 1 : 0;
+    a.grains = d_grain;
+    a.items = pl.d_items;
+    a.n_items = pl.n_groups;
+    a.counter = ctx->d_counter;
     a.scratch = ctx->d_scratch;
     a.scratch_stride = pl.stride;
-    a.max_ns = std::max(ctx->geo.max_ns, 1);
-    a.ne_pad = pl.lanes * pl.ept;
-    a.counter = ctx->d_counter;
+    a.energies_per_lane = pl.ept;
+    a.first_sweep = first ? 1 : 0;
+    a.parity = parity;
+    a.retarded = retarded ? 1 : 0;
     a.grid_blocks = pl.grid_blocks;
     a.block_threads = 128;
-    a.retarded = retarded ? 1 : 0;
-    a.energies = d_energies;
-    a.broadening = broadening;
     CK(scd::launch_sweep(ctx->fp64, a, st));
-    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], st));
     return SC_OK;
 }
 
@@ -277,8 +276,6 @@ sc_status copy_out(sc_ctx *ctx, void *dst, const void *src, size_t bytes, int on
     if (!on_device) CK(cudaStreamSynchronize(st));
     return SC_OK;
 }
-
-size_t npts(const sc_ctx *ctx) { return (size_t)ctx->geo.nx * ctx->geo.ny; }
 
 }  // namespace
 
@@ -317,6 +314,7 @@ sc_status sc_destroy(sc_ctx *ctx) {
     for (void *p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (!ctx->allocs.empty()) (void)cudaGetLastError();  // teardown errors are not the caller's
     delete ctx;
     return SC_OK;
 }
@@ -584,7 +582,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     }
 #undef CA
 #undef CP
-    sc_status st = make_plan(ctx, ctx->n_e, &ctx->main_plan);
+    sc_status st = make_plan(ctx, ctx->n_e, 0, &ctx->main_plan);
     if (st != SC_OK) {
         g_create_error = ctx->err;
         sc_destroy(ctx);
@@ -622,6 +620,8 @@ sc_status sc_get_info(const sc_ctx *ctx, sc_info *info) {
             info->ms_rotate = a;
             info->ms_sweep = b;
             info->ms_rotate_back = c;
+        } else {
+            (void)cudaGetLastError();  // a failed query must not linger as the thread's last error
         }
     }
     return SC_OK;
@@ -661,21 +661,20 @@ sc_status sc_reset_boundary(sc_ctx *ctx) {
 
 sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream) {
     CKS(check_ctx(ctx));
+    if (ctx->batch_member) return set_err(ctx, SC_ESTATE, "this context belongs to a batch: use sc_batch_sweep");
     cudaStream_t st = (cudaStream_t)stream;
-    const int nxt = 1 - ctx->cur;
-    CKS(run_sweep(ctx, *ctx->main_plan, ctx->n_e, false, nullptr, 0.0, ctx->d_img_out, ctx->d_exit[ctx->cur],
-                  ctx->d_exit[nxt], !ctx->have_boundary, st));
-    if (ctx->fp64)
-        CK(scd::launch_rotate_back(true, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
-                                   ctx->d_img_out, ctx->d_acc, st));
-    else
-        CK(scd::launch_rotate_back_f32(ctx->d_pair_f32, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
-                                       (const float4 *)ctx->d_img_out, ctx->d_acc, st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[0], st));
+    CKS(sc_internal::rotate_fields(ctx, st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], st));
+    const Plan &pl = *ctx->main_plan;
+    CKS(launch_plan_sweep(ctx, pl, pl.d_grain, false, !ctx->have_boundary, ctx->cur, st));
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], st));
+    CKS(sc_internal::rotate_back(ctx, st));
     if (ctx->timing) {
         CK(cudaEventRecord(ctx->ev[3], st));
         ctx->timed = true;
     }
-    ctx->cur = nxt;
+    ctx->cur ^= 1;
     ctx->have_boundary = true;
     ctx->have_sweep = true;
     ctx->have_outputs = false;
@@ -770,27 +769,21 @@ sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broad
             return set_err(ctx, SC_EINVAL, "energies must be symmetric about zero");
     cudaStream_t st = (cudaStream_t)stream;
     Plan *pl = nullptr;
-    CKS(make_plan(ctx, n_e, &pl));
+    CKS(make_plan(ctx, n_e, 0, &pl));
     const size_t nL = ctx->geo.lines.size();
     const size_t cplx = 2 * ctx->real_bytes;
     double *d_en = nullptr;
     void *d_ex[2] = {nullptr, nullptr};
     void *d_img = nullptr;
     double *d_out = nullptr;
+    scd::GrainSweep *d_gs = nullptr;
     sc_status rc = SC_OK;
-    auto cleanup = [&]() {
-        cudaStreamSynchronize(st);
-        dfree(ctx, d_en);
-        dfree(ctx, d_ex[0]);
-        dfree(ctx, d_ex[1]);
-        dfree(ctx, d_img);
-        if (d_out != ldos_out) dfree(ctx, d_out);
-    };
     do {
         cudaError_t e;
         if ((e = dalloc(ctx, &d_en, n_e * sizeof(double))) != cudaSuccess ||
             (e = dalloc(ctx, &d_ex[0], 2 * nL * n_e * cplx)) != cudaSuccess ||
             (e = dalloc(ctx, &d_ex[1], 2 * nL * n_e * cplx)) != cudaSuccess ||
+            (e = dalloc(ctx, &d_gs, sizeof(scd::GrainSweep))) != cudaSuccess ||
             (e = dalloc(ctx, &d_img, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes)) != cudaSuccess) {
             rc = set_err(ctx, SC_ENOMEM, std::string("ldos buffers: ") + cudaGetErrorString(e));
             break;
@@ -800,17 +793,33 @@ sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broad
             rc = set_err(ctx, SC_ENOMEM, "ldos output");
             break;
         }
+        scd::GrainSweep gs{};
+        gs.lines = ctx->d_lines;
+        gs.groups = pl->d_groups;
+        gs.image_in = ctx->d_img_in;
+        gs.image_out = d_img;
+        gs.exits[0] = d_ex[0];
+        gs.exits[1] = d_ex[1];
+        gs.energies = d_en;
+        gs.t = ctx->geo.prm.t;
+        gs.h = ctx->geo.prm.h;
+        gs.broadening = broadening;
+        gs.n_e = n_e;
+        gs.lanes = pl->lanes;
+        gs.lines_per_warp = pl->lines_per_warp;
+        gs.ne_pad = pl->lanes * pl->ept;
+        gs.max_ns = std::max(ctx->geo.max_ns, 1);
         if ((e = cudaMemcpyAsync(d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess) {
+            (e = cudaMemcpyAsync(d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
             rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
             break;
         }
-        int c = 0;
+        rc = sc_internal::rotate_fields(ctx, st);
         const int nb = std::max(1, n_burnin);
-        for (int it = 0; it < nb && rc == SC_OK; ++it) {
-            rc = run_sweep(ctx, *pl, n_e, true, d_en, broadening, d_img, d_ex[c], d_ex[1 - c], it == 0, st);
-            c = 1 - c;
-        }
+        for (int it = 0; it < nb && rc == SC_OK; ++it)
+            rc = launch_plan_sweep(ctx, *pl, d_gs, true, it == 0, it & 1, st);
         if (rc != SC_OK) break;
         if ((e = scd::launch_ldos_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
                                        d_img, n_e, d_out, st)) != cudaSuccess) {
@@ -825,7 +834,14 @@ sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broad
             }
         }
     } while (0);
-    cleanup();
+    cudaStreamSynchronize(st);
+    dfree(ctx, d_en);
+    dfree(ctx, d_ex[0]);
+    dfree(ctx, d_ex[1]);
+    dfree(ctx, d_img);
+    dfree(ctx, d_gs);
+    if (d_out != ldos_out) dfree(ctx, d_out);
+    // the rotated fields were overwritten with the same values; nothing else changed
     return rc;
 }
 

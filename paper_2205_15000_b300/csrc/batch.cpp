@@ -1,0 +1,391 @@
+// Batched sweep: many grains of uneven size, shape, pairing, temperature,
+// field and angle count in one persistent launch.  The work list holds
+// (grain, line group) items of every member, longest first; each grain keeps
+// its own lane layout (energy lanes per line), all grains share the number of
+// energies per lane, which is the kernel's template parameter and is chosen
+// by timing (sc_batch_autotune).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "context.hpp"
+
+struct sc_batch {
+    std::vector<sc_ctx *> members;
+    int device = 0;
+    bool fp64 = false;
+    int ept = 0;
+    int sm_count = 0;
+    scd::GrainSweep *d_grains = nullptr;
+    int2 *d_items = nullptr;
+    int32_t n_items = 0;
+    int64_t stride = 0;
+    int grid_blocks = 0;
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t *d_counter = nullptr;
+    int parity = 0;
+    bool have_boundary = false;
+    int64_t steps_per_sweep = 0;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool timed = false;
+    // captured iterations: graph[p] = one sweep starting from parity p (+ outputs)
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_outputs = -1;
+    int graph_ept = 0;
+    cudaEvent_t sync_ev[2] = {nullptr, nullptr};
+    bool failed = false;
+    std::string err;
+};
+
+namespace {
+
+sc_status berr(sc_batch *b, sc_status st, const std::string &msg) {
+    b->err = msg;
+    if (st == SC_ECUDA || st == SC_ENOMEM) b->failed = true;
+    sc_internal::set_thread_error(msg.c_str());
+    return st;
+}
+
+#define BCK(expr)                                                                    \
+    do {                                                                             \
+        cudaError_t e_ = (expr);                                                     \
+        if (e_ != cudaSuccess)                                                       \
+            return berr(b, e_ == cudaErrorMemoryAllocation ? SC_ENOMEM : SC_ECUDA,   \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+void free_graphs(sc_batch *b) {
+    for (auto &g : b->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->graph_outputs = -1;
+}
+
+void free_plan_buffers(sc_batch *b) {
+    cudaFree(b->d_grains);
+    cudaFree(b->d_items);
+    b->d_grains = nullptr;
+    b->d_items = nullptr;
+}
+
+// Lay out the work list for `ept` energies per lane.
+sc_status build(sc_batch *b, int ept) {
+    free_graphs(b);  // captured graphs refer to the buffers rebuilt here
+    std::vector<scd::GrainSweep> gs(b->members.size());
+    struct It {
+        int cost, grain, group;
+    };
+    std::vector<It> items;
+    int64_t stride = 0;
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        sc_ctx *c = b->members[g];
+        if (c->n_e > 32 * ept)
+            return berr(b, SC_EINVAL, "a member has more energies than 32 lanes x energies_per_lane");
+        Plan *pl = nullptr;
+        sc_status st = sc_internal::make_plan(c, c->n_e, ept, &pl);
+        if (st != SC_OK) return berr(b, st, c->err);
+        scd::GrainSweep &d = gs[g];
+        d.lines = c->d_lines;
+        d.groups = pl->d_groups;
+        d.image_in = c->d_img_in;
+        d.image_out = c->d_img_out;
+        d.exits[0] = c->d_exit[0];
+        d.exits[1] = c->d_exit[1];
+        d.energies = nullptr;
+        d.t = c->geo.prm.t;
+        d.h = c->geo.prm.h;
+        d.broadening = 0.0;
+        d.n_e = c->n_e;
+        d.lanes = pl->lanes;
+        d.lines_per_warp = pl->lines_per_warp;
+        d.ne_pad = pl->lanes * pl->ept;
+        d.max_ns = std::max(c->geo.max_ns, 1);
+        stride = std::max(stride, pl->stride);
+        // cost of a group ~ steps x energies handled per lane
+        for (int q = 0; q < pl->n_groups; ++q) items.push_back({pl->group_cost[q] * ept, (int)g, q});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+    std::vector<int2> flat(items.size());
+    for (size_t i = 0; i < items.size(); ++i) flat[i] = make_int2(items[i].grain, items[i].group);
+    free_plan_buffers(b);
+    BCK(cudaMalloc(&b->d_grains, gs.size() * sizeof(scd::GrainSweep)));
+    BCK(cudaMemcpy(b->d_grains, gs.data(), gs.size() * sizeof(scd::GrainSweep), cudaMemcpyHostToDevice));
+    BCK(cudaMalloc(&b->d_items, flat.size() * sizeof(int2)));
+    BCK(cudaMemcpy(b->d_items, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    b->n_items = (int32_t)flat.size();
+    b->stride = stride;
+    int occ = scd::sweep_occupancy(b->fp64, ept, 128);
+    if (occ < 1) occ = 1;
+    b->grid_blocks = std::max(1, std::min(b->sm_count * occ, (b->n_items + 3) / 4));
+    const size_t need = (size_t)b->grid_blocks * 4 * (size_t)stride * 2 * (b->fp64 ? 8 : 4);
+    if (need > b->scratch_bytes) {
+        cudaFree(b->d_scratch);
+        b->d_scratch = nullptr;
+        b->scratch_bytes = 0;
+        BCK(cudaMalloc(&b->d_scratch, need));
+        b->scratch_bytes = need;
+    }
+    b->ept = ept;
+    return SC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_batch_destroy(sc_batch *b) {
+    if (!b) return SC_EINVAL;
+    cudaSetDevice(b->device);
+    for (sc_ctx *c : b->members) sc_destroy(c);
+    free_plan_buffers(b);
+    cudaFree(b->d_scratch);
+    cudaFree(b->d_counter);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
+    free_graphs(b);
+    for (cudaEvent_t e : b->sync_ev)
+        if (e) cudaEventDestroy(e);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    (void)cudaGetLastError();  // teardown errors are not the caller's
+    delete b;
+    return SC_OK;
+}
+
+sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane, sc_batch **out) {
+    sc_internal::set_thread_error("");
+    if (!params || !out || n < 1) {
+        sc_internal::set_thread_error("need params, out and n >= 1");
+        return SC_EINVAL;
+    }
+    if (energies_per_lane < 0 || energies_per_lane > 8) {
+        sc_internal::set_thread_error("energies_per_lane must be 0 (automatic) or 1..8");
+        return SC_EINVAL;
+    }
+    *out = nullptr;
+    sc_batch *b = new (std::nothrow) sc_batch();
+    if (!b) return SC_ENOMEM;
+    int max_ne = 0;
+    for (int g = 0; g < n; ++g) {
+        if (params[g].precision != params[0].precision) {
+            sc_batch_destroy(b);
+            sc_internal::set_thread_error("all members of a batch need the same precision");
+            return SC_EINVAL;
+        }
+        if (params[g].host_only) {
+            sc_batch_destroy(b);
+            sc_internal::set_thread_error("batch members cannot be host_only");
+            return SC_EINVAL;
+        }
+        sc_ctx *c = nullptr;
+        sc_status st = sc_create(&params[g], &c);
+        if (st != SC_OK) {
+            std::string why = std::string("member ") + std::to_string(g) + ": " + sc_last_error(nullptr);
+            sc_batch_destroy(b);
+            sc_internal::set_thread_error(why.c_str());
+            return st;
+        }
+        c->batch_member = true;
+        b->members.push_back(c);
+        max_ne = std::max(max_ne, c->n_e);
+        int64_t steps = 0;
+        for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
+        b->steps_per_sweep += steps * c->n_e;
+    }
+    b->fp64 = params[0].precision == SC_PREC_FP64;
+    b->device = b->members[0]->device;
+    b->sm_count = b->members[0]->sm_count;
+    sc_status st = SC_OK;
+    cudaError_t e = cudaMalloc(&b->d_counter, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    if (e != cudaSuccess) st = SC_ECUDA;
+    int ept = energies_per_lane;
+    if (!ept) ept = std::min(8, std::max(4, (max_ne + 31) / 32));
+    if (st == SC_OK) st = build(b, ept);
+    if (st != SC_OK) {
+        std::string why = b->err.empty() ? "device setup failed" : b->err;
+        sc_batch_destroy(b);
+        sc_internal::set_thread_error(why.c_str());
+        return st;
+    }
+    *out = b;
+    return SC_OK;
+}
+
+sc_status sc_batch_member(sc_batch *b, int32_t i, sc_ctx **out) {
+    if (!b || !out || i < 0 || i >= (int32_t)b->members.size()) return SC_EINVAL;
+    *out = b->members[i];
+    return SC_OK;
+}
+
+sc_status sc_batch_sweep(sc_batch *b, void *stream) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    BCK(cudaSetDevice(b->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    for (sc_ctx *c : b->members) {
+        if (c->failed) return berr(b, SC_ESTATE, "a member context failed");
+        sc_status s = sc_internal::rotate_fields(c, st);
+        if (s != SC_OK) return berr(b, s, c->err);
+    }
+    BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
+    // while a graph is being captured the timing events become external event
+    // nodes, so that every replay records them
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BCK(cudaStreamIsCapturing(st, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    BCK(cudaEventRecordWithFlags(b->ev[0], st, ev_flags));
+    scd::SweepLaunch a{};
+    a.grains = b->d_grains;
+    a.items = b->d_items;
+    a.n_items = b->n_items;
+    a.counter = b->d_counter;
+    a.scratch = b->d_scratch;
+    a.scratch_stride = b->stride;
+    a.energies_per_lane = b->ept;
+    a.first_sweep = b->have_boundary ? 0 : 1;
+    a.parity = b->parity;
+    a.retarded = 0;
+    a.grid_blocks = b->grid_blocks;
+    a.block_threads = 128;
+    BCK(scd::launch_sweep(b->fp64, a, st));
+    BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
+    b->timed = true;
+    for (sc_ctx *c : b->members) {
+        sc_status s = sc_internal::rotate_back(c, st);
+        if (s != SC_OK) return berr(b, s, c->err);
+        c->cur = b->parity ^ 1;
+        c->have_boundary = true;
+        c->have_sweep = true;
+        c->have_outputs = false;
+    }
+    b->parity ^= 1;
+    b->have_boundary = true;
+    return SC_OK;
+}
+
+// one batch iteration (sweep, and optionally every member's outputs) on stream st
+static sc_status iteration(sc_batch *b, int with_outputs, cudaStream_t st) {
+    sc_status s = sc_batch_sweep(b, st);
+    if (s != SC_OK) return s;
+    if (with_outputs)
+        for (sc_ctx *c : b->members) {
+            s = sc_gap_update(c, nullptr, nullptr, 1, st);  // computes Delta_new, j, F on the device
+            if (s != SC_OK) return berr(b, s, c->err);
+        }
+    return SC_OK;
+}
+
+sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream) {
+    if (!b || n_sweeps < 0) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    BCK(cudaSetDevice(b->device));
+    cudaStream_t user = (cudaStream_t)stream;
+    if (!b->gstream) {
+        BCK(cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking));
+        BCK(cudaEventCreateWithFlags(&b->sync_ev[0], cudaEventDisableTiming));
+        BCK(cudaEventCreateWithFlags(&b->sync_ev[1], cudaEventDisableTiming));
+    }
+    // the first sweep from fresh boundary values runs eagerly (different launch arguments)
+    int done = 0;
+    BCK(cudaEventRecord(b->sync_ev[0], user));
+    BCK(cudaStreamWaitEvent(b->gstream, b->sync_ev[0], 0));
+    if (!b->have_boundary && n_sweeps > 0) {
+        sc_status s = iteration(b, with_outputs, b->gstream);
+        if (s != SC_OK) return s;
+        done = 1;
+    }
+    if (done < n_sweeps && (b->graph_outputs != (with_outputs ? 1 : 0) || b->graph_ept != b->ept || !b->graph[0])) {
+        free_graphs(b);
+        // capture one iteration per parity; the host state advances as if they ran,
+        // so after capturing both it is back where it started
+        for (int k = 0; k < 2; ++k) {
+            const int par = b->parity;
+            cudaGraph_t g = nullptr;
+            BCK(cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal));
+            sc_status s = iteration(b, with_outputs, b->gstream);
+            cudaError_t e = cudaStreamEndCapture(b->gstream, &g);
+            if (s != SC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            if (e != cudaSuccess) return berr(b, SC_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->graph[par], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return berr(b, SC_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+        }
+        b->graph_outputs = with_outputs ? 1 : 0;
+        b->graph_ept = b->ept;
+    }
+    for (; done < n_sweeps; ++done) {
+        BCK(cudaGraphLaunch(b->graph[b->parity], b->gstream));
+        // host mirror of what the graph did
+        for (sc_ctx *c : b->members) {
+            c->cur = b->parity ^ 1;
+            c->have_boundary = true;
+            c->have_sweep = true;
+            c->have_outputs = with_outputs != 0;
+        }
+        b->parity ^= 1;
+    }
+    BCK(cudaEventRecord(b->sync_ev[1], b->gstream));
+    BCK(cudaStreamWaitEvent(user, b->sync_ev[1], 0));
+    return SC_OK;
+}
+
+sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *stream) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    int max_ne = 0;
+    for (sc_ctx *c : b->members) max_ne = std::max(max_ne, c->n_e);
+    int best = b->ept;
+    float best_ms = 1e30f;
+    for (int ept = 2; ept <= 8; ++ept) {
+        if (max_ne > 32 * ept) continue;
+        sc_status s = build(b, ept);
+        if (s != SC_OK) return s;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {  // the second sweep is the one timed
+            s = sc_batch_sweep(b, stream);
+            if (s != SC_OK) return s;
+            BCK(cudaEventSynchronize(b->ev[1]));
+            BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = ept;
+        }
+    }
+    sc_status s = build(b, best);
+    if (s != SC_OK) return s;
+    if (energies_per_lane) *energies_per_lane = best;
+    return SC_OK;
+}
+
+sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
+    if (!b || !info) return SC_EINVAL;
+    std::memset(info, 0, sizeof *info);
+    info->n_grains = (int32_t)b->members.size();
+    info->n_items = b->n_items;
+    info->energies_per_lane = b->ept;
+    info->steps_per_sweep = b->steps_per_sweep;
+    info->scratch_bytes = (int64_t)b->scratch_bytes;
+    if (b->timed) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(b->ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
+            info->ms_sweep = ms;
+        else
+            (void)cudaGetLastError();  // a failed query must not linger as the thread's last error
+    }
+    return SC_OK;
+}
+
+}  // extern "C"

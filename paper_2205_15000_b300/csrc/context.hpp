@@ -1,0 +1,86 @@
+// Private definitions shared by the C-ABI implementation files (api.cpp, batch.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "geometry.hpp"
+#include "kernels.cuh"
+#include "sc.h"
+
+// How the sweep kernel maps (line, energy) work to lanes for one energy count.
+struct Plan {
+    int lanes = 0, ept = 0, lines_per_warp = 0;
+    int32_t *d_groups = nullptr;         // [n_groups][lines_per_warp] line indices, -1 padded
+    int32_t n_groups = 0;
+    std::vector<int> group_cost;         // steps of the longest line of each group
+    int2 *d_items = nullptr;             // (0, group), longest first: single-context launches
+    scd::GrainSweep *d_grain = nullptr;  // descriptor of the context's Matsubara sweep
+    int grid_blocks = 0;
+    int64_t stride = 0;                  // scratch elements (complex) per warp
+};
+
+struct sc_ctx {
+    scg::Geometry geo;
+    int device = 0;
+    bool fp64 = false;
+    int n_e = 0;
+    int forced_lanes = 0;
+    double normD = 0.0;
+    size_t real_bytes = 4;
+    scd::GridDev grid{};
+    // geometry on the device
+    uint8_t *d_mask = nullptr;
+    int32_t *d_ghost = nullptr;
+    scd::LineGeo *d_geo = nullptr;
+    int32_t *d_slot_line = nullptr;
+    scd::PairDev *d_pairs = nullptr;
+    scd::BackLine *d_back = nullptr;
+    scd::LineDev *d_lines = nullptr;
+    std::map<int, Plan> plans;  // key: lanes * 16 + ept
+    Plan *main_plan = nullptr;
+    // fields and results
+    double *d_delta = nullptr, *d_aind = nullptr, *d_acc = nullptr, *d_dnew = nullptr, *d_j = nullptr,
+           *d_F = nullptr, *d_sums = nullptr, *d_jsum = nullptr, *d_G = nullptr, *d_diff = nullptr;
+    int G_width = 0;
+    bool have_aind = false;
+    void *d_img_in = nullptr, *d_img_out = nullptr;
+    void *d_exit[2] = {nullptr, nullptr};
+    int cur = 0;  // d_exit[cur] holds the latest exit values
+    bool have_boundary = false;
+    bool have_sweep = false;
+    bool have_outputs = false;
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    int32_t *d_counter = nullptr;
+    int sm_count = 0;
+    // FP32 production path tables and buffers
+    scd::LineF32 *d_line_f32 = nullptr;
+    scd::PairF32 *d_pair_f32 = nullptr;
+    float2 *d_delta_f = nullptr, *d_aind_f = nullptr;
+    // kernel timings
+    bool timing = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed = false;
+    bool failed = false;
+    bool host_only = false;
+    bool batch_member = false;  // swept only through its batch
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+namespace sc_internal {
+sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg);
+cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes);
+void dfree(sc_ctx *ctx, void *p);
+// lanes/EPT plan for n_e energies (forced_ept = 0: choose); builds the line groups
+sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out);
+// fields of the context onto its lattices (rotate kernels)
+sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st);
+// FS average of the context's image into its accumulators (rotate-back kernels)
+sc_status rotate_back(sc_ctx *ctx, cudaStream_t st);
+sc_status check_ctx(sc_ctx *ctx);
+void set_thread_error(const char *msg);
+}  // namespace sc_internal

@@ -112,44 +112,48 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(Swee
     typedef Cx<T> C;
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int Lw = a.lanes_per_line, G = a.lines_per_warp;
-    const int gi = lane / Lw, r = lane - gi * Lw;
-    const T4 *__restrict__ img = (const T4 *)a.image_in;
-    const C *__restrict__ exit_prev = (const C *)a.exit_prev;
-    C *__restrict__ exit_cur = (C *)a.exit_cur;
-    C *slab = (C *)a.scratch + wid * a.scratch_stride + (int64_t)gi * a.max_ns * a.ne_pad;
-    const T h = (T)a.h;
-    const int n_e = a.n_e;
-
-    // the lane's energies: z = zr0 + i zi (+ a along the line)
-    T zr0[EPT], zi[EPT];
-    int nid[EPT], mir[EPT];
-    bool ev[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-        const int n = r + Lw * e;
-        ev[e] = n < n_e;
-        const int nn = ev[e] ? n : n_e - 1;
-        nid[e] = nn;
-        if (RET) {
-            zr0[e] = (T)a.energies[nn];
-            zi[e] = (T)a.broadening;
-            mir[e] = n_e - 1 - nn;
-        } else {
-            zr0[e] = T(0);
-            zi[e] = (T)(a.t * (nn + 0.5));
-            mir[e] = nn;
-        }
-    }
+    C *const warp_slab = (C *)a.scratch + wid * a.scratch_stride;
 
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(a.counter, 1);
         item = __shfl_sync(FULL_MASK, item, 0);
-        if (item >= a.n_groups) break;
-        const int L = a.groups[(int64_t)item * G + gi];
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        const GrainSweep &gs = a.grains[it.x];
+        const int Lw = gs.lanes, G = gs.lines_per_warp;
+        const int gi = lane / Lw, r = lane - gi * Lw;
+        const T4 *__restrict__ img = (const T4 *)gs.image_in;
+        const C *__restrict__ exit_prev = (const C *)gs.exits[a.parity];
+        C *__restrict__ exit_cur = (C *)gs.exits[a.parity ^ 1];
+        C *slab = warp_slab + (int64_t)gi * gs.max_ns * gs.ne_pad;
+        const T h = (T)gs.h;
+        const int n_e = gs.n_e;
+        const int ne_pad = gs.ne_pad;
+
+        // the lane's energies: z = zr0 + i zi (+ a along the line)
+        T zr0[EPT], zi[EPT];
+        int nid[EPT], mir[EPT];
+        bool ev[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int n = r + Lw * e;
+            ev[e] = n < n_e;
+            const int nn = ev[e] ? n : n_e - 1;
+            nid[e] = nn;
+            if (RET) {
+                zr0[e] = (T)gs.energies[nn];
+                zi[e] = (T)gs.broadening;
+                mir[e] = n_e - 1 - nn;
+            } else {
+                zr0[e] = T(0);
+                zi[e] = (T)(gs.t * (nn + 0.5));
+                mir[e] = nn;
+            }
+        }
+        const int L = gs.groups[(int64_t)it.y * G + gi];
         const bool lv = L >= 0;
-        const LineDev &ln = a.lines[lv ? L : 0];
+        const LineDev &ln = gs.lines[lv ? L : 0];
         const int ns = lv ? ln.ns : 0;
         const int nsl = ns > 0 ? ns : 1;
         const int nsteps = lv ? ns + 1 : 0;
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(Swee
                 step_apply<T>(c, g[e]);
             }
             if (i < ns) {
-                C *dst = slab + (int64_t)i * a.ne_pad + r;
+                C *dst = slab + (int64_t)i * ne_pad + r;
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) dst[Lw * e] = g[e];
             }
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(Swee
             const bool comb = act && j < ns;     // a sample to combine at
             C gf[EPT];
             if (comb) {
-                const C *src = slab + (int64_t)qs * a.ne_pad;
+                const C *src = slab + (int64_t)qs * ne_pad;
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) gf[e] = src[RET ? mir[e] : (r + Lw * e)];
             }
@@ -308,11 +312,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(Swee
                     o.y = -twopi * sfr;                         // Im Sf
                     o.z = fourpi * sg;                          // Sg
                     o.w = T(2) * (slo.x * sFi - slo.y * sFr);   // SF
-                    ((T4 *)a.image_out)[slot0 + qs] = o;
+                    ((T4 *)gs.image_out)[slot0 + qs] = o;
                 }
             } else if (comb) {
                 // LDOS: -Im g / pi = Re[(1 - p)/(1 + p)] = 2 Re(1/D) - 1
-                T *outl = (T *)a.image_out + (int64_t)(slot0 + qs) * n_e;
+                T *outl = (T *)gs.image_out + (int64_t)(slot0 + qs) * n_e;
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) {
                     if (!ev[e]) continue;

@@ -67,31 +67,40 @@ struct PairF32 {
     int32_t l_lo, l_hi, line0, pad;
 };
 
-struct SweepLaunch {
+// Everything the sweep needs of one grain (one context, or one member of a batch).
+struct GrainSweep {
     const LineDev *lines;
-    const int32_t *groups;     // [n_groups][lines_per_warp], -1 padded
-    int32_t n_groups;
-    int32_t lines_per_warp;    // G
-    int32_t lanes_per_line;    // Lw (G * Lw = 32)
-    int32_t energies_per_lane; // EPT (template)
-    int32_t n_e;
-    double t;                  // eps_n = t (n + 1/2)
-    double h;
+    const int32_t *groups;     // [n_groups][lines_per_warp] line indices, -1 padded
     const void *image_in;      // T4 per slot
-    void *image_out;           // T4 per slot
-    const void *exit_prev;     // complex T [2 n_lines][n_e]
-    void *exit_cur;
-    int32_t first_sweep;
-    void *scratch;             // per warp slab
-    int64_t scratch_stride;    // complex T elements per warp
-    int32_t max_ns;
+    void *image_out;           // T4 per slot (retarded mode: n_e values per slot)
+    void *exits[2];            // complex T [2 n_lines][n_e]; a sweep reads exits[parity]
+                               // (previous sweep) and writes exits[parity ^ 1]
+    const double *energies;    // retarded mode: n_e real energies, symmetric about zero
+    double t;                  // Matsubara energies eps_n = t (n + 1/2)
+    double h;                  // lattice spacing
+    double broadening;         // retarded mode: z = eps + i broadening
+    int32_t n_e;
+    int32_t lanes;             // energy lanes per line, Lw (lines_per_warp * Lw = 32)
+    int32_t lines_per_warp;
     int32_t ne_pad;            // Lw * EPT
+    int32_t max_ns;            // longest line of the grain
+    int32_t pad;
+};
+
+// One persistent launch over the work items (grain, line group) of any number
+// of grains; items are taken from an atomic counter, longest first.
+struct SweepLaunch {
+    const GrainSweep *grains;
+    const int2 *items;         // (grain, group)
+    int32_t n_items;
     int32_t *counter;
+    void *scratch;             // per-warp slab of parked gammas
+    int64_t scratch_stride;    // complex T elements per warp (>= G * max_ns * ne_pad of every grain)
+    int32_t energies_per_lane; // EPT (template)
+    int32_t first_sweep;       // start every line from the homogeneous solution
+    int32_t parity;            // which exit buffer holds the previous sweep's values
+    int32_t retarded;          // LDOS mode
     int32_t grid_blocks, block_threads;
-    // retarded (LDOS) mode: complex energies z_n = eps_n + i*delta, partner energy index
-    int32_t retarded;
-    const double *energies;    // n_e real energies (retarded mode)
-    double broadening;
 };
 
 // launchers (return cudaError_t)

@@ -45,6 +45,14 @@ class sc_params(ctypes.Structure):
     ]
 
 
+class sc_batch_info(ctypes.Structure):
+    _fields_ = [
+        ("n_grains", ctypes.c_int32), ("n_items", ctypes.c_int32),
+        ("energies_per_lane", ctypes.c_int32), ("steps_per_sweep", ctypes.c_int64),
+        ("scratch_bytes", ctypes.c_int64), ("ms_sweep", ctypes.c_double),
+    ]
+
+
 class sc_info(ctypes.Structure):
     _fields_ = [
         ("n_pairs", ctypes.c_int32), ("n_lines", ctypes.c_int32),
@@ -63,8 +71,9 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
-            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_last_error",
-            "sc_version"]
+            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_batch_create",
+            "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
+            "sc_batch_get_info", "sc_last_error", "sc_version"]
 
 
 def _load():
@@ -95,6 +104,13 @@ def _load():
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
+        "sc_batch_create": [vp, i32, i32, P(vp)],
+        "sc_batch_destroy": [vp],
+        "sc_batch_member": [vp, i32, P(vp)],
+        "sc_batch_sweep": [vp, vp],
+        "sc_batch_run": [vp, i32, i32, vp],
+        "sc_batch_autotune": [vp, P(i32), vp],
+        "sc_batch_get_info": [vp, P(sc_batch_info)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -246,6 +262,87 @@ def sc_sweep_lines_noalloc(samples, line_slot0, line_ns, line_len, entry, n_line
                                       float(h), _ptr(images), _ptr(exits), _stream(stream)))
 
 
+def sc_batch_create(params_list, energies_per_lane=0):
+    arr = (sc_params * len(params_list))(*params_list)
+    h = ctypes.c_void_p()
+    _check(lib.sc_batch_create(arr, len(params_list), int(energies_per_lane), ctypes.byref(h)))
+    return h
+
+
+def sc_batch_destroy(b):
+    _check(lib.sc_batch_destroy(b))
+
+
+def sc_batch_member(b, i):
+    h = ctypes.c_void_p()
+    _check(lib.sc_batch_member(b, int(i), ctypes.byref(h)))
+    return h
+
+
+def sc_batch_sweep(b, stream=None):
+    _check(lib.sc_batch_sweep(b, _stream(stream)))
+
+
+def sc_batch_run(b, n_sweeps, with_outputs=True, stream=None):
+    _check(lib.sc_batch_run(b, int(n_sweeps), int(bool(with_outputs)), _stream(stream)))
+
+
+def sc_batch_autotune(b, stream=None):
+    e = ctypes.c_int32(0)
+    _check(lib.sc_batch_autotune(b, ctypes.byref(e), _stream(stream)))
+    return e.value
+
+
+def sc_batch_get_info(b):
+    i = sc_batch_info()
+    _check(lib.sc_batch_get_info(b, ctypes.byref(i)))
+    return i
+
+
+class Batch:
+    """Many grains swept by one persistent launch."""
+
+    def __init__(self, prms, precision="fp32", energies_per_lane=0):
+        self.prms = [dict(p) for p in prms]
+        self._p = [make_params(p, precision) for p in prms]
+        self.h = sc_batch_create(self._p, energies_per_lane)
+        self.members = []
+        for i, p in enumerate(prms):
+            m = Context.__new__(Context)
+            m.prm = dict(p)
+            m._p = self._p[i]
+            m.h = sc_batch_member(self.h, i)
+            m.info = sc_get_info(m.h)
+            m.nx, m.ny, m.n_e, m.N = p["nx"], p["ny"], p["n_energies"], p["n_angles"]
+            m._owned = False
+            self.members.append(m)
+
+    def sweep(self, stream=None):
+        sc_batch_sweep(self.h, stream)
+
+    def autotune(self, stream=None):
+        return sc_batch_autotune(self.h, stream)
+
+    def run(self, n_sweeps, with_outputs=True, stream=None):
+        sc_batch_run(self.h, n_sweeps, with_outputs, stream)
+
+    def info(self):
+        return sc_batch_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            for m in self.members:
+                m.h = None
+            sc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """One grain: owns an sc_ctx.  Arrays in, arrays out (torch on the GPU)."""
 
@@ -260,9 +357,9 @@ class Context:
         self.N = prm["n_angles"]
 
     def close(self):
-        if self.h:
+        if self.h and getattr(self, "_owned", True):
             sc_destroy(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:

@@ -1,0 +1,107 @@
+"""Batched form: many grains of uneven size, shape, pairing, temperature,
+field and angle count in one persistent sweep launch must give every grain
+exactly what its own context gives (and, in FP64, what the oracle gives)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_15000_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _grains():
+    out = []
+    p = W.disc(4.0, 28, pairing=0, t=0.5, n_angles=16, n_energies=10, flux_quanta=0.7)
+    out.append((p, W.noisy_delta(p, 0.26, 0.1, seed=31)))
+    p = W.diamond(9.0, 36, pairing=1, t=0.2, n_angles=24, n_energies=40, flux_quanta=1.5)
+    out.append((p, W.noisy_delta(p, 0.24, 0.1, seed=32)))
+    p = W.polygon([0.0, 6.0, 7.0, 1.0], [0.0, -1.0, 5.0, 6.0], 0.25, pairing=1, t=0.3,
+                  n_angles=12, n_energies=27)
+    out.append((p, W.vortex_delta(p, 0.22, [(3.0, 2.5)], [-1], seed=33, rel_noise=0.05)))
+    p = W.square(6.0, 24, pairing=0, t=0.8, n_angles=8, n_energies=3)
+    out.append((p, W.noisy_delta(p, 0.15, 0.1, seed=34)))
+    return out
+
+
+def _outputs(ctx):
+    r = ctx.outputs()
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in r.items()}
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6)])
+@pytest.mark.parametrize("ept", [0, 3, 8])
+def test_batch_equals_single_contexts(precision, tol, ept):
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    b = sc.Batch([p for p, _ in grains], precision=precision, energies_per_lane=ept)
+    singles = [sc.Context(p, precision=precision) for p, _ in grains]
+    for (p, d), m, s in zip(grains, b.members, singles):
+        m.set_fields(d)
+        s.set_fields(d)
+    for it in range(3):
+        b.sweep()
+        for s in singles:
+            s.sweep()
+        for m, s in zip(b.members, singles):
+            rm, rs = _outputs(m), _outputs(s)
+            for k in ("delta_new", "j", "F"):
+                scale = max(np.max(np.abs(rs[k])), 1e-3)
+                assert np.max(np.abs(rm[k] - rs[k])) <= tol * scale, (it, k)
+    b.close()
+
+
+def test_batch_member_matches_oracle_fp64():
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    b = sc.Batch([p for p, _ in grains], precision="fp64")
+    for (p, d), m in zip(grains, b.members):
+        m.set_fields(d)
+    exits = [None] * len(grains)
+    for it in range(2):
+        b.sweep()
+        for g, (p, d) in enumerate(grains):
+            o = oracle.OracleGeom(p).full_sweep(d, None, exits[g])
+            exits[g] = o["exit"]
+            r = _outputs(b.members[g])
+            np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=1e-10, rtol=0)
+            np.testing.assert_allclose(r["j"], o["j"], atol=1e-10, rtol=0)
+    b.close()
+
+
+def test_batch_graph_run_and_autotune():
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    b = sc.Batch([p for p, _ in grains], precision="fp32")
+    ref = sc.Batch([p for p, _ in grains], precision="fp32")
+    for (p, d), m, mr in zip(grains, b.members, ref.members):
+        m.set_fields(d)
+        mr.set_fields(d)
+    ept = b.autotune()   # two timing sweeps per candidate
+    assert 2 <= ept <= 8
+    # reference: the same total number of eager sweeps
+    n_auto = sum(2 for e in range(2, 9) if max(p["n_energies"] for p, _ in grains) <= 32 * e)
+    for _ in range(n_auto):
+        ref.sweep()
+    b.run(5, with_outputs=True)        # graph replays
+    for _ in range(5):
+        ref.sweep()
+    for m, mr in zip(b.members, ref.members):
+        rm, rr = _outputs(m), _outputs(mr)
+        scale = np.max(np.abs(rr["delta_new"]))
+        assert np.max(np.abs(rm["delta_new"] - rr["delta_new"])) <= 2e-6 * scale
+    info = b.info()
+    assert info.n_grains == len(grains) and info.energies_per_lane == ept and info.steps_per_sweep > 0
+    b.close()
+    ref.close()
+
+
+def test_member_sweep_alone_is_rejected():
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    b = sc.Batch([p for p, _ in grains[:2]], precision="fp32")
+    b.members[0].set_fields(grains[0][1])
+    with pytest.raises(sc.ScError) as ei:
+        b.members[0].sweep()
+    assert ei.value.status == sc.SC_ESTATE
+    b.close()
