@@ -91,6 +91,7 @@ typedef struct {
     int64_t scratch_bytes;   /* device scratch used by the sweep */
     double ms_rotate, ms_sweep, ms_rotate_back; /* last sweep's kernel times when
                                 record_timings = 1 (sc_get_info then waits for that sweep) */
+    double ms_adjoint;       /* last adjoint sweep kernel, when record_timings = 1 */
 } sc_info;
 
 /* Fill defaults: 64x64 unit grid, s-wave disc, t = 0.5, 32 angles, 16 energies,
@@ -162,6 +163,19 @@ sc_status sc_picard_step(sc_ctx *ctx, void *stream);
    frozen for up to n_burnin sweeps.  ldos_out: n_e * nx * ny doubles. */
 sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening,
                   int32_t n_burnin, double *ldos_out, int on_device, void *stream);
+
+/* Adjoint of the last sweep (the differentiable form; the paper computes no
+   gradients).  Given the cotangents of that sweep's outputs -- dL/dDelta_new
+   (complex grid), dL/dj (vector grid), dL/dF(R) (grid), each NULL for zero,
+   and the scalar dL/d(F_total) -- it returns dL/dDelta(R) (complex grid) and
+   dL/dA_ind(R) (vector grid; may be NULL), with the boundary entry values of
+   the differentiated sweep held fixed.  Reverse mode through the closed-form
+   steps: per line the forward coherence functions are recomputed and parked
+   in device scratch, and the two adjoint chains run against their chains.
+   Requires a sweep of the current fields. */
+sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double *g_j,
+                           const double *g_F, double g_Ftotal, double *dL_ddelta,
+                           double *dL_daind, int on_device, void *stream);
 
 /* ---- batched form: many grains in one persistent launch ---------------- */
 typedef struct sc_batch sc_batch;

@@ -11,8 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libsc.so")
-SOURCES = ["kernels.cu", "lattice_f32.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu"]
-HEADERS = ["kernels.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp"]
+SOURCES = ["kernels.cu", "lattice_f32.cu", "adjoint.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu"]
+HEADERS = ["kernels.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp", "adjoint.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1,0 +1,38 @@
+// Launch interface of the adjoint sweep (see adjoint.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace scd {
+
+struct AdjointLaunch {
+    const GrainSweep *grain;   // the context's sweep descriptor (device)
+    const int2 *items;         // (0, group), longest first
+    int32_t n_items;
+    int32_t *counter;
+    void *scratch;             // per warp: [lines][max_ns][2][ne_pad] complex
+    int64_t scratch_stride;
+    const void *wimg;          // T4 per slot: cotangents of (Re Sf, Im Sf, Sg, SF)
+    void *gimg;                // T4 per slot, out (accumulated): cotangents of (Re, Im of Delta eta, a)
+    int32_t first_sweep;       // the differentiated sweep started from homogeneous values
+    int32_t parity;            // exit buffer the differentiated sweep read
+    int32_t energies_per_lane;
+    int32_t grid_blocks, block_threads;
+};
+
+cudaError_t launch_adjoint_sweep(bool fp64, const AdjointLaunch &a, cudaStream_t s);
+int adjoint_occupancy(bool fp64, int ept, int block_threads);
+cudaError_t launch_adjoint_outputs(const GridDev &grid, const uint8_t *mask, const double *delta,
+                                   const double *aind, double t, double normD, double kappa, double n_in,
+                                   const double *gdn, const double *gj, const double *gF, double gFtot,
+                                   double *gacc, double *gdelta, double *gaind, cudaStream_t s);
+cudaError_t launch_adjoint_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
+                                       const GridDev &grid, const uint8_t *mask, const double *gacc, void *wimg,
+                                       cudaStream_t s);
+cudaError_t launch_adjoint_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_line, int64_t n_slots,
+                                  const PairDev *pairs, const GridDev &grid, const int32_t *ghost,
+                                  const void *gimg, double *gdelta, double *gaind, cudaStream_t s);
+
+}  // namespace scd

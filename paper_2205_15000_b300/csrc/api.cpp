@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint.cuh"
 #include "context.hpp"
 
 namespace {
@@ -314,6 +315,8 @@ sc_status sc_destroy(sc_ctx *ctx) {
     for (void *p : ctx->allocs) cudaFree(p);
     for (cudaEvent_t e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->ev_adj)
+        if (e) cudaEventDestroy(e);
     if (!ctx->allocs.empty()) (void)cudaGetLastError();  // teardown errors are not the caller's
     delete ctx;
     return SC_OK;
@@ -549,6 +552,10 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             cudaError_t err = cudaEventCreate(&e);
             if (err != cudaSuccess) return fail_cuda(err, "cudaEventCreate");
         }
+        for (auto &e : ctx->ev_adj) {
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return fail_cuda(err, "cudaEventCreate");
+        }
     }
     {
         cudaError_t err = cudaMemset(ctx->d_delta, 0, 2 * np * sizeof(double));
@@ -624,6 +631,14 @@ sc_status sc_get_info(const sc_ctx *ctx, sc_info *info) {
             (void)cudaGetLastError();  // a failed query must not linger as the thread's last error
         }
     }
+    if (ctx->timing && ctx->adj_timed) {
+        float a = 0.f;
+        if (cudaEventSynchronize(ctx->ev_adj[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&a, ctx->ev_adj[0], ctx->ev_adj[1]) == cudaSuccess)
+            info->ms_adjoint = a;
+        else
+            (void)cudaGetLastError();
+    }
     return SC_OK;
 }
 
@@ -667,7 +682,8 @@ sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream) {
     CKS(sc_internal::rotate_fields(ctx, st));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[1], st));
     const Plan &pl = *ctx->main_plan;
-    CKS(launch_plan_sweep(ctx, pl, pl.d_grain, false, !ctx->have_boundary, ctx->cur, st));
+    ctx->last_first = !ctx->have_boundary;
+    CKS(launch_plan_sweep(ctx, pl, pl.d_grain, false, ctx->last_first, ctx->cur, st));
     if (ctx->timing) CK(cudaEventRecord(ctx->ev[2], st));
     CKS(sc_internal::rotate_back(ctx, st));
     if (ctx->timing) {
@@ -843,6 +859,89 @@ sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broad
     if (d_out != ldos_out) dfree(ctx, d_out);
     // the rotated fields were overwritten with the same values; nothing else changed
     return rc;
+}
+
+sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double *g_j, const double *g_F,
+                           double g_Ftotal, double *dL_ddelta, double *dL_daind, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!ctx->have_sweep) return set_err(ctx, SC_ESTATE, "the adjoint needs a sweep of the current fields");
+    if (!dL_ddelta) return set_err(ctx, SC_EINVAL, "dL_ddelta is required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t np = npts(ctx);
+    const size_t t4 = ctx->fp64 ? 32 : 16;
+    const Plan &pl = *ctx->main_plan;
+    if (!ctx->d_gacc) {
+        CK(dalloc(ctx, &ctx->d_gacc, 5 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gdelta, 2 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gaind, 2 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gin, 5 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_wimg, ctx->geo.n_slots * t4));
+        CK(dalloc(ctx, &ctx->d_gimg, ctx->geo.n_slots * t4));
+    }
+    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128));
+    const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+    const int64_t stride = 2 * pl.stride;
+    const size_t need = (size_t)blocks * 4 * (size_t)stride * 2 * ctx->real_bytes;
+    if (need > ctx->adj_scratch_bytes) {
+        dfree(ctx, ctx->d_adj_scratch);
+        ctx->d_adj_scratch = nullptr;
+        ctx->adj_scratch_bytes = 0;
+        CK(dalloc(ctx, &ctx->d_adj_scratch, need));
+        ctx->adj_scratch_bytes = need;
+    }
+    // output cotangents on the device
+    const double *gdn = g_delta_new, *gj = g_j, *gF = g_F;
+    if (!on_device) {
+        if (g_delta_new) {
+            CK(cudaMemcpyAsync(ctx->d_gin, g_delta_new, 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
+            gdn = ctx->d_gin;
+        }
+        if (g_j) {
+            CK(cudaMemcpyAsync(ctx->d_gin + 2 * np, g_j, 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
+            gj = ctx->d_gin + 2 * np;
+        }
+        if (g_F) {
+            CK(cudaMemcpyAsync(ctx->d_gin + 4 * np, g_F, np * sizeof(double), cudaMemcpyHostToDevice, st));
+            gF = ctx->d_gin + 4 * np;
+        }
+    }
+    CK(cudaMemsetAsync(ctx->d_gdelta, 0, 2 * np * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_gaind, 0, 2 * np * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_wimg, 0, ctx->geo.n_slots * t4, st));
+    CK(cudaMemsetAsync(ctx->d_gimg, 0, ctx->geo.n_slots * t4, st));
+    const double kappa = ctx->geo.prm.kappa;
+    const bool magn = kappa > 0.0 && std::isfinite(kappa) && ctx->have_aind;
+    CK(scd::launch_adjoint_outputs(ctx->grid, ctx->d_mask, ctx->d_delta, magn ? ctx->d_aind : nullptr,
+                                   ctx->geo.prm.t, ctx->normD, magn ? kappa : 0.0, (double)ctx->geo.n_in, gdn, gj, gF,
+                                   g_Ftotal, ctx->d_gacc, ctx->d_gdelta, ctx->d_gaind, st));
+    CK(scd::launch_adjoint_rotate_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                       ctx->d_gacc, ctx->d_wimg, st));
+    CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
+    scd::AdjointLaunch a{};
+    a.grain = pl.d_grain;
+    a.items = pl.d_items;
+    a.n_items = pl.n_groups;
+    a.counter = ctx->d_counter;
+    a.scratch = ctx->d_adj_scratch;
+    a.scratch_stride = stride;
+    a.wimg = ctx->d_wimg;
+    a.gimg = ctx->d_gimg;
+    a.first_sweep = ctx->last_first ? 1 : 0;
+    a.parity = ctx->cur ^ 1;  // the buffer the last sweep read its entry values from
+    a.energies_per_lane = pl.ept;
+    a.grid_blocks = blocks;
+    a.block_threads = 128;
+    if (ctx->timing) CK(cudaEventRecord(ctx->ev_adj[0], st));
+    CK(scd::launch_adjoint_sweep(ctx->fp64, a, st));
+    if (ctx->timing) {
+        CK(cudaEventRecord(ctx->ev_adj[1], st));
+        ctx->adj_timed = true;
+    }
+    CK(scd::launch_adjoint_rotate(ctx->fp64, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
+                                  ctx->d_ghost, ctx->d_gimg, ctx->d_gdelta, ctx->d_gaind, st));
+    CKS(copy_out(ctx, dL_ddelta, ctx->d_gdelta, 2 * np * sizeof(double), on_device, st));
+    CKS(copy_out(ctx, dL_daind, ctx->d_gaind, 2 * np * sizeof(double), on_device, st));
+    return SC_OK;
 }
 
 // ---- inspection ----------------------------------------------------------

@@ -63,10 +63,17 @@ struct sc_ctx {
     // kernel timings
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_adj[2] = {nullptr, nullptr};
     bool timed = false;
+    bool adj_timed = false;
     bool failed = false;
     bool host_only = false;
     bool batch_member = false;  // swept only through its batch
+    bool last_first = false;    // the last sweep started from homogeneous values
+    // adjoint buffers (allocated on first use)
+    double *d_gacc = nullptr, *d_gdelta = nullptr, *d_gaind = nullptr, *d_gin = nullptr;
+    void *d_wimg = nullptr, *d_gimg = nullptr, *d_adj_scratch = nullptr;
+    size_t adj_scratch_bytes = 0;
     std::string err;
     std::vector<void *> allocs;
 };

@@ -43,11 +43,14 @@ struct Mth<float> {
 
 template <>
 struct Mth<double> {
-    static __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
-    static __device__ __forceinline__ double rsqrt(double v) { return 1.0 / ::sqrt(v); }
-    static __device__ __forceinline__ double sqrt(double v) { return ::sqrt(v); }
-    static __device__ __forceinline__ double expneg(double u) { return ::exp(-u); }
-    static __device__ __forceinline__ void sincos_(double x, double *s, double *c) { ::sincos(x, s, c); }
+    static __host__ __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+    static __host__ __device__ __forceinline__ double rsqrt(double v) { return 1.0 / ::sqrt(v); }
+    static __host__ __device__ __forceinline__ double sqrt(double v) { return ::sqrt(v); }
+    static __host__ __device__ __forceinline__ double expneg(double u) { return ::exp(-u); }
+    static __host__ __device__ __forceinline__ void sincos_(double x, double *s, double *c) {
+        *s = ::sin(x);
+        *c = ::cos(x);
+    }
 };
 
 template <typename T>
@@ -79,10 +82,12 @@ struct StepCoef {
 };
 
 template <typename T>
-__device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, StepCoef<T> &c) {
+__host__ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, StepCoef<T> &c) {
     typedef Mth<T> M;
     const T x = d2 - zr * zr + zi * zi;  // Re Omega^2
     const T y = T(-2) * zr * zi;         // Im Omega^2
+    using ::fabs;
+    using ::copysign;
     const T r = M::sqrt(x * x + y * y);
     const T hs = T(0.5) * (r + fabs(x));
     const T q = M::rsqrt(hs);            // 1/s
@@ -117,13 +122,117 @@ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, S
 }
 
 template <typename T>
-__device__ __forceinline__ void step_apply(const StepCoef<T> &c, Cx<T> &g) {
+__host__ __device__ __forceinline__ void step_apply(const StepCoef<T> &c, Cx<T> &g) {
     const T dx = g.x - c.gh.x, dy = g.y - c.gh.y;
     const T nr = dx * c.E.x - dy * c.E.y, ni = dx * c.E.y + dy * c.E.x;
     const T dnr = T(1) - (c.K.x * dx - c.K.y * dy), dni = -(c.K.x * dy + c.K.y * dx);
     const T rd = Mth<T>::rcp(dnr * dnr + dni * dni);
     g.x = c.gh.x + (nr * dnr + ni * dni) * rd;
     g.y = c.gh.y + (ni * dnr - nr * dni) * rd;
+}
+
+// ---------------------------------------------------------------------------
+// Derivatives of one closed-form step, for the adjoint sweep.  The step
+// gamma' = Phi(gamma; P, Q, R) is analytic in gamma and, separately, in the
+// coefficients P = Delta*, Q = z, R = Delta (Delta and Delta* treated as
+// independent variables).  With Omega^2 = P R - Q^2, w = Q + i Omega,
+// gamma_h = -R/w, E = exp(-2 Omega ell), c = (1 - E)/(2 Omega), K = i P c,
+// delta = gamma - gamma_h, N = 1 - K delta:
+//   dPhi/dgamma = E / N^2
+//   dOmega/dP = R/(2 Omega), dOmega/dR = P/(2 Omega), dOmega/dQ = -Q/Omega
+//   dgamma_h/dP = i gamma_h^2/(2 Omega), dgamma_h/dQ = i gamma_h/Omega,
+//   dgamma_h/dR = i/(2 Omega)
+//   dE/dX = -2 ell E dOmega/dX,  dc/dX = (ell E - c)/Omega dOmega/dX
+//   dPhi/dX = dgamma_h/dX (1 - E/N^2) + (delta/N) dE/dX + (delta^2 E/N^2) dK/dX
+// ---------------------------------------------------------------------------
+template <typename T>
+struct StepGrad {
+    Cx<T> dg, dP, dQ, dR;  // dPhi/dgamma, dPhi/dP, dPhi/dQ, dPhi/dR
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b) {
+    return Cx<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ Cx<T> crcp(Cx<T> a) {
+    const T r = Mth<T>::rcp(a.x * a.x + a.y * a.y);
+    return Cx<T>{a.x * r, -a.y * r};
+}
+
+// One step from g over a segment with Delta = (dr, di), z = (zr, zi), length ell:
+// returns gamma' in g_out and the derivatives in G.
+template <typename T>
+__host__ __device__ __forceinline__ void step_grad(T dr, T di, T zr, T zi, T ell, Cx<T> g, Cx<T> &g_out,
+                                                   StepGrad<T> &G) {
+    typedef Mth<T> M;
+    typedef Cx<T> C;
+    using ::copysign;
+    using ::fabs;
+    const T d2 = dr * dr + di * di;
+    const T x = d2 - zr * zr + zi * zi;
+    const T y = T(-2) * zr * zi;
+    const T r = M::sqrt(x * x + y * y);
+    const T hs = T(0.5) * (r + fabs(x));
+    const T q = M::rsqrt(hs);
+    const T s = hs * q;
+    const T yq = T(0.5) * y * q;
+    C Om;
+    if (x >= T(0)) {
+        Om.x = s;
+        Om.y = yq;
+    } else {
+        Om.x = fabs(yq);
+        Om.y = copysign(s, y);
+    }
+    const C z{zr, zi}, D{dr, di}, Dc{dr, -di};
+    const C w{zr - Om.y, zi + Om.x};
+    const C iw = crcp(w);
+    const C i2O = crcp(C{T(2) * Om.x, T(2) * Om.y});  // 1/(2 Omega)
+    const C gh = cmul(C{-dr, -di}, iw);
+    const T eu = M::expneg(T(2) * ell * Om.x);
+    T sn, cs;
+    M::sincos_(T(2) * ell * Om.y, &sn, &cs);
+    const C E{eu * cs, -eu * sn};
+    const C c = cmul(C{T(1) - E.x, -E.y}, i2O);
+    const C iDc_c = cmul(Dc, c);
+    const C K{-iDc_c.y, iDc_c.x};  // i Delta* c
+    const C del{g.x - gh.x, g.y - gh.y};
+    const C Kd = cmul(K, del);
+    const C N{T(1) - Kd.x, -Kd.y};
+    const C iN = crcp(N);
+    const C A2 = cmul(del, iN);                 // delta / N
+    const C u = cmul(A2, E);
+    g_out = C{gh.x + u.x, gh.y + u.y};
+    const C EN2 = cmul(E, cmul(iN, iN));        // E / N^2
+    G.dg = EN2;
+    const C A1{T(1) - EN2.x, -EN2.y};
+    const C A3 = cmul(cmul(del, del), EN2);      // delta^2 E / N^2
+    // dOmega/dX
+    const C OmP = cmul(D, i2O), OmR = cmul(Dc, i2O);
+    const C OmQ = cmul(C{T(-2) * z.x, T(-2) * z.y}, i2O);
+    // dgamma_h/dX
+    const C gh2 = cmul(gh, gh);
+    const C t1 = cmul(gh2, i2O);
+    const C ghP{-t1.y, t1.x};
+    const C t2 = cmul(gh, i2O);
+    const C ghQ{T(-2) * t2.y, T(2) * t2.x};
+    const C ghR{-i2O.y, i2O.x};
+    // E_X = eX OmX, c_X = cX OmX
+    const C eX{T(-2) * ell * E.x, T(-2) * ell * E.y};
+    const C cX = cmul(C{T(2) * (ell * E.x - c.x), T(2) * (ell * E.y - c.y)}, i2O);
+    const C iDcX = cmul(Dc, cX);
+    const C Bk{-iDcX.y, iDcX.x};                 // i Delta* cX
+    const C B1 = cmul(A2, eX), B2 = cmul(A3, Bk);
+    const C B{B1.x + B2.x, B1.y + B2.y};
+    const C ic{-c.y, c.x};
+    const C p1 = cmul(ghP, A1), p2 = cmul(OmP, B), p3 = cmul(A3, ic);
+    G.dP = C{p1.x + p2.x + p3.x, p1.y + p2.y + p3.y};
+    const C q1 = cmul(ghQ, A1), q2 = cmul(OmQ, B);
+    G.dQ = C{q1.x + q2.x, q1.y + q2.y};
+    const C r1 = cmul(ghR, A1), r2 = cmul(OmR, B);
+    G.dR = C{r1.x + r2.x, r1.y + r2.y};
 }
 
 }  // namespace scd

@@ -62,7 +62,7 @@ class sc_info(ctypes.Structure):
         ("lanes_per_line", ctypes.c_int32), ("energies_per_lane", ctypes.c_int32),
         ("lines_per_warp", ctypes.c_int32), ("scratch_bytes", ctypes.c_int64),
         ("ms_rotate", ctypes.c_double), ("ms_sweep", ctypes.c_double),
-        ("ms_rotate_back", ctypes.c_double),
+        ("ms_rotate_back", ctypes.c_double), ("ms_adjoint", ctypes.c_double),
     ]
 
 
@@ -71,7 +71,8 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
-            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_batch_create",
+            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
+            "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
 
@@ -104,6 +105,7 @@ def _load():
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
+        "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_batch_create": [vp, i32, i32, P(vp)],
         "sc_batch_destroy": [vp],
         "sc_batch_member": [vp, i32, P(vp)],
@@ -260,6 +262,12 @@ def sc_sweep_lines_noalloc(samples, line_slot0, line_ns, line_len, entry, n_line
     _check(lib.sc_sweep_lines_noalloc(_ptr(samples), _ptr(line_slot0), _ptr(line_ns), _ptr(line_len),
                                       _ptr(entry), int(n_lines), int(max_ns), int(n_e), float(t),
                                       float(h), _ptr(images), _ptr(exits), _stream(stream)))
+
+
+def sc_sweep_adjoint(ctx, g_delta_new, g_j, g_F, g_Ftotal, dL_ddelta, dL_daind, on_device=True,
+                     stream=None):
+    _check(lib.sc_sweep_adjoint(ctx, _ptr(g_delta_new), _ptr(g_j), _ptr(g_F), float(g_Ftotal),
+                                _ptr(dL_ddelta), _ptr(dL_daind), int(on_device), _stream(stream)), ctx)
 
 
 def sc_batch_create(params_list, energies_per_lane=0):
@@ -425,6 +433,25 @@ class Context:
         out = np.zeros(4 * self.info.n_samples)
         _check(lib.sc_debug_images(self.h, _ptr(out)), self.h)
         return out.reshape(-1, 4)
+
+    def adjoint(self, g_delta_new=None, g_j=None, g_F=None, g_Ftotal=0.0, stream=None):
+        """dL/dDelta(R) (complex) and dL/dA_ind(R) for output cotangents of the
+        last sweep (torch tensors or arrays; None = zero)."""
+        import torch
+
+        def dev(x, shape_last):
+            if x is None:
+                return None
+            t = torch.as_tensor(x, device="cuda")
+            if t.is_complex():
+                t = torch.view_as_real(t.to(torch.complex128).contiguous())
+            return t.to(torch.float64).contiguous()
+        gdn, gj, gF = dev(g_delta_new, 2), dev(g_j, 2), dev(g_F, 1)
+        dd = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        sc_sweep_adjoint(self.h, gdn, gj, gF, g_Ftotal, dd, da, True, stream)
+        self._adj_keep = (gdn, gj, gF)
+        return torch.view_as_complex(dd), da
 
     def ldos(self, energies, broadening, n_burnin=20, stream=None):
         import torch
