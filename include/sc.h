@@ -177,6 +177,15 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
                            const double *g_F, double g_Ftotal, double *dL_ddelta,
                            double *dL_daind, int on_device, void *stream);
 
+/* Adjoint of sc_ldos for an LDOS-map loss: runs the same n_burnin retarded
+   sweeps as sc_ldos (boundary values converged with Delta, A frozen), then
+   differentiates the last one with its entry values held fixed.  g_ldos:
+   dL/dN(R, eps) with the layout of ldos_out (n_e * nx * ny).  Returns
+   dL/dDelta(R) (complex grid) and dL/dA_ind(R) (vector grid; may be NULL). */
+sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening,
+                          int32_t n_burnin, const double *g_ldos, double *dL_ddelta,
+                          double *dL_daind, int on_device, void *stream);
+
 /* ---- batched form: many grains in one persistent launch ---------------- */
 typedef struct sc_batch sc_batch;
 typedef struct {

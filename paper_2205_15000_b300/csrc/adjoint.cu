@@ -64,8 +64,11 @@ __device__ __forceinline__ void atomic_add4(typename Vec4<T>::type *p, T a, T b,
 
 }  // namespace
 
-template <typename T, int EPT>
+template <typename T, int EPT, bool RET>
 __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
+    // parked per (sample, energy): 0 = gamma then beta, 1 = local beta cotangent,
+    // 2 (retarded) = gamma cotangent handed to the mirror energy's lane
+    constexpr int NS = RET ? 3 : 2;
     typedef typename Vec4<T>::type T4;
     typedef Cx<T> C;
     const int lane = threadIdx.x & 31;
@@ -80,19 +83,28 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
     const C *__restrict__ exit_prev = (const C *)gs.exits[a.parity];
     const T h = (T)gs.h;
     const int n_e = gs.n_e, ne_pad = gs.ne_pad;
-    C *slab = warp_slab + (int64_t)gi * gs.max_ns * 2 * ne_pad;
+    C *slab = warp_slab + (int64_t)gi * gs.max_ns * NS * ne_pad;
     const T pi = T(3.141592653589793);
 
-    T zi[EPT];
-    int nid[EPT];
+    T zr0[EPT], zi[EPT];
+    int nid[EPT], mir[EPT];
     bool ev[EPT];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int n = r + Lw * e;
         ev[e] = n < n_e;
         nid[e] = ev[e] ? n : n_e - 1;
-        zi[e] = (T)(gs.t * (nid[e] + 0.5));
+        if (RET) {
+            zr0[e] = (T)gs.energies[nid[e]];
+            zi[e] = (T)gs.broadening;
+            mir[e] = n_e - 1 - nid[e];
+        } else {
+            zr0[e] = T(0);
+            zi[e] = (T)(gs.t * (nid[e] + 0.5));
+            mir[e] = nid[e];
+        }
     }
+    const T *__restrict__ wl = (const T *)a.wimg;  // retarded: n_e weights per slot
 
     for (;;) {
         int item = 0;
@@ -113,7 +125,8 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
         const T lead = (T)ln.lead, tail = (T)ln.tail;
         const int slot0 = ln.slot0;
         const T4 *li = img + slot0;
-        auto park = [&](int i, int k, int e) -> C & { return slab[((int64_t)i * 2 + k) * ne_pad + r + Lw * e]; };
+        auto park = [&](int i, int k, int e) -> C & { return slab[((int64_t)i * NS + k) * ne_pad + r + Lw * e]; };
+        auto parkn = [&](int i, int k, int n) -> C & { return slab[((int64_t)i * NS + k) * ne_pad + n]; };
 
         // ---------------- pass 1: gamma along +e_par ----------------
         C g[EPT], g0[EPT];
@@ -123,7 +136,7 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 StepCoef<T> c;
-                step_coef<T>(sp.x, sp.y, d2, sp.z, zi[e], lead, c);
+                step_coef<T>(sp.x, sp.y, d2, zr0[e] + sp.z, zi[e], lead, c);
                 g[e] = c.gh;
             }
         } else {
@@ -150,7 +163,7 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
 #pragma unroll
                 for (int e = 0; e < EPT; ++e) {
                     StepCoef<T> c;
-                    step_coef<T>(dr, di, d2, av, zi[e], ell, c);
+                    step_coef<T>(dr, di, d2, zr0[e] + av, zi[e], ell, c);
                     step_apply<T>(c, g[e]);
                 }
                 if (i < ns) {
@@ -171,7 +184,7 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
 #pragma unroll
             for (int e = 0; e < EPT; ++e) {
                 StepCoef<T> c;
-                step_coef<T>(sh.x, sh.y, d2, -sh.z, zi[e], tail, c);
+                step_coef<T>(sh.x, sh.y, d2, zr0[e] - sh.z, zi[e], tail, c);
                 b[e] = c.gh;
             }
         } else {
@@ -204,19 +217,21 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
                     const T ell = (j == 0) ? tail : (j == ns ? lead : h);
                     const T d2 = dr * dr + di * di;
                     T4 W = {};
-                    if (at_sample) W = wimg[slot0 + q];
+                    if (!RET && at_sample) W = wimg[slot0 + q];
                     const C Wf{W.x, W.y};
+                    C gst[EPT];
 #pragma unroll
                     for (int e = 0; e < EPT; ++e) {
                         // beta step (angle p + P: a -> -a)
                         StepCoef<T> cb;
-                        step_coef<T>(dr, di, d2, -av, zi[e], ell, cb);
+                        step_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, cb);
                         step_apply<T>(cb, b[e]);
                         // forward segment with the same samples, differentiated at its start
                         const C start = at_sample ? park(q, 0, e) : g0[e];
+                        gst[e] = start;
                         C dummy;
                         StepGrad<T> Gd;
-                        step_grad<T>(dr, di, av, zi[e], ell, start, dummy, Gd);
+                        step_grad<T>(dr, di, zr0[e] + av, zi[e], ell, start, dummy, Gd);
                         if (ev[e]) {
                             const C l = lam[e];
                             const C t1 = cmul(cconj(Gd.dR), l), t2 = cmul(Gd.dP, cconj(l));
@@ -225,7 +240,7 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
                             ca += cmul(cconj(Gd.dQ), l).x;
                         }
                         C lnew = cmul(cconj(Gd.dg), lam[e]);
-                        if (at_sample && ev[e]) {
+                        if (!RET && at_sample && ev[e]) {
                             const C gf = start, bt = b[e];
                             // D = 1 + gamma conj(beta)
                             const C Dd{T(1) + gf.x * bt.x + gf.y * bt.y, gf.y * bt.x - gf.x * bt.y};
@@ -246,14 +261,46 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
                             const C sF = cmuli(cscale(cadd(gf, bt), T(-2) * W.w));
                             sdr += sF.x;
                             sdi += sF.y;
-                            park(q, 0, e) = bt;
                             park(q, 1, e) = bbar;
-                        } else if (at_sample) {
-                            park(q, 0, e) = b[e];
+                        } else if (!RET && at_sample) {
                             park(q, 1, e) = C{T(0), T(0)};
                         }
                         lam[e] = lnew;
                     }
+                    if (RET && at_sample) {
+                        // LDOS value of this lane's energy n: 2 Re(1/D) - 1 with
+                        // D = 1 + gamma_f(mirror n) conj(beta_n); the gamma cotangent
+                        // belongs to the forward chain of the mirror energy
+#pragma unroll
+                        for (int e = 0; e < EPT; ++e) {
+                            C gbar{T(0), T(0)}, bbar{T(0), T(0)};
+                            if (ev[e]) {
+                                const T Wv = wl[(int64_t)(slot0 + q) * n_e + nid[e]];
+                                const C gf = parkn(q, 0, mir[e]), bt = b[e];
+                                const C Dd{T(1) + gf.x * bt.x + gf.y * bt.y, gf.y * bt.x - gf.x * bt.y};
+                                const C iD = crcp(Dd);
+                                const C iD2 = cmul(iD, iD);
+                                gbar = cscale(cmul(cconj(iD2), bt), T(-2) * Wv);
+                                bbar = cscale(cmul(iD2, gf), T(-2) * Wv);
+                            }
+                            if (ev[e]) parkn(q, 2, mir[e]) = gbar;  // each valid energy has one partner
+                            park(q, 1, e) = bbar;
+                        }
+                    }
+                }
+                if (RET) {
+                    __syncwarp();
+                    if (at_sample) {
+#pragma unroll
+                        for (int e = 0; e < EPT; ++e) {
+                            if (ev[e]) lam[e] = cadd(lam[e], park(q, 2, e));
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (at_sample) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) park(q, 0, e) = b[e];
                 }
                 cdr = line_sum(cdr, Lw);
                 cdi = line_sum(cdi, Lw);
@@ -298,7 +345,7 @@ __global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
                             const C start = i < ns ? park(i, 0, e) : b0[e];
                             C dummy;
                             StepGrad<T> Gd;
-                            step_grad<T>(dr, di, -av, zi[e], ell, start, dummy, Gd);
+                            step_grad<T>(dr, di, zr0[e] - av, zi[e], ell, start, dummy, Gd);
                             if (ev[e]) {
                                 const C m = mu[e];
                                 const C t1 = cmul(cconj(Gd.dR), m), t2 = cmul(Gd.dP, cconj(m));
@@ -424,6 +471,57 @@ __global__ void adjoint_rotate_back_kernel(const PairDev *__restrict__ pairs, in
     }
 }
 
+// transpose of the LDOS rotate-back: N(R, e_n) = sum_p [w_{p+P} X_p(n) + w_p X_p(mirror n)]
+template <typename T>
+__global__ void adjoint_ldos_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pairs,
+                                         const BackLine *__restrict__ bl, GridDev grid,
+                                         const uint8_t *__restrict__ mask, const double *__restrict__ gN,
+                                         int32_t n_e, T *__restrict__ wimg) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (idx >= npts || !mask[idx]) return;
+    const double gn = gN[(int64_t)n * npts + idx], gm = gN[(int64_t)(n_e - 1 - n) * npts + idx];
+    if (gn == 0.0 && gm == 0.0) return;
+    const double fi = (double)(idx % grid.nx), fj = (double)(idx / grid.nx);
+    for (int p = 0; p < n_pairs; ++p) {
+        const PairDev pp = pairs[p];
+        // slot value n enters N(n) with w_{p+P} and N(mirror n) with w_p
+        const double gv = pp.wb * gn + pp.wa * gm;
+        const double u = fma(fi, -pp.ey, fma(fj, pp.ex, pp.u0));
+        const double v = fma(fi, pp.ex, fma(fj, pp.ey, pp.v0));
+        const double fu = floor(u), fv = floor(v);
+        const int iu = (int)fu, iv = (int)fv;
+        const double wu = u - fu, wv = v - fv;
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const int l = min(max(iu + bb, pp.l_lo), pp.l_hi);
+            const BackLine Ln = bl[pp.line0 + (l - pp.l_lo)];
+            const double wlin = bb ? wu : 1.0 - wu;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int m = min(max(iv + c, Ln.m0), Ln.m0 + Ln.ns - 1);
+                const double w = wlin * (c ? wv : 1.0 - wv);
+                if (w == 0.0) continue;
+                atomicAdd(&wimg[(int64_t)(Ln.slot0 + (m - Ln.m0)) * n_e + n], (T)(w * gv));
+            }
+        }
+    }
+}
+
+cudaError_t launch_adjoint_ldos_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
+                                     const GridDev &grid, const uint8_t *mask, const double *gN, int32_t n_e,
+                                     void *wimg, cudaStream_t st) {
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    const int bs = 128;
+    dim3 nb((unsigned)((npts + bs - 1) / bs), (unsigned)n_e);
+    if (fp64)
+        adjoint_ldos_back_kernel<double><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, gN, n_e, (double *)wimg);
+    else
+        adjoint_ldos_back_kernel<float><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, gN, n_e, (float *)wimg);
+    return cudaGetLastError();
+}
+
 // transpose of rotate_fields: scatter the sample-value cotangents onto the grid
 template <typename T>
 __global__ void adjoint_rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__restrict__ slot_line,
@@ -467,12 +565,12 @@ __global__ void adjoint_rotate_kernel(const LineGeo *__restrict__ geo, const int
         }
 }
 
-template <typename T>
+template <typename T, bool RET>
 static cudaError_t adjoint_dispatch(const AdjointLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: adjoint_sweep_kernel<T, E><<<grid, block, 0, st>>>(a); break;
+    case E: adjoint_sweep_kernel<T, E, RET><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
@@ -481,7 +579,8 @@ static cudaError_t adjoint_dispatch(const AdjointLaunch &a, cudaStream_t st) {
 }
 
 cudaError_t launch_adjoint_sweep(bool fp64, const AdjointLaunch &a, cudaStream_t st) {
-    return fp64 ? adjoint_dispatch<double>(a, st) : adjoint_dispatch<float>(a, st);
+    if (a.retarded) return fp64 ? adjoint_dispatch<double, true>(a, st) : adjoint_dispatch<float, true>(a, st);
+    return fp64 ? adjoint_dispatch<double, false>(a, st) : adjoint_dispatch<float, false>(a, st);
 }
 
 int adjoint_occupancy(bool fp64, int ept, int bs) {
@@ -489,8 +588,8 @@ int adjoint_occupancy(bool fp64, int ept, int bs) {
     switch (ept) {
 #define SC_CASE(E)                                                                                        \
     case E:                                                                                               \
-        if (fp64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_sweep_kernel<double, E>, bs, 0); \
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_sweep_kernel<float, E>, bs, 0);       \
+        if (fp64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_sweep_kernel<double, E, true>, bs, 0); \
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_sweep_kernel<float, E, true>, bs, 0);       \
         break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE

@@ -19,6 +19,7 @@ struct AdjointLaunch {
     int32_t first_sweep;       // the differentiated sweep started from homogeneous values
     int32_t parity;            // exit buffer the differentiated sweep read
     int32_t energies_per_lane;
+    int32_t retarded;          // LDOS mode: wimg holds n_e weights per slot
     int32_t grid_blocks, block_threads;
 };
 
@@ -31,6 +32,9 @@ cudaError_t launch_adjoint_outputs(const GridDev &grid, const uint8_t *mask, con
 cudaError_t launch_adjoint_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
                                        const GridDev &grid, const uint8_t *mask, const double *gacc, void *wimg,
                                        cudaStream_t s);
+cudaError_t launch_adjoint_ldos_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
+                                     const GridDev &grid, const uint8_t *mask, const double *gN, int32_t n_e,
+                                     void *wimg, cudaStream_t s);
 cudaError_t launch_adjoint_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_line, int64_t n_slots,
                                   const PairDev *pairs, const GridDev &grid, const int32_t *ghost,
                                   const void *gimg, double *gdelta, double *gaind, cudaStream_t s);

@@ -775,89 +775,189 @@ sc_status sc_picard_step(sc_ctx *ctx, void *stream) {
     return SC_OK;
 }
 
-sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening, int32_t n_burnin,
-                  double *ldos_out, int on_device, void *stream) {
-    CKS(check_ctx(ctx));
-    if (!energies || n_e < 1 || !ldos_out) return set_err(ctx, SC_EINVAL, "energies and ldos_out are required");
+}  // extern "C"
+
+namespace {
+
+// Buffers of one LDOS evaluation (retarded sweeps with their own boundary values).
+struct LdosRun {
+    Plan *pl = nullptr;
+    double *d_en = nullptr;
+    void *d_ex[2] = {nullptr, nullptr};
+    void *d_img = nullptr;
+    scd::GrainSweep *d_gs = nullptr;
+    int last_parity = 0;
+    bool last_first = true;
+};
+
+void ldos_release(sc_ctx *ctx, LdosRun &R, cudaStream_t st) {
+    cudaStreamSynchronize(st);
+    dfree(ctx, R.d_en);
+    dfree(ctx, R.d_ex[0]);
+    dfree(ctx, R.d_ex[1]);
+    dfree(ctx, R.d_img);
+    dfree(ctx, R.d_gs);
+    R = LdosRun();
+}
+
+sc_status ldos_check(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening) {
+    if (!energies || n_e < 1) return set_err(ctx, SC_EINVAL, "energies are required");
     if (!(broadening > 0.0)) return set_err(ctx, SC_EINVAL, "broadening must be > 0");
     for (int k = 0; k < n_e; ++k)
         if (std::fabs(energies[k] + energies[n_e - 1 - k]) > 1e-12 * (1.0 + std::fabs(energies[k])))
             return set_err(ctx, SC_EINVAL, "energies must be symmetric about zero");
-    cudaStream_t st = (cudaStream_t)stream;
-    Plan *pl = nullptr;
-    CKS(make_plan(ctx, n_e, 0, &pl));
+    return SC_OK;
+}
+
+// Allocate, rotate the fields and run n_burnin retarded sweeps (Delta, A frozen).
+sc_status ldos_burnin(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening, int32_t n_burnin,
+                      LdosRun &R, cudaStream_t st) {
+    CKS(make_plan(ctx, n_e, 0, &R.pl));
+    const Plan *pl = R.pl;
     const size_t nL = ctx->geo.lines.size();
     const size_t cplx = 2 * ctx->real_bytes;
-    double *d_en = nullptr;
-    void *d_ex[2] = {nullptr, nullptr};
-    void *d_img = nullptr;
+    CK(dalloc(ctx, &R.d_en, n_e * sizeof(double)));
+    CK(dalloc(ctx, &R.d_ex[0], 2 * nL * n_e * cplx));
+    CK(dalloc(ctx, &R.d_ex[1], 2 * nL * n_e * cplx));
+    CK(dalloc(ctx, &R.d_gs, sizeof(scd::GrainSweep)));
+    CK(dalloc(ctx, &R.d_img, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes));
+    scd::GrainSweep gs{};
+    gs.lines = ctx->d_lines;
+    gs.groups = pl->d_groups;
+    gs.image_in = ctx->d_img_in;
+    gs.image_out = R.d_img;
+    gs.exits[0] = R.d_ex[0];
+    gs.exits[1] = R.d_ex[1];
+    gs.energies = R.d_en;
+    gs.t = ctx->geo.prm.t;
+    gs.h = ctx->geo.prm.h;
+    gs.broadening = broadening;
+    gs.n_e = n_e;
+    gs.lanes = pl->lanes;
+    gs.lines_per_warp = pl->lines_per_warp;
+    gs.ne_pad = pl->lanes * pl->ept;
+    gs.max_ns = std::max(ctx->geo.max_ns, 1);
+    CK(cudaMemcpyAsync(R.d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(R.d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(R.d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st));
+    CK(cudaStreamSynchronize(st));  // gs lives on this stack frame
+    CKS(sc_internal::rotate_fields(ctx, st));
+    const int nb = std::max(1, n_burnin);
+    for (int it = 0; it < nb; ++it) {
+        CKS(launch_plan_sweep(ctx, *pl, R.d_gs, true, it == 0, it & 1, st));
+        R.last_parity = it & 1;
+        R.last_first = it == 0;
+    }
+    return SC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_ldos(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening, int32_t n_burnin,
+                  double *ldos_out, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!ldos_out) return set_err(ctx, SC_EINVAL, "ldos_out is required");
+    CKS(ldos_check(ctx, energies, n_e, broadening));
+    cudaStream_t st = (cudaStream_t)stream;
+    LdosRun R;
     double *d_out = nullptr;
-    scd::GrainSweep *d_gs = nullptr;
-    sc_status rc = SC_OK;
-    do {
-        cudaError_t e;
-        if ((e = dalloc(ctx, &d_en, n_e * sizeof(double))) != cudaSuccess ||
-            (e = dalloc(ctx, &d_ex[0], 2 * nL * n_e * cplx)) != cudaSuccess ||
-            (e = dalloc(ctx, &d_ex[1], 2 * nL * n_e * cplx)) != cudaSuccess ||
-            (e = dalloc(ctx, &d_gs, sizeof(scd::GrainSweep))) != cudaSuccess ||
-            (e = dalloc(ctx, &d_img, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes)) != cudaSuccess) {
-            rc = set_err(ctx, SC_ENOMEM, std::string("ldos buffers: ") + cudaGetErrorString(e));
-            break;
-        }
+    sc_status rc = ldos_burnin(ctx, energies, n_e, broadening, n_burnin, R, st);
+    if (rc == SC_OK) {
+        cudaError_t e = cudaSuccess;
         if (on_device) d_out = ldos_out;
-        else if ((e = dalloc(ctx, &d_out, (size_t)n_e * npts(ctx) * sizeof(double))) != cudaSuccess) {
-            rc = set_err(ctx, SC_ENOMEM, "ldos output");
-            break;
-        }
-        scd::GrainSweep gs{};
-        gs.lines = ctx->d_lines;
-        gs.groups = pl->d_groups;
-        gs.image_in = ctx->d_img_in;
-        gs.image_out = d_img;
-        gs.exits[0] = d_ex[0];
-        gs.exits[1] = d_ex[1];
-        gs.energies = d_en;
-        gs.t = ctx->geo.prm.t;
-        gs.h = ctx->geo.prm.h;
-        gs.broadening = broadening;
-        gs.n_e = n_e;
-        gs.lanes = pl->lanes;
-        gs.lines_per_warp = pl->lines_per_warp;
-        gs.ne_pad = pl->lanes * pl->ept;
-        gs.max_ns = std::max(ctx->geo.max_ns, 1);
-        if ((e = cudaMemcpyAsync(d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
-            break;
-        }
-        rc = sc_internal::rotate_fields(ctx, st);
-        const int nb = std::max(1, n_burnin);
-        for (int it = 0; it < nb && rc == SC_OK; ++it)
-            rc = launch_plan_sweep(ctx, *pl, d_gs, true, it == 0, it & 1, st);
+        else e = dalloc(ctx, &d_out, (size_t)n_e * npts(ctx) * sizeof(double));
+        if (e == cudaSuccess)
+            e = scd::launch_ldos_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
+                                      R.d_img, n_e, d_out, st);
+        if (e == cudaSuccess && !on_device)
+            e = cudaMemcpyAsync(ldos_out, d_out, (size_t)n_e * npts(ctx) * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = set_err(ctx, SC_ECUDA, std::string("ldos: ") + cudaGetErrorString(e));
+    }
+    ldos_release(ctx, R, st);
+    if (d_out && d_out != ldos_out) dfree(ctx, d_out);
+    return rc;
+}
+
+sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening, int32_t n_burnin,
+                          const double *g_ldos, double *dL_ddelta, double *dL_daind, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    if (!g_ldos || !dL_ddelta) return set_err(ctx, SC_EINVAL, "g_ldos and dL_ddelta are required");
+    CKS(ldos_check(ctx, energies, n_e, broadening));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t np = npts(ctx);
+    LdosRun R;
+    double *d_gN = nullptr, *d_gd = nullptr, *d_ga = nullptr;
+    void *d_w = nullptr, *d_g = nullptr, *d_scr = nullptr;
+    sc_status rc = ldos_burnin(ctx, energies, n_e, broadening, n_burnin, R, st);
+    do {
         if (rc != SC_OK) break;
-        if ((e = scd::launch_ldos_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
-                                       d_img, n_e, d_out, st)) != cudaSuccess) {
-            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+        const Plan &pl = *R.pl;
+        const size_t t4 = ctx->fp64 ? 32 : 16;
+        const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128));
+        const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+        const int64_t stride = 3 * pl.stride;
+        cudaError_t e = cudaSuccess;
+        if ((e = dalloc(ctx, &d_gd, 2 * np * sizeof(double))) != cudaSuccess ||
+            (e = dalloc(ctx, &d_ga, 2 * np * sizeof(double))) != cudaSuccess ||
+            (e = dalloc(ctx, &d_w, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes)) != cudaSuccess ||
+            (e = dalloc(ctx, &d_g, (size_t)ctx->geo.n_slots * t4)) != cudaSuccess ||
+            (e = dalloc(ctx, &d_scr, (size_t)blocks * 4 * stride * 2 * ctx->real_bytes)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ENOMEM, std::string("ldos adjoint buffers: ") + cudaGetErrorString(e));
             break;
         }
+        const double *gN = g_ldos;
         if (!on_device) {
-            if ((e = cudaMemcpyAsync(ldos_out, d_out, (size_t)n_e * npts(ctx) * sizeof(double), cudaMemcpyDeviceToHost,
-                                     st)) != cudaSuccess) {
+            if ((e = dalloc(ctx, &d_gN, (size_t)n_e * np * sizeof(double))) != cudaSuccess ||
+                (e = cudaMemcpyAsync(d_gN, g_ldos, (size_t)n_e * np * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+                    cudaSuccess) {
                 rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
                 break;
             }
+            gN = d_gN;
         }
+        if ((e = cudaMemsetAsync(d_gd, 0, 2 * np * sizeof(double), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_ga, 0, 2 * np * sizeof(double), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_w, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d_g, 0, (size_t)ctx->geo.n_slots * t4, st)) != cudaSuccess ||
+            (e = scd::launch_adjoint_ldos_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid,
+                                               ctx->d_mask, gN, n_e, d_w, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        scd::AdjointLaunch a{};
+        a.grain = R.d_gs;
+        a.items = pl.d_items;
+        a.n_items = pl.n_groups;
+        a.counter = ctx->d_counter;
+        a.scratch = d_scr;
+        a.scratch_stride = stride;
+        a.wimg = d_w;
+        a.gimg = d_g;
+        a.first_sweep = R.last_first ? 1 : 0;
+        a.parity = R.last_parity;
+        a.energies_per_lane = pl.ept;
+        a.retarded = 1;
+        a.grid_blocks = blocks;
+        a.block_threads = 128;
+        if ((e = scd::launch_adjoint_sweep(ctx->fp64, a, st)) != cudaSuccess ||
+            (e = scd::launch_adjoint_rotate(ctx->fp64, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs,
+                                            ctx->grid, ctx->d_ghost, d_g, d_gd, d_ga, st)) != cudaSuccess) {
+            rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
+            break;
+        }
+        rc = copy_out(ctx, dL_ddelta, d_gd, 2 * np * sizeof(double), on_device, st);
+        if (rc == SC_OK) rc = copy_out(ctx, dL_daind, d_ga, 2 * np * sizeof(double), on_device, st);
     } while (0);
-    cudaStreamSynchronize(st);
-    dfree(ctx, d_en);
-    dfree(ctx, d_ex[0]);
-    dfree(ctx, d_ex[1]);
-    dfree(ctx, d_img);
-    dfree(ctx, d_gs);
-    if (d_out != ldos_out) dfree(ctx, d_out);
-    // the rotated fields were overwritten with the same values; nothing else changed
+    ldos_release(ctx, R, st);
+    dfree(ctx, d_gN);
+    dfree(ctx, d_gd);
+    dfree(ctx, d_ga);
+    dfree(ctx, d_w);
+    dfree(ctx, d_g);
+    dfree(ctx, d_scr);
     return rc;
 }
 
@@ -929,6 +1029,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     a.first_sweep = ctx->last_first ? 1 : 0;
     a.parity = ctx->cur ^ 1;  // the buffer the last sweep read its entry values from
     a.energies_per_lane = pl.ept;
+    a.retarded = 0;
     a.grid_blocks = blocks;
     a.block_threads = 128;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev_adj[0], st));

@@ -72,6 +72,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
+            "sc_ldos_adjoint",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
@@ -106,6 +107,7 @@ def _load():
         "sc_debug_images": [vp, vp],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
+        "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
         "sc_batch_create": [vp, i32, i32, P(vp)],
         "sc_batch_destroy": [vp],
         "sc_batch_member": [vp, i32, P(vp)],
@@ -270,6 +272,13 @@ def sc_sweep_adjoint(ctx, g_delta_new, g_j, g_F, g_Ftotal, dL_ddelta, dL_daind, 
                                 _ptr(dL_ddelta), _ptr(dL_daind), int(on_device), _stream(stream)), ctx)
 
 
+def sc_ldos_adjoint(ctx, energies, broadening, n_burnin, g_ldos, dL_ddelta, dL_daind, on_device=True,
+                    stream=None):
+    e = np.ascontiguousarray(energies, np.float64)
+    _check(lib.sc_ldos_adjoint(ctx, _ptr(e), len(e), float(broadening), int(n_burnin), _ptr(g_ldos),
+                               _ptr(dL_ddelta), _ptr(dL_daind), int(on_device), _stream(stream)), ctx)
+
+
 def sc_batch_create(params_list, energies_per_lane=0):
     arr = (sc_params * len(params_list))(*params_list)
     h = ctypes.c_void_p()
@@ -363,6 +372,7 @@ class Context:
         self.nx, self.ny = prm["nx"], prm["ny"]
         self.n_e = prm["n_energies"]
         self.N = prm["n_angles"]
+        self.sweep_count = 0
 
     def close(self):
         if self.h and getattr(self, "_owned", True):
@@ -413,6 +423,7 @@ class Context:
 
     def sweep(self, stream=None):
         sc_riccati_sweep(self.h, stream)
+        self.sweep_count = getattr(self, "sweep_count", 0) + 1
 
     def outputs(self, stream=None):
         import torch
@@ -451,6 +462,16 @@ class Context:
         da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
         sc_sweep_adjoint(self.h, gdn, gj, gF, g_Ftotal, dd, da, True, stream)
         self._adj_keep = (gdn, gj, gF)
+        return torch.view_as_complex(dd), da
+
+    def ldos_adjoint(self, energies, broadening, g_ldos, n_burnin=20, stream=None):
+        """dL/dDelta(R) (complex) and dL/dA_ind(R) for an LDOS-map cotangent g_ldos
+        (n_e x ny x nx)."""
+        import torch
+        g = torch.as_tensor(g_ldos, dtype=torch.float64, device="cuda").contiguous()
+        dd = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        sc_ldos_adjoint(self.h, energies, broadening, n_burnin, g, dd, da, True, stream)
         return torch.view_as_complex(dd), da
 
     def ldos(self, energies, broadening, n_burnin=20, stream=None):

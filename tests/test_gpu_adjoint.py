@@ -111,3 +111,79 @@ def test_fp32_adjoint_close_to_fp64():
     gd32, ga32 = _adjoint(p, d, a, "fp32", g_Ftotal=1.0)
     assert np.max(np.abs(gd32 - gd64)) <= 1e-3 * np.max(np.abs(gd64))
     assert np.max(np.abs(ga32 - ga64)) <= 1e-3 * np.max(np.abs(ga64))
+
+
+def _oracle_ldos_fixed(g, d, a, e, dl, ex):
+    im, _ = g.sweep(d, a, np.asarray(e) + 1j * dl, 1, ex)
+    return g.rotate_back(im, 1, len(e))
+
+
+def _oracle_ldos_exits(g, d, a, e, dl, n=400, tol=1e-13):
+    ex = None
+    z = np.asarray(e) + 1j * dl
+    for _ in range(n):
+        im, ex2 = g.sweep(d, a, z, 1, ex)
+        if ex is not None and np.max(np.abs(ex2 - ex)) < tol:
+            return ex2
+        ex = ex2
+    return ex
+
+
+def test_ldos_map_gradient_matches_oracle_fd():
+    """L2 misfit of the LDOS map to a synthetic target (another vortex position,
+    1% noise): autograd gradient vs central differences of the oracle's LDOS
+    with converged boundary values held fixed."""
+    import torch
+    from paper_2205_15000_b300 import sc
+    from paper_2205_15000_b300.autograd import ldos_map
+    p, d, a = _grain()
+    e = np.linspace(-0.2, 0.2, 6)
+    dl = 0.05
+    g = oracle.OracleGeom(p)
+    d_t = W.vortex_delta(p, 0.22, [(-1.0, -0.5)], [-1])
+    ex_t = _oracle_ldos_exits(g, d_t, a, e, dl)
+    rng = np.random.default_rng(9)
+    target = _oracle_ldos_fixed(g, d_t, a, e, dl, ex_t)
+    target = target * (1 + 0.01 * rng.standard_normal(target.shape))
+    m = g.mask().astype(bool)
+    ex = _oracle_ldos_exits(g, d, a, e, dl)
+
+    def loss(dd, aa):
+        N = _oracle_ldos_fixed(g, dd, aa, e, dl, ex)
+        return float(np.sum(((N - target) ** 2)[:, m]))
+    probes = _probes(p, g, 6, 44)
+    fd = _fd(loss, d, a, probes)
+    ctx = sc.Context(p, precision="fp64")
+    dt = torch.tensor(d, dtype=torch.complex128, device="cuda", requires_grad=True)
+    at = torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
+    N = ldos_map(ctx, dt, list(e), dl, at, n_burnin=400)
+    tgt = torch.tensor(target, device="cuda")
+    mk = torch.tensor(m, device="cuda")
+    L = (((N - tgt) ** 2) * mk).sum()
+    L.backward()
+    gd, ga = dt.grad.cpu().numpy(), at.grad.cpu().numpy()
+    adj = np.array([[gd[j, i].real, gd[j, i].imag, ga[j, i, 0], ga[j, i, 1]] for j, i in probes])
+    scale = np.max(np.abs(fd))
+    assert scale > 0
+    assert np.max(np.abs(adj - fd)) <= 1e-5 * scale, np.max(np.abs(adj - fd)) / scale
+
+
+def test_autograd_free_energy_matches_oracle_fd():
+    import torch
+    from paper_2205_15000_b300 import sc
+    from paper_2205_15000_b300.autograd import riccati_sweep
+    p, d, a = _grain()
+    g = oracle.OracleGeom(p)
+    ex = _oracle_converged_exits(g, d, a)
+    probes = _probes(p, g, 6, 45)
+    fd = _fd(lambda dd, aa: g.full_sweep(dd, aa, ex)["F_total"], d, a, probes)
+    ctx = sc.Context(p, precision="fp64")
+    ctx.set_fields(d, a)
+    sc.sc_burnin(ctx.h, 300, 1e-13)
+    dt = torch.tensor(d, dtype=torch.complex128, device="cuda", requires_grad=True)
+    at = torch.tensor(a, dtype=torch.float64, device="cuda", requires_grad=True)
+    dn, j, F, Ft = riccati_sweep(ctx, dt, at)
+    Ft.backward()
+    gd, ga = dt.grad.cpu().numpy(), at.grad.cpu().numpy()
+    adj = np.array([[gd[j_, i].real, gd[j_, i].imag, ga[j_, i, 0], ga[j_, i, 1]] for j_, i in probes])
+    assert np.max(np.abs(adj - fd)) <= 1e-6 * np.max(np.abs(fd))
