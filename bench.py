@@ -161,9 +161,16 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
-    workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
-        f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
+    if args.workload == "c4":
+        p, delta, aind = W.c4_disc_d()
+        workload = "c4_disc_d_128sq_64ang_40eps_vortex"
+    elif args.workload == "c5":
+        p, delta, aind = W.c5_square_d()
+        workload = "c5_square_d_1024sq_256ang_160eps_20vortices"
+    else:
+        p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
+        workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
+            f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     ctx = sc.Context(p, precision=args.precision, record_timings=True)
     info = ctx.info
     stream = torch.cuda.current_stream()
@@ -174,11 +181,16 @@ def run_ours(args):
     FF = torch.empty((p["ny"], p["nx"]), dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    gd = torch.empty((p["ny"], p["nx"], 2), dtype=torch.float64, device=dev)
+    ga = torch.empty_like(gd)
+
     def step():
         sc.sc_riccati_sweep(ctx.h, stream)
         sc.sc_gap_update(ctx.h, dn, True, False, stream)
         sc.sc_current(ctx.h, jj, True, stream)
         sc.sc_free_energy(ctx.h, FF, True, False, stream)
+        if args.adjoint:  # gradient of F_total with respect to Delta(R) and A_ind(R)
+            sc.sc_sweep_adjoint(ctx.h, None, None, None, 1.0, gd, ga, True, stream)
 
     for _ in range(args.warmup):
         step()
@@ -200,7 +212,7 @@ def run_ours(args):
         ev[i][1].record(stream)
         flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
         ki = sc.sc_get_info(ctx.h)  # waits for this step's sweep kernels
-        kern.append((ki.ms_rotate, ki.ms_sweep, ki.ms_rotate_back))
+        kern.append((ki.ms_rotate, ki.ms_sweep, ki.ms_rotate_back, ki.ms_adjoint))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -208,6 +220,8 @@ def run_ours(args):
     sweep_ms = statistics.mean(k[1] for k in kern)
     kernels_ms = {"rotate": statistics.mean(k[0] for k in kern), "sweep": sweep_ms,
                   "rotate_back": statistics.mean(k[2] for k in kern)}
+    if args.adjoint:
+        kernels_ms["adjoint_sweep"] = statistics.mean(k[3] for k in kern)
     clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
 
     # end to end through the public API with host buffers
@@ -216,7 +230,7 @@ def run_ours(args):
     h_j = torch.empty_like(h_dn).pin_memory()
     h_F = torch.empty((p["ny"], p["nx"]), dtype=torch.float64).pin_memory()
     e2e_ms = []
-    for i in range(max(3, min(args.steps, 10))):
+    for i in range(max(3, min(args.steps, 10)) if not args.no_e2e else 0):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -270,19 +284,23 @@ def run_ours(args):
                    "n_energies": p["n_energies"], "t": p["t"], "pairing": "dx2y2",
                    "flux_quanta": p["flux_quanta"], "precision": args.precision,
                    "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "step": "forward sweep + outputs" + (" + adjoint of F_total" if args.adjoint else ""),
+                   "grain": {k: p[k] for k in ("nx", "ny", "h", "t", "n_angles", "n_energies",
+                                               "flux_quanta", "pairing")}},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "sweep_kernel", "ms_per_launch": sweep_ms,
                      "kernels_ms_per_step": kernels_ms,
                      "peak_note": "FP32 lane issue 148 SM x 128 x max SM clock (derived)"},
-        "e2e": {"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
-                "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
+                 "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+                if e2e_ms else None),
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "wall_s": t_wall,
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.workload == "c2":
         line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"])
     print(json.dumps(line), flush=True)
     if dist:
@@ -380,8 +398,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="grid side (reduced cases for profiling)")
     ap.add_argument("--angles", type=int, default=128, help="Fermi angles (reduced cases for profiling)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3"],
-                    help="c2: one 256^2 d-wave [110] grain; c3: 64 grains in one batched launch")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: one 256^2 d-wave [110] grain; c3: 64 grains in one batched launch; "
+                         "c4: d-wave disc with a vortex (128^2); c5: 1024^2 d-wave square, 20 vortices")
+    ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grains", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:

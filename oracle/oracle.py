@@ -31,7 +31,7 @@ def lib():
         L.or_geom_area.argtypes = [ctypes.c_void_p]
         for name in ("or_geom_info", "or_geom_mask", "or_geom_ghost", "or_geom_lines",
                      "or_geom_links", "or_geom_quadrature", "or_sample_fields", "or_sweep",
-                     "or_rotate_back", "or_outputs", "or_vector_potential"):
+                     "or_rotate_back", "or_outputs", "or_vector_potential", "or_sweep_subset"):
             getattr(L, name).restype = ctypes.c_int
         L.or_norm_D.restype = ctypes.c_double
         L.or_norm_D.argtypes = [ctypes.c_double, ctypes.c_int]
@@ -219,6 +219,32 @@ class OracleGeom:
         if want_gammas:
             return im, ex, gam.view(np.complex128).reshape(2, self.n_samples_all, n_e)
         return im, ex
+
+    def sweep_subset(self, delta, aind, angles):
+        """First-sweep energy sums of the listed angles only (Matsubara);
+        returns a list of [samples][4] arrays, one per angle."""
+        d = _cplx_to_f64(delta)
+        a = None if aind is None else np.ascontiguousarray(aind, np.float64)
+        z = _cplx_to_f64(self.matsubara())
+        ang = np.ascontiguousarray(angles, np.int32)
+        L = self.lines()
+        ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+        per_pair = []
+        off = 0
+        for q in range(self.n_pairs):
+            nl = int(L["l_hi"][q] - L["l_lo"][q] + 1)
+            per_pair.append(int(ns[off:off + nl].sum()))
+            off += nl
+        sizes = [per_pair[k % self.n_pairs] for k in angles]
+        out = np.zeros(4 * sum(sizes))
+        rc = lib().or_sweep_subset(self._h, _p(d), _p(a), _p(z), int(self.n_e), _p(ang), len(ang), _p(out))
+        if rc:
+            raise RuntimeError(lib().or_last_error().decode())
+        res, o = [], 0
+        for sz in sizes:
+            res.append(out[4 * o:4 * (o + sz)].reshape(sz, 4))
+            o += sz
+        return res
 
     def rotate_back(self, images, mode=0, n_e=None):
         n_e = n_e if n_e is not None else self.n_e

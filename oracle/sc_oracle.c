@@ -1052,3 +1052,110 @@ double or_bulk_gap(int pairing, double t, int n_e, int N) {
     }
     return 0.5 * (lo + hi);
 }
+
+/* ---------------------------------------------------------------------- */
+/* First sweep (homogeneous entry values) for a chosen subset of angles:  */
+/* the same per-line integration as or_sweep, restricted so that a large  */
+/* grain can be checked angle by angle.  images: [n_sel][samples of the   */
+/* angle's pair][4] (mode-0 sums).                                        */
+/* ---------------------------------------------------------------------- */
+int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, const double *z,
+                    int n_e, const int *angles, int n_sel, double *images) {
+    int np = g->npair;
+    double h = g->P.h;
+    int sgc = g->P.charge_sign;
+    int64_t out_off = 0;
+    for (int si = 0; si < n_sel; ++si) {
+        int k = angles[si];
+        if (k < 0 || k >= g->N) return fail("angle out of range");
+        int p = k % np;
+        int sg = k < np ? 1 : -1;
+        int nsp = g->samp_off[p + 1] - g->samp_off[p];
+        double *dS = malloc(sizeof(double) * 2 * (nsp > 0 ? nsp : 1));
+        double *aS = malloc(sizeof(double) * 2 * (nsp > 0 ? nsp : 1));
+        if (or_sample_fields(g, delta, aind, p, dS, aS)) {
+            free(dS);
+            free(aS);
+            return -1;
+        }
+        double vx = g->vh[2 * k], vy = g->vh[2 * k + 1], eta = g->eta[k];
+        int nl = g->l_hi[p] - g->l_lo[p] + 1;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int li = 0; li < nl; ++li) {
+            int L = g->line_off[p] + li;
+            int ns = g->ns[L], m0 = g->m0[L], m1 = g->m1[L];
+            if (ns == 0) continue;
+            cplx *dseg = malloc(sizeof(cplx) * (ns + 1));
+            double *aseg = malloc(sizeof(double) * (ns + 1));
+            double *lseg = malloc(sizeof(double) * (ns + 1));
+            cplx *dsm = malloc(sizeof(cplx) * ns);
+            double *asm_ = malloc(sizeof(double) * ns);
+            int *sidx = malloc(sizeof(int) * ns);
+            for (int q = 0; q < ns; ++q) {
+                int m = sg > 0 ? m0 + q : m1 - q;
+                int idx = g->soff[L] + (m - m0);
+                sidx[q] = idx;
+                dsm[q] = eta * (dS[2 * idx] + I * dS[2 * idx + 1]);
+                asm_[q] = sgc * (vx * aS[2 * idx] + vy * aS[2 * idx + 1]);
+            }
+            double lead = sg > 0 ? m0 * h - g->smin[L] : g->smax[L] - m1 * h;
+            double tail = sg > 0 ? g->smax[L] - m1 * h : m0 * h - g->smin[L];
+            dseg[0] = dsm[0];
+            aseg[0] = asm_[0];
+            lseg[0] = lead > 0.0 ? lead : 0.0;
+            for (int q = 1; q < ns; ++q) {
+                dseg[q] = 0.5 * (dsm[q - 1] + dsm[q]);
+                aseg[q] = 0.5 * (asm_[q - 1] + asm_[q]);
+                lseg[q] = h;
+            }
+            dseg[ns] = dsm[ns - 1];
+            aseg[ns] = asm_[ns - 1];
+            lseg[ns] = tail > 0.0 ? tail : 0.0;
+            cplx *gam = malloc(sizeof(cplx) * ns), *gat = malloc(sizeof(cplx) * ns);
+            for (int q = 0; q < ns; ++q) {
+                double *im = &images[4 * (out_off + sidx[q])];
+                im[0] = im[1] = im[2] = im[3] = 0.0;
+            }
+            for (int n = 0; n < n_e; ++n) {
+                cplx zn = z[2 * n] + I * z[2 * n + 1];
+                cplx gm = riccati_fixed_point(conj(dseg[0]), zn + aseg[0], dseg[0]);
+                for (int q = 0; q <= ns; ++q) {
+                    gm = riccati_step(conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
+                    if (q < ns) gam[q] = gm;
+                }
+                cplx gt = riccati_fixed_point(-dseg[ns], zn + aseg[ns], -conj(dseg[ns]));
+                for (int q = ns; q >= 0; --q) {
+                    gt = riccati_step(-dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
+                    if (q > 0) gat[q - 1] = gt;
+                }
+                for (int q = 0; q < ns; ++q) {
+                    cplx ga = gam[q], gb = gat[q];
+                    cplx den = 1.0 + ga * gb;
+                    cplx gg = -I * M_PI * (1.0 - ga * gb) / den;
+                    cplx ff = -2.0 * I * M_PI * ga / den;
+                    cplx ft = 2.0 * I * M_PI * gb / den;
+                    cplx In = (conj(dsm[q]) * ff + dsm[q] * ft) / (M_PI + I * gg);
+                    double *im = &images[4 * (out_off + sidx[q])];
+                    cplx sf = ff + conj(ft);
+                    im[0] += creal(sf);
+                    im[1] += cimag(sf);
+                    im[2] += 2.0 * creal(gg);
+                    im[3] += 2.0 * creal(In);
+                }
+            }
+            free(gam);
+            free(gat);
+            free(dseg);
+            free(aseg);
+            free(lseg);
+            free(dsm);
+            free(asm_);
+            free(sidx);
+        }
+        free(dS);
+        free(aS);
+        out_off += nsp;
+    }
+    return 0;
+}
+

@@ -99,6 +99,11 @@ double or_norm_D(double t, int n_e);
 int or_outputs(const or_geom *g, const double *acc, const double *delta, const double *aind,
                double *delta_new, double *j, double *F, double *scalars);
 
+/* First sweep (homogeneous entries) for the listed angles only; images are
+   packed [selected angle][samples of its pair][4] (mode-0 sums). */
+int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, const double *z,
+                    int n_e, const int *angles, int n_sel, double *images);
+
 double or_greens(int m, int n, double h);
 /* A_ind = -(1/kappa^2) sum G (j - mean_mask j); direct double sum. j, aind: [nx*ny][2]. */
 int or_vector_potential(const or_geom *g, const double *j, double *aind);

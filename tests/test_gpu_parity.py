@@ -195,3 +195,39 @@ def test_c2_full_size_fp32_against_oracle():
         assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
         assert _rel(r["F"][m], o["F"][m]) < TOL_F
         assert abs(r["F_total"] - o["F_total"]) <= TOL_F * abs(o["F_total"])
+
+
+def test_c5_full_size_first_sweep_sampled_angles():
+    """Large workload (d-wave square side 200, 1024^2, 256 angles, 160
+    energies, 20 vortices): FP32 first-sweep energy sums on every sample of
+    two angles (one of each direction of a pair) against the oracle."""
+    import torch
+    sc = _sc()
+    p, delta, aind = W.c5_square_d()
+    g = oracle.OracleGeom(p)
+    P = g.n_pairs
+    angles = [37, P + 90]
+    ref = g.sweep_subset(delta, None, angles)
+    ctx = sc.Context(p, precision="fp32")
+    ctx.set_fields(delta)
+    ctx.sweep()
+    img = ctx.images()
+    L = g.lines()
+    ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+    per, off = [], 0
+    for q in range(P):
+        nl = int(L["l_hi"][q] - L["l_lo"][q] + 1)
+        per.append(int(ns[off:off + nl].sum()))
+        off += nl
+    start = np.concatenate([[0], np.cumsum(per)])
+    for k, r in zip(angles, ref):
+        q = k % P
+        mine = img[start[q]:start[q + 1]].copy()
+        if k >= P:
+            mine[:, 2] = -mine[:, 2]  # S_g changes sign with the direction; S_f, S_F do not
+        scale = np.max(np.abs(r), axis=0)
+        err = np.max(np.abs(mine - r), axis=0) / scale
+        # S_g feeds the current (tolerance 1e-4) and cancels strongly over 160 energies
+        assert np.all(err < np.array([2e-5, 2e-5, 1e-4, 2e-5])), (k, err)
+    del ctx
+    torch.cuda.empty_cache()
