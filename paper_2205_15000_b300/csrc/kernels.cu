@@ -106,8 +106,12 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
 // (gamma~(p) = conj gamma(p + P), Eq. symmetries), summed over the lane's
 // energies and then over the line's lanes by shuffles.
 // ---------------------------------------------------------------------------
+#ifndef SC_SWEEP_MIN_BLOCKS
+#define SC_SWEEP_MIN_BLOCKS 5  // FP32: 5 blocks of 128 threads per SM (at most 102 registers)
+#endif
+
 template <typename T, int EPT, bool RET>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) sweep_kernel(SweepLaunch a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1) sweep_kernel(SweepLaunch a) {
     typedef typename Vec4<T>::type T4;
     typedef Cx<T> C;
     const int lane = threadIdx.x & 31;
