@@ -81,12 +81,11 @@ struct StepCoef {
     Cx<T> gh, E, K;
 };
 
-// Coefficients from x + i y = Omega^2 = |Delta|^2 - z^2 given directly (lets a
-// caller hoist the parts of Omega^2 that do not change along a line).
 template <typename T>
-__host__ __device__ __forceinline__ void step_coef_xy(T dr, T di, T x, T y, T zr, T zi, T ell,
-                                                      StepCoef<T> &c) {
+__host__ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, StepCoef<T> &c) {
     typedef Mth<T> M;
+    const T x = d2 - zr * zr + zi * zi;  // Re Omega^2
+    const T y = T(-2) * zr * zi;         // Im Omega^2
     using ::fabs;
     using ::copysign;
     const T r = M::sqrt(x * x + y * y);
@@ -120,11 +119,6 @@ __host__ __device__ __forceinline__ void step_coef_xy(T dr, T di, T x, T y, T zr
     const T ccr = omr * i2r - omi * i2i, cci = omr * i2i + omi * i2r;
     c.K.x = -(dr * cci - di * ccr);  // K = i conj(Delta) (1 - E)/(2 Omega)
     c.K.y = dr * ccr + di * cci;
-}
-
-template <typename T>
-__host__ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi, T ell, StepCoef<T> &c) {
-    step_coef_xy<T>(dr, di, d2 - zr * zr + zi * zi, T(-2) * zr * zi, zr, zi, ell, c);
 }
 
 template <typename T>
