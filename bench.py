@@ -28,6 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_2205_15000_b300 import ranks  # noqa: E402
 from paper_2205_15000_b300 import workloads as W  # noqa: E402
 
 METRIC = "Riccati trajectory-steps/s"
@@ -149,16 +150,9 @@ def run_ours(args):
     import torch
     from paper_2205_15000_b300 import sc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    world, rank, local = ranks.env_ranks()
+    torch.cuda.set_device(local)
+    dist = ranks.init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
 
     if args.workload == "c4":
@@ -195,8 +189,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    ranks.barrier(dist)
     torch.cuda.synchronize()
     clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
@@ -245,15 +238,9 @@ def run_ours(args):
     d2h = (h_dn.numel() + h_j.numel() + h_F.numel()) * 8 + 2 * 8
 
     steps_per_step = info.steps_per_sweep
-    local_val = steps_per_step * args.steps / (total_ms * 1e-3)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms_max = float(t.item())
-        dist.barrier()
-    else:
-        total_ms_max = total_ms
-    value = world * steps_per_step * args.steps / (total_ms_max * 1e-3)
+    total_ms_max = ranks.max_over_ranks(dist, total_ms, dev)
+    ranks.barrier(dist)
+    value = ranks.throughput(steps_per_step * args.steps, world, total_ms_max * 1e-3)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -317,16 +304,9 @@ def run_batch(args):
     import torch
     from paper_2205_15000_b300 import sc
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    world, rank, local = ranks.env_ranks()
+    torch.cuda.set_device(local)
+    dist = ranks.init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     grains = W.c3_batch(n_grains=args.grains, seed=3 + rank)
     b = sc.Batch([p for p, _, _ in grains], precision=args.precision)
@@ -338,8 +318,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     info = b.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    if dist:
-        dist.barrier()
+    ranks.barrier(dist)
     clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
     cproc, cfile = _sample_clocks_start(clk_path) if rank == 0 else (None, None)
@@ -354,14 +333,11 @@ def run_batch(args):
         ksweep.append(b.info().ms_sweep)
     torch.cuda.synchronize()
     clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
-    total_ms = float(sum(a.elapsed_time(c) for a, c in ev))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * info.steps_per_sweep * args.steps / (total_ms * 1e-3)
+    total_ms = ranks.max_over_ranks(dist, float(sum(a.elapsed_time(c) for a, c in ev)), dev)
+    value = ranks.throughput(info.steps_per_sweep * args.steps, world, total_ms * 1e-3)
     if rank != 0:
-        dist.destroy_process_group()
+        if dist:
+            dist.destroy_process_group()
         return 0
     sweep_ms = statistics.mean(ksweep)
     pse = info.steps_per_sweep // 2  # ~ (pair, sample, energy) combinations

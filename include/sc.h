@@ -21,6 +21,9 @@
  * Errors: every call returns an sc_status.  Nothing aborts or exits.  A CUDA
  * error puts the context into a failed state; later calls return SC_ESTATE.
  * sc_last_error(ctx) (or sc_last_error(NULL) for sc_create) gives the message.
+ * For tests of the error paths, the environment variable SC_TEST_FAIL_ALLOC_AT=N
+ * (read by sc_create) makes the N-th device allocation of that context fail as
+ * if the device were out of memory; nothing is allocated for it.
  */
 #ifndef SC_H
 #define SC_H

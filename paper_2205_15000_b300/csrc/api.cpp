@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -31,6 +32,7 @@ sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg) {
 
 cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes) {
     void *v = nullptr;
+    if (ctx->fail_alloc_at >= 0 && ctx->alloc_count++ == ctx->fail_alloc_at) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
     if (e == cudaSuccess) {
         ctx->allocs.push_back(v);
@@ -364,6 +366,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         *out = ctx;
         return SC_OK;
     }
+    if (const char *fa = std::getenv("SC_TEST_FAIL_ALLOC_AT")) ctx->fail_alloc_at = std::atol(fa);
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) {

@@ -39,6 +39,12 @@ struct sc_batch {
     int graph_outputs = -1;
     int graph_ept = 0;
     cudaEvent_t sync_ev[2] = {nullptr, nullptr};
+    // per-member kernels (rotate, rotate-back, outputs) are small: spread them over
+    // auxiliary streams forked from and joined back to the sweep's stream
+    static constexpr int kAux = 8;
+    cudaStream_t aux[kAux] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kAux] = {};
     bool failed = false;
     std::string err;
 };
@@ -137,6 +143,20 @@ sc_status build(sc_batch *b, int ept) {
     return SC_OK;
 }
 
+sc_status fork(sc_batch *b, cudaStream_t st) {
+    BCK(cudaEventRecord(b->fork_ev, st));
+    for (int k = 0; k < sc_batch::kAux; ++k) BCK(cudaStreamWaitEvent(b->aux[k], b->fork_ev, 0));
+    return SC_OK;
+}
+
+sc_status join(sc_batch *b, cudaStream_t st) {
+    for (int k = 0; k < sc_batch::kAux; ++k) {
+        BCK(cudaEventRecord(b->join_ev[k], b->aux[k]));
+        BCK(cudaStreamWaitEvent(st, b->join_ev[k], 0));
+    }
+    return SC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -154,6 +174,11 @@ sc_status sc_batch_destroy(sc_batch *b) {
     for (cudaEvent_t e : b->sync_ev)
         if (e) cudaEventDestroy(e);
     if (b->gstream) cudaStreamDestroy(b->gstream);
+    for (int k = 0; k < sc_batch::kAux; ++k) {
+        if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     (void)cudaGetLastError();  // teardown errors are not the caller's
     delete b;
     return SC_OK;
@@ -206,6 +231,11 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     cudaError_t e = cudaMalloc(&b->d_counter, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int k = 0; k < sc_batch::kAux && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) st = SC_ECUDA;
     int ept = energies_per_lane;
     if (!ept) ept = std::min(8, std::max(4, (max_ne + 31) / 32));
@@ -231,11 +261,16 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     if (b->failed) return SC_ESTATE;
     BCK(cudaSetDevice(b->device));
     cudaStream_t st = (cudaStream_t)stream;
-    for (sc_ctx *c : b->members) {
+    sc_status fs = fork(b, st);
+    if (fs != SC_OK) return fs;
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        sc_ctx *c = b->members[g];
         if (c->failed) return berr(b, SC_ESTATE, "a member context failed");
-        sc_status s = sc_internal::rotate_fields(c, st);
+        sc_status s = sc_internal::rotate_fields(c, b->aux[g % sc_batch::kAux]);
         if (s != SC_OK) return berr(b, s, c->err);
     }
+    fs = join(b, st);
+    if (fs != SC_OK) return fs;
     BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
     // while a graph is being captured the timing events become external event
     // nodes, so that every replay records them
@@ -259,14 +294,19 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     BCK(scd::launch_sweep(b->fp64, a, st));
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
     b->timed = true;
-    for (sc_ctx *c : b->members) {
-        sc_status s = sc_internal::rotate_back(c, st);
+    fs = fork(b, st);
+    if (fs != SC_OK) return fs;
+    for (size_t g = 0; g < b->members.size(); ++g) {
+        sc_ctx *c = b->members[g];
+        sc_status s = sc_internal::rotate_back(c, b->aux[g % sc_batch::kAux]);
         if (s != SC_OK) return berr(b, s, c->err);
         c->cur = b->parity ^ 1;
         c->have_boundary = true;
         c->have_sweep = true;
         c->have_outputs = false;
     }
+    fs = join(b, st);
+    if (fs != SC_OK) return fs;
     b->parity ^= 1;
     b->have_boundary = true;
     return SC_OK;
@@ -276,11 +316,18 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
 static sc_status iteration(sc_batch *b, int with_outputs, cudaStream_t st) {
     sc_status s = sc_batch_sweep(b, st);
     if (s != SC_OK) return s;
-    if (with_outputs)
-        for (sc_ctx *c : b->members) {
-            s = sc_gap_update(c, nullptr, nullptr, 1, st);  // computes Delta_new, j, F on the device
+    if (with_outputs) {
+        s = fork(b, st);
+        if (s != SC_OK) return s;
+        for (size_t g = 0; g < b->members.size(); ++g) {
+            sc_ctx *c = b->members[g];
+            // computes Delta_new, j, F on the device
+            s = sc_gap_update(c, nullptr, nullptr, 1, b->aux[g % sc_batch::kAux]);
             if (s != SC_OK) return berr(b, s, c->err);
         }
+        s = join(b, st);
+        if (s != SC_OK) return s;
+    }
     return SC_OK;
 }
 

@@ -69,6 +69,10 @@ struct sc_ctx {
     bool failed = false;
     bool host_only = false;
     bool batch_member = false;  // swept only through its batch
+    // failure injection for tests: the fail_alloc_at-th device allocation of this
+    // context reports cudaErrorMemoryAllocation without touching the device (-1 = off)
+    long fail_alloc_at = -1;
+    long alloc_count = 0;
     bool last_first = false;    // the last sweep started from homogeneous values
     // adjoint buffers (allocated on first use)
     double *d_gacc = nullptr, *d_gdelta = nullptr, *d_gaind = nullptr, *d_gin = nullptr;
