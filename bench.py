@@ -351,12 +351,18 @@ def run_batch(args):
         "config": {"workload": f"c3_batch_{args.grains}_grains", "grains": args.grains,
                    "steps_per_sweep": info.steps_per_sweep, "work_items": info.n_items,
                    "energies_per_lane": ept, "precision": args.precision,
+                   "lane_fill": info.steps_per_sweep / max(info.lane_steps_per_sweep, 1),
+                   "sweep_launches": info.sweep_launches,
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": None, "kernel": "sweep_kernel",
                      "ms_per_launch": sweep_ms},
-        "gpu_launches": None, "clocks": clocks,
+        # per member: (FP32: field conversion,) rotate, rotate-back, outputs; plus
+        # one sweep launch per energies-per-lane class
+        "gpu_launches": ((4 if args.precision == "fp32" else 3) * args.grains
+                         + info.sweep_launches) * args.steps,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     if dist:

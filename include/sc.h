@@ -194,17 +194,22 @@ typedef struct sc_batch sc_batch;
 typedef struct {
     int32_t n_grains;
     int32_t n_items;           /* (grain, line group) work items of one sweep */
-    int32_t energies_per_lane; /* kernel layout shared by all members */
+    int32_t energies_per_lane; /* bound on any member's energies per lane */
     int64_t steps_per_sweep;   /* closed-form steps of one batch sweep, all grains */
     int64_t scratch_bytes;
     double ms_sweep;           /* last batch sweep kernel (CUDA events on its stream) */
+    int64_t lane_steps_per_sweep; /* steps the lanes execute, padded energy slots included */
+    int32_t sweep_launches;    /* uniform sweep launches per batch sweep (one per layout class) */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
    in sc_create) and one work list over all their (line group) items, longest
-   first, for a single persistent sweep launch.  energies_per_lane = 0 picks a
-   default; sc_batch_autotune chooses by timing.  Each member keeps its own
-   lanes-per-line layout.  The members are owned by the batch. */
+   first.  energies_per_lane (1..8) bounds the energies one lane carries; 0
+   picks a default; sc_batch_autotune chooses by timing.  Each member takes the
+   lanes per line (4, 8, 16, 32) and energies per lane (<= the bound) with the
+   fewest padded lane slots, then the most energies per lane.  Members with
+   equal energies per lane share one persistent launch; a batch sweep runs
+   these launches back to back.  The members are owned by the batch. */
 sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,
                           sc_batch **out);
 sc_status sc_batch_destroy(sc_batch *b);
@@ -212,7 +217,7 @@ sc_status sc_batch_destroy(sc_batch *b);
    above; sweeping it alone returns SC_ESTATE (its boundary values are the
    batch's). */
 sc_status sc_batch_member(sc_batch *b, int32_t i, sc_ctx **out);
-/* One sweep of every member (rotate per member, one persistent sweep launch,
+/* One sweep of every member (rotate per member, the persistent sweep launches,
    rotate-back per member); equivalent to sc_riccati_sweep on each member. */
 sc_status sc_batch_sweep(sc_batch *b, void *stream);
 /* n_sweeps batch sweeps (with_outputs = 1: plus every member's gap update,

@@ -137,6 +137,12 @@ sc_status check_ctx(sc_ctx *ctx) {
 sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out) {
     int lanes, ept;
     choose_lanes(n_e, ctx->forced_lanes, forced_ept, lanes, ept);
+    return make_plan_layout(ctx, n_e, lanes, ept, out);
+}
+
+sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out) {
+    if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return set_err(ctx, SC_EINVAL, "energy lanes per line must be 4, 8, 16 or 32");
     if (ept < 1 || ept > 8 || lanes * ept < n_e)
         return set_err(ctx, SC_EINVAL, "too many energies for the lane layout (at most 32 lanes x 8 per lane)");
     const int key = lanes * 16 + ept;
@@ -200,6 +206,7 @@ sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out) {
     gs.lines_per_warp = G;
     gs.ne_pad = lanes * ept;
     gs.max_ns = std::max(ctx->geo.max_ns, 1);
+    gs.ept = ept;
     CK(dalloc(ctx, &pl.d_grain, sizeof(gs)));
     CK(cudaMemcpy(pl.d_grain, &gs, sizeof(gs), cudaMemcpyHostToDevice));
     auto res = ctx->plans.emplace(key, std::move(pl));
@@ -840,6 +847,7 @@ sc_status ldos_burnin(sc_ctx *ctx, const double *energies, int32_t n_e, double b
     gs.lines_per_warp = pl->lines_per_warp;
     gs.ne_pad = pl->lanes * pl->ept;
     gs.max_ns = std::max(ctx->geo.max_ns, 1);
+    gs.ept = pl->ept;
     CK(cudaMemcpyAsync(R.d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(R.d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(R.d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st));

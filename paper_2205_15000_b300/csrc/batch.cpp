@@ -1,9 +1,10 @@
 // Batched sweep: many grains of uneven size, shape, pairing, temperature,
-// field and angle count in one persistent launch.  The work list holds
-// (grain, line group) items of every member, longest first; each grain keeps
-// its own lane layout (energy lanes per line), all grains share the number of
-// energies per lane, which is the kernel's template parameter and is chosen
-// by timing (sc_batch_autotune).
+// field and angle count swept by persistent launches over one work list of
+// (grain, line group) items, longest first.  Each grain has its own energy
+// layout (lanes per line, energies per lane); the energies per lane are the
+// kernel's template parameter, so the items form one class per distinct
+// count, and the classes run as back-to-back uniform launches on one stream.
+// The bound on energies per lane is chosen by timing (sc_batch_autotune).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,19 +19,24 @@ struct sc_batch {
     std::vector<sc_ctx *> members;
     int device = 0;
     bool fp64 = false;
-    int ept = 0;
+    int ept = 0;  // bound on energies per lane
     int sm_count = 0;
     scd::GrainSweep *d_grains = nullptr;
     int2 *d_items = nullptr;
     int32_t n_items = 0;
     int64_t stride = 0;
-    int grid_blocks = 0;
+    // one uniform launch per energies-per-lane class: items [first, first + n)
+    struct Class {
+        int ept, first, n, grid_blocks;
+    };
+    std::vector<Class> classes;
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
-    int32_t *d_counter = nullptr;
+    int32_t *d_counter = nullptr;  // one work counter per class (at most 8)
     int parity = 0;
     bool have_boundary = false;
     int64_t steps_per_sweep = 0;
+    int64_t lane_steps_per_sweep = 0;  // with padded energy slots, for the current layout
     cudaEvent_t ev[2] = {nullptr, nullptr};
     bool timed = false;
     // captured iterations: graph[p] = one sweep starting from parity p (+ outputs)
@@ -82,7 +88,23 @@ void free_plan_buffers(sc_batch *b) {
     b->d_items = nullptr;
 }
 
-// Lay out the work list for `ept` energies per lane.
+// Energy layout of one member with at most `ept_max` energies per lane: the
+// fewest padded lane slots (lanes x energies per lane >= n_e), then the most
+// energies per lane (fewer lanes: fewer shuffle rounds, more lines per warp).
+void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
+    int best = 1 << 30;
+    for (int l : {4, 8, 16, 32}) {
+        const int e = (n_e + l - 1) / l;
+        if (e < 1 || e > ept_max) continue;
+        if (l * e < best) {
+            best = l * e;
+            lanes = l;
+            ept = e;
+        }
+    }
+}
+
+// Lay out the work list for at most `ept` energies per lane.
 sc_status build(sc_batch *b, int ept) {
     free_graphs(b);  // captured graphs refer to the buffers rebuilt here
     std::vector<scd::GrainSweep> gs(b->members.size());
@@ -91,12 +113,15 @@ sc_status build(sc_batch *b, int ept) {
     };
     std::vector<It> items;
     int64_t stride = 0;
+    int64_t lane_steps = 0;
     for (size_t g = 0; g < b->members.size(); ++g) {
         sc_ctx *c = b->members[g];
         if (c->n_e > 32 * ept)
             return berr(b, SC_EINVAL, "a member has more energies than 32 lanes x energies_per_lane");
+        int lanes = 32, eg = ept;
+        member_layout(c->n_e, ept, lanes, eg);
         Plan *pl = nullptr;
-        sc_status st = sc_internal::make_plan(c, c->n_e, ept, &pl);
+        sc_status st = sc_internal::make_plan_layout(c, c->n_e, lanes, eg, &pl);
         if (st != SC_OK) return berr(b, st, c->err);
         scd::GrainSweep &d = gs[g];
         d.lines = c->d_lines;
@@ -114,13 +139,34 @@ sc_status build(sc_batch *b, int ept) {
         d.lines_per_warp = pl->lines_per_warp;
         d.ne_pad = pl->lanes * pl->ept;
         d.max_ns = std::max(c->geo.max_ns, 1);
+        d.ept = pl->ept;
         stride = std::max(stride, pl->stride);
+        int64_t steps = 0;
+        for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
+        lane_steps += steps * pl->lanes * pl->ept;
         // cost of a group ~ steps x energies handled per lane
-        for (int q = 0; q < pl->n_groups; ++q) items.push_back({pl->group_cost[q] * ept, (int)g, q});
+        for (int q = 0; q < pl->n_groups; ++q) items.push_back({pl->group_cost[q] * pl->ept, (int)g, q});
     }
-    std::stable_sort(items.begin(), items.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+    // classes by energies per lane (largest first), longest items first within each
+    std::stable_sort(items.begin(), items.end(), [&](const It &x, const It &y) {
+        const int ex = gs[x.grain].ept, ey = gs[y.grain].ept;
+        return ex != ey ? ex > ey : x.cost > y.cost;
+    });
     std::vector<int2> flat(items.size());
     for (size_t i = 0; i < items.size(); ++i) flat[i] = make_int2(items[i].grain, items[i].group);
+    std::vector<sc_batch::Class> classes;
+    for (size_t i = 0; i < items.size(); ++i) {
+        const int e = gs[items[i].grain].ept;
+        if (classes.empty() || classes.back().ept != e) classes.push_back({e, (int)i, 0, 0});
+        ++classes.back().n;
+    }
+    int max_blocks = 1;
+    for (auto &c : classes) {
+        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128);
+        if (occ < 1) occ = 1;
+        c.grid_blocks = std::max(1, std::min(b->sm_count * occ, (c.n + 3) / 4));
+        max_blocks = std::max(max_blocks, c.grid_blocks);
+    }
     free_plan_buffers(b);
     BCK(cudaMalloc(&b->d_grains, gs.size() * sizeof(scd::GrainSweep)));
     BCK(cudaMemcpy(b->d_grains, gs.data(), gs.size() * sizeof(scd::GrainSweep), cudaMemcpyHostToDevice));
@@ -128,10 +174,8 @@ sc_status build(sc_batch *b, int ept) {
     BCK(cudaMemcpy(b->d_items, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
     b->n_items = (int32_t)flat.size();
     b->stride = stride;
-    int occ = scd::sweep_occupancy(b->fp64, ept, 128);
-    if (occ < 1) occ = 1;
-    b->grid_blocks = std::max(1, std::min(b->sm_count * occ, (b->n_items + 3) / 4));
-    const size_t need = (size_t)b->grid_blocks * 4 * (size_t)stride * 2 * (b->fp64 ? 8 : 4);
+    b->classes = classes;
+    const size_t need = (size_t)max_blocks * 4 * (size_t)stride * 2 * (b->fp64 ? 8 : 4);
     if (need > b->scratch_bytes) {
         cudaFree(b->d_scratch);
         b->d_scratch = nullptr;
@@ -140,6 +184,7 @@ sc_status build(sc_batch *b, int ept) {
         b->scratch_bytes = need;
     }
     b->ept = ept;
+    b->lane_steps_per_sweep = lane_steps;
     return SC_OK;
 }
 
@@ -228,7 +273,7 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     b->device = b->members[0]->device;
     b->sm_count = b->members[0]->sm_count;
     sc_status st = SC_OK;
-    cudaError_t e = cudaMalloc(&b->d_counter, sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&b->d_counter, 8 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
@@ -271,27 +316,30 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     }
     fs = join(b, st);
     if (fs != SC_OK) return fs;
-    BCK(cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), st));
+    BCK(cudaMemsetAsync(b->d_counter, 0, 8 * sizeof(int32_t), st));
     // while a graph is being captured the timing events become external event
     // nodes, so that every replay records them
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     BCK(cudaStreamIsCapturing(st, &cap));
     const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     BCK(cudaEventRecordWithFlags(b->ev[0], st, ev_flags));
-    scd::SweepLaunch a{};
-    a.grains = b->d_grains;
-    a.items = b->d_items;
-    a.n_items = b->n_items;
-    a.counter = b->d_counter;
-    a.scratch = b->d_scratch;
-    a.scratch_stride = b->stride;
-    a.energies_per_lane = b->ept;
-    a.first_sweep = b->have_boundary ? 0 : 1;
-    a.parity = b->parity;
-    a.retarded = 0;
-    a.grid_blocks = b->grid_blocks;
-    a.block_threads = 128;
-    BCK(scd::launch_sweep(b->fp64, a, st));
+    for (size_t k = 0; k < b->classes.size(); ++k) {
+        const sc_batch::Class &c = b->classes[k];
+        scd::SweepLaunch a{};
+        a.grains = b->d_grains;
+        a.items = b->d_items + c.first;
+        a.n_items = c.n;
+        a.counter = b->d_counter + k;
+        a.scratch = b->d_scratch;
+        a.scratch_stride = b->stride;
+        a.energies_per_lane = c.ept;
+        a.first_sweep = b->have_boundary ? 0 : 1;
+        a.parity = b->parity;
+        a.retarded = 0;
+        a.grid_blocks = c.grid_blocks;
+        a.block_threads = 128;
+        BCK(scd::launch_sweep(b->fp64, a, st));
+    }
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
     b->timed = true;
     fs = fork(b, st);
@@ -424,6 +472,8 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     info->n_items = b->n_items;
     info->energies_per_lane = b->ept;
     info->steps_per_sweep = b->steps_per_sweep;
+    info->lane_steps_per_sweep = b->lane_steps_per_sweep;
+    info->sweep_launches = (int32_t)b->classes.size();
     info->scratch_bytes = (int64_t)b->scratch_bytes;
     if (b->timed) {
         float ms = 0.f;

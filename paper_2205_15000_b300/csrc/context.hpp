@@ -88,6 +88,8 @@ cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes);
 void dfree(sc_ctx *ctx, void *p);
 // lanes/EPT plan for n_e energies (forced_ept = 0: choose); builds the line groups
 sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out);
+// plan for an explicit layout: lanes in {4, 8, 16, 32}, lanes * ept >= n_e
+sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out);
 // fields of the context onto its lattices (rotate kernels)
 sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st);
 // FS average of the context's image into its accumulators (rotate-back kernels)

@@ -110,21 +110,13 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
 #define SC_SWEEP_MIN_BLOCKS 5  // FP32: 5 blocks of 128 threads per SM (at most 102 registers)
 #endif
 
+// One work item: the G lines of group it.y of grain gs, EPT energies per lane.
 template <typename T, int EPT, bool RET>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1) sweep_kernel(SweepLaunch a) {
+__device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
+                                           Cx<T> *const warp_slab, const int lane) {
     typedef typename Vec4<T>::type T4;
     typedef Cx<T> C;
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    C *const warp_slab = (C *)a.scratch + wid * a.scratch_stride;
-
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1);
-        item = __shfl_sync(FULL_MASK, item, 0);
-        if (item >= a.n_items) break;
-        const int2 it = a.items[item];
-        const GrainSweep &gs = a.grains[it.x];
+    {
         const int Lw = gs.lanes, G = gs.lines_per_warp;
         const int gi = lane / Lw, r = lane - gi * Lw;
         const T4 *__restrict__ img = (const T4 *)gs.image_in;
@@ -344,6 +336,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1)
                 if (ev[e]) exit_cur[(int64_t)ln.exit_b * n_e + nid[e]] = g[e];
         }
         __syncwarp();  // the slab is rewritten by the next item
+    }
+}
+
+template <typename T, int EPT, bool RET>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1) sweep_kernel(SweepLaunch a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    Cx<T> *const warp_slab = (Cx<T> *)a.scratch + wid * a.scratch_stride;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(FULL_MASK, item, 0);
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        sweep_item<T, EPT, RET>(a, it, a.grains[it.x], warp_slab, lane);
     }
 }
 

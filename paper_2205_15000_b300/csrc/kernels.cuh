@@ -82,9 +82,9 @@ struct GrainSweep {
     int32_t n_e;
     int32_t lanes;             // energy lanes per line, Lw (lines_per_warp * Lw = 32)
     int32_t lines_per_warp;
-    int32_t ne_pad;            // Lw * EPT
+    int32_t ne_pad;            // Lw * ept
     int32_t max_ns;            // longest line of the grain
-    int32_t pad;
+    int32_t ept;               // energies per lane (equals the launch's EPT)
 };
 
 // One persistent launch over the work items (grain, line group) of any number

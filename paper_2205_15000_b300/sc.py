@@ -50,6 +50,7 @@ class sc_batch_info(ctypes.Structure):
         ("n_grains", ctypes.c_int32), ("n_items", ctypes.c_int32),
         ("energies_per_lane", ctypes.c_int32), ("steps_per_sweep", ctypes.c_int64),
         ("scratch_bytes", ctypes.c_int64), ("ms_sweep", ctypes.c_double),
+        ("lane_steps_per_sweep", ctypes.c_int64), ("sweep_launches", ctypes.c_int32),
     ]
 
 

@@ -96,6 +96,29 @@ def test_batch_graph_run_and_autotune():
     ref.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_energy_layout_per_member(precision):
+    """Each member takes the layout with the fewest padded lane slots (at
+    most energies_per_lane energies per lane); one sweep launch per distinct
+    energies-per-lane count.  The batch reports the lane steps it executes."""
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    ept = 8
+    b = sc.Batch([p for p, _ in grains], precision=precision, energies_per_lane=ept)
+    expect, counts = 0, set()
+    for (p, _), m in zip(grains, b.members):
+        L = m.lines()
+        steps = int(np.sum(2 * (np.maximum(L["m1"] - L["m0"] + 1, 0) + 1)))
+        ne = p["n_energies"]
+        slots, lanes = min((l * -(-ne // l), l) for l in (4, 8, 16, 32) if -(-ne // l) <= ept)
+        counts.add(slots // lanes)
+        expect += steps * slots
+    info = b.info()
+    assert info.lane_steps_per_sweep == expect
+    assert info.sweep_launches == len(counts)
+    b.close()
+
+
 def test_member_sweep_alone_is_rejected():
     from paper_2205_15000_b300 import sc
     grains = _grains()
