@@ -64,8 +64,12 @@ __device__ __forceinline__ void atomic_add4(typename Vec4<T>::type *p, T a, T b,
 
 }  // namespace
 
+#ifndef SC_ADJOINT_MIN_BLOCKS
+#define SC_ADJOINT_MIN_BLOCKS 4  // FP32: 4 blocks of 128 threads per SM (at most 128 registers)
+#endif
+
 template <typename T, int EPT, bool RET>
-__global__ void __launch_bounds__(128) adjoint_sweep_kernel(AdjointLaunch a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 1) adjoint_sweep_kernel(AdjointLaunch a) {
     // parked per (sample, energy): 0 = gamma then beta, 1 = local beta cotangent,
     // 2 (retarded) = gamma cotangent handed to the mirror energy's lane
     constexpr int NS = RET ? 3 : 2;
