@@ -45,6 +45,10 @@ __device__ __forceinline__ Cx<T> cmuli(Cx<T> a) {  // i a
     return Cx<T>{-a.y, a.x};
 }
 
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename T>
 __device__ __forceinline__ T line_sum(T v, int Lw) {
 #pragma unroll
@@ -215,6 +219,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                 const bool act = j < nsteps;
                 const int q = nsl - 1 - j;  // sample reached (j < ns)
                 const bool at_sample = act && j < ns;
+                // the next step's parked gammas (written long ago) are fetched into L2
+                if (j + 1 < ns) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) prefetch_l2(&park(q - 1, 0, e));
+                }
                 T cdr = 0, cdi = 0, ca = 0, sdr = 0, sdi = 0;
                 if (act) {
                     const T dr = T(0.5) * (sh.x + slo.x), di = T(0.5) * (sh.y + slo.y), av = T(0.5) * (sh.z + slo.z);
@@ -223,19 +232,22 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                     T4 W = {};
                     if (!RET && at_sample) W = wimg[slot0 + q];
                     const C Wf{W.x, W.y};
-                    C gst[EPT];
 #pragma unroll
                     for (int e = 0; e < EPT; ++e) {
-                        // beta step (angle p + P: a -> -a)
-                        StepCoef<T> cb;
-                        step_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, cb);
-                        step_apply<T>(cb, b[e]);
-                        // forward segment with the same samples, differentiated at its start
+                        // the forward segment with the same samples, and the beta step
+                        // across it (angle p + P: a -> -a); for Matsubara energies the
+                        // two share Omega, E and c2 up to complex conjugation
+                        MobCoef<T> cf, cb;
+                        mob_coef<T>(dr, di, d2, zr0[e] + av, zi[e], ell, cf);
+                        if (RET)
+                            mob_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, cb);
+                        else
+                            mob_coef_mirror<T>(cf, dr, di, -av, zi[e], cb);
+                        b[e] = mob_apply<T>(cb, b[e]);
+                        // forward segment differentiated at its start
                         const C start = at_sample ? park(q, 0, e) : g0[e];
-                        gst[e] = start;
-                        C dummy;
                         StepGrad<T> Gd;
-                        step_grad<T>(dr, di, zr0[e] + av, zi[e], ell, start, dummy, Gd);
+                        mob_grad<T>(cf, dr, di, zr0[e] + av, zi[e], ell, start, Gd);
                         if (ev[e]) {
                             const C l = lam[e];
                             const C t1 = cmul(cconj(Gd.dR), l), t2 = cmul(Gd.dP, cconj(l));
@@ -315,12 +327,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                     const int hi = min(ns - j, ns - 1), lo = max(ns - 1 - j, 0);
                     T4 *ph = gimg + slot0 + hi;
                     T4 *pl = gimg + slot0 + lo;
-                    ph->x += T(0.5) * cdr;
-                    ph->y += T(0.5) * cdi;
-                    ph->z += T(0.5) * ca;
-                    pl->x += T(0.5) * cdr + (at_sample ? sdr : T(0));
-                    pl->y += T(0.5) * cdi + (at_sample ? sdi : T(0));
-                    pl->z += T(0.5) * ca;
+                    atomicAdd(&ph->x, T(0.5) * cdr);
+                    atomicAdd(&ph->y, T(0.5) * cdi);
+                    atomicAdd(&ph->z, T(0.5) * ca);
+                    atomicAdd(&pl->x, T(0.5) * cdr + (at_sample ? sdr : T(0)));
+                    atomicAdd(&pl->y, T(0.5) * cdi + (at_sample ? sdi : T(0)));
+                    atomicAdd(&pl->z, T(0.5) * ca);
                 }
                 if (act) {
                     sh = slo;
@@ -337,6 +349,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
             for (int i = 0; i < nmax; ++i) {
                 const bool act = i < nsteps;
                 T cdr = 0, cdi = 0, ca = 0;
+                // the next step's parked beta and beta cotangent are fetched into L2
+                if (i + 1 < ns) {
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        prefetch_l2(&park(i + 1, 0, e));
+                        prefetch_l2(&park(i + 1, 1, e));
+                    }
+                }
                 if (act) {
                     if (i == 0) {
 #pragma unroll
@@ -344,12 +364,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                     } else {
                         const T dr = T(0.5) * (sa.x + sb.x), di = T(0.5) * (sa.y + sb.y), av = T(0.5) * (sa.z + sb.z);
                         const T ell = (i == ns) ? tail : h;
+                        const T d2 = dr * dr + di * di;
 #pragma unroll
                         for (int e = 0; e < EPT; ++e) {
                             const C start = i < ns ? park(i, 0, e) : b0[e];
-                            C dummy;
+                            MobCoef<T> cb;
+                            mob_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, cb);
                             StepGrad<T> Gd;
-                            step_grad<T>(dr, di, zr0[e] - av, zi[e], ell, start, dummy, Gd);
+                            mob_grad<T>(cb, dr, di, zr0[e] - av, zi[e], ell, start, Gd);
                             if (ev[e]) {
                                 const C m = mu[e];
                                 const C t1 = cmul(cconj(Gd.dR), m), t2 = cmul(Gd.dP, cconj(m));
@@ -370,12 +392,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                     const int s0 = max(i - 1, 0), s1 = min(i, ns - 1);
                     T4 *p0 = gimg + slot0 + s0;
                     T4 *p1 = gimg + slot0 + s1;
-                    p0->x += T(0.5) * cdr;
-                    p0->y += T(0.5) * cdi;
-                    p0->z += T(0.5) * ca;
-                    p1->x += T(0.5) * cdr;
-                    p1->y += T(0.5) * cdi;
-                    p1->z += T(0.5) * ca;
+                    atomicAdd(&p0->x, T(0.5) * cdr);
+                    atomicAdd(&p0->y, T(0.5) * cdi);
+                    atomicAdd(&p0->z, T(0.5) * ca);
+                    atomicAdd(&p1->x, T(0.5) * cdr);
+                    atomicAdd(&p1->y, T(0.5) * cdi);
+                    atomicAdd(&p1->z, T(0.5) * ca);
                 }
                 if (act) {
                     sa = sb;

@@ -235,4 +235,120 @@ __host__ __device__ __forceinline__ void step_grad(T dr, T di, T zr, T zi, T ell
     G.dR = C{r1.x + r2.x, r1.y + r2.y};
 }
 
+// ---------------------------------------------------------------------------
+// The same step as a Moebius map, for the adjoint sweep.  The Riccati equation
+// d gamma/ds = i (Delta* gamma^2 + 2 z gamma + Delta) is the projective image of
+// (u, v)' = M (u, v) with M = [[i z, i Delta], [-i Delta*, -i z]] (gamma = u/v),
+// whose eigenvalues are +-Omega.  exp(M ell) = cosh(Omega ell) + sinh(Omega ell)
+// M/Omega; scaled by 2 exp(-Omega ell), with E = exp(-2 Omega ell) and
+// c2 = (1 - E)/Omega, its entries are
+//   a = 1 + E + i z c2,  b = i Delta c2,  c = -i Delta* c2,  d = 1 + E - i z c2,
+// and gamma' = (a gamma + b)/(c gamma + d), with ad - bc = 4E.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MobCoef {
+    Cx<T> a, b, c, d;  // gamma' = (a gamma + b)/(c gamma + d)
+    Cx<T> E, c2, iO;   // exp(-2 Omega ell), (1 - E)/Omega, 1/Omega
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ void mob_assemble(T dr, T di, T zr, T zi, MobCoef<T> &m) {
+    const T tr = zr * m.c2.x - zi * m.c2.y, ti = zr * m.c2.y + zi * m.c2.x;             // z c2
+    const T ur = dr * m.c2.x - di * m.c2.y, ui = dr * m.c2.y + di * m.c2.x;             // Delta c2
+    const T vr = dr * m.c2.x + di * m.c2.y, vi = dr * m.c2.y - di * m.c2.x;             // Delta* c2
+    const T ope = T(1) + m.E.x;
+    m.a = Cx<T>{ope - ti, m.E.y + tr};
+    m.d = Cx<T>{ope + ti, m.E.y - tr};
+    m.b = Cx<T>{-ui, ur};
+    m.c = Cx<T>{vi, -vr};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ void mob_coef(T dr, T di, T d2, T zr, T zi, T ell, MobCoef<T> &m) {
+    typedef Mth<T> M;
+    using ::copysign;
+    using ::fabs;
+    const T x = d2 - zr * zr + zi * zi;  // Re Omega^2
+    const T y = T(-2) * zr * zi;         // Im Omega^2
+    const T r = M::sqrt(x * x + y * y);
+    const T hs = T(0.5) * (r + fabs(x));
+    const T q = M::rsqrt(hs);
+    const T s = hs * q;
+    const T yq = T(0.5) * y * q;
+    T Or, Oi;
+    if (x >= T(0)) {
+        Or = s;
+        Oi = yq;
+    } else {
+        Or = fabs(yq);
+        Oi = copysign(s, y);
+    }
+    const T ro = M::rcp(Or * Or + Oi * Oi);
+    m.iO = Cx<T>{Or * ro, -Oi * ro};
+    const T eu = M::expneg(T(2) * ell * Or);
+    T sn, cs;
+    M::sincos_(T(2) * ell * Oi, &sn, &cs);
+    m.E = Cx<T>{eu * cs, -eu * sn};
+    const T omr = T(1) - m.E.x, omi = -m.E.y;
+    m.c2 = Cx<T>{omr * m.iO.x - omi * m.iO.y, omr * m.iO.y + omi * m.iO.x};
+    mob_assemble<T>(dr, di, zr, zi, m);
+}
+
+// Coefficients of the same segment for z' = -conj(z) (the opposite direction of
+// a Matsubara pair: z = a + i eps_n, z' = -a + i eps_n).  Omega^2 is conjugated,
+// and so are Omega, E and c2.
+template <typename T>
+__host__ __device__ __forceinline__ void mob_coef_mirror(const MobCoef<T> &f, T dr, T di, T zr, T zi,
+                                                         MobCoef<T> &m) {
+    m.E = Cx<T>{f.E.x, -f.E.y};
+    m.c2 = Cx<T>{f.c2.x, -f.c2.y};
+    m.iO = Cx<T>{f.iO.x, -f.iO.y};
+    mob_assemble<T>(dr, di, zr, zi, m);
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ Cx<T> mob_apply(const MobCoef<T> &m, Cx<T> g) {
+    const Cx<T> n{m.a.x * g.x - m.a.y * g.y + m.b.x, m.a.x * g.y + m.a.y * g.x + m.b.y};
+    const Cx<T> u = crcp(Cx<T>{m.c.x * g.x - m.c.y * g.y + m.d.x, m.c.x * g.y + m.c.y * g.x + m.d.y});
+    return cmul(n, u);
+}
+
+// Derivatives of gamma' = Phi(gamma; P = Delta*, Q = z, R = Delta) in the
+// Moebius form.  With u = 1/(c gamma + d) and Ab = gamma u, Bb = u,
+// Cb = -gamma' gamma u, Db = -gamma' u (the partials of gamma' by a, b, c, d):
+//   dPhi/dgamma = 4 E u^2
+//   dPhi/dX = Omega_X S + i c2 (Ab dQ + Bb dR - Cb dP - Db dQ)     (X in P, Q, R)
+//   S = -2 ell E (Ab + Db) + i kappa ((Ab - Db) z + Bb Delta - Cb Delta*)
+//   kappa = dc2/dOmega = (2 ell E - c2)/Omega
+//   Omega_R = Delta*/(2 Omega), Omega_P = Delta/(2 Omega), Omega_Q = -z/Omega
+template <typename T>
+__host__ __device__ __forceinline__ void mob_grad(const MobCoef<T> &m, T dr, T di, T zr, T zi, T ell, Cx<T> g,
+                                                  StepGrad<T> &G) {
+    typedef Cx<T> C;
+    const C u = crcp(C{m.c.x * g.x - m.c.y * g.y + m.d.x, m.c.x * g.y + m.c.y * g.x + m.d.y});
+    const C gp = cmul(C{m.a.x * g.x - m.a.y * g.y + m.b.x, m.a.x * g.y + m.a.y * g.x + m.b.y}, u);
+    const C Ab = cmul(g, u);
+    const C Db{-(gp.x * u.x - gp.y * u.y), -(gp.x * u.y + gp.y * u.x)};
+    const C Cb = cmul(g, Db);
+    const C u2 = cmul(u, u);
+    const C Eu2 = cmul(m.E, u2);
+    G.dg = C{T(4) * Eu2.x, T(4) * Eu2.y};
+    const C kap = cmul(C{T(2) * ell * m.E.x - m.c2.x, T(2) * ell * m.E.y - m.c2.y}, m.iO);
+    const C apd{Ab.x + Db.x, Ab.y + Db.y}, amd{Ab.x - Db.x, Ab.y - Db.y};
+    const C t1 = cmul(m.E, apd);
+    const C w1 = cmul(amd, C{zr, zi}), w2 = cmul(u, C{dr, di}), w3 = cmul(Cb, C{dr, -di});
+    const C w{w1.x + w2.x - w3.x, w1.y + w2.y - w3.y};
+    const C kw = cmul(kap, w);
+    const T m2l = T(-2) * ell;
+    const C S{m2l * t1.x - kw.y, m2l * t1.y + kw.x};          // -2 ell E (Ab + Db) + i kappa w
+    const C SO = cmul(S, m.iO);                                // S / Omega
+    const C sR = cmul(SO, C{T(0.5) * dr, T(-0.5) * di});       // S Delta*/(2 Omega)
+    const C sP = cmul(SO, C{T(0.5) * dr, T(0.5) * di});        // S Delta/(2 Omega)
+    const C sQ = cmul(SO, C{zr, zi});                          // S z / Omega
+    const C cB = cmul(m.c2, u), cC = cmul(m.c2, Cb), cA = cmul(m.c2, amd);
+    G.dR = C{sR.x - cB.y, sR.y + cB.x};
+    G.dP = C{sP.x + cC.y, sP.y - cC.x};
+    G.dQ = C{-sQ.x - cA.y, -sQ.y + cA.x};
+}
+
 }  // namespace scd
