@@ -40,6 +40,9 @@ ALG_FP32_OPS_PER_PSE = 2 * (58 + 18) + 22
 ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
+# FP64 pipe: ncu reports sm__inst_executed_pipe_fp64 peak 0.0625 warp instructions
+# per cycle per SM on B300, i.e. 2 lanes per cycle per SM
+FP64_LANES_PER_SM = 2
 
 
 def _measured_peaks():
@@ -248,10 +251,16 @@ def run_ours(args):
 
     peaks = _measured_peaks()
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    # FP32 issue roofline: 148 SMs x 128 FP32 lanes x max SM clock
-    peak_gops = SM_COUNT_B300 * FP32_LANES_PER_SM * sm_max * 1e6 / 1e9
+    # issue roofline of the arithmetic pipe the sweep runs on: 148 SMs x lanes per
+    # cycle (FP32: 128; FP64: 2) x max SM clock
+    lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
+    peak_gops = SM_COUNT_B300 * lanes * sm_max * 1e6 / 1e9
+    peak_note = ("FP32 lane issue 148 SM x 128 x max SM clock (derived)" if args.precision == "fp32" else
+                 "FP64 pipe 148 SM x 2 lanes/cycle (ncu pipe peak) x max SM clock (derived); the IEEE "
+                 "division, square root, exp and sin/cos sequences run on the same pipe")
     pse = info.points_per_sweep // 2  # (pair, sample, energy) combinations per sweep
-    ops = pse * (ALG_FP32_OPS_PER_PSE if args.precision == "fp32" else ALG_FP32_OPS_PER_PSE)
+    # the same arithmetic in either precision (transcendentals not counted)
+    ops = pse * ALG_FP32_OPS_PER_PSE
     achieved = ops / (sweep_ms * 1e-3) / 1e9
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     traffic = None
@@ -278,12 +287,13 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "sweep_kernel", "ms_per_launch": sweep_ms,
-                     "kernels_ms_per_step": kernels_ms,
-                     "peak_note": "FP32 lane issue 148 SM x 128 x max SM clock (derived)"},
+                     "kernels_ms_per_step": kernels_ms, "peak_note": peak_note},
         "e2e": ({"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
                  "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
                 if e2e_ms else None),
-        "gpu_launches": 4 * args.steps,
+        # per step: (FP32: field conversion,) rotate, sweep, rotate-back, outputs;
+        # adjoint: output cotangents, transposed rotate-back, adjoint sweep, transposed rotate
+        "gpu_launches": ((5 if args.precision == "fp32" else 4) + (4 if args.adjoint else 0)) * args.steps,
         "clocks": clocks,
         "wall_s": t_wall,
     }
@@ -342,7 +352,8 @@ def run_batch(args):
     sweep_ms = statistics.mean(ksweep)
     pse = info.steps_per_sweep // 2  # ~ (pair, sample, energy) combinations
     achieved = pse * ALG_FP32_OPS_PER_PSE / (sweep_ms * 1e-3) / 1e9
-    peak_gops = SM_COUNT_B300 * FP32_LANES_PER_SM * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
+    lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
+    peak_gops = SM_COUNT_B300 * lanes * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -356,8 +367,11 @@ def run_batch(args):
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved / peak_gops, "traffic": None, "kernel": "sweep_kernel",
-                     "ms_per_launch": sweep_ms},
+                     "frac": achieved / peak_gops, "traffic": None,
+                     "kernel": f"sweep_kernel ({info.sweep_launches} launches back to back per sweep)",
+                     "ms_per_sweep": sweep_ms,
+                     "peak_note": ("FP32" if args.precision == "fp32" else "FP64")
+                     + " lane issue 148 SM x lanes/cycle x max SM clock (derived)"},
         # per member: (FP32: field conversion,) rotate, rotate-back, outputs; plus
         # one sweep launch per energies-per-lane class
         "gpu_launches": ((4 if args.precision == "fp32" else 3) * args.grains

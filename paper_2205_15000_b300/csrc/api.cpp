@@ -245,6 +245,7 @@ namespace {
 
 using sc_internal::check_ctx;
 using sc_internal::make_plan;
+using sc_internal::make_plan_layout;
 
 // one persistent sweep launch over the plan's items for one grain descriptor
 sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *d_grain, bool retarded,
@@ -972,6 +973,29 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
     return rc;
 }
 
+// Layout of the adjoint sweep: the forward sweep's, unless its work items fill
+// less than half of the warps the adjoint kernel keeps resident (a small grain);
+// then twice the lanes per line (twice the items, fewer energies per lane) as
+// long as at least 3/4 of the lane slots carry an energy.
+static sc_status adjoint_plan(sc_ctx *ctx, Plan **out) {
+    Plan *pl = ctx->main_plan;
+    *out = pl;
+    if (ctx->forced_lanes) return SC_OK;
+    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl->ept, 128));
+    const int64_t resident = (int64_t)ctx->sm_count * occ * 4;
+    int lanes = pl->lanes, ept = pl->ept;
+    int64_t items = pl->n_groups;
+    while (lanes < 32 && 2 * items <= resident) {
+        const int l2 = 2 * lanes, e2 = (ctx->n_e + l2 - 1) / l2;
+        if (4 * ctx->n_e < 3 * l2 * e2) break;
+        lanes = l2;
+        ept = e2;
+        items *= 2;
+    }
+    if (lanes == pl->lanes) return SC_OK;
+    return make_plan_layout(ctx, ctx->n_e, lanes, ept, out);
+}
+
 sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double *g_j, const double *g_F,
                            double g_Ftotal, double *dL_ddelta, double *dL_daind, int on_device, void *stream) {
     CKS(check_ctx(ctx));
@@ -980,7 +1004,9 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     cudaStream_t st = (cudaStream_t)stream;
     const size_t np = npts(ctx);
     const size_t t4 = ctx->fp64 ? 32 : 16;
-    const Plan &pl = *ctx->main_plan;
+    Plan *apl = nullptr;
+    CKS(adjoint_plan(ctx, &apl));
+    const Plan &pl = *apl;
     if (!ctx->d_gacc) {
         CK(dalloc(ctx, &ctx->d_gacc, 5 * np * sizeof(double)));
         CK(dalloc(ctx, &ctx->d_gdelta, 2 * np * sizeof(double)));
