@@ -99,9 +99,10 @@ def _sample_clocks_stop(proc, f, path, device_index=0):
             "samples": len(sm)}
 
 
-def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16):
+def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16, keep=None):
     """The FP64 oracle on this host: the same grain and energies with a subset
-    of the Fermi angles (a bounded sample); returns steps/s and details."""
+    of the Fermi angles (a bounded sample); returns steps/s and details.  With
+    `keep` (a dict), the last sweep's outputs and the mask are stored in it."""
     import oracle
     q = dict(p)
     q["n_angles"] = angle_subset
@@ -116,11 +117,35 @@ def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16):
         o = g.full_sweep(delta, aind, ex)
         ex = o["exit"]
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep["out"] = o
+        keep["mask"] = g.mask().astype(bool)
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": steps * n_sweeps / dt, "unit": "trajectory-steps/s", "cores": threads,
             "kind": "oracle",
             "sample": f"{n_sweeps} FP64 sweep(s) of the same grain and 80 energies with "
                       f"{angle_subset} of 128 Fermi angles ({steps} steps per sweep), {dt:.2f} s"}
+
+
+def _errors_vs_oracle(p, delta, precision, keep):
+    """Max-norm errors of Delta_new, j and F(R) (relative to the oracle's max over
+    the grain) after two sweeps from fresh boundary values, the library in
+    `precision` against the FP64 oracle on the same inputs."""
+    from paper_2205_15000_b300 import sc
+    ctx = sc.Context(p, precision=precision)
+    ctx.set_fields(delta)
+    for _ in range(2):
+        ctx.sweep()
+    r = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ctx.outputs().items()}
+    o, m = keep["out"], keep["mask"]
+
+    def rel(a, b):
+        return float(np.max(np.abs(a[m] - b[m])) / max(np.max(np.abs(b[m])), 1e-300))
+    return {"delta_new": rel(r["delta_new"], o["delta_new"]), "j": rel(r["j"], o["j"]),
+            "F": rel(r["F"], o["F"]),
+            "F_total": abs(r["F_total"] - o["F_total"]) / abs(o["F_total"]),
+            "tolerance": {"delta_new": 1e-5, "j": 1e-4, "F": 1e-4},
+            "norm": "max over the grain, relative to the oracle's max; 2 sweeps from fresh boundary values"}
 
 
 def run_reference(args):
@@ -298,7 +323,9 @@ def run_ours(args):
         "wall_s": t_wall,
     }
     if not args.no_cpu_baseline and args.workload == "c2":
-        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"])
+        keep = {}
+        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"], keep)
+        line["errors_vs_fp64_oracle"] = _errors_vs_oracle(p, delta, args.precision, keep)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

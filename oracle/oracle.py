@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("kappa", ctypes.c_double), ("charge_sign", ctypes.c_int32),
         ("n_angles", ctypes.c_int32), ("n_energies", ctypes.c_int32),
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
+        ("stepper", ctypes.c_int32),
     ]
 
 
@@ -93,6 +94,19 @@ def quad_weight(k, n):
     return lib().or_quad_weight(int(k), int(n))
 
 
+STEPPERS = {"closed": 0, "midpoint": 1}
+
+
+def step_midpoint(P, Q, R, ell, ga):
+    """Implicit midpoint step (App. C, Eq. riccati_midpoint) of
+    d gamma/ds = i (P gamma^2 + 2 Q gamma + R) over a length ell."""
+    L = lib()
+    arr = [np.array([complex(v).real, complex(v).imag]) for v in (P, Q, R, ga)]
+    out = np.zeros(2)
+    L.or_step_midpoint(_p(arr[0]), _p(arr[1]), _p(arr[2]), ctypes.c_double(ell), _p(arr[3]), _p(out))
+    return complex(out[0], out[1])
+
+
 def step(P, Q, R, ell, ga):
     L = lib()
     arr = [np.array([complex(v).real, complex(v).imag]) for v in (P, Q, R, ga)]
@@ -116,6 +130,9 @@ class OracleGeom:
                 continue
             if name == "n_vert":
                 s.n_vert = len(prm.get("vx", [])) if prm.get("shape_kind", 0) == 1 else 0
+                continue
+            if name == "stepper":
+                s.stepper = STEPPERS[prm.get("stepper", "closed")]
                 continue
             setattr(s, name, prm[name])
         s.vx = vx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -266,6 +266,7 @@ or_geom *or_geom_create(const or_params *prm) {
     if (prm->nx < 2 || prm->ny < 2 || !(prm->h > 0)) { fail("bad grid"); return NULL; }
     if (prm->n_angles < 2 || prm->n_angles % 2) { fail("n_angles must be even"); return NULL; }
     if (prm->n_energies < 1) { fail("n_energies < 1"); return NULL; }
+    if (prm->stepper != 0 && prm->stepper != 1) { fail("stepper must be 0 or 1"); return NULL; }
     if (!(prm->t > 0 && prm->t <= 1)) { fail("t out of (0,1]"); return NULL; }
     if (prm->shape_kind == 1 && (prm->n_vert < 3 || !prm->vx || !prm->vy)) {
         fail("polygon needs >= 3 vertices");
@@ -664,6 +665,35 @@ static cplx riccati_step(cplx P, cplx Q, cplx R, double ell, cplx ga) {
     return gh + d * E / (1.0 - I * P * d * c);
 }
 
+/* Implicit midpoint rule (App. C): g1 = g0 + ell f((g0 + g1)/2) with
+   f(g) = i (P g^2 + 2 Q g + R).  Collecting powers of g1 gives
+   c2 g1^2 + c1 g1 + c0 = 0 with
+     c2 = i ell P / 4,
+     c1 = 2 c2 g0 + i ell Q - 1,
+     c0 = (c1 - c2 g0 + 2) g0 + i ell R
+   (for R = conj P, as for gamma and gamma~, i ell R = -4 conj(c2): the paper's
+   form), and the root that tends to -c0/c1 as P -> 0 is
+     g1 = 2 c0 / (-c1 + sqrt(c1^2 - 4 c2 c0))      (principal square root;
+   Re c1 < 0 whenever ell |P| < 2 and Im Q > 0, so the denominator is near -2 c1). */
+static cplx riccati_midpoint(cplx P, cplx Q, cplx R, double ell, cplx g0) {
+    cplx c2 = I * ell * P / 4.0;
+    cplx c1 = 2.0 * c2 * g0 + I * ell * Q - 1.0;
+    cplx c0 = (c1 - c2 * g0 + 2.0) * g0 + I * ell * R;
+    return 2.0 * c0 / (-c1 + csqrt(c1 * c1 - 4.0 * c2 * c0));
+}
+
+/* the step of the configured method */
+static cplx riccati_advance(const or_geom *g, cplx P, cplx Q, cplx R, double ell, cplx ga) {
+    return g->P.stepper == 1 ? riccati_midpoint(P, Q, R, ell, ga) : riccati_step(P, Q, R, ell, ga);
+}
+
+void or_step_midpoint(const double *P, const double *Q, const double *R, double ell,
+                      const double *ga, double *gb) {
+    cplx r = riccati_midpoint(P[0] + I * P[1], Q[0] + I * Q[1], R[0] + I * R[1], ell, ga[0] + I * ga[1]);
+    gb[0] = creal(r);
+    gb[1] = cimag(r);
+}
+
 void or_step(const double *P, const double *Q, const double *R, double ell, const double *ga,
              double *gb) {
     cplx r = riccati_step(P[0] + I * P[1], Q[0] + I * Q[1], R[0] + I * R[1], ell, ga[0] + I * ga[1]);
@@ -771,7 +801,7 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                     gm = riccati_fixed_point(conj(dseg[0]), zn + aseg[0], dseg[0]);
                 }
                 for (int q = 0; q < nseg; ++q) {
-                    gm = riccati_step(conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
+                    gm = riccati_advance(g, conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
                     if (q < ns) gam[q] = gm;
                 }
                 int64_t oi = 2 * (A * n_e + n);
@@ -795,7 +825,7 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                     gt = riccati_fixed_point(-dseg[ns], zn + aseg[ns], -conj(dseg[ns]));
                 }
                 for (int q = ns; q >= 0; --q) {
-                    gt = riccati_step(-dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
+                    gt = riccati_advance(g, -dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
                     if (q > 0) gat[q - 1] = gt;
                 }
                 int64_t ti = 2 * (NLA * n_e + A * n_e + n);
@@ -1120,12 +1150,12 @@ int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, c
                 cplx zn = z[2 * n] + I * z[2 * n + 1];
                 cplx gm = riccati_fixed_point(conj(dseg[0]), zn + aseg[0], dseg[0]);
                 for (int q = 0; q <= ns; ++q) {
-                    gm = riccati_step(conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
+                    gm = riccati_advance(g, conj(dseg[q]), zn + aseg[q], dseg[q], lseg[q], gm);
                     if (q < ns) gam[q] = gm;
                 }
                 cplx gt = riccati_fixed_point(-dseg[ns], zn + aseg[ns], -conj(dseg[ns]));
                 for (int q = ns; q >= 0; --q) {
-                    gt = riccati_step(-dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
+                    gt = riccati_advance(g, -dseg[q], zn + aseg[q], -conj(dseg[q]), lseg[q], gt);
                     if (q > 0) gat[q - 1] = gt;
                 }
                 for (int q = 0; q < ns; ++q) {

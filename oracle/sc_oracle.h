@@ -12,7 +12,8 @@
  *                                                              (Sec. 3.1, main algorithm)
  *   - Riccati equations for gamma and gamma~                   (Eqs. riccati, riccati_tilde)
  *     integrated with the closed-form step for piecewise-constant
- *     coefficients (the "stepping method" of App. C)
+ *     coefficients (the "stepping method" of App. C) or with the
+ *     implicit midpoint rule                                    (App. C, Eq. riccati_midpoint)
  *   - propagator from the coherence functions                  (Eq. riccati_parameterization)
  *   - gap equation in fixed-point form                         (Eq. gapeq_fixpoint)
  *   - current density                                          (Eq. current_density)
@@ -44,6 +45,8 @@ typedef struct {
     int32_t n_angles;        /* even */
     int32_t n_energies;      /* positive Matsubara energies */
     double lattice_ox, lattice_oy; /* lattice origin offset from the grid centre, units of h */
+    int32_t stepper;         /* 0 = closed-form step for piecewise-constant coefficients,
+                                1 = implicit midpoint rule (App. C, Eq. riccati_midpoint) */
 } or_params;
 
 typedef struct or_geom or_geom;
@@ -70,6 +73,11 @@ int or_geom_quadrature(const or_geom *g, double *w, double *vhat, double *eta);
 /* Closed-form step of d gamma/ds = i (P g^2 + 2 Q g + R) over a length ell. */
 void or_step(const double *P, const double *Q, const double *R, double ell,
              const double *ga, double *gb);
+
+/* Implicit midpoint step (App. C) of the same equation over a length ell:
+   gb = ga + ell i (P m^2 + 2 Q m + R) with m = (ga + gb)/2, solved as a quadratic. */
+void or_step_midpoint(const double *P, const double *Q, const double *R, double ell,
+                      const double *ga, double *gb);
 
 /* Fields sampled on the rotated lattice of one pair: delta (complex, without eta)
    and A_total (vector) at every sample, canonical order (line, m). */
