@@ -38,6 +38,9 @@ WORKLOAD = "c2_diamond_dx2y2_256sq_128ang_80eps"
 # propagator/energy-sum evaluation (22); MUFU operations counted separately (15)
 ALG_FP32_OPS_PER_PSE = 2 * (58 + 18) + 22
 ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
+# the implicit midpoint stepper: a quadratic per step (47 FP32 ops, 3 MUFU) with the
+# same propagator evaluation
+ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 47 + 22}
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
 # FP64 pipe: ncu reports sm__inst_executed_pipe_fp64 peak 0.0625 warp instructions
@@ -193,6 +196,7 @@ def run_ours(args):
         p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
             f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
+    p["stepper"] = args.stepper
     ctx = sc.Context(p, precision=args.precision, record_timings=True)
     info = ctx.info
     stream = torch.cuda.current_stream()
@@ -285,7 +289,7 @@ def run_ours(args):
                  "division, square root, exp and sin/cos sequences run on the same pipe")
     pse = info.points_per_sweep // 2  # (pair, sample, energy) combinations per sweep
     # the same arithmetic in either precision (transcendentals not counted)
-    ops = pse * ALG_FP32_OPS_PER_PSE
+    ops = pse * ALG_OPS_PER_PSE[args.stepper]
     achieved = ops / (sweep_ms * 1e-3) / 1e9
     prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
     traffic = None
@@ -303,7 +307,7 @@ def run_ours(args):
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": workload, "grid": [p["nx"], p["ny"]], "n_angles": p["n_angles"],
                    "n_energies": p["n_energies"], "t": p["t"], "pairing": "dx2y2",
-                   "flux_quanta": p["flux_quanta"], "precision": args.precision,
+                   "flux_quanta": p["flux_quanta"], "precision": args.precision, "stepper": args.stepper,
                    "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
                    "parallelism": f"replicas{world}",
                    "step": "forward sweep + outputs" + (" + adjoint of F_total" if args.adjoint else ""),
@@ -346,6 +350,8 @@ def run_batch(args):
     dist = ranks.init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     grains = W.c3_batch(n_grains=args.grains, seed=3 + rank)
+    for p, _, _ in grains:
+        p["stepper"] = args.stepper
     b = sc.Batch([p for p, _, _ in grains], precision=args.precision)
     for (p, d, _), m in zip(grains, b.members):
         m.set_fields(d)
@@ -378,7 +384,7 @@ def run_batch(args):
         return 0
     sweep_ms = statistics.mean(ksweep)
     pse = info.steps_per_sweep // 2  # ~ (pair, sample, energy) combinations
-    achieved = pse * ALG_FP32_OPS_PER_PSE / (sweep_ms * 1e-3) / 1e9
+    achieved = pse * ALG_OPS_PER_PSE[args.stepper] / (sweep_ms * 1e-3) / 1e9
     lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
     peak_gops = SM_COUNT_B300 * lanes * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
     line = {
@@ -388,7 +394,7 @@ def run_batch(args):
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": f"c3_batch_{args.grains}_grains", "grains": args.grains,
                    "steps_per_sweep": info.steps_per_sweep, "work_items": info.n_items,
-                   "energies_per_lane": ept, "precision": args.precision,
+                   "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
                    "lane_fill": info.steps_per_sweep / max(info.lane_steps_per_sweep, 1),
                    "sweep_launches": info.sweep_launches,
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
@@ -418,6 +424,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--stepper", default="closed", choices=["closed", "midpoint"],
+                    help="integrator along a line: closed-form step or implicit midpoint rule (App. C)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="grid side (reduced cases for profiling)")
     ap.add_argument("--angles", type=int, default=128, help="Fermi angles (reduced cases for profiling)")

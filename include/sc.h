@@ -48,6 +48,12 @@ typedef enum {
 
 typedef enum { SC_PAIR_S = 0, SC_PAIR_DX2Y2 = 1, SC_PAIR_DXY = 2, SC_PAIR_G = 3 } sc_pairing;
 typedef enum { SC_PREC_FP64 = 0, SC_PREC_FP32 = 1 } sc_precision;
+/* Integrator of Eq. riccati along a line (App. C).  CLOSED: the exact solution
+   for coefficients held constant on each segment (half-step values, linear
+   interpolation between samples).  MIDPOINT: the implicit midpoint rule with the
+   same half-step values, g1 = g0 + ell f((g0 + g1)/2), solved as a quadratic
+   (Eq. riccati_midpoint; the paper's production method). */
+typedef enum { SC_STEP_CLOSED = 0, SC_STEP_MIDPOINT = 1 } sc_stepper;
 
 /*
  * Problem statement of one grain (configuration appendix of the paper:
@@ -78,6 +84,9 @@ typedef struct {
                                 the discretisation on a machine without a GPU. */
     int32_t record_timings;  /* 1 = time the three kernels of every sweep with CUDA events on
                                 the sweep's stream (reported by sc_get_info) */
+    int32_t stepper;         /* sc_stepper: how each segment of a line is integrated
+                                (App. C); every sweep, burn-in, LDOS and adjoint of the
+                                context uses it */
 } sc_params;
 
 typedef struct {

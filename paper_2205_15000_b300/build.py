@@ -2,6 +2,7 @@
 
     python -m paper_2205_15000_b300.build
 """
+import concurrent.futures
 import os
 import subprocess
 import sys
@@ -11,8 +12,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libsc.so")
-SOURCES = ["kernels.cu", "lattice_f32.cu", "adjoint.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu"]
-HEADERS = ["kernels.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp", "adjoint.cuh"]
+SOURCES = ["kernels.cu", "sweep_f32.cu", "sweep_f64.cu", "lattice_f32.cu", "adjoint.cu", "adjoint_f32.cu",
+           "adjoint_f64.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu"]
+HEADERS = ["kernels.cuh", "sweep_kernel.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp", "adjoint.cuh",
+           "adjoint_kernel.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -25,17 +28,30 @@ def _stale():
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False):
-    if not force and not _stale():
-        return LIB
-    os.makedirs(LIBDIR, exist_ok=True)
-    cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-           "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES] + ["-lcudart"]
+def _compile(src, obj, verbose):
+    cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
+        print(" ".join(cmd), flush=True)
+    return subprocess.run(cmd, capture_output=not verbose, text=True)
+
+
+def build(force=False, verbose=False):
+    """Compile every source to an object (in parallel) and link libsc.so."""
+    if not force and not _stale():
+        return LIB
+    objdir = os.path.join(LIBDIR, "obj")
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, f + ".o") for f in SOURCES]
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(lambda so: _compile(so[0], so[1], verbose), zip(SOURCES, objs)))
+    for src, r in zip(SOURCES, results):
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout or ''}{r.stderr or ''}")
+    link = [NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
+    subprocess.run(link, check=True)
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

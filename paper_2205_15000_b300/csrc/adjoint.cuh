@@ -21,10 +21,16 @@ struct AdjointLaunch {
     int32_t energies_per_lane;
     int32_t retarded;          // LDOS mode: wimg holds n_e weights per slot
     int32_t grid_blocks, block_threads;
+    int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
 };
 
 cudaError_t launch_adjoint_sweep(bool fp64, const AdjointLaunch &a, cudaStream_t s);
-int adjoint_occupancy(bool fp64, int ept, int block_threads);
+int adjoint_occupancy(bool fp64, int ept, int block_threads, int stepper);
+// per-precision instantiations (adjoint_f32.cu, adjoint_f64.cu)
+cudaError_t launch_adjoint_sweep_f32(const AdjointLaunch &a, cudaStream_t s);
+cudaError_t launch_adjoint_sweep_f64(const AdjointLaunch &a, cudaStream_t s);
+int adjoint_occupancy_f32(int ept, int block_threads, int stepper);
+int adjoint_occupancy_f64(int ept, int block_threads, int stepper);
 cudaError_t launch_adjoint_outputs(const GridDev &grid, const uint8_t *mask, const double *delta,
                                    const double *aind, double t, double normD, double kappa, double n_in,
                                    const double *gdn, const double *gj, const double *gF, double gFtot,

@@ -185,7 +185,7 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     CK(dalloc(ctx, &pl.d_items, items.size() * sizeof(int2)));
     CK(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     const int bs = 128;
-    int occ = scd::sweep_occupancy(ctx->fp64, ept, bs);
+    int occ = scd::sweep_occupancy(ctx->fp64, ept, bs, ctx->stepper);
     if (occ < 1) occ = 1;
     pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
     pl.stride = (int64_t)G * std::max(ctx->geo.max_ns, 1) * lanes * ept;
@@ -265,6 +265,7 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     a.retarded = retarded ? 1 : 0;
     a.grid_blocks = pl.grid_blocks;
     a.block_threads = 128;
+    a.stepper = ctx->stepper;
     CK(scd::launch_sweep(ctx->fp64, a, st));
     return SC_OK;
 }
@@ -348,6 +349,10 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         g_create_error = "lanes_per_line must be 0, 4, 8, 16 or 32";
         return SC_EINVAL;
     }
+    if (p->stepper != SC_STEP_CLOSED && p->stepper != SC_STEP_MIDPOINT) {
+        g_create_error = "stepper must be SC_STEP_CLOSED or SC_STEP_MIDPOINT";
+        return SC_EINVAL;
+    }
     sc_ctx *ctx = new (std::nothrow) sc_ctx();
     if (!ctx) {
         g_create_error = "host allocation failed";
@@ -364,6 +369,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     ctx->real_bytes = ctx->fp64 ? 8 : 4;
     ctx->n_e = p->n_energies;
     ctx->forced_lanes = p->lanes_per_line;
+    ctx->stepper = p->stepper;
     {
         double s = 0.0;
         for (int n = 0; n < ctx->n_e; ++n) s += 1.0 / (2.0 * n + 1.0);
@@ -907,7 +913,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         if (rc != SC_OK) break;
         const Plan &pl = *R.pl;
         const size_t t4 = ctx->fp64 ? 32 : 16;
-        const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128));
+        const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
         const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
         const int64_t stride = 3 * pl.stride;
         cudaError_t e = cudaSuccess;
@@ -952,6 +958,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         a.parity = R.last_parity;
         a.energies_per_lane = pl.ept;
         a.retarded = 1;
+        a.stepper = ctx->stepper;
         a.grid_blocks = blocks;
         a.block_threads = 128;
         if ((e = scd::launch_adjoint_sweep(ctx->fp64, a, st)) != cudaSuccess ||
@@ -981,7 +988,7 @@ static sc_status adjoint_plan(sc_ctx *ctx, Plan **out) {
     Plan *pl = ctx->main_plan;
     *out = pl;
     if (ctx->forced_lanes) return SC_OK;
-    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl->ept, 128));
+    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl->ept, 128, ctx->stepper));
     const int64_t resident = (int64_t)ctx->sm_count * occ * 4;
     int lanes = pl->lanes, ept = pl->ept;
     int64_t items = pl->n_groups;
@@ -1015,7 +1022,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
         CK(dalloc(ctx, &ctx->d_wimg, ctx->geo.n_slots * t4));
         CK(dalloc(ctx, &ctx->d_gimg, ctx->geo.n_slots * t4));
     }
-    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128));
+    const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
     const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
     const int64_t stride = 2 * pl.stride;
     const size_t need = (size_t)blocks * 4 * (size_t)stride * 2 * ctx->real_bytes;
@@ -1067,6 +1074,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     a.parity = ctx->cur ^ 1;  // the buffer the last sweep read its entry values from
     a.energies_per_lane = pl.ept;
     a.retarded = 0;
+    a.stepper = ctx->stepper;
     a.grid_blocks = blocks;
     a.block_threads = 128;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev_adj[0], st));

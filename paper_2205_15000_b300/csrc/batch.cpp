@@ -20,6 +20,7 @@ struct sc_batch {
     int device = 0;
     bool fp64 = false;
     int ept = 0;  // bound on energies per lane
+    int stepper = 0;  // sc_stepper, shared by all members
     int sm_count = 0;
     scd::GrainSweep *d_grains = nullptr;
     int2 *d_items = nullptr;
@@ -162,7 +163,7 @@ sc_status build(sc_batch *b, int ept) {
     }
     int max_blocks = 1;
     for (auto &c : classes) {
-        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128);
+        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper);
         if (occ < 1) occ = 1;
         c.grid_blocks = std::max(1, std::min(b->sm_count * occ, (c.n + 3) / 4));
         max_blocks = std::max(max_blocks, c.grid_blocks);
@@ -244,9 +245,9 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     if (!b) return SC_ENOMEM;
     int max_ne = 0;
     for (int g = 0; g < n; ++g) {
-        if (params[g].precision != params[0].precision) {
+        if (params[g].precision != params[0].precision || params[g].stepper != params[0].stepper) {
             sc_batch_destroy(b);
-            sc_internal::set_thread_error("all members of a batch need the same precision");
+            sc_internal::set_thread_error("all members of a batch need the same precision and stepper");
             return SC_EINVAL;
         }
         if (params[g].host_only) {
@@ -270,6 +271,7 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
         b->steps_per_sweep += steps * c->n_e;
     }
     b->fp64 = params[0].precision == SC_PREC_FP64;
+    b->stepper = params[0].stepper;
     b->device = b->members[0]->device;
     b->sm_count = b->members[0]->sm_count;
     sc_status st = SC_OK;
@@ -338,6 +340,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.retarded = 0;
         a.grid_blocks = c.grid_blocks;
         a.block_threads = 128;
+        a.stepper = b->stepper;
         BCK(scd::launch_sweep(b->fp64, a, st));
     }
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));

@@ -28,6 +28,7 @@ struct sc_ctx {
     bool fp64 = false;
     int n_e = 0;
     int forced_lanes = 0;
+    int stepper = 0;  // sc_stepper
     double normD = 0.0;
     size_t real_bytes = 4;
     scd::GridDev grid{};

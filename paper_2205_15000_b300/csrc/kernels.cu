@@ -94,302 +94,13 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// The sweep.  A warp owns G = 32 / Lw lines of one work item; each line gets Lw
-// lanes and each lane EPT energies (n = lane_in_line + Lw * e).  Persistent:
-// warps take items (longest lines first) from an atomic counter.
-//
-// Forward pass: gamma of angle p from smin to smax; gamma at every sample is
-// parked in the warp's scratch slab ([line][sample][energy]).
-// Backward pass: gamma of angle p + P from smax to smin; at each sample the
-// parked gamma and the new one give the propagator of both angles
-// (gamma~(p) = conj gamma(p + P), Eq. symmetries), summed over the lane's
-// energies and then over the line's lanes by shuffles.
-// ---------------------------------------------------------------------------
-#ifndef SC_SWEEP_MIN_BLOCKS
-#define SC_SWEEP_MIN_BLOCKS 5  // FP32: 5 blocks of 128 threads per SM (at most 102 registers)
-#endif
-
-// One work item: the G lines of group it.y of grain gs, EPT energies per lane.
-template <typename T, int EPT, bool RET>
-__device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
-                                           Cx<T> *const warp_slab, const int lane) {
-    typedef typename Vec4<T>::type T4;
-    typedef Cx<T> C;
-    {
-        const int Lw = gs.lanes, G = gs.lines_per_warp;
-        const int gi = lane / Lw, r = lane - gi * Lw;
-        const T4 *__restrict__ img = (const T4 *)gs.image_in;
-        const C *__restrict__ exit_prev = (const C *)gs.exits[a.parity];
-        C *__restrict__ exit_cur = (C *)gs.exits[a.parity ^ 1];
-        C *slab = warp_slab + (int64_t)gi * gs.max_ns * gs.ne_pad;
-        const T h = (T)gs.h;
-        const int n_e = gs.n_e;
-        const int ne_pad = gs.ne_pad;
-
-        // the lane's energies: z = zr0 + i zi (+ a along the line)
-        T zr0[EPT], zi[EPT];
-        int nid[EPT], mir[EPT];
-        bool ev[EPT];
-#pragma unroll
-        for (int e = 0; e < EPT; ++e) {
-            const int n = r + Lw * e;
-            ev[e] = n < n_e;
-            const int nn = ev[e] ? n : n_e - 1;
-            nid[e] = nn;
-            if (RET) {
-                zr0[e] = (T)gs.energies[nn];
-                zi[e] = (T)gs.broadening;
-                mir[e] = n_e - 1 - nn;
-            } else {
-                zr0[e] = T(0);
-                zi[e] = (T)(gs.t * (nn + 0.5));
-                mir[e] = nn;
-            }
-        }
-        const int L = gs.groups[(int64_t)it.y * G + gi];
-        const bool lv = L >= 0;
-        const LineDev &ln = gs.lines[lv ? L : 0];
-        const int ns = lv ? ln.ns : 0;
-        const int nsl = ns > 0 ? ns : 1;
-        const int nsteps = lv ? ns + 1 : 0;
-        int nmax = nsteps;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(FULL_MASK, nmax, off));
-        const T lead = (T)ln.lead, tail = (T)ln.tail;
-        const int slot0 = ln.slot0;
-        const T4 *li = img + slot0;
-
-        // ---------------- forward: angle p, along +e_par ----------------
-        C g[EPT];
-        T4 sp = li[0];
-        if (a.first_sweep) {
-            const T d2 = sp.x * sp.x + sp.y * sp.y;
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                StepCoef<T> c;
-                step_coef<T>(sp.x, sp.y, d2, zr0[e] + sp.z, zi[e], lead, c);
-                g[e] = c.gh;
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                T gx = 0, gy = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const C v = exit_prev[(int64_t)ln.tap_f[q] * n_e + nid[e]];
-                    const T w = (T)ln.w_f[q];
-                    gx += w * v.x;
-                    gy += w * v.y;
-                }
-                g[e].x = gx;
-                g[e].y = gy;
-            }
-        }
-        // segment i joins samples max(i-1, 0) and min(i, nsl-1); the end segments
-        // (i = 0 and i = ns) see a single sample
-        T4 sq = sp;                      // s[min(i, nsl-1)]
-        T4 sn = li[min(1, nsl - 1)];     // s[min(i+1, nsl-1)], prefetched
-        for (int i = 0; i < nsteps; ++i) {
-            const T dr = T(0.5) * (sp.x + sq.x), di = T(0.5) * (sp.y + sq.y);
-            const T av = T(0.5) * (sp.z + sq.z);
-            const T ell = (i == 0) ? lead : (i == ns ? tail : h);
-            const T d2 = dr * dr + di * di;
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                StepCoef<T> c;
-                step_coef<T>(dr, di, d2, zr0[e] + av, zi[e], ell, c);
-                step_apply<T>(c, g[e]);
-            }
-            if (i < ns) {
-                C *dst = slab + (int64_t)i * ne_pad + r;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) dst[Lw * e] = g[e];
-            }
-            sp = sq;
-            sq = sn;
-            sn = li[min(i + 2, nsl - 1)];
-        }
-        if (lv) {
-#pragma unroll
-            for (int e = 0; e < EPT; ++e)
-                if (ev[e]) exit_cur[(int64_t)ln.exit_f * n_e + nid[e]] = g[e];
-        }
-
-        __syncwarp();  // parked gammas of other lanes are read in retarded mode
-
-        // ---------------- backward: angle p + P, along -e_par ----------------
-        // (a -> -a; samples visited nsl-1 ... 0)
-        T4 sh = li[nsl - 1];
-        if (a.first_sweep) {
-            const T d2 = sh.x * sh.x + sh.y * sh.y;
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                StepCoef<T> c;
-                step_coef<T>(sh.x, sh.y, d2, zr0[e] - sh.z, zi[e], tail, c);
-                g[e] = c.gh;
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                T gx = 0, gy = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const C v = exit_prev[(int64_t)ln.tap_b[q] * n_e + nid[e]];
-                    const T w = (T)ln.w_b[q];
-                    gx += w * v.x;
-                    gy += w * v.y;
-                }
-                g[e].x = gx;
-                g[e].y = gy;
-            }
-        }
-        // backward segment j joins samples min(nsl-j, nsl-1) and max(nsl-1-j, 0)
-        T4 slo = sh;                     // s[max(nsl-1-j, 0)] = sample reached (j < ns)
-        T4 snb = li[max(nsl - 2, 0)];    // prefetched s[max(nsl-2-j, 0)]
-        for (int j = 0; j < nmax; ++j) {
-            const bool act = j < nsteps;
-            const int qs = nsl - 1 - j;          // sample reached after this step
-            const bool comb = act && j < ns;     // a sample to combine at
-            C gf[EPT];
-            if (comb) {
-                const C *src = slab + (int64_t)qs * ne_pad;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) gf[e] = src[RET ? mir[e] : (r + Lw * e)];
-            }
-            if (act) {
-                const T dr = T(0.5) * (sh.x + slo.x), di = T(0.5) * (sh.y + slo.y);
-                const T av = T(0.5) * (sh.z + slo.z);
-                const T ell = (j == 0) ? tail : (j == ns ? lead : h);
-                const T d2 = dr * dr + di * di;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    StepCoef<T> c;
-                    step_coef<T>(dr, di, d2, zr0[e] - av, zi[e], ell, c);
-                    step_apply<T>(c, g[e]);
-                }
-            }
-            if (!RET) {
-                // propagator of angle p from gamma = gf, gamma~ = conj(g):
-                //   D = 1 + gf conj(g);  f + conj f~ = -2 i pi (gf/D + g/conj D)
-                //   2 Re g = 4 pi Im(1/D);  2 Re I = 2 Im(conj(Delta)(gf + g))
-                T sfr = 0, sfi = 0, sg = 0, sFr = 0, sFi = 0;
-                if (comb) {
-#pragma unroll
-                    for (int e = 0; e < EPT; ++e) {
-                        if (!ev[e]) continue;
-                        const C gb = g[e], ga = gf[e];
-                        const T pr = ga.x * gb.x + ga.y * gb.y;   // ga * conj(gb)
-                        const T pi_ = ga.y * gb.x - ga.x * gb.y;
-                        const T Dr = T(1) + pr, Di = pi_;
-                        const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
-                        const T ir = Dr * rD, ii = -Di * rD;      // 1/D
-                        sg += ii;
-                        // ga/D + gb conj(1/D)
-                        sfr += (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
-                        sfi += (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
-                        sFr += ga.x + gb.x;
-                        sFi += ga.y + gb.y;
-                    }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    if (off >= Lw) continue;
-                    sfr += __shfl_xor_sync(FULL_MASK, sfr, off);
-                    sfi += __shfl_xor_sync(FULL_MASK, sfi, off);
-                    sg += __shfl_xor_sync(FULL_MASK, sg, off);
-                    sFr += __shfl_xor_sync(FULL_MASK, sFr, off);
-                    sFi += __shfl_xor_sync(FULL_MASK, sFi, off);
-                }
-                if (comb && r == 0) {
-                    const T twopi = T(6.283185307179586), fourpi = T(12.566370614359172);
-                    T4 o;
-                    o.x = twopi * sfi;                          // Re Sf
-                    o.y = -twopi * sfr;                         // Im Sf
-                    o.z = fourpi * sg;                          // Sg
-                    o.w = T(2) * (slo.x * sFi - slo.y * sFr);   // SF
-                    ((T4 *)gs.image_out)[slot0 + qs] = o;
-                }
-            } else if (comb) {
-                // LDOS: -Im g / pi = Re[(1 - p)/(1 + p)] = 2 Re(1/D) - 1
-                T *outl = (T *)gs.image_out + (int64_t)(slot0 + qs) * n_e;
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    if (!ev[e]) continue;
-                    const C gb = g[e], ga = gf[e];
-                    const T pr = ga.x * gb.x + ga.y * gb.y;
-                    const T pi_ = ga.y * gb.x - ga.x * gb.y;
-                    const T Dr = T(1) + pr, Di = pi_;
-                    const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
-                    outl[nid[e]] = T(2) * Dr * rD - T(1);
-                }
-            }
-            if (act) {
-                sh = slo;
-                slo = snb;
-                snb = li[max(nsl - 3 - j, 0)];
-            }
-        }
-        if (lv) {
-#pragma unroll
-            for (int e = 0; e < EPT; ++e)
-                if (ev[e]) exit_cur[(int64_t)ln.exit_b * n_e + nid[e]] = g[e];
-        }
-        __syncwarp();  // the slab is rewritten by the next item
-    }
-}
-
-template <typename T, int EPT, bool RET>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1) sweep_kernel(SweepLaunch a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Cx<T> *const warp_slab = (Cx<T> *)a.scratch + wid * a.scratch_stride;
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1);
-        item = __shfl_sync(FULL_MASK, item, 0);
-        if (item >= a.n_items) break;
-        const int2 it = a.items[item];
-        sweep_item<T, EPT, RET>(a, it, a.grains[it.x], warp_slab, lane);
-    }
-}
-
-template <typename T, bool RET>
-static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
-    dim3 grid(a.grid_blocks), block(a.block_threads);
-    switch (a.energies_per_lane) {
-#define SC_CASE(E) \
-    case E: sweep_kernel<T, E, RET><<<grid, block, 0, st>>>(a); break;
-        SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
-#undef SC_CASE
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
+// The sweep kernels are instantiated per precision in sweep_f32.cu / sweep_f64.cu.
 cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t st) {
-    if (fp64) return a.retarded ? sweep_dispatch<double, true>(a, st) : sweep_dispatch<double, false>(a, st);
-    return a.retarded ? sweep_dispatch<float, true>(a, st) : sweep_dispatch<float, false>(a, st);
+    return fp64 ? launch_sweep_f64(a, st) : launch_sweep_f32(a, st);
 }
 
-template <typename T, bool RET>
-static int occ_dispatch(int ept, int bs) {
-    int n = 0;
-    switch (ept) {
-#define SC_CASE(E) \
-    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET>, bs, 0); break;
-        SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
-#undef SC_CASE
-        default: n = 0;
-    }
-    return n;
-}
-
-int sweep_occupancy(bool fp64, int ept, int bs) {
-    // the larger of the Matsubara and retarded instantiations bounds both
-    const int a = fp64 ? occ_dispatch<double, false>(ept, bs) : occ_dispatch<float, false>(ept, bs);
-    const int b = fp64 ? occ_dispatch<double, true>(ept, bs) : occ_dispatch<float, true>(ept, bs);
-    return a < b ? a : b;
+int sweep_occupancy(bool fp64, int ept, int bs, int stepper) {
+    return fp64 ? sweep_occupancy_f64(ept, bs, stepper) : sweep_occupancy_f32(ept, bs, stepper);
 }
 
 // ---------------------------------------------------------------------------

@@ -101,6 +101,8 @@ struct SweepLaunch {
     int32_t parity;            // which exit buffer holds the previous sweep's values
     int32_t retarded;          // LDOS mode
     int32_t grid_blocks, block_threads;
+    int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
+    int32_t pad;
 };
 
 // launchers (return cudaError_t)
@@ -119,7 +121,12 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
                                    const GridDev &grid, const uint8_t *mask, const float4 *image_out,
                                    double *acc, cudaStream_t s);
-int sweep_occupancy(bool fp64, int ept, int block_threads);
+int sweep_occupancy(bool fp64, int ept, int block_threads, int stepper);
+// per-precision instantiations (sweep_f32.cu, sweep_f64.cu)
+cudaError_t launch_sweep_f32(const SweepLaunch &a, cudaStream_t s);
+cudaError_t launch_sweep_f64(const SweepLaunch &a, cudaStream_t s);
+int sweep_occupancy_f32(int ept, int block_threads, int stepper);
+int sweep_occupancy_f64(int ept, int block_threads, int stepper);
 cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
                                const BackLine *bl, const GridDev &grid, const uint8_t *mask,
                                const void *image_out, double *acc, cudaStream_t s);

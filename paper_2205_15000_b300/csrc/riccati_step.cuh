@@ -351,4 +351,81 @@ __host__ __device__ __forceinline__ void mob_grad(const MobCoef<T> &m, T dr, T d
     G.dQ = C{-sQ.x - cA.y, -sQ.y + cA.x};
 }
 
+// ---------------------------------------------------------------------------
+// Implicit midpoint rule (App. C, Eq. riccati_midpoint):
+//   g1 = g0 + ell f((g0 + g1)/2),   f(g) = i (Delta* g^2 + 2 z g + Delta),
+// a quadratic c2 g1^2 + c1 g1 + c0 = 0 with c2 = i ell Delta*/4,
+// c1 = 2 c2 g0 + i ell z - 1, c0 = (c1 - c2 g0 + 2) g0 + i ell Delta, whose root
+// continuous in Delta is g1 = 2 c0/(-c1 + sqrt(c1^2 - 4 c2 c0)) (principal root;
+// Re c1 < 0 for ell |Delta| < 2, so the denominator stays near 2).
+// The per-segment factors c2 and i ell Delta are shared by all energies.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MidSeg {
+    Cx<T> c2;   // i ell Delta*/4
+    Cx<T> ild;  // i ell Delta
+    T ell;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ MidSeg<T> mid_seg(T dr, T di, T ell) {
+    const T q = T(0.25) * ell;
+    return MidSeg<T>{Cx<T>{q * di, q * dr}, Cx<T>{-ell * di, ell * dr}, ell};
+}
+
+// principal square root of x + i y (Re >= 0), the branch logic of the step's Omega
+template <typename T>
+__host__ __device__ __forceinline__ Cx<T> csqrt_principal(T x, T y) {
+    typedef Mth<T> M;
+    using ::copysign;
+    using ::fabs;
+    const T r = M::sqrt(x * x + y * y);
+    const T hs = T(0.5) * (r + fabs(x));
+    const T q = M::rsqrt(hs);
+    const T s = hs * q;
+    const T yq = T(0.5) * y * q;
+    if (x >= T(0)) return Cx<T>{s, yq};
+    return Cx<T>{fabs(yq), copysign(s, y)};
+}
+
+template <typename T>
+__host__ __device__ __forceinline__ Cx<T> midpoint_step(const MidSeg<T> &sg, T zr, T zi, Cx<T> g) {
+    const Cx<T> c2g = cmul(sg.c2, g);
+    const T lzr = sg.ell * zr, lzi = sg.ell * zi;
+    // c1 = 2 c2 g + i ell z - 1;  c1 - c2 g + 2 = c2 g + i ell z + 1
+    const Cx<T> c1{T(2) * c2g.x - lzi - T(1), T(2) * c2g.y + lzr};
+    const Cx<T> u{c2g.x - lzi + T(1), c2g.y + lzr};
+    const Cx<T> ug = cmul(u, g);
+    const Cx<T> c0{ug.x + sg.ild.x, ug.y + sg.ild.y};
+    const Cx<T> cc = cmul(sg.c2, c0);
+    const Cx<T> dsc{c1.x * c1.x - c1.y * c1.y - T(4) * cc.x, T(2) * c1.x * c1.y - T(4) * cc.y};
+    const Cx<T> sq = csqrt_principal<T>(dsc.x, dsc.y);
+    const Cx<T> iden = crcp(Cx<T>{sq.x - c1.x, sq.y - c1.y});
+    const Cx<T> r = cmul(c0, iden);
+    return Cx<T>{T(2) * r.x, T(2) * r.y};
+}
+
+// Derivatives of the midpoint step g1 = Phi(g0; P = Delta*, Q = z, R = Delta)
+// by implicit differentiation of g1 = g0 + ell f(m), m = (g0 + g1)/2:
+//   (1 - ell f'/2) dg1 = (1 + ell f'/2) dg0 + ell (f_P dP + f_Q dQ + f_R dR),
+//   f' = i (2 P m + 2 Q), f_P = i m^2, f_Q = 2 i m, f_R = i.
+template <typename T>
+__host__ __device__ __forceinline__ void midpoint_grad(const MidSeg<T> &sg, T dr, T di, T zr, T zi, Cx<T> g0,
+                                                       StepGrad<T> &G) {
+    typedef Cx<T> C;
+    const C g1 = midpoint_step<T>(sg, zr, zi, g0);
+    const C m{T(0.5) * (g0.x + g1.x), T(0.5) * (g0.y + g1.y)};
+    // h = ell f'/2 = i ell (Delta* m + z)
+    const C pm = cmul(C{dr, -di}, m);
+    const C h{-sg.ell * (pm.y + zi), sg.ell * (pm.x + zr)};
+    const C w = crcp(C{T(1) - h.x, -h.y});   // 1/(1 - ell f'/2)
+    G.dg = cmul(C{T(1) + h.x, h.y}, w);
+    const C lw{sg.ell * w.x, sg.ell * w.y};  // ell/(1 - ell f'/2)
+    G.dR = C{-lw.y, lw.x};                   // i ell w
+    const C mlw = cmul(m, lw);
+    G.dQ = C{T(-2) * mlw.y, T(2) * mlw.x};    // 2 i m ell w
+    const C m2lw = cmul(m, mlw);
+    G.dP = C{-m2lw.y, m2lw.x};                // i m^2 ell w
+}
+
 }  // namespace scd

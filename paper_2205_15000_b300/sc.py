@@ -18,6 +18,9 @@ SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ETIMEOUT, SC_ENUMERIC, SC_ESTATE, SC_E
 STATUS_NAMES = ["SC_OK", "SC_EINVAL", "SC_ENOMEM", "SC_ECUDA", "SC_ETIMEOUT", "SC_ENUMERIC",
                 "SC_ESTATE", "SC_ENOTCONV"]
 SC_PREC_FP64, SC_PREC_FP32 = 0, 1
+# sc_stepper: integrator of the Riccati equation along a line (App. C)
+SC_STEP_CLOSED, SC_STEP_MIDPOINT = 0, 1
+STEPPERS = {"closed": SC_STEP_CLOSED, "midpoint": SC_STEP_MIDPOINT}
 
 
 class ScError(RuntimeError):
@@ -42,6 +45,7 @@ class sc_params(ctypes.Structure):
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
         ("precision", ctypes.c_int32), ("lanes_per_line", ctypes.c_int32),
         ("host_only", ctypes.c_int32), ("record_timings", ctypes.c_int32),
+        ("stepper", ctypes.c_int32),
     ]
 
 
@@ -187,6 +191,7 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
     p.lanes_per_line = lanes_per_line
     p.host_only = 1 if host_only else 0
     p.record_timings = 1 if record_timings else 0
+    p.stepper = STEPPERS[d.get("stepper", "closed")]
     return p
 
 

@@ -47,6 +47,21 @@ def test_invalid_params_rejected(bad):
     assert ei.value.status == sc.SC_EINVAL
 
 
+def test_stepper_validated_and_default_closed():
+    """sc_params.stepper: 0 (closed form, the default) or 1 (implicit midpoint);
+    anything else is SC_EINVAL."""
+    assert sc.sc_params_default().stepper == sc.SC_STEP_CLOSED
+    p = W.disc(5.0, 32, n_angles=8, n_energies=2)
+    q = sc.make_params(dict(p, stepper="midpoint"), host_only=True)
+    assert q.stepper == sc.SC_STEP_MIDPOINT
+    h = sc.sc_create(q)
+    sc.sc_destroy(h)
+    q.stepper = 2
+    with pytest.raises(sc.ScError) as ei:
+        sc.sc_create(q)
+    assert ei.value.status == sc.SC_EINVAL
+
+
 def test_nonconvex_polygon_rejected():
     p = W.polygon([0.0, 4.0, 2.0, 4.0, 0.0], [0.0, 0.0, 1.0, 4.0, 4.0], 0.25, n_angles=8, n_energies=2)
     with pytest.raises(sc.ScError) as ei:

@@ -51,6 +51,29 @@ def test_batch_equals_single_contexts(precision, tol, ept):
     b.close()
 
 
+def test_batch_midpoint_equals_single_contexts():
+    """A batch with the implicit-midpoint stepper gives what each member's own
+    context gives (FP64)."""
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    prms = [dict(p, stepper="midpoint") for p, _ in grains]
+    b = sc.Batch(prms, precision="fp64", energies_per_lane=8)
+    singles = [sc.Context(p, precision="fp64") for p in prms]
+    for (_, d), m, s in zip(grains, b.members, singles):
+        m.set_fields(d)
+        s.set_fields(d)
+    for it in range(2):
+        b.sweep()
+        for s in singles:
+            s.sweep()
+        for m, s in zip(b.members, singles):
+            rm, rs = _outputs(m), _outputs(s)
+            for k in ("delta_new", "j", "F"):
+                scale = max(np.max(np.abs(rs[k])), 1e-3)
+                assert np.max(np.abs(rm[k] - rs[k])) <= 1e-12 * scale, (it, k)
+    b.close()
+
+
 def test_batch_member_matches_oracle_fp64():
     from paper_2205_15000_b300 import sc
     grains = _grains()

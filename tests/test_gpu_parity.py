@@ -89,9 +89,11 @@ def _oracle_pair_images(g, o_images):
     return o_images[: g.n_samples_all // 2]
 
 
+@pytest.mark.parametrize("stepper", ["closed", "midpoint"])
 @pytest.mark.parametrize("name", CASES)
-def test_fp64_sweep_matches_oracle(name):
+def test_fp64_sweep_matches_oracle(name, stepper):
     p, delta, aind = case(name)
+    p["stepper"] = stepper
     g, ctx, m, res = _run_both(p, delta, aind, "fp64")
     for it, R in enumerate(res):
         o, r = R["o"], R["r"]
@@ -104,9 +106,11 @@ def test_fp64_sweep_matches_oracle(name):
         assert abs(r["eps_G"] - o["eps_G"]) < 1e-9
 
 
+@pytest.mark.parametrize("stepper", ["closed", "midpoint"])
 @pytest.mark.parametrize("name", CASES)
-def test_fp32_sweep_within_tolerance(name):
+def test_fp32_sweep_within_tolerance(name, stepper):
     p, delta, aind = case(name)
+    p["stepper"] = stepper
     g, ctx, m, res = _run_both(p, delta, aind, "fp32")
     for R in res:
         o, r = R["o"], R["r"]
@@ -151,10 +155,12 @@ def test_picard_with_vector_potential_matches_oracle():
     assert abs(r["F_total"] - o["F_total"]) < 1e-10
 
 
+@pytest.mark.parametrize("stepper", ["closed", "midpoint"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
-def test_ldos_matches_oracle(precision, tol):
+def test_ldos_matches_oracle(precision, tol, stepper):
     sc = _sc()
     p = W.diamond(8.0, 32, pairing=1, t=0.5, n_angles=16, n_energies=1)
+    p["stepper"] = stepper
     d = W.noisy_delta(p, 0.22, 0.05, seed=21)
     e = np.linspace(-0.3, 0.3, 8)
     g = oracle.OracleGeom(p)
