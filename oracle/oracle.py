@@ -326,6 +326,31 @@ class OracleGeom:
                 aind = self.vector_potential(out["j"])
         return dict(delta=delta, aind=aind, history=np.array(hist), last=out, exit=exit_in)
 
+    def self_consistency(self, delta0, n_iter, params, aind0=None):
+        """Alg. suprcon with an accelerator of App. E (oracle/accel.py): each
+        iteration sweeps with the current (Delta, A_ind), forms g(x) =
+        (Delta_new, kappa^2 A from j) and takes the accelerator's step; boundary
+        values are carried over."""
+        from . import accel
+        kappa = self.prm["kappa"]
+        use_a = kappa > 0 and math.isfinite(kappa)
+        delta = np.array(delta0, dtype=np.complex128)
+        aind = np.zeros((self.ny, self.nx, 2)) if use_a and aind0 is None else (
+            None if aind0 is None else np.array(aind0, np.float64))
+        m = self.mask().astype(bool)
+        acc = accel.Accelerator(params)
+        ex = None
+        hist = []
+        for _ in range(n_iter):
+            out = self.full_sweep(delta, aind, ex)
+            ex = out["exit"]
+            hist.append(out["eps_G"])
+            a_new = self.vector_potential(out["j"]) if use_a else None
+            x = accel.pack(delta, aind, m, kappa)
+            g = accel.pack(out["delta_new"], a_new, m, kappa)
+            delta, aind = accel.unpack(acc.step(x, g), delta, aind, m, kappa)
+        return dict(delta=delta, aind=aind, history=np.array(hist), exit=ex, accelerator=acc)
+
     def ldos(self, delta, aind, energies, broadening, n_burnin=20, tol=1e-10):
         """LDOS N(R, eps)/N_F = -<Im g^R>/pi (Sec. 2) at eps + i*broadening,
         boundary values burnt in with Delta, A frozen."""
