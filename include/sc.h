@@ -168,6 +168,52 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream);
    A_ind <- from j (when kappa > 0). */
 sc_status sc_picard_step(sc_ctx *ctx, void *stream);
 
+/* ---- self-consistency accelerators (App. E) ----------------------------
+   The unknowns x = (Re Delta, Im Delta, kappa^2 A_x, kappa^2 A_y) (Eq. x_concat):
+   Delta over the grain's grid points, A_ind over the whole grid (only when
+   kappa > 0 is finite).  g(x) = (Delta_new, kappa^2 A from j) of the last sweep,
+   d = g(x) - x (Eq. difference).  Each call of sc_accelerate takes one step:
+     PICARD            x += alpha d                                  (Eq. picard)
+     POLYAK            v = (1 - beta) v + alpha d, x += v; v starts at 0
+     BARZILAI_BORWEIN  alpha *= BB1 (odd iterations) or BB2 (even), clamped to
+                       [step_size_min, step_size_max]; x += alpha d; the first
+                       iteration uses alpha = step_size
+     CONGACC           per component c: s = cos(m_c, d_c); alpha_c *= k^s
+                       (clamped); w_c = w* with cos(w* m_c + (1-w*) d_c, d_c) =
+                       s_min when s < s_min; m_c = w_c m_c + (1 - w_c) d_c;
+                       x_c += alpha_c m_c; the first iteration takes m_c = d_c
+   The history (velocity, previous d, moving averages, step sizes) lives in the
+   context; it restarts when the kind changes, after sc_set_fields and after
+   sc_accel_reset.  BB and CongAcc read dot products back to the host, so their
+   steps synchronise the stream. */
+typedef enum {
+    SC_ACC_PICARD = 0,
+    SC_ACC_POLYAK = 1,
+    SC_ACC_BARZILAI_BORWEIN = 2,
+    SC_ACC_CONGACC = 3
+} sc_accel_kind;
+
+typedef struct {
+    int32_t kind;               /* sc_accel_kind */
+    double step_size;           /* alpha (Picard, Polyak); initial alpha (BB, CongAcc); > 0 */
+    double drag;                /* Polyak beta, 0 < beta <= 1 */
+    double step_size_factor;    /* CongAcc k > 0 */
+    double cos_similarity_min;  /* CongAcc s_min in [-1, 1] */
+    double step_size_max, step_size_min;  /* BB and CongAcc clamps, 0 < min <= max */
+} sc_accel_params;
+
+/* The paper's listing defaults for `kind`: Picard 1.0; Polyak 2.0, drag 0.5;
+   BB 1.0 in [0.001, 100]; CongAcc 0.5, k = 1.234, s_min = 0.7, [0.001, 100]. */
+sc_status sc_accel_params_default(int32_t kind, sc_accel_params *p);
+/* One accelerator step after a sweep; Delta and A_ind of the context are
+   replaced by x_{i+1} (the next sweep reads them). */
+sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream);
+sc_status sc_accel_reset(sc_ctx *ctx);
+/* Accelerator history: steps taken, step sizes (BB/Picard/Polyak: alpha in
+   [0]; CongAcc: alpha_c for c = Re Delta, Im Delta, A_x, A_y) and CongAcc's
+   weights w_c; alpha and w may be NULL. */
+sc_status sc_accel_get_state(const sc_ctx *ctx, int32_t *iterations, double *alpha, double *w);
+
 /* Local density of states N(R, eps)/N_F = -<Im g^R(eps + i broadening)>/pi
    (Sec. 2).  energies: host array of n_e real energies that must be symmetric
    about zero (eps_k = -eps_{n_e-1-k}), because gamma~ at eps is taken from

@@ -270,7 +270,7 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     return SC_OK;
 }
 
-sc_status ensure_outputs(sc_ctx *ctx, cudaStream_t st) {
+sc_status ensure_outputs_impl(sc_ctx *ctx, cudaStream_t st) {
     if (!ctx->have_sweep) return set_err(ctx, SC_ESTATE, "no sweep since the fields were last set");
     if (ctx->have_outputs) return SC_OK;
     const double kappa = ctx->geo.prm.kappa;
@@ -290,6 +290,10 @@ sc_status copy_out(sc_ctx *ctx, void *dst, const void *src, size_t bytes, int on
 }
 
 }  // namespace
+
+namespace sc_internal {
+sc_status ensure_outputs(sc_ctx *ctx, cudaStream_t st) { return ensure_outputs_impl(ctx, st); }
+}  // namespace sc_internal
 
 extern "C" {
 
@@ -682,6 +686,7 @@ sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, i
     if (!on_device) CK(cudaStreamSynchronize(st));
     ctx->have_sweep = false;
     ctx->have_outputs = false;
+    ctx->acc_kind = -1;  // new fields start a new accelerator history
     return SC_OK;
 }
 
@@ -734,7 +739,7 @@ sc_status sc_burnin(sc_ctx *ctx, int32_t max_sweeps, double tol, void *stream) {
 sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_device, void *stream) {
     CKS(check_ctx(ctx));
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure_outputs(ctx, st));
+    CKS(ensure_outputs_impl(ctx, st));
     CKS(copy_out(ctx, delta_out, ctx->d_dnew, 2 * npts(ctx) * sizeof(double), on_device, st));
     if (eps_G) {
         double s[4];
@@ -749,14 +754,14 @@ sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_de
 sc_status sc_current(sc_ctx *ctx, double *j_out, int on_device, void *stream) {
     CKS(check_ctx(ctx));
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure_outputs(ctx, st));
+    CKS(ensure_outputs_impl(ctx, st));
     return copy_out(ctx, j_out, ctx->d_j, 2 * npts(ctx) * sizeof(double), on_device, st);
 }
 
 sc_status sc_free_energy(sc_ctx *ctx, double *F_total, double *density_out, int on_device, void *stream) {
     CKS(check_ctx(ctx));
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure_outputs(ctx, st));
+    CKS(ensure_outputs_impl(ctx, st));
     CKS(copy_out(ctx, density_out, ctx->d_F, npts(ctx) * sizeof(double), on_device, st));
     if (F_total) {
         double s[4];
@@ -772,7 +777,7 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream) {
     CKS(check_ctx(ctx));
     if (!ctx->d_G) return SC_OK;  // kappa <= 0: no induced field
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure_outputs(ctx, st));
+    CKS(ensure_outputs_impl(ctx, st));
     CK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, st));
     const double k = ctx->geo.prm.kappa;
     CK(scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in, ctx->d_G,
@@ -784,7 +789,7 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream) {
 sc_status sc_picard_step(sc_ctx *ctx, void *stream) {
     CKS(check_ctx(ctx));
     cudaStream_t st = (cudaStream_t)stream;
-    CKS(ensure_outputs(ctx, st));
+    CKS(ensure_outputs_impl(ctx, st));
     if (ctx->d_G) CKS(sc_update_vector_potential(ctx, stream));
     CK(scd::launch_copy_delta(2 * (int64_t)npts(ctx), ctx->d_dnew, ctx->d_delta, st));
     ctx->have_sweep = false;

@@ -79,6 +79,12 @@ struct sc_ctx {
     double *d_gacc = nullptr, *d_gdelta = nullptr, *d_gaind = nullptr, *d_gin = nullptr;
     void *d_wimg = nullptr, *d_gimg = nullptr, *d_adj_scratch = nullptr;
     size_t adj_scratch_bytes = 0;
+    // self-consistency accelerator (App. E), buffers allocated on first use
+    double *d_anew = nullptr, *d_acc_v = nullptr, *d_acc_prev = nullptr, *d_acc_m = nullptr;
+    double *d_acc_part = nullptr, *d_acc_sums = nullptr;
+    int acc_kind = -1;  // kind of the running history; -1: none (next call starts one)
+    long acc_iter = 0;
+    double acc_alpha = 0.0, acc_alpha_c[4] = {0, 0, 0, 0}, acc_w_c[4] = {0, 0, 0, 0};
     std::string err;
     std::vector<void *> allocs;
 };
@@ -96,5 +102,7 @@ sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st);
 // FS average of the context's image into its accumulators (rotate-back kernels)
 sc_status rotate_back(sc_ctx *ctx, cudaStream_t st);
 sc_status check_ctx(sc_ctx *ctx);
+// Delta_new, j, F of the last sweep on the device (outputs kernel, once per sweep)
+sc_status ensure_outputs(sc_ctx *ctx, cudaStream_t st);
 void set_thread_error(const char *msg);
 }  // namespace sc_internal

@@ -28,6 +28,9 @@ namespace scd {
 #ifndef SC_SWEEP_MIN_BLOCKS
 #define SC_SWEEP_MIN_BLOCKS 5  // FP32: 5 blocks of 128 threads per SM (at most 102 registers)
 #endif
+#ifndef SC_SWEEP_MIN_BLOCKS_MID
+#define SC_SWEEP_MIN_BLOCKS_MID 5  // FP32 implicit-midpoint instantiations
+#endif
 
 // One work item: the G lines of group it.y of grain gs, EPT energies per lane;
 // STEP 0 = closed-form step, 1 = implicit midpoint rule.
@@ -272,7 +275,8 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
 }
 
 template <typename T, int EPT, bool RET, int STEP>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_SWEEP_MIN_BLOCKS : 1) sweep_kernel(SweepLaunch a) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS) : 1)
+    sweep_kernel(SweepLaunch a) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Cx<T> *const warp_slab = (Cx<T> *)a.scratch + wid * a.scratch_stride;

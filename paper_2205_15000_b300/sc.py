@@ -71,13 +71,27 @@ class sc_info(ctypes.Structure):
     ]
 
 
+class sc_accel_params(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("step_size", ctypes.c_double), ("drag", ctypes.c_double),
+        ("step_size_factor", ctypes.c_double), ("cos_similarity_min", ctypes.c_double),
+        ("step_size_max", ctypes.c_double), ("step_size_min", ctypes.c_double),
+    ]
+
+
+# sc_accel_kind (App. E)
+SC_ACC_PICARD, SC_ACC_POLYAK, SC_ACC_BARZILAI_BORWEIN, SC_ACC_CONGACC = 0, 1, 2, 3
+ACCELERATORS = {"picard": SC_ACC_PICARD, "polyak": SC_ACC_POLYAK,
+                "barzilai-borwein": SC_ACC_BARZILAI_BORWEIN, "congacc": SC_ACC_CONGACC}
+
 # every symbol include/sc.h declares
 EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_get_mask",
             "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
-            "sc_ldos_adjoint",
+            "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
+            "sc_accel_get_state",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
@@ -113,6 +127,10 @@ def _load():
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
+        "sc_accel_params_default": [i32, P(sc_accel_params)],
+        "sc_accelerate": [vp, P(sc_accel_params), vp],
+        "sc_accel_reset": [vp],
+        "sc_accel_get_state": [vp, P(i32), vp, vp],
         "sc_batch_create": [vp, i32, i32, P(vp)],
         "sc_batch_destroy": [vp],
         "sc_batch_member": [vp, i32, P(vp)],
@@ -254,6 +272,37 @@ def sc_update_vector_potential(ctx, stream=None):
 
 def sc_picard_step(ctx, stream=None):
     _check(lib.sc_picard_step(ctx, _stream(stream)), ctx)
+
+
+def sc_accel_params_default(kind):
+    p = sc_accel_params()
+    _check(lib.sc_accel_params_default(int(ACCELERATORS.get(kind, kind)), ctypes.byref(p)))
+    return p
+
+
+def accel_params(name, **overrides):
+    """sc_accel_params with the paper's defaults for accelerator `name` and any
+    overrides (fields of sc_accel_params)."""
+    p = sc_accel_params_default(name)
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def sc_accelerate(ctx, params, stream=None):
+    _check(lib.sc_accelerate(ctx, ctypes.byref(params), _stream(stream)), ctx)
+
+
+def sc_accel_reset(ctx):
+    _check(lib.sc_accel_reset(ctx), ctx)
+
+
+def sc_accel_get_state(ctx):
+    it = ctypes.c_int32(0)
+    a = np.zeros(4)
+    w = np.zeros(4)
+    _check(lib.sc_accel_get_state(ctx, ctypes.byref(it), _ptr(a), _ptr(w)), ctx)
+    return it.value, a, w
 
 
 def sc_ldos(ctx, energies, broadening, n_burnin, ldos_out, on_device=True, stream=None):
@@ -479,6 +528,10 @@ class Context:
         da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
         sc_ldos_adjoint(self.h, energies, broadening, n_burnin, g, dd, da, True, stream)
         return torch.view_as_complex(dd), da
+
+    def accelerate(self, params, stream=None):
+        """One accelerator step (App. E) after a sweep: params from accel_params()."""
+        sc_accelerate(self.h, params, stream)
 
     def ldos(self, energies, broadening, n_burnin=20, stream=None):
         import torch

@@ -1,0 +1,119 @@
+"""Self-consistency accelerators (App. E) through the C ABI: the loop of
+Alg. suprcon with each accelerator against the oracle's loop (FP64, same
+seeded inputs), parameter validation, and iterations to convergence on a
+small-penetration-depth disc with a vortex."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import accel as oaccel
+from paper_2205_15000_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+KINDS = ["picard", "polyak", "barzilai-borwein", "congacc"]
+
+
+def _grain():
+    p = W.disc(4.0, 24, pairing=1, t=0.4, n_angles=12, n_energies=6, flux_quanta=1.2, kappa=3.0)
+    d0 = W.vortex_delta(p, 0.22, [(0.6, -0.3)], [-1], seed=51, rel_noise=0.05)
+    return p, d0
+
+
+def _gpu_loop(p, d0, kind, n_iter, precision="fp64"):
+    import torch
+    from paper_2205_15000_b300 import sc
+    ctx = sc.Context(p, precision=precision)
+    ctx.set_fields(d0)
+    prm = sc.accel_params(kind)
+    hist = []
+    for _ in range(n_iter):
+        ctx.sweep()
+        eps = ctypes_eps(sc, ctx)
+        hist.append(eps)
+        ctx.accelerate(prm)
+    torch.cuda.synchronize()
+    return ctx, np.array(hist)
+
+
+def ctypes_eps(sc, ctx):
+    import ctypes
+    eps = ctypes.c_double(0.0)
+    sc._check(sc.lib.sc_gap_update(ctx.h, None, ctypes.byref(eps), 1, None), ctx.h)
+    return eps.value
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_accelerated_loop_matches_oracle(kind):
+    """Six iterations of sweep + accelerator step: the residual history and the
+    final Delta_new, j of a seventh sweep agree with the oracle to 1e-10."""
+    from paper_2205_15000_b300 import sc
+    p, d0 = _grain()
+    n_iter = 6
+    g = oracle.OracleGeom(p)
+    ref = g.self_consistency(d0, n_iter, oaccel.default_params(kind))
+    ctx, hist = _gpu_loop(p, d0, kind, n_iter)
+    np.testing.assert_allclose(hist, ref["history"], rtol=1e-9, atol=1e-12)
+    # one more sweep from the accelerated fields on both sides
+    ctx.sweep()
+    r = ctx.outputs()
+    o = g.full_sweep(ref["delta"], ref["aind"], ref["exit"])
+    m = g.mask().astype(bool)
+    np.testing.assert_allclose(r["delta_new"].cpu().numpy()[m], o["delta_new"][m], atol=1e-10, rtol=0)
+    np.testing.assert_allclose(r["j"].cpu().numpy()[m], o["j"][m], atol=1e-10, rtol=0)
+    it, alpha, w = sc.sc_accel_get_state(ctx.h)
+    assert it == n_iter
+    acc = ref["accelerator"]
+    if kind == "barzilai-borwein":
+        assert abs(alpha[0] - acc.alpha) <= 1e-9 * acc.alpha
+    if kind == "congacc":
+        np.testing.assert_allclose(alpha, acc.alpha_c, rtol=1e-9)
+        np.testing.assert_allclose(w, acc.w_c, rtol=1e-8, atol=1e-12)
+
+
+def test_accelerator_parameters_validated():
+    from paper_2205_15000_b300 import sc
+    p, d0 = _grain()
+    ctx = sc.Context(p, precision="fp32")
+    ctx.set_fields(d0)
+    with pytest.raises(sc.ScError) as ei:  # no sweep yet
+        ctx.accelerate(sc.accel_params("picard"))
+    assert ei.value.status == sc.SC_ESTATE
+    ctx.sweep()
+    for bad in (dict(step_size=0.0), dict(drag=1.5), dict(step_size_min=0.0),
+                dict(step_size_max=1e-4), dict(cos_similarity_min=2.0), dict(kind=7)):
+        with pytest.raises(sc.ScError) as ei:
+            ctx.accelerate(sc.accel_params("congacc", **bad))
+        assert ei.value.status == sc.SC_EINVAL
+
+
+def _iterations_to_converge(p, d0, kind, tol=1e-5, max_iter=400):
+    from paper_2205_15000_b300 import sc
+    ctx = sc.Context(p, precision="fp32")
+    ctx.set_fields(d0)
+    prm = sc.accel_params(kind)
+    for i in range(max_iter):
+        ctx.sweep()
+        eps = ctypes_eps(sc, ctx)
+        if i > 0 and eps < tol:
+            return i
+        if not math.isfinite(eps) or eps > 1e3:
+            return None
+        ctx.accelerate(prm)
+    return None
+
+
+def test_adaptive_accelerators_converge_where_fixed_steps_struggle():
+    """A small penetration depth (kappa = 5) s-wave disc with a vortex, in the
+    spirit of example (g) of Table app:accelerator:table:comparison (smaller
+    grain): the adaptive methods (BB, CongAcc) reach eps_G < 1e-5, and faster
+    than Picard with its default step."""
+    p = W.disc(8.0, 64, pairing=0, t=0.5, n_angles=32, n_energies=16, flux_quanta=1.5, kappa=5.0)
+    d0 = W.vortex_delta(p, 0.24, [(0.0, 0.0)], [-1])
+    its = {k: _iterations_to_converge(p, d0, k) for k in KINDS}
+    print("iterations to eps_G < 1e-5:", its)
+    assert its["barzilai-borwein"] is not None and its["congacc"] is not None
+    for k in ("barzilai-borwein", "congacc"):
+        assert its["picard"] is None or its[k] < its["picard"]
