@@ -41,6 +41,7 @@ def lib():
         L.or_bulk_gap.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
         L.or_quad_weight.restype = ctypes.c_double
         L.or_quad_weight.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.or_geom_set_energy_weights.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -97,6 +98,36 @@ def quad_weight(k, n):
 STEPPERS = {"closed": 0, "midpoint": 1}
 
 
+def ozaki_poles(n):
+    """Ozaki's continued-fraction poles of the Fermi function (Ozaki, PRB 75,
+    035123 (2007); the energy sum of Sec. 3.1): the 2n x 2n symmetric
+    tridiagonal matrix with zero diagonal and off-diagonal 1/(2 sqrt((2m-1)(2m+1)))
+    has eigenvalues +-b_p; z_p = 1/b_p and R_p = v_p[0]^2/(4 b_p^2) give
+    1/(1 + e^x) = 1/2 - sum_p R_p [1/(x - i z_p) + 1/(x + i z_p)].
+    Returns z (ascending) and R."""
+    M = 2 * n
+    B = np.zeros((M, M))
+    m = np.arange(1, M)
+    off = 1.0 / (2.0 * np.sqrt((2 * m - 1.0) * (2 * m + 1.0)))
+    B[m - 1, m] = off
+    B[m, m - 1] = off
+    w, v = np.linalg.eigh(B)
+    pos = w > 0
+    b = w[pos]
+    z = 1.0 / b
+    R = v[0, pos] ** 2 / (4.0 * b * b)
+    o = np.argsort(z)
+    return z[o], R[o]
+
+
+def ozaki_energies(t, n):
+    """Positive energies (units of 2 pi kB Tc) and weights of the Ozaki sum:
+    T sum_n F(i eps_n) -> sum_p R_p T F(i T z_p) (+ the mirrored pole), so
+    eps_p = t z_p / (2 pi)."""
+    z, R = ozaki_poles(n)
+    return t * z / (2.0 * math.pi), R
+
+
 def step_midpoint(P, Q, R, ell, ga):
     """Implicit midpoint step (App. C, Eq. riccati_midpoint) of
     d gamma/ds = i (P gamma^2 + 2 Q gamma + R) over a length ell."""
@@ -149,6 +180,16 @@ class OracleGeom:
         self.nx, self.ny = prm["nx"], prm["ny"]
         self.N = prm["n_angles"]
         self.n_e = prm["n_energies"]
+        self.energy_sum = prm.get("energy_sum", "matsubara")
+        if self.energy_sum == "ozaki":
+            eps, w = ozaki_energies(prm["t"], self.n_e)
+            self._eps = eps
+            self._ewt = np.ascontiguousarray(w)
+            D = math.log(prm["t"]) + prm["t"] * float(np.sum(w / eps))
+            L.or_geom_set_energy_weights(self._h, _p(self._ewt), self.n_e, ctypes.c_double(D))
+            self.normD = D
+        elif self.energy_sum != "matsubara":
+            raise ValueError("energy_sum must be 'matsubara' or 'ozaki'")
 
     def __del__(self):
         try:
@@ -293,6 +334,10 @@ class OracleGeom:
 
     # ---- composed steps -------------------------------------------------
     def matsubara(self):
+        """The positive energies of the energy sums, times i: Matsubara
+        energies or Ozaki's poles."""
+        if self.energy_sum == "ozaki":
+            return 1j * self._eps
         return matsubara(self.prm["t"], self.n_e)
 
     def full_sweep(self, delta, aind=None, exit_in=None):

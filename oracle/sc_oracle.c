@@ -65,6 +65,8 @@ struct or_geom {
     double *w;              /* [N] quadrature weights */
     double *vh;             /* [N][2] Fermi velocity directions */
     double *eta;            /* [N] basis function */
+    double *ewt;            /* [n_energies] weights of the energy sums, NULL = 1 (Matsubara) */
+    double normD;           /* gap-equation normalisation when ewt is set */
     /* per pair */
     int *l_lo, *l_hi, *line_off, *samp_off; /* line_off/samp_off: [npair+1] */
     /* per line (pair-major) */
@@ -119,6 +121,18 @@ static double basis_eta(int pairing, double rot, double c, double s) {
 /* Normalisation of the fixed-point gap equation (Eq. gapeq_fixpoint), in
    units of 2 pi kB Tc with eps_n = t (n + 1/2):  ln t + pi T sum_n 1/|eps_n|
    = ln t + 2 sum_{n<Ne} 1/(2n+1). */
+int or_geom_set_energy_weights(or_geom *g, const double *w, int n_e, double normD) {
+    if (!g || n_e != g->P.n_energies) return 1;
+    free(g->ewt);
+    g->ewt = NULL;
+    if (w) {
+        g->ewt = malloc(sizeof(double) * n_e);
+        for (int n = 0; n < n_e; ++n) g->ewt[n] = w[n];
+        g->normD = normD;
+    }
+    return 0;
+}
+
 double or_norm_D(double t, int n_e) {
     double s = 0.0;
     for (int n = 0; n < n_e; ++n) s += 1.0 / (2.0 * n + 1.0);
@@ -256,7 +270,7 @@ void or_geom_free(or_geom *g) {
                     g->l_lo, g->l_hi, g->line_off, g->samp_off, g->smin, g->smax, g->m0,
                     g->m1, g->ns, g->edge_lo, g->edge_hi, g->soff, g->nearest_line,
                     g->lk_g_angle, g->lk_g_line, g->lk_g_w, g->lk_t_angle, g->lk_t_line,
-                    g->lk_t_w, g->ang_line_off, g->ang_samp_off};
+                    g->lk_t_w, g->ang_line_off, g->ang_samp_off, g->ewt};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(g);
 }
@@ -854,10 +868,11 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                         double *im = &images[4 * si];
                         if (n == 0) im[0] = im[1] = im[2] = im[3] = 0.0;
                         cplx sf = ff + conj(ft);
-                        im[0] += creal(sf);
-                        im[1] += cimag(sf);
-                        im[2] += 2.0 * creal(gg);
-                        im[3] += 2.0 * creal(In);
+                        double wn = g->ewt ? g->ewt[n] : 1.0;
+                        im[0] += wn * creal(sf);
+                        im[1] += wn * cimag(sf);
+                        im[2] += wn * 2.0 * creal(gg);
+                        im[3] += wn * 2.0 * creal(In);
                     } else {
                         images[si * n_e + n] = -cimag(gg) / M_PI;
                     }
@@ -949,7 +964,7 @@ int or_outputs(const or_geom *g, const double *acc, const double *delta, const d
     int nx = g->P.nx, ny = g->P.ny;
     double h = g->P.h, t = g->P.t;
     size_t npts = (size_t)nx * ny;
-    double D = or_norm_D(t, g->P.n_energies);
+    double D = g->ewt ? g->normD : or_norm_D(t, g->P.n_energies);
     double sgc = g->P.charge_sign;
     int magn = g->P.kappa > 0 && isfinite(g->P.kappa) && aind;
     double k2 = magn ? g->P.kappa * g->P.kappa : 0.0;
@@ -1167,10 +1182,11 @@ int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, c
                     cplx In = (conj(dsm[q]) * ff + dsm[q] * ft) / (M_PI + I * gg);
                     double *im = &images[4 * (out_off + sidx[q])];
                     cplx sf = ff + conj(ft);
-                    im[0] += creal(sf);
-                    im[1] += cimag(sf);
-                    im[2] += 2.0 * creal(gg);
-                    im[3] += 2.0 * creal(In);
+                    double wn = g->ewt ? g->ewt[n] : 1.0;
+                    im[0] += wn * creal(sf);
+                    im[1] += wn * cimag(sf);
+                    im[2] += wn * 2.0 * creal(gg);
+                    im[3] += wn * 2.0 * creal(In);
                 }
             }
             free(gam);

@@ -101,6 +101,10 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
 int or_rotate_back(const or_geom *g, const double *images, int mode, int n_e, double *acc);
 
 double or_norm_D(double t, int n_e);
+/* Weighted energy sums (Ozaki's poles, Sec. 3.1): the mode-0 images sum
+   w[n] * (terms of energy n) and the outputs use normD as the gap-equation
+   normalisation; w = NULL restores unit weights and the Matsubara D. */
+int or_geom_set_energy_weights(or_geom *g, const double *w, int n_e, double normD);
 
 /* Outputs from the mode-0 accumulators. delta_new: complex grid; j: [nx*ny][2];
    F: density grid; scalars[0]=F/Omega_A (mean over mask), scalars[1]=eps_G (l2). */
