@@ -197,6 +197,11 @@ def run_ours(args):
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
             f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     p["stepper"] = args.stepper
+    if args.energy_sum == "ozaki":
+        # Ozaki's poles up to the same energy cutoff (eps_c = 16 pi kB Tc)
+        p["energy_sum"] = "ozaki"
+        p["n_energies"] = W.ozaki_poles_for_cutoff(p["t"])
+        workload += f"_ozaki{p['n_energies']}"
     ctx = sc.Context(p, precision=args.precision, record_timings=True)
     info = ctx.info
     stream = torch.cuda.current_stream()
@@ -308,6 +313,7 @@ def run_ours(args):
         "config": {"workload": workload, "grid": [p["nx"], p["ny"]], "n_angles": p["n_angles"],
                    "n_energies": p["n_energies"], "t": p["t"], "pairing": "dx2y2",
                    "flux_quanta": p["flux_quanta"], "precision": args.precision, "stepper": args.stepper,
+                   "energy_sum": args.energy_sum,
                    "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
                    "parallelism": f"replicas{world}",
                    "step": "forward sweep + outputs" + (" + adjoint of F_total" if args.adjoint else ""),
@@ -352,6 +358,9 @@ def run_batch(args):
     grains = W.c3_batch(n_grains=args.grains, seed=3 + rank)
     for p, _, _ in grains:
         p["stepper"] = args.stepper
+        if args.energy_sum == "ozaki":
+            p["energy_sum"] = "ozaki"
+            p["n_energies"] = W.ozaki_poles_for_cutoff(p["t"])
     b = sc.Batch([p for p, _, _ in grains], precision=args.precision)
     for (p, d, _), m in zip(grains, b.members):
         m.set_fields(d)
@@ -395,6 +404,7 @@ def run_batch(args):
         "config": {"workload": f"c3_batch_{args.grains}_grains", "grains": args.grains,
                    "steps_per_sweep": info.steps_per_sweep, "work_items": info.n_items,
                    "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
+                   "energy_sum": args.energy_sum,
                    "lane_fill": info.steps_per_sweep / max(info.lane_steps_per_sweep, 1),
                    "sweep_launches": info.sweep_launches,
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
@@ -424,6 +434,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--energy-sum", default="matsubara", choices=["matsubara", "ozaki"],
+                    help="Matsubara energies below the cutoff, or Ozaki's poles reaching it")
     ap.add_argument("--stepper", default="closed", choices=["closed", "midpoint"],
                     help="integrator along a line: closed-form step or implicit midpoint rule (App. C)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

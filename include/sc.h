@@ -54,6 +54,13 @@ typedef enum { SC_PREC_FP64 = 0, SC_PREC_FP32 = 1 } sc_precision;
    same half-step values, g1 = g0 + ell f((g0 + g1)/2), solved as a quadratic
    (Eq. riccati_midpoint; the paper's production method). */
 typedef enum { SC_STEP_CLOSED = 0, SC_STEP_MIDPOINT = 1 } sc_stepper;
+/* Energy sums (Sec. 3.1).  MATSUBARA: eps_n = t (n + 1/2), n < n_energies, unit
+   weights, D = ln t + 2 sum 1/(2n + 1).  OZAKI: the continued-fraction poles of
+   the Fermi function (Ozaki 2007; the sum the paper uses): eps_p = t z_p / (2 pi)
+   with weights R_p (sc_ozaki_poles), and D = ln t + t sum_p R_p / eps_p; the
+   first poles coincide with Matsubara energies (R_p = 1), the later ones spread
+   out with larger weights, so far fewer energies reach a given cutoff. */
+typedef enum { SC_SUM_MATSUBARA = 0, SC_SUM_OZAKI = 1 } sc_energy_sum;
 
 /*
  * Problem statement of one grain (configuration appendix of the paper:
@@ -87,6 +94,9 @@ typedef struct {
     int32_t stepper;         /* sc_stepper: how each segment of a line is integrated
                                 (App. C); every sweep, burn-in, LDOS and adjoint of the
                                 context uses it */
+    int32_t energy_sum;      /* sc_energy_sum: which energies and weights the Matsubara
+                                sums use; with SC_SUM_OZAKI, n_energies is the number of
+                                Ozaki poles (at most 1024) */
 } sc_params;
 
 typedef struct {
@@ -105,6 +115,14 @@ typedef struct {
                                 record_timings = 1 (sc_get_info then waits for that sweep) */
     double ms_adjoint;       /* last adjoint sweep kernel, when record_timings = 1 */
 } sc_info;
+
+/* Ozaki's poles (host only, no context): z[p] ascending and residues R[p] of
+   the n-pole continued-fraction representation 1/(1 + e^x) =
+   1/2 - sum_p R_p [1/(x - i z_p) + 1/(x + i z_p)], 1 <= n <= 1024. */
+sc_status sc_ozaki_poles(int32_t n, double *z, double *R);
+/* The context's positive energies (units of 2 pi kB Tc) and their weights in
+   the energy sums (n_energies each). */
+sc_status sc_energy_grid(const sc_ctx *ctx, double *eps, double *weights);
 
 /* Fill defaults: 64x64 unit grid, s-wave disc, t = 0.5, 32 angles, 16 energies,
    charge -1, lattice offset (0.1, 0.2), FP32. */

@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
             mir[e] = n_e - 1 - nid[e];
         } else {
             zr0[e] = T(0);
-            zi[e] = (T)(gs.t * (nid[e] + 0.5));
+            zi[e] = gs.mats_eps ? (T)gs.mats_eps[nid[e]] : (T)(gs.t * (nid[e] + 0.5));
             mir[e] = nid[e];
         }
     }
@@ -261,10 +261,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                             const C gbar = cadd(cadd(ga, gb2), gcF);
                             const C ba = cmul(cmuli(cscale(iD2, T(2) * pi)), cadd(Wf, cmul(cmul(gf, gf), Wc)));
                             const C bb2 = cmul(cmuli(cscale(iD2, T(4) * pi * W.z)), gf);
-                            const C bbar = cadd(cadd(ba, bb2), gcF);
-                            lnew = cadd(lnew, gbar);
+                            C bbar = cadd(cadd(ba, bb2), gcF);
+                            // weighted energy sums (Ozaki's poles): every term of energy n
+                            // carries its weight
+                            const T wn = gs.mats_w ? (T)gs.mats_w[nid[e]] : T(1);
+                            lnew = cadd(lnew, cscale(gbar, wn));
+                            bbar = cscale(bbar, wn);
                             // direct dependence of S_F on the sample value: -2 i wF (gamma + beta)
-                            const C sF = cmuli(cscale(cadd(gf, bt), T(-2) * W.w));
+                            const C sF = cmuli(cscale(cadd(gf, bt), T(-2) * W.w * wn));
                             sdr += sF.x;
                             sdi += sF.y;
                             park(q, 1, e) = bbar;

@@ -185,7 +185,7 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     CK(dalloc(ctx, &pl.d_items, items.size() * sizeof(int2)));
     CK(cudaMemcpy(pl.d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
     const int bs = 128;
-    int occ = scd::sweep_occupancy(ctx->fp64, ept, bs, ctx->stepper);
+    int occ = scd::sweep_occupancy(ctx->fp64, ept, bs, ctx->stepper, ctx->d_ewt != nullptr);
     if (occ < 1) occ = 1;
     pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
     pl.stride = (int64_t)G * std::max(ctx->geo.max_ns, 1) * lanes * ept;
@@ -198,6 +198,8 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     gs.exits[0] = ctx->d_exit[0];
     gs.exits[1] = ctx->d_exit[1];
     gs.energies = nullptr;
+    gs.mats_eps = ctx->d_eps;  // nullptr for plain Matsubara energies
+    gs.mats_w = ctx->d_ewt;
     gs.t = ctx->geo.prm.t;
     gs.h = ctx->geo.prm.h;
     gs.broadening = 0.0;
@@ -266,6 +268,7 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     a.grid_blocks = pl.grid_blocks;
     a.block_threads = 128;
     a.stepper = ctx->stepper;
+    a.weighted = ctx->d_ewt != nullptr ? 1 : 0;
     CK(scd::launch_sweep(ctx->fp64, a, st));
     return SC_OK;
 }
@@ -357,6 +360,14 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         g_create_error = "stepper must be SC_STEP_CLOSED or SC_STEP_MIDPOINT";
         return SC_EINVAL;
     }
+    if (p->energy_sum != SC_SUM_MATSUBARA && p->energy_sum != SC_SUM_OZAKI) {
+        g_create_error = "energy_sum must be SC_SUM_MATSUBARA or SC_SUM_OZAKI";
+        return SC_EINVAL;
+    }
+    if (p->energy_sum == SC_SUM_OZAKI && (p->n_energies < 1 || p->n_energies > 1024)) {
+        g_create_error = "Ozaki sums take 1 to 1024 poles (n_energies)";
+        return SC_EINVAL;
+    }
     sc_ctx *ctx = new (std::nothrow) sc_ctx();
     if (!ctx) {
         g_create_error = "host allocation failed";
@@ -374,10 +385,22 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     ctx->n_e = p->n_energies;
     ctx->forced_lanes = p->lanes_per_line;
     ctx->stepper = p->stepper;
+    // energies and weights of the energy sums; D = ln t + t sum_n w_n / eps_n
+    // (Matsubara: eps_n = t (n + 1/2), w_n = 1, i.e. 2 sum 1/(2n + 1))
+    ctx->energy_sum = p->energy_sum;
+    ctx->eps.resize(ctx->n_e);
+    ctx->ewt.assign(ctx->n_e, 1.0);
+    if (p->energy_sum == SC_SUM_OZAKI) {
+        std::vector<double> z(ctx->n_e);
+        sc_ozaki_poles(ctx->n_e, z.data(), ctx->ewt.data());
+        for (int n = 0; n < ctx->n_e; ++n) ctx->eps[n] = p->t * z[n] / (2.0 * M_PI);
+    } else {
+        for (int n = 0; n < ctx->n_e; ++n) ctx->eps[n] = p->t * (n + 0.5);
+    }
     {
         double s = 0.0;
-        for (int n = 0; n < ctx->n_e; ++n) s += 1.0 / (2.0 * n + 1.0);
-        ctx->normD = std::log(p->t) + 2.0 * s;
+        for (int n = 0; n < ctx->n_e; ++n) s += ctx->ewt[n] / ctx->eps[n];
+        ctx->normD = std::log(p->t) + p->t * s;
     }
     if (p->host_only) {
         ctx->host_only = true;
@@ -559,6 +582,12 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     CA(ctx->d_img_in, G.n_slots * t4);
     CA(ctx->d_img_out, G.n_slots * t4);
     for (int b = 0; b < 2; ++b) CA(ctx->d_exit[b], 2 * nL * (size_t)ctx->n_e * cplx);
+    if (ctx->energy_sum == SC_SUM_OZAKI) {
+        CA(ctx->d_eps, ctx->n_e * sizeof(double));
+        CP(ctx->d_eps, ctx->eps.data(), ctx->n_e * sizeof(double));
+        CA(ctx->d_ewt, ctx->n_e * sizeof(double));
+        CP(ctx->d_ewt, ctx->ewt.data(), ctx->n_e * sizeof(double));
+    }
     if (!ctx->fp64) {
         CA(ctx->d_line_f32, nL * sizeof(scd::LineF32));
         CP(ctx->d_line_f32, lf.data(), nL * sizeof(scd::LineF32));
@@ -659,6 +688,15 @@ sc_status sc_get_info(const sc_ctx *ctx, sc_info *info) {
             info->ms_adjoint = a;
         else
             (void)cudaGetLastError();
+    }
+    return SC_OK;
+}
+
+sc_status sc_energy_grid(const sc_ctx *ctx, double *eps, double *weights) {
+    if (!ctx) return SC_EINVAL;
+    for (int n = 0; n < ctx->n_e; ++n) {
+        if (eps) eps[n] = ctx->eps[n];
+        if (weights) weights[n] = ctx->ewt[n];
     }
     return SC_OK;
 }

@@ -21,6 +21,7 @@ struct sc_batch {
     bool fp64 = false;
     int ept = 0;  // bound on energies per lane
     int stepper = 0;  // sc_stepper, shared by all members
+    bool weighted = false;  // Ozaki energy sums, shared by all members
     int sm_count = 0;
     scd::GrainSweep *d_grains = nullptr;
     int2 *d_items = nullptr;
@@ -132,6 +133,8 @@ sc_status build(sc_batch *b, int ept) {
         d.exits[0] = c->d_exit[0];
         d.exits[1] = c->d_exit[1];
         d.energies = nullptr;
+        d.mats_eps = c->d_eps;
+        d.mats_w = c->d_ewt;
         d.t = c->geo.prm.t;
         d.h = c->geo.prm.h;
         d.broadening = 0.0;
@@ -163,7 +166,7 @@ sc_status build(sc_batch *b, int ept) {
     }
     int max_blocks = 1;
     for (auto &c : classes) {
-        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper);
+        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper, b->weighted);
         if (occ < 1) occ = 1;
         c.grid_blocks = std::max(1, std::min(b->sm_count * occ, (c.n + 3) / 4));
         max_blocks = std::max(max_blocks, c.grid_blocks);
@@ -245,9 +248,10 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     if (!b) return SC_ENOMEM;
     int max_ne = 0;
     for (int g = 0; g < n; ++g) {
-        if (params[g].precision != params[0].precision || params[g].stepper != params[0].stepper) {
+        if (params[g].precision != params[0].precision || params[g].stepper != params[0].stepper ||
+            params[g].energy_sum != params[0].energy_sum) {
             sc_batch_destroy(b);
-            sc_internal::set_thread_error("all members of a batch need the same precision and stepper");
+            sc_internal::set_thread_error("all members of a batch need the same precision, stepper and energy sum");
             return SC_EINVAL;
         }
         if (params[g].host_only) {
@@ -272,6 +276,7 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     }
     b->fp64 = params[0].precision == SC_PREC_FP64;
     b->stepper = params[0].stepper;
+    b->weighted = params[0].energy_sum == SC_SUM_OZAKI;
     b->device = b->members[0]->device;
     b->sm_count = b->members[0]->sm_count;
     sc_status st = SC_OK;
@@ -341,6 +346,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.grid_blocks = c.grid_blocks;
         a.block_threads = 128;
         a.stepper = b->stepper;
+        a.weighted = b->weighted ? 1 : 0;
         BCK(scd::launch_sweep(b->fp64, a, st));
     }
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));

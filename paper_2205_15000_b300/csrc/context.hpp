@@ -29,6 +29,9 @@ struct sc_ctx {
     int n_e = 0;
     int forced_lanes = 0;
     int stepper = 0;  // sc_stepper
+    int energy_sum = 0;  // sc_energy_sum
+    std::vector<double> eps, ewt;  // energies and weights of the energy sums (host)
+    double *d_eps = nullptr, *d_ewt = nullptr;  // on the device for Ozaki sums, else nullptr
     double normD = 0.0;
     size_t real_bytes = 4;
     scd::GridDev grid{};

@@ -99,8 +99,8 @@ cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t st) {
     return fp64 ? launch_sweep_f64(a, st) : launch_sweep_f32(a, st);
 }
 
-int sweep_occupancy(bool fp64, int ept, int bs, int stepper) {
-    return fp64 ? sweep_occupancy_f64(ept, bs, stepper) : sweep_occupancy_f32(ept, bs, stepper);
+int sweep_occupancy(bool fp64, int ept, int bs, int stepper, bool weighted) {
+    return fp64 ? sweep_occupancy_f64(ept, bs, stepper, weighted) : sweep_occupancy_f32(ept, bs, stepper, weighted);
 }
 
 // ---------------------------------------------------------------------------

@@ -76,6 +76,8 @@ struct GrainSweep {
     void *exits[2];            // complex T [2 n_lines][n_e]; a sweep reads exits[parity]
                                // (previous sweep) and writes exits[parity ^ 1]
     const double *energies;    // retarded mode: n_e real energies, symmetric about zero
+    const double *mats_eps;    // Matsubara mode: positive energies (nullptr: eps_n = t (n + 1/2))
+    const double *mats_w;      // Matsubara mode: weights of the energy sums (nullptr: 1)
     double t;                  // Matsubara energies eps_n = t (n + 1/2)
     double h;                  // lattice spacing
     double broadening;         // retarded mode: z = eps + i broadening
@@ -102,7 +104,7 @@ struct SweepLaunch {
     int32_t retarded;          // LDOS mode
     int32_t grid_blocks, block_threads;
     int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
-    int32_t pad;
+    int32_t weighted;          // Matsubara mode: weighted energy sums (grains carry mats_w)
 };
 
 // launchers (return cudaError_t)
@@ -121,12 +123,12 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
                                    const GridDev &grid, const uint8_t *mask, const float4 *image_out,
                                    double *acc, cudaStream_t s);
-int sweep_occupancy(bool fp64, int ept, int block_threads, int stepper);
+int sweep_occupancy(bool fp64, int ept, int block_threads, int stepper, bool weighted);
 // per-precision instantiations (sweep_f32.cu, sweep_f64.cu)
 cudaError_t launch_sweep_f32(const SweepLaunch &a, cudaStream_t s);
 cudaError_t launch_sweep_f64(const SweepLaunch &a, cudaStream_t s);
-int sweep_occupancy_f32(int ept, int block_threads, int stepper);
-int sweep_occupancy_f64(int ept, int block_threads, int stepper);
+int sweep_occupancy_f32(int ept, int block_threads, int stepper, bool weighted);
+int sweep_occupancy_f64(int ept, int block_threads, int stepper, bool weighted);
 cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
                                const BackLine *bl, const GridDev &grid, const uint8_t *mask,
                                const void *image_out, double *acc, cudaStream_t s);

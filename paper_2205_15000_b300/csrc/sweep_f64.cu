@@ -5,6 +5,8 @@ namespace scd {
 
 cudaError_t launch_sweep_f64(const SweepLaunch &a, cudaStream_t st) { return sweep_launch_t<double>(a, st); }
 
-int sweep_occupancy_f64(int ept, int bs, int stepper) { return sweep_occupancy_t<double>(ept, bs, stepper); }
+int sweep_occupancy_f64(int ept, int bs, int stepper, bool weighted) {
+    return sweep_occupancy_t<double>(ept, bs, stepper, weighted);
+}
 
 }  // namespace scd

@@ -33,8 +33,9 @@ namespace scd {
 #endif
 
 // One work item: the G lines of group it.y of grain gs, EPT energies per lane;
-// STEP 0 = closed-form step, 1 = implicit midpoint rule.
-template <typename T, int EPT, bool RET, int STEP>
+// STEP 0 = closed-form step, 1 = implicit midpoint rule; WGT: weighted energy
+// sums (Ozaki's poles) in the Matsubara mode.
+template <typename T, int EPT, bool RET, int STEP, bool WGT>
 __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
                                            Cx<T> *const warp_slab, const int lane) {
     typedef typename Vec4<T>::type T4;
@@ -52,6 +53,7 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
 
         // the lane's energies: z = zr0 + i zi (+ a along the line)
         T zr0[EPT], zi[EPT];
+        T wv[WGT ? EPT : 1];  // weights of the lane's energies (WGT)
         int nid[EPT], mir[EPT];
         bool ev[EPT];
 #pragma unroll
@@ -66,8 +68,9 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                 mir[e] = n_e - 1 - nn;
             } else {
                 zr0[e] = T(0);
-                zi[e] = (T)(gs.t * (nn + 0.5));
+                zi[e] = gs.mats_eps ? (T)gs.mats_eps[nn] : (T)(gs.t * (nn + 0.5));
                 mir[e] = nn;
+                if constexpr (WGT) wv[e] = ev[e] ? (T)gs.mats_w[nn] : T(0);
             }
         }
         const int L = gs.groups[(int64_t)it.y * G + gi];
@@ -219,12 +222,23 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                         const T Dr = T(1) + pr, Di = pi_;
                         const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
                         const T ir = Dr * rD, ii = -Di * rD;      // 1/D
-                        sg += ii;
                         // ga/D + gb conj(1/D)
-                        sfr += (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
-                        sfi += (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
-                        sFr += ga.x + gb.x;
-                        sFi += ga.y + gb.y;
+                        const T fr = (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
+                        const T fi = (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
+                        if constexpr (WGT) {
+                            const T w = wv[e];
+                            sg += w * ii;
+                            sfr += w * fr;
+                            sfi += w * fi;
+                            sFr += w * (ga.x + gb.x);
+                            sFi += w * (ga.y + gb.y);
+                        } else {
+                            sg += ii;
+                            sfr += fr;
+                            sfi += fi;
+                            sFr += ga.x + gb.x;
+                            sFi += ga.y + gb.y;
+                        }
                     }
                 }
 #pragma unroll
@@ -274,7 +288,7 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
     }
 }
 
-template <typename T, int EPT, bool RET, int STEP>
+template <typename T, int EPT, bool RET, int STEP, bool WGT>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS) : 1)
     sweep_kernel(SweepLaunch a) {
     const int lane = threadIdx.x & 31;
@@ -286,16 +300,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLO
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
-        sweep_item<T, EPT, RET, STEP>(a, it, a.grains[it.x], warp_slab, lane);
+        sweep_item<T, EPT, RET, STEP, WGT>(a, it, a.grains[it.x], warp_slab, lane);
     }
 }
 
-template <typename T, bool RET, int STEP>
+template <typename T, bool RET, int STEP, bool WGT>
 static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: sweep_kernel<T, E, RET, STEP><<<grid, block, 0, st>>>(a); break;
+    case E: sweep_kernel<T, E, RET, STEP, WGT><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
@@ -303,20 +317,25 @@ static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t sweep_launch_t(const SweepLaunch &a, cudaStream_t st) {
-    if (a.stepper == 1)
-        return a.retarded ? sweep_dispatch<T, true, 1>(a, st) : sweep_dispatch<T, false, 1>(a, st);
-    if (a.stepper != 0) return cudaErrorInvalidValue;
-    return a.retarded ? sweep_dispatch<T, true, 0>(a, st) : sweep_dispatch<T, false, 0>(a, st);
+template <typename T, int STEP>
+static cudaError_t sweep_launch_s(const SweepLaunch &a, cudaStream_t st) {
+    if (a.retarded) return sweep_dispatch<T, true, STEP, false>(a, st);
+    return a.weighted ? sweep_dispatch<T, false, STEP, true>(a, st) : sweep_dispatch<T, false, STEP, false>(a, st);
 }
 
-template <typename T, bool RET, int STEP>
+template <typename T>
+static cudaError_t sweep_launch_t(const SweepLaunch &a, cudaStream_t st) {
+    if (a.stepper == 1) return sweep_launch_s<T, 1>(a, st);
+    if (a.stepper != 0) return cudaErrorInvalidValue;
+    return sweep_launch_s<T, 0>(a, st);
+}
+
+template <typename T, bool RET, int STEP, bool WGT>
 static int occ_dispatch(int ept, int bs) {
     int n = 0;
     switch (ept) {
 #define SC_CASE(E) \
-    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET, STEP>, bs, 0); break;
+    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET, STEP, WGT>, bs, 0); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: n = 0;
@@ -324,11 +343,18 @@ static int occ_dispatch(int ept, int bs) {
     return n;
 }
 
-// blocks per SM: the smaller of the Matsubara and retarded instantiations
+// blocks per SM: the smaller of the context's Matsubara instantiation (plain
+// or weighted) and the retarded one (both launch with the same plan)
 template <typename T>
-static int sweep_occupancy_t(int ept, int bs, int stepper) {
-    const int a = stepper == 1 ? occ_dispatch<T, false, 1>(ept, bs) : occ_dispatch<T, false, 0>(ept, bs);
-    const int b = stepper == 1 ? occ_dispatch<T, true, 1>(ept, bs) : occ_dispatch<T, true, 0>(ept, bs);
+static int sweep_occupancy_t(int ept, int bs, int stepper, bool weighted) {
+    int a, b;
+    if (stepper == 1) {
+        a = weighted ? occ_dispatch<T, false, 1, true>(ept, bs) : occ_dispatch<T, false, 1, false>(ept, bs);
+        b = occ_dispatch<T, true, 1, false>(ept, bs);
+    } else {
+        a = weighted ? occ_dispatch<T, false, 0, true>(ept, bs) : occ_dispatch<T, false, 0, false>(ept, bs);
+        b = occ_dispatch<T, true, 0, false>(ept, bs);
+    }
     return a < b ? a : b;
 }
 

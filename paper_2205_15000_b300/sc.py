@@ -21,6 +21,9 @@ SC_PREC_FP64, SC_PREC_FP32 = 0, 1
 # sc_stepper: integrator of the Riccati equation along a line (App. C)
 SC_STEP_CLOSED, SC_STEP_MIDPOINT = 0, 1
 STEPPERS = {"closed": SC_STEP_CLOSED, "midpoint": SC_STEP_MIDPOINT}
+# sc_energy_sum: energies and weights of the Matsubara sums (Sec. 3.1)
+SC_SUM_MATSUBARA, SC_SUM_OZAKI = 0, 1
+ENERGY_SUMS = {"matsubara": SC_SUM_MATSUBARA, "ozaki": SC_SUM_OZAKI}
 
 
 class ScError(RuntimeError):
@@ -45,7 +48,7 @@ class sc_params(ctypes.Structure):
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
         ("precision", ctypes.c_int32), ("lanes_per_line", ctypes.c_int32),
         ("host_only", ctypes.c_int32), ("record_timings", ctypes.c_int32),
-        ("stepper", ctypes.c_int32),
+        ("stepper", ctypes.c_int32), ("energy_sum", ctypes.c_int32),
     ]
 
 
@@ -91,7 +94,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
-            "sc_accel_get_state",
+            "sc_accel_get_state", "sc_ozaki_poles", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
@@ -127,6 +130,8 @@ def _load():
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
+        "sc_ozaki_poles": [i32, vp, vp],
+        "sc_energy_grid": [vp, vp, vp],
         "sc_accel_params_default": [i32, P(sc_accel_params)],
         "sc_accelerate": [vp, P(sc_accel_params), vp],
         "sc_accel_reset": [vp],
@@ -210,6 +215,7 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
     p.host_only = 1 if host_only else 0
     p.record_timings = 1 if record_timings else 0
     p.stepper = STEPPERS[d.get("stepper", "closed")]
+    p.energy_sum = ENERGY_SUMS[d.get("energy_sum", "matsubara")]
     return p
 
 
@@ -272,6 +278,19 @@ def sc_update_vector_potential(ctx, stream=None):
 
 def sc_picard_step(ctx, stream=None):
     _check(lib.sc_picard_step(ctx, _stream(stream)), ctx)
+
+
+def sc_ozaki_poles(n):
+    """Ozaki's poles z (ascending) and residues R of the n-pole representation."""
+    z, R = np.zeros(n), np.zeros(n)
+    _check(lib.sc_ozaki_poles(int(n), _ptr(z), _ptr(R)))
+    return z, R
+
+
+def sc_energy_grid(ctx, n_e):
+    eps, w = np.zeros(n_e), np.zeros(n_e)
+    _check(lib.sc_energy_grid(ctx, _ptr(eps), _ptr(w)), ctx)
+    return eps, w
 
 
 def sc_accel_params_default(kind):

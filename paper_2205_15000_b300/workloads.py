@@ -38,6 +38,14 @@ def n_energies_for_cutoff(t, eps_cut=8.0):
     return int(math.ceil(eps_cut / t - 0.5))
 
 
+def ozaki_poles_for_cutoff(t, eps_cut=8.0):
+    """Number of Ozaki poles whose largest energy t z_max/(2 pi) reaches the
+    cutoff, z_max ~ 0.84 pi n^2: the Ozaki counterpart of n_energies_for_cutoff
+    (at equal cutoff the Ozaki sum is the more accurate of the two)."""
+    n = max(1, int(math.ceil(math.sqrt(2.0 * eps_cut / (0.84 * t)))))
+    return n
+
+
 def base_params(**kw):
     p = dict(nx=64, ny=64, h=20.0 / 64, x0=-10.0, y0=-10.0, shape_kind=1, disc_cx=0.0,
              disc_cy=0.0, disc_r=0.0, vx=[], vy=[], pairing=0, crystal_rotation=0.0, t=0.5,

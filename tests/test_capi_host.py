@@ -62,6 +62,37 @@ def test_stepper_validated_and_default_closed():
     assert ei.value.status == sc.SC_EINVAL
 
 
+@pytest.mark.parametrize("n", [1, 4, 16, 100, 512])
+def test_ozaki_poles_match_the_oracle(n):
+    """The library's poles (bisection + inverse iteration) against the oracle's
+    (LAPACK eigen-decomposition of the same matrix)."""
+    z, R = sc.sc_ozaki_poles(n)
+    zo, Ro = oracle.ozaki_poles(n)
+    np.testing.assert_allclose(z, zo, rtol=1e-12)
+    np.testing.assert_allclose(R, Ro, rtol=1e-9)
+
+
+def test_ozaki_energy_grid_and_normalisation():
+    p = W.disc(5.0, 32, n_angles=8, n_energies=12, t=0.3)
+    p["energy_sum"] = "ozaki"
+    ctx = sc.Context(p, host_only=True)
+    eps, w = sc.sc_energy_grid(ctx.h, 12)
+    eo, wo = oracle.ozaki_energies(0.3, 12)
+    np.testing.assert_allclose(eps, eo, rtol=1e-12)
+    np.testing.assert_allclose(w, wo, rtol=1e-9)
+    g = oracle.OracleGeom(p)
+    assert abs(ctx.info.norm_D - g.normD) < 1e-10
+    q = dict(p, energy_sum="matsubara")
+    ctx2 = sc.Context(q, host_only=True)
+    eps2, w2 = sc.sc_energy_grid(ctx2.h, 12)
+    np.testing.assert_allclose(eps2, 0.3 * (np.arange(12) + 0.5), rtol=1e-15)
+    assert np.all(w2 == 1.0)
+    assert abs(ctx2.info.norm_D - oracle.norm_D(0.3, 12)) < 1e-13
+    with pytest.raises(sc.ScError) as ei:
+        sc.Context(dict(p, n_energies=2000), host_only=True)
+    assert ei.value.status == sc.SC_EINVAL
+
+
 def test_nonconvex_polygon_rejected():
     p = W.polygon([0.0, 4.0, 2.0, 4.0, 0.0], [0.0, 0.0, 1.0, 4.0, 4.0], 0.25, n_angles=8, n_energies=2)
     with pytest.raises(sc.ScError) as ei:

@@ -101,6 +101,23 @@ def test_midpoint_free_energy_gradient_matches_oracle_fd():
     assert np.max(np.abs(adj - fd)) <= 1e-6 * scale, np.max(np.abs(adj - fd)) / scale
 
 
+def test_ozaki_free_energy_gradient_matches_oracle_fd():
+    """The adjoint with Ozaki-weighted energy sums against central differences
+    of the oracle's weighted sweep."""
+    p, d, a = _grain()
+    p["energy_sum"] = "ozaki"
+    g = oracle.OracleGeom(p)
+    ex = _oracle_converged_exits(g, d, a)
+    loss = lambda dd, aa: g.full_sweep(dd, aa, ex)["F_total"]  # noqa: E731
+    probes = _probes(p, g, 8, 47)
+    fd = _fd(loss, d, a, probes)
+    gd, ga = _adjoint(p, d, a, "fp64", g_Ftotal=1.0)
+    adj = np.array([[gd[j, i].real, gd[j, i].imag, ga[j, i, 0], ga[j, i, 1]] for j, i in probes])
+    scale = np.max(np.abs(fd))
+    assert scale > 0
+    assert np.max(np.abs(adj - fd)) <= 1e-6 * scale, np.max(np.abs(adj - fd)) / scale
+
+
 def test_output_cotangent_gradient_matches_oracle_fd():
     p, d, a = _grain()
     g = oracle.OracleGeom(p)

@@ -74,6 +74,27 @@ def test_batch_midpoint_equals_single_contexts():
     b.close()
 
 
+def test_batch_ozaki_matches_oracle_fp64():
+    """A batch with Ozaki energy sums: every member equals the oracle's weighted
+    sweep (FP64)."""
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    prms = [dict(p, energy_sum="ozaki") for p, _ in grains]
+    b = sc.Batch(prms, precision="fp64")
+    for (_, d), m in zip(grains, b.members):
+        m.set_fields(d)
+    exits = [None] * len(grains)
+    for it in range(2):
+        b.sweep()
+        for gi, ((_, d), q) in enumerate(zip(grains, prms)):
+            o = oracle.OracleGeom(q).full_sweep(d, None, exits[gi])
+            exits[gi] = o["exit"]
+            r = _outputs(b.members[gi])
+            np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=1e-10, rtol=0)
+            np.testing.assert_allclose(r["j"], o["j"], atol=1e-10, rtol=0)
+    b.close()
+
+
 def test_batch_member_matches_oracle_fp64():
     from paper_2205_15000_b300 import sc
     grains = _grains()

@@ -121,6 +121,29 @@ def test_fp32_sweep_within_tolerance(name, stepper):
         assert np.max(np.abs(R["exits"] - o["exit"][0])) < 2e-5
 
 
+@pytest.mark.parametrize("stepper", ["closed", "midpoint"])
+@pytest.mark.parametrize("name", ["diamond_d_field", "disc_vortex_ragged", "polygon_dxy"])
+def test_ozaki_sums_match_oracle(name, stepper):
+    """Ozaki energies and weights (Sec. 3.1): FP64 sweeps = the oracle's weighted
+    sweeps to 1e-10; FP32 within the production tolerances."""
+    p, delta, aind = case(name)
+    p["stepper"] = stepper
+    p["energy_sum"] = "ozaki"
+    g, ctx, m, res = _run_both(p, delta, aind, "fp64", n_sweeps=2)
+    for R in res:
+        o, r = R["o"], R["r"]
+        np.testing.assert_allclose(R["exits"], o["exit"][0], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["j"], o["j"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["F"], o["F"], atol=TOL64, rtol=0)
+    g, ctx, m, res = _run_both(p, delta, aind, "fp32", n_sweeps=2)
+    for R in res:
+        o, r = R["o"], R["r"]
+        assert _rel(r["delta_new"][m], o["delta_new"][m]) < TOL_DELTA
+        assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
+        assert _rel(r["F"][m], o["F"][m]) < TOL_F
+
+
 @pytest.mark.parametrize("lanes", [4, 8, 16, 32])
 def test_lane_layouts_agree(lanes):
     """Every lanes-per-line layout (with padded energies) gives the FP64 result."""
