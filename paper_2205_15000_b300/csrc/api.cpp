@@ -640,6 +640,19 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
 #undef CA
 #undef CP
     sc_status st = make_plan(ctx, ctx->n_e, 0, &ctx->main_plan);
+    if (st == SC_OK && !ctx->forced_lanes) {
+        // A small grain (few lines, few energies) leaves resident warps without
+        // work: one doubling of the lanes per line doubles the work items, kept
+        // while the items stay fewer than the resident warps and >= 3/4 of the
+        // lane slots carry an energy (measured: 14 Ozaki poles on 256^2, 0.56 ->
+        // 0.44 ms; a grain that fills the GPU is left alone).
+        Plan *pl = ctx->main_plan;
+        const int occ = std::max(1, scd::sweep_occupancy(ctx->fp64, pl->ept, 128, ctx->stepper, ctx->d_ewt != nullptr));
+        const int64_t resident = (int64_t)ctx->sm_count * occ * 4;
+        const int l2 = 2 * pl->lanes, e2 = (ctx->n_e + l2 - 1) / l2;
+        if (pl->lanes < 32 && pl->n_groups < resident && 4 * ctx->n_e >= 3 * l2 * e2)
+            st = make_plan_layout(ctx, ctx->n_e, l2, e2, &ctx->main_plan);
+    }
     if (st != SC_OK) {
         g_create_error = ctx->err;
         sc_destroy(ctx);
