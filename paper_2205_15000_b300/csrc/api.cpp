@@ -280,7 +280,7 @@ sc_status ensure_outputs_impl(sc_ctx *ctx, cudaStream_t st) {
     const bool magn = kappa > 0.0 && std::isfinite(kappa) && ctx->have_aind;
     CK(scd::launch_outputs(ctx->grid, ctx->d_mask, ctx->d_acc, ctx->d_delta, magn ? ctx->d_aind : nullptr,
                            ctx->geo.prm.t, ctx->normD, magn ? kappa : 0.0, ctx->d_dnew, ctx->d_j, ctx->d_F,
-                           ctx->d_sums, st));
+                           ctx->d_sums, ctx->d_part, st));
     ctx->have_outputs = true;
     return SC_OK;
 }
@@ -576,6 +576,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     CA(ctx->d_j, 2 * np * sizeof(double));
     CA(ctx->d_F, np * sizeof(double));
     CA(ctx->d_sums, 8 * sizeof(double));
+    CA(ctx->d_part, (size_t)scd::reduce_blocks((int64_t)np) * 4 * sizeof(double));
     CA(ctx->d_jsum, 2 * sizeof(double));
     CA(ctx->d_diff, sizeof(double));
     CA(ctx->d_counter, sizeof(int32_t));
@@ -829,7 +830,7 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream) {
     if (!ctx->d_G) return SC_OK;  // kappa <= 0: no induced field
     cudaStream_t st = (cudaStream_t)stream;
     CKS(ensure_outputs_impl(ctx, st));
-    CK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, st));
+    CK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, ctx->d_part, st));
     const double k = ctx->geo.prm.kappa;
     CK(scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in, ctx->d_G,
                                     ctx->G_width, 1.0 / (k * k), ctx->d_aind, st));

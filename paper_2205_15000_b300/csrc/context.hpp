@@ -48,6 +48,7 @@ struct sc_ctx {
     // fields and results
     double *d_delta = nullptr, *d_aind = nullptr, *d_acc = nullptr, *d_dnew = nullptr, *d_j = nullptr,
            *d_F = nullptr, *d_sums = nullptr, *d_jsum = nullptr, *d_G = nullptr, *d_diff = nullptr;
+    double *d_part = nullptr;  // per-block partial sums of the grid reductions
     int G_width = 0;
     bool have_aind = false;
     void *d_img_in = nullptr, *d_img_out = nullptr;

@@ -255,7 +255,7 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
                                const double *__restrict__ acc, const double *__restrict__ delta,
                                const double *__restrict__ aind, double t, double normD, double kappa,
                                double *__restrict__ dn, double *__restrict__ jo,
-                               double *__restrict__ F, double *__restrict__ sums) {
+                               double *__restrict__ F, double *__restrict__ partials) {
     __shared__ double sh[32];
     const int nx = grid.nx, ny = grid.ny;
     const int64_t npts = (int64_t)nx * ny;
@@ -301,29 +301,44 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
     const double s1 = block_sum(den, sh);
     const double s2 = block_sum(fs, sh);
     const double s3 = block_sum(bad, sh);
-    if (threadIdx.x == 0) {
-        atomicAdd(&sums[0], s0);
-        atomicAdd(&sums[1], s1);
-        atomicAdd(&sums[2], s2);
-        atomicAdd(&sums[3], s3);
+    if (threadIdx.x == 0) {  // per-block partials, summed in block order by final_sums_kernel
+        double *pb = partials + 4 * (int64_t)blockIdx.x;
+        pb[0] = s0;
+        pb[1] = s1;
+        pb[2] = s2;
+        pb[3] = s3;
     }
 }
+
+// Deterministic completion of a block reduction: slot k of out = the sum over
+// blocks of partials[b][k], in a fixed order (strided per thread, then a fixed tree).
+__global__ void final_sums_kernel(const double *__restrict__ partials, int nblocks, int nslots,
+                                  double *__restrict__ out) {
+    __shared__ double sh[32];
+    for (int k = 0; k < nslots; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(int64_t)b * nslots + k];
+        const double tot = block_sum(v, sh);
+        if (threadIdx.x == 0) out[k] = tot;
+    }
+}
+
+int reduce_blocks(int64_t npts) { return (int)((npts + 255) / 256); }
 
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
                            const double *delta, const double *aind, double t, double normD,
                            double kappa, double *delta_new, double *j, double *F, double *sums,
-                           cudaStream_t st) {
+                           double *partials, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;
-    cudaError_t e = cudaMemsetAsync(sums, 0, 4 * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    const int bs = 256;
-    outputs_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(grid, mask, acc, delta, aind, t,
-                                                                    normD, kappa, delta_new, j, F, sums);
+    const int bs = 256, nb = reduce_blocks(npts);
+    outputs_kernel<<<(unsigned)nb, bs, 0, st>>>(grid, mask, acc, delta, aind, t, normD, kappa, delta_new, j, F,
+                                                partials);
+    final_sums_kernel<<<1, 256, 0, st>>>(partials, nb, 4, sums);
     return cudaGetLastError();
 }
 
 __global__ void mean_current_kernel(GridDev grid, const uint8_t *__restrict__ mask,
-                                    const double *__restrict__ j, double *sums) {
+                                    const double *__restrict__ j, double *partials) {
     __shared__ double sh[32];
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -335,18 +350,17 @@ __global__ void mean_current_kernel(GridDev grid, const uint8_t *__restrict__ ma
     const double sx = block_sum(jx, sh);
     const double sy = block_sum(jy, sh);
     if (threadIdx.x == 0) {
-        atomicAdd(&sums[0], sx);
-        atomicAdd(&sums[1], sy);
+        partials[2 * (int64_t)blockIdx.x] = sx;
+        partials[2 * (int64_t)blockIdx.x + 1] = sy;
     }
 }
 
 cudaError_t launch_mean_current(const GridDev &grid, const uint8_t *mask, const double *j,
-                                double *sums, cudaStream_t st) {
+                                double *sums, double *partials, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;
-    cudaError_t e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), st);
-    if (e != cudaSuccess) return e;
-    const int bs = 256;
-    mean_current_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(grid, mask, j, sums);
+    const int bs = 256, nb = reduce_blocks(npts);
+    mean_current_kernel<<<(unsigned)nb, bs, 0, st>>>(grid, mask, j, partials);
+    final_sums_kernel<<<1, 256, 0, st>>>(partials, nb, 2, sums);
     return cudaGetLastError();
 }
 

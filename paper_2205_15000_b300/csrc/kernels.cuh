@@ -132,12 +132,17 @@ int sweep_occupancy_f64(int ept, int block_threads, int stepper, bool weighted);
 cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
                                const BackLine *bl, const GridDev &grid, const uint8_t *mask,
                                const void *image_out, double *acc, cudaStream_t s);
+// Reductions over the grid finish in a fixed order (per-block partials, then
+// one block): the sums do not depend on scheduling.  partials: reduce_blocks(npts)
+// x 4 doubles of scratch.
+int reduce_blocks(int64_t npts);
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
                            const double *delta, const double *aind, double t, double normD,
                            double kappa, double *delta_new, double *j, double *F,
-                           double *sums /* [4]: num, den, Fsum, nonfinite */, cudaStream_t s);
+                           double *sums /* [4]: num, den, Fsum, nonfinite */, double *partials,
+                           cudaStream_t s);
 cudaError_t launch_mean_current(const GridDev &grid, const uint8_t *mask, const double *j,
-                                double *sums /* [2] */, cudaStream_t s);
+                                double *sums /* [2] */, double *partials, cudaStream_t s);
 cudaError_t launch_vector_potential(const GridDev &grid, const uint8_t *mask, const double *j,
                                     const double *jsum, double n_in, const double *G, int W,
                                     double inv_k2, double *aind, cudaStream_t s);

@@ -73,6 +73,20 @@ def test_accelerated_loop_matches_oracle(kind):
         np.testing.assert_allclose(w, acc.w_c, rtol=1e-8, atol=1e-12)
 
 
+def test_accelerated_loop_is_reproducible():
+    """Every reduction (residual, free energy, mean current, accelerator dot
+    products) finishes in a fixed order: two runs give bit-identical residual
+    histories and fields."""
+    p, d0 = _grain()
+    runs = []
+    for _ in range(2):
+        ctx, hist = _gpu_loop(p, d0, "barzilai-borwein", 12, precision="fp32")
+        ctx.sweep()
+        runs.append((hist, ctx.outputs()["F_total"]))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert runs[0][1] == runs[1][1]
+
+
 def test_accelerator_parameters_validated():
     from paper_2205_15000_b300 import sc
     p, d0 = _grain()

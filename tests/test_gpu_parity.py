@@ -212,6 +212,53 @@ def test_burnin_converges_boundary():
     np.testing.assert_allclose(ctx.exits(), o["exit"][0], atol=1e-9, rtol=0)
 
 
+def test_c1_plain_fp64_fifty_iterations_against_oracle():
+    """The small configuration (s-wave square side 20, 64^2, 32 angles, 16
+    energies, t = 0.5, no field, Delta = bulk (1 + 0.05 noise)): 50 Picard
+    iterations of the plain FP64 sweep against the oracle's, 1e-10."""
+    import torch
+    sc = _sc()
+    p, d0, _ = W.c1_square_s()
+    g = oracle.OracleGeom(p)
+    ref = g.picard(d0, 50)
+    ctx = sc.Context(p, precision="fp64")
+    ctx.set_fields(d0)
+    for _ in range(50):
+        ctx.sweep()
+        sc.sc_picard_step(ctx.h)
+    torch.cuda.synchronize()
+    ctx.sweep()
+    r = ctx.outputs()
+    o = g.full_sweep(ref["delta"], None, ref["exit"])
+    m = g.mask().astype(bool)
+    np.testing.assert_allclose(r["delta_new"].cpu().numpy()[m], o["delta_new"][m], atol=1e-10, rtol=0)
+    assert abs(r["F_total"] - o["F_total"]) < 1e-10
+    assert ref["history"][-1] < ref["history"][0]
+
+
+def test_c2_twenty_fp32_iterations_with_induced_field_against_oracle():
+    """The benchmark workload with its self-consistent induced field (kappa = 80):
+    20 Picard iterations (Delta <- Delta_new, A_ind <- from j) in FP32 against the
+    FP64 oracle's 20 iterations from the same inputs; the outputs of the 20th
+    sweep within the production tolerances."""
+    sc = _sc()
+    p, d0, _ = W.c2_diamond_d()
+    g = oracle.OracleGeom(p)
+    ref = g.picard(d0, 20)
+    ctx = sc.Context(p, precision="fp32")
+    ctx.set_fields(d0)
+    for it in range(20):
+        ctx.sweep()
+        if it < 19:
+            sc.sc_picard_step(ctx.h)
+    r = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ctx.outputs().items()}
+    o = ref["last"]
+    m = g.mask().astype(bool)
+    assert _rel(r["delta_new"][m], o["delta_new"][m]) < TOL_DELTA
+    assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
+    assert _rel(r["F"][m], o["F"][m]) < TOL_F
+
+
 def test_c2_full_size_fp32_against_oracle():
     """The benchmark workload (d-wave 45-degree square, 256^2, 128 angles, 80
     energies, 0.5 flux quanta): two FP32 sweeps against the oracle."""
