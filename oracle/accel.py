@@ -128,10 +128,14 @@ class Accelerator:
 
 
 def pack(delta, aind, mask, kappa):
-    """x from the grid fields: Delta over the grain points, kappa^2 A_ind over
-    the whole grid (the induced potential is a field on every grid point)."""
+    """x from the grid fields: Delta over the grain points (Re and Im of each
+    order-parameter component), kappa^2 A_ind over the whole grid (the induced
+    potential is a field on every grid point)."""
     m = mask.astype(bool)
-    x = [np.ascontiguousarray(delta[m].real), np.ascontiguousarray(delta[m].imag)]
+    comps = delta if np.ndim(delta) == 3 else [delta]
+    x = []
+    for dc in comps:
+        x += [np.ascontiguousarray(dc[m].real), np.ascontiguousarray(dc[m].imag)]
     if aind is not None and kappa > 0 and math.isfinite(kappa):
         x += [kappa ** 2 * aind[..., 0].ravel(), kappa ** 2 * aind[..., 1].ravel()]
     return x
@@ -143,9 +147,12 @@ def unpack(x, delta_like, aind_like, mask, kappa):
     point)."""
     m = mask.astype(bool)
     delta = np.array(delta_like, dtype=np.complex128)
-    delta[m] = x[0] + 1j * x[1]
+    nc = delta.shape[0] if delta.ndim == 3 else 1
+    for c in range(nc):
+        dc = delta[c] if delta.ndim == 3 else delta
+        dc[m] = x[2 * c] + 1j * x[2 * c + 1]
     aind = None if aind_like is None else np.array(aind_like, dtype=np.float64)
-    if len(x) == 4:
-        aind[..., 0] = (x[2] / kappa ** 2).reshape(aind.shape[:2])
-        aind[..., 1] = (x[3] / kappa ** 2).reshape(aind.shape[:2])
+    if len(x) == 2 * nc + 2:
+        aind[..., 0] = (x[2 * nc] / kappa ** 2).reshape(aind.shape[:2])
+        aind[..., 1] = (x[2 * nc + 1] / kappa ** 2).reshape(aind.shape[:2])
     return delta, aind

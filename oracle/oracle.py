@@ -61,6 +61,7 @@ class _Params(ctypes.Structure):
         ("n_angles", ctypes.c_int32), ("n_energies", ctypes.c_int32),
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
         ("stepper", ctypes.c_int32),
+        ("n_components", ctypes.c_int32), ("pairings", ctypes.c_int32 * 4), ("tc_ratios", ctypes.c_double * 4),
     ]
 
 
@@ -165,9 +166,20 @@ class OracleGeom:
             if name == "stepper":
                 s.stepper = STEPPERS[prm.get("stepper", "closed")]
                 continue
+            if name in ("n_components", "pairings", "tc_ratios"):
+                continue
+            if name == "pairing" and prm.get("components"):
+                s.pairing = int(prm["components"][0][0])
+                continue
             setattr(s, name, prm[name])
         s.vx = vx.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         s.vy = vy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        comps = prm.get("components") or [(prm["pairing"], 1.0)]
+        s.n_components = len(comps)
+        for c, (pairing, tcr) in enumerate(comps):
+            s.pairings[c] = int(pairing)
+            s.tc_ratios[c] = float(tcr)
+        self.C = len(comps)
         self._s = s
         h = L.or_geom_create(ctypes.byref(s))
         if not h:
@@ -306,23 +318,25 @@ class OracleGeom:
 
     def rotate_back(self, images, mode=0, n_e=None):
         n_e = n_e if n_e is not None else self.n_e
-        nout = 5 if mode == 0 else n_e
+        nout = 3 + 2 * self.C if mode == 0 else n_e
         acc = np.zeros(nout * self.nx * self.ny)
         im = np.ascontiguousarray(images, np.float64)
         lib().or_rotate_back(self._h, _p(im), int(mode), int(n_e), _p(acc))
         return acc.reshape(nout, self.ny, self.nx)
 
     def outputs(self, acc, delta, aind):
+        """Delta_new (per component: [C, ny, nx] when C > 1), j, F(R), F_total, eps_G."""
         d = _cplx_to_f64(delta)
         a = None if aind is None else np.ascontiguousarray(aind, np.float64)
         npts = self.nx * self.ny
-        dn = np.zeros(2 * npts)
+        dn = np.zeros(2 * npts * self.C)
         j = np.zeros(2 * npts)
         F = np.zeros(npts)
         sc = np.zeros(2)
         accf = np.ascontiguousarray(acc, np.float64)
         lib().or_outputs(self._h, _p(accf), _p(d), _p(a), _p(dn), _p(j), _p(F), _p(sc))
-        return dict(delta_new=dn.view(np.complex128).reshape(self.ny, self.nx),
+        shape = (self.C, self.ny, self.nx) if self.C > 1 else (self.ny, self.nx)
+        return dict(delta_new=dn.view(np.complex128).reshape(shape),
                     j=j.reshape(self.ny, self.nx, 2), F=F.reshape(self.ny, self.nx),
                     F_total=float(sc[0]), eps_G=float(sc[1]))
 

@@ -64,7 +64,10 @@ struct or_geom {
     int npair, N;
     double *w;              /* [N] quadrature weights */
     double *vh;             /* [N][2] Fermi velocity directions */
-    double *eta;            /* [N] basis function */
+    double *eta;            /* [N] basis function of component 0 (= eta_c) */
+    double *eta_c;          /* [C][N] basis functions of the components */
+    int C;                  /* order-parameter components */
+    double tcr[4];          /* T_c^Gamma / T_c */
     double *ewt;            /* [n_energies] weights of the energy sums, NULL = 1 (Matsubara) */
     double normD;           /* gap-equation normalisation when ewt is set */
     /* per pair */
@@ -266,11 +269,11 @@ static double polygon_area(int n, const double *x, const double *y) {
 
 void or_geom_free(or_geom *g) {
     if (!g) return;
-    void *ptrs[] = {g->vx, g->vy, g->nxe, g->nye, g->mask, g->ghost, g->w, g->vh, g->eta,
+    void *ptrs[] = {g->vx, g->vy, g->nxe, g->nye, g->mask, g->ghost, g->w, g->vh, /* eta is eta_c */
                     g->l_lo, g->l_hi, g->line_off, g->samp_off, g->smin, g->smax, g->m0,
                     g->m1, g->ns, g->edge_lo, g->edge_hi, g->soff, g->nearest_line,
                     g->lk_g_angle, g->lk_g_line, g->lk_g_w, g->lk_t_angle, g->lk_t_line,
-                    g->lk_t_w, g->ang_line_off, g->ang_samp_off, g->ewt};
+                    g->lk_t_w, g->ang_line_off, g->ang_samp_off, g->ewt, g->eta_c};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(g);
 }
@@ -281,6 +284,7 @@ or_geom *or_geom_create(const or_params *prm) {
     if (prm->n_angles < 2 || prm->n_angles % 2) { fail("n_angles must be even"); return NULL; }
     if (prm->n_energies < 1) { fail("n_energies < 1"); return NULL; }
     if (prm->stepper != 0 && prm->stepper != 1) { fail("stepper must be 0 or 1"); return NULL; }
+    if (prm->n_components < 0 || prm->n_components > 4) { fail("1 to 4 components"); return NULL; }
     if (!(prm->t > 0 && prm->t <= 1)) { fail("t out of (0,1]"); return NULL; }
     if (prm->shape_kind == 1 && (prm->n_vert < 3 || !prm->vx || !prm->vy)) {
         fail("polygon needs >= 3 vertices");
@@ -379,7 +383,10 @@ or_geom *or_geom_create(const or_params *prm) {
     g->npair = np;
     g->w = malloc(sizeof(double) * N);
     g->vh = malloc(sizeof(double) * 2 * N);
-    g->eta = malloc(sizeof(double) * N);
+    g->C = prm->n_components > 1 ? prm->n_components : 1;
+    g->eta_c = malloc(sizeof(double) * N * g->C);
+    g->eta = g->eta_c;
+    for (int c = 0; c < g->C; ++c) g->tcr[c] = prm->tc_ratios[c] > 0 ? prm->tc_ratios[c] : 1.0;
     for (int k = 0; k < np; ++k) {
         double phi = 2.0 * M_PI * k / N;
         g->vh[2 * k] = cos(phi);
@@ -389,7 +396,9 @@ or_geom *or_geom_create(const or_params *prm) {
     }
     for (int k = 0; k < N; ++k) {
         g->w[k] = or_quad_weight(k, N);
-        g->eta[k] = basis_eta(prm->pairing, prm->crystal_rotation, g->vh[2 * k], g->vh[2 * k + 1]);
+        for (int c = 0; c < g->C; ++c)
+            g->eta_c[(size_t)c * N + k] = basis_eta(c == 0 ? prm->pairing : prm->pairings[c], prm->crystal_rotation,
+                                                    g->vh[2 * k], g->vh[2 * k + 1]);
     }
 
     /* lattice origin: grid-box centre plus the offset (units of h) */
@@ -715,6 +724,18 @@ void or_step(const double *P, const double *Q, const double *R, double ell, cons
     gb[1] = cimag(r);
 }
 
+/* Delta(p, R) = sum_c eta_c(p) Delta_c(R) on the grid (complex, npts). */
+static double *combined_field(const or_geom *g, const double *delta, int p) {
+    size_t npts = (size_t)g->P.nx * g->P.ny;
+    double *f = calloc(2 * npts, sizeof(double));
+    for (int c = 0; c < g->C; ++c) {
+        double e = g->eta_c[(size_t)c * g->N + p];
+        const double *dc = delta + 2 * npts * c;
+        for (size_t i = 0; i < 2 * npts; ++i) f[i] += e * dc[i];
+    }
+    return f;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Sweep                                                                  */
 /* ---------------------------------------------------------------------- */
@@ -728,13 +749,22 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
     int sgc = g->P.charge_sign;
     int err = 0;
 
-    /* sample fields of every pair */
+    /* sample fields of every pair; with several components the sampled field is
+       Delta(p, R) = sum_c eta_c(p) Delta_c(R) (Eq. order_parameter; the basis
+       functions are even, eta(p + pi) = eta(p)), formed on the grid first since
+       bilinear sampling is linear */
     double **dS = malloc(sizeof(double *) * np), **aS = malloc(sizeof(double *) * np);
+    double **comb = calloc(np, sizeof(double *));
     for (int p = 0; p < np; ++p) {
         int ns = g->samp_off[p + 1] - g->samp_off[p];
         dS[p] = malloc(sizeof(double) * 2 * (ns > 0 ? ns : 1));
         aS[p] = malloc(sizeof(double) * 2 * (ns > 0 ? ns : 1));
-        if (or_sample_fields(g, delta, aind, p, dS[p], aS[p])) err = 1;
+        if (g->C > 1) {
+            comb[p] = combined_field(g, delta, p);
+            if (or_sample_fields(g, comb[p], aind, p, dS[p], aS[p])) err = 1;
+        } else if (or_sample_fields(g, delta, aind, p, dS[p], aS[p])) {
+            err = 1;
+        }
     }
     if (err) goto done;
 
@@ -749,7 +779,8 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
             int L = gline(g, p, l);
             int sg = k < np ? 1 : -1;
             double vx = g->vh[2 * k], vy = g->vh[2 * k + 1];
-            double eta = g->eta[k];
+            double eta = g->C > 1 ? 1.0 : g->eta[k];  /* combined fields already carry eta */
+            const double *dfield = g->C > 1 ? comb[p] : delta;
             int ns = g->ns[L];
             int m0 = g->m0[L], m1 = g->m1[L];
             /* coefficient of each segment in travel order: Delta(p,R) and a = sigma v.A */
@@ -772,7 +803,7 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                 double smid = 0.5 * (g->smin[L] + g->smax[L]);
                 double x = g->Ox - l * h * ey + smid * ex, y = g->Oy + l * h * ex + smid * ey;
                 double dd[2] = {0.0, 0.0}, AA[2] = {0.0, 0.0};
-                if (interp2(g, delta, x, y, dd) || a_total(g, aind, x, y, AA)) {
+                if (interp2(g, dfield, x, y, dd) || a_total(g, aind, x, y, AA)) {
 #pragma omp atomic write
                     err = 1;
                 }
@@ -892,7 +923,9 @@ done:
     for (int p = 0; p < np; ++p) {
         free(dS[p]);
         free(aS[p]);
+        free(comb[p]);
     }
+    free(comb);
     free(dS);
     free(aS);
     if (err) return fail("sample outside grid");
@@ -906,7 +939,7 @@ int or_rotate_back(const or_geom *g, const double *images, int mode, int n_e, do
     int nx = g->P.nx, ny = g->P.ny, N = g->N, np = g->npair;
     double h = g->P.h;
     int nv = mode == 0 ? 4 : n_e;
-    int nout = mode == 0 ? 5 : n_e;
+    int nout = mode == 0 ? 3 + 2 * g->C : n_e;
     size_t npts = (size_t)nx * ny;
     memset(acc, 0, sizeof(double) * nout * npts);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -940,11 +973,17 @@ int or_rotate_back(const or_geom *g, const double *images, int mode, int n_e, do
             }
             double wk = g->w[k];
             if (mode == 0) {
+                /* planes: <eta_0 Sf> (2), <v Sg> (2), <SF>, then <eta_c Sf> (2 per c >= 1) */
                 acc[0 * npts + idx] += wk * g->eta[k] * X[0];
                 acc[1 * npts + idx] += wk * g->eta[k] * X[1];
                 acc[2 * npts + idx] += wk * g->vh[2 * k] * X[2];
                 acc[3 * npts + idx] += wk * g->vh[2 * k + 1] * X[2];
                 acc[4 * npts + idx] += wk * X[3];
+                for (int c = 1; c < g->C; ++c) {
+                    double e = g->eta_c[(size_t)c * N + k];
+                    acc[(3 + 2 * c) * npts + idx] += wk * e * X[0];
+                    acc[(4 + 2 * c) * npts + idx] += wk * e * X[1];
+                }
             } else {
                 for (int c = 0; c < n_e; ++c) acc[c * npts + idx] += wk * X[c];
             }
@@ -971,23 +1010,33 @@ int or_outputs(const or_geom *g, const double *acc, const double *delta, const d
     double Fsum = 0.0, num = 0.0, den = 0.0;
     for (size_t idx = 0; idx < npts; ++idx) {
         if (!g->mask[idx]) {
-            delta_new[2 * idx] = delta_new[2 * idx + 1] = 0.0;
+            for (int c = 0; c < g->C; ++c) delta_new[2 * (c * npts + idx)] = delta_new[2 * (c * npts + idx) + 1] = 0.0;
             jout[2 * idx] = jout[2 * idx + 1] = 0.0;
             F[idx] = 0.0;
             continue;
         }
         int i = (int)(idx % nx), j = (int)(idx / nx);
-        /* Delta = T sum_n <eta f> / D, T = t/(2 pi) in units of 2 pi kB Tc */
-        double dr = t / (2.0 * M_PI) * acc[idx] / D;
-        double di = t / (2.0 * M_PI) * acc[npts + idx] / D;
-        delta_new[2 * idx] = dr;
-        delta_new[2 * idx + 1] = di;
+        /* component c (Eq. gapeq_fixpoint): Delta_c = T sum_n <eta_c f> / D_c,
+           D_c = ln(T/T_c^c) + pi T sum 1/|eps_n| = D - ln(T_c^c/T_c), T = t/(2 pi) */
+        double f = -0.5 * t * acc[4 * npts + idx];
+        for (int c = 0; c < g->C; ++c) {
+            double Dc = D - log(g->tcr[c]);
+            size_t pr = c == 0 ? 0 : (size_t)(3 + 2 * c), pi_ = c == 0 ? 1 : (size_t)(4 + 2 * c);
+            double dr = t / (2.0 * M_PI) * acc[pr * npts + idx] / Dc;
+            double di = t / (2.0 * M_PI) * acc[pi_ * npts + idx] / Dc;
+            size_t o = 2 * (c * npts + idx);
+            delta_new[o] = dr;
+            delta_new[o + 1] = di;
+            /* F(R) = sum_c |Delta_c|^2 D_c - (t/2) <SF> + (kappa^2/2) |B_ind|^2 */
+            double d2 = delta[o] * delta[o] + delta[o + 1] * delta[o + 1];
+            f += d2 * Dc;
+            double er = dr - delta[o], ei = di - delta[o + 1];
+            num += er * er + ei * ei;
+            den += d2;
+        }
         /* j = 2 e N_F T sum_n <v g>  ->  sigma (t/pi) <v Sg> in units of j0 */
         jout[2 * idx] = sgc * t / M_PI * acc[2 * npts + idx];
         jout[2 * idx + 1] = sgc * t / M_PI * acc[3 * npts + idx];
-        /* F(R) = |Delta|^2 D - (t/2) <SF> + (kappa^2/2) |B_ind|^2 */
-        double d2 = delta[2 * idx] * delta[2 * idx] + delta[2 * idx + 1] * delta[2 * idx + 1];
-        double f = d2 * D - 0.5 * t * acc[4 * npts + idx];
         if (magn) {
             /* B_ind = dAy/dx - dAx/dy, central differences (one-sided at the grid edge) */
             int ia = i > 0 ? i - 1 : i, ib = i < nx - 1 ? i + 1 : i;
@@ -1001,9 +1050,6 @@ int or_outputs(const or_geom *g, const double *acc, const double *delta, const d
         }
         F[idx] = f;
         Fsum += f;
-        double er = dr - delta[2 * idx], ei = di - delta[2 * idx + 1];
-        num += er * er + ei * ei;
-        den += d2;
     }
     scalars[0] = Fsum / (double)g->n_in;
     scalars[1] = den > 0 ? sqrt(num / den) : 0.0;
@@ -1118,12 +1164,15 @@ int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, c
         int nsp = g->samp_off[p + 1] - g->samp_off[p];
         double *dS = malloc(sizeof(double) * 2 * (nsp > 0 ? nsp : 1));
         double *aS = malloc(sizeof(double) * 2 * (nsp > 0 ? nsp : 1));
-        if (or_sample_fields(g, delta, aind, p, dS, aS)) {
+        double *comb = g->C > 1 ? combined_field(g, delta, p) : NULL;
+        int bad = or_sample_fields(g, comb ? comb : delta, aind, p, dS, aS);
+        free(comb);
+        if (bad) {
             free(dS);
             free(aS);
             return -1;
         }
-        double vx = g->vh[2 * k], vy = g->vh[2 * k + 1], eta = g->eta[k];
+        double vx = g->vh[2 * k], vy = g->vh[2 * k + 1], eta = g->C > 1 ? 1.0 : g->eta[k];
         int nl = g->l_hi[p] - g->l_lo[p] + 1;
 #pragma omp parallel for schedule(dynamic, 1)
         for (int li = 0; li < nl; ++li) {

@@ -22,7 +22,9 @@
  *   - local density of states                                  (Sec. 2, LDOS definition)
  * Units: lengths xi0, energies 2 pi kB Tc, A in Phi0/(pi xi0), j in j0.
  * Grid arrays are row-major [ny][nx]; complex and 2-vector grids interleave
- * their two components per point.
+ * their two components per point.  With several order-parameter components,
+ * Delta and Delta_new are [n_components][ny][nx] complex, and the mode-0
+ * accumulators gain two planes per component beyond the first.
  */
 #ifndef SC_ORACLE_H
 #define SC_ORACLE_H
@@ -47,6 +49,10 @@ typedef struct {
     double lattice_ox, lattice_oy; /* lattice origin offset from the grid centre, units of h */
     int32_t stepper;         /* 0 = closed-form step for piecewise-constant coefficients,
                                 1 = implicit midpoint rule (App. C, Eq. riccati_midpoint) */
+    int32_t n_components;    /* order-parameter components Delta_Gamma (Eq. order_parameter):
+                                0 or 1 = one (`pairing`), at most 4 */
+    int32_t pairings[4];     /* basis of component c >= 1 (component 0 uses `pairing`) */
+    double tc_ratios[4];     /* T_c^Gamma / T_c of each component (0 means 1) */
 } or_params;
 
 typedef struct or_geom or_geom;
