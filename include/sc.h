@@ -97,6 +97,15 @@ typedef struct {
     int32_t energy_sum;      /* sc_energy_sum: which energies and weights the Matsubara
                                 sums use; with SC_SUM_OZAKI, n_energies is the number of
                                 Ozaki poles (at most 1024) */
+    int32_t n_components;    /* order-parameter components Delta_Gamma (Eq. order_parameter,
+                                Delta(p, R) = sum_Gamma Delta_Gamma(R) eta_Gamma(p)): 0 or 1
+                                = one component (`pairing`), at most 4.  Delta (sc_set_fields)
+                                and Delta_new (sc_gap_update) are then
+                                [n_components][ny][nx] complex. */
+    int32_t pairings[4];     /* sc_pairing of components 1 .. n_components-1 (component 0
+                                uses `pairing`) */
+    double tc_ratios[4];     /* T_c^Gamma / T_c per component (Eq. gapeq_regularized);
+                                0 means 1 */
 } sc_params;
 
 typedef struct {
@@ -187,9 +196,9 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream);
 sc_status sc_picard_step(sc_ctx *ctx, void *stream);
 
 /* ---- self-consistency accelerators (App. E) ----------------------------
-   The unknowns x = (Re Delta, Im Delta, kappa^2 A_x, kappa^2 A_y) (Eq. x_concat):
-   Delta over the grain's grid points, A_ind over the whole grid (only when
-   kappa > 0 is finite).  g(x) = (Delta_new, kappa^2 A from j) of the last sweep,
+   The unknowns x = (Re Delta, Im Delta, kappa^2 A_x, kappa^2 A_y) (Eq. x_concat;
+   Re and Im of every order-parameter component): Delta over the grain's grid
+   points, A_ind over the whole grid (only when kappa > 0 is finite).  g(x) = (Delta_new, kappa^2 A from j) of the last sweep,
    d = g(x) - x (Eq. difference).  Each call of sc_accelerate takes one step:
      PICARD            x += alpha d                                  (Eq. picard)
      POLYAK            v = (1 - beta) v + alpha d, x += v; v starts at 0
@@ -228,8 +237,9 @@ sc_status sc_accel_params_default(int32_t kind, sc_accel_params *p);
 sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream);
 sc_status sc_accel_reset(sc_ctx *ctx);
 /* Accelerator history: steps taken, step sizes (BB/Picard/Polyak: alpha in
-   [0]; CongAcc: alpha_c for c = Re Delta, Im Delta, A_x, A_y) and CongAcc's
-   weights w_c; alpha and w may be NULL. */
+   [0]; CongAcc: alpha_c for c = Re Delta_0, Im Delta_0, ..., Re Delta_{C-1},
+   Im Delta_{C-1}, A_x, A_y, i.e. 2 n_components + 2 entries) and CongAcc's
+   weights w_c (same layout); alpha and w may be NULL. */
 sc_status sc_accel_get_state(const sc_ctx *ctx, int32_t *iterations, double *alpha, double *w);
 
 /* Local density of states N(R, eps)/N_F = -<Im g^R(eps + i broadening)>/pi

@@ -9,22 +9,26 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// component c of x and g at point i; false when the component does not exist there
+// component c of x and g at point i (Re, Im of each Delta component, then the
+// two A components); false when the component does not exist there
 __device__ __forceinline__ bool comp(const AccelArgs &a, int c, int64_t i, double &x, double &g) {
-    if (c < 2) {
+    const int nd = 2 * a.nc;
+    if (c < nd) {
         if (!a.mask[i]) return false;
-        x = a.delta[2 * i + c];
-        g = a.dnew[2 * i + c];
+        const int64_t o = 2 * ((c >> 1) * a.npts + i) + (c & 1);
+        x = a.delta[o];
+        g = a.dnew[o];
         return true;
     }
-    if (!a.aind) return false;
-    x = a.k2 * a.aind[2 * i + (c - 2)];
-    g = a.k2 * a.anew[2 * i + (c - 2)];
+    if (!a.aind || c >= nd + 2) return false;
+    x = a.k2 * a.aind[2 * i + (c - nd)];
+    g = a.k2 * a.anew[2 * i + (c - nd)];
     return true;
 }
 
 // Slots: 0 |dprev|^2, 1 dprev.(d - dprev), 2 |d - dprev|^2 (Barzilai-Borwein, all
 // components); 3 + 3c + {0, 1, 2} = m_c.d_c, |m_c|^2, |d_c|^2 (CongAcc, component c).
+// kAccelSums doubles per thread: the block reduction runs slot by slot.
 __global__ void accel_partials_kernel(AccelArgs a, double *__restrict__ partials) {
     double s[kAccelSums];
 #pragma unroll
@@ -32,7 +36,7 @@ __global__ void accel_partials_kernel(AccelArgs a, double *__restrict__ partials
     const int64_t n = a.npts;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < kAccelComps; ++c) {
             double x, g;
             if (!comp(a, c, i, x, g)) continue;
             const double d = g - x;
@@ -73,7 +77,7 @@ __global__ void accel_final_kernel(const double *__restrict__ partials, int bloc
 }
 
 struct Steps {
-    double alpha, beta, ac[4], wc[4];
+    double alpha, beta, ac[kAccelComps], wc[kAccelComps];
 };
 
 __global__ void accel_update_kernel(AccelArgs a, int kind, Steps st) {
@@ -81,7 +85,7 @@ __global__ void accel_update_kernel(AccelArgs a, int kind, Steps st) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kAccelComps; ++c) {
         double x, g;
         if (!comp(a, c, i, x, g)) continue;
         const double d = g - x;
@@ -98,10 +102,10 @@ __global__ void accel_update_kernel(AccelArgs a, int kind, Steps st) {
             if (kind == 2) a.dprev[c * n + i] = d;
             xn = x + st.alpha * d;
         }
-        if (c < 2)
-            a.delta[2 * i + c] = xn;
+        if (c < 2 * a.nc)
+            a.delta[2 * ((c >> 1) * n + i) + (c & 1)] = xn;
         else
-            a.aind[2 * i + (c - 2)] = xn / a.k2;
+            a.aind[2 * i + (c - 2 * a.nc)] = xn / a.k2;
     }
 }
 
@@ -124,7 +128,7 @@ cudaError_t launch_accel_update(const AccelArgs &a, int kind, double alpha, doub
     Steps st{};
     st.alpha = alpha;
     st.beta = beta;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kAccelComps; ++c) {
         st.ac[c] = alpha_c ? alpha_c[c] : 0.0;
         st.wc[c] = w_c ? w_c[c] : 0.0;
     }

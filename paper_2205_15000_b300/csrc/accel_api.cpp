@@ -87,7 +87,8 @@ sc_status sc_accel_reset(sc_ctx *ctx) {
 sc_status sc_accel_get_state(const sc_ctx *ctx, int32_t *iterations, double *alpha, double *w) {
     if (!ctx) return SC_EINVAL;
     if (iterations) *iterations = ctx->acc_kind < 0 ? 0 : (int32_t)ctx->acc_iter;
-    for (int c = 0; c < 4; ++c) {
+    const int ncomp = 2 * ctx->geo.n_comp + 2;
+    for (int c = 0; c < ncomp; ++c) {
         if (alpha) alpha[c] = ctx->acc_kind == SC_ACC_CONGACC ? ctx->acc_alpha_c[c] : (c == 0 ? ctx->acc_alpha : 0.0);
         if (w) w[c] = ctx->acc_kind == SC_ACC_CONGACC ? ctx->acc_w_c[c] : 0.0;
     }
@@ -115,25 +116,26 @@ sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream) {
                                          ctx->d_G, ctx->G_width, 1.0 / (kappa * kappa), ctx->d_anew, st));
     }
     const int blocks = scd::accel_reduce_blocks(n, ctx->sm_count);
-    ACK(alloc_once(ctx, &ctx->d_acc_v, 4 * n * sizeof(double)));
-    ACK(alloc_once(ctx, &ctx->d_acc_prev, 4 * n * sizeof(double)));
-    ACK(alloc_once(ctx, &ctx->d_acc_m, 4 * n * sizeof(double)));
+    ACK(alloc_once(ctx, &ctx->d_acc_v, scd::kAccelComps * n * sizeof(double)));
+    ACK(alloc_once(ctx, &ctx->d_acc_prev, scd::kAccelComps * n * sizeof(double)));
+    ACK(alloc_once(ctx, &ctx->d_acc_m, scd::kAccelComps * n * sizeof(double)));
     ACK(alloc_once(ctx, &ctx->d_acc_part, (size_t)blocks * scd::kAccelSums * sizeof(double)));
     ACK(alloc_once(ctx, &ctx->d_acc_sums, scd::kAccelSums * sizeof(double)));
     if (ctx->acc_kind != p->kind) {  // a new history
-        ACK(cudaMemsetAsync(ctx->d_acc_v, 0, 4 * n * sizeof(double), st));
-        ACK(cudaMemsetAsync(ctx->d_acc_prev, 0, 4 * n * sizeof(double), st));
-        ACK(cudaMemsetAsync(ctx->d_acc_m, 0, 4 * n * sizeof(double), st));
+        ACK(cudaMemsetAsync(ctx->d_acc_v, 0, scd::kAccelComps * n * sizeof(double), st));
+        ACK(cudaMemsetAsync(ctx->d_acc_prev, 0, scd::kAccelComps * n * sizeof(double), st));
+        ACK(cudaMemsetAsync(ctx->d_acc_m, 0, scd::kAccelComps * n * sizeof(double), st));
         ctx->acc_kind = p->kind;
         ctx->acc_iter = 0;
         ctx->acc_alpha = p->step_size;
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < scd::kAccelComps; ++c) {
             ctx->acc_alpha_c[c] = p->step_size;
             ctx->acc_w_c[c] = 0.0;
         }
     }
     scd::AccelArgs a{};
     a.npts = n;
+    a.nc = ctx->geo.n_comp;
     a.mask = ctx->d_mask;
     a.delta = ctx->d_delta;
     a.aind = magn ? ctx->d_aind : nullptr;
@@ -156,7 +158,7 @@ sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream) {
             const double num = bb1 ? s[0] : q, den = bb1 ? q : s[2];
             if (den > 0.0) ctx->acc_alpha = clamp(ctx->acc_alpha * num / den, p);
         } else {
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < scd::kAccelComps; ++c) {
                 const double md = s[3 + 3 * c], mm = s[4 + 3 * c], dd = s[5 + 3 * c];
                 if (!(mm > 0.0) || !(dd > 0.0)) continue;  // component absent or at rest
                 const double sim = md / std::sqrt(mm * dd);

@@ -43,7 +43,7 @@ __device__ __forceinline__ void atomic_add4(typename Vec4<T>::type *p, T a, T b,
 // Delta and A_ind terms of the free energy)
 __global__ void adjoint_outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
                                        const double *__restrict__ delta, const double *__restrict__ aind,
-                                       double t, double normD, double kappa, double n_in,
+                                       double t, CompNorm normD, double kappa, double n_in,
                                        const double *__restrict__ gdn, const double *__restrict__ gj,
                                        const double *__restrict__ gF, double gFtot, double *__restrict__ gacc,
                                        double *__restrict__ gdelta, double *__restrict__ gaind) {
@@ -52,11 +52,16 @@ __global__ void adjoint_outputs_kernel(GridDev grid, const uint8_t *__restrict__
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= npts) return;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    double ac[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // components c >= 1: cotangents of <eta_c Sf>
     if (mask[idx]) {
-        const double cd = t / (2.0 * 3.141592653589793) / normD;
         if (gdn) {
-            a0 = cd * gdn[2 * idx];
-            a1 = cd * gdn[2 * idx + 1];
+            for (int c = 0; c < grid.n_comp; ++c) {
+                const double cd = t / (2.0 * 3.141592653589793) / normD.D[c];
+                ac[2 * c] = cd * gdn[2 * (c * npts + idx)];
+                ac[2 * c + 1] = cd * gdn[2 * (c * npts + idx) + 1];
+            }
+            a0 = ac[0];
+            a1 = ac[1];
         }
         if (gj) {
             const double cj = grid.charge_sign * t / 3.141592653589793;
@@ -65,9 +70,12 @@ __global__ void adjoint_outputs_kernel(GridDev grid, const uint8_t *__restrict__
         }
         const double fb = (gF ? gF[idx] : 0.0) + gFtot / n_in;
         a4 = -0.5 * t * fb;
-        // F = |Delta|^2 D + ...: direct term
-        atomicAdd(&gdelta[2 * idx], 2.0 * normD * fb * delta[2 * idx]);
-        atomicAdd(&gdelta[2 * idx + 1], 2.0 * normD * fb * delta[2 * idx + 1]);
+        // F = sum_c |Delta_c|^2 D_c + ...: direct terms
+        for (int c = 0; c < grid.n_comp; ++c) {
+            const int64_t o = 2 * (c * npts + idx);
+            atomicAdd(&gdelta[o], 2.0 * normD.D[c] * fb * delta[o]);
+            atomicAdd(&gdelta[o + 1], 2.0 * normD.D[c] * fb * delta[o + 1]);
+        }
         if (aind && kappa > 0.0 && fb != 0.0) {
             const int i = (int)(idx % nx), j = (int)(idx / nx);
             const int ia = i > 0 ? i - 1 : i, ib = i < nx - 1 ? i + 1 : i;
@@ -87,6 +95,10 @@ __global__ void adjoint_outputs_kernel(GridDev grid, const uint8_t *__restrict__
     gacc[2 * npts + idx] = a2;
     gacc[3 * npts + idx] = a3;
     gacc[4 * npts + idx] = a4;
+    for (int c = 1; c < grid.n_comp; ++c) {
+        gacc[(3 + 2 * c) * npts + idx] = ac[2 * c];
+        gacc[(4 + 2 * c) * npts + idx] = ac[2 * c + 1];
+    }
 }
 
 // transpose of rotate_back: scatter the accumulator cotangents onto the slots
@@ -100,11 +112,20 @@ __global__ void adjoint_rotate_back_kernel(const PairDev *__restrict__ pairs, in
     if (idx >= npts || !mask[idx]) return;
     const double g0 = gacc[idx], g1 = gacc[npts + idx], g2 = gacc[2 * npts + idx], g3 = gacc[3 * npts + idx],
                  g4 = gacc[4 * npts + idx];
+    double gc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = 1; c < grid.n_comp; ++c) {
+        gc[2 * c] = gacc[(3 + 2 * c) * npts + idx];
+        gc[2 * c + 1] = gacc[(4 + 2 * c) * npts + idx];
+    }
     const double fi = (double)(idx % grid.nx), fj = (double)(idx / grid.nx);
     for (int p = 0; p < n_pairs; ++p) {
         const PairDev pp = pairs[p];
         const double ws = pp.wa + pp.wb;
-        const double wf0 = ws * pp.eta * g0, wf1 = ws * pp.eta * g1;
+        double wf0 = ws * pp.eta * g0, wf1 = ws * pp.eta * g1;
+        for (int c = 1; c < grid.n_comp; ++c) {  // S_f enters every component's plane
+            wf0 += ws * pp.eta_c[c] * gc[2 * c];
+            wf1 += ws * pp.eta_c[c] * gc[2 * c + 1];
+        }
         const double wg = ws * (pp.ex * g2 + pp.ey * g3), wF = ws * g4;
         const double u = fma(fi, -pp.ey, fma(fj, pp.ex, pp.u0));
         const double v = fma(fi, pp.ex, fma(fj, pp.ey, pp.v0));
@@ -214,6 +235,12 @@ __global__ void adjoint_rotate_kernel(const LineGeo *__restrict__ geo, const int
             if (src < 0 || w == 0.0) continue;
             atomicAdd(&gdelta[2 * (int64_t)src], w * pp.eta * gdr);
             atomicAdd(&gdelta[2 * (int64_t)src + 1], w * pp.eta * gdi);
+            // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample)
+            const int64_t npts = (int64_t)grid.nx * grid.ny;
+            for (int c = 1; c < grid.n_comp; ++c) {
+                atomicAdd(&gdelta[2 * (c * npts + src)], w * pp.eta_c[c] * gdr);
+                atomicAdd(&gdelta[2 * (c * npts + src) + 1], w * pp.eta_c[c] * gdi);
+            }
             if (gaind) {
                 atomicAdd(&gaind[2 * (int64_t)src], w * sa * pp.ex);
                 atomicAdd(&gaind[2 * (int64_t)src + 1], w * sa * pp.ey);
@@ -232,7 +259,7 @@ int adjoint_occupancy(bool fp64, int ept, int bs, int stepper) {
 }
 
 cudaError_t launch_adjoint_outputs(const GridDev &grid, const uint8_t *mask, const double *delta,
-                                   const double *aind, double t, double normD, double kappa, double n_in,
+                                   const double *aind, double t, const CompNorm &normD, double kappa, double n_in,
                                    const double *gdn, const double *gj, const double *gF, double gFtot,
                                    double *gacc, double *gdelta, double *gaind, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;

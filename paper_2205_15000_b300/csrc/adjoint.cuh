@@ -32,7 +32,7 @@ cudaError_t launch_adjoint_sweep_f64(const AdjointLaunch &a, cudaStream_t s);
 int adjoint_occupancy_f32(int ept, int block_threads, int stepper);
 int adjoint_occupancy_f64(int ept, int block_threads, int stepper);
 cudaError_t launch_adjoint_outputs(const GridDev &grid, const uint8_t *mask, const double *delta,
-                                   const double *aind, double t, double normD, double kappa, double n_in,
+                                   const double *aind, double t, const CompNorm &normD, double kappa, double n_in,
                                    const double *gdn, const double *gj, const double *gF, double gFtot,
                                    double *gacc, double *gdelta, double *gaind, cudaStream_t s);
 cudaError_t launch_adjoint_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,

@@ -223,7 +223,7 @@ sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st) {
                               st));
     } else {
         const int64_t np = (int64_t)ctx->geo.nx * ctx->geo.ny;
-        CK(scd::launch_fields_f32(np, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_delta_f,
+        CK(scd::launch_fields_f32(np, ctx->geo.n_comp, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_delta_f,
                                   ctx->d_aind_f, st));
         CK(scd::launch_rotate_f32(ctx->d_line_f32, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pair_f32, ctx->grid,
                                   ctx->d_ghost, ctx->d_delta_f, ctx->d_aind_f, (float4 *)ctx->d_img_in, st));
@@ -279,7 +279,7 @@ sc_status ensure_outputs_impl(sc_ctx *ctx, cudaStream_t st) {
     const double kappa = ctx->geo.prm.kappa;
     const bool magn = kappa > 0.0 && std::isfinite(kappa) && ctx->have_aind;
     CK(scd::launch_outputs(ctx->grid, ctx->d_mask, ctx->d_acc, ctx->d_delta, magn ? ctx->d_aind : nullptr,
-                           ctx->geo.prm.t, ctx->normD, magn ? kappa : 0.0, ctx->d_dnew, ctx->d_j, ctx->d_F,
+                           ctx->geo.prm.t, ctx->norms, magn ? kappa : 0.0, ctx->d_dnew, ctx->d_j, ctx->d_F,
                            ctx->d_sums, ctx->d_part, st));
     ctx->have_outputs = true;
     return SC_OK;
@@ -425,6 +425,8 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     gd.ox = G.ox;
     gd.oy = G.oy;
     gd.bfield = M_PI * p->flux_quanta / G.area;  // B = pi alpha / area in units of B0
+    gd.n_comp = G.n_comp;
+    for (int c = 0; c < 4; ++c) ctx->norms.D[c] = ctx->normD - std::log(G.tc_ratio[c]);
     gd.gx = p->gauge_cx;
     gd.gy = p->gauge_cy;
     gd.charge_sign = p->charge_sign;
@@ -477,6 +479,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         d.u0 = cx * (-pp.ey) + cy * pp.ex;  // (R - O).e_perp / h at grid point (0, 0)
         d.v0 = cx * pp.ex + cy * pp.ey;
         d.eta = pp.eta;
+        for (int c = 0; c < 4; ++c) d.eta_c[c] = pp.eta_c[c];
         d.wa = G.weight[q];
         d.wb = G.weight[q + P];
         d.l_lo = pp.l_lo;
@@ -521,6 +524,10 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             const double ws = G.weight[q] + G.weight[q + P];
             d.eta = (float)pp.eta;
             d.w_eta = (float)(ws * pp.eta);
+            for (int c = 0; c < 4; ++c) {
+                d.eta_c[c] = (float)pp.eta_c[c];
+                d.w_eta_c[c] = (float)(ws * pp.eta_c[c]);
+            }
             d.w_ex = (float)(ws * pp.ex);
             d.w_ey = (float)(ws * pp.ey);
             d.w_sum = (float)ws;
@@ -569,10 +576,11 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     CP(ctx->d_slot_line, slot_line.data(), slot_line.size() * sizeof(int32_t));
     CA(ctx->d_pairs, P * sizeof(scd::PairDev));
     CP(ctx->d_pairs, pdev.data(), P * sizeof(scd::PairDev));
-    CA(ctx->d_delta, 2 * np * sizeof(double));
+    const size_t nc = (size_t)G.n_comp;
+    CA(ctx->d_delta, 2 * np * nc * sizeof(double));
     CA(ctx->d_aind, 2 * np * sizeof(double));
-    CA(ctx->d_acc, 5 * np * sizeof(double));
-    CA(ctx->d_dnew, 2 * np * sizeof(double));
+    CA(ctx->d_acc, (3 + 2 * nc) * np * sizeof(double));
+    CA(ctx->d_dnew, 2 * np * nc * sizeof(double));
     CA(ctx->d_j, 2 * np * sizeof(double));
     CA(ctx->d_F, np * sizeof(double));
     CA(ctx->d_sums, 8 * sizeof(double));
@@ -594,7 +602,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         CP(ctx->d_line_f32, lf.data(), nL * sizeof(scd::LineF32));
         CA(ctx->d_pair_f32, P * sizeof(scd::PairF32));
         CP(ctx->d_pair_f32, pf.data(), P * sizeof(scd::PairF32));
-        CA(ctx->d_delta_f, np * sizeof(float2));
+        CA(ctx->d_delta_f, np * nc * sizeof(float2));
         CA(ctx->d_aind_f, np * sizeof(float2));
     }
     if (p->record_timings) {
@@ -609,7 +617,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         }
     }
     {
-        cudaError_t err = cudaMemset(ctx->d_delta, 0, 2 * np * sizeof(double));
+        cudaError_t err = cudaMemset(ctx->d_delta, 0, 2 * np * nc * sizeof(double));
         if (err == cudaSuccess) err = cudaMemset(ctx->d_aind, 0, 2 * np * sizeof(double));
         if (err == cudaSuccess) err = cudaMemset(ctx->d_img_out, 0, G.n_slots * t4);
         if (err != cudaSuccess) return fail_cuda(err, "memset");
@@ -727,7 +735,7 @@ sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, i
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 2 * npts(ctx) * sizeof(double);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(ctx->d_delta, delta, bytes, k, st));
+    CK(cudaMemcpyAsync(ctx->d_delta, delta, bytes * ctx->geo.n_comp, k, st));
     if (a_ind) {
         CK(cudaMemcpyAsync(ctx->d_aind, a_ind, bytes, k, st));
         ctx->have_aind = true;
@@ -792,7 +800,7 @@ sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_de
     CKS(check_ctx(ctx));
     cudaStream_t st = (cudaStream_t)stream;
     CKS(ensure_outputs_impl(ctx, st));
-    CKS(copy_out(ctx, delta_out, ctx->d_dnew, 2 * npts(ctx) * sizeof(double), on_device, st));
+    CKS(copy_out(ctx, delta_out, ctx->d_dnew, 2 * npts(ctx) * ctx->geo.n_comp * sizeof(double), on_device, st));
     if (eps_G) {
         double s[4];
         CK(cudaMemcpyAsync(s, ctx->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -843,7 +851,7 @@ sc_status sc_picard_step(sc_ctx *ctx, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     CKS(ensure_outputs_impl(ctx, st));
     if (ctx->d_G) CKS(sc_update_vector_potential(ctx, stream));
-    CK(scd::launch_copy_delta(2 * (int64_t)npts(ctx), ctx->d_dnew, ctx->d_delta, st));
+    CK(scd::launch_copy_delta(2 * (int64_t)npts(ctx) * ctx->geo.n_comp, ctx->d_dnew, ctx->d_delta, st));
     ctx->have_sweep = false;
     ctx->have_outputs = false;
     return SC_OK;
@@ -974,7 +982,8 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
         const int64_t stride = 3 * pl.stride;
         cudaError_t e = cudaSuccess;
-        if ((e = dalloc(ctx, &d_gd, 2 * np * sizeof(double))) != cudaSuccess ||
+        const size_t nc = (size_t)ctx->geo.n_comp;
+        if ((e = dalloc(ctx, &d_gd, 2 * np * nc * sizeof(double))) != cudaSuccess ||
             (e = dalloc(ctx, &d_ga, 2 * np * sizeof(double))) != cudaSuccess ||
             (e = dalloc(ctx, &d_w, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes)) != cudaSuccess ||
             (e = dalloc(ctx, &d_g, (size_t)ctx->geo.n_slots * t4)) != cudaSuccess ||
@@ -992,7 +1001,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
             }
             gN = d_gN;
         }
-        if ((e = cudaMemsetAsync(d_gd, 0, 2 * np * sizeof(double), st)) != cudaSuccess ||
+        if ((e = cudaMemsetAsync(d_gd, 0, 2 * np * nc * sizeof(double), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(d_ga, 0, 2 * np * sizeof(double), st)) != cudaSuccess ||
             (e = cudaMemsetAsync(d_w, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st)) != cudaSuccess ||
             (e = cudaMemsetAsync(d_g, 0, (size_t)ctx->geo.n_slots * t4, st)) != cudaSuccess ||
@@ -1024,7 +1033,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
             rc = set_err(ctx, SC_ECUDA, cudaGetErrorString(e));
             break;
         }
-        rc = copy_out(ctx, dL_ddelta, d_gd, 2 * np * sizeof(double), on_device, st);
+        rc = copy_out(ctx, dL_ddelta, d_gd, 2 * np * nc * sizeof(double), on_device, st);
         if (rc == SC_OK) rc = copy_out(ctx, dL_daind, d_ga, 2 * np * sizeof(double), on_device, st);
     } while (0);
     ldos_release(ctx, R, st);
@@ -1067,15 +1076,16 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     if (!dL_ddelta) return set_err(ctx, SC_EINVAL, "dL_ddelta is required");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t np = npts(ctx);
+    const size_t nc = (size_t)ctx->geo.n_comp;
     const size_t t4 = ctx->fp64 ? 32 : 16;
     Plan *apl = nullptr;
     CKS(adjoint_plan(ctx, &apl));
     const Plan &pl = *apl;
     if (!ctx->d_gacc) {
-        CK(dalloc(ctx, &ctx->d_gacc, 5 * np * sizeof(double)));
-        CK(dalloc(ctx, &ctx->d_gdelta, 2 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gacc, (3 + 2 * nc) * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gdelta, 2 * np * nc * sizeof(double)));
         CK(dalloc(ctx, &ctx->d_gaind, 2 * np * sizeof(double)));
-        CK(dalloc(ctx, &ctx->d_gin, 5 * np * sizeof(double)));
+        CK(dalloc(ctx, &ctx->d_gin, (2 * nc + 3) * np * sizeof(double)));
         CK(dalloc(ctx, &ctx->d_wimg, ctx->geo.n_slots * t4));
         CK(dalloc(ctx, &ctx->d_gimg, ctx->geo.n_slots * t4));
     }
@@ -1094,26 +1104,26 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     const double *gdn = g_delta_new, *gj = g_j, *gF = g_F;
     if (!on_device) {
         if (g_delta_new) {
-            CK(cudaMemcpyAsync(ctx->d_gin, g_delta_new, 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(ctx->d_gin, g_delta_new, 2 * np * nc * sizeof(double), cudaMemcpyHostToDevice, st));
             gdn = ctx->d_gin;
         }
         if (g_j) {
-            CK(cudaMemcpyAsync(ctx->d_gin + 2 * np, g_j, 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
-            gj = ctx->d_gin + 2 * np;
+            CK(cudaMemcpyAsync(ctx->d_gin + 2 * np * nc, g_j, 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
+            gj = ctx->d_gin + 2 * np * nc;
         }
         if (g_F) {
-            CK(cudaMemcpyAsync(ctx->d_gin + 4 * np, g_F, np * sizeof(double), cudaMemcpyHostToDevice, st));
-            gF = ctx->d_gin + 4 * np;
+            CK(cudaMemcpyAsync(ctx->d_gin + (2 * nc + 2) * np, g_F, np * sizeof(double), cudaMemcpyHostToDevice, st));
+            gF = ctx->d_gin + (2 * nc + 2) * np;
         }
     }
-    CK(cudaMemsetAsync(ctx->d_gdelta, 0, 2 * np * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->d_gdelta, 0, 2 * np * nc * sizeof(double), st));
     CK(cudaMemsetAsync(ctx->d_gaind, 0, 2 * np * sizeof(double), st));
     CK(cudaMemsetAsync(ctx->d_wimg, 0, ctx->geo.n_slots * t4, st));
     CK(cudaMemsetAsync(ctx->d_gimg, 0, ctx->geo.n_slots * t4, st));
     const double kappa = ctx->geo.prm.kappa;
     const bool magn = kappa > 0.0 && std::isfinite(kappa) && ctx->have_aind;
     CK(scd::launch_adjoint_outputs(ctx->grid, ctx->d_mask, ctx->d_delta, magn ? ctx->d_aind : nullptr,
-                                   ctx->geo.prm.t, ctx->normD, magn ? kappa : 0.0, (double)ctx->geo.n_in, gdn, gj, gF,
+                                   ctx->geo.prm.t, ctx->norms, magn ? kappa : 0.0, (double)ctx->geo.n_in, gdn, gj, gF,
                                    g_Ftotal, ctx->d_gacc, ctx->d_gdelta, ctx->d_gaind, st));
     CK(scd::launch_adjoint_rotate_back(ctx->fp64, ctx->d_pairs, ctx->geo.n_pairs, ctx->d_back, ctx->grid, ctx->d_mask,
                                        ctx->d_gacc, ctx->d_wimg, st));
@@ -1142,7 +1152,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     }
     CK(scd::launch_adjoint_rotate(ctx->fp64, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
                                   ctx->d_ghost, ctx->d_gimg, ctx->d_gdelta, ctx->d_gaind, st));
-    CKS(copy_out(ctx, dL_ddelta, ctx->d_gdelta, 2 * np * sizeof(double), on_device, st));
+    CKS(copy_out(ctx, dL_ddelta, ctx->d_gdelta, 2 * np * nc * sizeof(double), on_device, st));
     CKS(copy_out(ctx, dL_daind, ctx->d_gaind, 2 * np * sizeof(double), on_device, st));
     return SC_OK;
 }

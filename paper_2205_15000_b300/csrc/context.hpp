@@ -33,6 +33,7 @@ struct sc_ctx {
     std::vector<double> eps, ewt;  // energies and weights of the energy sums (host)
     double *d_eps = nullptr, *d_ewt = nullptr;  // on the device for Ozaki sums, else nullptr
     double normD = 0.0;
+    scd::CompNorm norms{};  // per order-parameter component: normD - ln(T_c^c / T_c)
     size_t real_bytes = 4;
     scd::GridDev grid{};
     // geometry on the device
@@ -88,7 +89,7 @@ struct sc_ctx {
     double *d_acc_part = nullptr, *d_acc_sums = nullptr;
     int acc_kind = -1;  // kind of the running history; -1: none (next call starts one)
     long acc_iter = 0;
-    double acc_alpha = 0.0, acc_alpha_c[4] = {0, 0, 0, 0}, acc_w_c[4] = {0, 0, 0, 0};
+    double acc_alpha = 0.0, acc_alpha_c[10] = {}, acc_w_c[10] = {};  // per x component (Re, Im of each Delta_c, A)
     std::string err;
     std::vector<void *> allocs;
 };

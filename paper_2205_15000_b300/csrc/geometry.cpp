@@ -163,6 +163,14 @@ std::string Geometry::build(const sc_params &p) {
     if (!(p.t > 0.0 && p.t <= 1.0)) return "t must be in (0, 1]";
     if (p.charge_sign != 1 && p.charge_sign != -1) return "charge_sign must be +1 or -1";
     if (p.pairing < 0 || p.pairing > 3) return "unknown pairing";
+    if (p.n_components < 0 || p.n_components > 4) return "n_components must be 0 to 4";
+    n_comp = p.n_components > 1 ? p.n_components : 1;
+    for (int c = 0; c < n_comp; ++c) {
+        const int pc = c == 0 ? p.pairing : p.pairings[c];
+        if (pc < 0 || pc > 3) return "unknown pairing of a component";
+        if (!(p.tc_ratios[c] >= 0.0) || !std::isfinite(p.tc_ratios[c])) return "tc_ratios must be >= 0";
+        tc_ratio[c] = p.tc_ratios[c] > 0.0 ? p.tc_ratios[c] : 1.0;
+    }
     n_pairs = n_angles / 2;
 
     if (p.shape_kind == 1) {
@@ -269,7 +277,11 @@ std::string Geometry::build(const sc_params &p) {
         const double phi = 2.0 * M_PI * q / n_angles;
         pairs[q].ex = std::cos(phi);
         pairs[q].ey = std::sin(phi);
-        pairs[q].eta = basis_function(p.pairing, p.crystal_rotation, pairs[q].ex, pairs[q].ey);
+        for (int c = 0; c < 4; ++c)
+            pairs[q].eta_c[c] = c < n_comp ? basis_function(c == 0 ? p.pairing : p.pairings[c], p.crystal_rotation,
+                                                            pairs[q].ex, pairs[q].ey)
+                                           : 0.0;
+        pairs[q].eta = pairs[q].eta_c[0];
         pairs[q].wsum = weight[q] + weight[q + n_pairs];
     }
 

@@ -36,7 +36,8 @@ struct LineInfo {
 
 struct PairInfo {
     double ex, ey;          // e_par = (cos phi_p, sin phi_p); e_perp = (-ey, ex)
-    double eta;             // basis function at phi_p (= at phi_p + pi)
+    double eta;             // basis function at phi_p (= at phi_p + pi), component 0
+    double eta_c[4];        // basis function of each order-parameter component
     double wsum;            // quadrature weight of phi_p plus that of phi_p + pi
     int32_t l_lo, l_hi, line0;
 };
@@ -51,6 +52,8 @@ public:
     double area = 0.0;
     double ox = 0.0, oy = 0.0;             // lattice origin
     int32_t nx = 0, ny = 0, n_angles = 0, n_pairs = 0;
+    int32_t n_comp = 1;                    // order-parameter components
+    double tc_ratio[4] = {1, 1, 1, 1};     // T_c^Gamma / T_c
     int64_t n_in = 0;
     std::vector<uint8_t> mask;
     std::vector<int32_t> ghost;            // (nx+2)*(ny+2)

@@ -66,14 +66,24 @@ __global__ void rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__
     const double y = grid.oy + lh * pp.ex + sc * pp.ey;
     double dr, di, ax = 0.0, ay = 0.0;
     bool ok = bilinear(grid, ghost, delta, x, y, dr, di);
+    dr *= pp.eta;
+    di *= pp.eta;
+    // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
+    const int64_t npts = (int64_t)grid.nx * grid.ny;
+    for (int c = 1; c < grid.n_comp; ++c) {
+        double er, ei;
+        ok = bilinear(grid, ghost, delta + 2 * npts * c, x, y, er, ei) && ok;
+        dr += pp.eta_c[c] * er;
+        di += pp.eta_c[c] * ei;
+    }
     if (aind) ok = bilinear(grid, ghost, aind, x, y, ax, ay) && ok;
     // external vector potential, symmetric gauge: A = B/2 (-(y - yg), x - xg)
     ax += -0.5 * grid.bfield * (y - grid.gy);
     ay += 0.5 * grid.bfield * (x - grid.gx);
     const double a = grid.charge_sign * (pp.ex * ax + pp.ey * ay);
     typename Vec4<T>::type o;
-    o.x = (T)(pp.eta * dr);
-    o.y = (T)(pp.eta * di);
+    o.x = (T)dr;
+    o.y = (T)di;
     o.z = (T)a;
     o.w = ok ? T(0) : T(1);  // 1 flags a sample whose stencil left the grid
     out[s] = o;
@@ -110,7 +120,7 @@ int sweep_occupancy(bool fp64, int ept, int bs, int stepper, bool weighted) {
 // each (clamped to the line); the bilinear mix of the four image slots enters
 // the Fermi-surface sums with the weights of both angles of the pair.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int NC>
 __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pairs,
                                    const BackLine *__restrict__ bl, GridDev grid,
                                    const uint8_t *__restrict__ mask,
@@ -120,6 +130,7 @@ __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= npts) return;
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    double ac[2 * NC] = {};  // <eta_c Sf> of components c >= 1
     if (mask[idx]) {
         const double fi = (double)(idx % grid.nx), fj = (double)(idx / grid.nx);
         for (int p = 0; p < n_pairs; ++p) {
@@ -153,6 +164,11 @@ __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_
             a2 += ws * pp.ex * x2;
             a3 += ws * pp.ey * x2;
             a4 += ws * x3;
+#pragma unroll
+            for (int c = 1; c < NC; ++c) {
+                ac[2 * c] += ws * pp.eta_c[c] * x0;
+                ac[2 * c + 1] += ws * pp.eta_c[c] * x1;
+            }
         }
     }
     acc[idx] = a0;
@@ -160,6 +176,11 @@ __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_
     acc[2 * npts + idx] = a2;
     acc[3 * npts + idx] = a3;
     acc[4 * npts + idx] = a4;
+#pragma unroll
+    for (int c = 1; c < NC; ++c) {
+        acc[(3 + 2 * c) * npts + idx] = ac[2 * c];
+        acc[(4 + 2 * c) * npts + idx] = ac[2 * c + 1];
+    }
 }
 
 cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs, const BackLine *bl,
@@ -168,12 +189,20 @@ cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int bs = 128;
     const unsigned nb = (unsigned)((npts + bs - 1) / bs);
-    if (fp64)
-        rotate_back_kernel<double><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
-                                                      (const double4_32a *)image_out, acc);
-    else
-        rotate_back_kernel<float><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
-                                                     (const float4 *)image_out, acc);
+#define SC_RB(NC)                                                                                            \
+    case NC:                                                                                                 \
+        if (fp64)                                                                                            \
+            rotate_back_kernel<double, NC><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,                \
+                                                              (const double4_32a *)image_out, acc);          \
+        else                                                                                                 \
+            rotate_back_kernel<float, NC><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,                 \
+                                                             (const float4 *)image_out, acc);                \
+        break;
+    switch (grid.n_comp) {
+        SC_RB(1) SC_RB(2) SC_RB(3) SC_RB(4)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SC_RB
     return cudaGetLastError();
 }
 
@@ -253,7 +282,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
                                const double *__restrict__ acc, const double *__restrict__ delta,
-                               const double *__restrict__ aind, double t, double normD, double kappa,
+                               const double *__restrict__ aind, double t, CompNorm normD, double kappa,
                                double *__restrict__ dn, double *__restrict__ jo,
                                double *__restrict__ F, double *__restrict__ partials) {
     __shared__ double sh[32];
@@ -263,20 +292,32 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
     double num = 0, den = 0, fs = 0, bad = 0;
     if (idx < npts) {
         if (!mask[idx]) {
-            dn[2 * idx] = dn[2 * idx + 1] = 0.0;
+            for (int c = 0; c < grid.n_comp; ++c) dn[2 * (c * npts + idx)] = dn[2 * (c * npts + idx) + 1] = 0.0;
             jo[2 * idx] = jo[2 * idx + 1] = 0.0;
             F[idx] = 0.0;
         } else {
-            const double c = t / (2.0 * 3.141592653589793) / normD;
-            const double dr = c * acc[idx], di = c * acc[npts + idx];
-            dn[2 * idx] = dr;
-            dn[2 * idx + 1] = di;
             const double cj = grid.charge_sign * t / 3.141592653589793;
             jo[2 * idx] = cj * acc[2 * npts + idx];
             jo[2 * idx + 1] = cj * acc[3 * npts + idx];
-            const double d0r = delta[2 * idx], d0i = delta[2 * idx + 1];
-            const double d2 = d0r * d0r + d0i * d0i;
-            double f = d2 * normD - 0.5 * t * acc[4 * npts + idx];
+            // component c (Eq. gapeq_fixpoint): Delta_c = (t/2pi) <eta_c Sf> / D_c;
+            // F gains |Delta_c|^2 D_c per component
+            double f = -0.5 * t * acc[4 * npts + idx];
+            bool fin = true;
+            for (int c = 0; c < grid.n_comp; ++c) {
+                const int64_t pr = c == 0 ? 0 : 3 + 2 * c, pim = c == 0 ? 1 : 4 + 2 * c;
+                const double k = t / (2.0 * 3.141592653589793) / normD.D[c];
+                const double dr = k * acc[pr * npts + idx], di = k * acc[pim * npts + idx];
+                const int64_t o = 2 * (c * npts + idx);
+                dn[o] = dr;
+                dn[o + 1] = di;
+                const double d0r = delta[o], d0i = delta[o + 1];
+                const double d2 = d0r * d0r + d0i * d0i;
+                f += d2 * normD.D[c];
+                const double er = dr - d0r, ei = di - d0i;
+                num += er * er + ei * ei;
+                den += d2;
+                fin = fin && isfinite(dr) && isfinite(di);
+            }
             if (aind && kappa > 0.0) {
                 const int i = (int)(idx % nx), j = (int)(idx / nx);
                 const int ia = i > 0 ? i - 1 : i, ib = i < nx - 1 ? i + 1 : i;
@@ -290,11 +331,7 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
             }
             F[idx] = f;
             fs = f;
-            const double er = dr - d0r, ei = di - d0i;
-            num = er * er + ei * ei;
-            den = d2;
-            bad = (isfinite(dr) && isfinite(di) && isfinite(f) && isfinite(jo[2 * idx]) &&
-                   isfinite(jo[2 * idx + 1])) ? 0.0 : 1.0;
+            bad = (fin && isfinite(f) && isfinite(jo[2 * idx]) && isfinite(jo[2 * idx + 1])) ? 0.0 : 1.0;
         }
     }
     const double s0 = block_sum(num, sh);
@@ -326,7 +363,7 @@ __global__ void final_sums_kernel(const double *__restrict__ partials, int nbloc
 int reduce_blocks(int64_t npts) { return (int)((npts + 255) / 256); }
 
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
-                           const double *delta, const double *aind, double t, double normD,
+                           const double *delta, const double *aind, double t, const CompNorm &normD,
                            double kappa, double *delta_new, double *j, double *F, double *sums,
                            double *partials, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;

@@ -29,9 +29,10 @@ struct LineGeo {
 struct PairDev {
     double ex, ey;       // e_par
     double u0, v0;       // lattice coordinates (line, sample) of grid point (0, 0), units of h
-    double eta;          // basis function of the pair
+    double eta;          // basis function of the pair (component 0)
     double wa, wb;       // quadrature weights of angle p and of angle p + P
     int32_t l_lo, l_hi, line0, pad;
+    double eta_c[4];     // basis function of each order-parameter component
 };
 
 // Per line, for the rotate-back kernel: nearest line with samples, its m0, ns, slot0.
@@ -45,6 +46,7 @@ struct GridDev {
     double bfield;       // external field, units of B0
     double gx, gy;       // gauge origin
     int32_t charge_sign;
+    int32_t n_comp;      // order-parameter components; Delta is [n_comp][ny][nx] complex
 };
 
 // FP32 production path: lattice coordinates in fixed point (2^-40 grid units),
@@ -60,11 +62,12 @@ struct LineF32 {
 struct PairF32 {
     int64_t dx, dy;                 // e_par in grid units per sample
     int64_t ui, uj, u0, vi, vj, v0; // u = i ui + j uj + u0, v = i vi + j vj + v0
-    float eta;                      // basis function
+    float eta;                      // basis function (component 0)
     float w_eta, w_ex, w_ey, w_sum; // (w_p + w_{p+P}) times eta, e_x, e_y, 1
     float wa, wb;                   // w_p, w_{p+P}
     float ex_f, ey_f;               // e_par in FP32
     int32_t l_lo, l_hi, line0, pad;
+    float eta_c[4], w_eta_c[4];     // per order-parameter component: eta, (w_p + w_{p+P}) eta
 };
 
 // Everything the sweep needs of one grain (one context, or one member of a batch).
@@ -114,7 +117,7 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
                           cudaStream_t s);
 cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
 // FP32 production path
-cudaError_t launch_fields_f32(int64_t npts, const double *delta, const double *aind, float2 *delta_f,
+cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, const double *aind, float2 *delta_f,
                               float2 *aind_f, cudaStream_t s);
 cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
                               const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
@@ -136,8 +139,14 @@ cudaError_t launch_rotate_back(bool fp64, const PairDev *pairs, int32_t n_pairs,
 // one block): the sums do not depend on scheduling.  partials: reduce_blocks(npts)
 // x 4 doubles of scratch.
 int reduce_blocks(int64_t npts);
+// Accumulator planes: <eta_0 Sf> (2), <v Sg> (2), <SF>, then <eta_c Sf> (2 per
+// component c >= 1): 3 + 2 n_comp planes of nx*ny doubles.
+// normD_c: the gap-equation normalisation of each component, D - ln(T_c^c/T_c).
+struct CompNorm {
+    double D[4];
+};
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
-                           const double *delta, const double *aind, double t, double normD,
+                           const double *delta, const double *aind, double t, const CompNorm &normD,
                            double kappa, double *delta_new, double *j, double *F,
                            double *sums /* [4]: num, den, Fsum, nonfinite */, double *partials,
                            cudaStream_t s);

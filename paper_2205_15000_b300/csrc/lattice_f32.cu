@@ -23,13 +23,16 @@ __device__ __forceinline__ void split_fixed(int64_t v, int &cell, float &frac) {
 
 }  // namespace
 
-__global__ void fields_f32_kernel(int64_t npts, const double2 *__restrict__ delta,
+// Delta (n_comp components, one after another) and A_ind to FP32
+__global__ void fields_f32_kernel(int64_t npts, int n_comp, const double2 *__restrict__ delta,
                                   const double2 *__restrict__ aind, float2 *__restrict__ df,
                                   float2 *__restrict__ af) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npts) return;
-    const double2 d = delta[i];
-    df[i] = make_float2((float)d.x, (float)d.y);
+    for (int c = 0; c < n_comp; ++c) {
+        const double2 d = delta[c * npts + i];
+        df[c * npts + i] = make_float2((float)d.x, (float)d.y);
+    }
     if (aind) {
         const double2 a = aind[i];
         af[i] = make_float2((float)a.x, (float)a.y);
@@ -38,11 +41,11 @@ __global__ void fields_f32_kernel(int64_t npts, const double2 *__restrict__ delt
     }
 }
 
-cudaError_t launch_fields_f32(int64_t npts, const double *delta, const double *aind, float2 *delta_f,
+cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, const double *aind, float2 *delta_f,
                               float2 *aind_f, cudaStream_t st) {
     const int bs = 256;
     fields_f32_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(
-        npts, (const double2 *)delta, (const double2 *)aind, delta_f, aind_f);
+        npts, n_comp, (const double2 *)delta, (const double2 *)aind, delta_f, aind_f);
     return cudaGetLastError();
 }
 
@@ -79,6 +82,15 @@ __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32
         const float ay = w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y;
         o.x = pp.eta * dr;
         o.y = pp.eta * di;
+        // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
+        const int64_t np = (int64_t)grid.nx * grid.ny;
+        for (int c = 1; c < grid.n_comp; ++c) {
+            const float2 *dc = df + c * np;
+            const float2 e00 = g00 >= 0 ? dc[g00] : z, e10 = g10 >= 0 ? dc[g10] : z;
+            const float2 e01 = g01 >= 0 ? dc[g01] : z, e11 = g11 >= 0 ? dc[g11] : z;
+            o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
+            o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
+        }
         o.z = ln.aext + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
         const bool ok = (g00 >= 0 || w00 == 0.f) && (g10 >= 0 || w10 == 0.f) && (g01 >= 0 || w01 == 0.f) &&
                         (g11 >= 0 || w11 == 0.f);
@@ -100,6 +112,7 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 
 // one thread per grid point: for every pair, bilinear gather of the four image
 // slots around the point's lattice coordinates and the Fermi-surface sum
+template <int NC>
 __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
                                        const BackLine *__restrict__ bl, GridDev grid,
                                        const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
@@ -108,10 +121,12 @@ __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= npts) return;
     double A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0;
+    double Ac[2 * NC] = {};  // <eta_c Sf> of components c >= 1
     if (mask[idx]) {
         const int64_t i = idx % grid.nx, j = idx / grid.nx;
         for (int p0 = 0; p0 < n_pairs; p0 += 16) {
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+            float ac[2 * NC] = {};
             const int pe = min(p0 + 16, n_pairs);
             for (int p = p0; p < pe; ++p) {
                 const PairF32 &pp = pairs[p];
@@ -140,12 +155,19 @@ __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_
                 a2 += pp.w_ex * x2;
                 a3 += pp.w_ey * x2;
                 a4 += pp.w_sum * x3;
+#pragma unroll
+                for (int c = 1; c < NC; ++c) {
+                    ac[2 * c] += pp.w_eta_c[c] * x0;
+                    ac[2 * c + 1] += pp.w_eta_c[c] * x1;
+                }
             }
             A0 += a0;
             A1 += a1;
             A2 += a2;
             A3 += a3;
             A4 += a4;
+#pragma unroll
+            for (int c = 2; c < 2 * NC; ++c) Ac[c] += ac[c];
         }
     }
     acc[idx] = A0;
@@ -153,6 +175,11 @@ __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_
     acc[2 * npts + idx] = A2;
     acc[3 * npts + idx] = A3;
     acc[4 * npts + idx] = A4;
+#pragma unroll
+    for (int c = 1; c < NC; ++c) {
+        acc[(3 + 2 * c) * npts + idx] = Ac[2 * c];
+        acc[(4 + 2 * c) * npts + idx] = Ac[2 * c + 1];
+    }
 }
 
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
@@ -160,8 +187,14 @@ cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const 
                                    double *acc, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int bs = 128;
-    rotate_back_f32_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(pairs, n_pairs, bl, grid, mask,
-                                                                           image_out, acc);
+    const unsigned nb = (unsigned)((npts + bs - 1) / bs);
+    switch (grid.n_comp) {
+        case 1: rotate_back_f32_kernel<1><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
+        case 2: rotate_back_f32_kernel<2><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
+        case 3: rotate_back_f32_kernel<3><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
+        case 4: rotate_back_f32_kernel<4><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

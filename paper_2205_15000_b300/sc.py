@@ -49,6 +49,7 @@ class sc_params(ctypes.Structure):
         ("precision", ctypes.c_int32), ("lanes_per_line", ctypes.c_int32),
         ("host_only", ctypes.c_int32), ("record_timings", ctypes.c_int32),
         ("stepper", ctypes.c_int32), ("energy_sum", ctypes.c_int32),
+        ("n_components", ctypes.c_int32), ("pairings", ctypes.c_int32 * 4), ("tc_ratios", ctypes.c_double * 4),
     ]
 
 
@@ -216,6 +217,13 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
     p.record_timings = 1 if record_timings else 0
     p.stepper = STEPPERS[d.get("stepper", "closed")]
     p.energy_sum = ENERGY_SUMS[d.get("energy_sum", "matsubara")]
+    comps = d.get("components")
+    if comps:  # [(pairing, T_c^Gamma / T_c), ...]; component 0 takes the place of `pairing`
+        p.n_components = len(comps)
+        p.pairing = int(comps[0][0])
+        for c, (pairing, tcr) in enumerate(comps):
+            p.pairings[c] = int(pairing)
+            p.tc_ratios[c] = float(tcr)
     return p
 
 
@@ -317,9 +325,11 @@ def sc_accel_reset(ctx):
 
 
 def sc_accel_get_state(ctx):
+    """(iterations, step sizes, CongAcc weights): arrays of 2 n_components + 2
+    entries (Re, Im of each Delta component, then A_x, A_y)."""
     it = ctypes.c_int32(0)
-    a = np.zeros(4)
-    w = np.zeros(4)
+    a = np.zeros(10)
+    w = np.zeros(10)
     _check(lib.sc_accel_get_state(ctx, ctypes.byref(it), _ptr(a), _ptr(w)), ctx)
     return it.value, a, w
 
@@ -499,9 +509,17 @@ class Context:
         sc_riccati_sweep(self.h, stream)
         self.sweep_count = getattr(self, "sweep_count", 0) + 1
 
+    @property
+    def n_comp(self):
+        return max(1, len(self.prm.get("components") or []))
+
+    def _dshape(self):
+        """Shape of Delta-like complex fields: (ny, nx), or (C, ny, nx) with C > 1 components."""
+        return (self.n_comp, self.ny, self.nx) if self.n_comp > 1 else (self.ny, self.nx)
+
     def outputs(self, stream=None):
         import torch
-        dn = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        dn = torch.empty(self._dshape() + (2,), dtype=torch.float64, device="cuda")
         j = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
         F = torch.empty((self.ny, self.nx), dtype=torch.float64, device="cuda")
         eps = sc_gap_update(self.h, dn, True, True, stream)
@@ -532,7 +550,7 @@ class Context:
                 t = torch.view_as_real(t.to(torch.complex128).contiguous())
             return t.to(torch.float64).contiguous()
         gdn, gj, gF = dev(g_delta_new, 2), dev(g_j, 2), dev(g_F, 1)
-        dd = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        dd = torch.empty(self._dshape() + (2,), dtype=torch.float64, device="cuda")
         da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
         sc_sweep_adjoint(self.h, gdn, gj, gF, g_Ftotal, dd, da, True, stream)
         self._adj_keep = (gdn, gj, gF)
@@ -543,7 +561,7 @@ class Context:
         (n_e x ny x nx)."""
         import torch
         g = torch.as_tensor(g_ldos, dtype=torch.float64, device="cuda").contiguous()
-        dd = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
+        dd = torch.empty(self._dshape() + (2,), dtype=torch.float64, device="cuda")
         da = torch.empty((self.ny, self.nx, 2), dtype=torch.float64, device="cuda")
         sc_ldos_adjoint(self.h, energies, broadening, n_burnin, g, dd, da, True, stream)
         return torch.view_as_complex(dd), da
