@@ -30,7 +30,7 @@ def lib():
         L.or_geom_area.restype = ctypes.c_double
         L.or_geom_area.argtypes = [ctypes.c_void_p]
         for name in ("or_geom_info", "or_geom_mask", "or_geom_ghost", "or_geom_lines",
-                     "or_geom_links", "or_geom_quadrature", "or_sample_fields", "or_sweep",
+                     "or_geom_links", "or_geom_chords", "or_external_a", "or_geom_quadrature", "or_sample_fields", "or_sweep",
                      "or_rotate_back", "or_outputs", "or_vector_potential", "or_sweep_subset"):
             getattr(L, name).restype = ctypes.c_int
         L.or_norm_D.restype = ctypes.c_double
@@ -44,6 +44,15 @@ def lib():
         L.or_geom_set_energy_weights.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double]
         _lib = L
     return _lib
+
+
+class _Part(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("add", ctypes.c_int32),
+        ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
+        ("n_vert", ctypes.c_int32),
+        ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double)),
+    ]
 
 
 class _Params(ctypes.Structure):
@@ -62,7 +71,13 @@ class _Params(ctypes.Structure):
         ("lattice_ox", ctypes.c_double), ("lattice_oy", ctypes.c_double),
         ("stepper", ctypes.c_int32),
         ("n_components", ctypes.c_int32), ("pairings", ctypes.c_int32 * 4), ("tc_ratios", ctypes.c_double * 4),
+        ("n_parts", ctypes.c_int32), ("parts", ctypes.POINTER(_Part)),
+        ("gauge", ctypes.c_int32),
     ]
+
+
+GAUGES = {"symmetric": 0, "landau": 1, "solenoid": 2}
+PART_KINDS = {"disc": 0, "polygon": 1}
 
 
 def _p(a):
@@ -166,7 +181,10 @@ class OracleGeom:
             if name == "stepper":
                 s.stepper = STEPPERS[prm.get("stepper", "closed")]
                 continue
-            if name in ("n_components", "pairings", "tc_ratios"):
+            if name in ("n_components", "pairings", "tc_ratios", "n_parts", "parts"):
+                continue
+            if name == "gauge":
+                s.gauge = GAUGES[prm.get("gauge", "symmetric")]
                 continue
             if name == "pairing" and prm.get("components"):
                 s.pairing = int(prm["components"][0][0])
@@ -180,6 +198,24 @@ class OracleGeom:
             s.pairings[c] = int(pairing)
             s.tc_ratios[c] = float(tcr)
         self.C = len(comps)
+        parts = prm.get("parts") or []
+        self._parts = (_Part * max(1, len(parts)))()
+        self._part_arrays = []
+        for k, q in enumerate(parts):
+            P = self._parts[k]
+            P.kind = PART_KINDS[q["kind"]]
+            P.add = 1 if q.get("add", True) else 0
+            if q["kind"] == "disc":
+                P.cx, P.cy, P.r = float(q["cx"]), float(q["cy"]), float(q["r"])
+            else:
+                ax = np.ascontiguousarray(q["vx"], np.float64)
+                ay = np.ascontiguousarray(q["vy"], np.float64)
+                self._part_arrays += [ax, ay]
+                P.n_vert = len(ax)
+                P.vx = ax.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                P.vy = ay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        s.n_parts = len(parts)
+        s.parts = ctypes.cast(self._parts, ctypes.POINTER(_Part))
         self._s = s
         h = L.or_geom_create(ctypes.byref(s))
         if not h:
@@ -232,13 +268,34 @@ class OracleGeom:
         smin, smax = np.zeros(n), np.zeros(n)
         m0, m1 = np.zeros(n, np.int32), np.zeros(n, np.int32)
         lib().or_geom_lines(self._h, _p(l_lo), _p(l_hi), _p(smin), _p(smax), _p(m0), _p(m1))
-        return dict(l_lo=l_lo, l_hi=l_hi, smin=smin, smax=smax, m0=m0, m1=m1)
+        pair, l = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        lib().or_geom_chords(self._h, _p(pair), _p(l))
+        return dict(l_lo=l_lo, l_hi=l_hi, smin=smin, smax=smax, m0=m0, m1=m1, pair=pair, l=l)
+
+    def chords_per_pair(self):
+        return np.bincount(self.lines()["pair"], minlength=self.n_pairs)
+
+    def samples_per_pair(self):
+        L = self.lines()
+        ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+        return np.bincount(L["pair"], weights=ns, minlength=self.n_pairs).astype(np.int64)
 
     def links(self):
+        """Entry links of gamma, [angle][chord][4]: tap angle, lattice line l of
+        the tapped chord, the tapped chord's index within its pair, weight."""
         n = 4 * self.n_lines_all
-        ta, tl, tw = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
-        lib().or_geom_links(self._h, _p(ta), _p(tl), _p(tw))
-        return dict(angle=ta.reshape(-1, 4), line=tl.reshape(-1, 4), w=tw.reshape(-1, 4))
+        ta, tl, tc, tw = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
+        lib().or_geom_links(self._h, _p(ta), _p(tl), _p(tc), _p(tw))
+        return dict(angle=ta.reshape(-1, 4), line=tl.reshape(-1, 4), chord=tc.reshape(-1, 4),
+                    w=tw.reshape(-1, 4))
+
+    def external_a(self, x, y):
+        """External vector potential of the gauge at the points (x, y)."""
+        xy = np.ascontiguousarray(np.stack([np.ravel(x), np.ravel(y)], axis=1), np.float64)
+        A = np.zeros_like(xy)
+        if lib().or_external_a(self._h, len(xy), _p(xy), _p(A)):
+            raise RuntimeError(lib().or_last_error().decode())
+        return A.reshape(np.shape(x) + (2,))
 
     def quadrature(self):
         w, vh, eta = np.zeros(self.N), np.zeros(2 * self.N), np.zeros(self.N)
@@ -248,18 +305,7 @@ class OracleGeom:
     def sample_fields(self, delta, aind, pair):
         d = _cplx_to_f64(delta)
         a = None if aind is None else np.ascontiguousarray(aind, np.float64)
-        lines = self.lines()
-        lo = sum(int(max(0, lines["m1"][i] - lines["m0"][i] + 1)) for i in range(self.n_lines))
-        # per-pair sample count
-        off = 0
-        counts = []
-        for p in range(self.n_pairs):
-            nl = int(lines["l_hi"][p] - lines["l_lo"][p] + 1)
-            c = sum(int(max(0, lines["m1"][off + i] - lines["m0"][off + i] + 1)) for i in range(nl))
-            counts.append(c)
-            off += nl
-        assert sum(counts) == lo
-        ns = counts[pair]
+        ns = int(self.samples_per_pair()[pair])
         ds = np.zeros(2 * max(ns, 1))
         av = np.zeros(2 * max(ns, 1))
         rc = lib().or_sample_fields(self._h, _p(d), _p(a), int(pair), _p(ds), _p(av))
@@ -297,14 +343,7 @@ class OracleGeom:
         a = None if aind is None else np.ascontiguousarray(aind, np.float64)
         z = _cplx_to_f64(self.matsubara())
         ang = np.ascontiguousarray(angles, np.int32)
-        L = self.lines()
-        ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
-        per_pair = []
-        off = 0
-        for q in range(self.n_pairs):
-            nl = int(L["l_hi"][q] - L["l_lo"][q] + 1)
-            per_pair.append(int(ns[off:off + nl].sum()))
-            off += nl
+        per_pair = [int(v) for v in self.samples_per_pair()]
         sizes = [per_pair[k % self.n_pairs] for k in angles]
         out = np.zeros(4 * sum(sizes))
         rc = lib().or_sweep_subset(self._h, _p(d), _p(a), _p(z), int(self.n_e), _p(ang), len(ang), _p(out))

@@ -52,10 +52,25 @@ static int fail(const char *msg) {
     return -1;
 }
 
+/* One part of the grain: a disc or a convex polygon, added or removed. */
+typedef struct {
+    int kind, add;          /* 0 disc, 1 convex polygon; 1 add, 0 remove */
+    double cx, cy, r;       /* disc */
+    int nv;                 /* polygon: CCW vertices and unit outward edge normals */
+    double *vx, *vy, *nx, *ny;
+} o_part;
+
+/* A chord end lies on the boundary of one part: the part, its polygon edge
+   (-1 for a disc), and +1 if the grain lies on the inner side of that
+   boundary (an added part) or -1 if on its outer side (a removed part). */
+typedef struct {
+    int part, edge, sign;
+} o_tag;
+
 struct or_geom {
     or_params P;
-    double *vx, *vy;        /* copied polygon vertices */
-    double *nxe, *nye;      /* unit outward edge normals */
+    int nparts;
+    o_part *parts;          /* a lone disc or polygon is one added part */
     uint8_t *mask;
     int32_t *ghost;         /* padded (nx+2)*(ny+2) */
     int64_t n_in;
@@ -70,18 +85,24 @@ struct or_geom {
     double tcr[4];          /* T_c^Gamma / T_c */
     double *ewt;            /* [n_energies] weights of the energy sums, NULL = 1 (Matsubara) */
     double normD;           /* gap-equation normalisation when ewt is set */
-    /* per pair */
-    int *l_lo, *l_hi, *line_off, *samp_off; /* line_off/samp_off: [npair+1] */
-    /* per line (pair-major) */
+    /* per pair: lattice lines l_lo..l_hi; chords line_off[p]..line_off[p+1]-1;
+       lattice-line records lat_off[p]..; samples samp_off[p].. */
+    int *l_lo, *l_hi, *line_off, *samp_off, *lat_off;
+    /* per lattice line: its chords lat_c0 .. lat_c0+lat_nc-1 (ascending s), the
+       nearest lattice line of the pair that has a chord (lat_chorded) and one
+       that has a chord with samples (lat_near), as line indices l */
+    int *lat_c0, *lat_nc, *lat_chorded, *lat_near;
+    /* per chord (pair-major, then l, then s) */
+    int *ch_pair, *ch_l;
     double *smin, *smax;
-    int *m0, *m1, *ns, *edge_lo, *edge_hi, *soff; /* soff: sample offset within the pair */
-    int *nearest_line;       /* per line: nearest line of the pair with samples */
-    /* links per angle: [N][nl(p)][4] (pair line count); angle offsets = line_off of pair */
+    o_tag *tag_lo, *tag_hi;
+    int *m0, *m1, *ns, *soff; /* soff: sample offset within the pair */
+    /* links per angle: [N][chords of the pair][4]: tap angle, tap chord (global index) */
     int *lk_g_angle, *lk_g_line;
     double *lk_g_w;
     int *lk_t_angle, *lk_t_line;
     double *lk_t_w;
-    int64_t *ang_line_off;   /* [N+1] cumulative line counts over angles */
+    int64_t *ang_line_off;   /* [N+1] cumulative chord counts over angles */
     int64_t *ang_samp_off;   /* [N+1] cumulative sample counts over angles */
 };
 
@@ -143,31 +164,49 @@ double or_norm_D(double t, int n_e) {
 }
 
 /* ---------------------------------------------------------------------- */
-/* Geometry                                                               */
+/* Geometry.  A grain is built by adding and removing discs and convex    */
+/* polygons in the listed order (Sec. 4 and App. B, composite             */
+/* geometries); a lone disc or polygon is the composite of one added part. */
 /* ---------------------------------------------------------------------- */
-/* signed distance outside the shape (negative inside) */
-static double sdist(const or_geom *g, double x, double y) {
-    if (g->P.shape_kind == 0) {
-        double dx = x - g->P.disc_cx, dy = y - g->P.disc_cy;
-        return sqrt(dx * dx + dy * dy) - g->P.disc_r;
+/* signed distance of one part (negative inside) */
+static double part_sdist(const o_part *q, double x, double y) {
+    if (q->kind == 0) {
+        double dx = x - q->cx, dy = y - q->cy;
+        return sqrt(dx * dx + dy * dy) - q->r;
     }
     double d = -INFINITY;
-    for (int e = 0; e < g->P.n_vert; ++e) {
-        double v = (x - g->vx[e]) * g->nxe[e] + (y - g->vy[e]) * g->nye[e];
+    for (int e = 0; e < q->nv; ++e) {
+        double v = (x - q->vx[e]) * q->nx[e] + (y - q->vy[e]) * q->ny[e];
         if (v > d) d = v;
     }
     return d;
 }
 
-/* Intersection of the line B + s*e with the shape: returns 0 if empty. */
-static int chord(const or_geom *g, double bx, double by, double ex, double ey, double *smin,
-                 double *smax, int *elo, int *ehi) {
-    double h = g->P.h;
+/* signed distance of the grain: the union takes the minimum, the removal of
+   a part the maximum with the part's negated distance */
+static double sdist(const or_geom *g, double x, double y) {
+    double d = INFINITY;
+    for (int k = 0; k < g->nparts; ++k) {
+        double dk = part_sdist(&g->parts[k], x, y);
+        if (g->parts[k].add) {
+            if (dk < d) d = dk;
+        } else if (-dk > d) {
+            d = -dk;
+        }
+    }
+    return d;
+}
+
+/* Interval of the line B + s*e inside one part: returns 0 if it is empty or
+   not longer than tol.  For a polygon, e0/e1 are the entering / leaving
+   edges: the lowest index whose bound is within tol of the extremum. */
+static int part_chord(const o_part *q, double bx, double by, double ex, double ey, double tol,
+                      double *smin, double *smax, int *elo, int *ehi) {
     *elo = *ehi = -1;
-    if (g->P.shape_kind == 0) {
-        double dx = bx - g->P.disc_cx, dy = by - g->P.disc_cy;
+    if (q->kind == 0) {
+        double dx = bx - q->cx, dy = by - q->cy;
         double b = dx * ex + dy * ey;
-        double c = dx * dx + dy * dy - g->P.disc_r * g->P.disc_r;
+        double c = dx * dx + dy * dy - q->r * q->r;
         double disc = b * b - c;
         if (disc <= 0.0) return 0;
         double r = sqrt(disc);
@@ -175,12 +214,12 @@ static int chord(const or_geom *g, double bx, double by, double ex, double ey, d
         *smax = -b + r;
     } else {
         double lo = -INFINITY, hi = INFINITY;
-        int n = g->P.n_vert;
+        int n = q->nv;
         double *bound = malloc(sizeof(double) * n);
         int *kind = malloc(sizeof(int) * n);
         for (int e = 0; e < n; ++e) {
-            double f0 = (bx - g->vx[e]) * g->nxe[e] + (by - g->vy[e]) * g->nye[e];
-            double ge = ex * g->nxe[e] + ey * g->nye[e];
+            double f0 = (bx - q->vx[e]) * q->nx[e] + (by - q->vy[e]) * q->ny[e];
+            double ge = ex * q->nx[e] + ey * q->ny[e];
             kind[e] = 0;
             if (ge > 0.0) {           /* leaving through edge e at s = -f0/ge */
                 bound[e] = -f0 / ge;
@@ -196,38 +235,147 @@ static int chord(const or_geom *g, double bx, double by, double ex, double ey, d
                 return 0;
             }
         }
-        /* active edges: lowest index within the tolerance of the extremum */
         for (int e = 0; e < n && *elo < 0; ++e)
-            if (kind[e] == -1 && bound[e] >= lo - TAU * h) *elo = e;
+            if (kind[e] == -1 && bound[e] >= lo - tol) *elo = e;
         for (int e = 0; e < n && *ehi < 0; ++e)
-            if (kind[e] == 1 && bound[e] <= hi + TAU * h) *ehi = e;
+            if (kind[e] == 1 && bound[e] <= hi + tol) *ehi = e;
         free(bound);
         free(kind);
         *smin = lo;
         *smax = hi;
     }
-    return (*smax - *smin) > TAU * h;
+    return (*smax - *smin) > tol;
 }
 
-static void normal_at(const or_geom *g, double px, double py, int edge, double *nx, double *ny) {
-    if (g->P.shape_kind == 0) {
-        double dx = px - g->P.disc_cx, dy = py - g->P.disc_cy;
+/* The chords of the line B + s*e: the maximal intervals of s inside the
+   grain, ascending, built part by part in order (union with an added part's
+   interval, difference with a removed part's).  Part intervals not longer
+   than tol are ignored; intervals that overlap or touch within tol merge; a
+   difference leaves only pieces longer than tol, and a removed interval that
+   overlaps a chord by no more than tol leaves it whole.  On equal ends the
+   earlier part keeps the end.  Arrays hold 2 * nparts + 1 entries. */
+static int comp_chords(const or_geom *g, double bx, double by, double ex, double ey, double tol,
+                       double *lo, double *hi, o_tag *tlo, o_tag *thi) {
+    int n = 0;
+    for (int k = 0; k < g->nparts; ++k) {
+        const o_part *q = &g->parts[k];
+        double a, b;
+        int ea, eb;
+        if (!part_chord(q, bx, by, ex, ey, tol, &a, &b, &ea, &eb)) continue;
+        o_tag ta = {k, ea, q->add ? 1 : -1}, tb = {k, eb, q->add ? 1 : -1};
+        if (q->add) {
+            int first = -1, last = -1;
+            for (int i = 0; i < n; ++i)
+                if (lo[i] <= b + tol && hi[i] >= a - tol) {
+                    if (first < 0) first = i;
+                    last = i;
+                }
+            if (first < 0) {
+                int pos = 0;
+                while (pos < n && lo[pos] < a) ++pos;
+                for (int i = n; i > pos; --i) {
+                    lo[i] = lo[i - 1];
+                    hi[i] = hi[i - 1];
+                    tlo[i] = tlo[i - 1];
+                    thi[i] = thi[i - 1];
+                }
+                lo[pos] = a;
+                hi[pos] = b;
+                tlo[pos] = ta;
+                thi[pos] = tb;
+                ++n;
+            } else {
+                if (a < lo[first]) {
+                    lo[first] = a;
+                    tlo[first] = ta;
+                }
+                if (b > hi[last]) {
+                    hi[first] = b;
+                    thi[first] = tb;
+                } else {
+                    hi[first] = hi[last];
+                    thi[first] = thi[last];
+                }
+                int gone = last - first;
+                for (int i = first + 1; i + gone < n; ++i) {
+                    lo[i] = lo[i + gone];
+                    hi[i] = hi[i + gone];
+                    tlo[i] = tlo[i + gone];
+                    thi[i] = thi[i + gone];
+                }
+                n -= gone;
+            }
+        } else {
+            double nlo[n + 1], nhi[n + 1];
+            o_tag ntl[n + 1], nth[n + 1];
+            int m = 0;
+            for (int i = 0; i < n; ++i) {
+                if (hi[i] <= a + tol || lo[i] >= b - tol) {
+                    nlo[m] = lo[i];
+                    nhi[m] = hi[i];
+                    ntl[m] = tlo[i];
+                    nth[m] = thi[i];
+                    ++m;
+                    continue;
+                }
+                if (a - lo[i] > tol) {
+                    nlo[m] = lo[i];
+                    nhi[m] = a;
+                    ntl[m] = tlo[i];
+                    nth[m] = ta;
+                    ++m;
+                }
+                if (hi[i] - b > tol) {
+                    nlo[m] = b;
+                    nhi[m] = hi[i];
+                    ntl[m] = tb;
+                    nth[m] = thi[i];
+                    ++m;
+                }
+            }
+            for (int i = 0; i < m; ++i) {
+                lo[i] = nlo[i];
+                hi[i] = nhi[i];
+                tlo[i] = ntl[i];
+                thi[i] = nth[i];
+            }
+            n = m;
+        }
+    }
+    return n;
+}
+
+/* outward normal of the grain at a chord end */
+static void end_normal(const or_geom *g, o_tag t, double px, double py, double *nx, double *ny) {
+    const o_part *q = &g->parts[t.part];
+    if (q->kind == 0) {
+        double dx = px - q->cx, dy = py - q->cy;
         double r = sqrt(dx * dx + dy * dy);
-        *nx = dx / r;
-        *ny = dy / r;
+        *nx = t.sign * dx / r;
+        *ny = t.sign * dy / r;
     } else {
-        *nx = g->nxe[edge];
-        *ny = g->nye[edge];
+        *nx = t.sign * q->nx[t.edge];
+        *ny = t.sign * q->ny[t.edge];
     }
 }
 
-/* line index of pair p: l in [l_lo, l_hi] -> global line index */
-static inline int gline(const or_geom *g, int p, int l) { return g->line_off[p] + (l - g->l_lo[p]); }
+/* lattice-line record of line l of pair p */
+static inline int glat(const or_geom *g, int p, int l) { return g->lat_off[p] + (l - g->l_lo[p]); }
 
-/* Bilinear link: exit values of angles bracketing direction (ux,uy) on lines
-   bracketing point (px,py).  Writes 4 taps. */
-static void make_link(const or_geom *g, double px, double py, double ux, double uy, int *ta,
-                      int *tl, double *tw) {
+/* Bilinear link: boundary values of the angles bracketing direction (ux,uy),
+   on the lattice lines bracketing point (px,py), which lies on the boundary
+   of part `part`.  The value is taken at each tapped chord's exit end (in
+   that angle's direction of travel) for gamma, which runs along the travel,
+   and at its entry end for gamma~ (at_entry = 1), which runs against it.  A
+   line index outside the pair's range is clamped; a line without chords is
+   replaced by the nearest one with chords.  On each line the candidates are
+   the chords whose end of interest lies on the same part, and the one whose
+   end lies nearest to the point along the line is taken; a line without a
+   candidate (it passes the part, e.g. beside a hole) gives its weight to the
+   other line's chord, and when neither line has one the nearest end of any
+   part is taken.  Writes 4 taps (angle, global chord index, weight). */
+static void make_link(const or_geom *g, double px, double py, double ux, double uy, int part,
+                      int at_entry, int *ta, int *tl, double *tw) {
     int N = g->N;
     double psi = atan2(uy, ux);
     if (psi < 0.0) psi += 2.0 * M_PI;
@@ -243,19 +391,66 @@ static void make_link(const or_geom *g, double px, double py, double ux, double 
         int p = j % g->npair;
         double epx = -g->vh[2 * p + 1], epy = g->vh[2 * p]; /* e_perp of the pair */
         double c = ((px - g->Ox) * epx + (py - g->Oy) * epy) / g->P.h;
+        double sp = (px - g->Ox) * g->vh[2 * p] + (py - g->Oy) * g->vh[2 * p + 1];
         int i0 = (int)floor(c);
         double wl = c - i0;
         int ls[2] = {i0, i0 + 1};
         double wls[2] = {1.0 - wl, wl};
+        int pick[2], same[2];
         for (int b = 0; b < 2; ++b) {
             int l = ls[b];
             if (l < g->l_lo[p]) l = g->l_lo[p];
             if (l > g->l_hi[p]) l = g->l_hi[p];
+            l = g->lat_chorded[glat(g, p, l)];
+            int lat = glat(g, p, l);
+            int best_any = -1, best_same = -1;
+            double d_any = INFINITY, d_same = INFINITY;
+            for (int q = 0; q < g->lat_nc[lat]; ++q) {
+                int L = g->lat_c0[lat] + q;
+                int hi_end = (j < g->npair) != (at_entry != 0);  /* the end at smax? */
+                double se = hi_end ? g->smax[L] : g->smin[L];
+                int ep = hi_end ? g->tag_hi[L].part : g->tag_lo[L].part;
+                double d = fabs(se - sp);
+                if (d < d_any) {
+                    d_any = d;
+                    best_any = L;
+                }
+                if (ep == part && d < d_same) {
+                    d_same = d;
+                    best_same = L;
+                }
+            }
+            same[b] = best_same >= 0;
+            pick[b] = same[b] ? best_same : best_any;
+        }
+        if (same[0] && !same[1]) pick[1] = pick[0];
+        if (same[1] && !same[0]) pick[0] = pick[1];
+        for (int b = 0; b < 2; ++b) {
             ta[2 * a + b] = j;
-            tl[2 * a + b] = l;
+            tl[2 * a + b] = pick[b];
             tw[2 * a + b] = was[a] * wls[b];
         }
     }
+}
+
+/* the chord with samples of lattice record `lat` nearest to the lattice
+   coordinate v (units of h) along the line: distance from v to [m0, m1];
+   ties to the chord of lower s */
+static int pick_sampled_chord(const or_geom *g, int lat, double v) {
+    int best = -1;
+    double bd = INFINITY;
+    for (int q = 0; q < g->lat_nc[lat]; ++q) {
+        int L = g->lat_c0[lat] + q;
+        if (g->ns[L] < 1) continue;
+        double d = 0.0;
+        if (v < g->m0[L]) d = g->m0[L] - v;
+        else if (v > g->m1[L]) d = v - g->m1[L];
+        if (d < bd) {
+            bd = d;
+            best = L;
+        }
+    }
+    return best;
 }
 
 static double polygon_area(int n, const double *x, const double *y) {
@@ -267,15 +462,168 @@ static double polygon_area(int n, const double *x, const double *y) {
     return 0.5 * s;
 }
 
+/* y of the points where the boundaries of parts a and b cross (appended) */
+static int crossings_y(const o_part *a, const o_part *b, double *ys) {
+    int n = 0;
+    if (a->kind == 0 && b->kind == 0) {
+        double dx = b->cx - a->cx, dy = b->cy - a->cy, d = sqrt(dx * dx + dy * dy);
+        if (d == 0.0 || d > a->r + b->r || d < fabs(a->r - b->r)) return 0;
+        double s = (a->r * a->r - b->r * b->r + d * d) / (2.0 * d);
+        double hh = a->r * a->r - s * s;
+        hh = hh > 0.0 ? sqrt(hh) : 0.0;
+        ys[n++] = a->cy + s * dy / d + hh * dx / d;
+        ys[n++] = a->cy + s * dy / d - hh * dx / d;
+        return n;
+    }
+    if (a->kind == 1 && b->kind == 0) return crossings_y(b, a, ys);
+    if (a->kind == 0) { /* circle a, polygon b: |P0 + t D - c|^2 = r^2 on each edge */
+        for (int e = 0; e < b->nv; ++e) {
+            int f = (e + 1) % b->nv;
+            double Dx = b->vx[f] - b->vx[e], Dy = b->vy[f] - b->vy[e];
+            double fx = b->vx[e] - a->cx, fy = b->vy[e] - a->cy;
+            double A = Dx * Dx + Dy * Dy, B = 2.0 * (fx * Dx + fy * Dy), C = fx * fx + fy * fy - a->r * a->r;
+            double disc = B * B - 4.0 * A * C;
+            if (disc < 0.0) continue;
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                double t = (-B + sgn * sqrt(disc)) / (2.0 * A);
+                if (t >= 0.0 && t <= 1.0) ys[n++] = b->vy[e] + t * Dy;
+            }
+        }
+        return n;
+    }
+    for (int e = 0; e < a->nv; ++e) { /* two polygons: edge against edge */
+        int f = (e + 1) % a->nv;
+        double rx = a->vx[f] - a->vx[e], ry = a->vy[f] - a->vy[e];
+        for (int k = 0; k < b->nv; ++k) {
+            int m = (k + 1) % b->nv;
+            double sx = b->vx[m] - b->vx[k], sy = b->vy[m] - b->vy[k];
+            double den = rx * sy - ry * sx;
+            if (den == 0.0) continue;
+            double qx = b->vx[k] - a->vx[e], qy = b->vy[k] - a->vy[e];
+            double t = (qx * sy - qy * sx) / den, u = (qx * ry - qy * rx) / den;
+            if (t >= 0.0 && t <= 1.0 && u >= 0.0 && u <= 1.0) ys[n++] = a->vy[e] + t * ry;
+        }
+    }
+    return n;
+}
+
+static int cmp_double(const void *a, const void *b) {
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : x > y;
+}
+
+/* Area of a composite grain: the integral over y of the total length of the
+   grain's horizontal chords.  Between consecutive breakpoints (top and bottom
+   of every disc, every polygon vertex, every crossing of two part boundaries)
+   each chord end stays on one disc half or one polygon edge, so the slab's
+   integral is exact: int sqrt(r^2 - u^2) du = (u sqrt(r^2 - u^2) + r^2 asin(u/r))/2
+   for a disc end, the midpoint value times the height for an edge end. */
+static double composite_area(const or_geom *g) {
+    int cap = 4;
+    for (int k = 0; k < g->nparts; ++k) cap += g->parts[k].kind == 0 ? 2 : g->parts[k].nv;
+    int maxv = 2;
+    for (int k = 0; k < g->nparts; ++k)
+        if (g->parts[k].kind == 1 && g->parts[k].nv > maxv) maxv = g->parts[k].nv;
+    cap += g->nparts * g->nparts * 2 * maxv * maxv;
+    double *ys = malloc(sizeof(double) * cap);
+    int ny = 0;
+    for (int k = 0; k < g->nparts; ++k) {
+        const o_part *q = &g->parts[k];
+        if (q->kind == 0) {
+            ys[ny++] = q->cy - q->r;
+            ys[ny++] = q->cy + q->r;
+        } else {
+            for (int e = 0; e < q->nv; ++e) ys[ny++] = q->vy[e];
+        }
+        for (int k2 = 0; k2 < k; ++k2) ny += crossings_y(&g->parts[k2], q, ys + ny);
+    }
+    qsort(ys, ny, sizeof(double), cmp_double);
+    int nc = 2 * g->nparts + 1;
+    double *lo = malloc(sizeof(double) * nc), *hi = malloc(sizeof(double) * nc);
+    o_tag *tlo = malloc(sizeof(o_tag) * nc), *thi = malloc(sizeof(o_tag) * nc);
+    double area = 0.0;
+    for (int s = 0; s + 1 < ny; ++s) {
+        double ya = ys[s], yb = ys[s + 1];
+        if (!(yb > ya)) continue;
+        double ym = 0.5 * (ya + yb);
+        int n = comp_chords(g, 0.0, ym, 1.0, 0.0, 0.0, lo, hi, tlo, thi);
+        for (int i = 0; i < n; ++i) {
+            for (int end = 0; end < 2; ++end) {
+                o_tag t = end ? thi[i] : tlo[i];
+                double xm = end ? hi[i] : lo[i];
+                const o_part *q = &g->parts[t.part];
+                double integ;
+                if (q->kind == 0) {
+                    double r = q->r, sg = xm >= q->cx ? 1.0 : -1.0;
+                    double ua = fmax(-r, fmin(r, ya - q->cy)), ub = fmax(-r, fmin(r, yb - q->cy));
+                    double Fa = 0.5 * (ua * sqrt(fmax(0.0, r * r - ua * ua)) + r * r * asin(ua / r));
+                    double Fb = 0.5 * (ub * sqrt(fmax(0.0, r * r - ub * ub)) + r * r * asin(ub / r));
+                    integ = q->cx * (yb - ya) + sg * (Fb - Fa);
+                } else {
+                    integ = xm * (yb - ya);  /* linear along the slab: exact at the midpoint */
+                }
+                area += end ? integ : -integ;
+            }
+        }
+    }
+    free(ys);
+    free(lo);
+    free(hi);
+    free(tlo);
+    free(thi);
+    return area;
+}
+
 void or_geom_free(or_geom *g) {
     if (!g) return;
-    void *ptrs[] = {g->vx, g->vy, g->nxe, g->nye, g->mask, g->ghost, g->w, g->vh, /* eta is eta_c */
-                    g->l_lo, g->l_hi, g->line_off, g->samp_off, g->smin, g->smax, g->m0,
-                    g->m1, g->ns, g->edge_lo, g->edge_hi, g->soff, g->nearest_line,
+    for (int k = 0; k < g->nparts && g->parts; ++k) {
+        free(g->parts[k].vx);
+        free(g->parts[k].vy);
+        free(g->parts[k].nx);
+        free(g->parts[k].ny);
+    }
+    void *ptrs[] = {g->parts, g->mask, g->ghost, g->w, g->vh, /* eta is eta_c */
+                    g->l_lo, g->l_hi, g->line_off, g->samp_off, g->lat_off, g->lat_c0, g->lat_nc,
+                    g->lat_chorded, g->lat_near, g->ch_pair, g->ch_l, g->smin, g->smax, g->tag_lo,
+                    g->tag_hi, g->m0, g->m1, g->ns, g->soff,
                     g->lk_g_angle, g->lk_g_line, g->lk_g_w, g->lk_t_angle, g->lk_t_line,
                     g->lk_t_w, g->ang_line_off, g->ang_samp_off, g->ewt, g->eta_c};
     for (size_t i = 0; i < sizeof ptrs / sizeof ptrs[0]; ++i) free(ptrs[i]);
     free(g);
+}
+
+/* copy one part; returns 0 or fails */
+static int load_part(o_part *q, int kind, int add, double cx, double cy, double r, int nv,
+                     const double *vx, const double *vy) {
+    memset(q, 0, sizeof *q);
+    q->kind = kind;
+    q->add = add ? 1 : 0;
+    if (kind == 0) {
+        if (!(r > 0)) return fail("disc radius must be > 0");
+        q->cx = cx;
+        q->cy = cy;
+        q->r = r;
+        return 0;
+    }
+    if (kind != 1) return fail("unknown part kind");
+    if (nv < 3 || !vx || !vy) return fail("polygon needs >= 3 vertices");
+    q->nv = nv;
+    q->vx = malloc(sizeof(double) * nv);
+    q->vy = malloc(sizeof(double) * nv);
+    q->nx = malloc(sizeof(double) * nv);
+    q->ny = malloc(sizeof(double) * nv);
+    memcpy(q->vx, vx, sizeof(double) * nv);
+    memcpy(q->vy, vy, sizeof(double) * nv);
+    for (int e = 0; e < nv; ++e) {
+        int f = (e + 1) % nv;
+        double dx = q->vx[f] - q->vx[e], dy = q->vy[f] - q->vy[e];
+        double len = sqrt(dx * dx + dy * dy);
+        if (!(len > 0)) return fail("polygon has a repeated vertex");
+        q->nx[e] = dy / len;   /* outward for counter-clockwise order */
+        q->ny[e] = -dx / len;
+    }
+    if (!(polygon_area(nv, q->vx, q->vy) > 0)) return fail("polygon must be counter-clockwise");
+    return 0;
 }
 
 or_geom *or_geom_create(const or_params *prm) {
@@ -286,37 +634,67 @@ or_geom *or_geom_create(const or_params *prm) {
     if (prm->stepper != 0 && prm->stepper != 1) { fail("stepper must be 0 or 1"); return NULL; }
     if (prm->n_components < 0 || prm->n_components > 4) { fail("1 to 4 components"); return NULL; }
     if (!(prm->t > 0 && prm->t <= 1)) { fail("t out of (0,1]"); return NULL; }
-    if (prm->shape_kind == 1 && (prm->n_vert < 3 || !prm->vx || !prm->vy)) {
-        fail("polygon needs >= 3 vertices");
-        return NULL;
-    }
+    if (prm->gauge < 0 || prm->gauge > 2) { fail("gauge must be 0, 1 or 2"); return NULL; }
     or_geom *g = calloc(1, sizeof *g);
     g->P = *prm;
     int nx = prm->nx, ny = prm->ny;
     double h = prm->h;
-    if (prm->shape_kind == 1) {
-        int n = prm->n_vert;
-        g->vx = malloc(sizeof(double) * n);
-        g->vy = malloc(sizeof(double) * n);
-        g->nxe = malloc(sizeof(double) * n);
-        g->nye = malloc(sizeof(double) * n);
-        memcpy(g->vx, prm->vx, sizeof(double) * n);
-        memcpy(g->vy, prm->vy, sizeof(double) * n);
-        for (int e = 0; e < n; ++e) {
-            int f = (e + 1) % n;
-            double dx = g->vx[f] - g->vx[e], dy = g->vy[f] - g->vy[e];
-            double len = sqrt(dx * dx + dy * dy);
-            g->nxe[e] = dy / len;   /* outward for counter-clockwise order */
-            g->nye[e] = -dx / len;
+
+    /* parts */
+    if (prm->shape_kind == 0 || prm->shape_kind == 1) {
+        g->nparts = 1;
+        g->parts = calloc(1, sizeof(o_part));
+        if (load_part(&g->parts[0], prm->shape_kind, 1, prm->disc_cx, prm->disc_cy, prm->disc_r,
+                      prm->n_vert, prm->vx, prm->vy)) {
+            or_geom_free(g);
+            return NULL;
         }
-        g->area = polygon_area(n, g->vx, g->vy);
-        if (!(g->area > 0)) { fail("polygon must be counter-clockwise"); or_geom_free(g); return NULL; }
+        const o_part *q = &g->parts[0];
+        g->area = q->kind == 0 ? M_PI * q->r * q->r : polygon_area(q->nv, q->vx, q->vy);
+    } else if (prm->shape_kind == 2) {
+        if (prm->n_parts < 1 || !prm->parts) { fail("composite grain needs parts"); or_geom_free(g); return NULL; }
+        g->nparts = prm->n_parts;
+        g->parts = calloc(prm->n_parts, sizeof(o_part));
+        for (int k = 0; k < prm->n_parts; ++k) {
+            const or_part *s = &prm->parts[k];
+            if (load_part(&g->parts[k], s->kind, s->add, s->cx, s->cy, s->r, s->n_vert, s->vx, s->vy)) {
+                or_geom_free(g);
+                return NULL;
+            }
+        }
+        g->area = composite_area(g);
+        if (!(g->area > 0)) { fail("composite grain has no area"); or_geom_free(g); return NULL; }
     } else {
-        if (!(prm->disc_r > 0)) { fail("disc radius"); or_geom_free(g); return NULL; }
-        g->area = M_PI * prm->disc_r * prm->disc_r;
+        fail("unknown shape_kind");
+        or_geom_free(g);
+        return NULL;
     }
-    g->P.vx = g->vx;
-    g->P.vy = g->vy;
+    g->P.vx = g->P.vy = NULL;
+    g->P.parts = NULL;
+
+    /* every added part lies inside the grid box */
+    {
+        double xlo = prm->x0, xhi = prm->x0 + nx * h, ylo = prm->y0, yhi = prm->y0 + ny * h;
+        int ok = 1;
+        for (int k = 0; k < g->nparts; ++k) {
+            const o_part *q = &g->parts[k];
+            if (!q->add) continue;
+            if (q->kind == 0) {
+                ok = ok && q->cx - q->r >= xlo && q->cx + q->r <= xhi && q->cy - q->r >= ylo &&
+                     q->cy + q->r <= yhi;
+            } else {
+                for (int e = 0; e < q->nv; ++e)
+                    ok = ok && q->vx[e] >= xlo && q->vx[e] <= xhi && q->vy[e] >= ylo && q->vy[e] <= yhi;
+            }
+        }
+        if (!ok) { fail("shape extends outside the grid box"); or_geom_free(g); return NULL; }
+    }
+    /* the solenoid gauge's flux line must lie outside the grain */
+    if (prm->gauge == 2 && !(sdist(g, prm->gauge_cx, prm->gauge_cy) > TAU * h)) {
+        fail("solenoid gauge: the flux line must lie outside the grain");
+        or_geom_free(g);
+        return NULL;
+    }
 
     /* mask: grid point centre inside (boundary counts as inside) */
     g->mask = calloc((size_t)nx * ny, 1);
@@ -330,20 +708,6 @@ or_geom *or_geom_create(const or_params *prm) {
             }
         }
     if (g->n_in == 0) { fail("empty mask"); or_geom_free(g); return NULL; }
-
-    /* shape must lie inside the grid box */
-    {
-        double xlo = prm->x0, xhi = prm->x0 + nx * h, ylo = prm->y0, yhi = prm->y0 + ny * h;
-        int ok = 1;
-        if (prm->shape_kind == 0) {
-            ok = prm->disc_cx - prm->disc_r >= xlo && prm->disc_cx + prm->disc_r <= xhi &&
-                 prm->disc_cy - prm->disc_r >= ylo && prm->disc_cy + prm->disc_r <= yhi;
-        } else {
-            for (int e = 0; e < prm->n_vert; ++e)
-                ok = ok && g->vx[e] >= xlo && g->vx[e] <= xhi && g->vy[e] >= ylo && g->vy[e] <= yhi;
-        }
-        if (!ok) { fail("shape extends outside the grid box"); or_geom_free(g); return NULL; }
-    }
 
     /* ghost map on the padded index range [-1,nx] x [-1,ny]: every index whose
        centre is within 1.5 h of the shape maps to the nearest in-mask grid point
@@ -405,85 +769,110 @@ or_geom *or_geom_create(const or_params *prm) {
     g->Ox = prm->x0 + 0.5 * nx * h + prm->lattice_ox * h;
     g->Oy = prm->y0 + 0.5 * ny * h + prm->lattice_oy * h;
     double rext = 0.0;
-    if (prm->shape_kind == 0) {
-        rext = hypot(prm->disc_cx - g->Ox, prm->disc_cy - g->Oy) + prm->disc_r;
-    } else {
-        for (int e = 0; e < prm->n_vert; ++e) {
-            double d = hypot(g->vx[e] - g->Ox, g->vy[e] - g->Oy);
+    for (int k = 0; k < g->nparts; ++k) {
+        const o_part *q = &g->parts[k];
+        if (!q->add) continue;
+        if (q->kind == 0) {
+            double d = hypot(q->cx - g->Ox, q->cy - g->Oy) + q->r;
             if (d > rext) rext = d;
+        } else {
+            for (int e = 0; e < q->nv; ++e) {
+                double d = hypot(q->vx[e] - g->Ox, q->vy[e] - g->Oy);
+                if (d > rext) rext = d;
+            }
         }
     }
     int Lmax = (int)ceil(rext / h) + 1;
 
-    /* lines per pair (first pass: ranges) */
+    /* chords of every lattice line of every pair */
+    int nc = 2 * g->nparts + 1;
+    double *clo = malloc(sizeof(double) * nc), *chi = malloc(sizeof(double) * nc);
+    o_tag *ctl = malloc(sizeof(o_tag) * nc), *cth = malloc(sizeof(o_tag) * nc);
     g->l_lo = malloc(sizeof(int) * np);
     g->l_hi = malloc(sizeof(int) * np);
     g->line_off = malloc(sizeof(int) * (np + 1));
     g->samp_off = malloc(sizeof(int) * (np + 1));
+    g->lat_off = malloc(sizeof(int) * (np + 1));
+    int nch = 0, cap_ch = 0, nlat = 0, cap_lat = 0;
+    g->line_off[0] = g->samp_off[0] = g->lat_off[0] = 0;
     for (int p = 0; p < np; ++p) {
         double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
         double qx = -ey, qy = ex;
         int lo = 1 << 30, hi = -(1 << 30);
-        for (int l = -Lmax; l <= Lmax; ++l) {
-            double s0, s1;
-            int a, b;
-            if (chord(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, &s0, &s1, &a, &b)) {
+        for (int l = -Lmax; l <= Lmax; ++l)
+            if (comp_chords(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, TAU * h, clo, chi, ctl, cth) > 0) {
                 if (l < lo) lo = l;
                 if (l > hi) hi = l;
             }
-        }
-        if (lo > hi) { fail("pair without lines"); or_geom_free(g); return NULL; }
+        if (lo > hi) { fail("pair without lines"); goto bad; }
         g->l_lo[p] = lo;
         g->l_hi[p] = hi;
-    }
-    g->line_off[0] = 0;
-    for (int p = 0; p < np; ++p) g->line_off[p + 1] = g->line_off[p] + g->l_hi[p] - g->l_lo[p] + 1;
-    int nl = g->line_off[np];
-    g->smin = malloc(sizeof(double) * nl);
-    g->smax = malloc(sizeof(double) * nl);
-    g->m0 = malloc(sizeof(int) * nl);
-    g->m1 = malloc(sizeof(int) * nl);
-    g->ns = malloc(sizeof(int) * nl);
-    g->edge_lo = malloc(sizeof(int) * nl);
-    g->edge_hi = malloc(sizeof(int) * nl);
-    g->soff = malloc(sizeof(int) * nl);
-    g->nearest_line = malloc(sizeof(int) * nl);
-    g->samp_off[0] = 0;
-    for (int p = 0; p < np; ++p) {
-        double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
-        double qx = -ey, qy = ex;
         int cnt = 0;
-        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
-            int L = gline(g, p, l);
-            double s0, s1;
-            int a, b;
-            if (!chord(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, &s0, &s1, &a, &b)) {
-                fail("line range of a pair is not contiguous (shape not convex?)");
-                or_geom_free(g);
-                return NULL;
+        for (int l = lo; l <= hi; ++l) {
+            int n = comp_chords(g, g->Ox + l * h * qx, g->Oy + l * h * qy, ex, ey, TAU * h, clo, chi, ctl, cth);
+            if (nlat >= cap_lat) {
+                cap_lat = cap_lat ? 2 * cap_lat : 256;
+                g->lat_c0 = realloc(g->lat_c0, sizeof(int) * cap_lat);
+                g->lat_nc = realloc(g->lat_nc, sizeof(int) * cap_lat);
             }
-            g->smin[L] = s0;
-            g->smax[L] = s1;
-            g->edge_lo[L] = a;
-            g->edge_hi[L] = b;
-            g->m0[L] = (int)ceil(s0 / h - TAU);
-            g->m1[L] = (int)floor(s1 / h + TAU);
-            g->ns[L] = g->m1[L] - g->m0[L] + 1;
-            if (g->ns[L] < 0) g->ns[L] = 0;
-            g->soff[L] = cnt;
-            cnt += g->ns[L];
+            g->lat_c0[nlat] = nch;
+            g->lat_nc[nlat] = n;
+            ++nlat;
+            for (int i = 0; i < n; ++i) {
+                if (nch >= cap_ch) {
+                    cap_ch = cap_ch ? 2 * cap_ch : 256;
+                    g->ch_pair = realloc(g->ch_pair, sizeof(int) * cap_ch);
+                    g->ch_l = realloc(g->ch_l, sizeof(int) * cap_ch);
+                    g->smin = realloc(g->smin, sizeof(double) * cap_ch);
+                    g->smax = realloc(g->smax, sizeof(double) * cap_ch);
+                    g->tag_lo = realloc(g->tag_lo, sizeof(o_tag) * cap_ch);
+                    g->tag_hi = realloc(g->tag_hi, sizeof(o_tag) * cap_ch);
+                    g->m0 = realloc(g->m0, sizeof(int) * cap_ch);
+                    g->m1 = realloc(g->m1, sizeof(int) * cap_ch);
+                    g->ns = realloc(g->ns, sizeof(int) * cap_ch);
+                    g->soff = realloc(g->soff, sizeof(int) * cap_ch);
+                }
+                int L = nch++;
+                g->ch_pair[L] = p;
+                g->ch_l[L] = l;
+                g->smin[L] = clo[i];
+                g->smax[L] = chi[i];
+                g->tag_lo[L] = ctl[i];
+                g->tag_hi[L] = cth[i];
+                g->m0[L] = (int)ceil(clo[i] / h - TAU);
+                g->m1[L] = (int)floor(chi[i] / h + TAU);
+                g->ns[L] = g->m1[L] - g->m0[L] + 1;
+                if (g->ns[L] < 0) g->ns[L] = 0;
+                g->soff[L] = cnt;
+                cnt += g->ns[L];
+            }
         }
+        g->line_off[p + 1] = nch;
         g->samp_off[p + 1] = g->samp_off[p] + cnt;
-        /* nearest line with samples (ties -> lower index) */
+        g->lat_off[p + 1] = nlat;
+    }
+    g->lat_chorded = malloc(sizeof(int) * (nlat > 0 ? nlat : 1));
+    g->lat_near = malloc(sizeof(int) * (nlat > 0 ? nlat : 1));
+    for (int p = 0; p < np; ++p) {
+        /* nearest lattice line with a chord, and with a chord that has samples
+           (ties -> lower index) */
+        int any = 0;
         for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
-            int best = -(1 << 30), bd = 1 << 30;
+            int lat = glat(g, p, l);
+            for (int q = 0; q < g->lat_nc[lat]; ++q) any = any || g->ns[g->lat_c0[lat] + q] > 0;
+        }
+        if (!any) { fail("pair without samples"); goto bad; }
+        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
+            int bc = 0, dc = 1 << 30, bs = 0, ds = 1 << 30;
             for (int l2 = g->l_lo[p]; l2 <= g->l_hi[p]; ++l2) {
-                if (g->ns[gline(g, p, l2)] < 1) continue;
-                int d = abs(l2 - l);
-                if (d < bd) { bd = d; best = l2; }
+                int lat2 = glat(g, p, l2), d = abs(l2 - l);
+                int sampled = 0;
+                for (int q = 0; q < g->lat_nc[lat2]; ++q) sampled = sampled || g->ns[g->lat_c0[lat2] + q] > 0;
+                if (g->lat_nc[lat2] > 0 && d < dc) { dc = d; bc = l2; }
+                if (sampled && d < ds) { ds = d; bs = l2; }
             }
-            if (bd == (1 << 30)) { fail("pair without samples"); or_geom_free(g); return NULL; }
-            g->nearest_line[gline(g, p, l)] = best;
+            g->lat_chorded[glat(g, p, l)] = bc;
+            g->lat_near[glat(g, p, l)] = bs;
         }
     }
 
@@ -493,14 +882,16 @@ or_geom *or_geom_create(const or_params *prm) {
     g->ang_line_off[0] = g->ang_samp_off[0] = 0;
     for (int k = 0; k < N; ++k) {
         int p = k % np;
-        g->ang_line_off[k + 1] = g->ang_line_off[k] + (g->l_hi[p] - g->l_lo[p] + 1);
+        g->ang_line_off[k + 1] = g->ang_line_off[k] + (g->line_off[p + 1] - g->line_off[p]);
         g->ang_samp_off[k + 1] = g->ang_samp_off[k] + (g->samp_off[p + 1] - g->samp_off[p]);
     }
 
     /* boundary links, Sec. 3.1 and Fig. riccati_fig_A: entry of gamma for
-       angle k on line l takes the exit value of the specularly reflected
+       angle k on a chord takes the exit value of the specularly reflected
        incoming direction; gamma~ starts from the gamma~ value that leaves
-       along the reflected outgoing direction. */
+       along the reflected outgoing direction.  The normal is the grain's
+       outward normal where the chord ends (for an end on a removed part, the
+       part's inward normal). */
     int64_t NL = g->ang_line_off[N];
     g->lk_g_angle = malloc(sizeof(int) * 4 * NL);
     g->lk_g_line = malloc(sizeof(int) * 4 * NL);
@@ -514,31 +905,42 @@ or_geom *or_geom_create(const or_params *prm) {
         double ex = g->vh[2 * p], ey = g->vh[2 * p + 1];
         double qx = -ey, qy = ex;
         double vx = g->vh[2 * k], vy = g->vh[2 * k + 1];
-        for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
-            int L = gline(g, p, l);
-            int64_t A = g->ang_line_off[k] + (l - g->l_lo[p]);
+        for (int L = g->line_off[p]; L < g->line_off[p + 1]; ++L) {
+            int l = g->ch_l[L];
+            int64_t A = g->ang_line_off[k] + (L - g->line_off[p]);
             double bx = g->Ox + l * h * qx, by = g->Oy + l * h * qy;
-            /* entry end and exit end of the line in the direction of travel */
+            /* entry end and exit end of the chord in the direction of travel */
             double s_in = sg > 0 ? g->smin[L] : g->smax[L];
             double s_out = sg > 0 ? g->smax[L] : g->smin[L];
-            int e_in = sg > 0 ? g->edge_lo[L] : g->edge_hi[L];
-            int e_out = sg > 0 ? g->edge_hi[L] : g->edge_lo[L];
+            o_tag t_in = sg > 0 ? g->tag_lo[L] : g->tag_hi[L];
+            o_tag t_out = sg > 0 ? g->tag_hi[L] : g->tag_lo[L];
             double pex = bx + s_in * ex, pey = by + s_in * ey;
             double nnx, nny;
-            normal_at(g, pex, pey, e_in, &nnx, &nny);
+            end_normal(g, t_in, pex, pey, &nnx, &nny);
             double vn = vx * nnx + vy * nny;
             double uix = vx - 2.0 * vn * nnx, uiy = vy - 2.0 * vn * nny;
-            make_link(g, pex, pey, uix, uiy, &g->lk_g_angle[4 * A], &g->lk_g_line[4 * A],
+            make_link(g, pex, pey, uix, uiy, t_in.part, 0, &g->lk_g_angle[4 * A], &g->lk_g_line[4 * A],
                       &g->lk_g_w[4 * A]);
             double pxx = bx + s_out * ex, pxy = by + s_out * ey;
-            normal_at(g, pxx, pxy, e_out, &nnx, &nny);
+            end_normal(g, t_out, pxx, pxy, &nnx, &nny);
             vn = vx * nnx + vy * nny;
             double uox = vx - 2.0 * vn * nnx, uoy = vy - 2.0 * vn * nny;
-            make_link(g, pxx, pxy, uox, uoy, &g->lk_t_angle[4 * A], &g->lk_t_line[4 * A],
+            make_link(g, pxx, pxy, uox, uoy, t_out.part, 1, &g->lk_t_angle[4 * A], &g->lk_t_line[4 * A],
                       &g->lk_t_w[4 * A]);
         }
     }
+    free(clo);
+    free(chi);
+    free(ctl);
+    free(cth);
     return g;
+bad:
+    free(clo);
+    free(chi);
+    free(ctl);
+    free(cth);
+    or_geom_free(g);
+    return NULL;
 }
 
 int or_geom_info(const or_geom *g, int64_t *info) {
@@ -574,11 +976,20 @@ int or_geom_lines(const or_geom *g, int32_t *l_lo, int32_t *l_hi, double *smin, 
     }
     return 0;
 }
-int or_geom_links(const or_geom *g, int32_t *ta, int32_t *tl, double *tw) {
+int or_geom_chords(const or_geom *g, int32_t *pair, int32_t *l) {
+    for (int L = 0; L < g->line_off[g->npair]; ++L) {
+        pair[L] = g->ch_pair[L];
+        l[L] = g->ch_l[L];
+    }
+    return 0;
+}
+int or_geom_links(const or_geom *g, int32_t *ta, int32_t *tl, int32_t *tc, double *tw) {
     int64_t n = 4 * g->ang_line_off[g->N];
     for (int64_t i = 0; i < n; ++i) {
+        int L = g->lk_g_line[i];
         ta[i] = g->lk_g_angle[i];
-        tl[i] = g->lk_g_line[i];
+        tl[i] = g->ch_l[L];
+        tc[i] = L - g->line_off[g->ch_pair[L]];
         tw[i] = g->lk_g_w[i];
     }
     return 0;
@@ -619,13 +1030,29 @@ static int interp2(const or_geom *g, const double *f, double x, double y, double
     return 0;
 }
 
-/* total vector potential at a point: analytic symmetric-gauge external part
-   A_ext = B/2 (-(y-yg), x-xg) with B = pi alpha / area (units B0), plus the
-   interpolated induced part */
+/* Total vector potential at a point: the external part of the gauge,
+   analytic, plus the interpolated induced part.  Symmetric gauge
+   A = B/2 (-(y-yg), x-xg) and landau gauge A = B (-(y-yg), 0) with
+   B = pi alpha / area (units B0; Sec. 5.1.2); solenoid gauge
+   A = alpha/(2 r) phi^ = alpha/(2 r^2) (-(y-yg), x-xg) (Eq. solenoid_gauge
+   with Phi_ext = alpha Phi0, units A0 = Phi0/(pi xi0)). */
 static int a_total(const or_geom *g, const double *aind, double x, double y, double A[2]) {
-    double B = M_PI * g->P.flux_quanta / g->area;
-    A[0] = -0.5 * B * (y - g->P.gauge_cy);
-    A[1] = 0.5 * B * (x - g->P.gauge_cx);
+    double dx = x - g->P.gauge_cx, dy = y - g->P.gauge_cy;
+    if (g->P.gauge == 2) {
+        double r2 = dx * dx + dy * dy;
+        if (!(r2 > 0.0)) return -1;
+        A[0] = -0.5 * g->P.flux_quanta * dy / r2;
+        A[1] = 0.5 * g->P.flux_quanta * dx / r2;
+    } else {
+        double B = M_PI * g->P.flux_quanta / g->area;
+        if (g->P.gauge == 1) {
+            A[0] = -B * dy;
+            A[1] = 0.0;
+        } else {
+            A[0] = -0.5 * B * dy;
+            A[1] = 0.5 * B * dx;
+        }
+    }
     if (aind) {
         double ai[2];
         if (interp2(g, aind, x, y, ai)) return -1;
@@ -635,12 +1062,18 @@ static int a_total(const or_geom *g, const double *aind, double x, double y, dou
     return 0;
 }
 
+int or_external_a(const or_geom *g, int n, const double *xy, double *A) {
+    for (int i = 0; i < n; ++i)
+        if (a_total(g, NULL, xy[2 * i], xy[2 * i + 1], &A[2 * i])) return fail("gauge singular at a point");
+    return 0;
+}
+
 int or_sample_fields(const or_geom *g, const double *delta, const double *aind, int p,
                      double *ds, double *as) {
     double h = g->P.h;
     double ex = g->vh[2 * p], ey = g->vh[2 * p + 1], qx = -ey, qy = ex;
-    for (int l = g->l_lo[p]; l <= g->l_hi[p]; ++l) {
-        int L = gline(g, p, l);
+    for (int L = g->line_off[p]; L < g->line_off[p + 1]; ++L) {
+        int l = g->ch_l[L];
         for (int m = g->m0[L]; m <= g->m1[L]; ++m) {
             int idx = g->soff[L] + (m - g->m0[L]);
             double x = g->Ox + l * h * qx + m * h * ex, y = g->Oy + l * h * qy + m * h * ey;
@@ -774,9 +1207,8 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
             int k = 0;
             while (g->ang_line_off[k + 1] <= A) ++k;
             int p = k % np;
-            int li = (int)(A - g->ang_line_off[k]);
-            int l = g->l_lo[p] + li;
-            int L = gline(g, p, l);
+            int L = g->line_off[p] + (int)(A - g->ang_line_off[k]);
+            int l = g->ch_l[L];
             int sg = k < np ? 1 : -1;
             double vx = g->vh[2 * k], vy = g->vh[2 * k + 1];
             double eta = g->C > 1 ? 1.0 : g->eta[k];  /* combined fields already carry eta */
@@ -836,9 +1268,8 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                     gm = 0.0;
                     for (int q = 0; q < 4; ++q) {
                         int ja = g->lk_g_angle[4 * A + q];
-                        int jl = g->lk_g_line[4 * A + q];
-                        int jp = ja % np;
-                        int64_t B = g->ang_line_off[ja] + (jl - g->l_lo[jp]);
+                        int jc = g->lk_g_line[4 * A + q];
+                        int64_t B = g->ang_line_off[ja] + (jc - g->line_off[ja % np]);
                         gm += g->lk_g_w[4 * A + q] *
                               (exit_in[2 * (B * n_e + n)] + I * exit_in[2 * (B * n_e + n) + 1]);
                     }
@@ -860,9 +1291,8 @@ int or_sweep(const or_geom *g, const double *delta, const double *aind, const do
                     gt = 0.0;
                     for (int q = 0; q < 4; ++q) {
                         int ja = g->lk_t_angle[4 * A + q];
-                        int jl = g->lk_t_line[4 * A + q];
-                        int jp = ja % np;
-                        int64_t B = g->ang_line_off[ja] + (jl - g->l_lo[jp]);
+                        int jc = g->lk_t_line[4 * A + q];
+                        int64_t B = g->ang_line_off[ja] + (jc - g->line_off[ja % np]);
                         int64_t ii = 2 * (NLA * n_e + B * n_e + n);
                         gt += g->lk_t_w[4 * A + q] * (exit_in[ii] + I * exit_in[ii + 1]);
                     }
@@ -960,8 +1390,9 @@ int or_rotate_back(const or_geom *g, const double *images, int mode, int n_e, do
                 int l = iu + b;
                 if (l < g->l_lo[p]) l = g->l_lo[p];
                 if (l > g->l_hi[p]) l = g->l_hi[p];
-                int l2 = g->nearest_line[gline(g, p, l)];
-                int L = gline(g, p, l2);
+                /* the nearest line with samples, and on it the sampled chord
+                   nearest to the point along the line */
+                int L = pick_sampled_chord(g, glat(g, p, g->lat_near[glat(g, p, l)]), v);
                 for (int a = 0; a < 2; ++a) {
                     int m = iv + a;
                     if (m < g->m0[L]) m = g->m0[L];
@@ -1173,7 +1604,7 @@ int or_sweep_subset(const or_geom *g, const double *delta, const double *aind, c
             return -1;
         }
         double vx = g->vh[2 * k], vy = g->vh[2 * k + 1], eta = g->C > 1 ? 1.0 : g->eta[k];
-        int nl = g->l_hi[p] - g->l_lo[p] + 1;
+        int nl = g->line_off[p + 1] - g->line_off[p];
 #pragma omp parallel for schedule(dynamic, 1)
         for (int li = 0; li < nl; ++li) {
             int L = g->line_off[p] + li;

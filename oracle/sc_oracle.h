@@ -30,18 +30,31 @@
 #define SC_ORACLE_H
 #include <stdint.h>
 
+/* One part of a composite grain (Sec. 4, composite geometries): a disc or a
+   convex polygon whose area is added to, or removed from, the grain built by
+   the parts before it. */
+typedef struct {
+    int32_t kind;            /* 0 = disc, 1 = convex polygon (CCW vertices) */
+    int32_t add;             /* 1 = add the area, 0 = remove it */
+    double cx, cy, r;        /* disc centre and radius */
+    int32_t n_vert;
+    const double *vx, *vy;
+} or_part;
+
 typedef struct {
     int32_t nx, ny;          /* grid points; point (i,j) at (x0+(i+.5)h, y0+(j+.5)h) */
     double h, x0, y0;
-    int32_t shape_kind;      /* 0 = disc, 1 = convex polygon (CCW vertices) */
+    int32_t shape_kind;      /* 0 = disc, 1 = convex polygon (CCW vertices),
+                                2 = composite: the parts below, in order */
     double disc_cx, disc_cy, disc_r;
     int32_t n_vert;
     const double *vx, *vy;
     int32_t pairing;         /* 0 s, 1 d_{x2-y2}, 2 d_xy, 3 g */
     double crystal_rotation; /* units of 2 pi */
     double t;                /* T / Tc */
-    double flux_quanta;      /* alpha = B_ext * area / Phi0 */
-    double gauge_cx, gauge_cy;
+    double flux_quanta;      /* alpha: symmetric / landau gauge, B_ext * area / Phi0;
+                                solenoid gauge, flux threading the hole / Phi0 */
+    double gauge_cx, gauge_cy; /* gauge origin (solenoid: the flux line) */
     double kappa;            /* <= 0 : no induced A */
     int32_t charge_sign;     /* +1 / -1 */
     int32_t n_angles;        /* even */
@@ -53,6 +66,11 @@ typedef struct {
                                 0 or 1 = one (`pairing`), at most 4 */
     int32_t pairings[4];     /* basis of component c >= 1 (component 0 uses `pairing`) */
     double tc_ratios[4];     /* T_c^Gamma / T_c of each component (0 means 1) */
+    int32_t n_parts;         /* composite grain (shape_kind 2) */
+    const or_part *parts;
+    int32_t gauge;           /* external vector potential: 0 symmetric B/2 (-y, x),
+                                1 landau B (-y, 0), 2 solenoid alpha/(2 r^2) (-y, x)
+                                (Eq. solenoid_gauge), all about the gauge origin */
 } or_params;
 
 typedef struct or_geom or_geom;
@@ -62,18 +80,27 @@ const char *or_last_error(void);
 or_geom *or_geom_create(const or_params *p);
 void or_geom_free(or_geom *g);
 
-/* info[0]=n_pairs info[1]=total lines over pairs info[2]=total samples over pairs
+/* info[0]=n_pairs info[1]=total chords over pairs info[2]=total samples over pairs
    info[3]=n_in (mask points) info[4]=total lines over all angles (= 2*info[1])
    info[5]=total samples over all angles (= 2*info[2]) */
 int or_geom_info(const or_geom *g, int64_t *info);
 double or_geom_area(const or_geom *g);
 int or_geom_mask(const or_geom *g, uint8_t *mask);
 int or_geom_ghost(const or_geom *g, int32_t *ghost);  /* (nx+2)*(ny+2), -1 where unused */
-/* per pair: l_lo, l_hi; per line (pair-major): smin, smax, m0, m1 */
+/* A "line" below is one chord: a maximal piece of a lattice line inside the
+   grain.  Convex grains have one chord per lattice line; composite grains can
+   have several (ordered by s) or none.
+   per pair: l_lo, l_hi; per chord (pair-major, then l, then s): smin, smax, m0, m1 */
 int or_geom_lines(const or_geom *g, int32_t *l_lo, int32_t *l_hi, double *smin,
                   double *smax, int32_t *m0, int32_t *m1);
-/* entry links of gamma, [angle][line][4]: tap angle, tap line (absolute index), weight */
-int or_geom_links(const or_geom *g, int32_t *tap_angle, int32_t *tap_line, double *tap_w);
+/* per chord: its pair and lattice line index l */
+int or_geom_chords(const or_geom *g, int32_t *pair, int32_t *l);
+/* entry links of gamma, [angle][chord][4]: tap angle, lattice line l of the tapped
+   chord, the tapped chord's index within its pair, weight */
+int or_geom_links(const or_geom *g, int32_t *tap_angle, int32_t *tap_line, int32_t *tap_chord,
+                  double *tap_w);
+/* external vector potential of the gauge at n points (xy: [n][2], A: [n][2]) */
+int or_external_a(const or_geom *g, int n, const double *xy, double *A);
 int or_geom_quadrature(const or_geom *g, double *w, double *vhat, double *eta);
 
 /* Closed-form step of d gamma/ds = i (P g^2 + 2 Q g + R) over a length ell. */

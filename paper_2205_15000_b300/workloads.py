@@ -100,6 +100,62 @@ def polygon(vx, vy, h, margin=0.5, **kw):
                        gauge_cy=float(np.mean(vy)), **kw)
 
 
+def regular_polygon(center, n_edges, side_length, rotation=0.0):
+    """Vertices (counter-clockwise) of a regular polygon: centre, number of
+    edges, side length and rotation in units of a full turn (App. B's
+    regular_polygon).  Unrotated, the first vertex lies on the -y side so that
+    a square (n_edges 4) has edges parallel to the axes."""
+    cx, cy = center
+    R = side_length / (2.0 * math.sin(math.pi / n_edges))
+    a0 = -math.pi / 2 - math.pi / n_edges + 2.0 * math.pi * rotation
+    vx = [cx + R * math.cos(a0 + 2.0 * math.pi * k / n_edges) for k in range(n_edges)]
+    vy = [cy + R * math.sin(a0 + 2.0 * math.pi * k / n_edges) for k in range(n_edges)]
+    return vx, vy
+
+
+def disc_part(center, radius, add=True):
+    return dict(kind="disc", add=add, cx=float(center[0]), cy=float(center[1]), r=float(radius))
+
+
+def polygon_part(vx, vy, add=True):
+    return dict(kind="polygon", add=add, vx=[float(v) for v in vx], vy=[float(v) for v in vy])
+
+
+def composite(parts, h, margin=1.0, gauge_center=None, **kw):
+    """Composite grain (Sec. 4 and App. B): discs and convex polygons added and
+    removed in the listed order.  The grid has spacing ~h and covers the added
+    parts with `margin` grid points to spare; the gauge origin defaults to the
+    centre of that box."""
+    xs, ys = [], []
+    for q in parts:
+        if not q.get("add", True):
+            continue
+        if q["kind"] == "disc":
+            xs += [q["cx"] - q["r"], q["cx"] + q["r"]]
+            ys += [q["cy"] - q["r"], q["cy"] + q["r"]]
+        else:
+            xs += list(q["vx"])
+            ys += list(q["vy"])
+    xlo, xhi, ylo, yhi = min(xs), max(xs), min(ys), max(ys)
+    ext = max(xhi - xlo, yhi - ylo) + 2 * margin * h
+    n = int(math.ceil(ext / h))
+    hh = ext / n
+    cx, cy = 0.5 * (xlo + xhi), 0.5 * (ylo + yhi)
+    gx, gy = gauge_center if gauge_center is not None else (cx, cy)
+    return base_params(nx=n, ny=n, h=hh, x0=cx - ext / 2, y0=cy - ext / 2, shape_kind=2,
+                       parts=[dict(q) for q in parts], gauge_cx=gx, gauge_cy=gy, **kw)
+
+
+def annulus(r_out, r_in, n, center=(0.0, 0.0), margin=0.0, **kw):
+    """Disc of radius r_out with a concentric hole of radius r_in (the annulus
+    of Sec. 5.1) on an n x n grid over its bounding box (+ margin)."""
+    cx, cy = center
+    ext = 2 * r_out + 2 * margin
+    return base_params(nx=n, ny=n, h=ext / n, x0=cx - ext / 2, y0=cy - ext / 2, shape_kind=2,
+                       parts=[disc_part(center, r_out), disc_part(center, r_in, add=False)],
+                       gauge_cx=cx, gauge_cy=cy, **kw)
+
+
 def grid_xy(p):
     x = p["x0"] + (np.arange(p["nx"]) + 0.5) * p["h"]
     y = p["y0"] + (np.arange(p["ny"]) + 0.5) * p["h"]
