@@ -62,6 +62,34 @@ typedef enum { SC_STEP_CLOSED = 0, SC_STEP_MIDPOINT = 1 } sc_stepper;
    out with larger weights, so far fewer energies reach a given cutoff. */
 typedef enum { SC_SUM_MATSUBARA = 0, SC_SUM_OZAKI = 1 } sc_energy_sum;
 
+/* External vector potential (App. B, "gauge"), about the gauge origin
+   (gauge_cx, gauge_cy):
+     SC_GAUGE_SYMMETRIC  A = B/2 (-(y - yg), x - xg)               (Sec. 5.1.2)
+     SC_GAUGE_LANDAU     A = B (-(y - yg), 0)
+     SC_GAUGE_SOLENOID   A = alpha / (2 r) phi^ = alpha/(2 r^2) (-(y - yg), x - xg)
+                         (Eq. solenoid_gauge: the flux alpha Phi0 threads a line
+                         at the origin, which must lie outside the grain, e.g. in
+                         the hole of an annulus)
+   with B = pi alpha / area (units B0 = Phi0/(pi xi0^2), area of the grain), alpha =
+   flux_quanta, A in units A0 = Phi0/(pi xi0). */
+typedef enum { SC_GAUGE_SYMMETRIC = 0, SC_GAUGE_LANDAU = 1, SC_GAUGE_SOLENOID = 2 } sc_gauge;
+
+/* Shape kinds: a disc, a convex polygon, or a composite of parts. */
+typedef enum { SC_SHAPE_DISC = 0, SC_SHAPE_POLYGON = 1, SC_SHAPE_COMPOSITE = 2 } sc_shape;
+
+/* One part of a composite grain (Sec. 4 and App. B, composite geometries):
+   a disc or a convex polygon whose area is added to, or removed from, the
+   grain made of the parts before it, in the listed order.  A grain with a
+   hole is a disc or polygon followed by a removed part; regular polygons are
+   given by their vertices. */
+typedef struct {
+    int32_t kind;            /* 0 = disc, 1 = convex polygon (counter-clockwise) */
+    int32_t add;             /* 1 = add the area, 0 = remove it */
+    double cx, cy, r;        /* disc centre and radius (xi0) */
+    int32_t n_vert;          /* polygon vertex count (>= 3) */
+    const double *vx, *vy;   /* polygon vertices (copied by sc_create) */
+} sc_part;
+
 /*
  * Problem statement of one grain (configuration appendix of the paper:
  * physics, geometry, numerics).  Call sc_params_default() first.
@@ -69,15 +97,17 @@ typedef enum { SC_SUM_MATSUBARA = 0, SC_SUM_OZAKI = 1 } sc_energy_sum;
 typedef struct {
     int32_t nx, ny;          /* grid points */
     double h, x0, y0;        /* spacing and lower-left corner of the grid box (xi0) */
-    int32_t shape_kind;      /* 0 = disc, 1 = convex polygon (counter-clockwise) */
+    int32_t shape_kind;      /* sc_shape: 0 = disc, 1 = convex polygon (counter-clockwise),
+                                2 = composite (n_parts, parts below) */
     double disc_cx, disc_cy, disc_r;
     int32_t n_vert;          /* polygon vertex count (>= 3) */
     const double *vx, *vy;   /* polygon vertices (copied by sc_create) */
     int32_t pairing;         /* sc_pairing (Table basis_functions) */
     double crystal_rotation; /* crystal a-axis rotation, units of 2 pi */
     double t;                /* temperature T/Tc, 0 < t <= 1 */
-    double flux_quanta;      /* alpha = B_ext * area / Phi0, symmetric gauge */
-    double gauge_cx, gauge_cy; /* symmetric-gauge origin */
+    double flux_quanta;      /* alpha: symmetric and landau gauges, B_ext * area / Phi0;
+                                solenoid gauge, the flux through the hole / Phi0 */
+    double gauge_cx, gauge_cy; /* gauge origin */
     double kappa;            /* penetration depth lambda0/xi0; <= 0 or inf: no induced A */
     int32_t charge_sign;     /* sign of the carrier charge, +1 or -1 */
     int32_t n_angles;        /* Fermi-surface angles, even */
@@ -106,6 +136,10 @@ typedef struct {
                                 uses `pairing`) */
     double tc_ratios[4];     /* T_c^Gamma / T_c per component (Eq. gapeq_regularized);
                                 0 means 1 */
+    int32_t n_parts;         /* composite grain: parts applied in order (copied by
+                                sc_create); every added part must lie inside the grid box */
+    const sc_part *parts;
+    int32_t gauge;           /* sc_gauge of the external vector potential */
 } sc_params;
 
 typedef struct {
@@ -313,16 +347,22 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
 sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *stream);
 sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info);
 
-/* ---- inspection (tests and tools) ------------------------------------- */
+/* ---- inspection (tests and tools) -------------------------------------
+ * A "line" is one chord: a maximal piece of a lattice line inside the grain,
+ * ordered by pair, lattice line l, then s.  Convex grains have one chord per
+ * lattice line; composite grains can have several or none. */
 /* per pair l_lo, l_hi (n_pairs each); per line smin, smax, m0, m1 (n_lines) */
 sc_status sc_debug_lines(const sc_ctx *ctx, int32_t *l_lo, int32_t *l_hi, double *smin,
                          double *smax, int32_t *m0, int32_t *m1);
+/* per line: its pair and lattice line index l (n_lines each; either may be NULL) */
+sc_status sc_debug_chords(const sc_ctx *ctx, int32_t *pair, int32_t *l);
 /* padded (nx+2)*(ny+2) nearest-grain-point map, -1 where unused */
 sc_status sc_debug_ghost(const sc_ctx *ctx, int32_t *ghost);
 /* entry links of gamma for every angle k and line (k-major, lines of pair k mod
-   n_pairs): 4 taps of (angle, absolute line index, weight) */
+   n_pairs): 4 taps of (angle, lattice line l of the tapped line, the tapped
+   line's index within its pair, weight); any pointer may be NULL */
 sc_status sc_debug_links(const sc_ctx *ctx, int32_t *tap_angle, int32_t *tap_line,
-                         double *tap_w);
+                         int32_t *tap_chord, double *tap_w);
 /* boundary exit values after the last sweep: complex [angle][line][energy] */
 sc_status sc_debug_exits(sc_ctx *ctx, double *exits);
 /* per-sample energy sums of the last sweep: [pair][sample][4] = (Re Sf, Im Sf,

@@ -135,7 +135,7 @@ __global__ void adjoint_rotate_back_kernel(const PairDev *__restrict__ pairs, in
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
             const int l = min(max(iu + bb, pp.l_lo), pp.l_hi);
-            const BackLine Ln = bl[pp.line0 + (l - pp.l_lo)];
+            const BackLine Ln = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
             const double wl = bb ? wu : 1.0 - wu;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -173,7 +173,7 @@ __global__ void adjoint_ldos_back_kernel(const PairDev *__restrict__ pairs, int3
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
             const int l = min(max(iu + bb, pp.l_lo), pp.l_hi);
-            const BackLine Ln = bl[pp.line0 + (l - pp.l_lo)];
+            const BackLine Ln = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
             const double wlin = bb ? wu : 1.0 - wu;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {

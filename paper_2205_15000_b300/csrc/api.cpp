@@ -159,7 +159,7 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     // groups of G neighbouring lines of one pair (similar lengths)
     std::vector<int32_t> flat;
     for (const auto &pp : ctx->geo.pairs) {
-        const int n = pp.l_hi - pp.l_lo + 1;
+        const int n = pp.n_lines;
         for (int i = 0; i < n; i += G) {
             int c = 0;
             for (int k = 0; k < G; ++k) {
@@ -429,6 +429,8 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     for (int c = 0; c < 4; ++c) ctx->norms.D[c] = ctx->normD - std::log(G.tc_ratio[c]);
     gd.gx = p->gauge_cx;
     gd.gy = p->gauge_cy;
+    gd.gauge = p->gauge;
+    gd.flux = p->flux_quanta;
     gd.charge_sign = p->charge_sign;
 
     // host tables
@@ -436,7 +438,6 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     const size_t nL = G.lines.size();
     std::vector<scd::LineGeo> lgeo(nL);
     std::vector<scd::LineDev> ldev(nL);
-    std::vector<scd::BackLine> lback(nL);
     std::vector<int32_t> slot_line(G.n_slots);
     for (size_t L = 0; L < nL; ++L) {
         const scg::LineInfo &li = G.lines[L];
@@ -466,9 +467,31 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             ld.tap_b[q] = li.bwd[q].slot;
             ld.w_b[q] = li.bwd[q].w;
         }
-        const scg::LineInfo &nn = G.lines[li.nearest];
-        lback[L] = scd::BackLine{li.nearest, nn.m0, nn.ns, nn.slot0};
     }
+    // rotate-back table: per lattice line, the sampled chords of the nearest
+    // lattice line that has some; one chord inline, several in a list after
+    // the per-line records
+    std::vector<scd::BackLine> lback(G.lats.size());
+    for (int q = 0; q < G.n_pairs; ++q) {
+        const scg::PairInfo &pp = G.pairs[q];
+        for (int l = pp.l_lo; l <= pp.l_hi; ++l) {
+            const scg::LatticeLine &src = G.lat(q, G.lat(q, l).sampled);
+            std::vector<int> cand;
+            for (int c = src.c0; c < src.c0 + src.nc; ++c)
+                if (G.lines[c].ns > 0) cand.push_back(c);
+            const scg::LineInfo &c0 = G.lines[cand[0]];
+            scd::BackLine &b = lback[pp.lat0 + (l - pp.l_lo)];
+            b = scd::BackLine{-1, c0.m0, c0.ns, c0.slot0};
+            if (cand.size() > 1) {
+                b.more = (int32_t)lback.size();
+                for (int c : cand) {
+                    const scg::LineInfo &lc = G.lines[c];
+                    lback.push_back(scd::BackLine{(int32_t)cand.size(), lc.m0, lc.ns, lc.slot0});
+                }
+            }
+        }
+    }
+    const size_t nBack = lback.size();
     std::vector<scd::PairDev> pdev(P);
     const double cx = 0.5 + (p->x0 - G.ox) / p->h, cy = 0.5 + (p->y0 - G.oy) / p->h;
     for (int q = 0; q < P; ++q) {
@@ -484,7 +507,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         d.wb = G.weight[q + P];
         d.l_lo = pp.l_lo;
         d.l_hi = pp.l_hi;
-        d.line0 = pp.line0;
+        d.lat0 = pp.lat0;
         d.pad = 0;
     }
 
@@ -502,9 +525,12 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             const double sh = li.ns > 0 ? (double)li.m0 : 0.5 * (li.smin + li.smax) / p->h;  // along, units of h
             lf[L].gx0 = to_fix(cxo + li.l * (-pp.ey) + sh * pp.ex);
             lf[L].gy0 = to_fix(cyo + li.l * pp.ex + sh * pp.ey);
-            // v.A_ext is constant on a line: B/2 (e_y (Ox - gx) - e_x (Oy - gy) - l h)
-            lf[L].aext = (float)(p->charge_sign * half_b *
-                                 (pp.ey * (G.ox - p->gauge_cx) - pp.ex * (G.oy - p->gauge_cy) - li.l * p->h));
+            // symmetric gauge: v.A_ext is constant on a line, B/2 (e_y (Ox - gx) - e_x (Oy - gy) - l h);
+            // the other gauges are evaluated at every sample
+            lf[L].aext = p->gauge != SC_GAUGE_SYMMETRIC
+                             ? 0.0f
+                             : (float)(p->charge_sign * half_b *
+                                       (pp.ey * (G.ox - p->gauge_cx) - pp.ex * (G.oy - p->gauge_cy) - li.l * p->h));
             lf[L].pair = li.pair;
             lf[L].ns = li.ns;
             lf[L].slot0 = li.slot0;
@@ -537,9 +563,12 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             d.ey_f = (float)pp.ey;
             d.l_lo = pp.l_lo;
             d.l_hi = pp.l_hi;
-            d.line0 = pp.line0;
+            d.lat0 = pp.lat0;
             d.pad = 0;
         }
+        // gauge origin in the same fixed-point grid coordinates
+        gd.gfx = to_fix((p->gauge_cx - p->x0) / p->h - 0.5);
+        gd.gfy = to_fix((p->gauge_cy - p->y0) / p->h - 0.5);
     }
 
     // device memory
@@ -570,8 +599,8 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     CP(ctx->d_geo, lgeo.data(), nL * sizeof(scd::LineGeo));
     CA(ctx->d_lines, nL * sizeof(scd::LineDev));
     CP(ctx->d_lines, ldev.data(), nL * sizeof(scd::LineDev));
-    CA(ctx->d_back, nL * sizeof(scd::BackLine));
-    CP(ctx->d_back, lback.data(), nL * sizeof(scd::BackLine));
+    CA(ctx->d_back, nBack * sizeof(scd::BackLine));
+    CP(ctx->d_back, lback.data(), nBack * sizeof(scd::BackLine));
     CA(ctx->d_slot_line, slot_line.size() * sizeof(int32_t));
     CP(ctx->d_slot_line, slot_line.data(), slot_line.size() * sizeof(int32_t));
     CA(ctx->d_pairs, P * sizeof(scd::PairDev));
@@ -1181,21 +1210,32 @@ sc_status sc_debug_ghost(const sc_ctx *ctx, int32_t *ghost) {
     return SC_OK;
 }
 
-sc_status sc_debug_links(const sc_ctx *ctx, int32_t *ta, int32_t *tl, double *tw) {
+sc_status sc_debug_links(const sc_ctx *ctx, int32_t *ta, int32_t *tl, int32_t *tc, double *tw) {
     if (!ctx) return SC_EINVAL;
     const scg::Geometry &G = ctx->geo;
     size_t o = 0;
     for (int k = 0; k < G.n_angles; ++k) {
         const scg::PairInfo &pp = G.pairs[k % G.n_pairs];
-        for (int l = pp.l_lo; l <= pp.l_hi; ++l) {
-            const scg::LineInfo &li = G.lines[pp.line0 + l - pp.l_lo];
+        for (int L = pp.line0; L < pp.line0 + pp.n_lines; ++L) {
+            const scg::LineInfo &li = G.lines[L];
             for (int q = 0; q < 4; ++q, ++o) {
                 const bool f = k < G.n_pairs;
                 if (ta) ta[o] = f ? li.dbg_fwd_angle[q] : li.dbg_bwd_angle[q];
                 if (tl) tl[o] = f ? li.dbg_fwd_line[q] : li.dbg_bwd_line[q];
+                if (tc) tc[o] = f ? li.dbg_fwd_chord[q] : li.dbg_bwd_chord[q];
                 if (tw) tw[o] = f ? li.fwd[q].w : li.bwd[q].w;
             }
         }
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_chords(const sc_ctx *ctx, int32_t *pair, int32_t *l) {
+    if (!ctx) return SC_EINVAL;
+    const scg::Geometry &G = ctx->geo;
+    for (size_t L = 0; L < G.lines.size(); ++L) {
+        if (pair) pair[L] = G.lines[L].pair;
+        if (l) l[L] = G.lines[L].l;
     }
     return SC_OK;
 }
@@ -1213,8 +1253,7 @@ sc_status sc_debug_exits(sc_ctx *ctx, double *exits) {
     size_t o = 0;
     for (int k = 0; k < G.n_angles; ++k) {
         const scg::PairInfo &pp = G.pairs[k % G.n_pairs];
-        for (int l = pp.l_lo; l <= pp.l_hi; ++l) {
-            const size_t L = pp.line0 + l - pp.l_lo;
+        for (size_t L = pp.line0; L < (size_t)(pp.line0 + pp.n_lines); ++L) {
             const size_t slot = k < G.n_pairs ? L : nL + L;
             for (int n2 = 0; n2 < ctx->n_e; ++n2, ++o) {
                 const size_t i = slot * ctx->n_e + n2;

@@ -77,9 +77,20 @@ __global__ void rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__
         di += pp.eta_c[c] * ei;
     }
     if (aind) ok = bilinear(grid, ghost, aind, x, y, ax, ay) && ok;
-    // external vector potential, symmetric gauge: A = B/2 (-(y - yg), x - xg)
-    ax += -0.5 * grid.bfield * (y - grid.gy);
-    ay += 0.5 * grid.bfield * (x - grid.gx);
+    // external vector potential of the gauge about (xg, yg): symmetric
+    // B/2 (-(y - yg), x - xg), landau B (-(y - yg), 0), solenoid
+    // alpha/(2 r^2) (-(y - yg), x - xg) (Eq. solenoid_gauge)
+    const double dxg = x - grid.gx, dyg = y - grid.gy;
+    if (grid.gauge == 2) {
+        const double c = 0.5 * grid.flux / (dxg * dxg + dyg * dyg);
+        ax += -c * dyg;
+        ay += c * dxg;
+    } else if (grid.gauge == 1) {
+        ax += -grid.bfield * dyg;
+    } else {
+        ax += -0.5 * grid.bfield * dyg;
+        ay += 0.5 * grid.bfield * dxg;
+    }
     const double a = grid.charge_sign * (pp.ex * ax + pp.ey * ay);
     typename Vec4<T>::type o;
     o.x = (T)dr;
@@ -144,7 +155,7 @@ __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
-                const BackLine L = bl[pp.line0 + (l - pp.l_lo)];
+                const BackLine L = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
                 const double wl = b ? wu : 1.0 - wu;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
@@ -231,7 +242,7 @@ __global__ void ldos_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pa
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
-                const BackLine L = bl[pp.line0 + (l - pp.l_lo)];
+                const BackLine L = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
                 const double wl = b ? wu : 1.0 - wu;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {

@@ -31,20 +31,57 @@ struct PairDev {
     double u0, v0;       // lattice coordinates (line, sample) of grid point (0, 0), units of h
     double eta;          // basis function of the pair (component 0)
     double wa, wb;       // quadrature weights of angle p and of angle p + P
-    int32_t l_lo, l_hi, line0, pad;
+    int32_t l_lo, l_hi, lat0, pad;  // lattice lines l_lo..l_hi; their BackLine records from lat0
     double eta_c[4];     // basis function of each order-parameter component
 };
 
-// Per line, for the rotate-back kernel: nearest line with samples, its m0, ns, slot0.
+// Per lattice line, for the rotate-back kernels: the sampled chord (m0, ns,
+// slot0) of the nearest lattice line that has one.  When that line has several
+// sampled chords (composite grains), `more` indexes a list of them further on
+// in the same table (each entry's `more` holding the list length), and the
+// chord nearest to the grid point along the line is taken; else more = -1.
 struct BackLine {
-    int32_t nearest, m0, ns, slot0;
+    int32_t more, m0, ns, slot0;
 };
+
+// Distance, along the line, from lattice coordinate iv + fv (units of h,
+// 0 <= fv < 1) to the samples m0 .. m0 + ns - 1 of a chord.
+template <typename F>
+__device__ __forceinline__ F chord_distance(const BackLine &c, int iv, F fv) {
+    const int m1 = c.m0 + c.ns - 1;
+    if (iv < c.m0) return (F)(c.m0 - iv) - fv;
+    if (iv > m1 || (iv == m1 && fv > F(0))) return (F)(iv - m1) + fv;
+    return F(0);
+}
+
+// The chord a rotate-back tap takes on lattice-line record L: the only one,
+// or the listed chord nearest to the point (ties to the chord of lower s).
+template <typename F>
+__device__ __forceinline__ BackLine back_chord(const BackLine *__restrict__ bl, BackLine L, int iv, F fv) {
+    if (L.more < 0) return L;
+    const int first = L.more;
+    BackLine best = bl[first];
+    F bd = chord_distance(best, iv, fv);
+    const int n = best.more;
+    for (int k = 1; k < n; ++k) {
+        const BackLine c = bl[first + k];
+        const F d = chord_distance(c, iv, fv);
+        if (d < bd) {
+            bd = d;
+            best = c;
+        }
+    }
+    return best;
+}
 
 struct GridDev {
     int32_t nx, ny;
     double h, x0, y0, ox, oy;
-    double bfield;       // external field, units of B0
+    double bfield;       // external field, units of B0 (symmetric and landau gauges)
     double gx, gy;       // gauge origin
+    double flux;         // flux quanta alpha (solenoid gauge)
+    int64_t gfx, gfy;    // gauge origin in fixed-point grid coordinates (FP32 path)
+    int32_t gauge;       // sc_gauge
     int32_t charge_sign;
     int32_t n_comp;      // order-parameter components; Delta is [n_comp][ny][nx] complex
 };
@@ -55,7 +92,7 @@ constexpr int kFixBits = 40;
 
 struct LineF32 {
     int64_t gx0, gy0;    // grid coordinates (x - x0)/h - 1/2 of the first slot's point
-    float aext;          // sigma v.A_ext: constant along a line in the symmetric gauge
+    float aext;          // sigma v.A_ext in the symmetric gauge (constant along a line); 0 otherwise
     int32_t pair, ns, slot0;
 };
 
@@ -66,7 +103,7 @@ struct PairF32 {
     float w_eta, w_ex, w_ey, w_sum; // (w_p + w_{p+P}) times eta, e_x, e_y, 1
     float wa, wb;                   // w_p, w_{p+P}
     float ex_f, ey_f;               // e_par in FP32
-    int32_t l_lo, l_hi, line0, pad;
+    int32_t l_lo, l_hi, lat0, pad;  // lattice lines l_lo..l_hi; their BackLine records from lat0
     float eta_c[4], w_eta_c[4];     // per order-parameter component: eta, (w_p + w_{p+P}) eta
 };
 

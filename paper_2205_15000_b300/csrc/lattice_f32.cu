@@ -50,7 +50,10 @@ cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, con
 }
 
 // one thread per image slot: bilinear Delta and A_ind at the sample, nearest
-// grain point for stencil points outside the grain
+// grain point for stencil points outside the grain; GAUGE (sc_gauge) selects
+// how A_ext enters: the symmetric gauge's per-line constant, or the landau /
+// solenoid potential at the sample
+template <int GAUGE>
 __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32_t *__restrict__ slot_line,
                                   int64_t n_slots, const PairF32 *__restrict__ pairs, GridDev grid,
                                   const int32_t *__restrict__ ghost, const float2 *__restrict__ df,
@@ -91,7 +94,25 @@ __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32
             o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
             o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
         }
-        o.z = ln.aext + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
+        float az = ln.aext;
+        if (GAUGE != 0) {
+            // landau and solenoid gauges: A_ext at the sample, from its exact
+            // fixed-point offset to the gauge origin
+            const float sc = (float)(grid.h / (double)(1ll << kFixBits));  // fixed-point unit times h
+            const float xr = (float)(ln.gx0 + (int64_t)q * pp.dx - grid.gfx) * sc;
+            const float yr = (float)(ln.gy0 + (int64_t)q * pp.dy - grid.gfy) * sc;
+            float axe, aye;
+            if (GAUGE == 2) {
+                const float c = 0.5f * (float)grid.flux / (xr * xr + yr * yr);
+                axe = -c * yr;
+                aye = c * xr;
+            } else {
+                axe = -(float)grid.bfield * yr;
+                aye = 0.f;
+            }
+            az += (float)grid.charge_sign * (pp.ex_f * axe + pp.ey_f * aye);
+        }
+        o.z = az + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
         const bool ok = (g00 >= 0 || w00 == 0.f) && (g10 >= 0 || w10 == 0.f) && (g01 >= 0 || w01 == 0.f) &&
                         (g11 >= 0 || w11 == 0.f);
         o.w = ok ? 0.f : 1.f;
@@ -104,9 +125,13 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
                               const float2 *delta_f, const float2 *aind_f, float4 *image_in,
                               cudaStream_t st) {
     const int bs = 256;
-    rotate_f32_kernel<<<(unsigned)((n_slots + bs - 1) / bs), bs, 0, st>>>(lines, slot_line, n_slots, pairs,
-                                                                          grid, ghost, delta_f, aind_f,
-                                                                          image_in);
+    const unsigned nb = (unsigned)((n_slots + bs - 1) / bs);
+    if (grid.gauge == 2)
+        rotate_f32_kernel<2><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
+    else if (grid.gauge == 1)
+        rotate_f32_kernel<1><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
+    else
+        rotate_f32_kernel<0><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
     return cudaGetLastError();
 }
 
@@ -135,8 +160,8 @@ __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_
                 split_fixed(i * pp.ui + j * pp.uj + pp.u0, iu, wu);
                 split_fixed(i * pp.vi + j * pp.vj + pp.v0, iv, wv);
                 const int la = min(max(iu, pp.l_lo), pp.l_hi), lb = min(max(iu + 1, pp.l_lo), pp.l_hi);
-                const BackLine La = bl[pp.line0 + (la - pp.l_lo)];
-                const BackLine Lb = bl[pp.line0 + (lb - pp.l_lo)];
+                const BackLine La = back_chord(bl, bl[pp.lat0 + (la - pp.l_lo)], iv, wv);
+                const BackLine Lb = back_chord(bl, bl[pp.lat0 + (lb - pp.l_lo)], iv, wv);
                 const int ma0 = min(max(iv, La.m0), La.m0 + La.ns - 1);
                 const int ma1 = min(max(iv + 1, La.m0), La.m0 + La.ns - 1);
                 const int mb0 = min(max(iv, Lb.m0), Lb.m0 + Lb.ns - 1);

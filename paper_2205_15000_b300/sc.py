@@ -32,6 +32,15 @@ class ScError(RuntimeError):
         self.status = status
 
 
+class sc_part(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("add", ctypes.c_int32),
+        ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double),
+        ("n_vert", ctypes.c_int32),
+        ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
 class sc_params(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
@@ -50,7 +59,13 @@ class sc_params(ctypes.Structure):
         ("host_only", ctypes.c_int32), ("record_timings", ctypes.c_int32),
         ("stepper", ctypes.c_int32), ("energy_sum", ctypes.c_int32),
         ("n_components", ctypes.c_int32), ("pairings", ctypes.c_int32 * 4), ("tc_ratios", ctypes.c_double * 4),
+        ("n_parts", ctypes.c_int32), ("parts", ctypes.POINTER(sc_part)),
+        ("gauge", ctypes.c_int32),
     ]
+
+
+GAUGES = {"symmetric": 0, "landau": 1, "solenoid": 2}
+PART_KINDS = {"disc": 0, "polygon": 1}
 
 
 class sc_batch_info(ctypes.Structure):
@@ -92,7 +107,7 @@ ACCELERATORS = {"picard": SC_ACC_PICARD, "polyak": SC_ACC_POLYAK,
 EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_get_mask",
             "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
-            "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links",
+            "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
             "sc_accel_get_state", "sc_ozaki_poles", "sc_energy_grid",
@@ -125,7 +140,8 @@ def _load():
         "sc_ldos": [vp, vp, i32, f64, i32, vp, ctypes.c_int, vp],
         "sc_debug_lines": [vp, vp, vp, vp, vp, vp, vp],
         "sc_debug_ghost": [vp, vp],
-        "sc_debug_links": [vp, vp, vp, vp],
+        "sc_debug_links": [vp, vp, vp, vp, vp],
+        "sc_debug_chords": [vp, vp, vp],
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
@@ -224,6 +240,25 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
         for c, (pairing, tcr) in enumerate(comps):
             p.pairings[c] = int(pairing)
             p.tc_ratios[c] = float(tcr)
+    p.gauge = GAUGES[d.get("gauge", "symmetric")]
+    parts = d.get("parts") or []
+    arr = (sc_part * max(1, len(parts)))()
+    keep = [arr]
+    for k, q in enumerate(parts):  # composite grain (Sec. 4): discs and convex polygons in order
+        arr[k].kind = PART_KINDS[q["kind"]]
+        arr[k].add = 1 if q.get("add", True) else 0
+        if q["kind"] == "disc":
+            arr[k].cx, arr[k].cy, arr[k].r = float(q["cx"]), float(q["cy"]), float(q["r"])
+        else:
+            ax = np.ascontiguousarray(q["vx"], np.float64)
+            ay = np.ascontiguousarray(q["vy"], np.float64)
+            keep += [ax, ay]
+            arr[k].n_vert = len(ax)
+            arr[k].vx = ax.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            arr[k].vy = ay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.n_parts = len(parts)
+    p.parts = ctypes.cast(arr, ctypes.POINTER(sc_part))
+    p._keep = (vx, vy, keep)
     return p
 
 
@@ -482,7 +517,9 @@ class Context:
         m0, m1 = np.zeros(L, np.int32), np.zeros(L, np.int32)
         _check(lib.sc_debug_lines(self.h, _ptr(lo), _ptr(hi), _ptr(smin), _ptr(smax), _ptr(m0),
                                   _ptr(m1)), self.h)
-        return dict(l_lo=lo, l_hi=hi, smin=smin, smax=smax, m0=m0, m1=m1)
+        pair, l = np.zeros(L, np.int32), np.zeros(L, np.int32)
+        _check(lib.sc_debug_chords(self.h, _ptr(pair), _ptr(l)), self.h)
+        return dict(l_lo=lo, l_hi=hi, smin=smin, smax=smax, m0=m0, m1=m1, pair=pair, l=l)
 
     def ghost(self):
         g = np.zeros((self.ny + 2, self.nx + 2), np.int32)
@@ -491,9 +528,10 @@ class Context:
 
     def links(self):
         n = 4 * 2 * self.info.n_lines
-        ta, tl, tw = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
-        _check(lib.sc_debug_links(self.h, _ptr(ta), _ptr(tl), _ptr(tw)), self.h)
-        return dict(angle=ta.reshape(-1, 4), line=tl.reshape(-1, 4), w=tw.reshape(-1, 4))
+        ta, tl, tc, tw = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n)
+        _check(lib.sc_debug_links(self.h, _ptr(ta), _ptr(tl), _ptr(tc), _ptr(tw)), self.h)
+        return dict(angle=ta.reshape(-1, 4), line=tl.reshape(-1, 4), chord=tc.reshape(-1, 4),
+                    w=tw.reshape(-1, 4))
 
     # -- compute (device) -------------------------------------------------
     def set_fields(self, delta, aind=None, stream=None):

@@ -106,6 +106,23 @@ def test_clockwise_polygon_rejected():
         sc.Context(p, host_only=True)
 
 
+def test_gauges_validated():
+    """The solenoid gauge needs its flux line outside the grain (Eq.
+    solenoid_gauge holds on the annulus R< <= r <= R>); unknown gauges and
+    empty composites are refused."""
+    with pytest.raises(sc.ScError):
+        sc.Context(W.disc(4.0, 32, n_angles=8, n_energies=2, gauge="solenoid", flux_quanta=0.5), host_only=True)
+    sc.Context(W.annulus(4.0, 1.5, 32, n_angles=8, n_energies=2, gauge="solenoid", flux_quanta=0.5), host_only=True)
+    p = sc.make_params(W.disc(4.0, 32, n_angles=8, n_energies=2), host_only=True)
+    p.gauge = 3
+    with pytest.raises(sc.ScError):
+        sc.sc_create(p)
+    p = sc.make_params(W.annulus(4.0, 1.5, 32, n_angles=8, n_energies=2), host_only=True)
+    p.n_parts = 0
+    with pytest.raises(sc.ScError):
+        sc.sc_create(p)
+
+
 def test_compute_on_host_only_context_is_state_error():
     c = sc.Context(W.disc(5.0, 32, n_angles=8, n_energies=2), host_only=True)
     with pytest.raises(sc.ScError) as ei:
@@ -121,6 +138,20 @@ GEOMS = {
     "polygon": lambda: W.polygon([0.0, 7.0, 9.0, 2.0], [0.0, -1.0, 6.0, 8.0], 0.3, n_angles=12, n_energies=3),
     "triangle": lambda: W.polygon([0.0, 5.0, 1.0], [0.0, 1.0, 4.0], 0.2, n_angles=18, n_energies=2),
     "rotated": lambda: W.square(9.0, 50, rotation=0.3, n_angles=10, n_energies=2, crystal_rotation=0.1),
+    # composite grains (Sec. 4): holes, unions, a removed polygon crossing the edge
+    "annulus": lambda: W.annulus(6.0, 2.5, 48, margin=0.3, n_angles=24, n_energies=2),
+    "square_hole": lambda: W.composite([W.disc_part((0, 0), 7.5), W.polygon_part(*W.regular_polygon((4.0, 0.5), 4, 3.0),
+                                                                                 add=False)], 0.3, n_angles=16, n_energies=2),
+    "two_discs": lambda: W.composite([W.disc_part((0, 0), 4.0), W.disc_part((5.0, 1.0), 3.0)], 0.25, n_angles=20,
+                                     n_energies=2),
+    "l_shape": lambda: W.composite([W.polygon_part([0, 6, 6, 0], [0, 0, 2, 2]), W.polygon_part([0, 2, 2, 0], [2, 2, 7, 7])],
+                                   0.2, n_angles=16, n_energies=2),
+    "bite": lambda: W.composite([W.polygon_part([0, 8, 8, 0], [0, 0, 8, 8]), W.disc_part((8.0, 4.0), 2.5, add=False),
+                                 W.polygon_part(*W.regular_polygon((2.0, 6.0), 3, 2.5, rotation=0.05), add=False)],
+                                0.25, n_angles=12, n_energies=2),
+    "squid": lambda: W.composite([W.polygon_part([0, 100, 100, 0], [-5, -5, 5, 5]),
+                                  W.polygon_part(*W.regular_polygon((50.0, 0.0), 8, 15.0)),
+                                  W.disc_part((50.0, 0.0), 8.0, add=False)], 1.0, n_angles=8, n_energies=2),
 }
 
 
@@ -135,7 +166,7 @@ def test_geometry_matches_oracle(name):
     np.testing.assert_array_equal(c.mask(), g.mask())
     np.testing.assert_array_equal(c.ghost(), g.ghost())
     a, b = c.lines(), g.lines()
-    for k in ("l_lo", "l_hi", "m0", "m1"):
+    for k in ("l_lo", "l_hi", "m0", "m1", "pair", "l"):
         np.testing.assert_array_equal(a[k], b[k])
     np.testing.assert_allclose(a["smin"], b["smin"], atol=1e-12, rtol=0)
     np.testing.assert_allclose(a["smax"], b["smax"], atol=1e-12, rtol=0)
@@ -145,8 +176,8 @@ def test_geometry_matches_oracle(name):
     for A in range(la["w"].shape[0]):
         da, db = {}, {}
         for q in range(4):
-            ka = (la["angle"][A, q], la["line"][A, q])
-            kb = (lb["angle"][A, q], lb["line"][A, q])
+            ka = (la["angle"][A, q], la["line"][A, q], la["chord"][A, q])
+            kb = (lb["angle"][A, q], lb["line"][A, q], lb["chord"][A, q])
             da[ka] = da.get(ka, 0.0) + la["w"][A, q]
             db[kb] = db.get(kb, 0.0) + lb["w"][A, q]
         keys = set(da) | set(db)

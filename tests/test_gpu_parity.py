@@ -290,11 +290,7 @@ def test_c5_full_size_first_sweep_sampled_angles():
     img = ctx.images()
     L = g.lines()
     ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
-    per, off = [], 0
-    for q in range(P):
-        nl = int(L["l_hi"][q] - L["l_lo"][q] + 1)
-        per.append(int(ns[off:off + nl].sum()))
-        off += nl
+    per = [int(ns[L["pair"] == q].sum()) for q in range(P)]
     start = np.concatenate([[0], np.cumsum(per)])
     for k, r in zip(angles, ref):
         q = k % P
