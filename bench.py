@@ -192,6 +192,9 @@ def run_ours(args):
     elif args.workload == "c5":
         p, delta, aind = W.c5_square_d()
         workload = "c5_square_d_1024sq_256ang_160eps_20vortices"
+    elif args.workload == "annulus":
+        p, delta, aind = W.annulus_d()
+        workload = "annulus_dx2y2_R25_r10_256sq_128ang_80eps_solenoid"
     else:
         p, delta, aind = W.c2_diamond_d(n=args.grid, n_angles=args.angles)
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
@@ -317,8 +320,9 @@ def run_ours(args):
                    "steps_per_sweep": steps_per_step, "l2": "flushed between timed steps",
                    "parallelism": f"replicas{world}",
                    "step": "forward sweep + outputs" + (" + adjoint of F_total" if args.adjoint else ""),
-                   "grain": {k: p[k] for k in ("nx", "ny", "h", "t", "n_angles", "n_energies",
-                                               "flux_quanta", "pairing")}},
+                   "grain": dict({k: p[k] for k in ("nx", "ny", "h", "t", "n_angles", "n_energies",
+                                                    "flux_quanta", "pairing")},
+                                 gauge=p.get("gauge", "symmetric"), parts=len(p.get("parts") or []))},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "sweep_kernel", "ms_per_launch": sweep_ms,
@@ -332,7 +336,7 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": t_wall,
     }
-    if not args.no_cpu_baseline and args.workload == "c2":
+    if not args.no_cpu_baseline and args.workload in ("c2", "annulus"):
         keep = {}
         line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"], keep)
         line["errors_vs_fp64_oracle"] = _errors_vs_oracle(p, delta, args.precision, keep)
@@ -441,9 +445,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="grid side (reduced cases for profiling)")
     ap.add_argument("--angles", type=int, default=128, help="Fermi angles (reduced cases for profiling)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "annulus"],
                     help="c2: one 256^2 d-wave [110] grain; c3: 64 grains in one batched launch; "
-                         "c4: d-wave disc with a vortex (128^2); c5: 1024^2 d-wave square, 20 vortices")
+                         "c4: d-wave disc with a vortex (128^2); c5: 1024^2 d-wave square, 20 vortices; "
+                         "annulus: d-wave annulus R> 25, R< 10 (256^2), solenoid gauge")
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grains", type=int, default=64)

@@ -68,7 +68,8 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                 mir[e] = n_e - 1 - nn;
             } else {
                 zr0[e] = T(0);
-                zi[e] = gs.mats_eps ? (T)gs.mats_eps[nn] : (T)(gs.t * (nn + 0.5));
+                // Ozaki's poles (WGT) come with their energies; Matsubara energies are t (n + 1/2)
+                zi[e] = WGT ? (T)gs.mats_eps[nn] : (T)(gs.t * (nn + 0.5));
                 mir[e] = nn;
                 if constexpr (WGT) wv[e] = ev[e] ? (T)gs.mats_w[nn] : T(0);
             }
@@ -223,19 +224,17 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                         const T rD = Mth<T>::rcp(Dr * Dr + Di * Di);
                         const T ir = Dr * rD, ii = -Di * rD;      // 1/D
                         // ga/D + gb conj(1/D)
-                        const T fr = (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
-                        const T fi = (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
                         if constexpr (WGT) {
                             const T w = wv[e];
                             sg += w * ii;
-                            sfr += w * fr;
-                            sfi += w * fi;
+                            sfr += w * ((ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii));
+                            sfi += w * ((ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii));
                             sFr += w * (ga.x + gb.x);
                             sFi += w * (ga.y + gb.y);
                         } else {
                             sg += ii;
-                            sfr += fr;
-                            sfi += fi;
+                            sfr += (ga.x * ir - ga.y * ii) + (gb.x * ir + gb.y * ii);
+                            sfi += (ga.x * ii + ga.y * ir) + (gb.y * ir - gb.x * ii);
                             sFr += ga.x + gb.x;
                             sFi += ga.y + gb.y;
                         }

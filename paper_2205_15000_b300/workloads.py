@@ -14,6 +14,9 @@ Workloads (grain sizes in xi0, energies in 2 pi kB Tc):
   c4_disc_d     d-wave disc radius 25, 128x128, 64 angles, t=0.2, one vortex
   c5_square_d   d-wave square side 200, 1024x1024, 256 angles, t=0.05 (160
                 energies), 20 vortices, kappa=80
+  annulus_d     d_{x2-y2} annulus R> = 25, R< = 10 (Sec. 5.1), 256x256, 128
+                angles, t=0.1 (80 energies), solenoid gauge with half a flux
+                quantum through the hole, no screening
 """
 import math
 
@@ -228,6 +231,15 @@ def c5_square_d(n=1024, n_angles=256, seed=5, n_vortex=20):
             centers.append((float(c[0]), float(c[1])))
     d = vortex_delta(p, BULK_GUESS[("dx2y2", 0.05)], centers, [-1] * n_vortex)
     return p, d, None
+
+
+def annulus_d(n=256, n_angles=128, flux=0.5, seed=6):
+    """The annulus of Sec. 5.1 (outer radius 25, inner 10) with d_{x2-y2}
+    pairing at t = 0.1, in the solenoid gauge (Eq. solenoid_gauge)."""
+    t = 0.1
+    p = annulus(25.0, 10.0, n, pairing=1, t=t, n_angles=n_angles, n_energies=n_energies_for_cutoff(t),
+                gauge="solenoid", flux_quanta=flux, kappa=0.0)
+    return p, noisy_delta(p, BULK_GUESS[("dx2y2", 0.1)], 0.05, seed=seed), None
 
 
 def random_convex_polygon(rng, radius, n_vert):
