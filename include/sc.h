@@ -186,6 +186,12 @@ sc_status sc_get_mask(const sc_ctx *ctx, uint8_t *mask);
    Delta(p, R) = Delta(R) eta(p).  Values outside the grain are ignored. */
 sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, int on_device,
                         void *stream);
+/* Copy the context's current fields out: Delta ([n_components][ny][nx]
+   complex) and the induced vector potential A_ind ([ny][nx][2]; zero when none
+   was set or computed), e.g. after sc_picard_step or sc_accelerate.  Either
+   pointer may be NULL; on_device = 1: device pointers (ordered on `stream`),
+   0: host pointers (the call waits for the copies). */
+sc_status sc_get_fields(sc_ctx *ctx, double *delta, double *a_ind, int on_device, void *stream);
 /* Forget the boundary coherence functions: the next sweep starts every
    trajectory from the local homogeneous solution. */
 sc_status sc_reset_boundary(sc_ctx *ctx);

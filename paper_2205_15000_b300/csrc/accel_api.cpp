@@ -112,8 +112,7 @@ sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream) {
     if (magn) {
         ACK(alloc_once(ctx, &ctx->d_anew, 2 * n * sizeof(double)));
         ACK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, ctx->d_part, st));
-        ACK(scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in,
-                                         ctx->d_G, ctx->G_width, 1.0 / (kappa * kappa), ctx->d_anew, st));
+        ACK(sc_internal::induced_field(ctx, ctx->d_anew, st));
     }
     const int blocks = scd::accel_reduce_blocks(n, ctx->sm_count);
     ACK(alloc_once(ctx, &ctx->d_acc_v, scd::kAccelComps * n * sizeof(double)));

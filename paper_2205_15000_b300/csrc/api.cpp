@@ -216,6 +216,17 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     return SC_OK;
 }
 
+// A = -(1/kappa^2) G * (j - <j>) from d_j and d_jsum (App. D): FFT convolution
+// where the padded grid fits, else the direct sum
+cudaError_t induced_field(sc_ctx *ctx, double *aind, cudaStream_t st) {
+    const double k = ctx->geo.prm.kappa;
+    if (ctx->vp_fft)
+        return scd::vecpot_fft_apply(ctx->vp, ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in,
+                                     1.0 / (k * k), aind, st);
+    return scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in, ctx->d_G,
+                                        ctx->G_width, 1.0 / (k * k), aind, st);
+}
+
 sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st) {
     if (ctx->fp64) {
         CK(scd::launch_rotate(true, ctx->d_geo, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pairs, ctx->grid,
@@ -674,6 +685,35 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             }
         CA(ctx->d_G, Gt.size() * sizeof(double));
         CP(ctx->d_G, Gt.data(), Gt.size() * sizeof(double));
+        // zero-padded FFT convolution (App. D) where the padded grid fits one
+        // shared-memory transform per row; larger grids keep the direct sum
+        scd::VecpotFft &f = ctx->vp;
+        f.lx = scd::vecpot_fft_log2(G.nx);
+        f.ly = scd::vecpot_fft_log2(G.ny);
+        f.px = 1 << f.lx;
+        f.py = 1 << f.ly;
+        if (f.px <= scd::kVecpotMaxFft && f.py <= scd::kVecpotMaxFft) {
+            auto twiddles = [](int n) {
+                std::vector<double2> t(n / 2);
+                for (int k = 0; k < n / 2; ++k)
+                    t[k] = make_double2(std::cos(2.0 * M_PI * k / n), -std::sin(2.0 * M_PI * k / n));
+                return t;
+            };
+            const std::vector<double2> tx = twiddles(f.px), ty = twiddles(f.py);
+            const size_t nb = (size_t)f.px * f.py * sizeof(double2);
+            CA(f.tw_x, tx.size() * sizeof(double2));
+            CP(f.tw_x, tx.data(), tx.size() * sizeof(double2));
+            CA(f.tw_y, ty.size() * sizeof(double2));
+            CP(f.tw_y, ty.data(), ty.size() * sizeof(double2));
+            CA(f.buf, nb);
+            CA(f.tbuf, nb);
+            CA(f.ghat, nb);
+            cudaError_t err = scd::vecpot_fft_attributes();
+            if (err == cudaSuccess) err = scd::vecpot_fft_prepare(f, ctx->d_G, W, G.nx, G.ny, 0);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(0);
+            if (err != cudaSuccess) return fail_cuda(err, "vector-potential transform");
+            ctx->vp_fft = true;
+        }
     }
 #undef CA
 #undef CP
@@ -779,6 +819,15 @@ sc_status sc_set_fields(sc_ctx *ctx, const double *delta, const double *a_ind, i
     return SC_OK;
 }
 
+sc_status sc_get_fields(sc_ctx *ctx, double *delta, double *a_ind, int on_device, void *stream) {
+    CKS(check_ctx(ctx));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 2 * npts(ctx) * sizeof(double);
+    if (delta) CKS(copy_out(ctx, delta, ctx->d_delta, bytes * ctx->geo.n_comp, on_device, st));
+    if (a_ind) CKS(copy_out(ctx, a_ind, ctx->d_aind, bytes, on_device, st));
+    return SC_OK;
+}
+
 sc_status sc_reset_boundary(sc_ctx *ctx) {
     CKS(check_ctx(ctx));
     ctx->have_boundary = false;
@@ -868,9 +917,7 @@ sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     CKS(ensure_outputs_impl(ctx, st));
     CK(scd::launch_mean_current(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, ctx->d_part, st));
-    const double k = ctx->geo.prm.kappa;
-    CK(scd::launch_vector_potential(ctx->grid, ctx->d_mask, ctx->d_j, ctx->d_jsum, (double)ctx->geo.n_in, ctx->d_G,
-                                    ctx->G_width, 1.0 / (k * k), ctx->d_aind, st));
+    CK(sc_internal::induced_field(ctx, ctx->d_aind, st));
     ctx->have_aind = true;
     return SC_OK;
 }

@@ -8,6 +8,7 @@
 
 #include "geometry.hpp"
 #include "kernels.cuh"
+#include "vecpot.cuh"
 #include "sc.h"
 
 // How the sweep kernel maps (line, energy) work to lanes for one energy count.
@@ -51,6 +52,8 @@ struct sc_ctx {
            *d_F = nullptr, *d_sums = nullptr, *d_jsum = nullptr, *d_G = nullptr, *d_diff = nullptr;
     double *d_part = nullptr;  // per-block partial sums of the grid reductions
     int G_width = 0;
+    scd::VecpotFft vp{};        // FFT convolution buffers (grids up to 2048 points a side)
+    bool vp_fft = false;
     bool have_aind = false;
     void *d_img_in = nullptr, *d_img_out = nullptr;
     void *d_exit[2] = {nullptr, nullptr};
@@ -95,6 +98,7 @@ struct sc_ctx {
 };
 
 namespace sc_internal {
+cudaError_t induced_field(sc_ctx *ctx, double *aind, cudaStream_t st);
 sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg);
 cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes);
 void dfree(sc_ctx *ctx, void *p);

@@ -105,7 +105,7 @@ ACCELERATORS = {"picard": SC_ACC_PICARD, "polyak": SC_ACC_POLYAK,
 
 # every symbol include/sc.h declares
 EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_get_mask",
-            "sc_set_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
+            "sc_set_fields", "sc_get_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
@@ -129,6 +129,7 @@ def _load():
         "sc_get_info": [vp, P(sc_info)],
         "sc_get_mask": [vp, vp],
         "sc_set_fields": [vp, vp, vp, ctypes.c_int, vp],
+        "sc_get_fields": [vp, vp, vp, ctypes.c_int, vp],
         "sc_reset_boundary": [vp],
         "sc_riccati_sweep": [vp, vp],
         "sc_burnin": [vp, i32, f64, vp],
@@ -542,6 +543,15 @@ class Context:
             a = torch.as_tensor(aind, dtype=torch.float64, device="cuda").contiguous()
         self._fields = (d, a)  # keep alive until the copy ran
         sc_set_fields(self.h, d, a, True, stream)
+
+    def fields(self, stream=None):
+        """The context's current Delta (complex, (ny, nx) or (C, ny, nx)) and
+        A_ind ((ny, nx, 2)) as device tensors."""
+        import torch
+        d = torch.empty(self._dshape() + (2,), dtype=torch.float64, device="cuda")
+        a = torch.empty((self.prm["ny"], self.prm["nx"], 2), dtype=torch.float64, device="cuda")
+        _check(lib.sc_get_fields(self.h, _ptr(d), _ptr(a), 1, _stream(stream)), self.h)
+        return torch.view_as_complex(d), a
 
     def sweep(self, stream=None):
         sc_riccati_sweep(self.h, stream)
