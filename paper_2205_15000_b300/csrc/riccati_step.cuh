@@ -88,7 +88,11 @@ __host__ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi,
     const T y = T(-2) * zr * zi;         // Im Omega^2
     using ::fabs;
     using ::copysign;
-    const T r = M::sqrt(x * x + y * y);
+    // |Omega|^2 = |Omega^2|: one reciprocal square root gives both r and the
+    // 1/(2 Omega) factor below
+    const T n2 = x * x + y * y;
+    const T rn = M::rsqrt(n2);           // 1/|Omega|^2
+    const T r = n2 * rn;                 // |Omega^2|
     const T hs = T(0.5) * (r + fabs(x));
     const T q = M::rsqrt(hs);            // 1/s
     const T s = hs * q;                  // s = sqrt((r + |x|)/2)
@@ -102,11 +106,10 @@ __host__ __device__ __forceinline__ void step_coef(T dr, T di, T d2, T zr, T zi,
         Oi = copysign(s, y);
     }
     const T wr = zr - Oi, wi = zi + Or;  // w = z + i Omega
-    // 1/w and 1/(2 Omega) from two reciprocals of squared moduli (the sweep is
-    // bound by FP32 issue, not by the reciprocal unit)
+    // 1/w from the reciprocal of its squared modulus; 1/(2 Omega) = conj(Omega)/(2 |Omega|^2)
     const T rw = M::rcp(wr * wr + wi * wi);
     const T iwr = wr * rw, iwi = -wi * rw;                    // 1/w
-    const T ro = T(0.5) * M::rcp(Or * Or + Oi * Oi);
+    const T ro = T(0.5) * rn;
     const T i2r = Or * ro, i2i = -Oi * ro;                    // 1/(2 Omega)
     c.gh.x = -(dr * iwr - di * iwi);
     c.gh.y = -(dr * iwi + di * iwr);
@@ -173,7 +176,11 @@ __host__ __device__ __forceinline__ void step_grad(T dr, T di, T zr, T zi, T ell
     const T d2 = dr * dr + di * di;
     const T x = d2 - zr * zr + zi * zi;
     const T y = T(-2) * zr * zi;
-    const T r = M::sqrt(x * x + y * y);
+    // |Omega|^2 = |Omega^2|: one reciprocal square root gives both r and the
+    // 1/(2 Omega) factor below
+    const T n2 = x * x + y * y;
+    const T rn = M::rsqrt(n2);           // 1/|Omega|^2
+    const T r = n2 * rn;                 // |Omega^2|
     const T hs = T(0.5) * (r + fabs(x));
     const T q = M::rsqrt(hs);
     const T s = hs * q;
@@ -270,7 +277,11 @@ __host__ __device__ __forceinline__ void mob_coef(T dr, T di, T d2, T zr, T zi, 
     using ::fabs;
     const T x = d2 - zr * zr + zi * zi;  // Re Omega^2
     const T y = T(-2) * zr * zi;         // Im Omega^2
-    const T r = M::sqrt(x * x + y * y);
+    // |Omega|^2 = |Omega^2|: one reciprocal square root gives both r and the
+    // 1/(2 Omega) factor below
+    const T n2 = x * x + y * y;
+    const T rn = M::rsqrt(n2);           // 1/|Omega|^2
+    const T r = n2 * rn;                 // |Omega^2|
     const T hs = T(0.5) * (r + fabs(x));
     const T q = M::rsqrt(hs);
     const T s = hs * q;
@@ -379,7 +390,11 @@ __host__ __device__ __forceinline__ Cx<T> csqrt_principal(T x, T y) {
     typedef Mth<T> M;
     using ::copysign;
     using ::fabs;
-    const T r = M::sqrt(x * x + y * y);
+    // |Omega|^2 = |Omega^2|: one reciprocal square root gives both r and the
+    // 1/(2 Omega) factor below
+    const T n2 = x * x + y * y;
+    const T rn = M::rsqrt(n2);           // 1/|Omega|^2
+    const T r = n2 * rn;                 // |Omega^2|
     const T hs = T(0.5) * (r + fabs(x));
     const T q = M::rsqrt(hs);
     const T s = hs * q;
