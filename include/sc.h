@@ -111,7 +111,7 @@ typedef struct {
     double kappa;            /* penetration depth lambda0/xi0; <= 0 or inf: no induced A */
     int32_t charge_sign;     /* sign of the carrier charge, +1 or -1 */
     int32_t n_angles;        /* Fermi-surface angles, even */
-    int32_t n_energies;      /* positive Matsubara energies eps_n = t (n + 1/2) */
+    int32_t n_energies;      /* positive Matsubara energies eps_n = t (n + 1/2); 0 = from eps_cut */
     double lattice_ox, lattice_oy; /* origin of the rotated lattices relative to the
                                       grid-box centre, units of h (default 0.1, 0.2) */
     int32_t precision;       /* sc_precision: FP64 plain sweep or FP32 production sweep */
@@ -140,6 +140,12 @@ typedef struct {
                                 sc_create); every added part must lie inside the grid box */
     const sc_part *parts;
     int32_t gauge;           /* sc_gauge of the external vector potential */
+    double eps_cut;          /* energy cutoff (units 2 pi kB Tc), used when n_energies = 0:
+                                Matsubara, the energies t (n + 1/2) below it; Ozaki, the
+                                fewest poles whose largest energy t z_max / 2 pi reaches it */
+    const uint8_t *mask;     /* optional [ny][nx] grain mask (1 = inside) that the caller
+                                expects; sc_create returns SC_EINVAL unless it equals the
+                                mask built from the shape (copied, not retained) */
 } sc_params;
 
 typedef struct {
@@ -163,6 +169,10 @@ typedef struct {
    the n-pole continued-fraction representation 1/(1 + e^x) =
    1/2 - sum_p R_p [1/(x - i z_p) + 1/(x + i z_p)], 1 <= n <= 1024. */
 sc_status sc_ozaki_poles(int32_t n, double *z, double *R);
+/* The fewest Ozaki poles whose largest energy t z_max / 2 pi reaches eps_cut
+   (units 2 pi kB Tc; host only), or 0 when 1024 poles do not reach it or the
+   arguments are not positive. */
+int32_t sc_ozaki_poles_for_cutoff(double t, double eps_cut);
 /* The context's positive energies (units of 2 pi kB Tc) and their weights in
    the energy sums (n_energies each). */
 sc_status sc_energy_grid(const sc_ctx *ctx, double *eps, double *weights);

@@ -375,6 +375,21 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         g_create_error = "energy_sum must be SC_SUM_MATSUBARA or SC_SUM_OZAKI";
         return SC_EINVAL;
     }
+    // n_energies = 0: the count follows from the energy cutoff
+    sc_params resolved = *p;
+    if (resolved.n_energies == 0) {
+        if (!(p->eps_cut > 0.0) || !(p->t > 0.0)) {
+            g_create_error = "n_energies = 0 needs eps_cut > 0 and t > 0";
+            return SC_EINVAL;
+        }
+        resolved.n_energies = p->energy_sum == SC_SUM_OZAKI ? sc_ozaki_poles_for_cutoff(p->t, p->eps_cut)
+                                                            : (int32_t)std::ceil(p->eps_cut / p->t - 0.5);
+        if (resolved.n_energies < 1) {
+            g_create_error = "eps_cut gives no energy";
+            return SC_EINVAL;
+        }
+    }
+    p = &resolved;
     if (p->energy_sum == SC_SUM_OZAKI && (p->n_energies < 1 || p->n_energies > 1024)) {
         g_create_error = "Ozaki sums take 1 to 1024 poles (n_energies)";
         return SC_EINVAL;
@@ -385,6 +400,9 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         return SC_ENOMEM;
     }
     std::string why = ctx->geo.build(*p);
+    if (why.empty() && p->mask &&
+        std::memcmp(p->mask, ctx->geo.mask.data(), ctx->geo.mask.size()) != 0)
+        why = "the given mask does not match the mask of the shape";
     if (!why.empty()) {
         g_create_error = why;
         delete ctx;

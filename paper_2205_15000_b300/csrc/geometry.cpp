@@ -468,6 +468,7 @@ std::string Geometry::build(const sc_params &p) {
     }
     prm.vx = prm.vy = nullptr;
     prm.parts = nullptr;
+    prm.mask = nullptr;
 
     // the grid box must contain every added part
     const double X0 = p.x0, X1 = p.x0 + nx * h, Y0 = p.y0, Y1 = p.y0 + ny * h;

@@ -120,3 +120,23 @@ extern "C" sc_status sc_ozaki_poles(int32_t n, double *z, double *R) {
     }
     return SC_OK;
 }
+
+extern "C" int32_t sc_ozaki_poles_for_cutoff(double t, double eps_cut) {
+    if (!(t > 0.0) || !(eps_cut > 0.0)) return 0;
+    for (int n = 1; n <= 1024; ++n) {
+        // smallest positive eigenvalue b_min (ascending index n of 2n): z_max = 1/b_min
+        const int M = 2 * n;
+        std::vector<double> off(M - 1);
+        for (int m = 1; m < M; ++m) off[m - 1] = 1.0 / (2.0 * std::sqrt((2.0 * m - 1.0) * (2.0 * m + 1.0)));
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 200 && hi - lo > 1e-17 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (sturm_count(off, mid) > n)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        if (t / (0.5 * (lo + hi)) / (2.0 * M_PI) >= eps_cut) return n;
+    }
+    return 0;
+}

@@ -61,6 +61,7 @@ class sc_params(ctypes.Structure):
         ("n_components", ctypes.c_int32), ("pairings", ctypes.c_int32 * 4), ("tc_ratios", ctypes.c_double * 4),
         ("n_parts", ctypes.c_int32), ("parts", ctypes.POINTER(sc_part)),
         ("gauge", ctypes.c_int32),
+        ("eps_cut", ctypes.c_double), ("mask", ctypes.POINTER(ctypes.c_uint8)),
     ]
 
 
@@ -110,7 +111,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
-            "sc_accel_get_state", "sc_ozaki_poles", "sc_energy_grid",
+            "sc_accel_get_state", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
@@ -149,6 +150,7 @@ def _load():
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
         "sc_ozaki_poles": [i32, vp, vp],
+        "sc_ozaki_poles_for_cutoff": [f64, f64],
         "sc_energy_grid": [vp, vp, vp],
         "sc_accel_params_default": [i32, P(sc_accel_params)],
         "sc_accelerate": [vp, P(sc_accel_params), vp],
@@ -259,6 +261,11 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
             arr[k].vy = ay.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     p.n_parts = len(parts)
     p.parts = ctypes.cast(arr, ctypes.POINTER(sc_part))
+    p.eps_cut = float(d.get("eps_cut", 0.0))
+    if d.get("mask") is not None:  # the caller's expectation of the grain mask, checked by sc_create
+        mk = np.ascontiguousarray(d["mask"], np.uint8)
+        keep.append(mk)
+        p.mask = mk.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
     p._keep = (vx, vy, keep)
     return p
 
@@ -329,6 +336,11 @@ def sc_ozaki_poles(n):
     z, R = np.zeros(n), np.zeros(n)
     _check(lib.sc_ozaki_poles(int(n), _ptr(z), _ptr(R)))
     return z, R
+
+
+def sc_ozaki_poles_for_cutoff(t, eps_cut):
+    """The fewest Ozaki poles whose largest energy reaches eps_cut (0: none)."""
+    return int(lib.sc_ozaki_poles_for_cutoff(ctypes.c_double(t), ctypes.c_double(eps_cut)))
 
 
 def sc_energy_grid(ctx, n_e):

@@ -5,6 +5,8 @@ oracle's, decision for decision."""
 import os
 import re
 
+import math
+
 import numpy as np
 import pytest
 
@@ -192,3 +194,32 @@ def test_steps_per_sweep_count():
     ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
     assert c.info.steps_per_sweep == p["n_energies"] * int(np.sum(2 * (ns + 1)))
     assert c.info.points_per_sweep == 2 * p["n_energies"] * int(ns.sum())
+
+
+@pytest.mark.parametrize("energy_sum", ["matsubara", "ozaki"])
+def test_energy_count_from_cutoff(energy_sum):
+    """n_energies = 0 takes the count from eps_cut: the Matsubara energies
+    t (n + 1/2) below it, or the fewest Ozaki poles whose largest energy
+    t z_max / 2 pi reaches it (counted here from the oracle's poles)."""
+    t, cut = 0.1, 8.0
+    base = W.disc(5.0, 32, n_angles=8, t=t, energy_sum=energy_sum)
+    if energy_sum == "matsubara":
+        expect = sum(1 for n in range(10000) if t * (n + 0.5) < cut)
+    else:
+        expect = next(n for n in range(1, 200) if t * oracle.ozaki_poles(n)[0][-1] / (2 * math.pi) >= cut)
+        assert sc.sc_ozaki_poles_for_cutoff(t, cut) == expect
+    c = sc.Context(dict(base, n_energies=0, eps_cut=cut), host_only=True)
+    r = sc.Context(dict(base, n_energies=expect), host_only=True)
+    assert c.info.steps_per_sweep == r.info.steps_per_sweep and c.info.norm_D == r.info.norm_D
+    with pytest.raises(sc.ScError):
+        sc.Context(dict(base, n_energies=0), host_only=True)
+
+
+def test_given_mask_must_match_the_shape():
+    p = W.annulus(6.0, 2.5, 48, margin=0.3, n_angles=8, n_energies=2)
+    m = sc.Context(p, host_only=True).mask()
+    sc.Context(dict(p, mask=m), host_only=True)
+    bad = m.copy()
+    bad[24, 24] ^= 1
+    with pytest.raises(sc.ScError):
+        sc.Context(dict(p, mask=bad), host_only=True)
