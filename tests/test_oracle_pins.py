@@ -584,3 +584,37 @@ def test_gauge_covariance_second_order():
     for c in range(3):
         assert 3.0 < errs[0][c] / errs[1][c] < 5.5
     assert errs[1][0] < 3e-4 and errs[1][1] < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# P11: charge conservation at self-consistency.  The Eilenberger equation
+# conserves the current only when Delta solves the gap equation (Sec. 2):
+# after Picard convergence the divergence of j in the interior is orders of
+# magnitude below that of a non-self-consistent field, and what remains is set
+# by the Fermi-surface quadrature (it falls with the angle count, not with h).
+# ---------------------------------------------------------------------------
+def _rms_divergence(p, j, sel):
+    h = p["h"]
+    dv = np.zeros(j.shape[:2])
+    dv[1:-1, 1:-1] = (j[1:-1, 2:, 0] - j[1:-1, :-2, 0] + j[2:, 1:-1, 1] - j[:-2, 1:-1, 1]) / (2 * h)
+    return float(np.sqrt(np.mean(dv[sel] ** 2)))
+
+
+def test_current_is_conserved_at_self_consistency():
+    out = {}
+    for n, N in ((24, 16), (24, 32), (48, 32)):
+        p = W.disc(4.0, n, margin=0.2, pairing=0, t=0.5, n_angles=N, n_energies=6, flux_quanta=1.0,
+                   charge_sign=-1)
+        g = oracle.OracleGeom(p)
+        X, Y = W.grid_xy(p)
+        sel = g.mask().astype(bool) & (np.hypot(X, Y) < 2.5)
+        d0 = W.noisy_delta(p, 0.26, 0.2, seed=5)
+        res = g.picard(d0, 150, update_a=False)
+        assert res["history"][-1] < 1e-6
+        j = res["last"]["j"]
+        scale = float(np.max(np.hypot(j[..., 0], j[..., 1])))
+        out[(n, N)] = (_rms_divergence(p, j, sel) / scale, _rms_divergence(p, g.full_sweep(d0)["j"], sel) / scale)
+    for conv, noisy in out.values():
+        assert conv < 3e-3 * noisy
+    assert out[(24, 32)][0] < out[(24, 16)][0] / 3           # set by the angular quadrature
+    assert 0.5 < out[(48, 32)][0] / out[(24, 32)][0] < 2.0    # not by the grid spacing
