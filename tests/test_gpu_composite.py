@@ -223,3 +223,55 @@ def test_batch_with_composite_members_equals_single_contexts(precision, tol):
                 scale = max(np.max(np.abs(rs[k])), 1e-3)
                 assert np.max(np.abs(rm[k] - rs[k])) <= tol * scale, (it, k)
     b.close()
+
+
+def test_options_compose_fp64():
+    """Every option at once -- two order-parameter components (chiral
+    d_xy + i d_x2-y2), Ozaki sums, the implicit midpoint stepper, an annulus
+    and the solenoid gauge with an induced field -- against the oracle to 1e-10."""
+    p = W.annulus(5.0, 2.0, 40, margin=0.3, pairing=2, t=0.4, n_angles=16, n_energies=5, gauge="solenoid",
+                  flux_quanta=0.7, charge_sign=-1)
+    p["components"] = [(2, 1.0), (1, 0.9)]
+    p["energy_sum"] = "ozaki"
+    p["stepper"] = "midpoint"
+    X, Y = W.grid_xy(p)
+    d = np.stack([0.15 * np.exp(-1j * np.arctan2(Y, X)), 0.15j * np.exp(-1j * np.arctan2(Y, X))])
+    d = d * (1 + 0.05 * W.noisy_delta(p, 1.0, 1.0, seed=80))
+    g, m, res = _run_both(p, d, _smooth_a(p, 0.02), "fp64", n_sweeps=2)
+    for R in res:
+        o, r = R["o"], R["r"]
+        np.testing.assert_allclose(R["exits"], o["exit"][0], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["j"], o["j"], atol=TOL64, rtol=0)
+        np.testing.assert_allclose(r["F"], o["F"], atol=TOL64, rtol=0)
+
+
+def test_batch_mixes_components_and_gauges():
+    """Batch members may differ in components, gauge and geometry: each equals
+    its own context (FP64)."""
+    from paper_2205_15000_b300 import sc
+    q1 = W.annulus(5.0, 2.0, 40, margin=0.3, pairing=2, t=0.4, n_angles=16, n_energies=5, gauge="solenoid",
+                   flux_quanta=0.7)
+    q1["components"] = [(2, 1.0), (1, 0.9)]
+    X, Y = W.grid_xy(q1)
+    d1 = np.stack([0.15 * np.exp(-1j * np.arctan2(Y, X)), 0.15j * np.exp(-1j * np.arctan2(Y, X))])
+    q2, d2, _ = case("two_discs_landau")
+    q3 = W.disc(4.0, 28, pairing=0, t=0.5, n_angles=16, n_energies=10, flux_quanta=0.7)
+    d3 = W.noisy_delta(q3, 0.26, 0.1, seed=81)
+    grains = [(q1, d1), (q2, d2), (q3, d3)]
+    b = sc.Batch([q for q, _ in grains], precision="fp64")
+    singles = [sc.Context(q, precision="fp64") for q, _ in grains]
+    for (q, d), mb, s in zip(grains, b.members, singles):
+        mb.set_fields(d)
+        s.set_fields(d)
+    for it in range(2):
+        b.sweep()
+        for s in singles:
+            s.sweep()
+        for mb, s in zip(b.members, singles):
+            rm = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in mb.outputs().items()}
+            rs = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in s.outputs().items()}
+            for k in ("delta_new", "j", "F"):
+                scale = max(np.max(np.abs(rs[k])), 1e-3)
+                assert np.max(np.abs(rm[k] - rs[k])) <= 1e-12 * scale, (it, k)
+    b.close()
