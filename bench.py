@@ -620,6 +620,56 @@ def run_accel_table(args):
     return 0
 
 
+def run_ldos(args):
+    """LDOS sweeps (Sec. 2): the C4 grain (d-wave disc R 25, 128^2, 64 angles,
+    t 0.2, one vortex) at 64 real energies spanning [-Delta0, Delta0] with the
+    broadening 0.05 Delta0 (Delta0 = the bulk gap maximum), 20 retarded sweeps
+    per call (boundary burn-in) and the rotate-back; steps counted as in the
+    Matsubara sweep (both directions, every segment, every energy)."""
+    import torch
+    from paper_2205_15000_b300 import sc
+    world, rank, local = ranks.env_ranks()
+    torch.cuda.set_device(local)
+    dist = ranks.init("nccl")
+    p, delta, _ = W.c4_disc_d()
+    d0 = math.sqrt(2.0) * W.BULK_GUESS[("dx2y2", 0.2)]
+    energies = np.linspace(-d0, d0, 64)
+    n_burnin = 20
+    ctx = sc.Context(p, precision=args.precision)
+    ctx.set_fields(delta)
+    info = ctx.info
+    stream = torch.cuda.current_stream()
+    out = torch.empty((len(energies), p["ny"], p["nx"]), dtype=torch.float64, device="cuda")
+    per_call = n_burnin * len(energies) * (info.steps_per_sweep // p["n_energies"])
+    for _ in range(args.warmup):
+        sc.sc_ldos(ctx.h, energies, 0.05 * d0, n_burnin, out, True, stream)
+    torch.cuda.synchronize()
+    ranks.barrier(dist)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a_, b_ in ev:
+        a_.record(stream)
+        sc.sc_ldos(ctx.h, energies, 0.05 * d0, n_burnin, out, True, stream)
+        b_.record(stream)
+    torch.cuda.synchronize()
+    ms = [a_.elapsed_time(b_) for a_, b_ in ev]
+    total = ranks.max_over_ranks(dist, float(sum(ms)), torch.device("cuda", local))
+    value = ranks.throughput(per_call * args.steps, world, total * 1e-3)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.median(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "c4_ldos_128sq_64ang_64energies_vortex", "n_energies": len(energies),
+                       "broadening": 0.05 * d0, "burnin_sweeps_per_step": n_burnin,
+                       "steps_per_call": per_call, "precision": args.precision,
+                       "step": "sc_ldos: retarded sweeps with burn-in + rotate-back"},
+            "gpu_launches": (2 + n_burnin + 1) * args.steps,
+        }), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,6 +691,7 @@ def main():
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grains", type=int, default=64)
+    ap.add_argument("--ldos", action="store_true", help="time the LDOS sweeps on the c4 grain (64 energies)")
     ap.add_argument("--accel-table", action="store_true",
                     help="iterations of the four accelerators on the examples of App. E's table")
     ap.add_argument("--accel-ppx", type=float, default=20.0, help="points per xi0 for --accel-table")
@@ -655,6 +706,8 @@ def main():
         return run_reference(args)
     if args.accel_table:
         return run_accel_table(args)
+    if args.ldos:
+        return run_ldos(args)
     if args.workload == "c3":
         return run_batch(args)
     return run_ours(args)
