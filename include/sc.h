@@ -111,7 +111,8 @@ typedef struct {
     double kappa;            /* penetration depth lambda0/xi0; <= 0 or inf: no induced A */
     int32_t charge_sign;     /* sign of the carrier charge, +1 or -1 */
     int32_t n_angles;        /* Fermi-surface angles, even */
-    int32_t n_energies;      /* positive Matsubara energies eps_n = t (n + 1/2); 0 = from eps_cut */
+    int32_t n_energies;      /* positive Matsubara energies eps_n = t (n + 1/2), at most 4096
+                                (more than 256 run as energy blocks); 0 = from eps_cut */
     double lattice_ox, lattice_oy; /* origin of the rotated lattices relative to the
                                       grid-box centre, units of h (default 0.1, 0.2) */
     int32_t precision;       /* sc_precision: FP64 plain sweep or FP32 production sweep */
@@ -293,7 +294,7 @@ sc_status sc_accel_reset(sc_ctx *ctx);
 sc_status sc_accel_get_state(const sc_ctx *ctx, int32_t *iterations, double *alpha, double *w);
 
 /* Local density of states N(R, eps)/N_F = -<Im g^R(eps + i broadening)>/pi
-   (Sec. 2).  energies: host array of n_e real energies that must be symmetric
+   (Sec. 2).  energies: host array of n_e <= 256 real energies that must be symmetric
    about zero (eps_k = -eps_{n_e-1-k}), because gamma~ at eps is taken from
    gamma at -eps (Eq. symmetries).  Boundary values are burnt in with Delta, A
    frozen for up to n_burnin sweeps.  ldos_out: n_e * nx * ny doubles. */

@@ -75,22 +75,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
     T zr0[EPT], zi[EPT];
     int nid[EPT], mir[EPT];
     bool ev[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-        const int n = r + Lw * e;
-        ev[e] = n < n_e;
-        nid[e] = ev[e] ? n : n_e - 1;
-        if (RET) {
-            zr0[e] = (T)gs.energies[nid[e]];
-            zi[e] = (T)gs.broadening;
-            mir[e] = n_e - 1 - nid[e];
-        } else {
-            zr0[e] = T(0);
-            zi[e] = gs.mats_eps ? (T)gs.mats_eps[nid[e]] : (T)(gs.t * (nid[e] + 0.5));
-            mir[e] = nid[e];
-        }
-    }
     const T *__restrict__ wl = (const T *)a.wimg;  // retarded: n_e weights per slot
+    const int nb = gs.n_blocks;
 
     for (;;) {
         int item = 0;
@@ -98,7 +84,26 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
         item = __shfl_sync(FULLM, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
-        const int L = gs.groups[(int64_t)it.y * G + gi];
+        // line group and energy block of this item (one block unless the energies
+        // exceed one lane layout)
+        const int grp = nb > 1 ? it.y / nb : it.y;
+        const int e0 = nb > 1 ? (it.y - grp * nb) * ne_pad : 0;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+            const int n = e0 + r + Lw * e;
+            ev[e] = n < n_e;
+            nid[e] = ev[e] ? n : n_e - 1;
+            if (RET) {
+                zr0[e] = (T)gs.energies[nid[e]];
+                zi[e] = (T)gs.broadening;
+                mir[e] = n_e - 1 - nid[e];
+            } else {
+                zr0[e] = T(0);
+                zi[e] = gs.mats_eps ? (T)gs.mats_eps[nid[e]] : (T)(gs.t * (nid[e] + 0.5));
+                mir[e] = nid[e];
+            }
+        }
+        const int L = gs.groups[(int64_t)grp * G + gi];
         const bool lv = L >= 0;
         const LineDev &ln = gs.lines[lv ? L : 0];
         const int ns = lv ? ln.ns : 0;  // lines without samples do not enter the loss

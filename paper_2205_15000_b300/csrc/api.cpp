@@ -95,6 +95,23 @@ void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ep
         return;
     }
     int best_pad = 1 << 30, best_l = 32, best_e = 8;
+    if (n_e > 32 * 8) {
+        // several energy blocks per line: the fewest padded lane slots, each block
+        // counted with 32 slots of per-block overhead (samples, coefficients)
+        for (int l : {32, 16, 8, 4})
+            for (int e = 8; e >= 1; --e) {
+                const int nb = (n_e + l * e - 1) / (l * e);
+                const int cost = nb * (l * e + 32);
+                if (cost < best_pad) {
+                    best_pad = cost;
+                    best_l = l;
+                    best_e = e;
+                }
+            }
+        lanes = best_l;
+        ept = best_e;
+        return;
+    }
     for (int l : {32, 16, 8, 4}) {
         const int e = (n_e + l - 1) / l;
         if (e > 8) continue;
@@ -143,9 +160,9 @@ sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out) {
 sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out) {
     if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
         return set_err(ctx, SC_EINVAL, "energy lanes per line must be 4, 8, 16 or 32");
-    if (ept < 1 || ept > 8 || lanes * ept < n_e)
-        return set_err(ctx, SC_EINVAL, "too many energies for the lane layout (at most 32 lanes x 8 per lane)");
-    const int key = lanes * 16 + ept;
+    if (ept < 1 || ept > 8) return set_err(ctx, SC_EINVAL, "energies per lane must be 1 to 8");
+    const int n_blocks = (n_e + lanes * ept - 1) / (lanes * ept);
+    const int key = n_blocks * 1024 + lanes * 16 + ept;
     auto it = ctx->plans.find(key);
     if (it != ctx->plans.end()) {
         *out = &it->second;
@@ -174,12 +191,16 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
         }
     }
     pl.n_groups = (int32_t)pl.group_cost.size();
+    pl.n_blocks = n_blocks;
+    pl.n_items = pl.n_groups * pl.n_blocks;
     std::vector<int> order(pl.n_groups);
     for (int i = 0; i < pl.n_groups; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return pl.group_cost[a] > pl.group_cost[b]; });
-    std::vector<int2> items(pl.n_groups);
-    for (int i = 0; i < pl.n_groups; ++i) items[i] = make_int2(0, order[i]);
+    // every energy block of a group is one item of the group's cost
+    std::vector<int2> items(pl.n_items);
+    for (int i = 0; i < pl.n_groups; ++i)
+        for (int k = 0; k < pl.n_blocks; ++k) items[(size_t)i * pl.n_blocks + k] = make_int2(0, order[i] * pl.n_blocks + k);
     CK(dalloc(ctx, &pl.d_groups, flat.size() * sizeof(int32_t)));
     CK(cudaMemcpy(pl.d_groups, flat.data(), flat.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(dalloc(ctx, &pl.d_items, items.size() * sizeof(int2)));
@@ -187,7 +208,7 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     const int bs = 128;
     int occ = scd::sweep_occupancy(ctx->fp64, ept, bs, ctx->stepper, ctx->d_ewt != nullptr);
     if (occ < 1) occ = 1;
-    pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+    pl.grid_blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_items + 3) / 4));
     pl.stride = (int64_t)G * std::max(ctx->geo.max_ns, 1) * lanes * ept;
     // descriptor of the context's own Matsubara sweep
     scd::GrainSweep gs{};
@@ -207,6 +228,7 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     gs.lanes = lanes;
     gs.lines_per_warp = G;
     gs.ne_pad = lanes * ept;
+    gs.n_blocks = pl.n_blocks;
     gs.max_ns = std::max(ctx->geo.max_ns, 1);
     gs.ept = ept;
     CK(dalloc(ctx, &pl.d_grain, sizeof(gs)));
@@ -265,10 +287,12 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
                             bool first, int parity, cudaStream_t st) {
     CKS(ensure_scratch(ctx, (size_t)pl.grid_blocks * 4 * (size_t)pl.stride * 2 * ctx->real_bytes));
     CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
+    if (!retarded && pl.n_blocks > 1)  // the energy blocks of a line add into the image
+        CK(cudaMemsetAsync(ctx->d_img_out, 0, (size_t)ctx->geo.n_slots * (ctx->fp64 ? 32 : 16), st));
     scd::SweepLaunch a{};
     a.grains = d_grain;
     a.items = pl.d_items;
-    a.n_items = pl.n_groups;
+    a.n_items = pl.n_items;
     a.counter = ctx->d_counter;
     a.scratch = ctx->d_scratch;
     a.scratch_stride = pl.stride;
@@ -280,6 +304,7 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     a.block_threads = 128;
     a.stepper = ctx->stepper;
     a.weighted = ctx->d_ewt != nullptr ? 1 : 0;
+    a.blocked = !retarded && pl.n_blocks > 1 ? 1 : 0;
     CK(scd::launch_sweep(ctx->fp64, a, st));
     return SC_OK;
 }
@@ -746,7 +771,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         const int occ = std::max(1, scd::sweep_occupancy(ctx->fp64, pl->ept, 128, ctx->stepper, ctx->d_ewt != nullptr));
         const int64_t resident = (int64_t)ctx->sm_count * occ * 4;
         const int l2 = 2 * pl->lanes, e2 = (ctx->n_e + l2 - 1) / l2;
-        if (pl->lanes < 32 && pl->n_groups < resident && 4 * ctx->n_e >= 3 * l2 * e2)
+        if (pl->lanes < 32 && pl->n_blocks == 1 && pl->n_groups < resident && 4 * ctx->n_e >= 3 * l2 * e2)
             st = make_plan_layout(ctx, ctx->n_e, l2, e2, &ctx->main_plan);
     }
     if (st != SC_OK) {
@@ -979,6 +1004,8 @@ void ldos_release(sc_ctx *ctx, LdosRun &R, cudaStream_t st) {
 sc_status ldos_check(sc_ctx *ctx, const double *energies, int32_t n_e, double broadening) {
     if (!energies || n_e < 1) return set_err(ctx, SC_EINVAL, "energies are required");
     if (!(broadening > 0.0)) return set_err(ctx, SC_EINVAL, "broadening must be > 0");
+    // gamma~ at eps comes from gamma at -eps parked by the same warp: one energy block
+    if (n_e > 32 * 8) return set_err(ctx, SC_EINVAL, "the LDOS takes at most 256 energies per call");
     for (int k = 0; k < n_e; ++k)
         if (std::fabs(energies[k] + energies[n_e - 1 - k]) > 1e-12 * (1.0 + std::fabs(energies[k])))
             return set_err(ctx, SC_EINVAL, "energies must be symmetric about zero");
@@ -1014,6 +1041,7 @@ sc_status ldos_burnin(sc_ctx *ctx, const double *energies, int32_t n_e, double b
     gs.ne_pad = pl->lanes * pl->ept;
     gs.max_ns = std::max(ctx->geo.max_ns, 1);
     gs.ept = pl->ept;
+    gs.n_blocks = 1;
     CK(cudaMemcpyAsync(R.d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(R.d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(R.d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st));
@@ -1073,7 +1101,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         const Plan &pl = *R.pl;
         const size_t t4 = ctx->fp64 ? 32 : 16;
         const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
-        const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+        const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_items + 3) / 4));
         const int64_t stride = 3 * pl.stride;
         cudaError_t e = cudaSuccess;
         const size_t nc = (size_t)ctx->geo.n_comp;
@@ -1108,7 +1136,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         scd::AdjointLaunch a{};
         a.grain = R.d_gs;
         a.items = pl.d_items;
-        a.n_items = pl.n_groups;
+        a.n_items = pl.n_items;
         a.counter = ctx->d_counter;
         a.scratch = d_scr;
         a.scratch_stride = stride;
@@ -1151,8 +1179,8 @@ static sc_status adjoint_plan(sc_ctx *ctx, Plan **out) {
     const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl->ept, 128, ctx->stepper));
     const int64_t resident = (int64_t)ctx->sm_count * occ * 4;
     int lanes = pl->lanes, ept = pl->ept;
-    int64_t items = pl->n_groups;
-    while (lanes < 32 && 2 * items <= resident) {
+    int64_t items = pl->n_items;
+    while (lanes < 32 && pl->n_blocks == 1 && 2 * items <= resident) {
         const int l2 = 2 * lanes, e2 = (ctx->n_e + l2 - 1) / l2;
         if (4 * ctx->n_e < 3 * l2 * e2) break;
         lanes = l2;
@@ -1184,7 +1212,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
         CK(dalloc(ctx, &ctx->d_gimg, ctx->geo.n_slots * t4));
     }
     const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
-    const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_groups + 3) / 4));
+    const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_items + 3) / 4));
     const int64_t stride = 2 * pl.stride;
     const size_t need = (size_t)blocks * 4 * (size_t)stride * 2 * ctx->real_bytes;
     if (need > ctx->adj_scratch_bytes) {
@@ -1225,7 +1253,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     scd::AdjointLaunch a{};
     a.grain = pl.d_grain;
     a.items = pl.d_items;
-    a.n_items = pl.n_groups;
+    a.n_items = pl.n_items;
     a.counter = ctx->d_counter;
     a.scratch = ctx->d_adj_scratch;
     a.scratch_stride = stride;

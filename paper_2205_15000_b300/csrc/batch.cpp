@@ -17,6 +17,8 @@
 
 struct sc_batch {
     std::vector<sc_ctx *> members;
+    std::vector<int> member_blocks;  // energy blocks of each member's layout
+    int blocked = 0;                 // some member splits its energies into blocks
     int device = 0;
     bool fp64 = false;
     int ept = 0;  // bound on energies per lane
@@ -104,12 +106,26 @@ void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
             ept = e;
         }
     }
+    if (best < (1 << 30)) return;
+    // more energies than one layout holds: energy blocks, each counted with 32
+    // slots of per-block overhead
+    for (int l : {32, 16, 8, 4})
+        for (int e = ept_max; e >= 1; --e) {
+            const int nb = (n_e + l * e - 1) / (l * e);
+            const int cost = nb * (l * e + 32);
+            if (cost < best) {
+                best = cost;
+                lanes = l;
+                ept = e;
+            }
+        }
 }
 
 // Lay out the work list for at most `ept` energies per lane.
 sc_status build(sc_batch *b, int ept) {
     free_graphs(b);  // captured graphs refer to the buffers rebuilt here
     std::vector<scd::GrainSweep> gs(b->members.size());
+    b->member_blocks.assign(b->members.size(), 1);
     struct It {
         int cost, grain, group;
     };
@@ -118,8 +134,6 @@ sc_status build(sc_batch *b, int ept) {
     int64_t lane_steps = 0;
     for (size_t g = 0; g < b->members.size(); ++g) {
         sc_ctx *c = b->members[g];
-        if (c->n_e > 32 * ept)
-            return berr(b, SC_EINVAL, "a member has more energies than 32 lanes x energies_per_lane");
         int lanes = 32, eg = ept;
         member_layout(c->n_e, ept, lanes, eg);
         Plan *pl = nullptr;
@@ -144,12 +158,16 @@ sc_status build(sc_batch *b, int ept) {
         d.ne_pad = pl->lanes * pl->ept;
         d.max_ns = std::max(c->geo.max_ns, 1);
         d.ept = pl->ept;
+        d.n_blocks = pl->n_blocks;
+        b->member_blocks[g] = pl->n_blocks;
         stride = std::max(stride, pl->stride);
         int64_t steps = 0;
         for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
-        lane_steps += steps * pl->lanes * pl->ept;
-        // cost of a group ~ steps x energies handled per lane
-        for (int q = 0; q < pl->n_groups; ++q) items.push_back({pl->group_cost[q] * pl->ept, (int)g, q});
+        lane_steps += steps * pl->lanes * pl->ept * pl->n_blocks;
+        // cost of a group ~ steps x energies handled per lane; one item per energy block
+        for (int q = 0; q < pl->n_groups; ++q)
+            for (int k = 0; k < pl->n_blocks; ++k)
+                items.push_back({pl->group_cost[q] * pl->ept, (int)g, q * pl->n_blocks + k});
     }
     // classes by energies per lane (largest first), longest items first within each
     std::stable_sort(items.begin(), items.end(), [&](const It &x, const It &y) {
@@ -189,6 +207,8 @@ sc_status build(sc_batch *b, int ept) {
     }
     b->ept = ept;
     b->lane_steps_per_sweep = lane_steps;
+    b->blocked = 0;
+    for (int nbk : b->member_blocks) b->blocked |= nbk > 1 ? 1 : 0;
     return SC_OK;
 }
 
@@ -320,6 +340,9 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         if (c->failed) return berr(b, SC_ESTATE, "a member context failed");
         sc_status s = sc_internal::rotate_fields(c, b->aux[g % sc_batch::kAux]);
         if (s != SC_OK) return berr(b, s, c->err);
+        if (b->blocked)  // the energy blocks of a line add into the zeroed images
+            BCK(cudaMemsetAsync(c->d_img_out, 0, (size_t)c->geo.n_slots * (c->fp64 ? 32 : 16),
+                                b->aux[g % sc_batch::kAux]));
     }
     fs = join(b, st);
     if (fs != SC_OK) return fs;
@@ -347,6 +370,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.block_threads = 128;
         a.stepper = b->stepper;
         a.weighted = b->weighted ? 1 : 0;
+        a.blocked = b->blocked;
         BCK(scd::launch_sweep(b->fp64, a, st));
     }
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));

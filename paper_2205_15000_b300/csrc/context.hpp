@@ -17,7 +17,9 @@ struct Plan {
     int32_t *d_groups = nullptr;         // [n_groups][lines_per_warp] line indices, -1 padded
     int32_t n_groups = 0;
     std::vector<int> group_cost;         // steps of the longest line of each group
-    int2 *d_items = nullptr;             // (0, group), longest first: single-context launches
+    int n_blocks = 1;                    // energy blocks of lanes x ept energies
+    int32_t n_items = 0;                 // n_groups x n_blocks work items
+    int2 *d_items = nullptr;             // (0, group x n_blocks + block), longest first: single-context launches
     scd::GrainSweep *d_grain = nullptr;  // descriptor of the context's Matsubara sweep
     int grid_blocks = 0;
     int64_t stride = 0;                  // scratch elements (complex) per warp

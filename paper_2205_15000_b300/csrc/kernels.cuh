@@ -127,6 +127,8 @@ struct GrainSweep {
     int32_t ne_pad;            // Lw * ept
     int32_t max_ns;            // longest line of the grain
     int32_t ept;               // energies per lane (equals the launch's EPT)
+    int32_t n_blocks;          // energy blocks of ne_pad energies: work item y of the grain is
+                               // line group y / n_blocks with the energies of block y % n_blocks
 };
 
 // One persistent launch over the work items (grain, line group) of any number
@@ -145,6 +147,8 @@ struct SweepLaunch {
     int32_t grid_blocks, block_threads;
     int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
     int32_t weighted;          // Matsubara mode: weighted energy sums (grains carry mats_w)
+    int32_t blocked;           // some grain splits its energies into blocks (its image is zeroed
+                               // before the launch and its blocks add into it)
 };
 
 // launchers (return cudaError_t)

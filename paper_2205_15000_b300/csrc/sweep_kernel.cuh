@@ -34,8 +34,10 @@ namespace scd {
 
 // One work item: the G lines of group it.y of grain gs, EPT energies per lane;
 // STEP 0 = closed-form step, 1 = implicit midpoint rule; WGT: weighted energy
-// sums (Ozaki's poles) in the Matsubara mode.
-template <typename T, int EPT, bool RET, int STEP, bool WGT>
+// sums (Ozaki's poles) in the Matsubara mode; BLK: the launch holds a grain whose
+// energies are split into blocks (every image of the launch is zeroed first and
+// the sample sums are added into it).
+template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK>
 __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
                                            Cx<T> *const warp_slab, const int lane) {
     typedef typename Vec4<T>::type T4;
@@ -50,6 +52,10 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
         const T h = (T)gs.h;
         const int n_e = gs.n_e;
         const int ne_pad = gs.ne_pad;
+        // energy block of this item (several when the energies exceed one lane layout)
+        const int nb = BLK ? gs.n_blocks : 1;
+        const int grp = BLK ? it.y / nb : it.y;
+        const int e0 = BLK ? (it.y - grp * nb) * ne_pad : 0;
 
         // the lane's energies: z = zr0 + i zi (+ a along the line)
         T zr0[EPT], zi[EPT];
@@ -58,7 +64,7 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
         bool ev[EPT];
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
-            const int n = r + Lw * e;
+            const int n = e0 + r + Lw * e;
             ev[e] = n < n_e;
             const int nn = ev[e] ? n : n_e - 1;
             nid[e] = nn;
@@ -74,7 +80,7 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                 if constexpr (WGT) wv[e] = ev[e] ? (T)gs.mats_w[nn] : T(0);
             }
         }
-        const int L = gs.groups[(int64_t)it.y * G + gi];
+        const int L = gs.groups[(int64_t)grp * G + gi];
         const bool lv = L >= 0;
         const LineDev &ln = gs.lines[lv ? L : 0];
         const int ns = lv ? ln.ns : 0;
@@ -256,7 +262,15 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                     o.y = -twopi * sfr;                         // Im Sf
                     o.z = fourpi * sg;                          // Sg
                     o.w = T(2) * (slo.x * sFi - slo.y * sFr);   // SF
-                    ((T4 *)gs.image_out)[slot0 + qs] = o;
+                    T4 *po = (T4 *)gs.image_out + slot0 + qs;
+                    if constexpr (BLK) {  // the blocks of a line add into the zeroed image
+                        atomicAdd(&po->x, o.x);
+                        atomicAdd(&po->y, o.y);
+                        atomicAdd(&po->z, o.z);
+                        atomicAdd(&po->w, o.w);
+                    } else {
+                        *po = o;
+                    }
                 }
             } else if (comb) {
                 // LDOS: -Im g / pi = Re[(1 - p)/(1 + p)] = 2 Re(1/D) - 1
@@ -287,7 +301,7 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
     }
 }
 
-template <typename T, int EPT, bool RET, int STEP, bool WGT>
+template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS) : 1)
     sweep_kernel(SweepLaunch a) {
     const int lane = threadIdx.x & 31;
@@ -299,16 +313,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLO
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
-        sweep_item<T, EPT, RET, STEP, WGT>(a, it, a.grains[it.x], warp_slab, lane);
+        sweep_item<T, EPT, RET, STEP, WGT, BLK>(a, it, a.grains[it.x], warp_slab, lane);
     }
 }
 
-template <typename T, bool RET, int STEP, bool WGT>
+template <typename T, bool RET, int STEP, bool WGT, bool BLK = false>
 static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: sweep_kernel<T, E, RET, STEP, WGT><<<grid, block, 0, st>>>(a); break;
+    case E: sweep_kernel<T, E, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
@@ -319,6 +333,9 @@ static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
 template <typename T, int STEP>
 static cudaError_t sweep_launch_s(const SweepLaunch &a, cudaStream_t st) {
     if (a.retarded) return sweep_dispatch<T, true, STEP, false>(a, st);
+    if (a.blocked)
+        return a.weighted ? sweep_dispatch<T, false, STEP, true, true>(a, st)
+                          : sweep_dispatch<T, false, STEP, false, true>(a, st);
     return a.weighted ? sweep_dispatch<T, false, STEP, true>(a, st) : sweep_dispatch<T, false, STEP, false>(a, st);
 }
 
