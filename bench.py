@@ -568,45 +568,74 @@ def run_accel_table(args):
                        for pc, (shift, tcr) in zip(pair_list, comps)])
         d0 = d0[0] if len(comps) == 1 else d0
         magn = p["kappa"] > 0 and math.isfinite(p["kappa"])
+        def iteration(ctx, m, prm, prev):
+            """One sweep + residuals + accelerator step of the Python loop; prev holds
+            (j, F) of the previous iteration."""
+            ctx.sweep()
+            o = ctx.outputs()
+            d_in, a_in = ctx.fields()
+            dn = o["delta_new"].reshape(d_in.shape)
+            # Eq. global_error per order-parameter component (l2 over the grain), and
+            # the change of j, A_ind and F between iterations
+            dd = (dn - d_in).reshape(-1, *m.shape)[:, m]
+            din = d_in.reshape(-1, *m.shape)[:, m]
+            errs = [float(torch.linalg.vector_norm(dd[c]) / max(float(torch.linalg.vector_norm(din[c])), 1e-300))
+                    for c in range(dd.shape[0])]
+            j = o["j"]
+            if prev[0] is not None:
+                errs.append(float(torch.linalg.vector_norm(j - prev[0]) / max(float(torch.linalg.vector_norm(prev[0])), 1e-30)))
+                errs.append(abs(o["F_total"] - prev[1]) / max(abs(prev[1]), 1e-300))
+            prev[0], prev[1] = j.clone(), o["F_total"]
+            ctx.accelerate(prm)
+            if magn:
+                _, a_out = ctx.fields()
+                na = float(torch.linalg.vector_norm(a_in))
+                errs.append(float(torch.linalg.vector_norm(a_out - a_in)) / na if na > 0 else 1.0)
+            return errs
+
+        # untimed warm-up of both loops: plan creation, module loads, torch's first kernels
+        warm = sc.Context(p, precision=args.precision)
+        warm.set_fields(d0)
+        mw = torch.as_tensor(warm.mask().astype(bool), device="cuda")
+        for kind in kinds:
+            prev = [None, None]
+            for _ in range(2):
+                iteration(warm, mw, sc.accel_params(kind), prev)
+            warm.self_consistency(sc.accel_params(kind), max_iter=2, tol=0.0, check_every=1)
+        torch.cuda.synchronize()
+        del warm
         res = {}
         for kind in kinds:
             ctx = sc.Context(p, precision=args.precision)
             ctx.set_fields(d0)
             m = torch.as_tensor(ctx.mask().astype(bool), device="cuda")
             prm = sc.accel_params(kind)
-            prev_j = prev_F = None
+            prev = [None, None]
             conv = None
             hist = []
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             for it in range(1, max_iter + 1):
-                ctx.sweep()
-                o = ctx.outputs()
-                d_in, a_in = ctx.fields()
-                dn = o["delta_new"].reshape(d_in.shape)
-                # Eq. global_error per order-parameter component (l2 over the grain), and
-                # the change of j, A_ind and F between iterations
-                dd = (dn - d_in).reshape(-1, *m.shape)[:, m]
-                din = d_in.reshape(-1, *m.shape)[:, m]
-                errs = [float(torch.linalg.vector_norm(dd[c]) / max(float(torch.linalg.vector_norm(din[c])), 1e-300))
-                        for c in range(dd.shape[0])]
-                j = o["j"]
-                if prev_j is not None:
-                    errs.append(float(torch.linalg.vector_norm(j - prev_j) / max(float(torch.linalg.vector_norm(prev_j)), 1e-30)))
-                    errs.append(abs(o["F_total"] - prev_F) / max(abs(prev_F), 1e-300))
-                prev_j, prev_F = j.clone(), o["F_total"]
-                ctx.accelerate(prm)
-                if magn:
-                    _, a_out = ctx.fields()
-                    na = float(torch.linalg.vector_norm(a_in))
-                    errs.append(float(torch.linalg.vector_norm(a_out - a_in)) / na if na > 0 else 1.0)
+                errs = iteration(ctx, m, prm, prev)
                 if it % 10 == 1:
                     hist.append(max(errs))
                 if it > 1 and max(errs) < tol:
                     conv = it
                     break
             torch.cuda.synchronize()
+            py_ms = (time.perf_counter() - t0) * 1e3 / it
+            # the same iterations through the native loop (sc_self_consistency), residual
+            # read only at the end
+            n_nat = min(it, 200)
+            ctx2 = sc.Context(p, precision=args.precision)
+            ctx2.set_fields(d0)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ctx2.self_consistency(prm, max_iter=n_nat, tol=0.0, check_every=1 << 30)
+            torch.cuda.synchronize()
+            native_ms = (time.perf_counter() - t1) * 1e3 / n_nat
             res[kind] = {"iterations": conv if conv is not None else f"not converged in {max_iter}",
-                         "ms_per_iteration": (time.perf_counter() - t0) * 1e3 / it,
+                         "ms_per_iteration": py_ms, "native_ms_per_iteration": native_ms,
                          "final_residual": max(errs), "residual_every_10": hist if args.accel_history else None}
         out[name] = {"ours": res, "paper": dict(zip(kinds, PAPER_ACCEL_TABLE[name])),
                      "grid": [p["nx"], p["ny"]], "ozaki_poles": p["n_energies"]}

@@ -286,6 +286,17 @@ sc_status sc_accel_params_default(int32_t kind, sc_accel_params *p);
 /* One accelerator step after a sweep; Delta and A_ind of the context are
    replaced by x_{i+1} (the next sweep reads them). */
 sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream);
+/* The self-consistency loop of Alg. suprcon run natively: per iteration a
+   sweep, then (every check_every iterations, and at max_iter) the residual
+   eps_G of Delta (Eq. global_error, l2) read back and compared with tol, then
+   the accelerator step (which updates A_ind when kappa is finite).  Stops
+   after the sweep whose residual is below tol (the context then holds those
+   fields, their boundary values and outputs) or after max_iter sweeps (no step
+   after the last).  iterations and eps_G (may be NULL) receive the sweeps run
+   and the last residual read.  Returns SC_OK when converged, SC_ENOTCONV
+   otherwise.  Only the residual checks wait for the device. */
+sc_status sc_self_consistency(sc_ctx *ctx, const sc_accel_params *p, int32_t max_iter, double tol,
+                              int32_t check_every, int32_t *iterations, double *eps_G, void *stream);
 sc_status sc_accel_reset(sc_ctx *ctx);
 /* Accelerator history: steps taken, step sizes (BB/Picard/Polyak: alpha in
    [0]; CongAcc: alpha_c for c = Re Delta_0, Im Delta_0, ..., Re Delta_{C-1},

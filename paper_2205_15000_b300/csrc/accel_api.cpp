@@ -177,3 +177,28 @@ sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream) {
 }
 
 }  // extern "C"
+
+extern "C" sc_status sc_self_consistency(sc_ctx *ctx, const sc_accel_params *p, int32_t max_iter, double tol,
+                                         int32_t check_every, int32_t *iterations, double *eps_G, void *stream) {
+    ACKS(sc_internal::check_ctx(ctx));
+    if (!p || max_iter < 1 || !(tol >= 0.0) || check_every < 1)
+        return set_err(ctx, SC_EINVAL, "self-consistency needs parameters, max_iter >= 1, tol >= 0, check_every >= 1");
+    double eps = -1.0;
+    int it = 0;
+    bool converged = false;
+    for (it = 1; it <= max_iter; ++it) {
+        ACKS(sc_riccati_sweep(ctx, stream));
+        if (it % check_every == 0 || it == max_iter) {
+            ACKS(sc_gap_update(ctx, nullptr, &eps, 1, stream));
+            if (eps < tol) {
+                converged = true;
+                break;
+            }
+        }
+        if (it == max_iter) break;
+        ACKS(sc_accelerate(ctx, p, stream));
+    }
+    if (iterations) *iterations = it > max_iter ? max_iter : it;
+    if (eps_G) *eps_G = eps;
+    return converged ? SC_OK : SC_ENOTCONV;
+}

@@ -111,7 +111,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
             "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
-            "sc_accel_get_state", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
+            "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
             "sc_batch_get_info", "sc_last_error", "sc_version"]
@@ -150,6 +150,7 @@ def _load():
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
         "sc_ozaki_poles": [i32, vp, vp],
+        "sc_self_consistency": [vp, P(sc_accel_params), i32, f64, i32, P(i32), P(f64), vp],
         "sc_ozaki_poles_for_cutoff": [f64, f64],
         "sc_energy_grid": [vp, vp, vp],
         "sc_accel_params_default": [i32, P(sc_accel_params)],
@@ -629,6 +630,17 @@ class Context:
     def accelerate(self, params, stream=None):
         """One accelerator step (App. E) after a sweep: params from accel_params()."""
         sc_accelerate(self.h, params, stream)
+
+    def self_consistency(self, params, max_iter=1000, tol=1e-5, check_every=1, stream=None):
+        """The native loop of Alg. suprcon (sweep, residual check, accelerator
+        step): returns (converged, iterations, eps_G)."""
+        it = ctypes.c_int32(0)
+        eps = ctypes.c_double(0.0)
+        st = lib.sc_self_consistency(self.h, ctypes.byref(params), int(max_iter), float(tol), int(check_every),
+                                     ctypes.byref(it), ctypes.byref(eps), _stream(stream))
+        if st not in (SC_OK, SC_ENOTCONV):
+            _check(st, self.h)
+        return st == SC_OK, it.value, eps.value
 
     def ldos(self, energies, broadening, n_burnin=20, stream=None):
         import torch

@@ -132,3 +132,37 @@ def test_adaptive_accelerators_converge_where_fixed_steps_struggle():
     assert its["barzilai-borwein"] is not None and its["congacc"] is not None
     for k in ("barzilai-borwein", "congacc"):
         assert its["picard"] is None or its[k] < its["picard"]
+
+
+@pytest.mark.parametrize("kind", ["picard", "barzilai-borwein"])
+def test_native_loop_equals_python_loop(kind):
+    """sc_self_consistency runs the same operations as a sweep/accelerate loop
+    driven from Python: identical fields after a fixed iteration count, and the
+    same stopping iteration for a tolerance."""
+    import torch
+    from paper_2205_15000_b300 import sc
+    p, d0 = _grain()
+    prm = sc.accel_params(kind)
+    a = sc.Context(p, precision="fp64")
+    a.set_fields(d0)
+    conv, it, eps = a.self_consistency(prm, max_iter=9, tol=0.0, check_every=100)
+    assert not conv and it == 9
+    b = sc.Context(p, precision="fp64")
+    b.set_fields(d0)
+    for k in range(9):
+        b.sweep()
+        if k < 8:
+            b.accelerate(prm)
+    fa, fb = a.fields(), b.fields()
+    torch.cuda.synchronize()
+    assert torch.equal(fa[0], fb[0]) and torch.equal(fa[1], fb[1])
+    assert eps == ctypes_eps(sc, b)
+    # stopping on the tolerance: the iteration at which the Python loop first meets
+    # it (without screening, where Picard converges too)
+    q = dict(p, kappa=0.0)
+    c = sc.Context(q, precision="fp64")
+    c.set_fields(d0)
+    conv, it, eps = c.self_consistency(prm, max_iter=400, tol=1e-3)
+    assert conv and eps < 1e-3 and it > 1
+    _, hist = _gpu_loop(q, d0, kind, it)
+    assert np.all(hist[:-1] >= 1e-3) and hist[-1] < 1e-3
