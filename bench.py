@@ -34,14 +34,16 @@ from paper_2205_15000_b300 import workloads as W  # noqa: E402
 
 METRIC = "Riccati trajectory-steps/s"
 WORKLOAD = "c2_diamond_dx2y2_256sq_128ang_80eps"
-# algorithmic FP32 lane-operations of the sweep kernel per (angle pair, sample,
-# energy): two closed-form steps (coefficients 58 + application 18 each) and one
-# propagator/energy-sum evaluation (22); MUFU operations counted separately (15)
-ALG_FP32_OPS_PER_PSE = 2 * (58 + 18) + 22
+# algorithmic FP32 lane-operations of the sweep per (angle pair, sample, energy):
+# two closed-form steps (coefficients gamma_h, E, K: 34; application of the
+# Moebius map: 18) and one propagator/energy-sum evaluation (21), with the terms
+# that depend only on the segment (Delta, the Doppler shift, its length) shared by
+# the energies and not counted; MUFU operations counted separately (15)
+ALG_FP32_OPS_PER_PSE = 2 * (34 + 18) + 21
 ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
 # the implicit midpoint stepper: a quadratic per step (47 FP32 ops, 3 MUFU) with the
 # same propagator evaluation
-ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 47 + 22}
+ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 47 + 21}
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
 # FP64 pipe: ncu reports sm__inst_executed_pipe_fp64 peak 0.0625 warp instructions
@@ -201,12 +203,14 @@ def run_ours(args):
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
             f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     p["stepper"] = args.stepper
+    if args.lanes:  # a fixed lane layout (profiling a small case in the layout of a large one)
+        workload += f"_lanes{args.lanes}"
     if args.energy_sum == "ozaki":
         # Ozaki's poles up to the same energy cutoff (eps_c = 16 pi kB Tc)
         p["energy_sum"] = "ozaki"
         p["n_energies"] = W.ozaki_poles_for_cutoff(p["t"])
         workload += f"_ozaki{p['n_energies']}"
-    ctx = sc.Context(p, precision=args.precision, record_timings=True)
+    ctx = sc.Context(p, precision=args.precision, lanes_per_line=args.lanes, record_timings=True)
     info = ctx.info
     stream = torch.cuda.current_stream()
     d_delta = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128)).contiguous().to(dev)
@@ -719,6 +723,8 @@ def main():
                          "annulus: d-wave annulus R> 25, R< 10 (256^2), solenoid gauge")
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
+                    help="energy lanes per line (0: the library's choice)")
     ap.add_argument("--grains", type=int, default=64)
     ap.add_argument("--ldos", action="store_true", help="time the LDOS sweeps on the c4 grain (64 energies)")
     ap.add_argument("--accel-table", action="store_true",

@@ -15,7 +15,7 @@ LIB = os.path.join(LIBDIR, "libsc.so")
 SOURCES = ["kernels.cu", "sweep_f32.cu", "sweep_f64.cu", "lattice_f32.cu", "adjoint.cu", "adjoint_f32.cu",
            "adjoint_f64.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu", "accel.cu", "accel_api.cpp", "ozaki.cpp", "vecpot.cu"]
 HEADERS = ["kernels.cuh", "sweep_kernel.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp", "adjoint.cuh",
-           "adjoint_kernel.cuh", "accel.cuh", "vecpot.cuh"]
+           "adjoint_kernel.cuh", "accel.cuh", "vecpot.cuh", "sweep_x2.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

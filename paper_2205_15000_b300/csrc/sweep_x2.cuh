@@ -1,0 +1,399 @@
+// The FP32 closed-form Matsubara sweep on packed pairs of energies.  Every lane
+// applies the same arithmetic to its EPT energies, so energies (2k, 2k+1) of a
+// lane travel as one float2 through the step and the propagator sums with
+// sm_100's two-wide FP32 instructions (fma/mul/add .f32x2): one issue slot per
+// two lane-operations, which is what bounds the scalar kernel.  The transcendental
+// unit instructions stay per energy; an odd EPT keeps its last energy scalar.
+//
+// Arithmetic is that of step_coef / step_apply (App. C closed-form step) and of
+// the propagator sums of the scalar sweep, rearranged for the packed form:
+//   * for Matsubara energies z = zr + i eps with zr = +-a shared by the lane's
+//     energies, Re Omega^2 = (|Delta|^2 - zr^2) + eps^2 and Im Omega^2 = -2 zr eps;
+//   * u = |Omega^2| + |Re Omega^2| = 2 s^2 and one rsqrt of u give sqrt(2) s and
+//     sqrt(2) y/(2s); the 1/sqrt(2) is folded into the per-segment constants;
+//   * signs are carried (-Re K, E - 1, -Im 1/D) so that most complex products are
+//     one multiply and one fused multiply-add.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "riccati_step.cuh"
+
+namespace scd {
+
+#ifndef FULL_MASK
+#define FULL_MASK 0xffffffffu
+#endif
+
+typedef float2 f2;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ f2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ f2 pk2(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 rsqrt2(f2 v) { return make_float2(Mth<float>::rsqrt(v.x), Mth<float>::rsqrt(v.y)); }
+__device__ __forceinline__ f2 rcp2(f2 v) { return make_float2(Mth<float>::rcp(v.x), Mth<float>::rcp(v.y)); }
+
+constexpr float kRs2 = 0.70710678118654752f;  // 1/sqrt(2)
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Per-segment constants shared by the lane's energies: Delta = dr + i di,
+// z = zr + i eps, segment length ell.
+struct Seg2 {
+    f2 c0;    // |Delta|^2 - zr^2
+    f2 m2zr;  // -2 zr
+    f2 zr, dr, di, ndr, ndi;
+    f2 el;   // -2 ell log2(e) / sqrt(2): sqrt(2) Re Omega -> log2 |E|
+    f2 ntl;  // -2 ell / sqrt(2): sqrt(2) Im Omega -> arg E
+};
+
+__device__ __forceinline__ Seg2 seg2(float dr, float di, float zr, float ell) {
+    Seg2 s;
+    s.c0 = bc2(dr * dr + di * di - zr * zr);
+    s.m2zr = bc2(-2.f * zr);
+    s.zr = bc2(zr);
+    s.dr = bc2(dr);
+    s.di = bc2(di);
+    s.ndr = bc2(-dr);
+    s.ndi = bc2(-di);
+    s.el = bc2(-2.f * kLog2e * kRs2 * ell);
+    s.ntl = bc2(-2.f * kRs2 * ell);
+    return s;
+}
+
+// gamma_h, E and K of the closed-form step for two energies eps (packed);
+// stored as (gh, E, -Re K, Im K).
+struct Coef2 {
+    f2 ghx, ghy, ex, ey, nkx, ky;
+};
+
+__device__ __forceinline__ void coef2(const Seg2 &s, const f2 eps, Coef2 &c) {
+    const f2 x = fma2(eps, eps, s.c0);        // Re Omega^2
+    const f2 y = mul2(eps, s.m2zr);           // Im Omega^2
+    const f2 n2 = fma2(x, x, mul2(y, y));     // |Omega|^4
+    const f2 rn = rsqrt2(n2);                 // 1/|Omega|^2
+    const f2 r = mul2(n2, rn);                // |Omega|^2
+    const f2 u = add2(r, make_float2(fabsf(x.x), fabsf(x.y)));  // 2 s^2
+    const f2 ru = rsqrt2(u);
+    const f2 sq = mul2(u, ru);                // sqrt(2) s
+    const f2 yq = mul2(y, ru);                // sqrt(2) y / (2 s)
+    // sqrt(2) Omega on the principal branch (Re Omega >= 0)
+    f2 orr, oi;
+    orr.x = x.x >= 0.f ? sq.x : fabsf(yq.x);
+    oi.x = x.x >= 0.f ? yq.x : copysignf(sq.x, y.x);
+    orr.y = x.y >= 0.f ? sq.y : fabsf(yq.y);
+    oi.y = x.y >= 0.f ? yq.y : copysignf(sq.y, y.y);
+    // w = z + i Omega and 1/w = iwr - i iwn
+    const f2 wr = fma2(oi, bc2(-kRs2), s.zr);
+    const f2 wi = fma2(orr, bc2(kRs2), eps);
+    const f2 rw = rcp2(fma2(wr, wr, mul2(wi, wi)));
+    const f2 iwr = mul2(wr, rw), iwn = mul2(wi, rw);
+    // 1/(2 Omega) = conj(Omega) / (2 |Omega|^2) = i2r - i i2n
+    const f2 t = mul2(rn, bc2(0.5f * kRs2));
+    const f2 i2r = mul2(orr, t), i2n = mul2(oi, t);
+    // gamma_h = -Delta / w
+    c.ghx = fma2(s.ndr, iwr, mul2(s.ndi, iwn));
+    c.ghy = fma2(s.dr, iwn, mul2(s.ndi, iwr));
+    // E = exp(-2 ell Omega) = eu (cos th + i sin th), th = -2 ell Im Omega
+    const f2 la = mul2(orr, s.el), th = mul2(oi, s.ntl);
+    const f2 eu = make_float2(ex2_approx(la.x), ex2_approx(la.y));
+    f2 sn, cs;
+    Mth<float>::sincos_(th.x, &sn.x, &cs.x);
+    Mth<float>::sincos_(th.y, &sn.y, &cs.y);
+    c.ex = mul2(eu, cs);
+    c.ey = mul2(eu, sn);
+    // (1 - E)/(2 Omega) = ccr + i cci with E - 1 = nomr + i ey
+    const f2 nomr = fma2(eu, cs, bc2(-1.f));
+    const f2 nccr = fma2(nomr, i2r, mul2(c.ey, i2n));      // -ccr
+    const f2 cci = fma2(nomr, i2n, mul2(neg2(c.ey), i2r));
+    // K = i conj(Delta) (1 - E)/(2 Omega)
+    c.nkx = fma2(s.di, nccr, mul2(s.dr, cci));             // -Re K
+    c.ky = fma2(s.ndr, nccr, mul2(s.di, cci));             // Im K
+}
+
+// gamma' = gamma_h + (gamma - gamma_h) E / (1 - K (gamma - gamma_h))
+__device__ __forceinline__ void apply2(const Coef2 &c, f2 &gx, f2 &gy) {
+    const f2 dx = sub2(gx, c.ghx), dy = sub2(gy, c.ghy);
+    const f2 nr = fma2(dx, c.ex, mul2(neg2(dy), c.ey));
+    const f2 ni = fma2(dx, c.ey, mul2(dy, c.ex));
+    const f2 dnr = fma2(c.nkx, dx, fma2(c.ky, dy, bc2(1.f)));
+    const f2 dni = fma2(c.nkx, dy, mul2(neg2(c.ky), dx));
+    const f2 rd = rcp2(fma2(dnr, dnr, mul2(dni, dni)));
+    gx = fma2(fma2(nr, dnr, mul2(ni, dni)), rd, c.ghx);
+    gy = fma2(fma2(ni, dnr, mul2(neg2(nr), dni)), rd, c.ghy);
+}
+
+// Propagator of angle p at one sample for two energies, from gamma = ga (parked,
+// forward) and gamma~ = conj(gb) (backward), added with weights m into the
+// packed sums: sfr, sfi (Re/Im of sum f + conj f~ up to -2 i pi), nsg (minus the
+// sum of Im 1/D), sFr, sFi (sum of ga + gb).
+struct Sums2 {
+    f2 sfr, sfi, nsg, sFr, sFi;
+};
+
+__device__ __forceinline__ void prop2(const f2 gax, const f2 gay, const f2 gbx, const f2 gby, const f2 m,
+                                      Sums2 &S) {
+    const f2 Dr = fma2(gax, gbx, fma2(gay, gby, bc2(1.f)));   // 1 + ga conj(gb)
+    const f2 Di = fma2(gay, gbx, mul2(neg2(gax), gby));
+    const f2 rD = rcp2(fma2(Dr, Dr, mul2(Di, Di)));
+    const f2 ir = mul2(Dr, rD), nii = mul2(Di, rD);           // 1/D = ir - i nii
+    const f2 Sx = add2(gax, gbx), Sy = add2(gay, gby);
+    const f2 Qy = sub2(gay, gby), Px = sub2(gbx, gax);
+    S.sfr = fma2(m, fma2(Sx, ir, mul2(Qy, nii)), S.sfr);
+    S.sfi = fma2(m, fma2(Sy, ir, mul2(Px, nii)), S.sfi);
+    S.nsg = fma2(m, nii, S.nsg);
+    S.sFr = fma2(m, Sx, S.sFr);
+    S.sFi = fma2(m, Sy, S.sFi);
+}
+
+// One work item of the packed sweep (see sweep_item for the layout of lines,
+// lanes and items).  The warp's slab holds, per sample, the NP parked pairs of
+// every lane as float4 (gx of the pair, gy of the pair) at [k][lane], then the
+// scalar tail energy of every lane.
+template <int EPT, bool WGT, bool BLK>
+__device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
+                                              Cx<float> *const warp_slab, const int lane) {
+    typedef Cx<float> C;
+    constexpr int NP = EPT / 2;
+    constexpr bool TAIL = (EPT & 1) != 0;
+    const int Lw = gs.lanes, G = gs.lines_per_warp;
+    const int gi = lane / Lw, r = lane - gi * Lw;
+    const float4 *__restrict__ img = (const float4 *)gs.image_in;
+    const C *__restrict__ exit_prev = (const C *)gs.exits[a.parity];
+    C *__restrict__ exit_cur = (C *)gs.exits[a.parity ^ 1];
+    C *slab = warp_slab + (int64_t)gi * gs.max_ns * gs.ne_pad;
+    const float h = (float)gs.h;
+    const int n_e = gs.n_e;
+    const int ne_pad = gs.ne_pad;
+    const int nb = BLK ? gs.n_blocks : 1;
+    const int grp = BLK ? it.y / nb : it.y;
+    const int e0 = BLK ? (it.y - grp * nb) * ne_pad : 0;
+
+    // the lane's energies eps_n (Matsubara t (n + 1/2), or Ozaki's poles) and the
+    // weights of their sums (0 for padded lane slots)
+    float zi[EPT], wv[EPT];
+    int nid[EPT];
+    bool ev[EPT];
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const int n = e0 + r + Lw * e;
+        ev[e] = n < n_e;
+        const int nn = ev[e] ? n : n_e - 1;
+        nid[e] = nn;
+        zi[e] = WGT ? (float)gs.mats_eps[nn] : (float)(gs.t * (nn + 0.5));
+        wv[e] = ev[e] ? (WGT ? (float)gs.mats_w[nn] : 1.f) : 0.f;
+    }
+    f2 Z[NP > 0 ? NP : 1], M[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        Z[k] = pk2(zi[2 * k], zi[2 * k + 1]);
+        M[k] = pk2(wv[2 * k], wv[2 * k + 1]);
+    }
+    const int L = gs.groups[(int64_t)grp * G + gi];
+    const bool lv = L >= 0;
+    const LineDev &ln = gs.lines[lv ? L : 0];
+    const int ns = lv ? ln.ns : 0;
+    const int nsl = ns > 0 ? ns : 1;
+    const int nsteps = lv ? ns + 1 : 0;
+    int nmax = nsteps;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) nmax = max(nmax, __shfl_xor_sync(FULL_MASK, nmax, off));
+    const float lead = (float)ln.lead, tail = (float)ln.tail;
+    const int slot0 = ln.slot0;
+    const float4 *li = img + slot0;
+    const int tail_off = 2 * NP * Lw + r;  // the tail energy's place in a sample's slab row
+
+    // entry values: the previous sweep's exits (4 taps) or gamma_h at the first sample
+    f2 GX[NP > 0 ? NP : 1], GY[NP > 0 ? NP : 1];
+    C gt{0.f, 0.f};
+    auto entry = [&](const int *taps, const double *w, float dr, float di, float zr, float ell) {
+        if (a.first_sweep) {
+            const Seg2 s = seg2(dr, di, zr, ell);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                Coef2 c;
+                coef2(s, Z[k], c);
+                GX[k] = c.ghx;
+                GY[k] = c.ghy;
+            }
+            if constexpr (TAIL) {
+                StepCoef<float> c;
+                step_coef<float>(dr, di, dr * dr + di * di, zr, zi[EPT - 1], ell, c);
+                gt = c.gh;
+            }
+        } else {
+            float gx[EPT], gy[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                float sx = 0.f, sy = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const C v = exit_prev[(int64_t)taps[q] * n_e + nid[e]];
+                    const float wq = (float)w[q];
+                    sx += wq * v.x;
+                    sy += wq * v.y;
+                }
+                gx[e] = sx;
+                gy[e] = sy;
+            }
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                GX[k] = pk2(gx[2 * k], gx[2 * k + 1]);
+                GY[k] = pk2(gy[2 * k], gy[2 * k + 1]);
+            }
+            if constexpr (TAIL) gt = C{gx[EPT - 1], gy[EPT - 1]};
+        }
+    };
+    auto exits = [&](int line) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            if (ev[2 * k]) exit_cur[(int64_t)line * n_e + nid[2 * k]] = C{GX[k].x, GY[k].x};
+            if (ev[2 * k + 1]) exit_cur[(int64_t)line * n_e + nid[2 * k + 1]] = C{GX[k].y, GY[k].y};
+        }
+        if constexpr (TAIL)
+            if (ev[EPT - 1]) exit_cur[(int64_t)line * n_e + nid[EPT - 1]] = gt;
+    };
+
+    // ---------------- forward: angle p, along +e_par ----------------
+    float4 sp = li[0];
+    entry(ln.tap_f, ln.w_f, sp.x, sp.y, sp.z, lead);
+    float4 sq = sp;
+    float4 sn = li[min(1, nsl - 1)];
+    for (int i = 0; i < nsteps; ++i) {
+        const float dr = 0.5f * (sp.x + sq.x), di = 0.5f * (sp.y + sq.y);
+        const float av = 0.5f * (sp.z + sq.z);
+        const float ell = (i == 0) ? lead : (i == ns ? tail : h);
+        const Seg2 s = seg2(dr, di, av, ell);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            Coef2 c;
+            coef2(s, Z[k], c);
+            apply2(c, GX[k], GY[k]);
+        }
+        if constexpr (TAIL) {
+            StepCoef<float> c;
+            step_coef<float>(dr, di, dr * dr + di * di, av, zi[EPT - 1], ell, c);
+            step_apply<float>(c, gt);
+        }
+        if (i < ns) {
+            C *row = slab + (int64_t)i * ne_pad;
+            float4 *row4 = (float4 *)row;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) row4[k * Lw + r] = make_float4(GX[k].x, GX[k].y, GY[k].x, GY[k].y);
+            if constexpr (TAIL) row[tail_off] = gt;
+        }
+        sp = sq;
+        sq = sn;
+        sn = li[min(i + 2, nsl - 1)];
+    }
+    if (lv) exits(ln.exit_f);
+
+    __syncwarp();
+
+    // ---------------- backward: angle p + P, along -e_par ----------------
+    float4 sh = li[nsl - 1];
+    entry(ln.tap_b, ln.w_b, sh.x, sh.y, -sh.z, tail);
+    float4 slo = sh;
+    float4 snb = li[max(nsl - 2, 0)];
+    for (int j = 0; j < nmax; ++j) {
+        const bool act = j < nsteps;
+        const int qs = nsl - 1 - j;
+        const bool comb = act && j < ns;
+        float4 pf[NP > 0 ? NP : 1];
+        C gft{0.f, 0.f};
+        if (comb) {
+            const C *row = slab + (int64_t)qs * ne_pad;
+            const float4 *row4 = (const float4 *)row;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) pf[k] = row4[k * Lw + r];
+            if constexpr (TAIL) gft = row[tail_off];
+        }
+        if (act) {
+            const float dr = 0.5f * (sh.x + slo.x), di = 0.5f * (sh.y + slo.y);
+            const float av = 0.5f * (sh.z + slo.z);
+            const float ell = (j == 0) ? tail : (j == ns ? lead : h);
+            const Seg2 s = seg2(dr, di, -av, ell);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                Coef2 c;
+                coef2(s, Z[k], c);
+                apply2(c, GX[k], GY[k]);
+            }
+            if constexpr (TAIL) {
+                StepCoef<float> c;
+                step_coef<float>(dr, di, dr * dr + di * di, -av, zi[EPT - 1], ell, c);
+                step_apply<float>(c, gt);
+            }
+        }
+        float sfr = 0.f, sfi = 0.f, sg = 0.f, sFr = 0.f, sFi = 0.f;
+        if (comb) {
+            Sums2 S{bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                prop2(make_float2(pf[k].x, pf[k].y), make_float2(pf[k].z, pf[k].w), GX[k], GY[k], M[k], S);
+            sfr = S.sfr.x + S.sfr.y;
+            sfi = S.sfi.x + S.sfi.y;
+            sg = -(S.nsg.x + S.nsg.y);
+            sFr = S.sFr.x + S.sFr.y;
+            sFi = S.sFi.x + S.sFi.y;
+            if constexpr (TAIL) {
+                const C gb = gt, ga = gft;
+                const float w = wv[EPT - 1];
+                const float Dr = 1.f + (ga.x * gb.x + ga.y * gb.y);
+                const float Di = ga.y * gb.x - ga.x * gb.y;
+                const float rD = Mth<float>::rcp(Dr * Dr + Di * Di);
+                const float ir = Dr * rD, ii = -Di * rD;
+                sg += w * ii;
+                sfr += w * ((ga.x + gb.x) * ir + (gb.y - ga.y) * ii);
+                sfi += w * ((ga.y + gb.y) * ir + (ga.x - gb.x) * ii);
+                sFr += w * (ga.x + gb.x);
+                sFi += w * (ga.y + gb.y);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            if (off >= Lw) continue;
+            sfr += __shfl_xor_sync(FULL_MASK, sfr, off);
+            sfi += __shfl_xor_sync(FULL_MASK, sfi, off);
+            sg += __shfl_xor_sync(FULL_MASK, sg, off);
+            sFr += __shfl_xor_sync(FULL_MASK, sFr, off);
+            sFi += __shfl_xor_sync(FULL_MASK, sFi, off);
+        }
+        if (comb && r == 0) {
+            const float twopi = 6.283185307179586f, fourpi = 12.566370614359172f;
+            float4 o;
+            o.x = twopi * sfi;                          // Re Sf
+            o.y = -twopi * sfr;                         // Im Sf
+            o.z = fourpi * sg;                          // Sg
+            o.w = 2.f * (slo.x * sFi - slo.y * sFr);    // SF
+            float4 *po = (float4 *)gs.image_out + slot0 + qs;
+            if constexpr (BLK) {
+                atomicAdd(&po->x, o.x);
+                atomicAdd(&po->y, o.y);
+                atomicAdd(&po->z, o.z);
+                atomicAdd(&po->w, o.w);
+            } else {
+                *po = o;
+            }
+        }
+        if (act) {
+            sh = slo;
+            slo = snb;
+            snb = li[max(nsl - 3 - j, 0)];
+        }
+    }
+    if (lv) exits(ln.exit_b);
+    __syncwarp();
+}
+
+}  // namespace scd
