@@ -22,6 +22,7 @@ struct AdjointLaunch {
     int32_t retarded;          // LDOS mode: wimg holds n_e weights per slot
     int32_t grid_blocks, block_threads;
     int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
+    int32_t blocked;           // the grain's energies are split into blocks (items carry the block)
 };
 
 cudaError_t launch_adjoint_sweep(bool fp64, const AdjointLaunch &a, cudaStream_t s);

@@ -50,7 +50,9 @@ __device__ __forceinline__ T line_sum(T v, int Lw) {
 #define SC_ADJOINT_MIN_BLOCKS 4  // FP32: 4 blocks of 128 threads per SM (at most 128 registers)
 #endif
 
-template <typename T, int EPT, bool RET, int STEP>
+// BLK: the grain's energies are split into blocks; each item carries its block and
+// the lane's energies are set up per item (once per launch otherwise).
+template <typename T, int EPT, bool RET, int STEP, bool BLK = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 1) adjoint_sweep_kernel(AdjointLaunch a) {
     // parked per (sample, energy): 0 = gamma then beta, 1 = local beta cotangent,
     // 2 (retarded) = gamma cotangent handed to the mirror energy's lane
@@ -76,18 +78,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
     int nid[EPT], mir[EPT];
     bool ev[EPT];
     const T *__restrict__ wl = (const T *)a.wimg;  // retarded: n_e weights per slot
-    const int nb = gs.n_blocks;
-
-    for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1);
-        item = __shfl_sync(FULLM, item, 0);
-        if (item >= a.n_items) break;
-        const int2 it = a.items[item];
-        // line group and energy block of this item (one block unless the energies
-        // exceed one lane layout)
-        const int grp = nb > 1 ? it.y / nb : it.y;
-        const int e0 = nb > 1 ? (it.y - grp * nb) * ne_pad : 0;
+    const int nb = BLK ? gs.n_blocks : 1;
+    // the lane's energies from energy e0 on
+    auto energies = [&](int e0) {
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int n = e0 + r + Lw * e;
@@ -103,6 +96,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
                 mir[e] = nid[e];
             }
         }
+    };
+    if constexpr (!BLK) energies(0);
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(a.counter, 1);
+        item = __shfl_sync(FULLM, item, 0);
+        if (item >= a.n_items) break;
+        const int2 it = a.items[item];
+        // line group and energy block of this item (one block unless the energies
+        // exceed one lane layout)
+        const int grp = BLK ? it.y / nb : it.y;
+        if constexpr (BLK) energies((it.y - grp * nb) * ne_pad);
         const int L = gs.groups[(int64_t)grp * G + gi];
         const bool lv = L >= 0;
         const LineDev &ln = gs.lines[lv ? L : 0];
@@ -412,12 +418,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
     }
 }
 
-template <typename T, bool RET, int STEP>
+template <typename T, bool RET, int STEP, bool BLK = false>
 static cudaError_t adjoint_dispatch(const AdjointLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: adjoint_sweep_kernel<T, E, RET, STEP><<<grid, block, 0, st>>>(a); break;
+    case E: adjoint_sweep_kernel<T, E, RET, STEP, BLK><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
@@ -427,10 +433,14 @@ static cudaError_t adjoint_dispatch(const AdjointLaunch &a, cudaStream_t st) {
 
 template <typename T>
 static cudaError_t adjoint_launch_t(const AdjointLaunch &a, cudaStream_t st) {
-    if (a.stepper == 1)
-        return a.retarded ? adjoint_dispatch<T, true, 1>(a, st) : adjoint_dispatch<T, false, 1>(a, st);
+    if (a.retarded && a.blocked) return cudaErrorInvalidValue;  // the LDOS keeps one energy block
+    if (a.stepper == 1) {
+        if (a.retarded) return adjoint_dispatch<T, true, 1>(a, st);
+        return a.blocked ? adjoint_dispatch<T, false, 1, true>(a, st) : adjoint_dispatch<T, false, 1>(a, st);
+    }
     if (a.stepper != 0) return cudaErrorInvalidValue;
-    return a.retarded ? adjoint_dispatch<T, true, 0>(a, st) : adjoint_dispatch<T, false, 0>(a, st);
+    if (a.retarded) return adjoint_dispatch<T, true, 0>(a, st);
+    return a.blocked ? adjoint_dispatch<T, false, 0, true>(a, st) : adjoint_dispatch<T, false, 0>(a, st);
 }
 
 // blocks per SM of the retarded instantiation (the larger one) bound both

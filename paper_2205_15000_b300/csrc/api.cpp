@@ -1264,6 +1264,7 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     a.energies_per_lane = pl.ept;
     a.retarded = 0;
     a.stepper = ctx->stepper;
+    a.blocked = pl.n_blocks > 1 ? 1 : 0;
     a.grid_blocks = blocks;
     a.block_threads = 128;
     if (ctx->timing) CK(cudaEventRecord(ctx->ev_adj[0], st));
