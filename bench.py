@@ -41,9 +41,9 @@ WORKLOAD = "c2_diamond_dx2y2_256sq_128ang_80eps"
 # the energies and not counted; MUFU operations counted separately (15)
 ALG_FP32_OPS_PER_PSE = 2 * (34 + 18) + 21
 ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
-# the implicit midpoint stepper: a quadratic per step (47 FP32 ops, 3 MUFU) with the
-# same propagator evaluation
-ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 47 + 21}
+# the implicit midpoint stepper: a quadratic per step (41 FP32 ops, 3 MUFU; ell zr
+# shared by the energies) with the same propagator evaluation
+ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 41 + 21}
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
 # FP64 pipe: ncu reports sm__inst_executed_pipe_fp64 peak 0.0625 warp instructions

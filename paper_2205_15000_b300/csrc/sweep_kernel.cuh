@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLO
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
-        if constexpr (sizeof(T) == 4 && STEP == 0 && !RET)  // FP32 closed form: packed energy pairs
-            sweep_item_x2<EPT, WGT, BLK>(a, it, a.grains[it.x], (Cx<float> *)warp_slab, lane);
+        if constexpr (sizeof(T) == 4)  // FP32: packed energy pairs
+            sweep_item_x2<EPT, RET, STEP, WGT, BLK>(a, it, a.grains[it.x], (Cx<float> *)warp_slab, lane);
         else
             sweep_item<T, EPT, RET, STEP, WGT, BLK>(a, it, a.grains[it.x], warp_slab, lane);
     }

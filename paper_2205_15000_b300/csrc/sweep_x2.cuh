@@ -47,21 +47,29 @@ __device__ __forceinline__ f2 rcp2(f2 v) { return make_float2(Mth<float>::rcp(v.
 constexpr float kRs2 = 0.70710678118654752f;  // 1/sqrt(2)
 constexpr float kLog2e = 1.4426950408889634f;
 
-// Per-segment constants shared by the lane's energies: Delta = dr + i di,
-// z = zr + i eps, segment length ell.
+// Per-segment constants shared by the lane's energies: Delta = dr + i di, the
+// segment length ell, and the part of z = zr + i zi that all energies share --
+// the Doppler shift zr = +-a for Matsubara energies (zi = eps_n per energy), the
+// broadening zi for the retarded sweep (zr = E_n +- a per energy).
 struct Seg2 {
-    f2 c0;    // |Delta|^2 - zr^2
-    f2 m2zr;  // -2 zr
-    f2 zr, dr, di, ndr, ndi;
+    f2 c0;    // Matsubara: |Delta|^2 - zr^2; retarded: |Delta|^2 + zi^2
+    f2 m2;    // Matsubara: -2 zr; retarded: -2 zi
+    f2 zs;    // Matsubara: zr; retarded: zi
+    f2 sh;    // retarded: the Doppler shift added to each energy
+    f2 dr, di, ndr, ndi;
     f2 el;   // -2 ell log2(e) / sqrt(2): sqrt(2) Re Omega -> log2 |E|
     f2 ntl;  // -2 ell / sqrt(2): sqrt(2) Im Omega -> arg E
 };
 
-__device__ __forceinline__ Seg2 seg2(float dr, float di, float zr, float ell) {
+template <bool RET>
+__device__ __forceinline__ Seg2 seg2(float dr, float di, float shift, float broad, float ell) {
     Seg2 s;
-    s.c0 = bc2(dr * dr + di * di - zr * zr);
-    s.m2zr = bc2(-2.f * zr);
-    s.zr = bc2(zr);
+    const float d2 = dr * dr + di * di;
+    const float zs = RET ? broad : shift;
+    s.c0 = bc2(RET ? d2 + zs * zs : d2 - zs * zs);
+    s.m2 = bc2(-2.f * zs);
+    s.zs = bc2(zs);
+    s.sh = bc2(shift);
     s.dr = bc2(dr);
     s.di = bc2(di);
     s.ndr = bc2(-dr);
@@ -71,15 +79,15 @@ __device__ __forceinline__ Seg2 seg2(float dr, float di, float zr, float ell) {
     return s;
 }
 
-// gamma_h, E and K of the closed-form step for two energies eps (packed);
+// gamma_h, E and K of the closed-form step for two energies (packed);
 // stored as (gh, E, -Re K, Im K).
 struct Coef2 {
     f2 ghx, ghy, ex, ey, nkx, ky;
 };
 
-__device__ __forceinline__ void coef2(const Seg2 &s, const f2 eps, Coef2 &c) {
-    const f2 x = fma2(eps, eps, s.c0);        // Re Omega^2
-    const f2 y = mul2(eps, s.m2zr);           // Im Omega^2
+// from Omega^2 = x + i y and z = zr + i zi
+__device__ __forceinline__ void coef2_core(const Seg2 &s, const f2 x, const f2 y, const f2 zr, const f2 zi,
+                                           Coef2 &c) {
     const f2 n2 = fma2(x, x, mul2(y, y));     // |Omega|^4
     const f2 rn = rsqrt2(n2);                 // 1/|Omega|^2
     const f2 r = mul2(n2, rn);                // |Omega|^2
@@ -94,8 +102,8 @@ __device__ __forceinline__ void coef2(const Seg2 &s, const f2 eps, Coef2 &c) {
     orr.y = x.y >= 0.f ? sq.y : fabsf(yq.y);
     oi.y = x.y >= 0.f ? yq.y : copysignf(sq.y, y.y);
     // w = z + i Omega and 1/w = iwr - i iwn
-    const f2 wr = fma2(oi, bc2(-kRs2), s.zr);
-    const f2 wi = fma2(orr, bc2(kRs2), eps);
+    const f2 wr = fma2(oi, bc2(-kRs2), zr);
+    const f2 wi = fma2(orr, bc2(kRs2), zi);
     const f2 rw = rcp2(fma2(wr, wr, mul2(wi, wi)));
     const f2 iwr = mul2(wr, rw), iwn = mul2(wi, rw);
     // 1/(2 Omega) = conj(Omega) / (2 |Omega|^2) = i2r - i i2n
@@ -119,6 +127,17 @@ __device__ __forceinline__ void coef2(const Seg2 &s, const f2 eps, Coef2 &c) {
     // K = i conj(Delta) (1 - E)/(2 Omega)
     c.nkx = fma2(s.di, nccr, mul2(s.dr, cci));             // -Re K
     c.ky = fma2(s.ndr, nccr, mul2(s.di, cci));             // Im K
+}
+
+// q: the energies' own part of z (Matsubara: eps_n; retarded: E_n)
+template <bool RET>
+__device__ __forceinline__ void coef2(const Seg2 &s, const f2 q, Coef2 &c) {
+    if constexpr (RET) {
+        const f2 zr = add2(q, s.sh);
+        coef2_core(s, fma2(neg2(zr), zr, s.c0), mul2(zr, s.m2), zr, s.zs, c);
+    } else {
+        coef2_core(s, fma2(q, q, s.c0), mul2(q, s.m2), s.zs, q, c);
+    }
 }
 
 // gamma' = gamma_h + (gamma - gamma_h) E / (1 - K (gamma - gamma_h))
@@ -156,15 +175,71 @@ __device__ __forceinline__ void prop2(const f2 gax, const f2 gay, const f2 gbx, 
     S.sFi = fma2(m, Sy, S.sFi);
 }
 
+// Implicit midpoint rule (App. C) for two energies: the root g1 of
+// c2 g1^2 + c1 g1 + c0 = 0 continuous in Delta, g1 = 2 c0 / (sqrt(c1^2 - 4 c2 c0) - c1),
+// with c2 = i ell Delta*/4, c1 = 2 c2 g0 + i ell z - 1, c0 = (c2 g0 + i ell z + 1) g0
+// + i ell Delta (the arithmetic of midpoint_step, packed).
+struct Mid2 {
+    f2 c2x, c2y, ildx, ildy, ell, nell;
+};
+
+__device__ __forceinline__ Mid2 mid2(float dr, float di, float ell) {
+    const float q = 0.25f * ell;
+    Mid2 m;
+    m.c2x = bc2(q * di);
+    m.c2y = bc2(q * dr);
+    m.ildx = bc2(-ell * di);
+    m.ildy = bc2(ell * dr);
+    m.ell = bc2(ell);
+    m.nell = bc2(-ell);
+    return m;
+}
+
+__device__ __forceinline__ void midpoint2(const Mid2 &m, const f2 zr, const f2 zi, f2 &gx, f2 &gy) {
+    const f2 c2gx = fma2(m.c2x, gx, mul2(neg2(m.c2y), gy));
+    const f2 c2gy = fma2(m.c2x, gy, mul2(m.c2y, gx));
+    const f2 lzr = mul2(m.ell, zr);
+    const f2 c1x = fma2(bc2(2.f), c2gx, fma2(m.nell, zi, bc2(-1.f)));
+    const f2 c1y = fma2(bc2(2.f), c2gy, lzr);
+    const f2 ux = add2(c2gx, fma2(m.nell, zi, bc2(1.f)));
+    const f2 uy = add2(c2gy, lzr);
+    const f2 c0x = fma2(ux, gx, fma2(neg2(uy), gy, m.ildx));
+    const f2 c0y = fma2(ux, gy, fma2(uy, gx, m.ildy));
+    const f2 ccx = fma2(m.c2x, c0x, mul2(neg2(m.c2y), c0y));
+    const f2 ccy = fma2(m.c2x, c0y, mul2(m.c2y, c0x));
+    const f2 dx = fma2(c1x, c1x, fma2(neg2(c1y), c1y, mul2(bc2(-4.f), ccx)));
+    const f2 dy = fma2(add2(c1x, c1x), c1y, mul2(bc2(-4.f), ccy));
+    // sqrt(2) times the principal square root of dx + i dy
+    const f2 n2 = fma2(dx, dx, mul2(dy, dy));
+    const f2 r = mul2(n2, rsqrt2(n2));
+    const f2 u = add2(r, make_float2(fabsf(dx.x), fabsf(dx.y)));
+    const f2 ru = rsqrt2(u);
+    const f2 sq = mul2(u, ru), yq = mul2(dy, ru);
+    f2 sr, si;
+    sr.x = dx.x >= 0.f ? sq.x : fabsf(yq.x);
+    si.x = dx.x >= 0.f ? yq.x : copysignf(sq.x, dy.x);
+    sr.y = dx.y >= 0.f ? sq.y : fabsf(yq.y);
+    si.y = dx.y >= 0.f ? yq.y : copysignf(sq.y, dy.y);
+    // g1 = 2 c0 / den, den = sqrt - c1; 2/den = idx - i idn
+    const f2 denx = fma2(sr, bc2(kRs2), neg2(c1x)), deny = fma2(si, bc2(kRs2), neg2(c1y));
+    const f2 rd = rcp2(mul2(bc2(0.5f), fma2(denx, denx, mul2(deny, deny))));
+    const f2 idx = mul2(denx, rd), idn = mul2(deny, rd);
+    gx = fma2(c0x, idx, mul2(c0y, idn));
+    gy = fma2(c0y, idx, mul2(neg2(c0x), idn));
+}
+
 // One work item of the packed sweep (see sweep_item for the layout of lines,
 // lanes and items).  The warp's slab holds, per sample, the NP parked pairs of
 // every lane as float4 (gx of the pair, gy of the pair) at [k][lane], then the
-// scalar tail energy of every lane.
-template <int EPT, bool WGT, bool BLK>
+// scalar tail energy of every lane.  STEP 0 = closed-form step, 1 = implicit
+// midpoint rule; RET: retarded sweep (LDOS) whose backward pass combines each
+// energy with the parked gamma of the mirror energy.
+template <int EPT, bool RET, int STEP, bool WGT, bool BLK>
 __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
                                               Cx<float> *const warp_slab, const int lane) {
     typedef Cx<float> C;
     constexpr int NP = EPT / 2;
+    constexpr int NPA = NP > 0 ? NP : 1;
     constexpr bool TAIL = (EPT & 1) != 0;
     const int Lw = gs.lanes, G = gs.lines_per_warp;
     const int gi = lane / Lw, r = lane - gi * Lw;
@@ -178,27 +253,41 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
     const int nb = BLK ? gs.n_blocks : 1;
     const int grp = BLK ? it.y / nb : it.y;
     const int e0 = BLK ? (it.y - grp * nb) * ne_pad : 0;
+    const float broad = RET ? (float)gs.broadening : 0.f;
 
-    // the lane's energies eps_n (Matsubara t (n + 1/2), or Ozaki's poles) and the
-    // weights of their sums (0 for padded lane slots)
-    float zi[EPT], wv[EPT];
+    // the lane's energies: Matsubara t (n + 1/2) or Ozaki's poles with the weights
+    // of their sums (0 for padded lane slots); retarded: the real energies E_n and,
+    // per energy, the float offset of the mirror energy's parked gamma in a slab row
+    float zq[EPT], wv[EPT];
     int nid[EPT];
     bool ev[EPT];
+    int mo[RET ? EPT : 1];
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int n = e0 + r + Lw * e;
         ev[e] = n < n_e;
         const int nn = ev[e] ? n : n_e - 1;
         nid[e] = nn;
-        zi[e] = WGT ? (float)gs.mats_eps[nn] : (float)(gs.t * (nn + 0.5));
-        wv[e] = ev[e] ? (WGT ? (float)gs.mats_w[nn] : 1.f) : 0.f;
+        if constexpr (RET) {
+            zq[e] = (float)gs.energies[nn];
+            wv[e] = 0.f;
+            const int nm = n_e - 1 - nn, em = nm / Lw, rm = nm - em * Lw;
+            mo[e] = em < 2 * NP ? 4 * ((em >> 1) * Lw + rm) + (em & 1) : 2 * (2 * NP * Lw + rm);
+        } else {
+            zq[e] = WGT ? (float)gs.mats_eps[nn] : (float)(gs.t * (nn + 0.5));
+            wv[e] = ev[e] ? (WGT ? (float)gs.mats_w[nn] : 1.f) : 0.f;
+        }
     }
-    f2 Z[NP > 0 ? NP : 1], M[NP > 0 ? NP : 1];
+    f2 Q[NPA], M[NPA];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        Z[k] = pk2(zi[2 * k], zi[2 * k + 1]);
+        Q[k] = pk2(zq[2 * k], zq[2 * k + 1]);
         M[k] = pk2(wv[2 * k], wv[2 * k + 1]);
     }
+    // z of energy e on a segment with Doppler shift sh
+    auto zr_of = [&](int e, float sh) { return RET ? zq[e] + sh : sh; };
+    auto zi_of = [&](int e) { return RET ? broad : zq[e]; };
+
     const int L = gs.groups[(int64_t)grp * G + gi];
     const bool lv = L >= 0;
     const LineDev &ln = gs.lines[lv ? L : 0];
@@ -213,22 +302,45 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
     const float4 *li = img + slot0;
     const int tail_off = 2 * NP * Lw + r;  // the tail energy's place in a sample's slab row
 
-    // entry values: the previous sweep's exits (4 taps) or gamma_h at the first sample
-    f2 GX[NP > 0 ? NP : 1], GY[NP > 0 ? NP : 1];
+    f2 GX[NPA], GY[NPA];
     C gt{0.f, 0.f};
-    auto entry = [&](const int *taps, const double *w, float dr, float di, float zr, float ell) {
-        if (a.first_sweep) {
-            const Seg2 s = seg2(dr, di, zr, ell);
+    // one step of every energy over a segment (Delta = dr + i di, shift sh, length ell)
+    auto step = [&](float dr, float di, float sh, float ell) {
+        if constexpr (STEP == 0) {
+            const Seg2 s = seg2<RET>(dr, di, sh, broad, ell);
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 Coef2 c;
-                coef2(s, Z[k], c);
+                coef2<RET>(s, Q[k], c);
+                apply2(c, GX[k], GY[k]);
+            }
+            if constexpr (TAIL) {
+                StepCoef<float> c;
+                step_coef<float>(dr, di, dr * dr + di * di, zr_of(EPT - 1, sh), zi_of(EPT - 1), ell, c);
+                step_apply<float>(c, gt);
+            }
+        } else {
+            const Mid2 m = mid2(dr, di, ell);
+#pragma unroll
+            for (int k = 0; k < NP; ++k)
+                midpoint2(m, RET ? add2(Q[k], bc2(sh)) : bc2(sh), RET ? bc2(broad) : Q[k], GX[k], GY[k]);
+            if constexpr (TAIL) gt = midpoint_step<float>(mid_seg<float>(dr, di, ell), zr_of(EPT - 1, sh), zi_of(EPT - 1), gt);
+        }
+    };
+    // entry values: the previous sweep's exits (4 taps) or gamma_h at the first sample
+    auto entry = [&](const int *taps, const double *w, float dr, float di, float sh, float ell) {
+        if (a.first_sweep) {
+            const Seg2 s = seg2<RET>(dr, di, sh, broad, ell);
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                Coef2 c;
+                coef2<RET>(s, Q[k], c);
                 GX[k] = c.ghx;
                 GY[k] = c.ghy;
             }
             if constexpr (TAIL) {
                 StepCoef<float> c;
-                step_coef<float>(dr, di, dr * dr + di * di, zr, zi[EPT - 1], ell, c);
+                step_coef<float>(dr, di, dr * dr + di * di, zr_of(EPT - 1, sh), zi_of(EPT - 1), ell, c);
                 gt = c.gh;
             }
         } else {
@@ -273,18 +385,7 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
         const float dr = 0.5f * (sp.x + sq.x), di = 0.5f * (sp.y + sq.y);
         const float av = 0.5f * (sp.z + sq.z);
         const float ell = (i == 0) ? lead : (i == ns ? tail : h);
-        const Seg2 s = seg2(dr, di, av, ell);
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            Coef2 c;
-            coef2(s, Z[k], c);
-            apply2(c, GX[k], GY[k]);
-        }
-        if constexpr (TAIL) {
-            StepCoef<float> c;
-            step_coef<float>(dr, di, dr * dr + di * di, av, zi[EPT - 1], ell, c);
-            step_apply<float>(c, gt);
-        }
+        step(dr, di, av, ell);
         if (i < ns) {
             C *row = slab + (int64_t)i * ne_pad;
             float4 *row4 = (float4 *)row;
@@ -298,7 +399,7 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
     }
     if (lv) exits(ln.exit_f);
 
-    __syncwarp();
+    __syncwarp();  // the retarded pass reads gammas parked by other lanes
 
     // ---------------- backward: angle p + P, along -e_par ----------------
     float4 sh = li[nsl - 1];
@@ -309,81 +410,111 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
         const bool act = j < nsteps;
         const int qs = nsl - 1 - j;
         const bool comb = act && j < ns;
-        float4 pf[NP > 0 ? NP : 1];
+        // parked gammas of the sample reached by this step (angle p): the lane's own
+        // energies, or (retarded) the mirror energies
+        f2 PX[NPA], PY[NPA];
         C gft{0.f, 0.f};
         if (comb) {
             const C *row = slab + (int64_t)qs * ne_pad;
-            const float4 *row4 = (const float4 *)row;
+            if constexpr (RET) {
+                const float *rowf = (const float *)row;
+                float px[EPT], py[EPT];
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pf[k] = row4[k * Lw + r];
-            if constexpr (TAIL) gft = row[tail_off];
+                for (int e = 0; e < EPT; ++e) {
+                    px[e] = rowf[mo[e]];
+                    py[e] = rowf[mo[e] + (mo[e] >= 4 * NP * Lw ? 1 : 2)];
+                }
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    PX[k] = pk2(px[2 * k], px[2 * k + 1]);
+                    PY[k] = pk2(py[2 * k], py[2 * k + 1]);
+                }
+                if constexpr (TAIL) gft = C{px[EPT - 1], py[EPT - 1]};
+            } else {
+                const float4 *row4 = (const float4 *)row;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    const float4 v = row4[k * Lw + r];
+                    PX[k] = make_float2(v.x, v.y);
+                    PY[k] = make_float2(v.z, v.w);
+                }
+                if constexpr (TAIL) gft = row[tail_off];
+            }
         }
         if (act) {
             const float dr = 0.5f * (sh.x + slo.x), di = 0.5f * (sh.y + slo.y);
             const float av = 0.5f * (sh.z + slo.z);
             const float ell = (j == 0) ? tail : (j == ns ? lead : h);
-            const Seg2 s = seg2(dr, di, -av, ell);
+            step(dr, di, -av, ell);
+        }
+        if constexpr (!RET) {
+            float sfr = 0.f, sfi = 0.f, sg = 0.f, sFr = 0.f, sFi = 0.f;
+            if (comb) {
+                Sums2 S{bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
+#pragma unroll
+                for (int k = 0; k < NP; ++k) prop2(PX[k], PY[k], GX[k], GY[k], M[k], S);
+                sfr = S.sfr.x + S.sfr.y;
+                sfi = S.sfi.x + S.sfi.y;
+                sg = -(S.nsg.x + S.nsg.y);
+                sFr = S.sFr.x + S.sFr.y;
+                sFi = S.sFi.x + S.sFi.y;
+                if constexpr (TAIL) {
+                    const C gb = gt, ga = gft;
+                    const float w = wv[EPT - 1];
+                    const float Dr = 1.f + (ga.x * gb.x + ga.y * gb.y);
+                    const float Di = ga.y * gb.x - ga.x * gb.y;
+                    const float rD = Mth<float>::rcp(Dr * Dr + Di * Di);
+                    const float ir = Dr * rD, ii = -Di * rD;
+                    sg += w * ii;
+                    sfr += w * ((ga.x + gb.x) * ir + (gb.y - ga.y) * ii);
+                    sfi += w * ((ga.y + gb.y) * ir + (ga.x - gb.x) * ii);
+                    sFr += w * (ga.x + gb.x);
+                    sFi += w * (ga.y + gb.y);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                if (off >= Lw) continue;
+                sfr += __shfl_xor_sync(FULL_MASK, sfr, off);
+                sfi += __shfl_xor_sync(FULL_MASK, sfi, off);
+                sg += __shfl_xor_sync(FULL_MASK, sg, off);
+                sFr += __shfl_xor_sync(FULL_MASK, sFr, off);
+                sFi += __shfl_xor_sync(FULL_MASK, sFi, off);
+            }
+            if (comb && r == 0) {
+                const float twopi = 6.283185307179586f, fourpi = 12.566370614359172f;
+                float4 o;
+                o.x = twopi * sfi;                          // Re Sf
+                o.y = -twopi * sfr;                         // Im Sf
+                o.z = fourpi * sg;                          // Sg
+                o.w = 2.f * (slo.x * sFi - slo.y * sFr);    // SF
+                float4 *po = (float4 *)gs.image_out + slot0 + qs;
+                if constexpr (BLK) {
+                    atomicAdd(&po->x, o.x);
+                    atomicAdd(&po->y, o.y);
+                    atomicAdd(&po->z, o.z);
+                    atomicAdd(&po->w, o.w);
+                } else {
+                    *po = o;
+                }
+            }
+        } else if (comb) {
+            // LDOS: -Im g / pi = 2 Re(1/D) - 1 with D = 1 + ga conj(gb)
+            float *outl = (float *)gs.image_out + (int64_t)(slot0 + qs) * n_e;
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
-                Coef2 c;
-                coef2(s, Z[k], c);
-                apply2(c, GX[k], GY[k]);
+                const f2 Dr = fma2(PX[k], GX[k], fma2(PY[k], GY[k], bc2(1.f)));
+                const f2 Di = fma2(PY[k], GX[k], mul2(neg2(PX[k]), GY[k]));
+                const f2 v = fma2(mul2(Dr, rcp2(fma2(Dr, Dr, mul2(Di, Di)))), bc2(2.f), bc2(-1.f));
+                if (ev[2 * k]) outl[nid[2 * k]] = v.x;
+                if (ev[2 * k + 1]) outl[nid[2 * k + 1]] = v.y;
             }
-            if constexpr (TAIL) {
-                StepCoef<float> c;
-                step_coef<float>(dr, di, dr * dr + di * di, -av, zi[EPT - 1], ell, c);
-                step_apply<float>(c, gt);
-            }
-        }
-        float sfr = 0.f, sfi = 0.f, sg = 0.f, sFr = 0.f, sFi = 0.f;
-        if (comb) {
-            Sums2 S{bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
-#pragma unroll
-            for (int k = 0; k < NP; ++k)
-                prop2(make_float2(pf[k].x, pf[k].y), make_float2(pf[k].z, pf[k].w), GX[k], GY[k], M[k], S);
-            sfr = S.sfr.x + S.sfr.y;
-            sfi = S.sfi.x + S.sfi.y;
-            sg = -(S.nsg.x + S.nsg.y);
-            sFr = S.sFr.x + S.sFr.y;
-            sFi = S.sFi.x + S.sFi.y;
             if constexpr (TAIL) {
                 const C gb = gt, ga = gft;
-                const float w = wv[EPT - 1];
                 const float Dr = 1.f + (ga.x * gb.x + ga.y * gb.y);
                 const float Di = ga.y * gb.x - ga.x * gb.y;
                 const float rD = Mth<float>::rcp(Dr * Dr + Di * Di);
-                const float ir = Dr * rD, ii = -Di * rD;
-                sg += w * ii;
-                sfr += w * ((ga.x + gb.x) * ir + (gb.y - ga.y) * ii);
-                sfi += w * ((ga.y + gb.y) * ir + (ga.x - gb.x) * ii);
-                sFr += w * (ga.x + gb.x);
-                sFi += w * (ga.y + gb.y);
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            if (off >= Lw) continue;
-            sfr += __shfl_xor_sync(FULL_MASK, sfr, off);
-            sfi += __shfl_xor_sync(FULL_MASK, sfi, off);
-            sg += __shfl_xor_sync(FULL_MASK, sg, off);
-            sFr += __shfl_xor_sync(FULL_MASK, sFr, off);
-            sFi += __shfl_xor_sync(FULL_MASK, sFi, off);
-        }
-        if (comb && r == 0) {
-            const float twopi = 6.283185307179586f, fourpi = 12.566370614359172f;
-            float4 o;
-            o.x = twopi * sfi;                          // Re Sf
-            o.y = -twopi * sfr;                         // Im Sf
-            o.z = fourpi * sg;                          // Sg
-            o.w = 2.f * (slo.x * sFi - slo.y * sFr);    // SF
-            float4 *po = (float4 *)gs.image_out + slot0 + qs;
-            if constexpr (BLK) {
-                atomicAdd(&po->x, o.x);
-                atomicAdd(&po->y, o.y);
-                atomicAdd(&po->z, o.z);
-                atomicAdd(&po->w, o.w);
-            } else {
-                *po = o;
+                if (ev[EPT - 1]) outl[nid[EPT - 1]] = 2.f * Dr * rD - 1.f;
             }
         }
         if (act) {
