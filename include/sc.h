@@ -396,6 +396,13 @@ sc_status sc_debug_exits(sc_ctx *ctx, double *exits);
 /* per-sample energy sums of the last sweep: [pair][sample][4] = (Re Sf, Im Sf,
    Sg, SF) for angle p (angle p + N/2 follows by symmetry) */
 sc_status sc_debug_images(sc_ctx *ctx, double *images);
+/* The FP64 reciprocal and reciprocal square root the sweep uses on the device
+   (Newton-Raphson iteration from the FP32 approximations, about 1 ulp; arguments
+   outside the float range take the IEEE operations), evaluated on n values: x,
+   rcp and rsqrt are device pointers to n doubles (caller-owned); the call waits
+   for the stream.  SC_EINVAL for n < 0 or a null pointer with n > 0, SC_ECUDA
+   for a failed launch (message in sc_last_error(NULL)). */
+sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, void *stream);
 
 /* ---- allocation-free line sweep ---------------------------------------
  * No counterpart in the paper: an engineering entry point for callers that

@@ -1324,6 +1324,21 @@ sc_status sc_debug_links(const sc_ctx *ctx, int32_t *ta, int32_t *tl, int32_t *t
     return SC_OK;
 }
 
+sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, void *stream) {
+    g_create_error.clear();
+    if (n < 0 || (n > 0 && (!x || !rcp || !rsqrt))) {
+        g_create_error = "sc_debug_fp64_math: n < 0 or a null pointer";
+        return SC_EINVAL;
+    }
+    cudaError_t e = scd::launch_fp64_math(x, n, rcp, rsqrt, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        g_create_error = cudaGetErrorString(e);
+        return SC_ECUDA;
+    }
+    return SC_OK;
+}
+
 sc_status sc_debug_chords(const sc_ctx *ctx, int32_t *pair, int32_t *l) {
     if (!ctx) return SC_EINVAL;
     const scg::Geometry &G = ctx->geo;

@@ -100,6 +100,21 @@ __global__ void rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__
     out[s] = o;
 }
 
+__global__ void fp64_math_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ rcp,
+                                 double *__restrict__ rsq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    rcp[i] = Mth<double>::rcp(x[i]);
+    rsq[i] = Mth<double>::rsqrt(x[i]);
+}
+
+cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int bs = 256;
+    fp64_math_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(x, n, rcp, rsqrt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_line, int64_t n_slots,
                           const PairDev *pairs, const GridDev &grid, const int32_t *ghost,
                           const double *delta, const double *aind, void *image_in,

@@ -157,6 +157,8 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
                           const double *delta, const double *aind, void *image_in,
                           cudaStream_t s);
 cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
+// the FP64 device reciprocal and reciprocal square root of the sweep on n values
+cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s);
 // FP32 production path
 cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, const double *aind, float2 *delta_f,
                               float2 *aind_f, cudaStream_t s);

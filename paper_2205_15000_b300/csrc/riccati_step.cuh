@@ -41,15 +41,51 @@ struct Mth<float> {
     }
 };
 
+// FP64 on the device: reciprocal and reciprocal square root by Newton-Raphson
+// iteration from the FP32 unit approximations (relative error below 2^-22):
+//   1/v:       r <- r + r (1 - v r)
+//   1/sqrt(v): y <- y + y (1/2 - (v/2) y^2)
+// each step squares the relative error, so two steps pass double precision
+// (about 1 ulp, not the correctly rounded IEEE result).  Arguments whose FP32
+// approximation is zero, infinite or NaN (outside the float range) take the IEEE
+// operation.  sin and cos share one argument reduction (sincos).  The host keeps
+// the IEEE forms.
 template <>
 struct Mth<double> {
-    static __host__ __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
-    static __host__ __device__ __forceinline__ double rsqrt(double v) { return 1.0 / ::sqrt(v); }
+    static __host__ __device__ __forceinline__ double rcp(double v) {
+#ifdef __CUDA_ARCH__
+        const float s = Mth<float>::rcp((float)v);
+        if (!(fabsf(s) < 3.0e38f) || s == 0.f) return 1.0 / v;
+        double r = (double)s;
+        r = fma(r, fma(-v, r, 1.0), r);
+        r = fma(r, fma(-v, r, 1.0), r);
+        return r;
+#else
+        return 1.0 / v;
+#endif
+    }
+    static __host__ __device__ __forceinline__ double rsqrt(double v) {
+#ifdef __CUDA_ARCH__
+        const float s = Mth<float>::rsqrt((float)v);
+        if (!(s < 3.0e38f) || !(s > 0.f)) return 1.0 / ::sqrt(v);
+        double y = (double)s;
+        const double hv = 0.5 * v;
+        y = fma(y, fma(-hv * y, y, 0.5), y);
+        y = fma(y, fma(-hv * y, y, 0.5), y);
+        return y;
+#else
+        return 1.0 / ::sqrt(v);
+#endif
+    }
     static __host__ __device__ __forceinline__ double sqrt(double v) { return ::sqrt(v); }
     static __host__ __device__ __forceinline__ double expneg(double u) { return ::exp(-u); }
     static __host__ __device__ __forceinline__ void sincos_(double x, double *s, double *c) {
+#ifdef __CUDA_ARCH__
+        ::sincos(x, s, c);
+#else
         *s = ::sin(x);
         *c = ::cos(x);
+#endif
     }
 };
 

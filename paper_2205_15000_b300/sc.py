@@ -109,7 +109,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_get_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
-            "sc_debug_exits", "sc_debug_images", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
+            "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
@@ -146,6 +146,7 @@ def _load():
         "sc_debug_chords": [vp, vp, vp],
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
+        "sc_debug_fp64_math": [vp, i64, vp, vp, vp],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
@@ -342,6 +343,16 @@ def sc_ozaki_poles(n):
 def sc_ozaki_poles_for_cutoff(t, eps_cut):
     """The fewest Ozaki poles whose largest energy reaches eps_cut (0: none)."""
     return int(lib.sc_ozaki_poles_for_cutoff(ctypes.c_double(t), ctypes.c_double(eps_cut)))
+
+
+def sc_debug_fp64_math(x, stream=None):
+    """The sweep's FP64 device reciprocal and reciprocal square root of the
+    device tensor x (float64): returns (1/x, 1/sqrt(x)) as device tensors."""
+    import torch
+    x = x.contiguous()
+    rcp, rsq = torch.empty_like(x), torch.empty_like(x)
+    _check(lib.sc_debug_fp64_math(_ptr(x), x.numel(), _ptr(rcp), _ptr(rsq), _stream(stream)))
+    return rcp, rsq
 
 
 def sc_energy_grid(ctx, n_e):
