@@ -137,19 +137,25 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 
 // one thread per grid point: for every pair, bilinear gather of the four image
 // slots around the point's lattice coordinates and the Fermi-surface sum
+// A block of four warps takes 32 consecutive grid points; warp q sums the 16-pair
+// chunks q, q + 4, q + 8, ... of every point (FP32 within a chunk, FP64 across
+// chunks), so the lanes of a warp gather neighbouring samples of the same pair;
+// warp 0 adds the four partial sums in a fixed order.
 template <int NC>
-__global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
+__global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
                                        const BackLine *__restrict__ bl, GridDev grid,
                                        const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
                                        double *__restrict__ acc) {
+    constexpr int NV = 5 + 2 * NC;
+    __shared__ double part[3][NV][32];
     const int64_t npts = (int64_t)grid.nx * grid.ny;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= npts) return;
-    double A0 = 0, A1 = 0, A2 = 0, A3 = 0, A4 = 0;
-    double Ac[2 * NC] = {};  // <eta_c Sf> of components c >= 1
-    if (mask[idx]) {
+    const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
+    const bool live = idx < npts;
+    double A[NV] = {};  // the point's sums; [5 + 2c], [6 + 2c]: <eta_c Sf> of components c >= 1
+    if (live && mask[idx]) {
         const int64_t i = idx % grid.nx, j = idx / grid.nx;
-        for (int p0 = 0; p0 < n_pairs; p0 += 16) {
+        for (int p0 = 16 * q; p0 < n_pairs; p0 += 64) {
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
             float ac[2 * NC] = {};
             const int pe = min(p0 + 16, n_pairs);
@@ -186,24 +192,32 @@ __global__ void rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_
                     ac[2 * c + 1] += pp.w_eta_c[c] * x1;
                 }
             }
-            A0 += a0;
-            A1 += a1;
-            A2 += a2;
-            A3 += a3;
-            A4 += a4;
+            A[0] += a0;
+            A[1] += a1;
+            A[2] += a2;
+            A[3] += a3;
+            A[4] += a4;
 #pragma unroll
-            for (int c = 2; c < 2 * NC; ++c) Ac[c] += ac[c];
+            for (int c = 2; c < 2 * NC; ++c) A[3 + c] += ac[c];
         }
     }
-    acc[idx] = A0;
-    acc[npts + idx] = A1;
-    acc[2 * npts + idx] = A2;
-    acc[3 * npts + idx] = A3;
-    acc[4 * npts + idx] = A4;
+    if (q > 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) part[q - 1][v][lane] = A[v];
+    }
+    __syncthreads();
+    if (q != 0 || !live) return;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) A[v] = (A[v] + part[0][v][lane]) + (part[1][v][lane] + part[2][v][lane]);
+    acc[idx] = A[0];
+    acc[npts + idx] = A[1];
+    acc[2 * npts + idx] = A[2];
+    acc[3 * npts + idx] = A[3];
+    acc[4 * npts + idx] = A[4];
 #pragma unroll
     for (int c = 1; c < NC; ++c) {
-        acc[(3 + 2 * c) * npts + idx] = Ac[2 * c];
-        acc[(4 + 2 * c) * npts + idx] = Ac[2 * c + 1];
+        acc[(3 + 2 * c) * npts + idx] = A[3 + 2 * c];
+        acc[(4 + 2 * c) * npts + idx] = A[4 + 2 * c];
     }
 }
 
@@ -212,7 +226,7 @@ cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const 
                                    double *acc, cudaStream_t st) {
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int bs = 128;
-    const unsigned nb = (unsigned)((npts + bs - 1) / bs);
+    const unsigned nb = (unsigned)((npts + 31) / 32);  // 32 grid points per block of four warps
     switch (grid.n_comp) {
         case 1: rotate_back_f32_kernel<1><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
         case 2: rotate_back_f32_kernel<2><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
