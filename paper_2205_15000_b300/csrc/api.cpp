@@ -255,11 +255,10 @@ sc_status rotate_fields(sc_ctx *ctx, cudaStream_t st) {
                               ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_img_in,
                               st));
     } else {
-        const int64_t np = (int64_t)ctx->geo.nx * ctx->geo.ny;
-        CK(scd::launch_fields_f32(np, ctx->geo.n_comp, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr, ctx->d_delta_f,
-                                  ctx->d_aind_f, st));
+        CK(scd::launch_fields_f32(ctx->grid, ctx->d_ghost, ctx->d_delta, ctx->have_aind ? ctx->d_aind : nullptr,
+                                  ctx->d_pad0, ctx->d_padc, st));
         CK(scd::launch_rotate_f32(ctx->d_line_f32, ctx->d_slot_line, ctx->geo.n_slots, ctx->d_pair_f32, ctx->grid,
-                                  ctx->d_ghost, ctx->d_delta_f, ctx->d_aind_f, (float4 *)ctx->d_img_in, st));
+                                  ctx->d_ghost, ctx->d_pad0, ctx->d_padc, (float4 *)ctx->d_img_in, st));
     }
     return SC_OK;
 }
@@ -685,8 +684,9 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         CP(ctx->d_line_f32, lf.data(), nL * sizeof(scd::LineF32));
         CA(ctx->d_pair_f32, P * sizeof(scd::PairF32));
         CP(ctx->d_pair_f32, pf.data(), P * sizeof(scd::PairF32));
-        CA(ctx->d_delta_f, np * nc * sizeof(float2));
-        CA(ctx->d_aind_f, np * sizeof(float2));
+        const size_t npad = (size_t)(ctx->geo.nx + 2) * (ctx->geo.ny + 2);
+        CA(ctx->d_pad0, npad * sizeof(float4));
+        CA(ctx->d_padc, npad * (nc > 1 ? nc - 1 : 1) * sizeof(float2));
     }
     if (p->record_timings) {
         ctx->timing = true;

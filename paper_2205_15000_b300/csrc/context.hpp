@@ -70,7 +70,10 @@ struct sc_ctx {
     // FP32 production path tables and buffers
     scd::LineF32 *d_line_f32 = nullptr;
     scd::PairF32 *d_pair_f32 = nullptr;
-    float2 *d_delta_f = nullptr, *d_aind_f = nullptr;
+    // FP32 fields on the ghost-padded grid ((nx+2) x (ny+2)): (Re, Im Delta_0, A_ind)
+    // and Delta of components c >= 1
+    float4 *d_pad0 = nullptr;
+    float2 *d_padc = nullptr;
     // kernel timings
     bool timing = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};

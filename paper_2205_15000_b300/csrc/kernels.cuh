@@ -160,11 +160,13 @@ cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
 // the FP64 device reciprocal and reciprocal square root of the sweep on n values
 cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s);
 // FP32 production path
-cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, const double *aind, float2 *delta_f,
-                              float2 *aind_f, cudaStream_t s);
+// FP32 fields on the ghost-padded grid: every padded point takes the values of its
+// nearest grain point (ghost map), zero where it has none
+cudaError_t launch_fields_f32(const GridDev &grid, const int32_t *ghost, const double *delta, const double *aind,
+                              float4 *pad0, float2 *padc, cudaStream_t s);
 cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
                               const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
-                              const float2 *delta_f, const float2 *aind_f, float4 *image_in,
+                              const float4 *pad0, const float2 *padc, float4 *image_in,
                               cudaStream_t s);
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
                                    const GridDev &grid, const uint8_t *mask, const float4 *image_out,

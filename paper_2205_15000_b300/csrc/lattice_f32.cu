@@ -23,29 +23,46 @@ __device__ __forceinline__ void split_fixed(int64_t v, int &cell, float &frac) {
 
 }  // namespace
 
-// Delta (n_comp components, one after another) and A_ind to FP32
-__global__ void fields_f32_kernel(int64_t npts, int n_comp, const double2 *__restrict__ delta,
-                                  const double2 *__restrict__ aind, float2 *__restrict__ df,
-                                  float2 *__restrict__ af) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= npts) return;
-    for (int c = 0; c < n_comp; ++c) {
-        const double2 d = delta[c * npts + i];
-        df[c * npts + i] = make_float2((float)d.x, (float)d.y);
+// Delta (n_comp components, one after another) and A_ind to FP32 on the padded
+// grid (nx+2) x (ny+2): each padded point takes the values of its nearest grain
+// point (the ghost map), zero where it has none, so the rotation gathers its
+// bilinear stencil directly
+__global__ void fields_f32_kernel(GridDev grid, const int32_t *__restrict__ ghost, const double2 *__restrict__ delta,
+                                  const double2 *__restrict__ aind, float4 *__restrict__ pad0,
+                                  float2 *__restrict__ padc) {
+    const int64_t npad = (int64_t)(grid.nx + 2) * (grid.ny + 2);
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= npad) return;
+    const int64_t np = (int64_t)grid.nx * grid.ny;
+    const int g = ghost[b];
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g >= 0) {
+        const double2 d = delta[g];
+        v.x = (float)d.x;
+        v.y = (float)d.y;
+        if (aind) {
+            const double2 a = aind[g];
+            v.z = (float)a.x;
+            v.w = (float)a.y;
+        }
     }
-    if (aind) {
-        const double2 a = aind[i];
-        af[i] = make_float2((float)a.x, (float)a.y);
-    } else {
-        af[i] = make_float2(0.f, 0.f);
+    pad0[b] = v;
+    for (int c = 1; c < grid.n_comp; ++c) {
+        float2 e = make_float2(0.f, 0.f);
+        if (g >= 0) {
+            const double2 d = delta[c * np + g];
+            e = make_float2((float)d.x, (float)d.y);
+        }
+        padc[(c - 1) * npad + b] = e;
     }
 }
 
-cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, const double *aind, float2 *delta_f,
-                              float2 *aind_f, cudaStream_t st) {
+cudaError_t launch_fields_f32(const GridDev &grid, const int32_t *ghost, const double *delta, const double *aind,
+                              float4 *pad0, float2 *padc, cudaStream_t st) {
+    const int64_t npad = (int64_t)(grid.nx + 2) * (grid.ny + 2);
     const int bs = 256;
-    fields_f32_kernel<<<(unsigned)((npts + bs - 1) / bs), bs, 0, st>>>(
-        npts, n_comp, (const double2 *)delta, (const double2 *)aind, delta_f, aind_f);
+    fields_f32_kernel<<<(unsigned)((npad + bs - 1) / bs), bs, 0, st>>>(
+        grid, ghost, (const double2 *)delta, (const double2 *)aind, pad0, padc);
     return cudaGetLastError();
 }
 
@@ -56,8 +73,8 @@ cudaError_t launch_fields_f32(int64_t npts, int n_comp, const double *delta, con
 template <int GAUGE>
 __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32_t *__restrict__ slot_line,
                                   int64_t n_slots, const PairF32 *__restrict__ pairs, GridDev grid,
-                                  const int32_t *__restrict__ ghost, const float2 *__restrict__ df,
-                                  const float2 *__restrict__ af, float4 *__restrict__ out) {
+                                  const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
+                                  const float2 *__restrict__ padc, float4 *__restrict__ out) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
     const LineF32 ln = lines[slot_line[s]];
@@ -71,29 +88,24 @@ __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32
     if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
         const int px = grid.nx + 2;
         const int base = (j0 + 1) * px + (i0 + 1);
-        const int g00 = ghost[base], g10 = ghost[base + 1], g01 = ghost[base + px], g11 = ghost[base + px + 1];
+        const float4 p00 = pad0[base], p10 = pad0[base + 1], p01 = pad0[base + px], p11 = pad0[base + px + 1];
         const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
-        // a stencil point without a grain neighbour only occurs with zero weight
-        const float2 z = make_float2(0.f, 0.f);
-        const float2 d00 = g00 >= 0 ? df[g00] : z, d10 = g10 >= 0 ? df[g10] : z;
-        const float2 d01 = g01 >= 0 ? df[g01] : z, d11 = g11 >= 0 ? df[g11] : z;
-        const float2 a00 = g00 >= 0 ? af[g00] : z, a10 = g10 >= 0 ? af[g10] : z;
-        const float2 a01 = g01 >= 0 ? af[g01] : z, a11 = g11 >= 0 ? af[g11] : z;
-        const float dr = w00 * d00.x + w10 * d10.x + w01 * d01.x + w11 * d11.x;
-        const float di = w00 * d00.y + w10 * d10.y + w01 * d01.y + w11 * d11.y;
-        const float ax = w00 * a00.x + w10 * a10.x + w01 * a01.x + w11 * a11.x;
-        const float ay = w00 * a00.y + w10 * a10.y + w01 * a01.y + w11 * a11.y;
+        const float dr = w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x;
+        const float di = w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y;
+        const float ax = w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z;
+        const float ay = w00 * p00.w + w10 * p10.w + w01 * p01.w + w11 * p11.w;
         o.x = pp.eta * dr;
         o.y = pp.eta * di;
         // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
-        const int64_t np = (int64_t)grid.nx * grid.ny;
+        const int64_t npad = (int64_t)px * (grid.ny + 2);
         for (int c = 1; c < grid.n_comp; ++c) {
-            const float2 *dc = df + c * np;
-            const float2 e00 = g00 >= 0 ? dc[g00] : z, e10 = g10 >= 0 ? dc[g10] : z;
-            const float2 e01 = g01 >= 0 ? dc[g01] : z, e11 = g11 >= 0 ? dc[g11] : z;
+            const float2 *pc = padc + (c - 1) * npad;
+            const float2 e00 = pc[base], e10 = pc[base + 1], e01 = pc[base + px], e11 = pc[base + px + 1];
             o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
             o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
         }
+        // a stencil point without a grain neighbour (ghost -1) only occurs with zero weight
+        const int g00 = ghost[base], g10 = ghost[base + 1], g01 = ghost[base + px], g11 = ghost[base + px + 1];
         float az = ln.aext;
         if (GAUGE != 0) {
             // landau and solenoid gauges: A_ext at the sample, from its exact
@@ -122,22 +134,21 @@ __global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32
 
 cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
                               const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
-                              const float2 *delta_f, const float2 *aind_f, float4 *image_in,
+                              const float4 *pad0, const float2 *padc, float4 *image_in,
                               cudaStream_t st) {
     const int bs = 256;
     const unsigned nb = (unsigned)((n_slots + bs - 1) / bs);
     if (grid.gauge == 2)
-        rotate_f32_kernel<2><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
+        rotate_f32_kernel<2><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
     else if (grid.gauge == 1)
-        rotate_f32_kernel<1><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
+        rotate_f32_kernel<1><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
     else
-        rotate_f32_kernel<0><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, delta_f, aind_f, image_in);
+        rotate_f32_kernel<0><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
     return cudaGetLastError();
 }
 
-// one thread per grid point: for every pair, bilinear gather of the four image
-// slots around the point's lattice coordinates and the Fermi-surface sum
-// A block of four warps takes 32 consecutive grid points; warp q sums the 16-pair
+// Rotate back: for every pair, bilinear gather of the four image slots around the
+// grid point's lattice coordinates and the Fermi-surface sum.  A block of four warps takes 32 consecutive grid points; warp q sums the 16-pair
 // chunks q, q + 4, q + 8, ... of every point (FP32 within a chunk, FP64 across
 // chunks), so the lanes of a warp gather neighbouring samples of the same pair;
 // warp 0 adds the four partial sums in a fixed order.
