@@ -77,8 +77,14 @@ cudaError_t dalloc(sc_ctx *ctx, P **p, size_t bytes) {
     return e;
 }
 
-// energy lanes per line and energies per lane: least padding, then EPT near 4
-void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ept) {
+// energy lanes per line and energies per lane: least padding, then EPT near 4.
+// wide (the FP32 sweep on packed energy pairs, at most 256 energies): 16 or 32
+// lanes per line may carry up to 10 energies each, and among layouts with equal
+// padding the one with fewer issue units per line (lanes x energy pairs, an odd
+// energy counting as a pair) wins (c5, 160 energies: 16 x 10 against 32 x 5,
+// sweep 119.9 -> 110.4 ms; 8 lanes x 10 on c2 is slower than 16 x 5, its four
+// lines per warp differing in length)
+void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ept, bool wide) {
     if (forced_ept) {
         ept = forced_ept;
         lanes = 32;
@@ -114,9 +120,15 @@ void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ep
     }
     for (int l : {32, 16, 8, 4}) {
         const int e = (n_e + l - 1) / l;
-        if (e > 8) continue;
+        if (e > (wide && l >= 16 ? 10 : 8)) continue;
         const int pad = l * e;
-        if (pad < best_pad || (pad == best_pad && std::abs(e - 4) < std::abs(best_e - 4))) {
+        bool better = pad < best_pad;
+        if (pad == best_pad) {
+            const int units = l * ((e + 1) / 2), best_units = best_l * ((best_e + 1) / 2);
+            better = wide && units != best_units ? units < best_units
+                                                 : std::abs(e - 4) < std::abs(best_e - 4);
+        }
+        if (better) {
             best_pad = pad;
             best_l = l;
             best_e = e;
@@ -151,16 +163,17 @@ sc_status check_ctx(sc_ctx *ctx) {
     return SC_OK;
 }
 
-sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out) {
+sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out, bool wide) {
     int lanes, ept;
-    choose_lanes(n_e, ctx->forced_lanes, forced_ept, lanes, ept);
+    choose_lanes(n_e, ctx->forced_lanes, forced_ept, lanes, ept, wide && !ctx->fp64 && n_e <= 32 * 8);
     return make_plan_layout(ctx, n_e, lanes, ept, out);
 }
 
 sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out) {
     if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
         return set_err(ctx, SC_EINVAL, "energy lanes per line must be 4, 8, 16 or 32");
-    if (ept < 1 || ept > 8) return set_err(ctx, SC_EINVAL, "energies per lane must be 1 to 8");
+    if (ept < 1 || ept > (ctx->fp64 ? 8 : 10))
+        return set_err(ctx, SC_EINVAL, ctx->fp64 ? "energies per lane must be 1 to 8" : "energies per lane must be 1 to 10");
     const int n_blocks = (n_e + lanes * ept - 1) / (lanes * ept);
     const int key = n_blocks * 1024 + lanes * 16 + ept;
     auto it = ctx->plans.find(key);
@@ -760,7 +773,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     }
 #undef CA
 #undef CP
-    sc_status st = make_plan(ctx, ctx->n_e, 0, &ctx->main_plan);
+    sc_status st = make_plan(ctx, ctx->n_e, 0, &ctx->main_plan, true);
     if (st == SC_OK && !ctx->forced_lanes) {
         // A small grain (few lines, few energies) leaves resident warps without
         // work: one doubling of the lanes per line doubles the work items, kept
@@ -1175,6 +1188,13 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
 static sc_status adjoint_plan(sc_ctx *ctx, Plan **out) {
     Plan *pl = ctx->main_plan;
     *out = pl;
+    if (pl->ept > 8) {
+        // the adjoint kernel keeps at most 8 energies per lane
+        if (ctx->forced_lanes)
+            return set_err(ctx, SC_EINVAL, "the adjoint takes at most 8 energies per lane: more lanes per line");
+        CKS(make_plan(ctx, ctx->n_e, 0, &pl));
+        *out = pl;
+    }
     if (ctx->forced_lanes) return SC_OK;
     const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl->ept, 128, ctx->stepper));
     const int64_t resident = (int64_t)ctx->sm_count * occ * 4;

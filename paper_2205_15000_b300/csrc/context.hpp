@@ -108,7 +108,7 @@ sc_status set_err(sc_ctx *c, sc_status st, const std::string &msg);
 cudaError_t dalloc_bytes(sc_ctx *ctx, void **p, size_t bytes);
 void dfree(sc_ctx *ctx, void *p);
 // lanes/EPT plan for n_e energies (forced_ept = 0: choose); builds the line groups
-sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out);
+sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out, bool wide = false);
 // plan for an explicit layout: lanes in {4, 8, 16, 32}, lanes * ept >= n_e
 sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out);
 // fields of the context onto its lattices (rotate kernels)

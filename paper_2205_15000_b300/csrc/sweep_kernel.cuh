@@ -302,8 +302,16 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
     }
 }
 
+// 9 or 10 energies per lane (FP32 Matsubara/Ozaki sweep on 16 or 32 lanes per
+// line): 4 blocks per SM, 128 registers
+#ifndef SC_SWEEP_MIN_BLOCKS_WIDE
+#define SC_SWEEP_MIN_BLOCKS_WIDE 4
+#endif
+
 template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK = false>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS) : 1)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? (EPT > 8 ? SC_SWEEP_MIN_BLOCKS_WIDE
+                                                                 : (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS))
+                                                      : 1)
     sweep_kernel(SweepLaunch a) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -328,6 +336,16 @@ static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
 #define SC_CASE(E) \
     case E: sweep_kernel<T, E, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
+        case 9:
+        case 10:
+            // the wide layouts exist for the FP32 sweep without energy blocks only
+            if constexpr (sizeof(T) == 4 && !RET && !BLK) {
+                if (a.energies_per_lane == 9) sweep_kernel<T, 9, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a);
+                else sweep_kernel<T, 10, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a);
+                break;
+            } else {
+                return cudaErrorInvalidValue;
+            }
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
     }
@@ -358,6 +376,15 @@ static int occ_dispatch(int ept, int bs) {
     case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET, STEP, WGT>, bs, 0); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
+        case 9:
+        case 10:
+            if constexpr (sizeof(T) == 4 && !RET) {
+                if (ept == 9) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 9, RET, STEP, WGT>, bs, 0);
+                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 10, RET, STEP, WGT>, bs, 0);
+            } else {
+                n = 0;
+            }
+            break;
         default: n = 0;
     }
     return n;
@@ -368,6 +395,9 @@ static int occ_dispatch(int ept, int bs) {
 template <typename T>
 static int sweep_occupancy_t(int ept, int bs, int stepper, bool weighted) {
     int a, b;
+    if (ept > 8)  // the wide layouts have no retarded instantiation (the LDOS keeps at most 8)
+        return stepper == 1 ? (weighted ? occ_dispatch<T, false, 1, true>(ept, bs) : occ_dispatch<T, false, 1, false>(ept, bs))
+                            : (weighted ? occ_dispatch<T, false, 0, true>(ept, bs) : occ_dispatch<T, false, 0, false>(ept, bs));
     if (stepper == 1) {
         a = weighted ? occ_dispatch<T, false, 1, true>(ept, bs) : occ_dispatch<T, false, 1, false>(ept, bs);
         b = occ_dispatch<T, true, 1, false>(ept, bs);
