@@ -59,6 +59,88 @@ def _measured_peaks():
         return {}
 
 
+class ClockSampler:
+    """SM clock and clock-event reasons read through NVML (the driver's
+    libnvidia-ml, read-only queries) every 2 ms by a thread that runs exactly while
+    the timed steps run.  Falls back to the nvidia-smi sampler when NVML cannot be
+    opened."""
+
+    REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+               "sw_power_cap": 0x4, "hw_power_brake_slowdown": 0x80}
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, device_index, smi_path):
+        import ctypes
+        import threading
+        self.samples, self.reasons, self.smax = [], set(), None
+        self.stop_flag = threading.Event()
+        self.thread = None
+        self.smi = None
+        self.smi_path, self.index = smi_path, device_index
+        try:
+            import torch
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit")
+            want = str(torch.cuda.get_device_properties(device_index).uuid)
+            want = want if want.startswith("GPU-") else "GPU-" + want
+            n = ctypes.c_uint(0)
+            nv.nvmlDeviceGetCount_v2(ctypes.byref(n))
+            handle = None
+            for i in range(n.value):
+                h = ctypes.c_void_p()
+                if nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(i), ctypes.byref(h)) != 0:
+                    continue
+                buf = ctypes.create_string_buffer(96)
+                if nv.nvmlDeviceGetUUID(h, buf, ctypes.c_uint(96)) == 0 and buf.value.decode() == want:
+                    handle = h
+                    break
+            if handle is None:
+                raise RuntimeError("no NVML device with the CUDA device's UUID")
+            clk = ctypes.c_uint(0)
+            if nv.nvmlDeviceGetMaxClockInfo(handle, ctypes.c_int(self.NVML_CLOCK_SM), ctypes.byref(clk)) != 0:
+                raise RuntimeError("nvmlDeviceGetMaxClockInfo")
+            self.smax = float(clk.value)
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.nvml, self.h = nv, handle
+        except Exception:
+            self.nvml = None
+            self.smi = _sample_clocks_start(smi_path)
+
+    def _run(self):
+        import ctypes
+        nv, h = self.nvml, self.h
+        clk, r = ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self.stop_flag.is_set():
+            if nv.nvmlDeviceGetClockInfo(h, ctypes.c_int(self.NVML_CLOCK_SM), ctypes.byref(clk)) == 0:
+                self.samples.append(float(clk.value))
+            if self.reason_fn(h, ctypes.byref(r)) == 0:
+                for name, bit in self.REASONS.items():
+                    if r.value & bit:
+                        self.reasons.add(name)
+            self.stop_flag.wait(0.002)
+
+    def start(self):
+        if self.nvml is not None:
+            import threading
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+        return self
+
+    def stop(self):
+        if self.nvml is None:
+            return _sample_clocks_stop(*(self.smi or (None, None)), self.smi_path, self.index)
+        self.stop_flag.set()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        if not self.samples:
+            return None
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.smax,
+                "reasons": sorted(self.reasons), "samples": len(self.samples),
+                "source": "NVML every 2 ms during the timed steps"}
+
+
 def _sample_clocks_start(path):
     try:
         f = open(path, "w")
@@ -238,11 +320,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
-    cproc, cfile = _sample_clocks_start(clk_path) if rank == 0 else (None, None)
+    sampler = ClockSampler(local, clk_path) if rank == 0 else None
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     kern = []  # per timed step: (rotate, sweep, rotate_back) from the library's events
+    if sampler:
+        sampler.start()
     t_wall = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
@@ -260,7 +344,7 @@ def run_ours(args):
                   "rotate_back": statistics.mean(k[2] for k in kern)}
     if args.adjoint:
         kernels_ms["adjoint_sweep"] = statistics.mean(k[3] for k in kern)
-    clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
+    clocks = sampler.stop() if sampler else None
 
     # end to end through the public API with host buffers: every step copies its
     # input Delta from pinned host memory and reads Delta_new, j and F back into
@@ -433,10 +517,12 @@ def run_batch(args):
     ranks.barrier(dist)
     clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
     os.makedirs(os.path.dirname(clk_path), exist_ok=True)
-    cproc, cfile = _sample_clocks_start(clk_path) if rank == 0 else (None, None)
+    sampler = ClockSampler(local, clk_path) if rank == 0 else None
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ksweep = []
+    if sampler:
+        sampler.start()
     for i in range(args.steps):
         ev[i][0].record(stream)
         b.run(1, True, stream)
@@ -444,7 +530,7 @@ def run_batch(args):
         flush.fill_(float(i))
         ksweep.append(b.info().ms_sweep)
     torch.cuda.synchronize()
-    clocks = _sample_clocks_stop(cproc, cfile, clk_path, local) if rank == 0 else None
+    clocks = sampler.stop() if sampler else None
     total_ms = ranks.max_over_ranks(dist, float(sum(a.elapsed_time(c) for a, c in ev)), dev)
     value = ranks.throughput(info.steps_per_sweep * args.steps, world, total_ms * 1e-3)
     if rank != 0:
