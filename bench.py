@@ -348,16 +348,17 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: every step copies its
     # input Delta from pinned host memory and reads Delta_new, j and F back into
-    # pinned host memory.  The copies run on a second stream through device
-    # staging buffers, so that step i's read-back and step i+1's upload overlap
-    # the sweeps; L2 is flushed at the start of every step, inside the timed region.
+    # pinned host memory.  Uploads and read-backs run on two more streams through
+    # double-buffered device staging, so that step i+1's upload and step i-1's
+    # read-back overlap step i's sweep; L2 is flushed at the start of every step,
+    # inside the timed region.
     pin_delta = torch.view_as_real(torch.as_tensor(delta, dtype=torch.complex128)).contiguous().pin_memory()
     h_out = [[torch.empty((p["ny"], p["nx"], 2), dtype=torch.float64).pin_memory(),
               torch.empty((p["ny"], p["nx"], 2), dtype=torch.float64).pin_memory(),
               torch.empty((p["ny"], p["nx"]), dtype=torch.float64).pin_memory()] for _ in range(2)]
     d_in = [torch.empty_like(pin_delta, device=dev) for _ in range(2)]
     d_out = [[torch.empty_like(h, device=dev) for h in h_out[0]] for _ in range(2)]
-    cs = torch.cuda.Stream()
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
     e2e_ms = []
     e2e_enqueue_ms = None
     n_e2e = max(5, min(args.steps, 20)) if not args.no_e2e else 0
@@ -369,11 +370,11 @@ def run_ours(args):
             ev_read = [torch.cuda.Event() for _ in range(n_steps)]
             for i in range(n_steps):
                 b = i % 2
-                with torch.cuda.stream(cs):
+                with torch.cuda.stream(cs_in):
                     if i >= 2:
-                        cs.wait_event(ev_used[i - 2])    # the buffer's previous upload was consumed
+                        cs_in.wait_event(ev_used[i - 2])  # the buffer's previous upload was consumed
                     d_in[b].copy_(pin_delta, non_blocking=True)
-                    ev_in[i].record(cs)
+                    ev_in[i].record(cs_in)
                 stream.wait_event(ev_in[i])
                 if i >= 2:
                     stream.wait_event(ev_read[i - 2])    # the output buffers were read back
@@ -385,11 +386,11 @@ def run_ours(args):
                 sc.sc_current(ctx.h, d_out[b][1], True, stream)
                 sc.sc_free_energy(ctx.h, d_out[b][2], True, False, stream)
                 ev_out[i].record(stream)
-                with torch.cuda.stream(cs):
-                    cs.wait_event(ev_out[i])
+                with torch.cuda.stream(cs_out):
+                    cs_out.wait_event(ev_out[i])
                     for h_, d_ in zip(h_out[b], d_out[b]):
                         h_.copy_(d_, non_blocking=True)
-                    ev_read[i].record(cs)
+                    ev_read[i].record(cs_out)
             t_enq = time.perf_counter()
             torch.cuda.synchronize()
             return t_enq
