@@ -54,3 +54,19 @@ def test_adjoint_refuses_a_forced_wide_layout():
     ctx.sweep()
     with pytest.raises(sc.ScError):
         ctx.adjoint(g_Ftotal=1.0)
+
+
+@pytest.mark.parametrize("n_e,layout", [(160, (16, 10)), (80, (16, 5)), (144, (16, 9)), (128, (32, 4))])
+def test_layout_choice_on_a_grain_that_fills_the_gpu(n_e, layout):
+    """Least padding first; among equal padding the fewest issue units per line
+    (16 x 10 rather than 32 x 5 for 160 energies; 32 x 4 and 16 x 8 tie and keep
+    4 energies per lane)."""
+    from paper_2205_15000_b300 import sc
+    p, _, _ = W.c2_diamond_d(n=256, n_angles=64)
+    p["n_energies"] = n_e
+    ctx = sc.Context(p, precision="fp32")
+    info = sc.sc_get_info(ctx.h)
+    assert (info.lanes_per_line, info.energies_per_lane) == layout
+    # FP64 keeps at most 8 energies per lane
+    ctx64 = sc.Context(p, precision="fp64")
+    assert sc.sc_get_info(ctx64.h).energies_per_lane <= 8
