@@ -349,10 +349,11 @@ typedef struct {
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
    in sc_create) and one work list over all their (line group) items, longest
-   first.  energies_per_lane (1..8) bounds the energies one lane carries; 0
-   picks a default; sc_batch_autotune chooses by timing.  Each member takes the
-   lanes per line (4, 8, 16, 32) and energies per lane (<= the bound) with the
-   fewest padded lane slots, then the most energies per lane.  Members with
+   first.  energies_per_lane (1..8; FP32 batches 1..10) bounds the energies
+   one lane carries; 0 picks a default; sc_batch_autotune chooses by timing.
+   Each member takes the lanes per line (4, 8, 16, 32) and energies per lane
+   (<= the bound; 9 and 10 only on 16 or 32 lanes per line and without energy
+   blocks) with the fewest padded lane slots, then the most energies per lane.  Members with
    equal energies per lane share one persistent launch; a batch sweep runs
    these launches back to back.  The members are owned by the batch. */
 sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,

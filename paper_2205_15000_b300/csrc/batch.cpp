@@ -97,9 +97,11 @@ void free_plan_buffers(sc_batch *b) {
 // energies per lane (fewer lanes: fewer shuffle rounds, more lines per warp).
 void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
     int best = 1 << 30;
+    // 9 or 10 energies per lane only on 16 or 32 lanes per line (FP32 bounds above 8);
+    // among equal padding the fewer lanes (fewer issue units per line) come first
     for (int l : {4, 8, 16, 32}) {
         const int e = (n_e + l - 1) / l;
-        if (e < 1 || e > ept_max) continue;
+        if (e < 1 || e > (l >= 16 ? ept_max : std::min(ept_max, 8))) continue;
         if (l * e < best) {
             best = l * e;
             lanes = l;
@@ -110,7 +112,7 @@ void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
     // more energies than one layout holds: energy blocks, each counted with 32
     // slots of per-block overhead
     for (int l : {32, 16, 8, 4})
-        for (int e = ept_max; e >= 1; --e) {
+        for (int e = std::min(ept_max, 8); e >= 1; --e) {
             const int nb = (n_e + l * e - 1) / (l * e);
             const int cost = nb * (l * e + 32);
             if (cost < best) {
@@ -259,8 +261,10 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
         sc_internal::set_thread_error("need params, out and n >= 1");
         return SC_EINVAL;
     }
-    if (energies_per_lane < 0 || energies_per_lane > 8) {
-        sc_internal::set_thread_error("energies_per_lane must be 0 (automatic) or 1..8");
+    const int ept_cap = params[0].precision == SC_PREC_FP64 ? 8 : 10;
+    if (energies_per_lane < 0 || energies_per_lane > ept_cap) {
+        sc_internal::set_thread_error(ept_cap == 8 ? "energies_per_lane must be 0 (automatic) or 1..8"
+                                                   : "energies_per_lane must be 0 (automatic) or 1..10");
         return SC_EINVAL;
     }
     *out = nullptr;
@@ -476,7 +480,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     for (sc_ctx *c : b->members) max_ne = std::max(max_ne, c->n_e);
     int best = b->ept;
     float best_ms = 1e30f;
-    for (int ept = 2; ept <= 8; ++ept) {
+    for (int ept = 2; ept <= (b->fp64 ? 8 : 10); ++ept) {
         if (max_ne > 32 * ept) continue;
         sc_status s = build(b, ept);
         if (s != SC_OK) return s;
