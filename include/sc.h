@@ -116,7 +116,9 @@ typedef struct {
     double lattice_ox, lattice_oy; /* origin of the rotated lattices relative to the
                                       grid-box centre, units of h (default 0.1, 0.2) */
     int32_t precision;       /* sc_precision: FP64 plain sweep or FP32 production sweep */
-    int32_t lanes_per_line;  /* 0 = automatic; else 4, 8, 16 or 32 energy lanes per line */
+    int32_t lanes_per_line;  /* 0 = automatic; else 4, 8, 16 or 32 energy lanes per line
+                                (the energies per lane then follow: at most 8, or 10 for an
+                                FP32 sweep on 16 or 32 lanes; the adjoint takes at most 8) */
     int32_t host_only;       /* 1 = build the geometry tables only (no device memory); every
                                 call that computes then returns SC_ESTATE.  For inspecting
                                 the discretisation on a machine without a GPU. */
@@ -159,7 +161,9 @@ typedef struct {
     int64_t points_per_sweep;/* (angle, energy, sample) points where g is formed */
     double area;             /* exact grain area (xi0^2) */
     double norm_D;           /* gap-equation normalisation ln t + 2 sum 1/(2n+1) */
-    int32_t lanes_per_line, energies_per_lane, lines_per_warp;
+    int32_t lanes_per_line, energies_per_lane, lines_per_warp; /* the sweep's lane layout:
+                                energies per lane 1..8, or 9..10 for the FP32 sweep on 16
+                                or 32 lanes per line */
     int64_t scratch_bytes;   /* device scratch used by the sweep */
     double ms_rotate, ms_sweep, ms_rotate_back; /* last sweep's kernel times when
                                 record_timings = 1 (sc_get_info then waits for that sweep) */
