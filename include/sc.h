@@ -211,7 +211,7 @@ sc_status sc_get_fields(sc_ctx *ctx, double *delta, double *a_ind, int on_device
    trajectory from the local homogeneous solution. */
 sc_status sc_reset_boundary(sc_ctx *ctx);
 
-/* One Riccati sweep (Alg. suprcon inner loop): for every angle pair, line and
+/* One Riccati sweep (Algorithm 1 inner loop): for every angle pair, line and
    positive Matsubara energy integrate gamma (Eq. riccati) along and gamma~
    (Eq. riccati_tilde) against the Fermi velocity with the closed-form
    constant-coefficient step, starting from the boundary values of the
@@ -246,7 +246,7 @@ sc_status sc_free_energy(sc_ctx *ctx, double *F_total, double *density_out, int 
    A_ind = -(1/kappa^2) sum G (j - <j>), full correlation; becomes the
    context's A_ind.  No-op when kappa <= 0. */
 sc_status sc_update_vector_potential(sc_ctx *ctx, void *stream);
-/* One Picard step of Alg. suprcon (App. E, alpha = 1): Delta <- Delta_new,
+/* One Picard step of Algorithm 1 (App. E, alpha = 1): Delta <- Delta_new,
    A_ind <- from j (when kappa > 0). */
 sc_status sc_picard_step(sc_ctx *ctx, void *stream);
 
@@ -290,7 +290,7 @@ sc_status sc_accel_params_default(int32_t kind, sc_accel_params *p);
 /* One accelerator step after a sweep; Delta and A_ind of the context are
    replaced by x_{i+1} (the next sweep reads them). */
 sc_status sc_accelerate(sc_ctx *ctx, const sc_accel_params *p, void *stream);
-/* The self-consistency loop of Alg. suprcon run natively: per iteration a
+/* The self-consistency loop of Algorithm 1 run natively: per iteration a
    sweep, then (every check_every iterations, and at max_iter) the residual
    eps_G of Delta (Eq. global_error, l2) read back and compared with tol, then
    the accelerator step (which updates A_ind when kappa is finite).  Stops

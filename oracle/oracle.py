@@ -394,7 +394,7 @@ class OracleGeom:
         return matsubara(self.prm["t"], self.n_e)
 
     def full_sweep(self, delta, aind=None, exit_in=None):
-        """Sweep at the positive Matsubara energies + outputs (Alg. suprcon body)."""
+        """Sweep at the positive Matsubara energies + outputs (Algorithm 1 body)."""
         im, ex = self.sweep(delta, aind, self.matsubara(), 0, exit_in)
         acc = self.rotate_back(im, 0)
         out = self.outputs(acc, delta, aind)
@@ -404,7 +404,7 @@ class OracleGeom:
         return out
 
     def picard(self, delta0, n_iter, aind0=None, update_a=True):
-        """Fixed-point iteration of Alg. suprcon with the Picard step (alpha = 1):
+        """Fixed-point iteration of Algorithm 1 with the Picard step (alpha = 1):
         Delta <- Delta_new, A_ind <- from j, boundary values carried over."""
         delta = np.array(delta0, dtype=np.complex128)
         aind = None if aind0 is None else np.array(aind0, np.float64)
@@ -425,7 +425,7 @@ class OracleGeom:
         return dict(delta=delta, aind=aind, history=np.array(hist), last=out, exit=exit_in)
 
     def self_consistency(self, delta0, n_iter, params, aind0=None):
-        """Alg. suprcon with an accelerator of App. E (oracle/accel.py): each
+        """Algorithm 1 with an accelerator of App. E (oracle/accel.py): each
         iteration sweeps with the current (Delta, A_ind), forms g(x) =
         (Delta_new, kappa^2 A from j) and takes the accelerator's step; boundary
         values are carried over."""

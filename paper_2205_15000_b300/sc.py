@@ -643,7 +643,7 @@ class Context:
         sc_accelerate(self.h, params, stream)
 
     def self_consistency(self, params, max_iter=1000, tol=1e-5, check_every=1, stream=None):
-        """The native loop of Alg. suprcon (sweep, residual check, accelerator
+        """The native loop of Algorithm 1 (sweep, residual check, accelerator
         step): returns (converged, iterations, eps_G)."""
         it = ctypes.c_int32(0)
         eps = ctypes.c_double(0.0)

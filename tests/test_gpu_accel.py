@@ -1,5 +1,5 @@
 """Self-consistency accelerators (App. E) through the C ABI: the loop of
-Alg. suprcon with each accelerator against the oracle's loop (FP64, same
+Algorithm 1 with each accelerator against the oracle's loop (FP64, same
 seeded inputs), parameter validation, and iterations to convergence on a
 small-penetration-depth disc with a vortex."""
 import math

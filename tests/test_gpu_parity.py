@@ -155,7 +155,7 @@ def test_lane_layouts_agree(lanes):
 
 
 def test_picard_with_vector_potential_matches_oracle():
-    """Three iterations of Alg. suprcon with Picard steps and the App. D
+    """Three iterations of Algorithm 1 with Picard steps and the App. D
     vector-potential update, FP64, against the oracle's loop."""
     sc = _sc()
     import torch

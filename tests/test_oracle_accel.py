@@ -2,7 +2,7 @@
 that do not come from the oracle: reductions to the Picard step, the exact
 secant step of Barzilai-Borwein on linear problems, the classical BB formulas
 in terms of s = x_i - x_{i-1} and y = d_{i-1} - d_i, the similarity weight of
-CongAcc, and the Picard loop of Alg. suprcon."""
+CongAcc, and the Picard loop of Algorithm 1."""
 import math
 
 import numpy as np
@@ -132,7 +132,7 @@ def test_accelerators_solve_a_linear_fixed_point(kind):
 
 def test_picard_loop_equals_alg_suprcon_picard():
     """The accelerated loop with Picard, alpha = 1, is the plain fixed-point
-    iteration of Alg. suprcon (Delta <- Delta_new, A_ind <- from j)."""
+    iteration of Algorithm 1 (Delta <- Delta_new, A_ind <- from j)."""
     p = W.disc(4.0, 24, pairing=0, t=0.5, n_angles=12, n_energies=5, flux_quanta=1.2, kappa=3.0)
     d0 = W.vortex_delta(p, 0.25, [(0.5, 0.0)], [-1])
     g = oracle.OracleGeom(p)

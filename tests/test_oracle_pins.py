@@ -534,7 +534,7 @@ def test_zero_bias_state_at_110_edge_scales_inverse_broadening():
 
 
 # ---------------------------------------------------------------------------
-# Self-consistency loop (Alg. suprcon with the Picard step, App. E)
+# Self-consistency loop (Algorithm 1 with the Picard step, App. E)
 # ---------------------------------------------------------------------------
 def test_c1_picard_converges_to_bulk():
     """P3: s-wave square from a noisy bulk guess: the global error (Eq.
