@@ -130,7 +130,7 @@ def test_accelerators_solve_a_linear_fixed_point(kind):
     assert np.linalg.norm(xs[-1] - xs_true) < 1e-8 * np.linalg.norm(xs_true)
 
 
-def test_picard_loop_equals_alg_suprcon_picard():
+def test_picard_loop_equals_algorithm_1_picard():
     """The accelerated loop with Picard, alpha = 1, is the plain fixed-point
     iteration of Algorithm 1 (Delta <- Delta_new, A_ind <- from j)."""
     p = W.disc(4.0, 24, pairing=0, t=0.5, n_angles=12, n_energies=5, flux_quanta=1.2, kappa=3.0)
