@@ -20,6 +20,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -323,8 +324,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ranks.barrier(dist)
     torch.cuda.synchronize()
-    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_r{rank}_{os.getpid()}.csv")
     sampler = ClockSampler(local, clk_path) if rank == 0 else None
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -521,8 +521,7 @@ def run_batch(args):
     info = b.info()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ranks.barrier(dist)
-    clk_path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv")
-    os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+    clk_path = os.path.join(tempfile.gettempdir(), f"bench_clocks_r{rank}_{os.getpid()}.csv")
     sampler = ClockSampler(local, clk_path) if rank == 0 else None
     time.sleep(0.3)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
