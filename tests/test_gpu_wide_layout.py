@@ -70,3 +70,29 @@ def test_layout_choice_on_a_grain_that_fills_the_gpu(n_e, layout):
     # FP64 keeps at most 8 energies per lane
     ctx64 = sc.Context(p, precision="fp64")
     assert sc.sc_get_info(ctx64.h).energies_per_lane <= 8
+
+
+def test_batch_with_a_wide_member_matches_oracle():
+    """A batch bounded by 10 energies per lane: the 150-energy member runs 16 x 10
+    in its own class launch, the 40-energy member 8 x 5; both against the oracle
+    after two sweeps (FP32 tolerances)."""
+    from paper_2205_15000_b300 import sc
+    p1, d1 = _grain(150)
+    p2 = W.disc(4.0, 28, pairing=0, t=0.5, n_angles=16, n_energies=40, flux_quanta=0.7)
+    d2 = W.noisy_delta(p2, 0.26, 0.1, seed=82)
+    b = sc.Batch([p1, p2], precision="fp32", energies_per_lane=10)
+    for m, d in zip(b.members, (d1, d2)):
+        m.set_fields(d)
+    for _ in range(2):
+        b.sweep()
+    for m, (p, d) in zip(b.members, ((p1, d1), (p2, d2))):
+        g = oracle.OracleGeom(p)
+        mask = g.mask().astype(bool)
+        ex = None
+        for _ in range(2):
+            o = g.full_sweep(d, None, ex)
+            ex = o["exit"]
+        r = _outputs(m)
+        assert np.max(np.abs(r["delta_new"][mask] - o["delta_new"][mask])) < 1e-5 * np.max(np.abs(o["delta_new"][mask]))
+        assert np.max(np.abs(r["F"][mask] - o["F"][mask])) < 1e-4 * np.max(np.abs(o["F"][mask]))
+    b.close()
