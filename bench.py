@@ -291,6 +291,9 @@ def run_ours(args):
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
             f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     p["stepper"] = args.stepper
+    if args.energies:  # another energy count on the same grain (profiling the wide layouts)
+        p["n_energies"] = args.energies
+        workload += f"_{args.energies}eps"
     if args.lanes:  # a fixed lane layout (profiling a small case in the layout of a large one)
         workload += f"_lanes{args.lanes}"
     if args.energy_sum == "ozaki":
@@ -814,6 +817,7 @@ def main():
                          "annulus: d-wave annulus R> 25, R< 10 (256^2), solenoid gauge")
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--energies", type=int, default=0, help="energy count (0: the workload's own)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
                     help="energy lanes per line (0: the library's choice)")
     ap.add_argument("--grains", type=int, default=64)
