@@ -3,7 +3,8 @@
 // lane travel as one float2 through the step and the propagator sums with
 // sm_100's two-wide FP32 instructions (fma/mul/add .f32x2): one issue slot per
 // two lane-operations, which is what bounds the scalar kernel.  The transcendental
-// unit instructions stay per energy; an odd EPT keeps its last energy scalar.
+// unit instructions stay per energy; an odd EPT runs its last energy through the
+// same formulation on single values.
 //
 // Arithmetic is that of step_coef / step_apply (App. C closed-form step) and of
 // the propagator sums of the scalar sweep, rearranged for the packed form:
@@ -44,6 +45,43 @@ __device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ f2 rsqrt2(f2 v) { return make_float2(Mth<float>::rsqrt(v.x), Mth<float>::rsqrt(v.y)); }
 __device__ __forceinline__ f2 rcp2(f2 v) { return make_float2(Mth<float>::rcp(v.x), Mth<float>::rcp(v.y)); }
 
+// The same operations on one value: the odd last energy of a lane runs the same
+// formulation as the pairs (templates below on V = f2 or float).
+__device__ __forceinline__ float add2(float a, float b) { return a + b; }
+__device__ __forceinline__ float sub2(float a, float b) { return a - b; }
+__device__ __forceinline__ float mul2(float a, float b) { return a * b; }
+__device__ __forceinline__ float fma2(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float neg2(float a) { return -a; }
+__device__ __forceinline__ float rsqrt2(float v) { return Mth<float>::rsqrt(v); }
+__device__ __forceinline__ float rcp2(float v) { return Mth<float>::rcp(v); }
+
+template <typename V>
+__device__ __forceinline__ V bcv(float v);
+template <>
+__device__ __forceinline__ f2 bcv<f2>(float v) { return bc2(v); }
+template <>
+__device__ __forceinline__ float bcv<float>(float v) { return v; }
+
+__device__ __forceinline__ f2 absv(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float absv(float a) { return fabsf(a); }
+__device__ __forceinline__ f2 ex2v(f2 a) { return make_float2(ex2_approx(a.x), ex2_approx(a.y)); }
+__device__ __forceinline__ float ex2v(float a) { return ex2_approx(a); }
+__device__ __forceinline__ void sincosv(float t, float &s, float &c) { Mth<float>::sincos_(t, &s, &c); }
+__device__ __forceinline__ void sincosv(f2 t, f2 &s, f2 &c) {
+    sincosv(t.x, s.x, c.x);
+    sincosv(t.y, s.y, c.y);
+}
+// sqrt(2) times the principal square root (Re >= 0) of x + i y, from sq = sqrt(2) s
+// and yq = sqrt(2) y/(2 s), s = sqrt((|x + i y| + |x|)/2)
+__device__ __forceinline__ void principal(float x, float y, float sq, float yq, float &re, float &im) {
+    re = x >= 0.f ? sq : fabsf(yq);
+    im = x >= 0.f ? yq : copysignf(sq, y);
+}
+__device__ __forceinline__ void principal(f2 x, f2 y, f2 sq, f2 yq, f2 &re, f2 &im) {
+    principal(x.x, y.x, sq.x, yq.x, re.x, im.x);
+    principal(x.y, y.y, sq.y, yq.y, re.y, im.y);
+}
+
 constexpr float kRs2 = 0.70710678118654752f;  // 1/sqrt(2)
 constexpr float kLog2e = 1.4426950408889634f;
 
@@ -51,89 +89,90 @@ constexpr float kLog2e = 1.4426950408889634f;
 // segment length ell, and the part of z = zr + i zi that all energies share --
 // the Doppler shift zr = +-a for Matsubara energies (zi = eps_n per energy), the
 // broadening zi for the retarded sweep (zr = E_n +- a per energy).
-struct Seg2 {
-    f2 c0;    // Matsubara: |Delta|^2 - zr^2; retarded: |Delta|^2 + zi^2
-    f2 m2;    // Matsubara: -2 zr; retarded: -2 zi
-    f2 zs;    // Matsubara: zr; retarded: zi
-    f2 sh;    // retarded: the Doppler shift added to each energy
-    f2 dr, di, ndr, ndi;
-    f2 el;   // -2 ell log2(e) / sqrt(2): sqrt(2) Re Omega -> log2 |E|
-    f2 ntl;  // -2 ell / sqrt(2): sqrt(2) Im Omega -> arg E
+template <typename V>
+struct SegT {
+    V c0;    // Matsubara: |Delta|^2 - zr^2; retarded: |Delta|^2 + zi^2
+    V m2;    // Matsubara: -2 zr; retarded: -2 zi
+    V zs;    // Matsubara: zr; retarded: zi
+    V sh;    // retarded: the Doppler shift added to each energy
+    V dr, di, ndr, ndi;
+    V el;   // -2 ell log2(e) / sqrt(2): sqrt(2) Re Omega -> log2 |E|
+    V ntl;  // -2 ell / sqrt(2): sqrt(2) Im Omega -> arg E
 };
+typedef SegT<f2> Seg2;
 
-template <bool RET>
-__device__ __forceinline__ Seg2 seg2(float dr, float di, float shift, float broad, float ell) {
-    Seg2 s;
+template <bool RET, typename V = f2>
+__device__ __forceinline__ SegT<V> seg2(float dr, float di, float shift, float broad, float ell) {
+    SegT<V> s;
     const float d2 = dr * dr + di * di;
     const float zs = RET ? broad : shift;
-    s.c0 = bc2(RET ? d2 + zs * zs : d2 - zs * zs);
-    s.m2 = bc2(-2.f * zs);
-    s.zs = bc2(zs);
-    s.sh = bc2(shift);
-    s.dr = bc2(dr);
-    s.di = bc2(di);
-    s.ndr = bc2(-dr);
-    s.ndi = bc2(-di);
-    s.el = bc2(-2.f * kLog2e * kRs2 * ell);
-    s.ntl = bc2(-2.f * kRs2 * ell);
+    s.c0 = bcv<V>(RET ? d2 + zs * zs : d2 - zs * zs);
+    s.m2 = bcv<V>(-2.f * zs);
+    s.zs = bcv<V>(zs);
+    s.sh = bcv<V>(shift);
+    s.dr = bcv<V>(dr);
+    s.di = bcv<V>(di);
+    s.ndr = bcv<V>(-dr);
+    s.ndi = bcv<V>(-di);
+    s.el = bcv<V>(-2.f * kLog2e * kRs2 * ell);
+    s.ntl = bcv<V>(-2.f * kRs2 * ell);
     return s;
 }
 
-// gamma_h, E and K of the closed-form step for two energies (packed);
+// gamma_h, E and K of the closed-form step for two energies (packed) or one;
 // stored as (gh, E, -Re K, Im K).
-struct Coef2 {
-    f2 ghx, ghy, ex, ey, nkx, ky;
+template <typename V>
+struct CoefT {
+    V ghx, ghy, ex, ey, nkx, ky;
 };
+typedef CoefT<f2> Coef2;
 
 // from Omega^2 = x + i y and z = zr + i zi
-__device__ __forceinline__ void coef2_core(const Seg2 &s, const f2 x, const f2 y, const f2 zr, const f2 zi,
-                                           Coef2 &c) {
-    const f2 n2 = fma2(x, x, mul2(y, y));     // |Omega|^4
-    const f2 rn = rsqrt2(n2);                 // 1/|Omega|^2
-    const f2 r = mul2(n2, rn);                // |Omega|^2
-    const f2 u = add2(r, make_float2(fabsf(x.x), fabsf(x.y)));  // 2 s^2
-    const f2 ru = rsqrt2(u);
-    const f2 sq = mul2(u, ru);                // sqrt(2) s
-    const f2 yq = mul2(y, ru);                // sqrt(2) y / (2 s)
+template <typename V>
+__device__ __forceinline__ void coef2_core(const SegT<V> &s, const V x, const V y, const V zr, const V zi,
+                                           CoefT<V> &c) {
+    const V n2 = fma2(x, x, mul2(y, y));     // |Omega|^4
+    const V rn = rsqrt2(n2);                 // 1/|Omega|^2
+    const V r = mul2(n2, rn);                // |Omega|^2
+    const V u = add2(r, absv(x));            // 2 s^2
+    const V ru = rsqrt2(u);
+    const V sq = mul2(u, ru);                // sqrt(2) s
+    const V yq = mul2(y, ru);                // sqrt(2) y / (2 s)
     // sqrt(2) Omega on the principal branch (Re Omega >= 0)
-    f2 orr, oi;
-    orr.x = x.x >= 0.f ? sq.x : fabsf(yq.x);
-    oi.x = x.x >= 0.f ? yq.x : copysignf(sq.x, y.x);
-    orr.y = x.y >= 0.f ? sq.y : fabsf(yq.y);
-    oi.y = x.y >= 0.f ? yq.y : copysignf(sq.y, y.y);
+    V orr, oi;
+    principal(x, y, sq, yq, orr, oi);
     // w = z + i Omega and 1/w = iwr - i iwn
-    const f2 wr = fma2(oi, bc2(-kRs2), zr);
-    const f2 wi = fma2(orr, bc2(kRs2), zi);
-    const f2 rw = rcp2(fma2(wr, wr, mul2(wi, wi)));
-    const f2 iwr = mul2(wr, rw), iwn = mul2(wi, rw);
+    const V wr = fma2(oi, bcv<V>(-kRs2), zr);
+    const V wi = fma2(orr, bcv<V>(kRs2), zi);
+    const V rw = rcp2(fma2(wr, wr, mul2(wi, wi)));
+    const V iwr = mul2(wr, rw), iwn = mul2(wi, rw);
     // 1/(2 Omega) = conj(Omega) / (2 |Omega|^2) = i2r - i i2n
-    const f2 t = mul2(rn, bc2(0.5f * kRs2));
-    const f2 i2r = mul2(orr, t), i2n = mul2(oi, t);
+    const V t = mul2(rn, bcv<V>(0.5f * kRs2));
+    const V i2r = mul2(orr, t), i2n = mul2(oi, t);
     // gamma_h = -Delta / w
     c.ghx = fma2(s.ndr, iwr, mul2(s.ndi, iwn));
     c.ghy = fma2(s.dr, iwn, mul2(s.ndi, iwr));
     // E = exp(-2 ell Omega) = eu (cos th + i sin th), th = -2 ell Im Omega
-    const f2 la = mul2(orr, s.el), th = mul2(oi, s.ntl);
-    const f2 eu = make_float2(ex2_approx(la.x), ex2_approx(la.y));
-    f2 sn, cs;
-    Mth<float>::sincos_(th.x, &sn.x, &cs.x);
-    Mth<float>::sincos_(th.y, &sn.y, &cs.y);
+    const V la = mul2(orr, s.el), th = mul2(oi, s.ntl);
+    const V eu = ex2v(la);
+    V sn, cs;
+    sincosv(th, sn, cs);
     c.ex = mul2(eu, cs);
     c.ey = mul2(eu, sn);
     // (1 - E)/(2 Omega) = ccr + i cci with E - 1 = nomr + i ey
-    const f2 nomr = fma2(eu, cs, bc2(-1.f));
-    const f2 nccr = fma2(nomr, i2r, mul2(c.ey, i2n));      // -ccr
-    const f2 cci = fma2(nomr, i2n, mul2(neg2(c.ey), i2r));
+    const V nomr = fma2(eu, cs, bcv<V>(-1.f));
+    const V nccr = fma2(nomr, i2r, mul2(c.ey, i2n));      // -ccr
+    const V cci = fma2(nomr, i2n, mul2(neg2(c.ey), i2r));
     // K = i conj(Delta) (1 - E)/(2 Omega)
     c.nkx = fma2(s.di, nccr, mul2(s.dr, cci));             // -Re K
     c.ky = fma2(s.ndr, nccr, mul2(s.di, cci));             // Im K
 }
 
 // q: the energies' own part of z (Matsubara: eps_n; retarded: E_n)
-template <bool RET>
-__device__ __forceinline__ void coef2(const Seg2 &s, const f2 q, Coef2 &c) {
+template <bool RET, typename V>
+__device__ __forceinline__ void coef2(const SegT<V> &s, const V q, CoefT<V> &c) {
     if constexpr (RET) {
-        const f2 zr = add2(q, s.sh);
+        const V zr = add2(q, s.sh);
         coef2_core(s, fma2(neg2(zr), zr, s.c0), mul2(zr, s.m2), zr, s.zs, c);
     } else {
         coef2_core(s, fma2(q, q, s.c0), mul2(q, s.m2), s.zs, q, c);
@@ -141,13 +180,14 @@ __device__ __forceinline__ void coef2(const Seg2 &s, const f2 q, Coef2 &c) {
 }
 
 // gamma' = gamma_h + (gamma - gamma_h) E / (1 - K (gamma - gamma_h))
-__device__ __forceinline__ void apply2(const Coef2 &c, f2 &gx, f2 &gy) {
-    const f2 dx = sub2(gx, c.ghx), dy = sub2(gy, c.ghy);
-    const f2 nr = fma2(dx, c.ex, mul2(neg2(dy), c.ey));
-    const f2 ni = fma2(dx, c.ey, mul2(dy, c.ex));
-    const f2 dnr = fma2(c.nkx, dx, fma2(c.ky, dy, bc2(1.f)));
-    const f2 dni = fma2(c.nkx, dy, mul2(neg2(c.ky), dx));
-    const f2 rd = rcp2(fma2(dnr, dnr, mul2(dni, dni)));
+template <typename V>
+__device__ __forceinline__ void apply2(const CoefT<V> &c, V &gx, V &gy) {
+    const V dx = sub2(gx, c.ghx), dy = sub2(gy, c.ghy);
+    const V nr = fma2(dx, c.ex, mul2(neg2(dy), c.ey));
+    const V ni = fma2(dx, c.ey, mul2(dy, c.ex));
+    const V dnr = fma2(c.nkx, dx, fma2(c.ky, dy, bcv<V>(1.f)));
+    const V dni = fma2(c.nkx, dy, mul2(neg2(c.ky), dx));
+    const V rd = rcp2(fma2(dnr, dnr, mul2(dni, dni)));
     gx = fma2(fma2(nr, dnr, mul2(ni, dni)), rd, c.ghx);
     gy = fma2(fma2(ni, dnr, mul2(neg2(nr), dni)), rd, c.ghy);
 }
@@ -179,51 +219,52 @@ __device__ __forceinline__ void prop2(const f2 gax, const f2 gay, const f2 gbx, 
 // c2 g1^2 + c1 g1 + c0 = 0 continuous in Delta, g1 = 2 c0 / (sqrt(c1^2 - 4 c2 c0) - c1),
 // with c2 = i ell Delta*/4, c1 = 2 c2 g0 + i ell z - 1, c0 = (c2 g0 + i ell z + 1) g0
 // + i ell Delta (the arithmetic of midpoint_step, packed).
-struct Mid2 {
-    f2 c2x, c2y, ildx, ildy, ell, nell;
+template <typename V>
+struct MidT {
+    V c2x, c2y, ildx, ildy, ell, nell;
 };
+typedef MidT<f2> Mid2;
 
-__device__ __forceinline__ Mid2 mid2(float dr, float di, float ell) {
+template <typename V = f2>
+__device__ __forceinline__ MidT<V> mid2(float dr, float di, float ell) {
     const float q = 0.25f * ell;
-    Mid2 m;
-    m.c2x = bc2(q * di);
-    m.c2y = bc2(q * dr);
-    m.ildx = bc2(-ell * di);
-    m.ildy = bc2(ell * dr);
-    m.ell = bc2(ell);
-    m.nell = bc2(-ell);
+    MidT<V> m;
+    m.c2x = bcv<V>(q * di);
+    m.c2y = bcv<V>(q * dr);
+    m.ildx = bcv<V>(-ell * di);
+    m.ildy = bcv<V>(ell * dr);
+    m.ell = bcv<V>(ell);
+    m.nell = bcv<V>(-ell);
     return m;
 }
 
-__device__ __forceinline__ void midpoint2(const Mid2 &m, const f2 zr, const f2 zi, f2 &gx, f2 &gy) {
-    const f2 c2gx = fma2(m.c2x, gx, mul2(neg2(m.c2y), gy));
-    const f2 c2gy = fma2(m.c2x, gy, mul2(m.c2y, gx));
-    const f2 lzr = mul2(m.ell, zr);
-    const f2 c1x = fma2(bc2(2.f), c2gx, fma2(m.nell, zi, bc2(-1.f)));
-    const f2 c1y = fma2(bc2(2.f), c2gy, lzr);
-    const f2 ux = add2(c2gx, fma2(m.nell, zi, bc2(1.f)));
-    const f2 uy = add2(c2gy, lzr);
-    const f2 c0x = fma2(ux, gx, fma2(neg2(uy), gy, m.ildx));
-    const f2 c0y = fma2(ux, gy, fma2(uy, gx, m.ildy));
-    const f2 ccx = fma2(m.c2x, c0x, mul2(neg2(m.c2y), c0y));
-    const f2 ccy = fma2(m.c2x, c0y, mul2(m.c2y, c0x));
-    const f2 dx = fma2(c1x, c1x, fma2(neg2(c1y), c1y, mul2(bc2(-4.f), ccx)));
-    const f2 dy = fma2(add2(c1x, c1x), c1y, mul2(bc2(-4.f), ccy));
+template <typename V>
+__device__ __forceinline__ void midpoint2(const MidT<V> &m, const V zr, const V zi, V &gx, V &gy) {
+    const V c2gx = fma2(m.c2x, gx, mul2(neg2(m.c2y), gy));
+    const V c2gy = fma2(m.c2x, gy, mul2(m.c2y, gx));
+    const V lzr = mul2(m.ell, zr);
+    const V c1x = fma2(bcv<V>(2.f), c2gx, fma2(m.nell, zi, bcv<V>(-1.f)));
+    const V c1y = fma2(bcv<V>(2.f), c2gy, lzr);
+    const V ux = add2(c2gx, fma2(m.nell, zi, bcv<V>(1.f)));
+    const V uy = add2(c2gy, lzr);
+    const V c0x = fma2(ux, gx, fma2(neg2(uy), gy, m.ildx));
+    const V c0y = fma2(ux, gy, fma2(uy, gx, m.ildy));
+    const V ccx = fma2(m.c2x, c0x, mul2(neg2(m.c2y), c0y));
+    const V ccy = fma2(m.c2x, c0y, mul2(m.c2y, c0x));
+    const V dx = fma2(c1x, c1x, fma2(neg2(c1y), c1y, mul2(bcv<V>(-4.f), ccx)));
+    const V dy = fma2(add2(c1x, c1x), c1y, mul2(bcv<V>(-4.f), ccy));
     // sqrt(2) times the principal square root of dx + i dy
-    const f2 n2 = fma2(dx, dx, mul2(dy, dy));
-    const f2 r = mul2(n2, rsqrt2(n2));
-    const f2 u = add2(r, make_float2(fabsf(dx.x), fabsf(dx.y)));
-    const f2 ru = rsqrt2(u);
-    const f2 sq = mul2(u, ru), yq = mul2(dy, ru);
-    f2 sr, si;
-    sr.x = dx.x >= 0.f ? sq.x : fabsf(yq.x);
-    si.x = dx.x >= 0.f ? yq.x : copysignf(sq.x, dy.x);
-    sr.y = dx.y >= 0.f ? sq.y : fabsf(yq.y);
-    si.y = dx.y >= 0.f ? yq.y : copysignf(sq.y, dy.y);
+    const V n2 = fma2(dx, dx, mul2(dy, dy));
+    const V r = mul2(n2, rsqrt2(n2));
+    const V u = add2(r, absv(dx));
+    const V ru = rsqrt2(u);
+    const V sq = mul2(u, ru), yq = mul2(dy, ru);
+    V sr, si;
+    principal(dx, dy, sq, yq, sr, si);
     // g1 = 2 c0 / den, den = sqrt - c1; 2/den = idx - i idn
-    const f2 denx = fma2(sr, bc2(kRs2), neg2(c1x)), deny = fma2(si, bc2(kRs2), neg2(c1y));
-    const f2 rd = rcp2(mul2(bc2(0.5f), fma2(denx, denx, mul2(deny, deny))));
-    const f2 idx = mul2(denx, rd), idn = mul2(deny, rd);
+    const V denx = fma2(sr, bcv<V>(kRs2), neg2(c1x)), deny = fma2(si, bcv<V>(kRs2), neg2(c1y));
+    const V rd = rcp2(mul2(bcv<V>(0.5f), fma2(denx, denx, mul2(deny, deny))));
+    const V idx = mul2(denx, rd), idn = mul2(deny, rd);
     gx = fma2(c0x, idx, mul2(c0y, idn));
     gy = fma2(c0y, idx, mul2(neg2(c0x), idn));
 }
@@ -315,16 +356,17 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
                 apply2(c, GX[k], GY[k]);
             }
             if constexpr (TAIL) {
-                StepCoef<float> c;
-                step_coef<float>(dr, di, dr * dr + di * di, zr_of(EPT - 1, sh), zi_of(EPT - 1), ell, c);
-                step_apply<float>(c, gt);
+                const SegT<float> s1 = seg2<RET, float>(dr, di, sh, broad, ell);
+                CoefT<float> c;
+                coef2<RET>(s1, zq[EPT - 1], c);
+                apply2(c, gt.x, gt.y);
             }
         } else {
             const Mid2 m = mid2(dr, di, ell);
 #pragma unroll
             for (int k = 0; k < NP; ++k)
                 midpoint2(m, RET ? add2(Q[k], bc2(sh)) : bc2(sh), RET ? bc2(broad) : Q[k], GX[k], GY[k]);
-            if constexpr (TAIL) gt = midpoint_step<float>(mid_seg<float>(dr, di, ell), zr_of(EPT - 1, sh), zi_of(EPT - 1), gt);
+            if constexpr (TAIL) midpoint2(mid2<float>(dr, di, ell), zr_of(EPT - 1, sh), zi_of(EPT - 1), gt.x, gt.y);
         }
     };
     // entry values: the previous sweep's exits (4 taps) or gamma_h at the first sample
@@ -339,9 +381,10 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
                 GY[k] = c.ghy;
             }
             if constexpr (TAIL) {
-                StepCoef<float> c;
-                step_coef<float>(dr, di, dr * dr + di * di, zr_of(EPT - 1, sh), zi_of(EPT - 1), ell, c);
-                gt = c.gh;
+                const SegT<float> s1 = seg2<RET, float>(dr, di, sh, broad, ell);
+                CoefT<float> c;
+                coef2<RET>(s1, zq[EPT - 1], c);
+                gt = C{c.ghx, c.ghy};
             }
         } else {
             float gx[EPT], gy[EPT];
