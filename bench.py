@@ -1,4 +1,5 @@
-"""Benchmark of the Riccati sweep: trajectory-steps/s on one grain.
+"""Benchmark of the Riccati sweep: trajectory-steps/s, FP32 batched against
+the plain FP64 sweep on the same grains.
 
 One step = one pass of the whole hot path over the workload: rotate Delta and
 A onto the lattices, the Riccati sweep (all angle pairs, lines and Matsubara
@@ -6,12 +7,19 @@ energies, propagator and energy sums fused), rotate-back with the
 Fermi-surface average, then gap update, current and free energy.  Boundary
 values carry over from step to step (Delta and A frozen: burn-in sweeps).
 
-Workload: d_{x2-y2} square rotated by 45 deg ([110] edges), side 50 xi0,
-256x256 grid over the bounding box, 128 Fermi angles, t = 0.1, Matsubara
-cutoff 16 pi kB Tc (80 energies), 0.5 flux quanta, kappa = 80; seeded
-synthetic Delta = 0.240792 (1 + 0.05 Z).
+Default workload (c3): 64 seeded grains, discs and random convex polygons of
+radius 10-40 xi0 at grid spacing 0.2 xi0, s or d_{x2-y2} pairing, t uniform in
+[0.05, 0.8] with the Matsubara cutoff 16 pi kB Tc (10-160 energies), 0-5 flux
+quanta, 64-256 Fermi angles; Delta = bulk guess x (1 + 0.05 Z).  The line also
+carries the plain FP64 batch on the same grains (`fp64_plain`), the C-ABI
+end-to-end step with host buffers (`e2e`) and the errors of four grains
+against the FP64 oracle.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+Other workloads: c2 (d_{x2-y2} square rotated by 45 deg, side 50 xi0, 256^2,
+128 angles, t = 0.1, 80 energies, 0.5 flux quanta, kappa = 80), c4, c5,
+annulus (--workload).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c3|c2|c4|c5|annulus]
     python bench.py --impl reference      # the FP64 CPU oracle on this host
 """
 import argparse
@@ -186,6 +194,21 @@ def _sample_clocks_stop(proc, f, path, device_index=0):
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def _profiled_traffic(workload, precision):
+    """DRAM bytes (read + write) of the dominant kernel per sweep from the ncu
+    capture recorded in profiles/sweep_traffic.json for this workload and
+    precision, or None when no capture of the current build is recorded."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
+            entries = json.load(f)
+    except Exception:
+        return None
+    for tr in entries if isinstance(entries, list) else [entries]:
+        if tr.get("precision") == precision and tr.get("workload") == workload:
+            return tr.get("dram_bytes_per_sweep", tr.get("dram_bytes_per_launch"))
+    return None
 
 
 def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16, keep=None):
@@ -445,15 +468,7 @@ def run_ours(args):
     # the same arithmetic in either precision (transcendentals not counted)
     ops = pse * ALG_OPS_PER_PSE[args.stepper]
     achieved = ops / (sweep_ms * 1e-3) / 1e9
-    prof = os.path.join(ROOT, "profiles", "sweep_traffic.json")
-    traffic = None
-    try:
-        with open(prof) as f:
-            tr = json.load(f)
-        if tr.get("precision") == args.precision and tr.get("workload") == workload:
-            traffic = tr.get("dram_bytes_per_launch")
-    except Exception:
-        pass
+    traffic = _profiled_traffic(workload, args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
@@ -495,12 +510,94 @@ def run_ours(args):
     return 0
 
 
+def _c3_members_for_errors(grains, steps):
+    """Members whose outputs are compared with the oracle: the smallest and the
+    largest by trajectory-steps per sweep, then the s-wave and the d-wave member
+    nearest the median size among the rest (discs and polygons both occur)."""
+    order = sorted(range(len(grains)), key=lambda i: steps[i])
+    pick = [order[0], order[-1]]
+    med = steps[order[len(order) // 2]]
+    for pairing in (0, 1):
+        rest = [i for i in order if i not in pick and grains[i][0]["pairing"] == pairing]
+        if rest:
+            pick.append(min(rest, key=lambda i: abs(steps[i] - med)))
+    return pick
+
+
+def _c3_reference_members(grains, steps):
+    """The bounded sample one step of the reference arm sweeps: the members at
+    the 1/8, 3/8 and 5/8 points of the size order (about 2e8 trajectory-steps)."""
+    order = sorted(range(len(grains)), key=lambda i: steps[i])
+    n = len(order)
+    return [order[n // 8], order[(3 * n) // 8], order[(5 * n) // 8]]
+
+
+def _oracle_steps(p):
+    import oracle
+    L = oracle.OracleGeom(p).lines()
+    ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
+    return p["n_energies"] * int(np.sum(2 * (ns + 1)))
+
+
+def _member_outputs(m):
+    o = m.outputs()
+    return {"delta_new": o["delta_new"].cpu().numpy(), "j": o["j"].cpu().numpy(),
+            "F": o["F"].cpu().numpy(), "F_total": o["F_total"]}
+
+
+def _rel_errors(r, o, m):
+    def rel(a, b):
+        return float(np.max(np.abs(a[m] - b[m])) / max(np.max(np.abs(b[m])), 1e-300))
+    return {"delta_new": rel(r["delta_new"], o["delta_new"]), "j": rel(r["j"], o["j"]),
+            "F": rel(r["F"], o["F"]), "F_total": abs(r["F_total"] - o["F_total"]) / abs(o["F_total"])}
+
+
+def run_reference_batch(args):
+    """Reference arm on the batched workload: each step is one FP64 oracle sweep
+    (with outputs) of a fixed bounded sample of the 64 grains."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    grains = W.c3_batch(n_grains=args.grains, seed=3)
+    steps = [_oracle_steps(p) for p, _, _ in grains]
+    sub = _c3_reference_members(grains, steps)
+    geoms = [oracle.OracleGeom(grains[i][0]) for i in sub]
+    n_steps = sum(steps[i] for i in sub)
+    secs = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for g, i in zip(geoms, sub):
+            g.full_sweep(grains[i][1], None, None)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            secs.append(dt)
+    v = n_steps * len(secs) / sum(secs)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = (f"one FP64 oracle sweep with outputs of grains {sub} of the {args.grains} "
+              f"({n_steps} trajectory-steps, {statistics.mean(secs):.2f} s)")
+    line = {"metric": METRIC, "value": v, "unit": "trajectory-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(statistics.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": f"c3_batch_{args.grains}_grains", "sample": sample,
+                       "step": "one bounded sample of the batched workload (3 of its grains)"},
+            "cpu_baseline": {"value": v, "unit": "trajectory-steps/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "trajectory-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args):
     """The batched form: 64 seeded grains (discs and convex polygons, radius
     10-40 xi0, h = 0.2, s/d pairing, t in [0.05, 0.8], 0-5 flux quanta, 64-256
-    angles) swept by one persistent launch per iteration, iterations replayed
-    as captured CUDA graphs; every member's gap update, current and free
-    energy included in a step."""
+    angles) swept by persistent launches fed by one work list, iterations
+    replayed as captured CUDA graphs; every member's gap update, current and
+    free energy included in a step.  Beside the FP32 batch: the plain FP64
+    batch on the same grains, the C-ABI end-to-end step with host buffers, and
+    the errors of four members against the FP64 oracle."""
     import torch
     from paper_2205_15000_b300 import sc
 
@@ -514,11 +611,23 @@ def run_batch(args):
         if args.energy_sum == "ozaki":
             p["energy_sum"] = "ozaki"
             p["n_energies"] = W.ozaki_poles_for_cutoff(p["t"])
-    b = sc.Batch([p for p, _, _ in grains], precision=args.precision)
+    workload = f"c3_batch_{args.grains}_grains" + ("" if args.stepper == "closed" else f"_{args.stepper}") + \
+        ("" if args.energy_sum == "matsubara" else "_ozaki")
+    stream = torch.cuda.current_stream()
+    want_oracle = not args.no_cpu_baseline and rank == 0
+
+    b = sc.Batch([p for p, _, _ in grains], precision=args.precision, energies_per_lane=args.ept)
     for (p, d, _), m in zip(grains, b.members):
         m.set_fields(d)
-    stream = torch.cuda.current_stream()
-    ept = b.autotune(stream)
+    msteps = [m.info.steps_per_sweep for m in b.members]
+    check = _c3_members_for_errors(grains, msteps)
+    # outputs of the checked members after two sweeps from fresh boundary values
+    got = {}
+    if want_oracle:
+        b.run(2, True, stream)
+        torch.cuda.synchronize()
+        got[args.precision] = {i: _member_outputs(b.members[i]) for i in check}
+    ept = b.autotune(stream) if not args.ept else args.ept
     b.run(args.warmup, True, stream)
     torch.cuda.synchronize()
     info = b.info()
@@ -531,55 +640,201 @@ def run_batch(args):
     ksweep = []
     if sampler:
         sampler.start()
+    t_wall = time.perf_counter()
     for i in range(args.steps):
         ev[i][0].record(stream)
         b.run(1, True, stream)
         ev[i][1].record(stream)
-        flush.fill_(float(i))
-        ksweep.append(b.info().ms_sweep)
+        flush.fill_(float(i))  # evict L2 between timed steps (outside the events)
+        ksweep.append(b.info().ms_sweep)  # waits for this step's sweep launches
     torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop() if sampler else None
     total_ms = ranks.max_over_ranks(dist, float(sum(a.elapsed_time(c) for a, c in ev)), dev)
     value = ranks.throughput(info.steps_per_sweep * args.steps, world, total_ms * 1e-3)
+    sweep_ms = statistics.mean(ksweep)
+
+    # end to end through the public API with host buffers: every step uploads all
+    # members' Delta from pinned host memory, sets them (sc_set_fields), runs one
+    # batch iteration (sc_batch_run with outputs) and reads every member's
+    # Delta_new, j and F back (sc_gap_update / sc_current / sc_free_energy into
+    # device staging, then one copy into pinned host memory).  Uploads and
+    # read-backs run on two more streams through double-buffered staging.
+    e2e = None
+    if not args.no_e2e:
+        npt = [p["nx"] * p["ny"] for p, _, _ in grains]
+        off = np.concatenate([[0], np.cumsum(npt)]).astype(np.int64)
+        tot = int(off[-1])
+        h_in = torch.empty((tot, 2), dtype=torch.float64).pin_memory()
+        for (p, d, _), o0 in zip(grains, off[:-1]):
+            h_in[o0:o0 + p["nx"] * p["ny"]] = torch.view_as_real(
+                torch.as_tensor(np.ascontiguousarray(d, np.complex128).reshape(-1)))
+        # outputs of member g at 5 x its first point: Delta_new (complex), j (2 reals), F
+        d_in = [torch.empty((tot, 2), dtype=torch.float64, device=dev) for _ in range(2)]
+        d_out = [torch.empty(5 * tot, dtype=torch.float64, device=dev) for _ in range(2)]
+        h_out = [torch.empty(5 * tot, dtype=torch.float64).pin_memory() for _ in range(2)]
+        cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def e2e_steps(n_steps):
+            ev_in = [torch.cuda.Event() for _ in range(n_steps)]
+            ev_used = [torch.cuda.Event() for _ in range(n_steps)]
+            ev_out = [torch.cuda.Event() for _ in range(n_steps)]
+            ev_read = [torch.cuda.Event() for _ in range(n_steps)]
+            for i in range(n_steps):
+                k = i % 2
+                with torch.cuda.stream(cs_in):
+                    if i >= 2:
+                        cs_in.wait_event(ev_used[i - 2])  # the buffer's previous upload was consumed
+                    d_in[k].copy_(h_in, non_blocking=True)
+                    ev_in[i].record(cs_in)
+                stream.wait_event(ev_in[i])
+                if i >= 2:
+                    stream.wait_event(ev_read[i - 2])  # the output staging was read back
+                flush.fill_(float(i))
+                for m, o0, o1 in zip(b.members, off[:-1], off[1:]):
+                    sc.sc_set_fields(m.h, d_in[k][o0:o1], None, True, stream)
+                ev_used[i].record(stream)
+                sc.sc_batch_run(b.h, 1, True, stream)
+                for m, o0, o1 in zip(b.members, off[:-1], off[1:]):
+                    n, q = int(o1 - o0), 5 * int(o0)
+                    sc.sc_gap_update(m.h, d_out[k][q:q + 2 * n], True, False, stream)
+                    sc.sc_current(m.h, d_out[k][q + 2 * n:q + 4 * n], True, stream)
+                    sc.sc_free_energy(m.h, d_out[k][q + 4 * n:q + 5 * n], True, False, stream)
+                ev_out[i].record(stream)
+                with torch.cuda.stream(cs_out):
+                    cs_out.wait_event(ev_out[i])
+                    h_out[k].copy_(d_out[k], non_blocking=True)
+                    ev_read[i].record(cs_out)
+            t_enq = time.perf_counter()
+            torch.cuda.synchronize()
+            return t_enq
+
+        e2e_steps(3)  # untimed: the copy streams' and the pinned buffers' first use
+        n_e2e = max(5, min(args.steps, 20))
+        t0 = time.perf_counter()
+        t_enq = e2e_steps(n_e2e)
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / n_e2e
+        e2e = {"value": info.steps_per_sweep / (e2e_ms * 1e-3), "unit": "trajectory-steps/s",
+               "h2d_bytes_per_step": int(h_in.numel() * 8), "d2h_bytes_per_step": int(h_out[0].numel() * 8),
+               "ms_per_step": e2e_ms, "host_enqueue_ms_per_step": (t_enq - t0) * 1e3 / n_e2e,
+               "steps": n_e2e}
+    fp32_launches = info.sweep_launches
+    fp32_lane_fill = info.steps_per_sweep / max(info.lane_steps_per_sweep, 1)
+    b.close()
+    del b
+
+    # the plain FP64 batch on the same grains (same work list and launch scheme;
+    # its energies-per-lane bound left at the library's default)
+    fp64 = None
+    if args.precision == "fp32" and not args.no_fp64:
+        b64 = sc.Batch([p for p, _, _ in grains], precision="fp64")
+        for (p, d, _), m in zip(grains, b64.members):
+            m.set_fields(d)
+        b64.run(2, True, stream)  # the first sweep from fresh boundary values, then one replay
+        torch.cuda.synchronize()
+        if want_oracle:
+            got["fp64"] = {i: _member_outputs(b64.members[i]) for i in check}
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.fp64_steps)]
+        k64 = []
+        for a_, c_ in ev64:
+            a_.record(stream)
+            b64.run(1, True, stream)
+            c_.record(stream)
+            flush.fill_(1.0)
+            k64.append(b64.info().ms_sweep)
+        torch.cuda.synchronize()
+        ms64 = sum(a_.elapsed_time(c_) for a_, c_ in ev64) / len(ev64)
+        i64 = b64.info()
+        v64 = i64.steps_per_sweep / (ms64 * 1e-3)
+        sm_max = (clocks or {}).get("sm_max_mhz") or 2032.0
+        pk64 = SM_COUNT_B300 * FP64_LANES_PER_SM * sm_max * 1e6 / 1e9
+        ach64 = (i64.steps_per_sweep // 2) * ALG_OPS_PER_PSE[args.stepper] / (statistics.mean(k64) * 1e-3) / 1e9
+        fp64 = {"value": v64, "unit": "trajectory-steps/s", "ms_per_step": ms64, "steps": len(ev64),
+                "warmup": 2, "energies_per_lane": i64.energies_per_lane, "sweep_launches": i64.sweep_launches,
+                "speedup_fp32_over_fp64": value / v64,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": pk64, "unit": "Gop/s",
+                             "frac": ach64 / pk64, "ms_per_sweep": statistics.mean(k64),
+                             "peak_note": "FP64 pipe 148 SM x 2 lanes/cycle (ncu pipe peak) x max SM clock (derived)"}}
+        b64.close()
+        del b64
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
-    sweep_ms = statistics.mean(ksweep)
     pse = info.steps_per_sweep // 2  # ~ (pair, sample, energy) combinations
     achieved = pse * ALG_OPS_PER_PSE[args.stepper] / (sweep_ms * 1e-3) / 1e9
     lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
     peak_gops = SM_COUNT_B300 * lanes * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
+    traffic = _profiled_traffic(workload, args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"c3_batch_{args.grains}_grains", "grains": args.grains,
+        "config": {"workload": workload, "grains": args.grains,
                    "steps_per_sweep": info.steps_per_sweep, "work_items": info.n_items,
                    "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
-                   "energy_sum": args.energy_sum,
-                   "lane_fill": info.steps_per_sweep / max(info.lane_steps_per_sweep, 1),
-                   "sweep_launches": info.sweep_launches,
+                   "energy_sum": args.energy_sum, "lane_fill": fp32_lane_fill,
+                   "sweep_launches": fp32_launches,
+                   "step": "one batch iteration: every member's rotate, the sweep, rotate-back and outputs",
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                     "frac": achieved / peak_gops, "traffic": None,
-                     "kernel": f"sweep_kernel ({info.sweep_launches} launches back to back per sweep)",
+                     "frac": achieved / peak_gops, "traffic": traffic,
+                     "kernel": f"sweep_kernel ({fp32_launches} launches back to back per sweep)",
                      "ms_per_sweep": sweep_ms,
+                     "ops_per_unit": f"{ALG_OPS_PER_PSE[args.stepper]} FP32 lane-operations per (angle pair, "
+                                     "sample, energy): the optimised closed-form formulation, terms that depend "
+                                     "only on the segment excluded",
                      "peak_note": ("FP32" if args.precision == "fp32" else "FP64")
                      + " lane issue 148 SM x lanes/cycle x max SM clock (derived)"},
-        # per member: (FP32: field conversion,) rotate, rotate-back, outputs; plus
-        # one sweep launch per energies-per-lane class
-        "gpu_launches": ((4 if args.precision == "fp32" else 3) * args.grains
-                         + info.sweep_launches) * args.steps,
+        "fp64_plain": fp64,
+        "e2e": e2e,
+        # per member: (FP32: field conversion,) rotate, rotate-back, outputs and the
+        # final sums; plus one sweep launch per energies-per-lane class
+        "gpu_launches": ((5 if args.precision == "fp32" else 4) * args.grains + fp32_launches) * args.steps,
         "clocks": clocks,
+        "wall_s": t_wall,
     }
+    if want_oracle:
+        import oracle
+        errs, secs, n_steps = {}, 0.0, 0
+        for i in check:
+            p, d, _ = grains[i]
+            g = oracle.OracleGeom(p)
+            mk = g.mask().astype(bool)
+            ex = None
+            t0 = time.perf_counter()
+            for _ in range(2):
+                o = g.full_sweep(d, None, ex)
+                ex = o["exit"]
+            secs += time.perf_counter() - t0
+            n_steps += 2 * msteps[i]
+            errs[str(i)] = {"grain": {"shape": "disc" if p["shape_kind"] == 0 else "polygon",
+                                      "pairing": "s" if p["pairing"] == 0 else "dx2y2", "grid": p["nx"],
+                                      "n_angles": p["n_angles"], "n_energies": p["n_energies"],
+                                      "t": p["t"], "flux_quanta": p["flux_quanta"],
+                                      "steps_per_sweep": msteps[i]}}
+            for prec, res in got.items():
+                errs[str(i)][prec] = _rel_errors(res[i], o, mk)
+        worst = {k: max(errs[str(i)][args.precision][k] for i in check) for k in ("delta_new", "j", "F")}
+        line["errors_vs_fp64_oracle"] = {
+            "members": errs, "worst_" + args.precision: worst,
+            "tolerance": {"delta_new": 1e-5, "j": 1e-4, "F": 1e-4},
+            "within_tolerance": all(worst[k] <= tol for k, tol in (("delta_new", 1e-5), ("j", 1e-4), ("F", 1e-4))),
+            "norm": "max over the grain, relative to the oracle's max; 2 sweeps from fresh boundary values"}
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        line["cpu_baseline"] = {
+            "value": n_steps / secs, "unit": "trajectory-steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"2 FP64 oracle sweeps with outputs of grains {check} of the {args.grains} "
+                      f"(a subset: the smallest, the largest, an s-wave and a d-wave grain; "
+                      f"{n_steps} trajectory-steps, {secs:.1f} s)"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
-
 
 
 # ---------------------------------------------------------------------------
@@ -811,8 +1066,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=256, help="grid side (reduced cases for profiling)")
     ap.add_argument("--angles", type=int, default=128, help="Fermi angles (reduced cases for profiling)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "annulus"],
-                    help="c2: one 256^2 d-wave [110] grain; c3: 64 grains in one batched launch; "
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5", "annulus"],
+                    help="c3 (default): 64 grains swept as one batch; c2: one 256^2 d-wave [110] grain; "
                          "c4: d-wave disc with a vortex (128^2); c5: 1024^2 d-wave square, 20 vortices; "
                          "annulus: d-wave annulus R> 25, R< 10 (256^2), solenoid gauge")
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
@@ -821,6 +1076,10 @@ def main():
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
                     help="energy lanes per line (0: the library's choice)")
     ap.add_argument("--grains", type=int, default=64)
+    ap.add_argument("--ept", type=int, default=0,
+                    help="batch bound on energies per lane (0: chosen by sc_batch_autotune)")
+    ap.add_argument("--no-fp64", action="store_true", help="batch: skip the plain FP64 comparison arm")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="batch: timed steps of the plain FP64 arm")
     ap.add_argument("--ldos", action="store_true", help="time the LDOS sweeps on the c4 grain (64 energies)")
     ap.add_argument("--accel-table", action="store_true",
                     help="iterations of the four accelerators on the examples of App. E's table")
@@ -833,7 +1092,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        return run_reference(args)
+        return run_reference_batch(args) if args.workload == "c3" else run_reference(args)
     if args.accel_table:
         return run_accel_table(args)
     if args.ldos:
