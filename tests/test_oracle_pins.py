@@ -89,6 +89,18 @@ def test_bulk_gap_near_tc_ginzburg_landau():
         assert abs(d / ref - 1) < 3 * one_minus_t + 2e-3
 
 
+@pytest.mark.parametrize("pairing,t,ne,anchor", [(0, 0.5, 16, 0.268717), (1, 0.1, 80, 0.240792),
+                                                 (1, 0.2, 40, 0.240128), (1, 0.05, 160, 0.240871)])
+def test_bulk_gap_anchor_values(pairing, t, ne, anchor):
+    """The truncated bulk gap equation (Eq. gapeq_fixpoint with the regularised
+    normalisation of Eq. gapeq_regularized, energies below the cutoff) solved
+    independently to six decimals for the workloads' temperatures and energy
+    counts (units 2 pi kB Tc; the d-wave value is the amplitude of
+    Delta(phi) = Delta sqrt(2) cos 2 phi).  1024 angles stand in for the
+    continuum angle average."""
+    assert abs(oracle.bulk_gap(pairing, t, ne, 1024) - anchor) < 6e-7
+
+
 def test_bulk_gap_vanishes_at_tc():
     # at t = 1 the right-hand side at Delta = 0 equals D exactly (the
     # regularisation puts Tc where the cutoff sum starts); only rounding is left
@@ -226,6 +238,134 @@ def _ang_line_off(g):
     nl = L["l_hi"] - L["l_lo"] + 1
     N = g.N
     return np.concatenate([[0], np.cumsum([nl[k % g.n_pairs] for k in range(N)])])
+
+
+def _link_shape(kind):
+    """Grain, and the outward normal of the grain at a boundary point P with
+    the part it lies on (None where the normal is ambiguous: polygon vertices)."""
+    if kind == "disc":
+        p = W.disc(12.0, 96, n_angles=64, n_energies=1)
+
+        def normal(P):
+            d = P - np.array([p["disc_cx"], p["disc_cy"]])
+            return d / np.hypot(*d), 0
+        return p, normal
+    if kind == "polygon":
+        rng = np.random.default_rng(11)
+        while True:  # a seeded strictly convex heptagon
+            vx, vy = W.random_convex_polygon(rng, 11.0, 7)
+            e = np.diff(np.stack([vx, vy], axis=1), axis=0, append=[[vx[0], vy[0]]])
+            if np.min(e[:, 0] * np.roll(e[:, 1], -1) - e[:, 1] * np.roll(e[:, 0], -1)) > 1.0:
+                break
+        p = W.polygon(vx, vy, 0.25, n_angles=48, n_energies=1)
+        V = np.stack([vx, vy], axis=1)
+
+        def normal(P):
+            if np.min(np.hypot(*(V - P).T)) < 1e-6:
+                return None, None
+            best, nrm = np.inf, None
+            for i in range(len(V)):
+                a, b = V[i], V[(i + 1) % len(V)]
+                e = b - a
+                s = np.clip(np.dot(P - a, e) / np.dot(e, e), 0.0, 1.0)
+                d = np.hypot(*(a + s * e - P))
+                if d < best:  # counter-clockwise vertices: the outward normal is (e_y, -e_x)
+                    best, nrm = d, np.array([e[1], -e[0]]) / np.hypot(*e)
+            return nrm, 0
+        return p, normal
+    r_out, r_in = 12.0, 5.0
+    p = W.annulus(r_out, r_in, 96, n_angles=64, n_energies=1)
+
+    def normal(P):
+        d = P / np.hypot(*P)
+        # on the hole the grain's outward normal points into the hole
+        return (d, 0) if np.hypot(*P) > 0.5 * (r_out + r_in) else (-d, 1)
+    return p, normal
+
+
+@pytest.mark.parametrize("kind", ["disc", "polygon", "annulus"])
+def test_link_weights_interpolate_affine_exits(kind):
+    """Sec. 3.1 and Fig. riccati_fig_A: the entry value of gamma is the exit
+    value along the specularly reflected incoming direction, interpolated
+    linearly in the Fermi angle and in the lattice-line coordinate.  With exit
+    values affine in (angle index j, lattice line l), f = B j + C l, the 4-tap
+    gather must return B u + C sum_a w_a c_a exactly, where the reflection
+    point, the normal, u = psi N / 2 pi and c_a = (P - O).e_perp(phi_a) / h are
+    recomputed here from circle and edge geometry.  Exchanging the two angle
+    weights or the two line weights of a link breaks the identity (checked
+    below on the same links)."""
+    p, normal = _link_shape(kind)
+    g = oracle.OracleGeom(p)
+    N, npair, h = p["n_angles"], g.n_pairs, p["h"]
+    O = np.array([p["x0"] + 0.5 * p["nx"] * h + p["lattice_ox"] * h,
+                  p["y0"] + 0.5 * p["ny"] * h + p["lattice_oy"] * h])
+    phi = 2 * np.pi * np.arange(N) / N
+    vh = np.stack([np.cos(phi), np.sin(phi)], axis=1)
+    L = g.lines()
+    lk = g.links()
+    chorded = set(zip(L["pair"].tolist(), L["l"].tolist()))
+    line_off = np.concatenate([[0], np.cumsum(np.bincount(L["pair"], minlength=npair))])
+    B, C = 0.731, -1.377
+
+    def lattice_line_ok(pa, l, part):
+        """Lattice line l of pair pa carries a chord whose end (in either
+        direction of travel) lies on `part`."""
+        if (pa, l) not in chorded:
+            return False
+        if kind != "annulus":
+            return True
+        d = abs(np.dot(O + l * h * np.array([-vh[pa, 1], vh[pa, 0]]), np.array([-vh[pa, 1], vh[pa, 0]])))
+        return d < 5.0 - 1e-9 if part == 1 else d < 12.0 - 1e-9
+
+    checked, swap_a_fail, swap_l_fail, A = 0, 0, 0, 0
+    for k in range(N):
+        pk = k % npair
+        epar, eperp = vh[pk], np.array([-vh[pk, 1], vh[pk, 0]])
+        for Lc in range(line_off[pk], line_off[pk + 1]):
+            row = A
+            A += 1
+            s_in = L["smin"][Lc] if k < npair else L["smax"][Lc]
+            P = O + L["l"][Lc] * h * eperp + s_in * epar
+            n, part = normal(P)
+            if n is None:
+                continue
+            v = vh[k]
+            vin = v - 2.0 * np.dot(v, n) * n
+            u = (math.atan2(vin[1], vin[0]) % (2 * np.pi)) * N / (2 * np.pi)
+            j0 = math.floor(u)
+            wa = u - j0
+            cs, ok = [], True
+            for j in (j0, j0 + 1):
+                pa = j % N % npair
+                c = float(np.dot(P - O, np.array([-vh[pa, 1], vh[pa, 0]]))) / h
+                cs.append(c)
+                ok &= all(lattice_line_ok(pa, math.floor(c) + b, part) for b in (0, 1))
+            if not ok:
+                continue
+            want = B * u + C * ((1 - wa) * cs[0] + wa * cs[1])
+            ta, tl, tw = lk["angle"][row], lk["line"][row], lk["w"][row]
+            jj = ta + N * np.round((u - ta) / N)  # unwrapped next to u
+            assert np.all(np.abs(jj - u)[tw > 1e-12] <= 1 + 1e-9)
+            got = float(np.sum(tw * (B * jj + C * tl)))
+            assert abs(got - want) < 1e-10, (kind, k, Lc, got, want)
+            checked += 1
+            # the same gather with the angle weights, or the line weights, exchanged
+            lo_a = jj < u
+            w_a = np.where(lo_a, 1 - wa, wa)
+            sw_a = tw / w_a * np.where(lo_a, wa, 1 - wa)
+            if abs(float(np.sum(sw_a * (B * jj + C * tl))) - want) > 1e-6:
+                swap_a_fail += 1
+            sw_l = tw.copy()
+            for q in (0, 2):  # taps (2a, 2a+1) are the lower and upper line of angle a
+                c = cs[0] if jj[q] < u else cs[1]
+                wl = c - math.floor(c)
+                if 1e-3 < abs(wl - 0.5) < 0.5 - 1e-3 and tw[q] > 0:
+                    sw_l[q], sw_l[q + 1] = tw[q] / (1 - wl) * wl, tw[q + 1] / wl * (1 - wl)
+            if abs(float(np.sum(sw_l * (B * jj + C * tl))) - want) > 1e-6:
+                swap_l_fail += 1
+    assert A == lk["w"].shape[0]
+    assert checked > 0.5 * A, (checked, A)
+    assert swap_a_fail > 0.9 * checked and swap_l_fail > 0.9 * checked, (swap_a_fail, swap_l_fail, checked)
 
 
 # ---------------------------------------------------------------------------
