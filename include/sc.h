@@ -442,11 +442,14 @@ sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rs
  * Limits: n_e <= 256 and max(max_ns, 1) * 32 * ceil(n_e / 32) <= 4 Mi
  * (SC_EINVAL otherwise, with the reason in sc_last_error(NULL)).
  * The first call on each device looks up the device address of the static
- * array (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call uses the same array and leaves its contents behind;
- * nothing in it needs to start at zero.  Calls whose kernels overlap on the GPU
- * (different streams, or several host threads) race on the array: serialise
- * them. */
+ * array (cudaGetSymbolAddress) and loads the kernels of all eight energy
+ * layouts (ceil(n_e / 32) = 1..8), so that no later call loads code or
+ * allocates, whatever its n_e; make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind; nothing in it
+ * needs to start at zero.  Calls whose kernels overlap on the GPU (different
+ * streams, or several host threads) race on the array: serialise them.
+ * SC_ECUDA without a launch when a CUDA error from earlier work is already
+ * pending on the calling thread (the error is left for its owner). */
 sc_status sc_sweep_lines_noalloc(const float *samples, const int32_t *line_slot0,
                                  const int32_t *line_ns, const float *line_len,
                                  const float *entry, int32_t n_lines, int32_t max_ns,

@@ -186,8 +186,12 @@ __global__ void __launch_bounds__(128) sweep_lines_static_kernel(
     }
 }
 
-// Looks up the device address of the scratch array for the current device.
-// Runs once per device (on that device's first call).
+// Looks up the device address of the scratch array for the current device and
+// loads every energy layout's kernel.  Runs once per device (on that device's
+// first call).  Under CUDA's lazy module loading a kernel is otherwise loaded at
+// its first launch, which can allocate device memory for its code and
+// synchronise; querying each instantiation's attributes here moves all of that
+// into the first call.
 sc_status noalloc_setup(int dev, void **ptr, int *sms) {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch_ptr[dev]) {
@@ -196,6 +200,18 @@ sc_status noalloc_setup(int dev, void **ptr, int *sms) {
         if (e != cudaSuccess || !p) {
             sc_internal::set_thread_error("cudaGetSymbolAddress of the static scratch failed");
             return SC_ECUDA;
+        }
+        const void *kernels[8] = {(const void *)sweep_lines_static_kernel<1>, (const void *)sweep_lines_static_kernel<2>,
+                                  (const void *)sweep_lines_static_kernel<3>, (const void *)sweep_lines_static_kernel<4>,
+                                  (const void *)sweep_lines_static_kernel<5>, (const void *)sweep_lines_static_kernel<6>,
+                                  (const void *)sweep_lines_static_kernel<7>, (const void *)sweep_lines_static_kernel<8>};
+        for (const void *k : kernels) {
+            cudaFuncAttributes attr;
+            e = cudaFuncGetAttributes(&attr, k);
+            if (e != cudaSuccess) {
+                sc_internal::set_thread_error("loading the allocation-free sweep kernels failed");
+                return SC_ECUDA;
+            }
         }
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -254,6 +270,12 @@ extern "C" sc_status sc_sweep_lines_noalloc(const float *samples, const int32_t 
     if (warps > n_lines) warps = n_lines;
     const int per_block = warps >= 4 ? 4 : (int)warps;
     const int blocks = (int)(warps / per_block);
+    // an error left by earlier work on this thread is not this call's: report it
+    // without clearing it, and launch nothing
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        sc_internal::set_thread_error("a CUDA error from earlier work is pending on this thread; nothing launched");
+        return SC_ECUDA;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const float4 *sm = (const float4 *)samples;
     const float2 *len = (const float2 *)line_len;
@@ -271,8 +293,9 @@ extern "C" sc_status sc_sweep_lines_noalloc(const float *samples, const int32_t 
 #undef SC_CASE
         default: sc_internal::set_thread_error("bad energy layout"); return SC_EINVAL;
     }
-    if (cudaGetLastError() != cudaSuccess) {
-        sc_internal::set_thread_error("kernel launch failed");
+    const cudaError_t e = cudaGetLastError();  // this launch's own error (none was pending)
+    if (e != cudaSuccess) {
+        sc_internal::set_thread_error(cudaGetErrorString(e));
         return SC_ECUDA;
     }
     return SC_OK;
