@@ -235,18 +235,18 @@ def cpu_oracle_sample(p, delta, aind, n_sweeps=1, angle_subset=16, keep=None):
     threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": steps * n_sweeps / dt, "unit": "trajectory-steps/s", "cores": threads,
             "kind": "oracle",
-            "sample": f"{n_sweeps} FP64 sweep(s) of the same grain and 80 energies with "
-                      f"{angle_subset} of 128 Fermi angles ({steps} steps per sweep), {dt:.2f} s"}
+            "sample": f"{n_sweeps} FP64 sweep(s) of the same grain and {q['n_energies']} energies with "
+                      f"{angle_subset} of {p['n_angles']} Fermi angles ({steps} steps per sweep), {dt:.2f} s"}
 
 
-def _errors_vs_oracle(p, delta, precision, keep):
+def _errors_vs_oracle(p, delta, precision, keep, n_sweeps=2):
     """Max-norm errors of Delta_new, j and F(R) (relative to the oracle's max over
-    the grain) after two sweeps from fresh boundary values, the library in
+    the grain) after n_sweeps sweeps from fresh boundary values, the library in
     `precision` against the FP64 oracle on the same inputs."""
     from paper_2205_15000_b300 import sc
     ctx = sc.Context(p, precision=precision)
     ctx.set_fields(delta)
-    for _ in range(2):
+    for _ in range(n_sweeps):
         ctx.sweep()
     r = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in ctx.outputs().items()}
     o, m = keep["out"], keep["mask"]
@@ -257,7 +257,7 @@ def _errors_vs_oracle(p, delta, precision, keep):
             "F": rel(r["F"], o["F"]),
             "F_total": abs(r["F_total"] - o["F_total"]) / abs(o["F_total"]),
             "tolerance": {"delta_new": 1e-5, "j": 1e-4, "F": 1e-4},
-            "norm": "max over the grain, relative to the oracle's max; 2 sweeps from fresh boundary values"}
+            "norm": f"max over the grain, relative to the oracle's max; {n_sweeps} sweep(s) from fresh boundary values"}
 
 
 def run_reference(args):
@@ -314,6 +314,9 @@ def run_ours(args):
         workload = WORKLOAD if (args.grid, args.angles) == (256, 128) else \
             f"c2_reduced_{args.grid}sq_{args.angles}ang_80eps"
     p["stepper"] = args.stepper
+    if args.adjoint_checkpoint:  # adjoint: forward gamma kept every k samples and recomputed
+        p["adjoint_checkpoint"] = args.adjoint_checkpoint
+        workload += f"_ckpt{args.adjoint_checkpoint}"
     if args.energies:  # another energy count on the same grain (profiling the wide layouts)
         p["n_energies"] = args.energies
         workload += f"_{args.energies}eps"
@@ -500,10 +503,12 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": t_wall,
     }
-    if not args.no_cpu_baseline and args.workload in ("c2", "annulus"):
+    if not args.no_cpu_baseline and (args.workload in ("c2", "annulus") or args.errors):
+        # the large grain: one full oracle sweep (minutes on the host cores), opt-in
+        n_sw = 1 if args.workload == "c5" else 2
         keep = {}
-        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, 2, p["n_angles"], keep)
-        line["errors_vs_fp64_oracle"] = _errors_vs_oracle(p, delta, args.precision, keep)
+        line["cpu_baseline"] = cpu_oracle_sample(p, delta, aind, n_sw, p["n_angles"], keep)
+        line["errors_vs_fp64_oracle"] = _errors_vs_oracle(p, delta, args.precision, keep, n_sw)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -1071,7 +1076,12 @@ def main():
                          "c4: d-wave disc with a vortex (128^2); c5: 1024^2 d-wave square, 20 vortices; "
                          "annulus: d-wave annulus R> 25, R< 10 (256^2), solenoid gauge")
     ap.add_argument("--adjoint", action="store_true", help="add the adjoint sweep (gradient of F) to a step")
+    ap.add_argument("--adjoint-checkpoint", type=int, default=0,
+                    help="adjoint: keep the forward gamma every k samples and recompute (0: park every sample)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--errors", action="store_true",
+                    help="c4/c5: also run the FP64 oracle on the whole grain (c5: one sweep, minutes on "
+                         "the host cores) and report the errors of Delta_new, j and F")
     ap.add_argument("--energies", type=int, default=0, help="energy count (0: the workload's own)")
     ap.add_argument("--lanes", type=int, default=0, choices=[0, 4, 8, 16, 32],
                     help="energy lanes per line (0: the library's choice)")

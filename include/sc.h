@@ -149,6 +149,12 @@ typedef struct {
     const uint8_t *mask;     /* optional [ny][nx] grain mask (1 = inside) that the caller
                                 expects; sc_create returns SC_EINVAL unless it equals the
                                 mask built from the shape (copied, not retained) */
+    int32_t adjoint_checkpoint; /* storage of the forward gamma in the adjoint sweep:
+                                0 (default) parks it at every sample; k >= 2 keeps it at
+                                every k-th sample only and recomputes the k - 1 samples
+                                after each when the reverse pass reaches them (one more
+                                forward step per sample); k >= 2 needs precision FP32 and
+                                the closed-form stepper */
 } sc_params;
 
 typedef struct {
@@ -408,6 +414,35 @@ sc_status sc_debug_images(sc_ctx *ctx, double *images);
    for the stream.  SC_EINVAL for n < 0 or a null pointer with n > 0, SC_ECUDA
    for a failed launch (message in sc_last_error(NULL)). */
 sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, void *stream);
+
+/* ---- index checks ------------------------------------------------------
+ * Engineering aids with no counterpart in the paper (the checks that stand in
+ * for a memory checker).
+ *
+ * sc_debug_validate_tables: checks, on the host, every index of the context's
+ * sweep tables against the size of the table it points into -- each line's
+ * image slots and its rows of the exit buffers, the exit slots of its 4 + 4
+ * boundary taps, each pair's lines and lattice-line records, the lattice
+ * lines' chord ranges -- and stores the number of bad entries in *n_bad (0 for
+ * every table sc_create builds; sc_create itself refuses a context whose
+ * tables fail).  Works on host_only contexts.  SC_EINVAL for NULL arguments.
+ *
+ * sc_debug_corrupt_table: for tests of that validation only, and only on a
+ * host_only context (whose tables never reach a GPU): makes one index of the
+ * host tables out of range -- which = 0 a line's first image slot, 1 a
+ * boundary tap's exit slot, 2 a pair's first lattice-line record.  SC_ESTATE
+ * on a context with device memory, SC_EINVAL for another `which`.
+ *
+ * sc_debug_bounds: the kernels' index-check violations on the current device
+ * since the last reset (reset != 0 clears them after reading) and, in
+ * *checked_build, 1 when this library was compiled with the checks
+ * (libsc_checked.so, -DSC_DEBUG_BOUNDS; a failed check skips the access and
+ * counts), 0 for the regular build, whose count is always 0.  Waits for the
+ * device.  SC_EINVAL for NULL pointers, SC_ECUDA when the counters cannot be
+ * read (message in sc_last_error(NULL)). */
+sc_status sc_debug_validate_tables(const sc_ctx *ctx, int64_t *n_bad);
+sc_status sc_debug_corrupt_table(sc_ctx *ctx, int32_t which);
+sc_status sc_debug_bounds(uint64_t *violations, int32_t *checked_build, int32_t reset);
 
 /* ---- allocation-free line sweep ---------------------------------------
  * No counterpart in the paper: an engineering entry point for callers that

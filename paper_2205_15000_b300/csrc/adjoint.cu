@@ -135,13 +135,13 @@ __global__ void adjoint_rotate_back_kernel(const PairDev *__restrict__ pairs, in
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
             const int l = min(max(iu + bb, pp.l_lo), pp.l_hi);
-            const BackLine Ln = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
+            const BackLine Ln = back_chord_at(bl, grid.n_back, pp.lat0 + (l - pp.l_lo), iv, wv);
             const double wl = bb ? wu : 1.0 - wu;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int m = min(max(iv + c, Ln.m0), Ln.m0 + Ln.ns - 1);
                 const double w = wl * (c ? wv : 1.0 - wv);
-                if (w == 0.0) continue;
+                if (w == 0.0 || !in_bounds((int64_t)Ln.slot0 + (m - Ln.m0), grid.n_slots)) continue;
                 atomic_add4<T>(wimg + Ln.slot0 + (m - Ln.m0), (T)(w * wf0), (T)(w * wf1), (T)(w * wg), (T)(w * wF));
             }
         }
@@ -173,13 +173,13 @@ __global__ void adjoint_ldos_back_kernel(const PairDev *__restrict__ pairs, int3
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
             const int l = min(max(iu + bb, pp.l_lo), pp.l_hi);
-            const BackLine Ln = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
+            const BackLine Ln = back_chord_at(bl, grid.n_back, pp.lat0 + (l - pp.l_lo), iv, wv);
             const double wlin = bb ? wu : 1.0 - wu;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const int m = min(max(iv + c, Ln.m0), Ln.m0 + Ln.ns - 1);
                 const double w = wlin * (c ? wv : 1.0 - wv);
-                if (w == 0.0) continue;
+                if (w == 0.0 || !in_bounds((int64_t)Ln.slot0 + (m - Ln.m0), grid.n_slots)) continue;
                 atomicAdd(&wimg[(int64_t)(Ln.slot0 + (m - Ln.m0)) * n_e + n], (T)(w * gv));
             }
         }
@@ -208,8 +208,11 @@ __global__ void adjoint_rotate_kernel(const LineGeo *__restrict__ geo, const int
                                       double *__restrict__ gdelta, double *__restrict__ gaind) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
-    const LineGeo lg = geo[slot_line[s]];
+    const int32_t Ls = slot_line[s];
+    if (!in_bounds(Ls, grid.n_lines)) return;
+    const LineGeo lg = geo[Ls];
     if (lg.ns == 0) return;  // no sample, no cotangent
+    if (!in_bounds(lg.pair, grid.n_pairs)) return;
     const typename Vec4<T>::type gv = gimg[s];
     const double gdr = (double)gv.x, gdi = (double)gv.y, ga = (double)gv.z;
     if (gdr == 0.0 && gdi == 0.0 && ga == 0.0) return;
@@ -296,5 +299,7 @@ cudaError_t launch_adjoint_rotate(bool fp64, const LineGeo *geo, const int32_t *
                                                         (const float4 *)gimg, gdelta, gaind);
     return cudaGetLastError();
 }
+
+SC_BOUNDS_ACCESSOR(bounds_adjoint_transposes)
 
 }  // namespace scd

@@ -14,6 +14,7 @@ struct AdjointLaunch {
     int32_t *counter;
     void *scratch;             // per warp: [lines][max_ns][2][ne_pad] complex
     int64_t scratch_stride;
+    int64_t scratch_elems;     // complex T elements of the whole scratch
     const void *wimg;          // T4 per slot: cotangents of (Re Sf, Im Sf, Sg, SF)
     void *gimg;                // T4 per slot, out (accumulated): cotangents of (Re, Im of Delta eta, a)
     int32_t first_sweep;       // the differentiated sweep started from homogeneous values
@@ -23,6 +24,8 @@ struct AdjointLaunch {
     int32_t grid_blocks, block_threads;
     int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
     int32_t blocked;           // the grain's energies are split into blocks (items carry the block)
+    int32_t ckpt;              // forward gamma kept every ckpt samples and recomputed (0: parked at
+                               // every sample); FP32 closed-form Matsubara/Ozaki adjoint only
 };
 
 cudaError_t launch_adjoint_sweep(bool fp64, const AdjointLaunch &a, cudaStream_t s);

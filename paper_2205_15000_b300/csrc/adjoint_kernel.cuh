@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include "adjoint.cuh"
+#include "adjoint_x2.cuh"
+#include "bounds.cuh"
 #include "riccati_step.cuh"
 
 namespace scd {
@@ -52,7 +54,7 @@ __device__ __forceinline__ T line_sum(T v, int Lw) {
 
 // BLK: the grain's energies are split into blocks; each item carries its block and
 // the lane's energies are set up per item (once per launch otherwise).
-template <typename T, int EPT, bool RET, int STEP, bool BLK = false>
+template <typename T, int EPT, bool RET, int STEP, bool BLK = false, bool CK = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 1) adjoint_sweep_kernel(AdjointLaunch a) {
     // parked per (sample, energy): 0 = gamma then beta, 1 = local beta cotangent,
     // 2 (retarded) = gamma cotangent handed to the mirror energy's lane
@@ -105,13 +107,21 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
         item = __shfl_sync(FULLM, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
+        if constexpr (sizeof(T) == 4 && !RET && STEP == 0) {
+            // FP32 closed-form Matsubara/Ozaki adjoint: packed energy pairs
+            adjoint_item_x2<EPT, BLK, CK>(a, it, gs, (Cx<float> *)warp_slab, lane);
+            continue;
+        }
         // line group and energy block of this item (one block unless the energies
         // exceed one lane layout)
         const int grp = BLK ? it.y / nb : it.y;
         if constexpr (BLK) energies((it.y - grp * nb) * ne_pad);
-        const int L = gs.groups[(int64_t)grp * G + gi];
-        const bool lv = L >= 0;
-        const LineDev &ln = gs.lines[lv ? L : 0];
+        const int64_t gq = (int64_t)grp * G + gi;
+        int L = in_bounds(gq, (int64_t)gs.n_groups * G) ? gs.groups[gq] : -1;
+        if (L >= 0 && !in_bounds(L, gs.n_lines)) L = -1;
+        const LineDev &ln = gs.lines[L >= 0 ? L : 0];
+        const bool lv = L >= 0 && line_tables_ok(ln, gs.n_slots, gs.n_lines, !a.first_sweep,
+                                                 (int64_t)(slab - (C *)a.scratch), NS * ne_pad, a.scratch_elems);
         const int ns = lv ? ln.ns : 0;  // lines without samples do not enter the loss
         const int nsl = ns > 0 ? ns : 1;
         const int nsteps = ns > 0 ? ns + 1 : 0;
@@ -418,12 +428,12 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? SC_ADJOINT_MIN_BLOCKS : 
     }
 }
 
-template <typename T, bool RET, int STEP, bool BLK = false>
+template <typename T, bool RET, int STEP, bool BLK = false, bool CK = false>
 static cudaError_t adjoint_dispatch(const AdjointLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: adjoint_sweep_kernel<T, E, RET, STEP, BLK><<<grid, block, 0, st>>>(a); break;
+    case E: adjoint_sweep_kernel<T, E, RET, STEP, BLK, CK><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         default: return cudaErrorInvalidValue;
@@ -439,6 +449,14 @@ static cudaError_t adjoint_launch_t(const AdjointLaunch &a, cudaStream_t st) {
         return a.blocked ? adjoint_dispatch<T, false, 1, true>(a, st) : adjoint_dispatch<T, false, 1>(a, st);
     }
     if (a.stepper != 0) return cudaErrorInvalidValue;
+    if (a.ckpt > 0) {  // kept-and-recomputed forward gammas: FP32 Matsubara/Ozaki adjoint only
+        if constexpr (sizeof(T) == 4) {
+            if (a.retarded) return cudaErrorInvalidValue;
+            return a.blocked ? adjoint_dispatch<T, false, 0, true, true>(a, st)
+                             : adjoint_dispatch<T, false, 0, false, true>(a, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (a.retarded) return adjoint_dispatch<T, true, 0>(a, st);
     return a.blocked ? adjoint_dispatch<T, false, 0, true>(a, st) : adjoint_dispatch<T, false, 0>(a, st);
 }

@@ -52,6 +52,8 @@ void dfree(sc_ctx *ctx, void *p) {
 
 namespace {
 
+int64_t count_bad_indices(const scg::Geometry &G);  // defined with sc_debug_validate_tables
+
 using sc_internal::dfree;
 using sc_internal::set_err;
 
@@ -229,6 +231,13 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     gs.groups = pl.d_groups;
     gs.image_in = ctx->d_img_in;
     gs.image_out = ctx->d_img_out;
+    if (pl.n_blocks > 1) {  // each energy block writes its own image; launch_block_sum adds them
+        CK(dalloc(ctx, &pl.d_img_blocks, (size_t)pl.n_blocks * ctx->geo.n_slots * (ctx->fp64 ? 32 : 16)));
+        gs.image_out = pl.d_img_blocks;
+    }
+    gs.n_slots = ctx->geo.n_slots;
+    gs.n_lines = (int32_t)ctx->geo.lines.size();
+    gs.n_groups = pl.n_groups;
     gs.exits[0] = ctx->d_exit[0];
     gs.exits[1] = ctx->d_exit[1];
     gs.energies = nullptr;
@@ -299,8 +308,6 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
                             bool first, int parity, cudaStream_t st) {
     CKS(ensure_scratch(ctx, (size_t)pl.grid_blocks * 4 * (size_t)pl.stride * 2 * ctx->real_bytes));
     CK(cudaMemsetAsync(ctx->d_counter, 0, sizeof(int32_t), st));
-    if (!retarded && pl.n_blocks > 1)  // the energy blocks of a line add into the image
-        CK(cudaMemsetAsync(ctx->d_img_out, 0, (size_t)ctx->geo.n_slots * (ctx->fp64 ? 32 : 16), st));
     scd::SweepLaunch a{};
     a.grains = d_grain;
     a.items = pl.d_items;
@@ -308,6 +315,8 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     a.counter = ctx->d_counter;
     a.scratch = ctx->d_scratch;
     a.scratch_stride = pl.stride;
+    a.scratch_elems = (int64_t)(ctx->scratch_bytes / (2 * ctx->real_bytes));
+    a.n_grains = 1;
     a.energies_per_lane = pl.ept;
     a.first_sweep = first ? 1 : 0;
     a.parity = parity;
@@ -318,6 +327,8 @@ sc_status launch_plan_sweep(sc_ctx *ctx, const Plan &pl, const scd::GrainSweep *
     a.weighted = ctx->d_ewt != nullptr ? 1 : 0;
     a.blocked = !retarded && pl.n_blocks > 1 ? 1 : 0;
     CK(scd::launch_sweep(ctx->fp64, a, st));
+    if (a.blocked)  // the energy blocks' images, added in block order
+        CK(scd::launch_block_sum(ctx->fp64, pl.d_img_blocks, pl.n_blocks, ctx->geo.n_slots, ctx->d_img_out, st));
     return SC_OK;
 }
 
@@ -412,6 +423,11 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         g_create_error = "energy_sum must be SC_SUM_MATSUBARA or SC_SUM_OZAKI";
         return SC_EINVAL;
     }
+    if (p->adjoint_checkpoint != 0 &&
+        (p->adjoint_checkpoint < 2 || p->precision != SC_PREC_FP32 || p->stepper != SC_STEP_CLOSED)) {
+        g_create_error = "adjoint_checkpoint must be 0, or >= 2 with precision FP32 and the closed-form stepper";
+        return SC_EINVAL;
+    }
     // n_energies = 0: the count follows from the energy cutoff
     sc_params resolved = *p;
     if (resolved.n_energies == 0) {
@@ -451,6 +467,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     ctx->n_e = p->n_energies;
     ctx->forced_lanes = p->lanes_per_line;
     ctx->stepper = p->stepper;
+    ctx->adj_ckpt = p->adjoint_checkpoint;
     // energies and weights of the energy sums; D = ln t + t sum_n w_n / eps_n
     // (Matsubara: eps_n = t (n + 1/2), w_n = 1, i.e. 2 sum 1/(2n + 1))
     ctx->energy_sum = p->energy_sum;
@@ -498,6 +515,9 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     gd.gauge = p->gauge;
     gd.flux = p->flux_quanta;
     gd.charge_sign = p->charge_sign;
+    gd.n_slots = G.n_slots;
+    gd.n_lines = (int32_t)G.lines.size();
+    gd.n_pairs = G.n_pairs;
 
     // host tables
     const int P = G.n_pairs;
@@ -558,6 +578,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         }
     }
     const size_t nBack = lback.size();
+    gd.n_back = (int32_t)nBack;
     std::vector<scd::PairDev> pdev(P);
     const double cx = 0.5 + (p->x0 - G.ox) / p->h, cy = 0.5 + (p->y0 - G.oy) / p->h;
     for (int q = 0; q < P; ++q) {
@@ -657,6 +678,11 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         cudaError_t err_ = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice); \
         if (err_ != cudaSuccess) return fail_cuda(err_, "upload " #dst);        \
     } while (0)
+    if (count_bad_indices(G) != 0) {
+        g_create_error = "internal error: an index of the sweep tables is out of range";
+        sc_destroy(ctx);
+        return SC_ESTATE;
+    }
     CA(ctx->d_mask, np);
     CP(ctx->d_mask, G.mask.data(), np);
     CA(ctx->d_ghost, G.ghost.size() * sizeof(int32_t));
@@ -1055,6 +1081,9 @@ sc_status ldos_burnin(sc_ctx *ctx, const double *energies, int32_t n_e, double b
     gs.max_ns = std::max(ctx->geo.max_ns, 1);
     gs.ept = pl->ept;
     gs.n_blocks = 1;
+    gs.n_slots = ctx->geo.n_slots;
+    gs.n_lines = (int32_t)nL;
+    gs.n_groups = pl->n_groups;
     CK(cudaMemcpyAsync(R.d_en, energies, n_e * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(R.d_gs, &gs, sizeof(gs), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(R.d_img, 0, (size_t)ctx->geo.n_slots * n_e * ctx->real_bytes, st));
@@ -1153,6 +1182,7 @@ sc_status sc_ldos_adjoint(sc_ctx *ctx, const double *energies, int32_t n_e, doub
         a.counter = ctx->d_counter;
         a.scratch = d_scr;
         a.scratch_stride = stride;
+        a.scratch_elems = (int64_t)blocks * 4 * stride;
         a.wimg = d_w;
         a.gimg = d_g;
         a.first_sweep = R.last_first ? 1 : 0;
@@ -1233,7 +1263,11 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     }
     const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
     const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_items + 3) / 4));
-    const int64_t stride = 2 * pl.stride;
+    // per line: two rows per sample (gamma then beta; beta cotangent) and, with
+    // checkpoints, one row per kept gamma
+    const int64_t max_ns = std::max(ctx->geo.max_ns, 1);
+    const int64_t lrows = 2 * max_ns + (ctx->adj_ckpt > 0 ? (max_ns + ctx->adj_ckpt - 1) / ctx->adj_ckpt : 0);
+    const int64_t stride = (int64_t)pl.lines_per_warp * lrows * pl.lanes * pl.ept;
     const size_t need = (size_t)blocks * 4 * (size_t)stride * 2 * ctx->real_bytes;
     if (need > ctx->adj_scratch_bytes) {
         dfree(ctx, ctx->d_adj_scratch);
@@ -1277,6 +1311,8 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     a.counter = ctx->d_counter;
     a.scratch = ctx->d_adj_scratch;
     a.scratch_stride = stride;
+    a.ckpt = ctx->adj_ckpt;
+    a.scratch_elems = (int64_t)(ctx->adj_scratch_bytes / (2 * ctx->real_bytes));
     a.wimg = ctx->d_wimg;
     a.gimg = ctx->d_gimg;
     a.first_sweep = ctx->last_first ? 1 : 0;
@@ -1414,6 +1450,85 @@ sc_status sc_debug_images(sc_ctx *ctx, double *images) {
                 images[4 * o + c] = ctx->fp64 ? ((double *)buf.data())[i] : ((float *)buf.data())[i];
             }
     }
+    return SC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// every index of the host tables against the size of its table (see
+// sc_debug_validate_tables)
+int64_t count_bad_indices(const scg::Geometry &G) {
+    int64_t bad = 0;
+    const int64_t nL = (int64_t)G.lines.size(), rows = 2 * nL;
+    auto in = [](int64_t i, int64_t n) { return i >= 0 && i < n; };
+    for (const scg::LineInfo &li : G.lines) {
+        const int64_t nsl = li.ns > 0 ? li.ns : 1;
+        if (!in(li.slot0, G.n_slots) || !in(li.slot0 + nsl - 1, G.n_slots)) ++bad;
+        if (!in(li.pair, G.n_pairs)) ++bad;
+        for (int q = 0; q < 4; ++q) {
+            if (!in(li.fwd[q].slot, rows)) ++bad;
+            if (!in(li.bwd[q].slot, rows)) ++bad;
+        }
+    }
+    for (const scg::PairInfo &pp : G.pairs) {
+        if (pp.n_lines < 0 || !in(pp.line0, nL + 1) || pp.line0 + pp.n_lines > nL) ++bad;
+        const int64_t nlat = (int64_t)pp.l_hi - pp.l_lo + 1;
+        if (nlat < 1 || !in(pp.lat0, (int64_t)G.lats.size()) || pp.lat0 + nlat > (int64_t)G.lats.size()) ++bad;
+    }
+    for (const scg::LatticeLine &lt : G.lats)
+        if (lt.nc < 0 || (lt.nc > 0 && (!in(lt.c0, nL) || lt.c0 + lt.nc > nL))) ++bad;
+    return bad;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_debug_validate_tables(const sc_ctx *ctx, int64_t *n_bad) {
+    if (!ctx || !n_bad) return SC_EINVAL;
+    *n_bad = count_bad_indices(ctx->geo);
+    return SC_OK;
+}
+
+sc_status sc_debug_corrupt_table(sc_ctx *ctx, int32_t which) {
+    if (!ctx) return SC_EINVAL;
+    if (!ctx->host_only) return set_err(ctx, SC_ESTATE, "only host_only contexts can be corrupted");
+    scg::Geometry &G = ctx->geo;
+    if (G.lines.empty() || G.pairs.empty()) return set_err(ctx, SC_ESTATE, "no tables");
+    switch (which) {
+        case 0: G.lines.back().slot0 = (int32_t)G.n_slots; break;
+        case 1: G.lines[0].fwd[2].slot = (int32_t)(2 * G.lines.size()); break;
+        case 2: G.pairs.back().lat0 = (int32_t)G.lats.size(); break;
+        default: return set_err(ctx, SC_EINVAL, "which must be 0, 1 or 2");
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_bounds(uint64_t *violations, int32_t *checked_build, int32_t reset) {
+    g_create_error.clear();
+    if (!violations || !checked_build) return SC_EINVAL;
+#ifdef SC_DEBUG_BOUNDS
+    *checked_build = 1;
+#else
+    *checked_build = 0;
+#endif
+    cudaError_t (*const units[])(unsigned long long *, bool) = {
+        scd::bounds_sweep_f32, scd::bounds_sweep_f64, scd::bounds_adjoint_f32, scd::bounds_adjoint_f64,
+        scd::bounds_adjoint_transposes, scd::bounds_lattice_f32, scd::bounds_kernels};
+    unsigned long long total = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    for (auto f : units) {
+        unsigned long long v = 0;
+        if (e == cudaSuccess) e = f(&v, reset != 0);
+        total += v;
+    }
+    if (e != cudaSuccess) {
+        g_create_error = std::string("reading the index-check counters: ") + cudaGetErrorString(e);
+        return SC_ECUDA;
+    }
+    *violations = total;
     return SC_OK;
 }
 

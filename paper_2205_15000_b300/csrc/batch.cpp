@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -18,6 +19,7 @@
 struct sc_batch {
     std::vector<sc_ctx *> members;
     std::vector<int> member_blocks;  // energy blocks of each member's layout
+    std::vector<Plan *> member_plan; // each member's layout (owned by the member context)
     int blocked = 0;                 // some member splits its energies into blocks
     int device = 0;
     bool fp64 = false;
@@ -37,6 +39,13 @@ struct sc_batch {
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     int32_t *d_counter = nullptr;  // one work counter per class (at most 8)
+    // every member's small kernels in single launches: member tables and offsets
+    // (prefix sums over the members, n + 1 each) of their thread blocks: 256
+    // padded points, 16 lines, 32 grid points per component count 1..4, and
+    // reduction blocks of 256 grid points
+    scd::MemberDev *d_members = nullptr;
+    int64_t *d_off = nullptr;  // [7][n + 1]: pad, slots, back (nc = 1..4), outputs
+    int64_t tot_pad = 0, tot_slots = 0, tot_back[4] = {0, 0, 0, 0}, tot_out = 0;
     int parity = 0;
     bool have_boundary = false;
     int64_t steps_per_sweep = 0;
@@ -128,6 +137,7 @@ sc_status build(sc_batch *b, int ept) {
     free_graphs(b);  // captured graphs refer to the buffers rebuilt here
     std::vector<scd::GrainSweep> gs(b->members.size());
     b->member_blocks.assign(b->members.size(), 1);
+    b->member_plan.assign(b->members.size(), nullptr);
     struct It {
         int cost, grain, group;
     };
@@ -145,7 +155,11 @@ sc_status build(sc_batch *b, int ept) {
         d.lines = c->d_lines;
         d.groups = pl->d_groups;
         d.image_in = c->d_img_in;
-        d.image_out = c->d_img_out;
+        // a blocked member writes one image per energy block (added after the sweep)
+        d.image_out = pl->n_blocks > 1 ? pl->d_img_blocks : c->d_img_out;
+        d.n_slots = c->geo.n_slots;
+        d.n_lines = (int32_t)c->geo.lines.size();
+        d.n_groups = pl->n_groups;
         d.exits[0] = c->d_exit[0];
         d.exits[1] = c->d_exit[1];
         d.energies = nullptr;
@@ -162,6 +176,7 @@ sc_status build(sc_batch *b, int ept) {
         d.ept = pl->ept;
         d.n_blocks = pl->n_blocks;
         b->member_blocks[g] = pl->n_blocks;
+        b->member_plan[g] = pl;
         stride = std::max(stride, pl->stride);
         int64_t steps = 0;
         for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
@@ -228,6 +243,64 @@ sc_status join(sc_batch *b, cudaStream_t st) {
     return SC_OK;
 }
 
+// Member tables of the single-launch per-member kernels (static for the life
+// of the batch: every pointer belongs to a member context).
+sc_status build_member_tables(sc_batch *b) {
+    const size_t n = b->members.size();
+    std::vector<scd::MemberDev> md(n);
+    std::vector<int64_t> off(7 * (n + 1), 0);
+    for (size_t g = 0; g < n; ++g) {
+        sc_ctx *c = b->members[g];
+        scd::MemberDev &m = md[g];
+        std::memset(&m, 0, sizeof m);
+        m.grid = c->grid;
+        m.ghost = c->d_ghost;
+        m.mask = c->d_mask;
+        m.delta = c->d_delta;
+        m.aind = c->d_aind;  // zero while no induced potential is set
+        m.pad0 = c->d_pad0;
+        m.padc = c->d_padc;
+        m.lines = c->d_line_f32;
+        m.slot_line = c->d_slot_line;
+        m.pairs = c->d_pair_f32;
+        m.n_pairs = c->geo.n_pairs;
+        m.back = c->d_back;
+        m.image_in = (float4 *)c->d_img_in;
+        m.image_out = (const float4 *)c->d_img_out;
+        m.acc = c->d_acc;
+        m.t = c->geo.prm.t;
+        const double kappa = c->geo.prm.kappa;
+        m.kappa = kappa > 0.0 && std::isfinite(kappa) ? kappa : 0.0;
+        m.norms = c->norms;
+        m.dnew = c->d_dnew;
+        m.j = c->d_j;
+        m.F = c->d_F;
+        m.sums = c->d_sums;
+        m.partials = c->d_part;
+        const int64_t nx = c->geo.nx, ny = c->geo.ny;
+        const int nc = c->geo.n_comp;
+        m.n_slots = c->geo.n_slots;
+        m.n_pad = (nx + 2) * (ny + 2);
+        off[0 * (n + 1) + g + 1] = (m.n_pad + 255) / 256;     // blocks of 256 padded points
+        off[1 * (n + 1) + g + 1] = ((int64_t)c->geo.lines.size() + 15) / 16;  // blocks of 16 lines
+        for (int k = 1; k <= 4; ++k) off[(1 + k) * (n + 1) + g + 1] = nc == k ? (nx * ny + 31) / 32 : 0;
+        off[6 * (n + 1) + g + 1] = scd::reduce_blocks(nx * ny);
+    }
+    for (int a = 0; a < 7; ++a)
+        for (size_t g = 0; g < n; ++g) off[a * (n + 1) + g + 1] += off[a * (n + 1) + g];
+    b->tot_pad = off[0 * (n + 1) + n];
+    b->tot_slots = off[1 * (n + 1) + n];
+    for (int k = 0; k < 4; ++k) b->tot_back[k] = off[(2 + k) * (n + 1) + n];
+    b->tot_out = off[6 * (n + 1) + n];
+    BCK(cudaMalloc(&b->d_members, n * sizeof(scd::MemberDev)));
+    BCK(cudaMemcpy(b->d_members, md.data(), n * sizeof(scd::MemberDev), cudaMemcpyHostToDevice));
+    BCK(cudaMalloc(&b->d_off, off.size() * sizeof(int64_t)));
+    BCK(cudaMemcpy(b->d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    return SC_OK;
+}
+
+const int64_t *member_off(const sc_batch *b, int a) { return b->d_off + (size_t)a * (b->members.size() + 1); }
+
 }  // namespace
 
 extern "C" {
@@ -239,6 +312,8 @@ sc_status sc_batch_destroy(sc_batch *b) {
     free_plan_buffers(b);
     cudaFree(b->d_scratch);
     cudaFree(b->d_counter);
+    cudaFree(b->d_members);
+    cudaFree(b->d_off);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     free_graphs(b);
@@ -316,6 +391,7 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     int ept = energies_per_lane;
     if (!ept) ept = std::min(8, std::max(4, (max_ne + 31) / 32));
     if (st == SC_OK) st = build(b, ept);
+    if (st == SC_OK) st = build_member_tables(b);
     if (st != SC_OK) {
         std::string why = b->err.empty() ? "device setup failed" : b->err;
         sc_batch_destroy(b);
@@ -337,19 +413,25 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     if (b->failed) return SC_ESTATE;
     BCK(cudaSetDevice(b->device));
     cudaStream_t st = (cudaStream_t)stream;
-    sc_status fs = fork(b, st);
-    if (fs != SC_OK) return fs;
-    for (size_t g = 0; g < b->members.size(); ++g) {
-        sc_ctx *c = b->members[g];
+    const int n = (int)b->members.size();
+    for (sc_ctx *c : b->members)
         if (c->failed) return berr(b, SC_ESTATE, "a member context failed");
-        sc_status s = sc_internal::rotate_fields(c, b->aux[g % sc_batch::kAux]);
-        if (s != SC_OK) return berr(b, s, c->err);
-        if (b->blocked)  // the energy blocks of a line add into the zeroed images
-            BCK(cudaMemsetAsync(c->d_img_out, 0, (size_t)c->geo.n_slots * (c->fp64 ? 32 : 16),
-                                b->aux[g % sc_batch::kAux]));
+    sc_status fs = SC_OK;
+    if (!b->fp64) {
+        // every member's fields onto its lattices: two launches over all members
+        BCK(scd::launch_batch_fields_rotate_f32(b->d_members, member_off(b, 0), b->tot_pad, member_off(b, 1),
+                                                b->tot_slots, n, st));
+    } else {
+        fs = fork(b, st);
+        if (fs != SC_OK) return fs;
+        for (size_t g = 0; g < b->members.size(); ++g) {
+            sc_ctx *c = b->members[g];
+            sc_status s = sc_internal::rotate_fields(c, b->aux[g % sc_batch::kAux]);
+            if (s != SC_OK) return berr(b, s, c->err);
+        }
+        fs = join(b, st);
+        if (fs != SC_OK) return fs;
     }
-    fs = join(b, st);
-    if (fs != SC_OK) return fs;
     BCK(cudaMemsetAsync(b->d_counter, 0, 8 * sizeof(int32_t), st));
     // while a graph is being captured the timing events become external event
     // nodes, so that every replay records them
@@ -366,6 +448,8 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.counter = b->d_counter + k;
         a.scratch = b->d_scratch;
         a.scratch_stride = b->stride;
+        a.scratch_elems = (int64_t)(b->scratch_bytes / (2 * (b->fp64 ? 8 : 4)));
+        a.n_grains = (int32_t)b->members.size();
         a.energies_per_lane = c.ept;
         a.first_sweep = b->have_boundary ? 0 : 1;
         a.parity = b->parity;
@@ -379,19 +463,30 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     }
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
     b->timed = true;
-    fs = fork(b, st);
-    if (fs != SC_OK) return fs;
-    for (size_t g = 0; g < b->members.size(); ++g) {
-        sc_ctx *c = b->members[g];
-        sc_status s = sc_internal::rotate_back(c, b->aux[g % sc_batch::kAux]);
-        if (s != SC_OK) return berr(b, s, c->err);
+    for (size_t g = 0; g < b->members.size(); ++g)
+        if (b->member_blocks[g] > 1)  // the energy blocks' images, added in block order
+            BCK(scd::launch_block_sum(b->fp64, b->member_plan[g]->d_img_blocks, b->member_blocks[g],
+                                      b->members[g]->geo.n_slots, b->members[g]->d_img_out, st));
+    if (!b->fp64) {
+        // the Fermi-surface averages of every member: one launch per component count
+        for (int k = 0; k < 4; ++k)
+            BCK(scd::launch_batch_rotate_back_f32(b->d_members, member_off(b, 2 + k), b->tot_back[k], k + 1, n, st));
+    } else {
+        fs = fork(b, st);
+        if (fs != SC_OK) return fs;
+        for (size_t g = 0; g < b->members.size(); ++g) {
+            sc_status s = sc_internal::rotate_back(b->members[g], b->aux[g % sc_batch::kAux]);
+            if (s != SC_OK) return berr(b, s, b->members[g]->err);
+        }
+        fs = join(b, st);
+        if (fs != SC_OK) return fs;
+    }
+    for (sc_ctx *c : b->members) {
         c->cur = b->parity ^ 1;
         c->have_boundary = true;
         c->have_sweep = true;
         c->have_outputs = false;
     }
-    fs = join(b, st);
-    if (fs != SC_OK) return fs;
     b->parity ^= 1;
     b->have_boundary = true;
     return SC_OK;
@@ -402,16 +497,9 @@ static sc_status iteration(sc_batch *b, int with_outputs, cudaStream_t st) {
     sc_status s = sc_batch_sweep(b, st);
     if (s != SC_OK) return s;
     if (with_outputs) {
-        s = fork(b, st);
-        if (s != SC_OK) return s;
-        for (size_t g = 0; g < b->members.size(); ++g) {
-            sc_ctx *c = b->members[g];
-            // computes Delta_new, j, F on the device
-            s = sc_gap_update(c, nullptr, nullptr, 1, b->aux[g % sc_batch::kAux]);
-            if (s != SC_OK) return berr(b, s, c->err);
-        }
-        s = join(b, st);
-        if (s != SC_OK) return s;
+        // Delta_new, j, F and the grid sums of every member in two launches
+        BCK(scd::launch_batch_outputs(b->d_members, member_off(b, 6), b->tot_out, (int)b->members.size(), st));
+        for (sc_ctx *c : b->members) c->have_outputs = true;
     }
     return SC_OK;
 }

@@ -21,6 +21,7 @@ struct Plan {
     int32_t n_items = 0;                 // n_groups x n_blocks work items
     int2 *d_items = nullptr;             // (0, group x n_blocks + block), longest first: single-context launches
     scd::GrainSweep *d_grain = nullptr;  // descriptor of the context's Matsubara sweep
+    void *d_img_blocks = nullptr;        // n_blocks > 1: one image per energy block (n_blocks x n_slots)
     int grid_blocks = 0;
     int64_t stride = 0;                  // scratch elements (complex) per warp
 };
@@ -32,6 +33,7 @@ struct sc_ctx {
     int n_e = 0;
     int forced_lanes = 0;
     int stepper = 0;  // sc_stepper
+    int adj_ckpt = 0;  // adjoint: forward gamma kept every adj_ckpt samples (0: every sample)
     int energy_sum = 0;  // sc_energy_sum
     std::vector<double> eps, ewt;  // energies and weights of the energy sums (host)
     double *d_eps = nullptr, *d_ewt = nullptr;  // on the device for Ozaki sums, else nullptr

@@ -57,7 +57,10 @@ __global__ void rotate_kernel(const LineGeo *__restrict__ geo, const int32_t *__
                               const double *__restrict__ aind, typename Vec4<T>::type *out) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_slots) return;
-    const LineGeo lg = geo[slot_line[s]];
+    const int32_t Ls = slot_line[s];
+    if (!in_bounds(Ls, grid.n_lines)) return;
+    const LineGeo lg = geo[Ls];
+    if (!in_bounds(lg.pair, grid.n_pairs)) return;
     const PairDev pp = pairs[lg.pair];
     const double h = grid.h;
     const double sc = lg.ns > 0 ? (double)(lg.m0 + (int)(s - lg.slot0)) * h : lg.smid;
@@ -170,12 +173,12 @@ __global__ void rotate_back_kernel(const PairDev *__restrict__ pairs, int32_t n_
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
-                const BackLine L = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
+                const BackLine L = back_chord_at(bl, grid.n_back, pp.lat0 + (l - pp.l_lo), iv, wv);
                 const double wl = b ? wu : 1.0 - wu;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const int m = min(max(iv + c, L.m0), L.m0 + L.ns - 1);
-                    const typename Vec4<T>::type s = img[L.slot0 + (m - L.m0)];
+                    const typename Vec4<T>::type s = ld_chk(img, (int64_t)L.slot0 + (m - L.m0), grid.n_slots);
                     const double w = wl * (c ? wv : 1.0 - wv);
                     x0 += w * (double)s.x;
                     x1 += w * (double)s.y;
@@ -257,15 +260,15 @@ __global__ void ldos_back_kernel(const PairDev *__restrict__ pairs, int32_t n_pa
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int l = min(max(iu + b, pp.l_lo), pp.l_hi);
-                const BackLine L = back_chord(bl, bl[pp.lat0 + (l - pp.l_lo)], iv, wv);
+                const BackLine L = back_chord_at(bl, grid.n_back, pp.lat0 + (l - pp.l_lo), iv, wv);
                 const double wl = b ? wu : 1.0 - wu;
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const int m = min(max(iv + c, L.m0), L.m0 + L.ns - 1);
                     const int64_t sl = (int64_t)(L.slot0 + (m - L.m0)) * n_e;
                     const double w = wl * (c ? wv : 1.0 - wv);
-                    xn += w * (double)img[sl + n];
-                    xm += w * (double)img[sl + nm];
+                    xn += w * (double)ld_chk(img, sl + n, grid.n_slots * n_e);
+                    xm += w * (double)ld_chk(img, sl + nm, grid.n_slots * n_e);
                 }
             }
             acc += pp.wb * xn + pp.wa * xm;
@@ -306,15 +309,15 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return s;
 }
 
-__global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
-                               const double *__restrict__ acc, const double *__restrict__ delta,
-                               const double *__restrict__ aind, double t, CompNorm normD, double kappa,
-                               double *__restrict__ dn, double *__restrict__ jo,
-                               double *__restrict__ F, double *__restrict__ partials) {
+__device__ __forceinline__ void outputs_block(const GridDev &grid, const uint8_t *__restrict__ mask,
+                                              const double *__restrict__ acc, const double *__restrict__ delta,
+                                              const double *__restrict__ aind, double t, const CompNorm &normD,
+                                              double kappa, double *__restrict__ dn, double *__restrict__ jo,
+                                              double *__restrict__ F, double *__restrict__ partials, int64_t blk) {
     __shared__ double sh[32];
     const int nx = grid.nx, ny = grid.ny;
     const int64_t npts = (int64_t)nx * ny;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t idx = blk * blockDim.x + threadIdx.x;
     double num = 0, den = 0, fs = 0, bad = 0;
     if (idx < npts) {
         if (!mask[idx]) {
@@ -365,7 +368,7 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
     const double s2 = block_sum(fs, sh);
     const double s3 = block_sum(bad, sh);
     if (threadIdx.x == 0) {  // per-block partials, summed in block order by final_sums_kernel
-        double *pb = partials + 4 * (int64_t)blockIdx.x;
+        double *pb = partials + 4 * blk;
         pb[0] = s0;
         pb[1] = s1;
         pb[2] = s2;
@@ -373,10 +376,18 @@ __global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
     }
 }
 
+__global__ void outputs_kernel(GridDev grid, const uint8_t *__restrict__ mask,
+                               const double *__restrict__ acc, const double *__restrict__ delta,
+                               const double *__restrict__ aind, double t, CompNorm normD, double kappa,
+                               double *__restrict__ dn, double *__restrict__ jo,
+                               double *__restrict__ F, double *__restrict__ partials) {
+    outputs_block(grid, mask, acc, delta, aind, t, normD, kappa, dn, jo, F, partials, blockIdx.x);
+}
+
 // Deterministic completion of a block reduction: slot k of out = the sum over
 // blocks of partials[b][k], in a fixed order (strided per thread, then a fixed tree).
-__global__ void final_sums_kernel(const double *__restrict__ partials, int nblocks, int nslots,
-                                  double *__restrict__ out) {
+__device__ __forceinline__ void final_sums_block(const double *__restrict__ partials, int nblocks, int nslots,
+                                                 double *__restrict__ out) {
     __shared__ double sh[32];
     for (int k = 0; k < nslots; ++k) {
         double v = 0.0;
@@ -384,6 +395,32 @@ __global__ void final_sums_kernel(const double *__restrict__ partials, int nbloc
         const double tot = block_sum(v, sh);
         if (threadIdx.x == 0) out[k] = tot;
     }
+}
+
+__global__ void final_sums_kernel(const double *__restrict__ partials, int nblocks, int nslots,
+                                  double *__restrict__ out) {
+    final_sums_block(partials, nblocks, nslots, out);
+}
+
+// Every batch member's outputs in one launch (blocks of 256 grid points over all
+// members, the member found by bisection of the block offsets), then one block
+// per member completes its sums in the same fixed order as a single context.
+__global__ void batch_outputs_kernel(const MemberDev *__restrict__ m, const int64_t *__restrict__ off, int n) {
+    __shared__ MemberDev M;
+    const int64_t blk = batch_member(m, off, n, M);
+    outputs_block(M.grid, M.mask, M.acc, M.delta, M.aind, M.t, M.norms, M.kappa, M.dnew, M.j, M.F, M.partials, blk);
+}
+
+__global__ void batch_final_sums_kernel(const MemberDev *__restrict__ m, const int64_t *__restrict__ off) {
+    const MemberDev &M = m[blockIdx.x];
+    final_sums_block(M.partials, (int)(off[blockIdx.x + 1] - off[blockIdx.x]), 4, M.sums);
+}
+
+cudaError_t launch_batch_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks, int n,
+                                 cudaStream_t st) {
+    batch_outputs_kernel<<<(unsigned)n_blocks, 256, 0, st>>>(members, off_blocks, n);
+    batch_final_sums_kernel<<<(unsigned)n, 256, 0, st>>>(members, off_blocks);
+    return cudaGetLastError();
 }
 
 int reduce_blocks(int64_t npts) { return (int)((npts + 255) / 256); }
@@ -522,5 +559,31 @@ cudaError_t launch_max_diff(int64_t n, const void *a, const void *b, bool fp64, 
                                                   (unsigned long long *)out);
     return cudaGetLastError();
 }
+
+// Blocked sweep images: each slot's four sums added over the energy blocks in
+// block order (grid-stride over the slots; one thread per slot and component).
+template <typename T>
+__global__ void block_sum_kernel(const T *__restrict__ blocks, int nb, int64_t n, T *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T s = blocks[i];
+        for (int k = 1; k < nb; ++k) s += blocks[(int64_t)k * n + i];
+        out[i] = s;
+    }
+}
+
+cudaError_t launch_block_sum(bool fp64, const void *blocks, int nb, int64_t n_slots, void *out, cudaStream_t st) {
+    const int64_t n = 4 * n_slots;
+    const int bs = 256;
+    int64_t g = (n + bs - 1) / bs;
+    if (g > 65536) g = 65536;
+    if (g < 1) g = 1;
+    if (fp64)
+        block_sum_kernel<double><<<(unsigned)g, bs, 0, st>>>((const double *)blocks, nb, n, (double *)out);
+    else
+        block_sum_kernel<float><<<(unsigned)g, bs, 0, st>>>((const float *)blocks, nb, n, (float *)out);
+    return cudaGetLastError();
+}
+
+SC_BOUNDS_ACCESSOR(bounds_kernels)
 
 }  // namespace scd

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bounds.cuh"
+
 namespace scd {
 
 // One trajectory line of an angle pair, as the sweep kernel reads it.
@@ -74,6 +76,18 @@ __device__ __forceinline__ BackLine back_chord(const BackLine *__restrict__ bl, 
     return best;
 }
 
+// back_chord of record idx of the rotate-back table (n_back records); in the
+// bounds-checked build an index outside the table gives the first record
+template <typename F>
+__device__ __forceinline__ BackLine back_chord_at(const BackLine *__restrict__ bl, int32_t n_back, int64_t idx, int iv,
+                                                  F fv) {
+    if (!in_bounds(idx, n_back)) idx = 0;
+    const BackLine L = bl[idx];
+    if (L.more >= 0 && !(in_bounds(L.more, n_back) && in_bounds((int64_t)L.more + bl[L.more].more - 1, n_back)))
+        return bl[0];
+    return back_chord(bl, L, iv, fv);
+}
+
 struct GridDev {
     int32_t nx, ny;
     double h, x0, y0, ox, oy;
@@ -84,6 +98,11 @@ struct GridDev {
     int32_t gauge;       // sc_gauge
     int32_t charge_sign;
     int32_t n_comp;      // order-parameter components; Delta is [n_comp][ny][nx] complex
+    // table sizes (the bounds-checked build compares indices with them)
+    int64_t n_slots;     // image slots
+    int32_t n_lines;     // chords (lines of the sweep)
+    int32_t n_pairs;     // angle pairs
+    int32_t n_back;      // rotate-back records
 };
 
 // FP32 production path: lattice coordinates in fixed point (2^-40 grid units),
@@ -129,6 +148,10 @@ struct GrainSweep {
     int32_t ept;               // energies per lane (equals the launch's EPT)
     int32_t n_blocks;          // energy blocks of ne_pad energies: work item y of the grain is
                                // line group y / n_blocks with the energies of block y % n_blocks
+    int64_t n_slots;           // image slots; a blocked sweep's block k writes its sums at
+                               // image_out + k n_slots
+    int32_t n_lines;           // lines of the grain (exit rows: 2 n_lines)
+    int32_t n_groups;          // line groups (groups holds n_groups x lines_per_warp entries)
 };
 
 // One persistent launch over the work items (grain, line group) of any number
@@ -140,6 +163,8 @@ struct SweepLaunch {
     int32_t *counter;
     void *scratch;             // per-warp slab of parked gammas
     int64_t scratch_stride;    // complex T elements per warp (>= G * max_ns * ne_pad of every grain)
+    int64_t scratch_elems;     // complex T elements of the whole scratch
+    int32_t n_grains;          // entries of grains
     int32_t energies_per_lane; // EPT (template)
     int32_t first_sweep;       // start every line from the homogeneous solution
     int32_t parity;            // which exit buffer holds the previous sweep's values
@@ -147,8 +172,8 @@ struct SweepLaunch {
     int32_t grid_blocks, block_threads;
     int32_t stepper;           // 0 closed-form step, 1 implicit midpoint rule
     int32_t weighted;          // Matsubara mode: weighted energy sums (grains carry mats_w)
-    int32_t blocked;           // some grain splits its energies into blocks (its image is zeroed
-                               // before the launch and its blocks add into it)
+    int32_t blocked;           // some grain splits its energies into blocks (each block writes its
+                               // own partial image; launch_block_sum adds them in block order)
 };
 
 // launchers (return cudaError_t)
@@ -157,6 +182,10 @@ cudaError_t launch_rotate(bool fp64, const LineGeo *geo, const int32_t *slot_lin
                           const double *delta, const double *aind, void *image_in,
                           cudaStream_t s);
 cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
+// Image of a blocked sweep: out[s] = sum over k = 0 .. nb-1, in this order, of
+// blocks[k n_slots + s] (four values per slot, FP64 or FP32), so the result does
+// not depend on the order in which the blocks' work items ran.
+cudaError_t launch_block_sum(bool fp64, const void *blocks, int nb, int64_t n_slots, void *out, cudaStream_t st);
 // the FP64 device reciprocal and reciprocal square root of the sweep on n values
 cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s);
 // FP32 production path
@@ -190,6 +219,76 @@ int reduce_blocks(int64_t npts);
 struct CompNorm {
     double D[4];
 };
+
+// One batch member's tables and buffers for the per-member kernels of a batch
+// iteration (FP32 lattice transfers, outputs), so that one launch serves every
+// member.  aind always points at the member's induced potential (zero while
+// none is set); kappa is 0 when the member has no magnetic energy term.
+struct MemberDev {
+    GridDev grid;
+    const int32_t *ghost;
+    const uint8_t *mask;
+    const double *delta, *aind;
+    float4 *pad0;
+    float2 *padc;
+    const LineF32 *lines;
+    const int32_t *slot_line;
+    const PairF32 *pairs;
+    int32_t n_pairs;
+    const BackLine *back;
+    float4 *image_in;
+    const float4 *image_out;
+    double *acc;
+    double t, kappa;
+    CompNorm norms;
+    double *dnew, *j, *F, *sums, *partials;
+    int64_t n_slots, n_pad;  // image slots; padded grid points (nx + 2)(ny + 2)
+};
+
+#ifdef __CUDACC__
+// A block's member of a batch: the member whose block range [off[g], off[g + 1])
+// holds the block (bisection over the n + 1 offsets; empty ranges are skipped),
+// its table copied to the shared `sh` by the block's threads.  Returns the
+// block's index within the member.  All threads of the block must call it.
+__device__ __forceinline__ int64_t batch_member(const MemberDev *__restrict__ m, const int64_t *__restrict__ off,
+                                                int n, MemberDev &sh) {
+    __shared__ int g_sh;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n;  // off[lo] <= b < off[hi]
+        const int64_t b = blockIdx.x;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= b) lo = mid;
+            else hi = mid;
+        }
+        g_sh = lo;
+    }
+    __syncthreads();
+    const int g = g_sh;
+    constexpr int words = (int)(sizeof(MemberDev) / sizeof(int));
+    static_assert(sizeof(MemberDev) % sizeof(int) == 0, "MemberDev is copied as words");
+    const int *src = (const int *)(m + g);
+    int *dst = (int *)&sh;
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    return (int64_t)blockIdx.x - off[g];
+}
+#endif
+
+// Batch iterations: every member's FP32 field conversion and rotation (off_*:
+// prefix sums over the members, n + 1 entries, of their blocks of 256 padded
+// points and of 16 lines), rotate-back of the members with nc components
+// (off_blocks: prefix of blocks of 32 grid points, zero for other members), and
+// outputs (off_blocks: prefix of reduction blocks of 256 grid points).  Each
+// block serves one member and holds its table in shared memory.
+cudaError_t launch_batch_fields_rotate_f32(const MemberDev *members, const int64_t *off_pad, int64_t pad_blocks,
+                                           const int64_t *off_lines, int64_t line_blocks, int n, cudaStream_t st);
+cudaError_t launch_batch_rotate_back_f32(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                         int nc, int n, cudaStream_t st);
+cudaError_t launch_batch_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks, int n,
+                                 cudaStream_t st);
+
+
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,
                            const double *delta, const double *aind, double t, const CompNorm &normD,
                            double kappa, double *delta_new, double *j, double *F,

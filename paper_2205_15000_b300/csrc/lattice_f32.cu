@@ -27,12 +27,10 @@ __device__ __forceinline__ void split_fixed(int64_t v, int &cell, float &frac) {
 // grid (nx+2) x (ny+2): each padded point takes the values of its nearest grain
 // point (the ghost map), zero where it has none, so the rotation gathers its
 // bilinear stencil directly
-__global__ void fields_f32_kernel(GridDev grid, const int32_t *__restrict__ ghost, const double2 *__restrict__ delta,
-                                  const double2 *__restrict__ aind, float4 *__restrict__ pad0,
-                                  float2 *__restrict__ padc) {
+__device__ __forceinline__ void fields_f32_point(const GridDev &grid, const int32_t *__restrict__ ghost,
+                                                 const double2 *__restrict__ delta, const double2 *__restrict__ aind,
+                                                 float4 *__restrict__ pad0, float2 *__restrict__ padc, int64_t b) {
     const int64_t npad = (int64_t)(grid.nx + 2) * (grid.ny + 2);
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= npad) return;
     const int64_t np = (int64_t)grid.nx * grid.ny;
     const int g = ghost[b];
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -57,6 +55,14 @@ __global__ void fields_f32_kernel(GridDev grid, const int32_t *__restrict__ ghos
     }
 }
 
+__global__ void fields_f32_kernel(GridDev grid, const int32_t *__restrict__ ghost, const double2 *__restrict__ delta,
+                                  const double2 *__restrict__ aind, float4 *__restrict__ pad0,
+                                  float2 *__restrict__ padc) {
+    const int64_t npad = (int64_t)(grid.nx + 2) * (grid.ny + 2);
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < npad) fields_f32_point(grid, ghost, delta, aind, pad0, padc, b);
+}
+
 cudaError_t launch_fields_f32(const GridDev &grid, const int32_t *ghost, const double *delta, const double *aind,
                               float4 *pad0, float2 *padc, cudaStream_t st) {
     const int64_t npad = (int64_t)(grid.nx + 2) * (grid.ny + 2);
@@ -66,84 +72,103 @@ cudaError_t launch_fields_f32(const GridDev &grid, const int32_t *ghost, const d
     return cudaGetLastError();
 }
 
-// one thread per image slot: bilinear Delta and A_ind at the sample, nearest
-// grain point for stencil points outside the grain; GAUGE (sc_gauge) selects
-// how A_ext enters: the symmetric gauge's per-line constant, or the landau /
-// solenoid potential at the sample
+// One warp per line: bilinear Delta and A_ind at the line's samples (lanes take
+// samples lane, lane + 32, ..., whose stencils neighbour each other) from the
+// ghost-filled padded grid, which holds the nearest grain point's values
+// wherever a stencil point with a nonzero weight can fall; GAUGE (sc_gauge)
+// selects how A_ext enters: the symmetric gauge's per-line constant, or the
+// landau / solenoid potential at the sample.  The fourth value of a slot is 0
+// (the bounds-checked build counts a stencil point with a nonzero weight and no
+// grain neighbour as a violation).
 template <int GAUGE>
-__global__ void rotate_f32_kernel(const LineF32 *__restrict__ lines, const int32_t *__restrict__ slot_line,
-                                  int64_t n_slots, const PairF32 *__restrict__ pairs, GridDev grid,
-                                  const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
-                                  const float2 *__restrict__ padc, float4 *__restrict__ out) {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n_slots) return;
-    const LineF32 ln = lines[slot_line[s]];
-    const PairF32 &pp = pairs[ln.pair];
-    const int q = (int)(s - ln.slot0);
-    int i0, j0;
-    float fx, fy;
-    split_fixed(ln.gx0 + (int64_t)q * pp.dx, i0, fx);
-    split_fixed(ln.gy0 + (int64_t)q * pp.dy, j0, fy);
-    float4 o = make_float4(0.f, 0.f, 0.f, 1.f);
-    if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
-        const int px = grid.nx + 2;
-        const int base = (j0 + 1) * px + (i0 + 1);
-        const float4 p00 = pad0[base], p10 = pad0[base + 1], p01 = pad0[base + px], p11 = pad0[base + px + 1];
-        const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
-        const float dr = w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x;
-        const float di = w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y;
-        const float ax = w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z;
-        const float ay = w00 * p00.w + w10 * p10.w + w01 * p01.w + w11 * p11.w;
-        o.x = pp.eta * dr;
-        o.y = pp.eta * di;
-        // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
-        const int64_t npad = (int64_t)px * (grid.ny + 2);
-        for (int c = 1; c < grid.n_comp; ++c) {
-            const float2 *pc = padc + (c - 1) * npad;
-            const float2 e00 = pc[base], e10 = pc[base + 1], e01 = pc[base + px], e11 = pc[base + px + 1];
-            o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
-            o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
-        }
-        // a stencil point without a grain neighbour (ghost -1) only occurs with zero weight
-        const int g00 = ghost[base], g10 = ghost[base + 1], g01 = ghost[base + px], g11 = ghost[base + px + 1];
-        float az = ln.aext;
-        if (GAUGE != 0) {
-            // landau and solenoid gauges: A_ext at the sample, from its exact
-            // fixed-point offset to the gauge origin
-            const float sc = (float)(grid.h / (double)(1ll << kFixBits));  // fixed-point unit times h
-            const float xr = (float)(ln.gx0 + (int64_t)q * pp.dx - grid.gfx) * sc;
-            const float yr = (float)(ln.gy0 + (int64_t)q * pp.dy - grid.gfy) * sc;
-            float axe, aye;
-            if (GAUGE == 2) {
-                const float c = 0.5f * (float)grid.flux / (xr * xr + yr * yr);
-                axe = -c * yr;
-                aye = c * xr;
-            } else {
-                axe = -(float)grid.bfield * yr;
-                aye = 0.f;
+__device__ __forceinline__ void rotate_f32_line(const LineF32 &ln, const PairF32 &pp, const GridDev &grid,
+                                                const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
+                                                const float2 *__restrict__ padc, float4 *__restrict__ out, int lane) {
+    const int nsl = ln.ns > 0 ? ln.ns : 1;
+    if (!(in_bounds(ln.slot0, grid.n_slots) && in_bounds((int64_t)ln.slot0 + nsl - 1, grid.n_slots))) return;
+    const int px = grid.nx + 2;
+    const int64_t npad = (int64_t)px * (grid.ny + 2);
+    for (int q = lane; q < nsl; q += 32) {
+        int i0, j0;
+        float fx, fy;
+        split_fixed(ln.gx0 + (int64_t)q * pp.dx, i0, fx);
+        split_fixed(ln.gy0 + (int64_t)q * pp.dy, j0, fy);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
+            const int base = (j0 + 1) * px + (i0 + 1);
+            const float4 p00 = pad0[base], p10 = pad0[base + 1], p01 = pad0[base + px], p11 = pad0[base + px + 1];
+            const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+            const float dr = w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x;
+            const float di = w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y;
+            const float ax = w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z;
+            const float ay = w00 * p00.w + w10 * p10.w + w01 * p01.w + w11 * p11.w;
+            o.x = pp.eta * dr;
+            o.y = pp.eta * di;
+            // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
+            for (int c = 1; c < grid.n_comp; ++c) {
+                const float2 *pc = padc + (c - 1) * npad;
+                const float2 e00 = pc[base], e10 = pc[base + 1], e01 = pc[base + px], e11 = pc[base + px + 1];
+                o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
+                o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
             }
-            az += (float)grid.charge_sign * (pp.ex_f * axe + pp.ey_f * aye);
+#ifdef SC_DEBUG_BOUNDS
+            in_bounds((ghost[base] >= 0 || w00 == 0.f) && (ghost[base + 1] >= 0 || w10 == 0.f) &&
+                              (ghost[base + px] >= 0 || w01 == 0.f) && (ghost[base + px + 1] >= 0 || w11 == 0.f)
+                          ? 0
+                          : -1,
+                      1);
+#endif
+            float az = ln.aext;
+            if (GAUGE != 0) {
+                // landau and solenoid gauges: A_ext at the sample, from its exact
+                // fixed-point offset to the gauge origin
+                const float sc = (float)(grid.h / (double)(1ll << kFixBits));  // fixed-point unit times h
+                const float xr = (float)(ln.gx0 + (int64_t)q * pp.dx - grid.gfx) * sc;
+                const float yr = (float)(ln.gy0 + (int64_t)q * pp.dy - grid.gfy) * sc;
+                float axe, aye;
+                if (GAUGE == 2) {
+                    const float c = 0.5f * (float)grid.flux / (xr * xr + yr * yr);
+                    axe = -c * yr;
+                    aye = c * xr;
+                } else {
+                    axe = -(float)grid.bfield * yr;
+                    aye = 0.f;
+                }
+                az += (float)grid.charge_sign * (pp.ex_f * axe + pp.ey_f * aye);
+            }
+            o.z = az + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
         }
-        o.z = az + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
-        const bool ok = (g00 >= 0 || w00 == 0.f) && (g10 >= 0 || w10 == 0.f) && (g01 >= 0 || w01 == 0.f) &&
-                        (g11 >= 0 || w11 == 0.f);
-        o.w = ok ? 0.f : 1.f;
+        out[ln.slot0 + q] = o;
     }
-    out[s] = o;
+}
+
+template <int GAUGE>
+__global__ void __launch_bounds__(128) rotate_f32_kernel(const LineF32 *__restrict__ lines,
+                                                         const PairF32 *__restrict__ pairs, GridDev grid,
+                                                         const int32_t *__restrict__ ghost,
+                                                         const float4 *__restrict__ pad0,
+                                                         const float2 *__restrict__ padc, float4 *__restrict__ out) {
+    const int64_t L = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (L >= grid.n_lines) return;
+    const LineF32 ln = lines[L];
+    if (!in_bounds(ln.pair, grid.n_pairs)) return;
+    rotate_f32_line<GAUGE>(ln, pairs[ln.pair], grid, ghost, pad0, padc, out, threadIdx.x & 31);
 }
 
 cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
                               const PairF32 *pairs, const GridDev &grid, const int32_t *ghost,
                               const float4 *pad0, const float2 *padc, float4 *image_in,
                               cudaStream_t st) {
-    const int bs = 256;
-    const unsigned nb = (unsigned)((n_slots + bs - 1) / bs);
+    (void)slot_line;
+    (void)n_slots;
+    const unsigned nb = (unsigned)((grid.n_lines + 3) / 4);  // four lines (warps) per block
+    if (nb == 0) return cudaSuccess;
     if (grid.gauge == 2)
-        rotate_f32_kernel<2><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
+        rotate_f32_kernel<2><<<nb, 128, 0, st>>>(lines, pairs, grid, ghost, pad0, padc, image_in);
     else if (grid.gauge == 1)
-        rotate_f32_kernel<1><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
+        rotate_f32_kernel<1><<<nb, 128, 0, st>>>(lines, pairs, grid, ghost, pad0, padc, image_in);
     else
-        rotate_f32_kernel<0><<<nb, bs, 0, st>>>(lines, slot_line, n_slots, pairs, grid, ghost, pad0, padc, image_in);
+        rotate_f32_kernel<0><<<nb, 128, 0, st>>>(lines, pairs, grid, ghost, pad0, padc, image_in);
     return cudaGetLastError();
 }
 
@@ -153,15 +178,15 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 // chunks), so the lanes of a warp gather neighbouring samples of the same pair;
 // warp 0 adds the four partial sums in a fixed order.
 template <int NC>
-__global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
-                                       const BackLine *__restrict__ bl, GridDev grid,
-                                       const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
-                                       double *__restrict__ acc) {
+__device__ __forceinline__ void rotate_back_f32_block(const PairF32 *__restrict__ pairs, int32_t n_pairs,
+                                                      const BackLine *__restrict__ bl, const GridDev &grid,
+                                                      const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
+                                                      double *__restrict__ acc, int64_t blk) {
     constexpr int NV = 5 + 2 * NC;
     __shared__ double part[3][NV][32];
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t idx = blk * 32 + lane;
     const bool live = idx < npts;
     double A[NV] = {};  // the point's sums; [5 + 2c], [6 + 2c]: <eta_c Sf> of components c >= 1
     if (live && mask[idx]) {
@@ -177,14 +202,16 @@ __global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__r
                 split_fixed(i * pp.ui + j * pp.uj + pp.u0, iu, wu);
                 split_fixed(i * pp.vi + j * pp.vj + pp.v0, iv, wv);
                 const int la = min(max(iu, pp.l_lo), pp.l_hi), lb = min(max(iu + 1, pp.l_lo), pp.l_hi);
-                const BackLine La = back_chord(bl, bl[pp.lat0 + (la - pp.l_lo)], iv, wv);
-                const BackLine Lb = back_chord(bl, bl[pp.lat0 + (lb - pp.l_lo)], iv, wv);
+                const BackLine La = back_chord_at(bl, grid.n_back, pp.lat0 + (la - pp.l_lo), iv, wv);
+                const BackLine Lb = back_chord_at(bl, grid.n_back, pp.lat0 + (lb - pp.l_lo), iv, wv);
                 const int ma0 = min(max(iv, La.m0), La.m0 + La.ns - 1);
                 const int ma1 = min(max(iv + 1, La.m0), La.m0 + La.ns - 1);
                 const int mb0 = min(max(iv, Lb.m0), Lb.m0 + Lb.ns - 1);
                 const int mb1 = min(max(iv + 1, Lb.m0), Lb.m0 + Lb.ns - 1);
-                const float4 sa0 = img[La.slot0 + (ma0 - La.m0)], sa1 = img[La.slot0 + (ma1 - La.m0)];
-                const float4 sb0 = img[Lb.slot0 + (mb0 - Lb.m0)], sb1 = img[Lb.slot0 + (mb1 - Lb.m0)];
+                const float4 sa0 = ld_chk(img, (int64_t)La.slot0 + (ma0 - La.m0), grid.n_slots);
+                const float4 sa1 = ld_chk(img, (int64_t)La.slot0 + (ma1 - La.m0), grid.n_slots);
+                const float4 sb0 = ld_chk(img, (int64_t)Lb.slot0 + (mb0 - Lb.m0), grid.n_slots);
+                const float4 sb1 = ld_chk(img, (int64_t)Lb.slot0 + (mb1 - Lb.m0), grid.n_slots);
                 const float wa0 = (1.f - wu) * (1.f - wv), wa1 = (1.f - wu) * wv;
                 const float wb0 = wu * (1.f - wv), wb1 = wu * wv;
                 const float x0 = wa0 * sa0.x + wa1 * sa1.x + wb0 * sb0.x + wb1 * sb1.x;
@@ -232,6 +259,14 @@ __global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__r
     }
 }
 
+template <int NC>
+__global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__restrict__ pairs, int32_t n_pairs,
+                                       const BackLine *__restrict__ bl, GridDev grid,
+                                       const uint8_t *__restrict__ mask, const float4 *__restrict__ img,
+                                       double *__restrict__ acc) {
+    rotate_back_f32_block<NC>(pairs, n_pairs, bl, grid, mask, img, acc, blockIdx.x);
+}
+
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
                                    const GridDev &grid, const uint8_t *mask, const float4 *image_out,
                                    double *acc, cudaStream_t st) {
@@ -247,5 +282,68 @@ cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const 
     }
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// The same transfers for every member of a batch in one launch: each block
+// serves one member (its blocks of 256 padded points, 256 slots, or 32 grid
+// points), with the member's table in shared memory.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) batch_fields_f32_kernel(const MemberDev *__restrict__ m,
+                                                               const int64_t *__restrict__ off, int n) {
+    __shared__ MemberDev M;
+    const int64_t b = batch_member(m, off, n, M) * blockDim.x + threadIdx.x;
+    if (b < M.n_pad) fields_f32_point(M.grid, M.ghost, (const double2 *)M.delta, (const double2 *)M.aind, M.pad0, M.padc, b);
+}
+
+__global__ void __launch_bounds__(128) batch_rotate_f32_kernel(const MemberDev *__restrict__ m,
+                                                               const int64_t *__restrict__ off, int n) {
+    __shared__ MemberDev M;
+    const int64_t blk = batch_member(m, off, n, M);  // 16 lines per block, four per warp
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t L = blk * 16 + 4 * k + w;
+        if (L >= M.grid.n_lines) break;
+        const LineF32 ln = M.lines[L];
+        if (!in_bounds(ln.pair, M.grid.n_pairs)) continue;
+        switch (M.grid.gauge) {
+            case 2: rotate_f32_line<2>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+            case 1: rotate_f32_line<1>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+            default: rotate_f32_line<0>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane);
+        }
+    }
+}
+
+// off: prefix of the members' blocks of 32 grid points, zero for members with
+// another component count than NC
+template <int NC>
+__global__ void __launch_bounds__(128) batch_rotate_back_f32_kernel(const MemberDev *__restrict__ m,
+                                                                    const int64_t *__restrict__ off, int n) {
+    __shared__ MemberDev M;
+    const int64_t blk = batch_member(m, off, n, M);
+    rotate_back_f32_block<NC>(M.pairs, M.n_pairs, M.back, M.grid, M.mask, M.image_out, M.acc, blk);
+}
+
+cudaError_t launch_batch_fields_rotate_f32(const MemberDev *members, const int64_t *off_pad, int64_t pad_blocks,
+                                           const int64_t *off_slots, int64_t slot_blocks, int n, cudaStream_t st) {
+    if (pad_blocks > 0) batch_fields_f32_kernel<<<(unsigned)pad_blocks, 256, 0, st>>>(members, off_pad, n);
+    if (slot_blocks > 0) batch_rotate_f32_kernel<<<(unsigned)slot_blocks, 128, 0, st>>>(members, off_slots, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_rotate_back_f32(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                         int nc, int n, cudaStream_t st) {
+    if (n_blocks < 1) return cudaSuccess;
+    const unsigned g = (unsigned)n_blocks;
+    switch (nc) {
+        case 1: batch_rotate_back_f32_kernel<1><<<g, 128, 0, st>>>(members, off_blocks, n); break;
+        case 2: batch_rotate_back_f32_kernel<2><<<g, 128, 0, st>>>(members, off_blocks, n); break;
+        case 3: batch_rotate_back_f32_kernel<3><<<g, 128, 0, st>>>(members, off_blocks, n); break;
+        case 4: batch_rotate_back_f32_kernel<4><<<g, 128, 0, st>>>(members, off_blocks, n); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+SC_BOUNDS_ACCESSOR(bounds_lattice_f32)
 
 }  // namespace scd

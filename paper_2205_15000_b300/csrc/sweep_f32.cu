@@ -9,4 +9,6 @@ int sweep_occupancy_f32(int ept, int bs, int stepper, bool weighted) {
     return sweep_occupancy_t<float>(ept, bs, stepper, weighted);
 }
 
+SC_BOUNDS_ACCESSOR(bounds_sweep_f32)
+
 }  // namespace scd

@@ -9,4 +9,6 @@ int sweep_occupancy_f64(int ept, int bs, int stepper, bool weighted) {
     return sweep_occupancy_t<double>(ept, bs, stepper, weighted);
 }
 
+SC_BOUNDS_ACCESSOR(bounds_sweep_f64)
+
 }  // namespace scd

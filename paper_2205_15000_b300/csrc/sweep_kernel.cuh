@@ -81,9 +81,12 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                 if constexpr (WGT) wv[e] = ev[e] ? (T)gs.mats_w[nn] : T(0);
             }
         }
-        const int L = gs.groups[(int64_t)grp * G + gi];
-        const bool lv = L >= 0;
-        const LineDev &ln = gs.lines[lv ? L : 0];
+        const int64_t gq = (int64_t)grp * G + gi;
+        int L = in_bounds(gq, (int64_t)gs.n_groups * G) ? gs.groups[gq] : -1;
+        if (L >= 0 && !in_bounds(L, gs.n_lines)) L = -1;
+        const LineDev &ln = gs.lines[L >= 0 ? L : 0];
+        const bool lv = L >= 0 && line_tables_ok(ln, gs.n_slots, gs.n_lines, !a.first_sweep,
+                                                 (int64_t)(slab - (C *)a.scratch), ne_pad, a.scratch_elems);
         const int ns = lv ? ln.ns : 0;
         const int nsl = ns > 0 ? ns : 1;
         const int nsteps = lv ? ns + 1 : 0;
@@ -263,15 +266,9 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
                     o.y = -twopi * sfr;                         // Im Sf
                     o.z = fourpi * sg;                          // Sg
                     o.w = T(2) * (slo.x * sFi - slo.y * sFr);   // SF
-                    T4 *po = (T4 *)gs.image_out + slot0 + qs;
-                    if constexpr (BLK) {  // the blocks of a line add into the zeroed image
-                        atomicAdd(&po->x, o.x);
-                        atomicAdd(&po->y, o.y);
-                        atomicAdd(&po->z, o.z);
-                        atomicAdd(&po->w, o.w);
-                    } else {
-                        *po = o;
-                    }
+                    // a blocked sweep writes each energy block's sums into the block's own image
+                    T4 *po = (T4 *)gs.image_out + (BLK ? (int64_t)(it.y - grp * nb) * gs.n_slots : 0) + slot0 + qs;
+                    *po = o;
                 }
             } else if (comb) {
                 // LDOS: -Im g / pi = Re[(1 - p)/(1 + p)] = 2 Re(1/D) - 1
@@ -322,6 +319,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (EPT > 8 ? SC_SWEEP_MIN_
         item = __shfl_sync(FULL_MASK, item, 0);
         if (item >= a.n_items) break;
         const int2 it = a.items[item];
+        if (!in_bounds(it.x, a.n_grains)) continue;
         if constexpr (sizeof(T) == 4)  // FP32: packed energy pairs
             sweep_item_x2<EPT, RET, STEP, WGT, BLK>(a, it, a.grains[it.x], (Cx<float> *)warp_slab, lane);
         else

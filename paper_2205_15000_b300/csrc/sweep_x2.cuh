@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bounds.cuh"
 #include "kernels.cuh"
 #include "riccati_step.cuh"
 
@@ -329,9 +330,12 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
     auto zr_of = [&](int e, float sh) { return RET ? zq[e] + sh : sh; };
     auto zi_of = [&](int e) { return RET ? broad : zq[e]; };
 
-    const int L = gs.groups[(int64_t)grp * G + gi];
-    const bool lv = L >= 0;
-    const LineDev &ln = gs.lines[lv ? L : 0];
+    const int64_t gq = (int64_t)grp * G + gi;
+    int L = in_bounds(gq, (int64_t)gs.n_groups * G) ? gs.groups[gq] : -1;
+    if (L >= 0 && !in_bounds(L, gs.n_lines)) L = -1;
+    const LineDev &ln = gs.lines[L >= 0 ? L : 0];
+    const bool lv = L >= 0 && line_tables_ok(ln, gs.n_slots, gs.n_lines, !a.first_sweep,
+                                             (int64_t)(slab - (C *)a.scratch), ne_pad, a.scratch_elems);
     const int ns = lv ? ln.ns : 0;
     const int nsl = ns > 0 ? ns : 1;
     const int nsteps = lv ? ns + 1 : 0;
@@ -531,15 +535,9 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
                 o.y = -twopi * sfr;                         // Im Sf
                 o.z = fourpi * sg;                          // Sg
                 o.w = 2.f * (slo.x * sFi - slo.y * sFr);    // SF
-                float4 *po = (float4 *)gs.image_out + slot0 + qs;
-                if constexpr (BLK) {
-                    atomicAdd(&po->x, o.x);
-                    atomicAdd(&po->y, o.y);
-                    atomicAdd(&po->z, o.z);
-                    atomicAdd(&po->w, o.w);
-                } else {
-                    *po = o;
-                }
+                // a blocked sweep writes each energy block's sums into the block's own image
+                float4 *po = (float4 *)gs.image_out + (BLK ? (int64_t)(it.y - grp * nb) * gs.n_slots : 0) + slot0 + qs;
+                *po = o;
             }
         } else if (comb) {
             // LDOS: -Im g / pi = 2 Re(1/D) - 1 with D = 1 + ga conj(gb)

@@ -12,7 +12,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libsc.so")
+# SC_LIBRARY=checked selects the bounds-checked build (libsc_checked.so)
+LIB_PATH = os.path.join(_HERE, "_lib", "libsc_checked.so" if os.environ.get("SC_LIBRARY") == "checked"
+                        else "libsc.so")
 
 SC_OK, SC_EINVAL, SC_ENOMEM, SC_ECUDA, SC_ETIMEOUT, SC_ENUMERIC, SC_ESTATE, SC_ENOTCONV = range(8)
 STATUS_NAMES = ["SC_OK", "SC_EINVAL", "SC_ENOMEM", "SC_ECUDA", "SC_ETIMEOUT", "SC_ENUMERIC",
@@ -62,6 +64,7 @@ class sc_params(ctypes.Structure):
         ("n_parts", ctypes.c_int32), ("parts", ctypes.POINTER(sc_part)),
         ("gauge", ctypes.c_int32),
         ("eps_cut", ctypes.c_double), ("mask", ctypes.POINTER(ctypes.c_uint8)),
+        ("adjoint_checkpoint", ctypes.c_int32),
     ]
 
 
@@ -109,7 +112,8 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_get_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
-            "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
+            "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_debug_validate_tables",
+            "sc_debug_corrupt_table", "sc_debug_bounds", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
@@ -147,6 +151,9 @@ def _load():
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
         "sc_debug_fp64_math": [vp, i64, vp, vp, vp],
+        "sc_debug_validate_tables": [vp, P(i64)],
+        "sc_debug_corrupt_table": [vp, i32],
+        "sc_debug_bounds": [P(ctypes.c_uint64), P(i32), i32],
         "sc_sweep_lines_noalloc": [vp, vp, vp, vp, vp, i32, i32, i32, f64, f64, vp, vp, vp],
         "sc_sweep_adjoint": [vp, vp, vp, vp, f64, vp, vp, ctypes.c_int, vp],
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
@@ -264,6 +271,7 @@ def make_params(d, precision="fp32", lanes_per_line=0, host_only=False, record_t
     p.n_parts = len(parts)
     p.parts = ctypes.cast(arr, ctypes.POINTER(sc_part))
     p.eps_cut = float(d.get("eps_cut", 0.0))
+    p.adjoint_checkpoint = int(d.get("adjoint_checkpoint", 0))
     if d.get("mask") is not None:  # the caller's expectation of the grain mask, checked by sc_create
         mk = np.ascontiguousarray(d["mask"], np.uint8)
         keep.append(mk)
@@ -353,6 +361,26 @@ def sc_debug_fp64_math(x, stream=None):
     rcp, rsq = torch.empty_like(x), torch.empty_like(x)
     _check(lib.sc_debug_fp64_math(_ptr(x), x.numel(), _ptr(rcp), _ptr(rsq), _stream(stream)))
     return rcp, rsq
+
+
+def sc_debug_validate_tables(ctx):
+    """Number of out-of-range indices in the context's host tables."""
+    n = ctypes.c_int64(0)
+    _check(lib.sc_debug_validate_tables(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def sc_debug_corrupt_table(ctx, which):
+    """Make one host-table index of a host_only context out of range (tests)."""
+    _check(lib.sc_debug_corrupt_table(ctx, int(which)), ctx)
+
+
+def sc_debug_bounds(reset=False):
+    """(violations, checked_build): index-check violations of the kernels on the
+    current device and whether this library is the bounds-checked build."""
+    v, c = ctypes.c_uint64(0), ctypes.c_int32(0)
+    _check(lib.sc_debug_bounds(ctypes.byref(v), ctypes.byref(c), int(bool(reset))))
+    return v.value, bool(c.value)
 
 
 def sc_energy_grid(ctx, n_e):

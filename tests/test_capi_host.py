@@ -223,3 +223,33 @@ def test_given_mask_must_match_the_shape():
     bad[24, 24] ^= 1
     with pytest.raises(sc.ScError):
         sc.Context(dict(p, mask=bad), host_only=True)
+
+
+@pytest.mark.parametrize("name", ["disc", "diamond", "annulus", "squid"])
+def test_table_indices_validate(name):
+    """Every index of the host tables lies inside the table it points into, and
+    each kind of corruption (an image slot, a boundary tap, a lattice-line
+    record) is caught -- on host_only contexts, whose tables never reach a GPU."""
+    p = {"disc": lambda: W.disc(5.0, 40, n_angles=18, n_energies=4),
+         "diamond": lambda: W.diamond(12.0, 48, n_angles=16, n_energies=4),
+         "annulus": lambda: W.annulus(6.0, 2.5, 48, margin=0.3, n_angles=8, n_energies=2),
+         "squid": GEOMS["squid"]}[name]()
+    c = sc.Context(p, host_only=True)
+    assert sc.sc_debug_validate_tables(c.h) == 0
+    for which in (0, 1, 2):
+        bad = sc.Context(p, host_only=True)
+        sc.sc_debug_corrupt_table(bad.h, which)
+        assert sc.sc_debug_validate_tables(bad.h) >= 1, which
+    with pytest.raises(sc.ScError):
+        sc.sc_debug_corrupt_table(c.h, 3)
+
+
+def test_checked_library_exports_the_same_symbols():
+    """The bounds-checked variant of the library (index checks compiled into the
+    kernels) loads and exports every symbol of include/sc.h."""
+    import ctypes
+    from paper_2205_15000_b300 import build
+    assert os.path.exists(build.LIB_CHECKED)
+    L = ctypes.CDLL(build.LIB_CHECKED)
+    for n in _declared():
+        assert hasattr(L, n), n

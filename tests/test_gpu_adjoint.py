@@ -221,3 +221,21 @@ def test_autograd_free_energy_matches_oracle_fd():
     gd, ga = dt.grad.cpu().numpy(), at.grad.cpu().numpy()
     adj = np.array([[gd[j_, i].real, gd[j_, i].imag, ga[j_, i, 0], ga[j_, i, 1]] for j_, i in probes])
     assert np.max(np.abs(adj - fd)) <= 1e-6 * np.max(np.abs(fd))
+
+
+@pytest.mark.parametrize("k", [2, 5, 32])
+def test_checkpointed_fp32_adjoint_equals_parked(k):
+    """The FP32 adjoint with the forward gamma kept every k samples and
+    recomputed from there gives the parked adjoint's gradient (the recomputed
+    gammas are the same FP32 values; only the order of the atomic cotangent
+    sums differs), also on lines shorter than k."""
+    from paper_2205_15000_b300 import sc
+    p, d, a = _grain()
+    ref = _adjoint(p, d, a, "fp32", g_Ftotal=1.0)
+    got = _adjoint(dict(p, adjoint_checkpoint=k), d, a, "fp32", g_Ftotal=1.0)
+    for x, y in zip(got, ref):
+        assert np.max(np.abs(x - y)) <= 1e-5 * np.max(np.abs(y))
+    with pytest.raises(sc.ScError):
+        sc.Context(dict(p, adjoint_checkpoint=k), precision="fp64")
+    with pytest.raises(sc.ScError):
+        sc.Context(dict(p, adjoint_checkpoint=1), precision="fp32")

@@ -276,13 +276,19 @@ def test_c2_full_size_fp32_against_oracle():
 def test_c5_full_size_first_sweep_sampled_angles():
     """Large workload (d-wave square side 200, 1024^2, 256 angles, 160
     energies, 20 vortices): FP32 first-sweep energy sums on every sample of
-    two angles (one of each direction of a pair) against the oracle."""
+    eight angles, both directions of four pairs spread over the Fermi circle,
+    against the oracle.  S_f and S_F within 2e-5 of their largest value on the
+    angle; S_g = sum of -Im 1/D with D = 1 + gamma conj(gamma~) within 4e-5: near
+    the vortex cores at t = 0.05 the low-energy D comes close to zero and
+    magnifies the FP32 rounding of the coefficients (measured 2.6e-5; a
+    compensated energy sum leaves it unchanged, so it is not the summation)."""
     import torch
     sc = _sc()
     p, delta, aind = W.c5_square_d()
     g = oracle.OracleGeom(p)
     P = g.n_pairs
-    angles = [37, P + 90]
+    pairs = [5, 37, 70, 101]
+    angles = [q for q in pairs] + [q + P for q in pairs]
     ref = g.sweep_subset(delta, None, angles)
     ctx = sc.Context(p, precision="fp32")
     ctx.set_fields(delta)
@@ -292,6 +298,7 @@ def test_c5_full_size_first_sweep_sampled_angles():
     ns = np.maximum(L["m1"] - L["m0"] + 1, 0)
     per = [int(ns[L["pair"] == q].sum()) for q in range(P)]
     start = np.concatenate([[0], np.cumsum(per)])
+    worst = np.zeros(4)
     for k, r in zip(angles, ref):
         q = k % P
         mine = img[start[q]:start[q + 1]].copy()
@@ -299,7 +306,8 @@ def test_c5_full_size_first_sweep_sampled_angles():
             mine[:, 2] = -mine[:, 2]  # S_g changes sign with the direction; S_f, S_F do not
         scale = np.max(np.abs(r), axis=0)
         err = np.max(np.abs(mine - r), axis=0) / scale
-        # S_g feeds the current (tolerance 1e-4) and cancels strongly over 160 energies
-        assert np.all(err < np.array([2e-5, 2e-5, 1e-4, 2e-5])), (k, err)
+        worst = np.maximum(worst, err)
+    print("c5 first-sweep image errors (Re Sf, Im Sf, Sg, SF):", worst)
+    assert np.all(worst < np.array([2e-5, 2e-5, 4e-5, 2e-5])), worst
     del ctx
     torch.cuda.empty_cache()
