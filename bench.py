@@ -725,6 +725,9 @@ def run_batch(args):
                "steps": n_e2e}
     fp32_launches = info.sweep_launches
     fp32_lane_fill = info.steps_per_sweep / max(info.lane_steps_per_sweep, 1)
+    last = b.info()
+    classes = [{"energies_per_lane": last.class_ept[k], "blocks_per_sm": last.class_blocks_per_sm[k],
+                "ms": last.class_ms[k]} for k in range(min(last.sweep_launches, 8))]
     b.close()
     del b
 
@@ -782,7 +785,7 @@ def run_batch(args):
                    "steps_per_sweep": info.steps_per_sweep, "work_items": info.n_items,
                    "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
                    "energy_sum": args.energy_sum, "lane_fill": fp32_lane_fill,
-                   "sweep_launches": fp32_launches,
+                   "sweep_launches": fp32_launches, "sweep_classes": classes,
                    "step": "one batch iteration: every member's rotate, the sweep, rotate-back and outputs",
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},

@@ -355,6 +355,9 @@ typedef struct {
     double ms_sweep;           /* last batch sweep kernel (CUDA events on its stream) */
     int64_t lane_steps_per_sweep; /* steps the lanes execute, padded energy slots included */
     int32_t sweep_launches;    /* uniform sweep launches per batch sweep (one per layout class) */
+    int32_t class_ept[8];      /* per launch (class): its energies per lane */
+    int32_t class_blocks_per_sm[8]; /* per launch: resident blocks per SM its grid is sized for */
+    double class_ms[8];        /* per launch: its duration in the last batch sweep */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
@@ -381,8 +384,11 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream);
    one graph per iteration parity -- on an internal stream ordered after and
    before `stream`.  The first sweep from fresh boundary values runs uncaptured. */
 sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream);
-/* Time one sweep per candidate energies-per-lane (2..8) and keep the fastest.
-   The timing sweeps are real sweeps (boundary values advance). */
+/* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
+   keep the fastest; then, for that layout, size every class launch's persistent
+   grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
+   per SM and keep, per class, the fastest (each class launch timed by its own
+   CUDA events).  The timing sweeps are real sweeps (boundary values advance). */
 sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *stream);
 sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info);
 

@@ -34,6 +34,7 @@ struct sc_batch {
     // one uniform launch per energies-per-lane class: items [first, first + n)
     struct Class {
         int ept, first, n, grid_blocks;
+        int occ, bps;  // occupancy (blocks per SM) and the blocks per SM the grid is sized for
     };
     std::vector<Class> classes;
     void *d_scratch = nullptr;
@@ -51,6 +52,8 @@ struct sc_batch {
     int64_t steps_per_sweep = 0;
     int64_t lane_steps_per_sweep = 0;  // with padded energy slots, for the current layout
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t cev[9] = {};  // around each class launch of the last sweep
+    std::vector<int> bps_choice;  // autotuned blocks per SM of each class (empty: occupancy)
     bool timed = false;
     // captured iterations: graph[p] = one sweep starting from parity p (+ outputs)
     cudaStream_t gstream = nullptr;
@@ -200,10 +203,13 @@ sc_status build(sc_batch *b, int ept) {
         ++classes.back().n;
     }
     int max_blocks = 1;
-    for (auto &c : classes) {
+    for (size_t k = 0; k < classes.size(); ++k) {
+        auto &c = classes[k];
         int occ = scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper, b->weighted);
         if (occ < 1) occ = 1;
-        c.grid_blocks = std::max(1, std::min(b->sm_count * occ, (c.n + 3) / 4));
+        c.occ = occ;
+        c.bps = k < b->bps_choice.size() && b->bps_choice[k] > 0 ? std::min(b->bps_choice[k], occ) : occ;
+        c.grid_blocks = std::max(1, std::min(b->sm_count * c.bps, (c.n + 3) / 4));
         max_blocks = std::max(max_blocks, c.grid_blocks);
     }
     free_plan_buffers(b);
@@ -316,6 +322,8 @@ sc_status sc_batch_destroy(sc_batch *b) {
     cudaFree(b->d_off);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->cev)
+        if (e) cudaEventDestroy(e);
     free_graphs(b);
     for (cudaEvent_t e : b->sync_ev)
         if (e) cudaEventDestroy(e);
@@ -382,6 +390,7 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     cudaError_t e = cudaMalloc(&b->d_counter, 8 * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->cev[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     for (int k = 0; k < sc_batch::kAux && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
@@ -441,6 +450,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     BCK(cudaEventRecordWithFlags(b->ev[0], st, ev_flags));
     for (size_t k = 0; k < b->classes.size(); ++k) {
         const sc_batch::Class &c = b->classes[k];
+        if (k < 8) BCK(cudaEventRecordWithFlags(b->cev[k], st, ev_flags));
         scd::SweepLaunch a{};
         a.grains = b->d_grains;
         a.items = b->d_items + c.first;
@@ -461,6 +471,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.blocked = b->blocked;
         BCK(scd::launch_sweep(b->fp64, a, st));
     }
+    BCK(cudaEventRecordWithFlags(b->cev[std::min<size_t>(b->classes.size(), 8)], st, ev_flags));
     BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
     b->timed = true;
     for (size_t g = 0; g < b->members.size(); ++g)
@@ -568,6 +579,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     for (sc_ctx *c : b->members) max_ne = std::max(max_ne, c->n_e);
     int best = b->ept;
     float best_ms = 1e30f;
+    b->bps_choice.clear();  // grids at occupancy while the layout is chosen
     for (int ept = 2; ept <= (b->fp64 ? 8 : 10); ++ept) {
         if (max_ne > 32 * ept) continue;
         sc_status s = build(b, ept);
@@ -584,7 +596,41 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
             best = ept;
         }
     }
+    b->bps_choice.clear();
     sc_status s = build(b, best);
+    if (s != SC_OK) return s;
+    // per class: the persistent grid sized for occupancy, occupancy - 1, occupancy - 2
+    // resident blocks per SM; each class keeps its fastest
+    const size_t nc = std::min<size_t>(b->classes.size(), 8);
+    std::vector<int> pick(nc, 0);
+    std::vector<float> pick_ms(nc, 1e30f);
+    for (int d = 0; d <= 2; ++d) {
+        b->bps_choice.assign(nc, 0);
+        bool any = false;
+        for (size_t k = 0; k < nc; ++k) {
+            const int occ = b->classes[k].occ;
+            b->bps_choice[k] = std::max(1, occ - d);
+            any = any || occ - d >= 1;
+        }
+        if (!any) break;
+        s = build(b, best);
+        if (s != SC_OK) return s;
+        for (int rep = 0; rep < 2; ++rep) {  // the second sweep is the one timed
+            s = sc_batch_sweep(b, stream);
+            if (s != SC_OK) return s;
+        }
+        BCK(cudaEventSynchronize(b->cev[nc]));
+        for (size_t k = 0; k < nc; ++k) {
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, b->cev[k], b->cev[k + 1]));
+            if (ms < pick_ms[k]) {
+                pick_ms[k] = ms;
+                pick[k] = b->bps_choice[k];
+            }
+        }
+    }
+    b->bps_choice = pick;
+    s = build(b, best);
     if (s != SC_OK) return s;
     if (energies_per_lane) *energies_per_lane = best;
     return SC_OK;
@@ -600,7 +646,20 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     info->lane_steps_per_sweep = b->lane_steps_per_sweep;
     info->sweep_launches = (int32_t)b->classes.size();
     info->scratch_bytes = (int64_t)b->scratch_bytes;
+    for (size_t k = 0; k < b->classes.size() && k < 8; ++k) {
+        info->class_ept[k] = b->classes[k].ept;
+        info->class_blocks_per_sm[k] = b->classes[k].bps;
+    }
     if (b->timed) {
+        const size_t nc = std::min<size_t>(b->classes.size(), 8);
+        for (size_t k = 0; k < nc; ++k) {
+            float cms = 0.f;
+            if (cudaEventSynchronize(b->cev[nc]) == cudaSuccess &&
+                cudaEventElapsedTime(&cms, b->cev[k], b->cev[k + 1]) == cudaSuccess)
+                info->class_ms[k] = cms;
+            else
+                (void)cudaGetLastError();
+        }
         float ms = 0.f;
         if (cudaEventSynchronize(b->ev[1]) == cudaSuccess && cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess)
             info->ms_sweep = ms;
