@@ -53,6 +53,13 @@ ALG_MUFU_OPS_PER_PSE = 2 * 7 + 1
 # the implicit midpoint stepper: a quadratic per step (41 FP32 ops, 3 MUFU; ell zr
 # shared by the energies) with the same propagator evaluation
 ALG_OPS_PER_PSE = {"closed": ALG_FP32_OPS_PER_PSE, "midpoint": 2 * 41 + 21}
+# the adjoint sweep (closed-form step) per (angle pair, sample, energy), counted the
+# same way from its arithmetic: pass 1 one step (34 + 18); pass 2 the forward
+# segment's Moebius coefficients (40), their mirror for beta (17), beta's step (20),
+# the step derivatives (112), the coefficient cotangents (19) and the propagator
+# cotangents at the sample (80); pass 3 beta's coefficients (40), derivatives (112)
+# and cotangents (21); 23 MUFU operations
+ALG_ADJ_OPS_PER_PSE = (34 + 18) + (40 + 17 + 20 + 112 + 19 + 80) + (40 + 112 + 21)
 SM_COUNT_B300 = 148
 FP32_LANES_PER_SM = 128
 # FP64 pipe: ncu reports sm__inst_executed_pipe_fp64 peak 0.0625 warp instructions
@@ -194,6 +201,16 @@ def _sample_clocks_stop(proc, f, path, device_index=0):
         return None
     return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
             "samples": len(sm)}
+
+
+def _measured_fma_peak():
+    """The library's measured FP32 lane-FMA rate (packed and scalar chains, the larger;
+    Gop/s), taken after the timed steps; None when it cannot be measured."""
+    from paper_2205_15000_b300 import sc
+    try:
+        return max(sc.sc_debug_fma_rate(True), sc.sc_debug_fma_rate(False)) / 1e9
+    except Exception:
+        return None
 
 
 def _profiled_traffic(workload, precision):
@@ -490,7 +507,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
                      "kernel": "sweep_kernel", "ms_per_launch": sweep_ms,
-                     "kernels_ms_per_step": kernels_ms, "peak_note": peak_note},
+                     "kernels_ms_per_step": kernels_ms, "peak_note": peak_note,
+                     "ops_per_unit": f"{ALG_OPS_PER_PSE[args.stepper]} lane-operations per (angle pair, sample, "
+                                     "energy), the optimised formulation, terms that depend only on the segment "
+                                     "excluded"},
         "e2e": ({"value": steps_per_step / (statistics.median(e2e_ms) * 1e-3),
                  "unit": "trajectory-steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                  "ms_per_step": statistics.median(e2e_ms), "host_enqueue_ms_per_step": e2e_enqueue_ms}
@@ -503,6 +523,21 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": t_wall,
     }
+    if args.precision == "fp32":
+        pm = _measured_fma_peak()
+        if pm:
+            line["roofline"]["peak_measured"] = pm
+            line["roofline"]["frac_of_measured"] = achieved / pm
+            line["roofline"]["peak_measured_note"] = ("sc_debug_fma_rate after the timed steps: 8 blocks of 256 "
+                                                      "threads per SM, 8 independent FMA chains per thread")
+    if args.adjoint and args.stepper == "closed":
+        adj_ms = kernels_ms["adjoint_sweep"]
+        adj_ach = pse * ALG_ADJ_OPS_PER_PSE / (adj_ms * 1e-3) / 1e9
+        line["roofline_adjoint"] = {
+            "bound": "alu", "achieved": adj_ach, "peak": peak_gops, "unit": "Gop/s", "frac": adj_ach / peak_gops,
+            "kernel": "adjoint_sweep_kernel", "ms_per_launch": adj_ms, "over_forward_sweep": adj_ms / sweep_ms,
+            "ops_per_unit": f"{ALG_ADJ_OPS_PER_PSE} lane-operations per (angle pair, sample, energy): three "
+                            "passes, counted like the sweep's"}
     if not args.no_cpu_baseline and (args.workload in ("c2", "annulus") or args.errors):
         # the large grain: one full oracle sweep (minutes on the host cores), opt-in
         n_sw = 1 if args.workload == "c5" else 2
@@ -776,6 +811,7 @@ def run_batch(args):
     lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
     peak_gops = SM_COUNT_B300 * lanes * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
     traffic = _profiled_traffic(workload, args.precision)
+    pm = _measured_fma_peak() if args.precision == "fp32" else None
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -797,7 +833,10 @@ def run_batch(args):
                                      "sample, energy): the optimised closed-form formulation, terms that depend "
                                      "only on the segment excluded",
                      "peak_note": ("FP32" if args.precision == "fp32" else "FP64")
-                     + " lane issue 148 SM x lanes/cycle x max SM clock (derived)"},
+                     + " lane issue 148 SM x lanes/cycle x max SM clock (derived)",
+                     "peak_measured": pm, "frac_of_measured": (achieved / pm) if pm else None,
+                     "peak_measured_note": "sc_debug_fma_rate after the timed steps: 8 blocks of 256 threads per SM, "
+                                           "8 independent FMA chains per thread"},
         "fp64_plain": fp64,
         "e2e": e2e,
         # per member: (FP32: field conversion,) rotate, rotate-back, outputs and the

@@ -420,6 +420,14 @@ sc_status sc_debug_images(sc_ctx *ctx, double *images);
    for the stream.  SC_EINVAL for n < 0 or a null pointer with n > 0, SC_ECUDA
    for a failed launch (message in sc_last_error(NULL)). */
 sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, void *stream);
+/* Measured FP32 fused multiply-add rate of this GPU (no counterpart in the paper;
+   the measured side of the sweep's roofline): lane operations per second of a
+   launch of 8 blocks of 256 threads per SM, each thread running eight independent
+   chains of 100000 FMAs -- scalar (packed = 0) or two-wide fma.rn.f32x2, two lane
+   operations per instruction (packed != 0).  Allocates and frees a small output
+   buffer and waits for the stream.  SC_EINVAL for a NULL pointer, SC_ECUDA on a
+   CUDA error (message in sc_last_error(NULL)). */
+sc_status sc_debug_fma_rate(int32_t packed, double *lane_ops_per_s, void *stream);
 
 /* ---- index checks ------------------------------------------------------
  * Engineering aids with no counterpart in the paper (the checks that stand in

@@ -18,6 +18,9 @@
 
 namespace scd {
 
+// fetch the line of global memory holding p into L2 (a hint; no register result)
+__device__ __forceinline__ void l2_hint(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // complex value(s) with packed parts: V = f2 (two energies) or float (one)
 template <typename V>
 struct CV {
@@ -165,7 +168,8 @@ __device__ __forceinline__ void mob_grad_v(const MobV<V> &m, float dr, float di,
 // One work item of the packed FP32 adjoint (Matsubara or Ozaki energies, the
 // closed-form step).  Slab rows per sample: [0] gamma then beta, [1] the local
 // beta cotangent, each as NP float4 pairs per lane ([k][lane]) and the scalar
-// tail energy of every lane.  CK: pass 1 keeps gamma only at the samples
+// tail energy of every lane; after them (and the kept rows) one row each for the
+// entry values of gamma and beta.  CK: pass 1 keeps gamma only at the samples
 // 0, k, 2k, ... (k = a.ckpt) in rows after the 2 max_ns sample rows, and pass 2
 // recomputes the samples of each stretch [ck, ck + k) from its kept value (the
 // same steps as pass 1, so the same values) when it enters the stretch.
@@ -187,7 +191,9 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
     const float h = (float)gs.h;
     const int n_e = gs.n_e, ne_pad = gs.ne_pad;
     const int ck = CK ? a.ckpt : 1;
-    const int64_t lrows = 2 * (int64_t)gs.max_ns + (CK ? (gs.max_ns + ck - 1) / ck : 0);  // rows per line
+    const int64_t nkept = CK ? (gs.max_ns + ck - 1) / ck : 0;
+    // rows per line: two per sample, the kept gammas, and the entry values of gamma and beta
+    const int64_t lrows = 2 * (int64_t)gs.max_ns + nkept + 2;
     C *slab = warp_slab + (int64_t)gi * lrows * ne_pad;
     const float pi = 3.141592653589793f;
     const int nb = BLK ? gs.n_blocks : 1;
@@ -248,6 +254,18 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
     auto st1 = [&](int i, int k, const P1 v) { row(i, k)[tail_off] = C{v.x, v.y}; };
     // kept gamma c (CK): the row after the sample rows
     auto krow = [&](int c) -> C * { return slab + (2 * (int64_t)gs.max_ns + c) * ne_pad; };
+    // entry values of gamma (k = 0) and beta (k = 1), parked rather than held in registers
+    C *const erow[2] = {slab + (2 * (int64_t)gs.max_ns + nkept) * ne_pad,
+                        slab + (2 * (int64_t)gs.max_ns + nkept + 1) * ne_pad};
+    auto est2 = [&](int k, int p, const P2 v) {
+        ((float4 *)erow[k])[p * Lw + r] = make_float4(v.x.x, v.x.y, v.y.x, v.y.y);
+    };
+    auto eld2 = [&](int k, int p) -> P2 {
+        const float4 v = ((const float4 *)erow[k])[p * Lw + r];
+        return P2{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+    };
+    auto est1 = [&](int k, const P1 v) { erow[k][tail_off] = C{v.x, v.y}; };
+    auto eld1 = [&](int k) -> P1 { return P1{erow[k][tail_off].x, erow[k][tail_off].y}; };
     // entry values: the previous sweep's exits (4 taps) or gamma_h of the first segment
     auto entry = [&](const int *taps, const double *w, const float4 s, float zr, float ell, P2 *gp, P1 &gt) {
         if (a.first_sweep) {
@@ -285,13 +303,13 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
     };
 
     // ---------------- pass 1: gamma along +e_par (the forward sweep's steps) ----------------
-    P2 g[NPA], g0[NPA];
-    P1 gt{0.f, 0.f}, gt0{0.f, 0.f};
+    P2 g[NPA];
+    P1 gt{0.f, 0.f};
     float4 sp = li[0];
     entry(ln.tap_f, ln.w_f, sp, sp.z, lead, g, gt);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) g0[k] = g[k];
-    gt0 = gt;
+    for (int k = 0; k < NP; ++k) est2(0, k, g[k]);
+    if constexpr (TAIL) est1(0, gt);
     {
         float4 sq = sp;
         for (int i = 0; i < nsteps; ++i) {
@@ -332,22 +350,28 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
     __syncwarp();
 
     // ---------------- pass 2: beta along -e_par, gamma adjoint ----------------
-    P2 b[NPA], b0[NPA], lam[NPA];
-    P1 bt{0.f, 0.f}, bt0{0.f, 0.f}, lat{0.f, 0.f};
+    P2 b[NPA], lam[NPA];
+    P1 bt{0.f, 0.f}, lat{0.f, 0.f};
     float4 sh = li[nsl - 1];
     entry(ln.tap_b, ln.w_b, sh, -sh.z, tail, b, bt);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
-        b0[k] = b[k];
+        est2(1, k, b[k]);
         lam[k] = P2{bc2(0.f), bc2(0.f)};
     }
-    bt0 = bt;
+    if constexpr (TAIL) est1(1, bt);
     {
         float4 slo = sh;
         for (int j = 0; j < nmax; ++j) {
             const bool act = j < nsteps;
             const int q = nsl - 1 - j;  // sample reached (j < ns)
             const bool at_sample = act && j < ns;
+            // the next step's parked gammas (written long ago) are fetched into L2
+            if (!CK && j + 1 < ns) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) l2_hint((const float4 *)row(q - 1, 0) + k * Lw + r);
+                if constexpr (TAIL) l2_hint(row(q - 1, 0) + tail_off);
+            }
             float cdr = 0.f, cdi = 0.f, ca = 0.f, sdr = 0.f, sdi = 0.f;
             if (act) {
                 const float dr = 0.5f * (sh.x + slo.x), di = 0.5f * (sh.y + slo.y), av = 0.5f * (sh.z + slo.z);
@@ -444,7 +468,7 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
                 }
 #pragma unroll
                 for (int k = 0; k < NP; ++k) {
-                    const P2 start = at_sample ? ld2(q, 0, k) : g0[k];
+                    const P2 start = at_sample ? ld2(q, 0, k) : eld2(0, k);
                     P2 bbar{bc2(0.f), bc2(0.f)};
                     one(b[k], lam[k], start, Q[k], M[k], EVM[k], Cdr, Cdi, Ca, Sdr, Sdi, bbar);
                     if (at_sample) st2(q, 1, k, bbar);
@@ -455,7 +479,7 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
                 sdr = Sdr.x + Sdr.y;
                 sdi = Sdi.x + Sdi.y;
                 if constexpr (TAIL) {
-                    const P1 start = at_sample ? ld1(q, 0) : gt0;
+                    const P1 start = at_sample ? ld1(q, 0) : eld1(0);
                     P1 bbar{0.f, 0.f};
                     one(bt, lat, start, zq[EPT - 1], wv[EPT - 1], evt, cdr, cdi, ca, sdr, sdi, bbar);
                     if (at_sample) st1(q, 1, bbar);
@@ -501,6 +525,18 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
         float4 sa = li[0], sb = li[0];
         for (int i = 0; i < nmax; ++i) {
             const bool act = i < nsteps;
+            // the next step's parked beta and beta cotangent are fetched into L2
+            if (i + 1 < ns) {
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    l2_hint((const float4 *)row(i + 1, 0) + k * Lw + r);
+                    l2_hint((const float4 *)row(i + 1, 1) + k * Lw + r);
+                }
+                if constexpr (TAIL) {
+                    l2_hint(row(i + 1, 0) + tail_off);
+                    l2_hint(row(i + 1, 1) + tail_off);
+                }
+            }
             float cdr = 0.f, cdi = 0.f, ca = 0.f;
             if (act) {
                 if (i == 0) {
@@ -528,7 +564,7 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
                     };
 #pragma unroll
                     for (int k = 0; k < NP; ++k) {
-                        const P2 start = i < ns ? ld2(i, 0, k) : b0[k];
+                        const P2 start = i < ns ? ld2(i, 0, k) : eld2(1, k);
                         const P2 cot = i < ns ? ld2(i, 1, k) : P2{bc2(0.f), bc2(0.f)};
                         one(mu[k], start, Q[k], EVM[k], Cdr, Cdi, Ca, cot);
                     }
@@ -536,7 +572,7 @@ __device__ __forceinline__ void adjoint_item_x2(const AdjointLaunch &a, const in
                     cdi = Cdi.x + Cdi.y;
                     ca = Ca.x + Ca.y;
                     if constexpr (TAIL) {
-                        const P1 start = i < ns ? ld1(i, 0) : bt0;
+                        const P1 start = i < ns ? ld1(i, 0) : eld1(1);
                         const P1 cot = i < ns ? ld1(i, 1) : P1{0.f, 0.f};
                         one(mut, start, zq[EPT - 1], evt, cdr, cdi, ca, cot);
                     }

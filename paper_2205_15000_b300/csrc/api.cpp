@@ -1263,10 +1263,10 @@ sc_status sc_sweep_adjoint(sc_ctx *ctx, const double *g_delta_new, const double 
     }
     const int occ = std::max(1, scd::adjoint_occupancy(ctx->fp64, pl.ept, 128, ctx->stepper));
     const int blocks = std::max(1, std::min(ctx->sm_count * occ, (pl.n_items + 3) / 4));
-    // per line: two rows per sample (gamma then beta; beta cotangent) and, with
-    // checkpoints, one row per kept gamma
+    // per line: two rows per sample (gamma then beta; beta cotangent), with
+    // checkpoints one row per kept gamma, and the entry values of gamma and beta
     const int64_t max_ns = std::max(ctx->geo.max_ns, 1);
-    const int64_t lrows = 2 * max_ns + (ctx->adj_ckpt > 0 ? (max_ns + ctx->adj_ckpt - 1) / ctx->adj_ckpt : 0);
+    const int64_t lrows = 2 * max_ns + (ctx->adj_ckpt > 0 ? (max_ns + ctx->adj_ckpt - 1) / ctx->adj_ckpt : 0) + 2;
     const int64_t stride = (int64_t)pl.lines_per_warp * lrows * pl.lanes * pl.ept;
     const size_t need = (size_t)blocks * 4 * (size_t)stride * 2 * ctx->real_bytes;
     if (need > ctx->adj_scratch_bytes) {
@@ -1388,6 +1388,20 @@ sc_status sc_debug_fp64_math(const double *x, int64_t n, double *rcp, double *rs
     }
     cudaError_t e = scd::launch_fp64_math(x, n, rcp, rsqrt, (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        g_create_error = cudaGetErrorString(e);
+        return SC_ECUDA;
+    }
+    return SC_OK;
+}
+
+sc_status sc_debug_fma_rate(int32_t packed, double *lane_ops_per_s, void *stream) {
+    g_create_error.clear();
+    if (!lane_ops_per_s) return SC_EINVAL;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = scd::measure_fma_rate(packed != 0, sms, lane_ops_per_s, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         g_create_error = cudaGetErrorString(e);
         return SC_ECUDA;

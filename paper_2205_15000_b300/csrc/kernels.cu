@@ -111,6 +111,63 @@ __global__ void fp64_math_kernel(const double *__restrict__ x, int64_t n, double
     rsq[i] = Mth<double>::rsqrt(x[i]);
 }
 
+// FP32 fused multiply-add rate: eight independent chains per thread, scalar or
+// two-wide (fma.rn.f32x2: two lane-operations per instruction)
+template <bool PK>
+__global__ void __launch_bounds__(256) fma_rate_kernel(float *out, int iters, float a, float b) {
+    float s = 0.f;
+    if constexpr (PK) {
+        float2 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = make_float2((float)(threadIdx.x + k), (float)(blockIdx.x + k));
+        const float2 A = make_float2(a, a), B = make_float2(b, b);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = __ffma2_rn(x[k], A, B);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += x[k].x + x[k].y;
+    } else {
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = (float)(threadIdx.x + k);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += x[k];
+    }
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+cudaError_t measure_fma_rate(bool packed, int sm_count, double *lane_ops_per_s, cudaStream_t st) {
+    const int blocks = sm_count * 8, threads = 256, iters = 100000;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(float));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the second launch is timed
+        e = cudaEventRecord(e0, st);
+        if (packed)
+            fma_rate_kernel<true><<<blocks, threads, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+        else
+            fma_rate_kernel<false><<<blocks, threads, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e == cudaSuccess)
+        *lane_ops_per_s = (double)blocks * threads * 8.0 * iters * (packed ? 2.0 : 1.0) / (ms * 1e-3);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    return e;
+}
+
 cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int bs = 256;

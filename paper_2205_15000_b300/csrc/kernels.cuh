@@ -188,6 +188,9 @@ cudaError_t launch_sweep(bool fp64, const SweepLaunch &a, cudaStream_t s);
 cudaError_t launch_block_sum(bool fp64, const void *blocks, int nb, int64_t n_slots, void *out, cudaStream_t st);
 // the FP64 device reciprocal and reciprocal square root of the sweep on n values
 cudaError_t launch_fp64_math(const double *x, int64_t n, double *rcp, double *rsqrt, cudaStream_t s);
+// lane fused multiply-adds per second of a launch of eight blocks of 256 threads per SM,
+// eight independent chains per thread (scalar, or two-wide when packed)
+cudaError_t measure_fma_rate(bool packed, int sm_count, double *lane_ops_per_s, cudaStream_t st);
 // FP32 production path
 // FP32 fields on the ghost-padded grid: every padded point takes the values of its
 // nearest grain point (ghost map), zero where it has none

@@ -114,7 +114,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_set_fields", "sc_get_fields", "sc_reset_boundary", "sc_riccati_sweep", "sc_burnin",
             "sc_gap_update", "sc_current", "sc_free_energy", "sc_update_vector_potential",
             "sc_picard_step", "sc_ldos", "sc_debug_lines", "sc_debug_ghost", "sc_debug_links", "sc_debug_chords",
-            "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_debug_validate_tables",
+            "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_debug_fma_rate", "sc_debug_validate_tables",
             "sc_debug_corrupt_table", "sc_debug_bounds", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
@@ -153,6 +153,7 @@ def _load():
         "sc_debug_exits": [vp, vp],
         "sc_debug_images": [vp, vp],
         "sc_debug_fp64_math": [vp, i64, vp, vp, vp],
+        "sc_debug_fma_rate": [i32, P(f64), vp],
         "sc_debug_validate_tables": [vp, P(i64)],
         "sc_debug_corrupt_table": [vp, i32],
         "sc_debug_bounds": [P(ctypes.c_uint64), P(i32), i32],
@@ -363,6 +364,13 @@ def sc_debug_fp64_math(x, stream=None):
     rcp, rsq = torch.empty_like(x), torch.empty_like(x)
     _check(lib.sc_debug_fp64_math(_ptr(x), x.numel(), _ptr(rcp), _ptr(rsq), _stream(stream)))
     return rcp, rsq
+
+
+def sc_debug_fma_rate(packed=True, stream=None):
+    """Measured FP32 lane fused multiply-adds per second of this GPU."""
+    r = ctypes.c_double(0.0)
+    _check(lib.sc_debug_fma_rate(int(bool(packed)), ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def sc_debug_validate_tables(ctx):
