@@ -822,6 +822,7 @@ def run_batch(args):
                    "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
                    "energy_sum": args.energy_sum, "lane_fill": fp32_lane_fill,
                    "sweep_launches": fp32_launches, "sweep_classes": classes,
+                   "min_lanes_per_line": last.min_lanes_per_line,
                    "step": "one batch iteration: every member's rotate, the sweep, rotate-back and outputs",
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},

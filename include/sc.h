@@ -358,6 +358,7 @@ typedef struct {
     int32_t class_ept[8];      /* per launch (class): its energies per lane */
     int32_t class_blocks_per_sm[8]; /* per launch: resident blocks per SM its grid is sized for */
     double class_ms[8];        /* per launch: its duration in the last batch sweep */
+    int32_t min_lanes_per_line; /* fewest energy lanes per line a member may take */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
@@ -385,7 +386,9 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream);
    before `stream`.  The first sweep from fresh boundary values runs uncaptured. */
 sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream);
 /* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
-   keep the fastest; then, for that layout, size every class launch's persistent
+   keep the fastest; then the fewest lanes per line a member may take (4, 8, 16:
+   at most 8, 4, 2 lines per warp, which a warp steps as long as its longest);
+   then, for that layout, size every class launch's persistent
    grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
    per SM and keep, per class, the fastest (each class launch timed by its own
    CUDA events).  The timing sweeps are real sweeps (boundary values advance). */

@@ -24,6 +24,7 @@ struct sc_batch {
     int device = 0;
     bool fp64 = false;
     int ept = 0;  // bound on energies per lane
+    int min_lanes = 4;  // fewest energy lanes per line a member may take (at most 32 / min_lanes lines per warp)
     int stepper = 0;  // sc_stepper, shared by all members
     bool weighted = false;  // Ozaki energy sums, shared by all members
     int sm_count = 0;
@@ -107,11 +108,12 @@ void free_plan_buffers(sc_batch *b) {
 // Energy layout of one member with at most `ept_max` energies per lane: the
 // fewest padded lane slots (lanes x energies per lane >= n_e), then the most
 // energies per lane (fewer lanes: fewer shuffle rounds, more lines per warp).
-void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
+void member_layout(int n_e, int ept_max, int min_lanes, int &lanes, int &ept) {
     int best = 1 << 30;
     // 9 or 10 energies per lane only on 16 or 32 lanes per line (FP32 bounds above 8);
     // among equal padding the fewer lanes (fewer issue units per line) come first
     for (int l : {4, 8, 16, 32}) {
+        if (l < min_lanes) continue;
         const int e = (n_e + l - 1) / l;
         if (e < 1 || e > (l >= 16 ? ept_max : std::min(ept_max, 8))) continue;
         if (l * e < best) {
@@ -124,7 +126,7 @@ void member_layout(int n_e, int ept_max, int &lanes, int &ept) {
     // more energies than one layout holds: energy blocks, each counted with 32
     // slots of per-block overhead
     for (int l : {32, 16, 8, 4})
-        for (int e = std::min(ept_max, 8); e >= 1; --e) {
+        for (int e = std::min(ept_max, 8); e >= 1 && l >= min_lanes; --e) {
             const int nb = (n_e + l * e - 1) / (l * e);
             const int cost = nb * (l * e + 32);
             if (cost < best) {
@@ -150,7 +152,7 @@ sc_status build(sc_batch *b, int ept) {
     for (size_t g = 0; g < b->members.size(); ++g) {
         sc_ctx *c = b->members[g];
         int lanes = 32, eg = ept;
-        member_layout(c->n_e, ept, lanes, eg);
+        member_layout(c->n_e, ept, b->min_lanes, lanes, eg);
         Plan *pl = nullptr;
         sc_status st = sc_internal::make_plan_layout(c, c->n_e, lanes, eg, &pl);
         if (st != SC_OK) return berr(b, st, c->err);
@@ -580,6 +582,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     int best = b->ept;
     float best_ms = 1e30f;
     b->bps_choice.clear();  // grids at occupancy while the layout is chosen
+    b->min_lanes = 4;
     for (int ept = 2; ept <= (b->fp64 ? 8 : 10); ++ept) {
         if (max_ne > 32 * ept) continue;
         sc_status s = build(b, ept);
@@ -596,6 +599,27 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
             best = ept;
         }
     }
+    // the fewest lanes per line (the most lines per warp): a warp steps all its lines
+    // as long as its longest, so more lines per warp trade padding for idle lanes
+    int best_min = b->min_lanes;
+    best_ms = 1e30f;
+    for (int ml : {4, 8, 16}) {
+        b->min_lanes = ml;
+        sc_status s = build(b, best);
+        if (s != SC_OK) return s;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            s = sc_batch_sweep(b, stream);
+            if (s != SC_OK) return s;
+            BCK(cudaEventSynchronize(b->ev[1]));
+            BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_min = ml;
+        }
+    }
+    b->min_lanes = best_min;
     b->bps_choice.clear();
     sc_status s = build(b, best);
     if (s != SC_OK) return s;
@@ -646,6 +670,7 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     info->lane_steps_per_sweep = b->lane_steps_per_sweep;
     info->sweep_launches = (int32_t)b->classes.size();
     info->scratch_bytes = (int64_t)b->scratch_bytes;
+    info->min_lanes_per_line = b->min_lanes;
     for (size_t k = 0; k < b->classes.size() && k < 8; ++k) {
         info->class_ept[k] = b->classes[k].ept;
         info->class_blocks_per_sm[k] = b->classes[k].bps;
