@@ -695,9 +695,9 @@ def run_batch(args):
     sweep_ms = statistics.mean(ksweep)
 
     # end to end through the public API with host buffers: every step uploads all
-    # members' Delta from pinned host memory, sets them (sc_set_fields), runs one
-    # batch iteration (sc_batch_run with outputs) and reads every member's
-    # Delta_new, j and F back (sc_gap_update / sc_current / sc_free_energy into
+    # members' Delta from pinned host memory into device staging, sets them
+    # (sc_batch_set_fields), runs one batch iteration (sc_batch_run with outputs)
+    # and reads every member's Delta_new, j and F back (sc_batch_get_outputs into
     # device staging, then one copy into pinned host memory).  Uploads and
     # read-backs run on two more streams through double-buffered staging.
     e2e = None
@@ -709,7 +709,7 @@ def run_batch(args):
         for (p, d, _), o0 in zip(grains, off[:-1]):
             h_in[o0:o0 + p["nx"] * p["ny"]] = torch.view_as_real(
                 torch.as_tensor(np.ascontiguousarray(d, np.complex128).reshape(-1)))
-        # outputs of member g at 5 x its first point: Delta_new (complex), j (2 reals), F
+        # outputs of all members: Delta_new (complex), then j (2 reals), then F
         d_in = [torch.empty((tot, 2), dtype=torch.float64, device=dev) for _ in range(2)]
         d_out = [torch.empty(5 * tot, dtype=torch.float64, device=dev) for _ in range(2)]
         h_out = [torch.empty(5 * tot, dtype=torch.float64).pin_memory() for _ in range(2)]
@@ -731,15 +731,11 @@ def run_batch(args):
                 if i >= 2:
                     stream.wait_event(ev_read[i - 2])  # the output staging was read back
                 flush.fill_(float(i))
-                for m, o0, o1 in zip(b.members, off[:-1], off[1:]):
-                    sc.sc_set_fields(m.h, d_in[k][o0:o1], None, True, stream)
+                sc.sc_batch_set_fields(b.h, d_in[k], True, stream)
                 ev_used[i].record(stream)
                 sc.sc_batch_run(b.h, 1, True, stream)
-                for m, o0, o1 in zip(b.members, off[:-1], off[1:]):
-                    n, q = int(o1 - o0), 5 * int(o0)
-                    sc.sc_gap_update(m.h, d_out[k][q:q + 2 * n], True, False, stream)
-                    sc.sc_current(m.h, d_out[k][q + 2 * n:q + 4 * n], True, stream)
-                    sc.sc_free_energy(m.h, d_out[k][q + 4 * n:q + 5 * n], True, False, stream)
+                sc.sc_batch_get_outputs(b.h, d_out[k][:2 * tot], d_out[k][2 * tot:4 * tot], d_out[k][4 * tot:],
+                                        True, stream)
                 ev_out[i].record(stream)
                 with torch.cuda.stream(cs_out):
                     cs_out.wait_event(ev_out[i])

@@ -394,6 +394,24 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
    CUDA events).  The timing sweeps are real sweeps (boundary values advance). */
 sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *stream);
 sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info);
+/* Every member's Delta at once (the batch form of sc_set_fields without A_ind):
+   delta_all holds the members' complex Delta one after another, member g's
+   n_components x ny x nx values (doubles re, im) at the offset of the members
+   before it.  on_device = 1: a device pointer, read by one kernel on `stream`;
+   0: a host pointer, copied to a device buffer of the batch (allocated on the
+   first such call) and the call waits for the copy.  Every member's induced
+   vector potential is set to zero.  SC_EINVAL for NULL, SC_ESTATE after a
+   failure, SC_ECUDA on a CUDA error. */
+sc_status sc_batch_set_fields(sc_batch *b, const double *delta_all, int on_device, void *stream);
+/* Every member's Delta_new, j and F(R) of the last batch iteration with outputs
+   (sc_batch_run with with_outputs = 1), one after another in the layout of
+   sc_batch_set_fields (Delta_new: n_components x ny x nx complex; j: ny x nx x 2;
+   F: ny x nx); any of the three may be NULL.  on_device = 1: device pointers,
+   filled by one kernel on `stream`; 0: host pointers, through a device buffer of
+   the batch (allocated on the first such call), and the call waits.  SC_ESTATE
+   when a member has no outputs of its last sweep. */
+sc_status sc_batch_get_outputs(sc_batch *b, double *delta_new_all, double *j_all, double *F_all, int on_device,
+                               void *stream);
 
 /* ---- inspection (tests and tools) -------------------------------------
  * A "line" is one chord: a maximal piece of a lattice line inside the grain,

@@ -48,6 +48,11 @@ struct sc_batch {
     scd::MemberDev *d_members = nullptr;
     int64_t *d_off = nullptr;  // [7][n + 1]: pad, slots, back (nc = 1..4), outputs
     int64_t tot_pad = 0, tot_slots = 0, tot_back[4] = {0, 0, 0, 0}, tot_out = 0;
+    // arrays of all members' fields and outputs (sc_batch_set_fields / _get_outputs):
+    // [0] prefix of n_comp nx ny (complex Delta values), [1] prefix of nx ny
+    int64_t *d_pt = nullptr;
+    int64_t tot_cplx = 0, tot_pts = 0;
+    double *d_stage_in = nullptr, *d_stage_out = nullptr;  // host-pointer transfers (lazy)
     int parity = 0;
     bool have_boundary = false;
     int64_t steps_per_sweep = 0;
@@ -304,6 +309,16 @@ sc_status build_member_tables(sc_batch *b) {
     BCK(cudaMemcpy(b->d_members, md.data(), n * sizeof(scd::MemberDev), cudaMemcpyHostToDevice));
     BCK(cudaMalloc(&b->d_off, off.size() * sizeof(int64_t)));
     BCK(cudaMemcpy(b->d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    std::vector<int64_t> pt(2 * (n + 1), 0);
+    for (size_t g = 0; g < n; ++g) {
+        const int64_t np = (int64_t)b->members[g]->geo.nx * b->members[g]->geo.ny;
+        pt[g + 1] = pt[g] + np * b->members[g]->geo.n_comp;
+        pt[(n + 1) + g + 1] = pt[(n + 1) + g] + np;
+    }
+    b->tot_cplx = pt[n];
+    b->tot_pts = pt[2 * n + 1];
+    BCK(cudaMalloc(&b->d_pt, pt.size() * sizeof(int64_t)));
+    BCK(cudaMemcpy(b->d_pt, pt.data(), pt.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     return SC_OK;
 }
 
@@ -322,6 +337,9 @@ sc_status sc_batch_destroy(sc_batch *b) {
     cudaFree(b->d_counter);
     cudaFree(b->d_members);
     cudaFree(b->d_off);
+    cudaFree(b->d_pt);
+    cudaFree(b->d_stage_in);
+    cudaFree(b->d_stage_out);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->cev)
@@ -657,6 +675,56 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     s = build(b, best);
     if (s != SC_OK) return s;
     if (energies_per_lane) *energies_per_lane = best;
+    return SC_OK;
+}
+
+sc_status sc_batch_set_fields(sc_batch *b, const double *delta_all, int on_device, void *stream) {
+    if (!b || !delta_all) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    BCK(cudaSetDevice(b->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const double *src = delta_all;
+    if (!on_device) {
+        if (!b->d_stage_in) BCK(cudaMalloc(&b->d_stage_in, 2 * (size_t)b->tot_cplx * sizeof(double)));
+        BCK(cudaMemcpyAsync(b->d_stage_in, delta_all, 2 * (size_t)b->tot_cplx * sizeof(double),
+                            cudaMemcpyHostToDevice, st));
+        src = b->d_stage_in;
+    }
+    BCK(scd::launch_batch_set_fields(b->d_members, member_off(b, 6), b->tot_out, b->d_pt, (int)b->members.size(),
+                                     src, st));
+    if (!on_device) BCK(cudaStreamSynchronize(st));
+    for (sc_ctx *c : b->members) {
+        c->have_aind = false;
+        c->have_sweep = false;
+        c->have_outputs = false;
+        c->acc_kind = -1;
+    }
+    return SC_OK;
+}
+
+sc_status sc_batch_get_outputs(sc_batch *b, double *delta_new_all, double *j_all, double *F_all, int on_device,
+                               void *stream) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    for (sc_ctx *c : b->members)
+        if (!c->have_outputs) return berr(b, SC_ESTATE, "a member has no outputs of its last sweep");
+    BCK(cudaSetDevice(b->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->members.size();
+    if (on_device) {
+        BCK(scd::launch_batch_get_outputs(b->d_members, member_off(b, 6), b->tot_out, b->d_pt, n, delta_new_all,
+                                          j_all, F_all, st));
+        return SC_OK;
+    }
+    const size_t nd = 2 * (size_t)b->tot_cplx, nj = 2 * (size_t)b->tot_pts, nf = (size_t)b->tot_pts;
+    if (!b->d_stage_out) BCK(cudaMalloc(&b->d_stage_out, (nd + nj + nf) * sizeof(double)));
+    double *sd = b->d_stage_out, *sj = sd + nd, *sf = sj + nj;
+    BCK(scd::launch_batch_get_outputs(b->d_members, member_off(b, 6), b->tot_out, b->d_pt, n,
+                                      delta_new_all ? sd : nullptr, j_all ? sj : nullptr, F_all ? sf : nullptr, st));
+    if (delta_new_all) BCK(cudaMemcpyAsync(delta_new_all, sd, nd * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (j_all) BCK(cudaMemcpyAsync(j_all, sj, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (F_all) BCK(cudaMemcpyAsync(F_all, sf, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
     return SC_OK;
 }
 

@@ -473,6 +473,89 @@ __global__ void batch_final_sums_kernel(const MemberDev *__restrict__ m, const i
     final_sums_block(M.partials, (int)(off[blockIdx.x + 1] - off[blockIdx.x]), 4, M.sums);
 }
 
+// The members' grid points, 256 per block: Delta (all component planes) in, A_ind
+// zeroed; or Delta_new, j, F out.  The arrays of all members hold member after member;
+// pt_off[g] is where member g starts, in complex values for Delta (the sum of n_comp
+// nx ny over the members before it).
+__global__ void batch_set_fields_kernel(const MemberDev *__restrict__ m, const int64_t *__restrict__ off, int n,
+                                        const int64_t *__restrict__ pt_off, const double *__restrict__ delta_all) {
+    __shared__ MemberDev M;
+    __shared__ int64_t base_sh;
+    const int64_t blk = batch_member(m, off, n, M);
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid;
+        }
+        base_sh = pt_off[lo];
+    }
+    __syncthreads();
+    const int64_t np = (int64_t)M.grid.nx * M.grid.ny;
+    const int64_t i = blk * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    double *d = (double *)M.delta;  // the member's own buffers
+    for (int c = 0; c < M.grid.n_comp; ++c) {
+        const int64_t o = 2 * (c * np + i);
+        d[o] = delta_all[2 * base_sh + o];
+        d[o + 1] = delta_all[2 * base_sh + o + 1];
+    }
+    double *a = (double *)M.aind;
+    a[2 * i] = 0.0;
+    a[2 * i + 1] = 0.0;
+}
+
+// pt_off here: prefix over the members of n_comp np (Delta_new) and, separately,
+// of np (j, F), passed as [2][n + 1]
+__global__ void batch_get_outputs_kernel(const MemberDev *__restrict__ m, const int64_t *__restrict__ off, int n,
+                                         const int64_t *__restrict__ pt_off, double *__restrict__ dnew_all,
+                                         double *__restrict__ j_all, double *__restrict__ F_all) {
+    __shared__ MemberDev M;
+    __shared__ int64_t bc_sh, bp_sh;
+    const int64_t blk = batch_member(m, off, n, M);
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= (int64_t)blockIdx.x) lo = mid;
+            else hi = mid;
+        }
+        bc_sh = pt_off[lo];
+        bp_sh = pt_off[(n + 1) + lo];
+    }
+    __syncthreads();
+    const int64_t np = (int64_t)M.grid.nx * M.grid.ny;
+    const int64_t i = blk * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    if (dnew_all)
+        for (int c = 0; c < M.grid.n_comp; ++c) {
+            const int64_t o = 2 * (c * np + i);
+            dnew_all[2 * bc_sh + o] = M.dnew[o];
+            dnew_all[2 * bc_sh + o + 1] = M.dnew[o + 1];
+        }
+    if (j_all) {
+        j_all[2 * (bp_sh + i)] = M.j[2 * i];
+        j_all[2 * (bp_sh + i) + 1] = M.j[2 * i + 1];
+    }
+    if (F_all) F_all[bp_sh + i] = M.F[i];
+}
+
+cudaError_t launch_batch_set_fields(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                    const int64_t *pt_off, int n, const double *delta_all, cudaStream_t st) {
+    if (n_blocks > 0) batch_set_fields_kernel<<<(unsigned)n_blocks, 256, 0, st>>>(members, off_blocks, n, pt_off, delta_all);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_get_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                     const int64_t *pt_off, int n, double *dnew_all, double *j_all, double *F_all,
+                                     cudaStream_t st) {
+    if (n_blocks > 0)
+        batch_get_outputs_kernel<<<(unsigned)n_blocks, 256, 0, st>>>(members, off_blocks, n, pt_off, dnew_all, j_all,
+                                                                     F_all);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks, int n,
                                  cudaStream_t st) {
     batch_outputs_kernel<<<(unsigned)n_blocks, 256, 0, st>>>(members, off_blocks, n);

@@ -290,6 +290,15 @@ cudaError_t launch_batch_rotate_back_f32(const MemberDev *members, const int64_t
                                          int nc, int n, cudaStream_t st);
 cudaError_t launch_batch_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks, int n,
                                  cudaStream_t st);
+// Members' fields from / outputs to arrays of all members one after another
+// (off_blocks: prefix of blocks of 256 grid points; pt_off: prefix of grid points).
+// set: Delta (n_comp planes) from delta_all, A_ind zeroed.  get: Delta_new, j, F
+// into the arrays that are not null.
+cudaError_t launch_batch_set_fields(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                    const int64_t *pt_off, int n, const double *delta_all, cudaStream_t st);
+cudaError_t launch_batch_get_outputs(const MemberDev *members, const int64_t *off_blocks, int64_t n_blocks,
+                                     const int64_t *pt_off, int n, double *dnew_all, double *j_all, double *F_all,
+                                     cudaStream_t st);
 
 
 cudaError_t launch_outputs(const GridDev &grid, const uint8_t *mask, const double *acc,

@@ -120,7 +120,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
-            "sc_batch_get_info", "sc_last_error", "sc_version"]
+            "sc_batch_get_info", "sc_batch_set_fields", "sc_batch_get_outputs", "sc_last_error", "sc_version"]
 
 
 def _load():
@@ -175,6 +175,8 @@ def _load():
         "sc_batch_run": [vp, i32, i32, vp],
         "sc_batch_autotune": [vp, P(i32), vp],
         "sc_batch_get_info": [vp, P(sc_batch_info)],
+        "sc_batch_set_fields": [vp, vp, ctypes.c_int, vp],
+        "sc_batch_get_outputs": [vp, vp, vp, vp, ctypes.c_int, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -496,6 +498,17 @@ def sc_batch_get_info(b):
     i = sc_batch_info()
     _check(lib.sc_batch_get_info(b, ctypes.byref(i)))
     return i
+
+
+def sc_batch_set_fields(b, delta_all, on_device=True, stream=None):
+    """Every member's Delta from one array (members one after another)."""
+    _check(lib.sc_batch_set_fields(b, _ptr(delta_all), int(on_device), _stream(stream)))
+
+
+def sc_batch_get_outputs(b, delta_new_all=None, j_all=None, F_all=None, on_device=True, stream=None):
+    """Every member's Delta_new, j, F into arrays of all members (any may be None)."""
+    _check(lib.sc_batch_get_outputs(b, _ptr(delta_new_all), _ptr(j_all), _ptr(F_all), int(on_device),
+                                    _stream(stream)))
 
 
 class Batch:

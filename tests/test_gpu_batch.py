@@ -172,3 +172,52 @@ def test_member_sweep_alone_is_rejected():
         b.members[0].sweep()
     assert ei.value.status == sc.SC_ESTATE
     b.close()
+
+
+@pytest.mark.parametrize("precision,on_device", [("fp32", True), ("fp32", False), ("fp64", True)])
+def test_batch_wide_fields_and_outputs_equal_member_calls(precision, on_device):
+    """sc_batch_set_fields / sc_batch_get_outputs (every member's Delta in, every
+    member's Delta_new, j, F out, members one after another) give bit for bit what
+    the per-member calls give, with device and with host arrays; a two-component
+    member carries both planes."""
+    import torch
+    from paper_2205_15000_b300 import sc
+    p1 = W.disc(4.0, 28, pairing=0, t=0.5, n_angles=16, n_energies=10, flux_quanta=0.7)
+    p2 = W.diamond(8.0, 30, pairing=1, t=0.3, n_angles=16, n_energies=12, flux_quanta=0.3)
+    p3 = W.disc(4.0, 26, pairing=2, t=0.5, n_angles=16, n_energies=8)
+    p3["components"] = [(2, 1.0), (1, 1.0)]
+    d1 = W.noisy_delta(p1, 0.26, 0.1, seed=71)
+    d2 = W.noisy_delta(p2, 0.23, 0.1, seed=72)
+    d3 = np.stack([W.noisy_delta(p3, 0.2, 0.1, seed=73), 0.1j * W.noisy_delta(p3, 0.2, 0.1, seed=74)])
+    prms, ds = [p1, p2, p3], [d1, d2, d3]
+    ref = sc.Batch(prms, precision=precision)
+    for m, d in zip(ref.members, ds):
+        m.set_fields(d)
+    ref.run(2, True)
+    want = [m.outputs() for m in ref.members]
+    b = sc.Batch(prms, precision=precision)
+    flat = np.concatenate([np.ascontiguousarray(d, np.complex128).reshape(-1) for d in ds])
+    arr = np.ascontiguousarray(flat.view(np.float64))
+    src = torch.from_numpy(arr).cuda() if on_device else arr
+    sc.sc_batch_set_fields(b.h, src, on_device)
+    b.run(2, True)
+    n_c = sum(d.size for d in ds)
+    n_p = sum(p["nx"] * p["ny"] for p in prms)
+    if on_device:
+        dn, j, F = (torch.empty(k, dtype=torch.float64, device="cuda") for k in (2 * n_c, 2 * n_p, n_p))
+    else:
+        dn, j, F = np.zeros(2 * n_c), np.zeros(2 * n_p), np.zeros(n_p)
+    sc.sc_batch_get_outputs(b.h, dn, j, F, on_device)
+    torch.cuda.synchronize()
+    dn, j, F = ((x.cpu().numpy() if on_device else x) for x in (dn, j, F))
+    oc = op = 0
+    for w, d, p in zip(want, ds, prms):
+        npt = p["nx"] * p["ny"]
+        got_dn = dn[2 * oc:2 * (oc + d.size)].view(np.complex128).reshape(d.shape)
+        np.testing.assert_array_equal(got_dn, w["delta_new"].cpu().numpy())
+        np.testing.assert_array_equal(j[2 * op:2 * (op + npt)].reshape(p["ny"], p["nx"], 2), w["j"].cpu().numpy())
+        np.testing.assert_array_equal(F[op:op + npt].reshape(p["ny"], p["nx"]), w["F"].cpu().numpy())
+        oc += d.size
+        op += npt
+    ref.close()
+    b.close()
