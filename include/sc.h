@@ -116,9 +116,11 @@ typedef struct {
     double lattice_ox, lattice_oy; /* origin of the rotated lattices relative to the
                                       grid-box centre, units of h (default 0.1, 0.2) */
     int32_t precision;       /* sc_precision: FP64 plain sweep or FP32 production sweep */
-    int32_t lanes_per_line;  /* 0 = automatic; else 4, 8, 16 or 32 energy lanes per line
+    int32_t lanes_per_line;  /* 0 = automatic; else 2, 4, 8, 16 or 32 energy lanes per line
                                 (the energies per lane then follow: at most 8, or 10 for an
-                                FP32 sweep on 16 or 32 lanes; the adjoint takes at most 8) */
+                                FP32 sweep on 2, 16 or 32 lanes; the adjoint takes at most 8).
+                                A warp holds 32 / lanes_per_line lines of one angle pair,
+                                taken longest first. */
     int32_t host_only;       /* 1 = build the geometry tables only (no device memory); every
                                 call that computes then returns SC_ESTATE.  For inspecting
                                 the discretisation on a machine without a GPU. */
@@ -365,9 +367,10 @@ typedef struct {
    in sc_create) and one work list over all their (line group) items, longest
    first.  energies_per_lane (1..8; FP32 batches 1..10) bounds the energies
    one lane carries; 0 picks a default; sc_batch_autotune chooses by timing.
-   Each member takes the lanes per line (4, 8, 16, 32) and energies per lane
-   (<= the bound; 9 and 10 only on 16 or 32 lanes per line and without energy
-   blocks) with the fewest padded lane slots, then the most energies per lane.  Members with
+   Each member takes the lanes per line (2, 4, 8, 16, 32; at least the batch's
+   fewest, 2 unless sc_batch_autotune raises it) and energies per lane (<= the
+   bound; 9 and 10 only without energy blocks) with the fewest padded lane
+   slots, then the most energies per lane.  Members with
    equal energies per lane share one persistent launch; a batch sweep runs
    these launches back to back.  The members are owned by the batch. */
 sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,
@@ -385,9 +388,14 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream);
    one graph per iteration parity -- on an internal stream ordered after and
    before `stream`.  The first sweep from fresh boundary values runs uncaptured. */
 sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream);
+/* Forget every member's boundary coherence functions: the next batch sweep
+   starts every trajectory from the local homogeneous solution, as the first
+   sweep after sc_batch_create does.  The layout (energies per lane, lanes per
+   line, blocks per SM) is kept. */
+sc_status sc_batch_reset_boundary(sc_batch *b);
 /* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
-   keep the fastest; then the fewest lanes per line a member may take (4, 8, 16:
-   at most 8, 4, 2 lines per warp, which a warp steps as long as its longest);
+   keep the fastest; then the fewest lanes per line a member may take (2, 4, 8, 16:
+   at most 16, 8, 4, 2 lines per warp, which a warp steps as long as its longest);
    then, for that layout, size every class launch's persistent
    grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
    per SM and keep, per class, the fastest (each class launch timed by its own

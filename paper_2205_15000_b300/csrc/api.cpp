@@ -81,7 +81,8 @@ cudaError_t dalloc(sc_ctx *ctx, P **p, size_t bytes) {
 
 // energy lanes per line and energies per lane: least padding, then EPT near 4.
 // wide (the FP32 sweep on packed energy pairs, at most 256 energies): 16 or 32
-// lanes per line may carry up to 10 energies each, and among layouts with equal
+// lanes per line may carry up to 10 energies each, so may 2 lanes per line (16
+// lines per warp, at most 20 energies), and among layouts with equal
 // padding the one with fewer issue units per line (lanes x energy pairs, an odd
 // energy counting as a pair) wins (c5, 160 energies: 16 x 10 against 32 x 5,
 // sweep 119.9 -> 110.4 ms; 8 lanes x 10 on c2 is slower than 16 x 5, its four
@@ -120,9 +121,10 @@ void choose_lanes(int n_e, int forced_lanes, int forced_ept, int &lanes, int &ep
         ept = best_e;
         return;
     }
-    for (int l : {32, 16, 8, 4}) {
+    for (int l : {32, 16, 8, 4, 2}) {
+        if (l == 2 && !wide) continue;
         const int e = (n_e + l - 1) / l;
-        if (e > (wide && l >= 16 ? 10 : 8)) continue;
+        if (e > (wide && (l >= 16 || l == 2) ? 10 : 8)) continue;
         const int pad = l * e;
         bool better = pad < best_pad;
         if (pad == best_pad) {
@@ -172,8 +174,8 @@ sc_status make_plan(sc_ctx *ctx, int n_e, int forced_ept, Plan **out, bool wide)
 }
 
 sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out) {
-    if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
-        return set_err(ctx, SC_EINVAL, "energy lanes per line must be 4, 8, 16 or 32");
+    if (lanes != 2 && lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return set_err(ctx, SC_EINVAL, "energy lanes per line must be 2, 4, 8, 16 or 32");
     if (ept < 1 || ept > (ctx->fp64 ? 8 : 10))
         return set_err(ctx, SC_EINVAL, ctx->fp64 ? "energies per lane must be 1 to 8" : "energies per lane must be 1 to 10");
     const int n_blocks = (n_e + lanes * ept - 1) / (lanes * ept);
@@ -188,16 +190,22 @@ sc_status make_plan_layout(sc_ctx *ctx, int n_e, int lanes, int ept, Plan **out)
     pl.ept = ept;
     pl.lines_per_warp = 32 / lanes;
     const int G = pl.lines_per_warp;
-    // groups of G neighbouring lines of one pair (similar lengths)
+    // groups of G lines of one pair, the pair's lines taken longest first: a warp
+    // steps its lines as long as the longest, so lines of equal length share a warp
     std::vector<int32_t> flat;
+    std::vector<int32_t> by_len;
     for (const auto &pp : ctx->geo.pairs) {
         const int n = pp.n_lines;
+        by_len.resize(n);
+        for (int i = 0; i < n; ++i) by_len[i] = pp.line0 + i;
+        std::stable_sort(by_len.begin(), by_len.end(),
+                         [&](int32_t a, int32_t b) { return ctx->geo.lines[a].ns > ctx->geo.lines[b].ns; });
         for (int i = 0; i < n; i += G) {
             int c = 0;
             for (int k = 0; k < G; ++k) {
                 if (i + k < n) {
-                    flat.push_back(pp.line0 + i + k);
-                    c = std::max(c, ctx->geo.lines[pp.line0 + i + k].ns + 1);
+                    flat.push_back(by_len[i + k]);
+                    c = std::max(c, ctx->geo.lines[by_len[i + k]].ns + 1);
                 } else {
                     flat.push_back(-1);
                 }
@@ -410,9 +418,9 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
         g_create_error = "unknown precision";
         return SC_EINVAL;
     }
-    if (p->lanes_per_line != 0 && p->lanes_per_line != 4 && p->lanes_per_line != 8 && p->lanes_per_line != 16 &&
-        p->lanes_per_line != 32) {
-        g_create_error = "lanes_per_line must be 0, 4, 8, 16 or 32";
+    if (p->lanes_per_line != 0 && p->lanes_per_line != 2 && p->lanes_per_line != 4 && p->lanes_per_line != 8 &&
+        p->lanes_per_line != 16 && p->lanes_per_line != 32) {
+        g_create_error = "lanes_per_line must be 0, 2, 4, 8, 16 or 32";
         return SC_EINVAL;
     }
     if (p->stepper != SC_STEP_CLOSED && p->stepper != SC_STEP_MIDPOINT) {
@@ -621,6 +629,7 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
             lf[L].pair = li.pair;
             lf[L].ns = li.ns;
             lf[L].slot0 = li.slot0;
+            lf[L].m0 = li.ns > 0 ? li.m0 : (int32_t)std::floor(sh);
         }
         const double cx = 0.5 + (p->x0 - G.ox) / p->h, cy = 0.5 + (p->y0 - G.oy) / p->h;
         for (int q = 0; q < P; ++q) {

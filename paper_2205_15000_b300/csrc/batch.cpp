@@ -24,7 +24,7 @@ struct sc_batch {
     int device = 0;
     bool fp64 = false;
     int ept = 0;  // bound on energies per lane
-    int min_lanes = 4;  // fewest energy lanes per line a member may take (at most 32 / min_lanes lines per warp)
+    int min_lanes = 2;  // fewest energy lanes per line a member may take (at most 32 / min_lanes lines per warp)
     int stepper = 0;  // sc_stepper, shared by all members
     bool weighted = false;  // Ozaki energy sums, shared by all members
     int sm_count = 0;
@@ -43,7 +43,7 @@ struct sc_batch {
     int32_t *d_counter = nullptr;  // one work counter per class (at most 8)
     // every member's small kernels in single launches: member tables and offsets
     // (prefix sums over the members, n + 1 each) of their thread blocks: 256
-    // padded points, 16 lines, 32 grid points per component count 1..4, and
+    // padded points, 16 lines, tiles of 8 x 4 grid points per component count 1..4, and
     // reduction blocks of 256 grid points
     scd::MemberDev *d_members = nullptr;
     int64_t *d_off = nullptr;  // [7][n + 1]: pad, slots, back (nc = 1..4), outputs
@@ -115,12 +115,12 @@ void free_plan_buffers(sc_batch *b) {
 // energies per lane (fewer lanes: fewer shuffle rounds, more lines per warp).
 void member_layout(int n_e, int ept_max, int min_lanes, int &lanes, int &ept) {
     int best = 1 << 30;
-    // 9 or 10 energies per lane only on 16 or 32 lanes per line (FP32 bounds above 8);
-    // among equal padding the fewer lanes (fewer issue units per line) come first
-    for (int l : {4, 8, 16, 32}) {
+    // among equal padding the fewer lanes (fewer issue units per line, fewer
+    // shuffle rounds) come first
+    for (int l : {2, 4, 8, 16, 32}) {
         if (l < min_lanes) continue;
         const int e = (n_e + l - 1) / l;
-        if (e < 1 || e > (l >= 16 ? ept_max : std::min(ept_max, 8))) continue;
+        if (e < 1 || e > ept_max) continue;
         if (l * e < best) {
             best = l * e;
             lanes = l;
@@ -296,7 +296,7 @@ sc_status build_member_tables(sc_batch *b) {
         m.n_pad = (nx + 2) * (ny + 2);
         off[0 * (n + 1) + g + 1] = (m.n_pad + 255) / 256;     // blocks of 256 padded points
         off[1 * (n + 1) + g + 1] = ((int64_t)c->geo.lines.size() + 15) / 16;  // blocks of 16 lines
-        for (int k = 1; k <= 4; ++k) off[(1 + k) * (n + 1) + g + 1] = nc == k ? (nx * ny + 31) / 32 : 0;
+        for (int k = 1; k <= 4; ++k) off[(1 + k) * (n + 1) + g + 1] = nc == k ? scd::back_tiles(nx, ny) : 0;
         off[6 * (n + 1) + g + 1] = scd::reduce_blocks(nx * ny);
     }
     for (int a = 0; a < 7; ++a)
@@ -535,6 +535,14 @@ static sc_status iteration(sc_batch *b, int with_outputs, cudaStream_t st) {
     return SC_OK;
 }
 
+sc_status sc_batch_reset_boundary(sc_batch *b) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    b->have_boundary = false;
+    for (sc_ctx *c : b->members) c->have_boundary = false;
+    return SC_OK;
+}
+
 sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream) {
     if (!b || n_sweeps < 0) return SC_EINVAL;
     if (b->failed) return SC_ESTATE;
@@ -600,7 +608,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     int best = b->ept;
     float best_ms = 1e30f;
     b->bps_choice.clear();  // grids at occupancy while the layout is chosen
-    b->min_lanes = 4;
+    b->min_lanes = 2;
     for (int ept = 2; ept <= (b->fp64 ? 8 : 10); ++ept) {
         if (max_ne > 32 * ept) continue;
         sc_status s = build(b, ept);
@@ -621,7 +629,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     // as long as its longest, so more lines per warp trade padding for idle lanes
     int best_min = b->min_lanes;
     best_ms = 1e30f;
-    for (int ml : {4, 8, 16}) {
+    for (int ml : {2, 4, 8, 16}) {
         b->min_lanes = ml;
         sc_status s = build(b, best);
         if (s != SC_OK) return s;

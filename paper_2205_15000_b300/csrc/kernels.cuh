@@ -113,7 +113,13 @@ struct LineF32 {
     int64_t gx0, gy0;    // grid coordinates (x - x0)/h - 1/2 of the first slot's point
     float aext;          // sigma v.A_ext in the symmetric gauge (constant along a line); 0 otherwise
     int32_t pair, ns, slot0;
+    int32_t m0;          // lattice index (along the line, units of h) of the first slot's point
 };
+
+// The FP32 rotate-back takes a grid in tiles of 8 x 4 points, one point per lane
+// of a warp, tiles along x first: the tile's points fall on at most about nine
+// lattice lines and nine samples per line at any angle.
+__host__ __device__ inline int64_t back_tiles(int64_t nx, int64_t ny) { return ((nx + 7) / 8) * ((ny + 3) / 4); }
 
 struct PairF32 {
     int64_t dx, dy;                 // e_par in grid units per sample
@@ -281,7 +287,7 @@ __device__ __forceinline__ int64_t batch_member(const MemberDev *__restrict__ m,
 // Batch iterations: every member's FP32 field conversion and rotation (off_*:
 // prefix sums over the members, n + 1 entries, of their blocks of 256 padded
 // points and of 16 lines), rotate-back of the members with nc components
-// (off_blocks: prefix of blocks of 32 grid points, zero for other members), and
+// (off_blocks: prefix of tiles of 8 x 4 grid points, back_tiles, zero for other members), and
 // outputs (off_blocks: prefix of reduction blocks of 256 grid points).  Each
 // block serves one member and holds its table in shared memory.
 cudaError_t launch_batch_fields_rotate_f32(const MemberDev *members, const int64_t *off_pad, int64_t pad_blocks,

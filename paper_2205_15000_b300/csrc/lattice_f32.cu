@@ -6,6 +6,7 @@
 // weight an exact fraction; the interpolation itself runs in FP32 and the
 // Fermi-surface sums are accumulated in FP32 over blocks of 16 pairs and then
 // in FP64.  The FP64 sweep keeps the plain FP64 kernels in kernels.cu.
+#include <climits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -72,73 +73,101 @@ cudaError_t launch_fields_f32(const GridDev &grid, const int32_t *ghost, const d
     return cudaGetLastError();
 }
 
-// One warp per line: bilinear Delta and A_ind at the line's samples (lanes take
-// samples lane, lane + 32, ..., whose stencils neighbour each other) from the
-// ghost-filled padded grid, which holds the nearest grain point's values
-// wherever a stencil point with a nonzero weight can fall; GAUGE (sc_gauge)
-// selects how A_ext enters: the symmetric gauge's per-line constant, or the
-// landau / solenoid potential at the sample.  The fourth value of a slot is 0
-// (the bounds-checked build counts a stencil point with a nonzero weight and no
-// grain neighbour as a violation).
+// Bilinear Delta and A_ind at sample q of a line from the ghost-filled padded
+// grid, which holds the nearest grain point's values wherever a stencil point
+// with a nonzero weight can fall; GAUGE (sc_gauge) selects how A_ext enters: the
+// symmetric gauge's per-line constant, or the landau / solenoid potential at the
+// sample.  The fourth value of a slot is 0 (the bounds-checked build counts a
+// stencil point with a nonzero weight and no grain neighbour as a violation).
 template <int GAUGE>
-__device__ __forceinline__ void rotate_f32_line(const LineF32 &ln, const PairF32 &pp, const GridDev &grid,
-                                                const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
-                                                const float2 *__restrict__ padc, float4 *__restrict__ out, int lane) {
-    const int nsl = ln.ns > 0 ? ln.ns : 1;
-    if (!(in_bounds(ln.slot0, grid.n_slots) && in_bounds((int64_t)ln.slot0 + nsl - 1, grid.n_slots))) return;
+__device__ __forceinline__ float4 rotate_f32_sample(const LineF32 &ln, const PairF32 &pp, const GridDev &grid,
+                                                    const int32_t *__restrict__ ghost,
+                                                    const float4 *__restrict__ pad0, const float2 *__restrict__ padc,
+                                                    int q) {
     const int px = grid.nx + 2;
     const int64_t npad = (int64_t)px * (grid.ny + 2);
-    for (int q = lane; q < nsl; q += 32) {
-        int i0, j0;
-        float fx, fy;
-        split_fixed(ln.gx0 + (int64_t)q * pp.dx, i0, fx);
-        split_fixed(ln.gy0 + (int64_t)q * pp.dy, j0, fy);
-        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
-            const int base = (j0 + 1) * px + (i0 + 1);
-            const float4 p00 = pad0[base], p10 = pad0[base + 1], p01 = pad0[base + px], p11 = pad0[base + px + 1];
-            const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
-            const float dr = w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x;
-            const float di = w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y;
-            const float ax = w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z;
-            const float ay = w00 * p00.w + w10 * p10.w + w01 * p01.w + w11 * p11.w;
-            o.x = pp.eta * dr;
-            o.y = pp.eta * di;
-            // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
-            for (int c = 1; c < grid.n_comp; ++c) {
-                const float2 *pc = padc + (c - 1) * npad;
-                const float2 e00 = pc[base], e10 = pc[base + 1], e01 = pc[base + px], e11 = pc[base + px + 1];
-                o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
-                o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
-            }
-#ifdef SC_DEBUG_BOUNDS
-            in_bounds((ghost[base] >= 0 || w00 == 0.f) && (ghost[base + 1] >= 0 || w10 == 0.f) &&
-                              (ghost[base + px] >= 0 || w01 == 0.f) && (ghost[base + px + 1] >= 0 || w11 == 0.f)
-                          ? 0
-                          : -1,
-                      1);
-#endif
-            float az = ln.aext;
-            if (GAUGE != 0) {
-                // landau and solenoid gauges: A_ext at the sample, from its exact
-                // fixed-point offset to the gauge origin
-                const float sc = (float)(grid.h / (double)(1ll << kFixBits));  // fixed-point unit times h
-                const float xr = (float)(ln.gx0 + (int64_t)q * pp.dx - grid.gfx) * sc;
-                const float yr = (float)(ln.gy0 + (int64_t)q * pp.dy - grid.gfy) * sc;
-                float axe, aye;
-                if (GAUGE == 2) {
-                    const float c = 0.5f * (float)grid.flux / (xr * xr + yr * yr);
-                    axe = -c * yr;
-                    aye = c * xr;
-                } else {
-                    axe = -(float)grid.bfield * yr;
-                    aye = 0.f;
-                }
-                az += (float)grid.charge_sign * (pp.ex_f * axe + pp.ey_f * aye);
-            }
-            o.z = az + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
+    int i0, j0;
+    float fx, fy;
+    split_fixed(ln.gx0 + (int64_t)q * pp.dx, i0, fx);
+    split_fixed(ln.gy0 + (int64_t)q * pp.dy, j0, fy);
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i0 >= -1 && i0 <= grid.nx - 1 && j0 >= -1 && j0 <= grid.ny - 1) {
+        const int base = (j0 + 1) * px + (i0 + 1);
+        const float4 p00 = pad0[base], p10 = pad0[base + 1], p01 = pad0[base + px], p11 = pad0[base + px + 1];
+        const float w00 = (1.f - fx) * (1.f - fy), w10 = fx * (1.f - fy), w01 = (1.f - fx) * fy, w11 = fx * fy;
+        const float dr = w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x;
+        const float di = w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y;
+        const float ax = w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z;
+        const float ay = w00 * p00.w + w10 * p10.w + w01 * p01.w + w11 * p11.w;
+        o.x = pp.eta * dr;
+        o.y = pp.eta * di;
+        // Delta(p, sample) = sum_c eta_c(p) Delta_c(sample) (Eq. order_parameter)
+        for (int c = 1; c < grid.n_comp; ++c) {
+            const float2 *pc = padc + (c - 1) * npad;
+            const float2 e00 = pc[base], e10 = pc[base + 1], e01 = pc[base + px], e11 = pc[base + px + 1];
+            o.x += pp.eta_c[c] * (w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x);
+            o.y += pp.eta_c[c] * (w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y);
         }
-        out[ln.slot0 + q] = o;
+#ifdef SC_DEBUG_BOUNDS
+        in_bounds((ghost[base] >= 0 || w00 == 0.f) && (ghost[base + 1] >= 0 || w10 == 0.f) &&
+                          (ghost[base + px] >= 0 || w01 == 0.f) && (ghost[base + px + 1] >= 0 || w11 == 0.f)
+                      ? 0
+                      : -1,
+                  1);
+#else
+        (void)ghost;
+#endif
+        float az = ln.aext;
+        if (GAUGE != 0) {
+            // landau and solenoid gauges: A_ext at the sample, from its exact
+            // fixed-point offset to the gauge origin
+            const float sc = (float)(grid.h / (double)(1ll << kFixBits));  // fixed-point unit times h
+            const float xr = (float)(ln.gx0 + (int64_t)q * pp.dx - grid.gfx) * sc;
+            const float yr = (float)(ln.gy0 + (int64_t)q * pp.dy - grid.gfy) * sc;
+            float axe, aye;
+            if (GAUGE == 2) {
+                const float c = 0.5f * (float)grid.flux / (xr * xr + yr * yr);
+                axe = -c * yr;
+                aye = c * xr;
+            } else {
+                axe = -(float)grid.bfield * yr;
+                aye = 0.f;
+            }
+            az += (float)grid.charge_sign * (pp.ex_f * axe + pp.ey_f * aye);
+        }
+        o.z = az + (float)grid.charge_sign * (pp.ex_f * ax + pp.ey_f * ay);
+    }
+    return o;
+}
+
+// One warp per four consecutive lines (lines of a pair are neighbours on the
+// lattice), eight lanes per line: lane (k, s) takes the sample of line L0 + k at
+// lattice index mb + s, so one pass of the warp covers a patch of 8 samples x 4
+// lines -- its bilinear stencils lie within about nine grid rows and columns at
+// any angle -- and stores 8 consecutive slots (128 bytes) of each line.
+template <int GAUGE>
+__device__ __forceinline__ void rotate_f32_quad(const LineF32 *__restrict__ lines, int64_t L0, int32_t n_lines,
+                                                const PairF32 *__restrict__ pairs, const GridDev &grid,
+                                                const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
+                                                const float2 *__restrict__ padc, float4 *__restrict__ out, int lane) {
+    const int k = lane >> 3, s = lane & 7;
+    const int64_t L = L0 + k;
+    LineF32 ln{};
+    bool ok = L < n_lines;
+    if (ok) ln = lines[L];
+    ok = ok && in_bounds(ln.pair, grid.n_pairs);
+    const int nsl = ln.ns > 0 ? ln.ns : 1;
+    ok = ok && in_bounds(ln.slot0, grid.n_slots) && in_bounds((int64_t)ln.slot0 + nsl - 1, grid.n_slots);
+    int lo = ok ? ln.m0 : INT_MAX, hi = ok ? ln.m0 + nsl : INT_MIN;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+    }
+    const PairF32 &pp = pairs[ok ? ln.pair : 0];
+    for (int mb = lo; mb < hi; mb += 8) {
+        const int q = mb + s - ln.m0;
+        if (ok && q >= 0 && q < nsl) out[ln.slot0 + q] = rotate_f32_sample<GAUGE>(ln, pp, grid, ghost, pad0, padc, q);
     }
 }
 
@@ -148,11 +177,9 @@ __global__ void __launch_bounds__(128) rotate_f32_kernel(const LineF32 *__restri
                                                          const int32_t *__restrict__ ghost,
                                                          const float4 *__restrict__ pad0,
                                                          const float2 *__restrict__ padc, float4 *__restrict__ out) {
-    const int64_t L = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-    if (L >= grid.n_lines) return;
-    const LineF32 ln = lines[L];
-    if (!in_bounds(ln.pair, grid.n_pairs)) return;
-    rotate_f32_line<GAUGE>(ln, pairs[ln.pair], grid, ghost, pad0, padc, out, threadIdx.x & 31);
+    const int64_t L0 = (int64_t)blockIdx.x * 16 + 4 * (threadIdx.x >> 5);  // 16 lines per block
+    if (L0 >= grid.n_lines) return;
+    rotate_f32_quad<GAUGE>(lines, L0, grid.n_lines, pairs, grid, ghost, pad0, padc, out, threadIdx.x & 31);
 }
 
 cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, int64_t n_slots,
@@ -161,7 +188,7 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
                               cudaStream_t st) {
     (void)slot_line;
     (void)n_slots;
-    const unsigned nb = (unsigned)((grid.n_lines + 3) / 4);  // four lines (warps) per block
+    const unsigned nb = (unsigned)((grid.n_lines + 15) / 16);  // 16 lines per block, four per warp
     if (nb == 0) return cudaSuccess;
     if (grid.gauge == 2)
         rotate_f32_kernel<2><<<nb, 128, 0, st>>>(lines, pairs, grid, ghost, pad0, padc, image_in);
@@ -173,7 +200,9 @@ cudaError_t launch_rotate_f32(const LineF32 *lines, const int32_t *slot_line, in
 }
 
 // Rotate back: for every pair, bilinear gather of the four image slots around the
-// grid point's lattice coordinates and the Fermi-surface sum.  A block of four warps takes 32 consecutive grid points; warp q sums the 16-pair
+// grid point's lattice coordinates and the Fermi-surface sum.  A block of four
+// warps takes a tile of 8 x 4 grid points (so a warp's gathers of one pair touch
+// a patch of about nine lattice lines and samples); warp q sums the 16-pair
 // chunks q, q + 4, q + 8, ... of every point (FP32 within a chunk, FP64 across
 // chunks), so the lanes of a warp gather neighbouring samples of the same pair;
 // warp 0 adds the four partial sums in a fixed order.
@@ -186,11 +215,14 @@ __device__ __forceinline__ void rotate_back_f32_block(const PairF32 *__restrict_
     __shared__ double part[3][NV][32];
     const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t idx = blk * 32 + lane;
-    const bool live = idx < npts;
+    // the block's tile of 8 x 4 points (back_tiles), one point per lane
+    const int64_t tiles_x = (grid.nx + 7) / 8;
+    const int64_t ty = blk / tiles_x, tx = blk - ty * tiles_x;
+    const int64_t i = tx * 8 + (lane & 7), j = ty * 4 + (lane >> 3);
+    const bool live = i < grid.nx && j < grid.ny;
+    const int64_t idx = live ? j * grid.nx + i : 0;
     double A[NV] = {};  // the point's sums; [5 + 2c], [6 + 2c]: <eta_c Sf> of components c >= 1
     if (live && mask[idx]) {
-        const int64_t i = idx % grid.nx, j = idx / grid.nx;
         for (int p0 = 16 * q; p0 < n_pairs; p0 += 64) {
             float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
             float ac[2 * NC] = {};
@@ -270,9 +302,8 @@ __global__ void __launch_bounds__(128) rotate_back_f32_kernel(const PairF32 *__r
 cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const BackLine *bl,
                                    const GridDev &grid, const uint8_t *mask, const float4 *image_out,
                                    double *acc, cudaStream_t st) {
-    const int64_t npts = (int64_t)grid.nx * grid.ny;
     const int bs = 128;
-    const unsigned nb = (unsigned)((npts + 31) / 32);  // 32 grid points per block of four warps
+    const unsigned nb = (unsigned)back_tiles(grid.nx, grid.ny);  // a tile of 8 x 4 points per block of four warps
     switch (grid.n_comp) {
         case 1: rotate_back_f32_kernel<1><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
         case 2: rotate_back_f32_kernel<2><<<nb, bs, 0, st>>>(pairs, n_pairs, bl, grid, mask, image_out, acc); break;
@@ -299,21 +330,17 @@ __global__ void __launch_bounds__(128) batch_rotate_f32_kernel(const MemberDev *
                                                                const int64_t *__restrict__ off, int n) {
     __shared__ MemberDev M;
     const int64_t blk = batch_member(m, off, n, M);  // 16 lines per block, four per warp
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int k = 0; k < 4; ++k) {
-        const int64_t L = blk * 16 + 4 * k + w;
-        if (L >= M.grid.n_lines) break;
-        const LineF32 ln = M.lines[L];
-        if (!in_bounds(ln.pair, M.grid.n_pairs)) continue;
-        switch (M.grid.gauge) {
-            case 2: rotate_f32_line<2>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
-            case 1: rotate_f32_line<1>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
-            default: rotate_f32_line<0>(ln, M.pairs[ln.pair], M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane);
-        }
+    const int64_t L0 = blk * 16 + 4 * (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (L0 >= M.grid.n_lines) return;
+    switch (M.grid.gauge) {
+        case 2: rotate_f32_quad<2>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+        case 1: rotate_f32_quad<1>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+        default: rotate_f32_quad<0>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane);
     }
 }
 
-// off: prefix of the members' blocks of 32 grid points, zero for members with
+// off: prefix of the members' tiles of 8 x 4 grid points, zero for members with
 // another component count than NC
 template <int NC>
 __global__ void __launch_bounds__(128) batch_rotate_back_f32_kernel(const MemberDev *__restrict__ m,

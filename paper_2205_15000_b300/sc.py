@@ -119,7 +119,8 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
-            "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_autotune",
+            "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_reset_boundary",
+            "sc_batch_autotune",
             "sc_batch_get_info", "sc_batch_set_fields", "sc_batch_get_outputs", "sc_last_error", "sc_version"]
 
 
@@ -173,6 +174,7 @@ def _load():
         "sc_batch_member": [vp, i32, P(vp)],
         "sc_batch_sweep": [vp, vp],
         "sc_batch_run": [vp, i32, i32, vp],
+        "sc_batch_reset_boundary": [vp],
         "sc_batch_autotune": [vp, P(i32), vp],
         "sc_batch_get_info": [vp, P(sc_batch_info)],
         "sc_batch_set_fields": [vp, vp, ctypes.c_int, vp],
@@ -488,6 +490,11 @@ def sc_batch_run(b, n_sweeps, with_outputs=True, stream=None):
     _check(lib.sc_batch_run(b, int(n_sweeps), int(bool(with_outputs)), _stream(stream)))
 
 
+def sc_batch_reset_boundary(b):
+    """The next batch sweep starts from fresh boundary values (layout kept)."""
+    _check(lib.sc_batch_reset_boundary(b))
+
+
 def sc_batch_autotune(b, stream=None):
     e = ctypes.c_int32(0)
     _check(lib.sc_batch_autotune(b, ctypes.byref(e), _stream(stream)))
@@ -537,6 +544,9 @@ class Batch:
 
     def run(self, n_sweeps, with_outputs=True, stream=None):
         sc_batch_run(self.h, n_sweeps, with_outputs, stream)
+
+    def reset_boundary(self):
+        sc_batch_reset_boundary(self.h)
 
     def info(self):
         return sc_batch_get_info(self.h)

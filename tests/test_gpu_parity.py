@@ -144,7 +144,7 @@ def test_ozaki_sums_match_oracle(name, stepper):
         assert _rel(r["F"][m], o["F"][m]) < TOL_F
 
 
-@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [2, 4, 8, 16, 32])
 def test_lane_layouts_agree(lanes):
     """Every lanes-per-line layout (with padded energies) gives the FP64 result."""
     p, delta, aind = case("disc_vortex_ragged")
@@ -152,6 +152,27 @@ def test_lane_layouts_agree(lanes):
     r, o = res[-1]["r"], res[-1]["o"]
     np.testing.assert_allclose(r["delta_new"], o["delta_new"], atol=TOL64, rtol=0)
     np.testing.assert_allclose(r["j"], o["j"], atol=TOL64, rtol=0)
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 16])
+@pytest.mark.parametrize("stepper", ["closed", "midpoint"])
+def test_fp32_lane_layouts_within_tolerance(lanes, stepper):
+    """The packed FP32 sweep on 2 lanes per line (16 lines per warp, 7 energies per
+    lane), 4 and 16 lanes, against the oracle over three sweeps (boundary values
+    carried over), images and exits included."""
+    p, delta, aind = case("disc_vortex_ragged")
+    p["stepper"] = stepper
+    g, ctx, m, res = _run_both(p, delta, aind, "fp32", lanes=lanes)
+    assert _sc().sc_get_info(ctx.h).lanes_per_line == lanes
+    for R in res:
+        o, r = R["o"], R["r"]
+        assert _rel(r["delta_new"][m], o["delta_new"][m]) < TOL_DELTA
+        assert _rel(r["j"][m], o["j"][m], J_FLOOR) < TOL_J
+        assert _rel(r["F"][m], o["F"][m]) < TOL_F
+        assert np.max(np.abs(R["exits"] - o["exit"][0])) < 2e-5
+        oi = _oracle_pair_images(g, o["images"])
+        err = np.max(np.abs(R["images"] - oi), axis=0) / np.max(np.abs(oi), axis=0)
+        assert np.all(err < 4e-5), err
 
 
 def test_picard_with_vector_potential_matches_oracle():
