@@ -150,7 +150,9 @@ __device__ __forceinline__ void rotate_f32_quad(const LineF32 *__restrict__ line
                                                 const PairF32 *__restrict__ pairs, const GridDev &grid,
                                                 const int32_t *__restrict__ ghost, const float4 *__restrict__ pad0,
                                                 const float2 *__restrict__ padc, float4 *__restrict__ out, int lane) {
-    const int k = lane >> 3, s = lane & 7;
+    // each quarter-warp (8 lanes, one wavefront of 16-byte loads) takes 2 lines x 4
+    // samples: lines k = 0..3, samples s = 0..7 of the patch
+    const int k = ((lane >> 2) & 1) + 2 * (lane >> 4), s = (lane & 3) + 4 * ((lane >> 3) & 1);
     const int64_t L = L0 + k;
     LineF32 ln{};
     bool ok = L < n_lines;
@@ -218,7 +220,8 @@ __device__ __forceinline__ void rotate_back_f32_block(const PairF32 *__restrict_
     // the block's tile of 8 x 4 points (back_tiles), one point per lane
     const int64_t tiles_x = (grid.nx + 7) / 8;
     const int64_t ty = blk / tiles_x, tx = blk - ty * tiles_x;
-    const int64_t i = tx * 8 + (lane & 7), j = ty * 4 + (lane >> 3);
+    // each quarter-warp takes 4 x 2 of the tile's points
+    const int64_t i = tx * 8 + (lane & 3) + 4 * ((lane >> 3) & 1), j = ty * 4 + ((lane >> 2) & 1) + 2 * (lane >> 4);
     const bool live = i < grid.nx && j < grid.ny;
     const int64_t idx = live ? j * grid.nx + i : 0;
     double A[NV] = {};  // the point's sums; [5 + 2c], [6 + 2c]: <eta_c Sf> of components c >= 1
