@@ -18,9 +18,6 @@
 
 namespace scd {
 
-// fetch the line of global memory holding p into L2 (a hint; no register result)
-__device__ __forceinline__ void l2_hint(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // complex value(s) with packed parts: V = f2 (two energies) or float (one)
 template <typename V>
 struct CV {

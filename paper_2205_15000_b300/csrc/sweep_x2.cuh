@@ -83,6 +83,9 @@ __device__ __forceinline__ void principal(f2 x, f2 y, f2 sq, f2 yq, f2 &re, f2 &
     principal(x.y, y.y, sq.y, yq.y, re.y, im.y);
 }
 
+// fetch the line of global memory holding p into L2 (a hint; no register result)
+__device__ __forceinline__ void l2_hint(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 constexpr float kRs2 = 0.70710678118654752f;  // 1/sqrt(2)
 constexpr float kLog2e = 1.4426950408889634f;
 

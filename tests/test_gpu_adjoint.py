@@ -147,6 +147,24 @@ def test_fp32_adjoint_close_to_fp64():
     assert np.max(np.abs(ga32 - ga64)) <= 1e-3 * np.max(np.abs(ga64))
 
 
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_fp32_adjoint_in_forced_lane_layouts(lanes):
+    """The FP32 adjoint in a forced layout (2 lanes per line: 16 lines per warp, 4
+    energies per lane; 4 and 8 lanes) against the FP64 adjoint: the lines of a
+    warp and the lane sums of the cotangents in every layout."""
+    from paper_2205_15000_b300 import sc
+    p, d, a = _grain()
+    gd64, ga64 = _adjoint(p, d, a, "fp64", g_Ftotal=1.0)
+    ctx = sc.Context(p, precision="fp32", lanes_per_line=lanes)
+    assert sc.sc_get_info(ctx.h).lanes_per_line == lanes
+    ctx.set_fields(d, a)
+    sc.sc_burnin(ctx.h, 300, 1e-6)
+    ctx.sweep()
+    gd32, ga32 = (x.cpu().numpy() for x in ctx.adjoint(g_Ftotal=1.0))
+    assert np.max(np.abs(gd32 - gd64)) <= 1e-3 * np.max(np.abs(gd64))
+    assert np.max(np.abs(ga32 - ga64)) <= 1e-3 * np.max(np.abs(ga64))
+
+
 def _oracle_ldos_fixed(g, d, a, e, dl, ex):
     im, _ = g.sweep(d, a, np.asarray(e) + 1j * dl, 1, ex)
     return g.rotate_back(im, 1, len(e))
