@@ -517,7 +517,10 @@ def run_ours(args):
                 if e2e_ms else None),
         # per step: (FP32: field conversion,) rotate, sweep, rotate-back, outputs;
         # adjoint: output cotangents, transposed rotate-back, adjoint sweep, transposed rotate
-        "gpu_launches": ((5 if args.precision == "fp32" else 4) + (4 if args.adjoint else 0)) * args.steps,
+        # a step: (FP32: field conversion,) rotate, sweep, (energy-block sums,)
+        # rotate-back, outputs and their final sums; the adjoint's launches on top
+        "gpu_launches": ((6 if args.precision == "fp32" else 5) + (1 if p["n_energies"] > 32 * 8 else 0)
+                         + (4 if args.adjoint else 0)) * args.steps,
         "loop_glue": ({"vector_potential_ms": vp_ms, "method": "zero-padded FFT convolution, FP64",
                        "outside_timed_region": True} if vp_ms is not None else None),
         "clocks": clocks,
@@ -757,6 +760,7 @@ def run_batch(args):
                "ms_per_step": e2e_ms, "host_enqueue_ms_per_step": (t_enq - t0) * 1e3 / n_e2e,
                "steps": n_e2e}
     fp32_launches = info.sweep_launches
+    launches_per_iteration = info.launches_per_iteration
     fp32_lane_fill = info.steps_per_sweep / max(info.lane_steps_per_sweep, 1)
     last = b.info()
     classes = [{"energies_per_lane": last.class_ept[k], "blocks_per_sm": last.class_blocks_per_sm[k],
@@ -838,9 +842,10 @@ def run_batch(args):
                                            "8 independent FMA chains per thread"},
         "fp64_plain": fp64,
         "e2e": e2e,
-        # per member: (FP32: field conversion,) rotate, rotate-back, outputs and the
-        # final sums; plus one sweep launch per energies-per-lane class
-        "gpu_launches": ((5 if args.precision == "fp32" else 4) * args.grains + fp32_launches) * args.steps,
+        # one iteration: (FP32) the field conversion and rotation over all members,
+        # one sweep launch per energies-per-lane class, energy-block sums, the
+        # rotate-back (one launch per component count present), outputs and final sums
+        "gpu_launches": launches_per_iteration * args.steps,
         "clocks": clocks,
         "wall_s": t_wall,
     }

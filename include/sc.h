@@ -361,6 +361,8 @@ typedef struct {
     int32_t class_blocks_per_sm[8]; /* per launch: resident blocks per SM its grid is sized for */
     double class_ms[8];        /* per launch: its duration in the last batch sweep */
     int32_t min_lanes_per_line; /* fewest energy lanes per line a member may take */
+    int32_t launches_per_iteration; /* kernel launches of one batch iteration with outputs
+                                       (sc_batch_run with with_outputs = 1) */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as

@@ -747,6 +747,16 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     info->sweep_launches = (int32_t)b->classes.size();
     info->scratch_bytes = (int64_t)b->scratch_bytes;
     info->min_lanes_per_line = b->min_lanes;
+    // the launches sc_batch_sweep and the outputs of iteration() make
+    int32_t nl = (int32_t)b->classes.size() + 2;  // sweep classes; outputs and their final sums
+    for (int nbk : b->member_blocks) nl += nbk > 1 ? 1 : 0;  // energy-block sums
+    if (!b->fp64) {
+        nl += (b->tot_pad > 0) + (b->tot_slots > 0);
+        for (int k = 0; k < 4; ++k) nl += b->tot_back[k] > 0;
+    } else {
+        nl += 2 * (int32_t)b->members.size();  // rotate and rotate-back per member
+    }
+    info->launches_per_iteration = nl;
     for (size_t k = 0; k < b->classes.size() && k < 8; ++k) {
         info->class_ept[k] = b->classes[k].ept;
         info->class_blocks_per_sm[k] = b->classes[k].bps;

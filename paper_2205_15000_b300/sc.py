@@ -80,6 +80,7 @@ class sc_batch_info(ctypes.Structure):
         ("lane_steps_per_sweep", ctypes.c_int64), ("sweep_launches", ctypes.c_int32),
         ("class_ept", ctypes.c_int32 * 8), ("class_blocks_per_sm", ctypes.c_int32 * 8),
         ("class_ms", ctypes.c_double * 8), ("min_lanes_per_line", ctypes.c_int32),
+        ("launches_per_iteration", ctypes.c_int32),
     ]
 
 

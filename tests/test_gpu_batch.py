@@ -160,6 +160,10 @@ def test_batch_energy_layout_per_member(precision):
     info = b.info()
     assert info.lane_steps_per_sweep == expect
     assert info.sweep_launches == len(counts)
+    # FP32: field conversion, rotation, rotate-back (one component count), outputs and
+    # final sums around the class launches; FP64: rotate and rotate-back per member
+    extra = 5 if precision == "fp32" else 2 + 2 * len(grains)
+    assert info.launches_per_iteration == info.sweep_launches + extra
     b.close()
 
 
