@@ -764,7 +764,7 @@ def run_batch(args):
     fp32_lane_fill = info.steps_per_sweep / max(info.lane_steps_per_sweep, 1)
     last = b.info()
     classes = [{"energies_per_lane": last.class_ept[k], "blocks_per_sm": last.class_blocks_per_sm[k],
-                "ms": last.class_ms[k]} for k in range(min(last.sweep_launches, 8))]
+                "ms": last.class_ms[k]} for k in range(last.sweep_launches)]
     b.close()
     del b
 
@@ -824,6 +824,8 @@ def run_batch(args):
                    "energies_per_lane": ept, "precision": args.precision, "stepper": args.stepper,
                    "energy_sum": args.energy_sum, "lane_fill": fp32_lane_fill,
                    "sweep_launches": fp32_launches, "sweep_classes": classes,
+                   "two_part_members": last.split_members,
+                   "autotune_split_ms": {"with_parts": last.split_ms_on, "without": last.split_ms_off},
                    "min_lanes_per_line": last.min_lanes_per_line,
                    "step": "one batch iteration: every member's rotate, the sweep, rotate-back and outputs",
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",

@@ -354,15 +354,19 @@ typedef struct {
     int32_t energies_per_lane; /* bound on any member's energies per lane */
     int64_t steps_per_sweep;   /* closed-form steps of one batch sweep, all grains */
     int64_t scratch_bytes;
-    double ms_sweep;           /* last batch sweep kernel (CUDA events on its stream) */
+    double ms_sweep;           /* last batch sweep: its class launches and the sums of energy
+                                  blocks and parts (CUDA events on its stream) */
     int64_t lane_steps_per_sweep; /* steps the lanes execute, padded energy slots included */
     int32_t sweep_launches;    /* uniform sweep launches per batch sweep (one per layout class) */
-    int32_t class_ept[8];      /* per launch (class): its energies per lane */
-    int32_t class_blocks_per_sm[8]; /* per launch: resident blocks per SM its grid is sized for */
-    double class_ms[8];        /* per launch: its duration in the last batch sweep */
+    int32_t class_ept[16];     /* per launch (class, sweep_launches of them): its energies per lane */
+    int32_t class_blocks_per_sm[16]; /* per launch: resident blocks per SM its grid is sized for */
+    double class_ms[16];       /* per launch: its duration in the last batch sweep */
     int32_t min_lanes_per_line; /* fewest energy lanes per line a member may take */
     int32_t launches_per_iteration; /* kernel launches of one batch iteration with outputs
                                        (sc_batch_run with with_outputs = 1) */
+    int32_t split_members;      /* members whose energies run as two parts in their own layouts */
+    double split_ms_on, split_ms_off; /* sc_batch_autotune's sweep times with and without two-part
+                                         members (0 before it runs) */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
@@ -372,7 +376,12 @@ typedef struct {
    Each member takes the lanes per line (2, 4, 8, 16, 32; at least the batch's
    fewest, 2 unless sc_batch_autotune raises it) and energies per lane (<= the
    bound; 9 and 10 only without energy blocks) with the fewest padded lane
-   slots, then the most energies per lane.  Members with
+   slots, then the most energies per lane.  An FP32 member whose layout pads
+   its energies may instead run them as two parts, [0, n1) and [n1, n_e), each
+   in its own layout and image (added in order after the sweep), where the
+   padded lane slots weighted by the measured cost of a lane-step at each
+   energies-per-lane count fall by at least 2 % (132 energies: 2 x 10 and
+   16 x 7 instead of 16 x 9).  Members with
    equal energies per lane share one persistent launch; a batch sweep runs
    these launches back to back.  The members are owned by the batch. */
 sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,
@@ -398,6 +407,7 @@ sc_status sc_batch_reset_boundary(sc_batch *b);
 /* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
    keep the fastest; then the fewest lanes per line a member may take (2, 4, 8, 16:
    at most 16, 8, 4, 2 lines per warp, which a warp steps as long as its longest);
+   then (FP32) the members in two energy parts where that pays or all in one;
    then, for that layout, size every class launch's persistent
    grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
    per SM and keep, per class, the fastest (each class launch timed by its own

@@ -20,6 +20,10 @@ struct sc_batch {
     std::vector<sc_ctx *> members;
     std::vector<int> member_blocks;  // energy blocks of each member's layout
     std::vector<Plan *> member_plan; // each member's layout (owned by the member context)
+    std::vector<int> member_parts;   // 2: the member's energies in two parts of their own layouts
+    std::vector<void *> part_img;    // per member: the two parts' images (2 n_slots float4), lazily
+    bool split = true;               // FP32: members may take two energy parts
+    float split_ms[2] = {0.f, 0.f};  // the autotune's sweep times with and without parts
     int blocked = 0;                 // some member splits its energies into blocks
     int device = 0;
     bool fp64 = false;
@@ -29,6 +33,7 @@ struct sc_batch {
     bool weighted = false;  // Ozaki energy sums, shared by all members
     int sm_count = 0;
     scd::GrainSweep *d_grains = nullptr;
+    int32_t n_gs = 0;  // sweep descriptors: one per member, two for a member in two energy parts
     int2 *d_items = nullptr;
     int32_t n_items = 0;
     int64_t stride = 0;
@@ -40,7 +45,8 @@ struct sc_batch {
     std::vector<Class> classes;
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
-    int32_t *d_counter = nullptr;  // one work counter per class (at most 8)
+    static constexpr int kMaxClasses = 16;  // energies-per-lane classes (1..10 energies per lane)
+    int32_t *d_counter = nullptr;  // one work counter per class
     // every member's small kernels in single launches: member tables and offsets
     // (prefix sums over the members, n + 1 each) of their thread blocks: 256
     // padded points, 16 lines, tiles of 8 x 4 grid points per component count 1..4, and
@@ -58,7 +64,7 @@ struct sc_batch {
     int64_t steps_per_sweep = 0;
     int64_t lane_steps_per_sweep = 0;  // with padded energy slots, for the current layout
     cudaEvent_t ev[2] = {nullptr, nullptr};
-    cudaEvent_t cev[9] = {};  // around each class launch of the last sweep
+    cudaEvent_t cev[kMaxClasses + 1] = {};  // around each class launch of the last sweep
     std::vector<int> bps_choice;  // autotuned blocks per SM of each class (empty: occupancy)
     bool timed = false;
     // captured iterations: graph[p] = one sweep starting from parity p (+ outputs)
@@ -142,12 +148,52 @@ void member_layout(int n_e, int ept_max, int min_lanes, int &lanes, int &ept) {
         }
 }
 
+// Relative cost of a lane layout per line and sample: its lane slots over the
+// fraction of the FP32 peak a lane-step reaches with that many energies per lane
+// (measured per class on the 64-grain batch: 0.58-0.61 from 5 energies per lane
+// up, 0.53 at 4, 0.45 at 3; 1 and 2 estimated).
+double layout_cost(int lanes, int ept) {
+    static const double rate[5] = {1.0, 0.25, 0.35, 0.45, 0.53};
+    return (double)lanes * ept / (ept < 5 ? rate[ept] : 0.6);
+}
+
+struct Part {
+    int first, n, lanes, ept;
+};
+
+// The member's energies as one layout, or (FP32) as two parts [0, n1) and
+// [n1, n_e), each in its own layout, where that costs at least 2 % less than
+// the padded single layout (e.g. 132 energies: 2 x 10 and 16 x 7 lanes x
+// energies instead of 16 x 9).
+std::vector<Part> member_parts(int n_e, int ept_max, int min_lanes, bool split) {
+    int lanes = 32, ept = ept_max;
+    member_layout(n_e, ept_max, min_lanes, lanes, ept);
+    std::vector<Part> one{{0, n_e, lanes, ept}};
+    if (!split || lanes * ept <= n_e || n_e > 32 * ept_max) return one;  // no padding, or blocks
+    double best = 0.95 * layout_cost(lanes, ept);
+    std::vector<Part> res = one;
+    for (int n1 = 1; n1 < n_e; ++n1) {
+        int l1 = 32, e1 = ept_max, l2 = 32, e2 = ept_max;
+        member_layout(n1, ept_max, min_lanes, l1, e1);
+        member_layout(n_e - n1, ept_max, min_lanes, l2, e2);
+        if (e1 < 5 || e2 < 5) continue;  // a part repeats the per-sample work of every line
+        const double c = layout_cost(l1, e1) + layout_cost(l2, e2);
+        if (c < best) {
+            best = c;
+            res = {{0, n1, l1, e1}, {n1, n_e - n1, l2, e2}};
+        }
+    }
+    return res;
+}
+
 // Lay out the work list for at most `ept` energies per lane.
 sc_status build(sc_batch *b, int ept) {
     free_graphs(b);  // captured graphs refer to the buffers rebuilt here
-    std::vector<scd::GrainSweep> gs(b->members.size());
+    std::vector<scd::GrainSweep> gs;
     b->member_blocks.assign(b->members.size(), 1);
     b->member_plan.assign(b->members.size(), nullptr);
+    b->member_parts.assign(b->members.size(), 1);
+    b->part_img.resize(b->members.size(), nullptr);
     struct It {
         int cost, grain, group;
     };
@@ -156,45 +202,59 @@ sc_status build(sc_batch *b, int ept) {
     int64_t lane_steps = 0;
     for (size_t g = 0; g < b->members.size(); ++g) {
         sc_ctx *c = b->members[g];
-        int lanes = 32, eg = ept;
-        member_layout(c->n_e, ept, b->min_lanes, lanes, eg);
-        Plan *pl = nullptr;
-        sc_status st = sc_internal::make_plan_layout(c, c->n_e, lanes, eg, &pl);
-        if (st != SC_OK) return berr(b, st, c->err);
-        scd::GrainSweep &d = gs[g];
-        d.lines = c->d_lines;
-        d.groups = pl->d_groups;
-        d.image_in = c->d_img_in;
-        // a blocked member writes one image per energy block (added after the sweep)
-        d.image_out = pl->n_blocks > 1 ? pl->d_img_blocks : c->d_img_out;
-        d.n_slots = c->geo.n_slots;
-        d.n_lines = (int32_t)c->geo.lines.size();
-        d.n_groups = pl->n_groups;
-        d.exits[0] = c->d_exit[0];
-        d.exits[1] = c->d_exit[1];
-        d.energies = nullptr;
-        d.mats_eps = c->d_eps;
-        d.mats_w = c->d_ewt;
-        d.t = c->geo.prm.t;
-        d.h = c->geo.prm.h;
-        d.broadening = 0.0;
-        d.n_e = c->n_e;
-        d.lanes = pl->lanes;
-        d.lines_per_warp = pl->lines_per_warp;
-        d.ne_pad = pl->lanes * pl->ept;
-        d.max_ns = std::max(c->geo.max_ns, 1);
-        d.ept = pl->ept;
-        d.n_blocks = pl->n_blocks;
-        b->member_blocks[g] = pl->n_blocks;
-        b->member_plan[g] = pl;
-        stride = std::max(stride, pl->stride);
-        int64_t steps = 0;
-        for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
-        lane_steps += steps * pl->lanes * pl->ept * pl->n_blocks;
-        // cost of a group ~ steps x energies handled per lane; one item per energy block
-        for (int q = 0; q < pl->n_groups; ++q)
-            for (int k = 0; k < pl->n_blocks; ++k)
-                items.push_back({pl->group_cost[q] * pl->ept, (int)g, q * pl->n_blocks + k});
+        const std::vector<Part> parts = member_parts(c->n_e, ept, b->min_lanes, b->split && !b->fp64);
+        const bool two = parts.size() > 1;
+        b->member_parts[g] = (int)parts.size();
+        if (two && !b->part_img[g]) {  // zeroed once: slots no sample writes stay zero
+            BCK(cudaMalloc(&b->part_img[g], 2 * (size_t)c->geo.n_slots * sizeof(float4)));
+            BCK(cudaMemset(b->part_img[g], 0, 2 * (size_t)c->geo.n_slots * sizeof(float4)));
+        }
+        for (size_t k = 0; k < parts.size(); ++k) {
+            const int lanes = parts[k].lanes, eg = parts[k].ept;
+            Plan *pl = nullptr;
+            sc_status st = sc_internal::make_plan_layout(c, two ? parts[k].n : c->n_e, lanes, eg, &pl);
+            if (st != SC_OK) return berr(b, st, c->err);
+            gs.emplace_back();
+            scd::GrainSweep &d = gs.back();
+            const int gi = (int)gs.size() - 1;
+            d.lines = c->d_lines;
+            d.groups = pl->d_groups;
+            d.image_in = c->d_img_in;
+            // a blocked member writes one image per energy block (added after the sweep)
+            d.image_out = pl->n_blocks > 1 ? pl->d_img_blocks : c->d_img_out;
+            d.n_slots = c->geo.n_slots;
+            d.n_lines = (int32_t)c->geo.lines.size();
+            d.n_groups = pl->n_groups;
+            d.exits[0] = c->d_exit[0];
+            d.exits[1] = c->d_exit[1];
+            d.energies = nullptr;
+            d.mats_eps = c->d_eps;
+            d.mats_w = c->d_ewt;
+            d.t = c->geo.prm.t;
+            d.h = c->geo.prm.h;
+            d.broadening = 0.0;
+            d.n_e = c->n_e;
+            d.lanes = pl->lanes;
+            d.lines_per_warp = pl->lines_per_warp;
+            d.ne_pad = pl->lanes * pl->ept;
+            d.max_ns = std::max(c->geo.max_ns, 1);
+            d.ept = pl->ept;
+            d.n_blocks = pl->n_blocks;
+            d.e_first = parts[k].first;
+            d.e_count = two ? parts[k].n : 0;
+            if (two)  // each part sums into its own image; the two are added after the sweep
+                d.image_out = (char *)b->part_img[g] + k * (size_t)c->geo.n_slots * sizeof(float4);
+            b->member_blocks[g] = pl->n_blocks;
+            b->member_plan[g] = pl;
+            stride = std::max(stride, pl->stride);
+            int64_t steps = 0;
+            for (const auto &li : c->geo.lines) steps += 2 * (int64_t)(li.ns + 1);
+            lane_steps += steps * pl->lanes * pl->ept * pl->n_blocks;
+            // cost of a group ~ steps x energies handled per lane; one item per energy block
+            for (int q = 0; q < pl->n_groups; ++q)
+                for (int kb = 0; kb < pl->n_blocks; ++kb)
+                    items.push_back({pl->group_cost[q] * pl->ept, gi, q * pl->n_blocks + kb});
+        }
     }
     // classes by energies per lane (largest first), longest items first within each
     std::stable_sort(items.begin(), items.end(), [&](const It &x, const It &y) {
@@ -225,6 +285,7 @@ sc_status build(sc_batch *b, int ept) {
     BCK(cudaMalloc(&b->d_items, flat.size() * sizeof(int2)));
     BCK(cudaMemcpy(b->d_items, flat.data(), flat.size() * sizeof(int2), cudaMemcpyHostToDevice));
     b->n_items = (int32_t)flat.size();
+    b->n_gs = (int32_t)gs.size();
     b->stride = stride;
     b->classes = classes;
     const size_t need = (size_t)max_blocks * 4 * (size_t)stride * 2 * (b->fp64 ? 8 : 4);
@@ -340,6 +401,7 @@ sc_status sc_batch_destroy(sc_batch *b) {
     cudaFree(b->d_pt);
     cudaFree(b->d_stage_in);
     cudaFree(b->d_stage_out);
+    for (void *q : b->part_img) cudaFree(q);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->cev)
@@ -407,10 +469,10 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     b->device = b->members[0]->device;
     b->sm_count = b->members[0]->sm_count;
     sc_status st = SC_OK;
-    cudaError_t e = cudaMalloc(&b->d_counter, 8 * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&b->d_counter, sc_batch::kMaxClasses * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
-    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->cev[k]);
+    for (int k = 0; k <= sc_batch::kMaxClasses && e == cudaSuccess; ++k) e = cudaEventCreate(&b->cev[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     for (int k = 0; k < sc_batch::kAux && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
@@ -461,7 +523,9 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         fs = join(b, st);
         if (fs != SC_OK) return fs;
     }
-    BCK(cudaMemsetAsync(b->d_counter, 0, 8 * sizeof(int32_t), st));
+    if (b->classes.size() > (size_t)sc_batch::kMaxClasses)
+        return berr(b, SC_ESTATE, "more energies-per-lane classes than work counters");
+    BCK(cudaMemsetAsync(b->d_counter, 0, sc_batch::kMaxClasses * sizeof(int32_t), st));
     // while a graph is being captured the timing events become external event
     // nodes, so that every replay records them
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -470,7 +534,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     BCK(cudaEventRecordWithFlags(b->ev[0], st, ev_flags));
     for (size_t k = 0; k < b->classes.size(); ++k) {
         const sc_batch::Class &c = b->classes[k];
-        if (k < 8) BCK(cudaEventRecordWithFlags(b->cev[k], st, ev_flags));
+        BCK(cudaEventRecordWithFlags(b->cev[k], st, ev_flags));
         scd::SweepLaunch a{};
         a.grains = b->d_grains;
         a.items = b->d_items + c.first;
@@ -479,7 +543,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.scratch = b->d_scratch;
         a.scratch_stride = b->stride;
         a.scratch_elems = (int64_t)(b->scratch_bytes / (2 * (b->fp64 ? 8 : 4)));
-        a.n_grains = (int32_t)b->members.size();
+        a.n_grains = b->n_gs;
         a.energies_per_lane = c.ept;
         a.first_sweep = b->have_boundary ? 0 : 1;
         a.parity = b->parity;
@@ -491,13 +555,18 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.blocked = b->blocked;
         BCK(scd::launch_sweep(b->fp64, a, st));
     }
-    BCK(cudaEventRecordWithFlags(b->cev[std::min<size_t>(b->classes.size(), 8)], st, ev_flags));
-    BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
-    b->timed = true;
-    for (size_t g = 0; g < b->members.size(); ++g)
+    BCK(cudaEventRecordWithFlags(b->cev[b->classes.size()], st, ev_flags));
+    for (size_t g = 0; g < b->members.size(); ++g) {
         if (b->member_blocks[g] > 1)  // the energy blocks' images, added in block order
             BCK(scd::launch_block_sum(b->fp64, b->member_plan[g]->d_img_blocks, b->member_blocks[g],
                                       b->members[g]->geo.n_slots, b->members[g]->d_img_out, st));
+        if (b->member_parts[g] > 1)  // the two energy parts' images, first part first
+            BCK(scd::launch_block_sum(false, b->part_img[g], 2, b->members[g]->geo.n_slots,
+                                      b->members[g]->d_img_out, st));
+    }
+    // the sweep's time: the class launches and the sums that complete the images
+    BCK(cudaEventRecordWithFlags(b->ev[1], st, ev_flags));
+    b->timed = true;
     if (!b->fp64) {
         // the Fermi-surface averages of every member: one launch per component count
         for (int k = 0; k < 4; ++k)
@@ -646,12 +715,33 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
         }
     }
     b->min_lanes = best_min;
+    // FP32: members in two energy parts (each in its own layout) or in one
+    if (!b->fp64) {
+        float t[2] = {0.f, 0.f};  // with, without
+        for (int v = 0; v < 2; ++v) {
+            b->split = v == 0;
+            sc_status s = build(b, best);
+            if (s != SC_OK) return s;
+            for (int rep = 0; rep < 3; ++rep) {  // the second and third sweeps are timed
+                s = sc_batch_sweep(b, stream);
+                if (s != SC_OK) return s;
+                BCK(cudaEventSynchronize(b->ev[1]));
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+                if (rep > 0) t[v] += ms;
+            }
+        }
+        const float ms_on = 0.5f * t[0], ms_off = 0.5f * t[1];
+        b->split = ms_on <= ms_off;
+        b->split_ms[0] = ms_on;
+        b->split_ms[1] = ms_off;
+    }
     b->bps_choice.clear();
     sc_status s = build(b, best);
     if (s != SC_OK) return s;
     // per class: the persistent grid sized for occupancy, occupancy - 1, occupancy - 2
     // resident blocks per SM; each class keeps its fastest
-    const size_t nc = std::min<size_t>(b->classes.size(), 8);
+    const size_t nc = b->classes.size();
     std::vector<int> pick(nc, 0);
     std::vector<float> pick_ms(nc, 1e30f);
     for (int d = 0; d <= 2; ++d) {
@@ -750,6 +840,7 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     // the launches sc_batch_sweep and the outputs of iteration() make
     int32_t nl = (int32_t)b->classes.size() + 2;  // sweep classes; outputs and their final sums
     for (int nbk : b->member_blocks) nl += nbk > 1 ? 1 : 0;  // energy-block sums
+    for (int np : b->member_parts) nl += np > 1 ? 1 : 0;     // sums of two energy parts
     if (!b->fp64) {
         nl += (b->tot_pad > 0) + (b->tot_slots > 0);
         for (int k = 0; k < 4; ++k) nl += b->tot_back[k] > 0;
@@ -757,12 +848,17 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
         nl += 2 * (int32_t)b->members.size();  // rotate and rotate-back per member
     }
     info->launches_per_iteration = nl;
-    for (size_t k = 0; k < b->classes.size() && k < 8; ++k) {
+    info->split_ms_on = b->split_ms[0];
+    info->split_ms_off = b->split_ms[1];
+    info->split_members = 0;
+    for (int np : b->member_parts) info->split_members += np > 1 ? 1 : 0;
+    static_assert(sc_batch::kMaxClasses <= 16, "sc_batch_info holds 16 classes");
+    for (size_t k = 0; k < b->classes.size(); ++k) {
         info->class_ept[k] = b->classes[k].ept;
         info->class_blocks_per_sm[k] = b->classes[k].bps;
     }
     if (b->timed) {
-        const size_t nc = std::min<size_t>(b->classes.size(), 8);
+        const size_t nc = b->classes.size();
         for (size_t k = 0; k < nc; ++k) {
             float cms = 0.f;
             if (cudaEventSynchronize(b->cev[nc]) == cudaSuccess &&

@@ -158,6 +158,8 @@ struct GrainSweep {
                                // image_out + k n_slots
     int32_t n_lines;           // lines of the grain (exit rows: 2 n_lines)
     int32_t n_groups;          // line groups (groups holds n_groups x lines_per_warp entries)
+    int32_t e_first, e_count;  // a part of the grain's energies, [e_first, e_first + e_count),
+                               // in its own layout and image (e_count 0: all n_e energies)
 };
 
 // One persistent launch over the work items (grain, line group) of any number

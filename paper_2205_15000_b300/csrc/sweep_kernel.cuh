@@ -56,7 +56,9 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
         // energy block of this item (several when the energies exceed one lane layout)
         const int nb = BLK ? gs.n_blocks : 1;
         const int grp = BLK ? it.y / nb : it.y;
-        const int e0 = BLK ? (it.y - grp * nb) * ne_pad : 0;
+        // this item's energies: the grain's part [e_first, e_end), its block of ne_pad
+        const int e_end = gs.e_count > 0 ? gs.e_first + gs.e_count : n_e;
+        const int e0 = gs.e_first + (BLK ? (it.y - grp * nb) * ne_pad : 0);
 
         // the lane's energies: z = zr0 + i zi (+ a along the line)
         T zr0[EPT], zi[EPT];
@@ -66,8 +68,8 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
 #pragma unroll
         for (int e = 0; e < EPT; ++e) {
             const int n = e0 + r + Lw * e;
-            ev[e] = n < n_e;
-            const int nn = ev[e] ? n : n_e - 1;
+            ev[e] = n < e_end;
+            const int nn = ev[e] ? n : e_end - 1;
             nid[e] = nn;
             if (RET) {
                 zr0[e] = (T)gs.energies[nn];

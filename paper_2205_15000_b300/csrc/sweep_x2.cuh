@@ -297,7 +297,9 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
     const int ne_pad = gs.ne_pad;
     const int nb = BLK ? gs.n_blocks : 1;
     const int grp = BLK ? it.y / nb : it.y;
-    const int e0 = BLK ? (it.y - grp * nb) * ne_pad : 0;
+    // this item's energies: the grain's part [e_first, e_end), its block of ne_pad
+    const int e_end = gs.e_count > 0 ? gs.e_first + gs.e_count : n_e;
+    const int e0 = gs.e_first + (BLK ? (it.y - grp * nb) * ne_pad : 0);
     const float broad = RET ? (float)gs.broadening : 0.f;
 
     // the lane's energies: Matsubara t (n + 1/2) or Ozaki's poles with the weights
@@ -310,8 +312,8 @@ __device__ __forceinline__ void sweep_item_x2(const SweepLaunch &a, const int2 i
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
         const int n = e0 + r + Lw * e;
-        ev[e] = n < n_e;
-        const int nn = ev[e] ? n : n_e - 1;
+        ev[e] = n < e_end;
+        const int nn = ev[e] ? n : e_end - 1;
         nid[e] = nn;
         if constexpr (RET) {
             zq[e] = (float)gs.energies[nn];

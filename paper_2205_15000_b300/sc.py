@@ -78,9 +78,10 @@ class sc_batch_info(ctypes.Structure):
         ("energies_per_lane", ctypes.c_int32), ("steps_per_sweep", ctypes.c_int64),
         ("scratch_bytes", ctypes.c_int64), ("ms_sweep", ctypes.c_double),
         ("lane_steps_per_sweep", ctypes.c_int64), ("sweep_launches", ctypes.c_int32),
-        ("class_ept", ctypes.c_int32 * 8), ("class_blocks_per_sm", ctypes.c_int32 * 8),
-        ("class_ms", ctypes.c_double * 8), ("min_lanes_per_line", ctypes.c_int32),
-        ("launches_per_iteration", ctypes.c_int32),
+        ("class_ept", ctypes.c_int32 * 16), ("class_blocks_per_sm", ctypes.c_int32 * 16),
+        ("class_ms", ctypes.c_double * 16), ("min_lanes_per_line", ctypes.c_int32),
+        ("launches_per_iteration", ctypes.c_int32), ("split_members", ctypes.c_int32),
+        ("split_ms_on", ctypes.c_double), ("split_ms_off", ctypes.c_double),
     ]
 
 

@@ -247,3 +247,72 @@ def test_batch_reset_boundary_restarts_from_fresh_values():
         np.testing.assert_array_equal(x, y)
     assert any(np.max(np.abs(x - y)) > 0 for x, y in zip(first, carried))
     b.close()
+
+
+def test_batch_member_in_two_energy_parts():
+    """A member whose 132 energies would pad 16 x 9 lane slots runs as two parts in
+    their own layouts (2 x 10 and 16 x 7) whose images are added after the sweep:
+    three batch iterations equal the single FP32 context (16 x 9) to FP32 rounding
+    and the FP64 oracle within the production tolerances; without parts the batch
+    takes the single layout."""
+    from paper_2205_15000_b300 import sc
+    p = W.disc(3.0, 24, pairing=1, t=0.06, n_angles=16, n_energies=132, flux_quanta=0.4)
+    d = W.vortex_delta(p, 0.24, [(0.5, -0.3)], [-1], seed=35, rel_noise=0.05)
+    q = W.square(4.0, 20, pairing=0, t=0.5, n_angles=8, n_energies=12)
+    dq = W.noisy_delta(q, 0.2, 0.1, seed=36)
+    b = sc.Batch([p, q], precision="fp32", energies_per_lane=10)
+    info = b.info()
+    assert info.split_members == 1 and info.launches_per_iteration == info.sweep_launches + 6
+    for m, x in zip(b.members, (d, dq)):
+        m.set_fields(x)
+    ref = sc.Context(p, precision="fp32")
+    ref.set_fields(d)
+    g = oracle.OracleGeom(p)
+    mk = g.mask().astype(bool)
+    ex = None
+    for it in range(3):
+        b.run(1, True)
+        ref.sweep()
+        o = g.full_sweep(d, None, ex)
+        ex = o["exit"]
+        rb, rr = _outputs(b.members[0]), _outputs(ref)
+        for k in ("delta_new", "j", "F"):
+            scale = np.max(np.abs(rr[k]))
+            assert np.max(np.abs(rb[k] - rr[k])) <= 2e-6 * scale, (it, k)
+        assert np.max(np.abs(rb["delta_new"][mk] - o["delta_new"][mk])) <= 1e-5 * np.max(np.abs(o["delta_new"][mk]))
+        assert np.max(np.abs(rb["j"][mk] - o["j"][mk])) <= 1e-4 * np.max(np.abs(o["j"][mk]))
+        assert np.max(np.abs(rb["F"][mk] - o["F"][mk])) <= 1e-4 * np.max(np.abs(o["F"][mk]))
+    b.close()
+
+
+def test_batch_with_ten_energies_per_lane_classes():
+    """Ten members whose energy counts (2, 4, ..., 20 on 2 lanes per line) give ten
+    energies-per-lane classes, each its own launch with its own work counter: three
+    graph-replayed iterations equal the members' single FP32 contexts."""
+    from paper_2205_15000_b300 import sc
+    prms, ds = [], []
+    for k in range(10):
+        p = W.disc(2.5 + 0.1 * k, 16 + k, margin=0.2, pairing=k % 2, t=0.3, n_angles=8,
+                   n_energies=2 * (k + 1), flux_quanta=0.2)
+        prms.append(p)
+        ds.append(W.noisy_delta(p, 0.2, 0.1, seed=60 + k))
+    b = sc.Batch(prms, precision="fp32", energies_per_lane=10)
+    info = b.info()
+    assert info.sweep_launches == 10
+    assert sorted(info.class_ept[k] for k in range(10)) == list(range(1, 11))
+    refs = []
+    for p, d, m in zip(prms, ds, b.members):
+        m.set_fields(d)
+        r = sc.Context(p, precision="fp32")
+        r.set_fields(d)
+        refs.append(r)
+    b.run(3, True)
+    for r in refs:
+        for _ in range(3):
+            r.sweep()
+    for m, r in zip(b.members, refs):
+        om, orf = _outputs(m), _outputs(r)
+        for k in ("delta_new", "j", "F"):
+            assert np.max(np.abs(om[k] - orf[k])) <= 2e-6 * np.max(np.abs(orf[k])), k
+        r.close()
+    b.close()
