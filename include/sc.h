@@ -376,12 +376,13 @@ typedef struct {
    Each member takes the lanes per line (2, 4, 8, 16, 32; at least the batch's
    fewest, 2 unless sc_batch_autotune raises it) and energies per lane (<= the
    bound; 9 and 10 only without energy blocks) with the fewest padded lane
-   slots, then the most energies per lane.  An FP32 member whose layout pads
-   its energies may instead run them as two parts, [0, n1) and [n1, n_e), each
-   in its own layout and image (added in order after the sweep), where the
-   padded lane slots weighted by the measured cost of a lane-step at each
-   energies-per-lane count fall by at least 2 % (132 energies: 2 x 10 and
-   16 x 7 instead of 16 x 9).  Members with
+   slots, then the most energies per lane.  After sc_batch_autotune has found
+   it faster, an FP32 member whose layout pads its energies runs them as two
+   parts, [0, n1) and [n1, n_e), each in its own layout and image (added in
+   order after the sweep), where the padded lane slots weighted by the measured
+   cost of a lane-step at each energies-per-lane count fall by at least 5 % and
+   both parts keep 5 or more energies per lane (132 energies: 2 x 10 and 16 x 7
+   instead of 16 x 9).  Members with
    equal energies per lane share one persistent launch; a batch sweep runs
    these launches back to back.  The members are owned by the batch. */
 sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_per_lane,
@@ -399,6 +400,11 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream);
    one graph per iteration parity -- on an internal stream ordered after and
    before `stream`.  The first sweep from fresh boundary values runs uncaptured. */
 sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void *stream);
+/* FP32 batches: on = 1 lets padded members run their energies as two parts
+   (the rule above), 0 keeps every member in one layout; the work list is laid
+   out again (captured graphs are dropped).  SC_EINVAL for an FP64 batch with
+   on = 1. */
+sc_status sc_batch_set_energy_parts(sc_batch *b, int32_t on);
 /* Forget every member's boundary coherence functions: the next batch sweep
    starts every trajectory from the local homogeneous solution, as the first
    sweep after sc_batch_create does.  The layout (energies per lane, lanes per
@@ -407,7 +413,8 @@ sc_status sc_batch_reset_boundary(sc_batch *b);
 /* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
    keep the fastest; then the fewest lanes per line a member may take (2, 4, 8, 16:
    at most 16, 8, 4, 2 lines per warp, which a warp steps as long as its longest);
-   then (FP32) the members in two energy parts where that pays or all in one;
+   then (FP32) the members in two energy parts where that is more than 1 %
+   faster, else all in one;
    then, for that layout, size every class launch's persistent
    grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
    per SM and keep, per class, the fastest (each class launch timed by its own

@@ -22,7 +22,7 @@ struct sc_batch {
     std::vector<Plan *> member_plan; // each member's layout (owned by the member context)
     std::vector<int> member_parts;   // 2: the member's energies in two parts of their own layouts
     std::vector<void *> part_img;    // per member: the two parts' images (2 n_slots float4), lazily
-    bool split = true;               // FP32: members may take two energy parts
+    bool split = false;              // FP32: members may take two energy parts (autotuned)
     float split_ms[2] = {0.f, 0.f};  // the autotune's sweep times with and without parts
     int blocked = 0;                 // some member splits its energies into blocks
     int device = 0;
@@ -162,9 +162,9 @@ struct Part {
 };
 
 // The member's energies as one layout, or (FP32) as two parts [0, n1) and
-// [n1, n_e), each in its own layout, where that costs at least 2 % less than
-// the padded single layout (e.g. 132 energies: 2 x 10 and 16 x 7 lanes x
-// energies instead of 16 x 9).
+// [n1, n_e), each in its own layout with at least 5 energies per lane, where
+// that costs at least 5 % less than the padded single layout (e.g. 132
+// energies: 2 x 10 and 16 x 7 lanes x energies instead of 16 x 9).
 std::vector<Part> member_parts(int n_e, int ept_max, int min_lanes, bool split) {
     int lanes = 32, ept = ept_max;
     member_layout(n_e, ept_max, min_lanes, lanes, ept);
@@ -604,6 +604,15 @@ static sc_status iteration(sc_batch *b, int with_outputs, cudaStream_t st) {
     return SC_OK;
 }
 
+sc_status sc_batch_set_energy_parts(sc_batch *b, int32_t on) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    if (on && b->fp64) return berr(b, SC_EINVAL, "energy parts are an FP32 layout");
+    BCK(cudaSetDevice(b->device));
+    b->split = on != 0;
+    return build(b, b->ept);
+}
+
 sc_status sc_batch_reset_boundary(sc_batch *b) {
     if (!b) return SC_EINVAL;
     if (b->failed) return SC_ESTATE;
@@ -732,7 +741,7 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
             }
         }
         const float ms_on = 0.5f * t[0], ms_off = 0.5f * t[1];
-        b->split = ms_on <= ms_off;
+        b->split = ms_on < 0.99f * ms_off;  // parts only where they are clearly faster
         b->split_ms[0] = ms_on;
         b->split_ms[1] = ms_off;
     }

@@ -122,6 +122,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_reset_boundary",
+            "sc_batch_set_energy_parts",
             "sc_batch_autotune",
             "sc_batch_get_info", "sc_batch_set_fields", "sc_batch_get_outputs", "sc_last_error", "sc_version"]
 
@@ -177,6 +178,7 @@ def _load():
         "sc_batch_sweep": [vp, vp],
         "sc_batch_run": [vp, i32, i32, vp],
         "sc_batch_reset_boundary": [vp],
+        "sc_batch_set_energy_parts": [vp, i32],
         "sc_batch_autotune": [vp, P(i32), vp],
         "sc_batch_get_info": [vp, P(sc_batch_info)],
         "sc_batch_set_fields": [vp, vp, ctypes.c_int, vp],
@@ -490,6 +492,11 @@ def sc_batch_sweep(b, stream=None):
 
 def sc_batch_run(b, n_sweeps, with_outputs=True, stream=None):
     _check(lib.sc_batch_run(b, int(n_sweeps), int(bool(with_outputs)), _stream(stream)))
+
+
+def sc_batch_set_energy_parts(b, on):
+    """FP32: let padded members run their energies as two parts (layout rebuilt)."""
+    _check(lib.sc_batch_set_energy_parts(b, int(bool(on))))
 
 
 def sc_batch_reset_boundary(b):

@@ -261,6 +261,8 @@ def test_batch_member_in_two_energy_parts():
     q = W.square(4.0, 20, pairing=0, t=0.5, n_angles=8, n_energies=12)
     dq = W.noisy_delta(q, 0.2, 0.1, seed=36)
     b = sc.Batch([p, q], precision="fp32", energies_per_lane=10)
+    assert b.info().split_members == 0  # one layout per member unless asked for
+    sc.sc_batch_set_energy_parts(b.h, True)
     info = b.info()
     assert info.split_members == 1 and info.launches_per_iteration == info.sweep_launches + 6
     for m, x in zip(b.members, (d, dq)):
@@ -282,7 +284,13 @@ def test_batch_member_in_two_energy_parts():
         assert np.max(np.abs(rb["delta_new"][mk] - o["delta_new"][mk])) <= 1e-5 * np.max(np.abs(o["delta_new"][mk]))
         assert np.max(np.abs(rb["j"][mk] - o["j"][mk])) <= 1e-4 * np.max(np.abs(o["j"][mk]))
         assert np.max(np.abs(rb["F"][mk] - o["F"][mk])) <= 1e-4 * np.max(np.abs(o["F"][mk]))
+    sc.sc_batch_set_energy_parts(b.h, False)
+    assert b.info().split_members == 0
     b.close()
+    b64 = sc.Batch([q], precision="fp64")
+    with pytest.raises(sc.ScError):
+        sc.sc_batch_set_energy_parts(b64.h, True)
+    b64.close()
 
 
 def test_batch_with_ten_energies_per_lane_classes():
