@@ -61,6 +61,20 @@ def run():
         for key in ("delta_new", "j", "F"):
             out[f"batch_{k}_{key}"] = o[key].cpu().numpy()
     b.close()
+    # a member in two energy parts (132 energies: 2 x 10 and 16 x 7 lanes x energies)
+    p132 = W.disc(3.0, 24, pairing=1, t=0.06, n_angles=16, n_energies=132, flux_quanta=0.4)
+    d132 = W.vortex_delta(p132, 0.24, [(0.5, -0.3)], [-1], seed=35, rel_noise=0.05)
+    b = sc.Batch([p132, gr["diamond"][0]], precision="fp32", energies_per_lane=10)
+    sc.sc_batch_set_energy_parts(b.h, True)
+    assert b.info().split_members >= 1
+    for m, d in zip(b.members, (d132, gr["diamond"][1])):
+        m.set_fields(d)
+    b.run(3, True)
+    for m, k in zip(b.members, ("disc_132", "diamond")):
+        o = m.outputs()
+        for key in ("delta_new", "j", "F"):
+            out[f"parts_{k}_{key}"] = o[key].cpu().numpy()
+    b.close()
     torch.cuda.synchronize()
     v, checked = sc.sc_debug_bounds()
     return out, v, checked

@@ -3,7 +3,8 @@ every line, line-group, slot, sample, exit-tap, slab-row, padded-grid and
 rotate-back index of the kernels is compared with the size of its table, a
 failed check skips the access and counts) stands in for a device memory
 checker.  On the parity grains -- three convex and composite grains in both
-precisions, an energy-blocked grain, the adjoint, the LDOS and a batch -- it
+precisions, an energy-blocked grain, the adjoint, the LDOS, a batch and a batch
+with a member in two energy parts -- it
 must count no violation and give the regular build's results bit for bit
 (the adjoint, whose cotangents are added with atomics in no fixed order, to
 rounding)."""
