@@ -56,7 +56,7 @@ __global__ void adjoint_outputs_kernel(GridDev grid, const uint8_t *__restrict__
     if (mask[idx]) {
         if (gdn) {
             for (int c = 0; c < grid.n_comp; ++c) {
-                const double cd = t / (2.0 * 3.141592653589793) / normD.D[c];
+                const double cd = normD.kD[c];
                 ac[2 * c] = cd * gdn[2 * (c * npts + idx)];
                 ac[2 * c + 1] = cd * gdn[2 * (c * npts + idx) + 1];
             }

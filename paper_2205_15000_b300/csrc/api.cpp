@@ -517,7 +517,10 @@ sc_status sc_create(const sc_params *p, sc_ctx **out) {
     gd.oy = G.oy;
     gd.bfield = M_PI * p->flux_quanta / G.area;  // B = pi alpha / area in units of B0
     gd.n_comp = G.n_comp;
-    for (int c = 0; c < 4; ++c) ctx->norms.D[c] = ctx->normD - std::log(G.tc_ratio[c]);
+    for (int c = 0; c < 4; ++c) {
+        ctx->norms.D[c] = ctx->normD - std::log(G.tc_ratio[c]);
+        ctx->norms.kD[c] = p->t / (2.0 * 3.141592653589793) / ctx->norms.D[c];
+    }
     gd.gx = p->gauge_cx;
     gd.gy = p->gauge_cy;
     gd.gauge = p->gauge;

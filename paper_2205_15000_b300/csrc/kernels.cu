@@ -391,7 +391,7 @@ __device__ __forceinline__ void outputs_block(const GridDev &grid, const uint8_t
             bool fin = true;
             for (int c = 0; c < grid.n_comp; ++c) {
                 const int64_t pr = c == 0 ? 0 : 3 + 2 * c, pim = c == 0 ? 1 : 4 + 2 * c;
-                const double k = t / (2.0 * 3.141592653589793) / normD.D[c];
+                const double k = normD.kD[c];
                 const double dr = k * acc[pr * npts + idx], di = k * acc[pim * npts + idx];
                 const int64_t o = 2 * (c * npts + idx);
                 dn[o] = dr;
@@ -423,7 +423,7 @@ __device__ __forceinline__ void outputs_block(const GridDev &grid, const uint8_t
     const double s0 = block_sum(num, sh);
     const double s1 = block_sum(den, sh);
     const double s2 = block_sum(fs, sh);
-    const double s3 = block_sum(bad, sh);
+    const double s3 = (double)__syncthreads_count(bad != 0.0);  // points with a non-finite value
     if (threadIdx.x == 0) {  // per-block partials, summed in block order by final_sums_kernel
         double *pb = partials + 4 * blk;
         pb[0] = s0;

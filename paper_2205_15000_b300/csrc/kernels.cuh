@@ -229,6 +229,7 @@ int reduce_blocks(int64_t npts);
 // normD_c: the gap-equation normalisation of each component, D - ln(T_c^c/T_c).
 struct CompNorm {
     double D[4];
+    double kD[4];  // t / (2 pi D[c]): Delta_c = kD[c] <eta_c Sf> (Eq. gapeq_fixpoint)
 };
 
 // One batch member's tables and buffers for the per-member kernels of a batch
