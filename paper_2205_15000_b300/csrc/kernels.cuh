@@ -1,6 +1,7 @@
 // Device data layouts and kernel launchers of the Riccati sweep.
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "bounds.cuh"
@@ -121,16 +122,23 @@ struct LineF32 {
 // lattice lines and nine samples per line at any angle.
 __host__ __device__ inline int64_t back_tiles(int64_t nx, int64_t ny) { return ((nx + 7) / 8) * ((ny + 3) / 4); }
 
-struct PairF32 {
-    int64_t dx, dy;                 // e_par in grid units per sample
+// The fields the rotate-back reads for every (grid point, pair) come first, in
+// 16-byte groups that it loads as vectors (five loads per pair instead of one per
+// field).
+struct alignas(16) PairF32 {
     int64_t ui, uj, u0, vi, vj, v0; // u = i ui + j uj + u0, v = i vi + j vj + v0
-    float eta;                      // basis function (component 0)
+    int32_t l_lo, l_hi, lat0, pad;  // lattice lines l_lo..l_hi; their BackLine records from lat0
     float w_eta, w_ex, w_ey, w_sum; // (w_p + w_{p+P}) times eta, e_x, e_y, 1
+    float w_eta_c[4];               // per order-parameter component: (w_p + w_{p+P}) eta_c
+    int64_t dx, dy;                 // e_par in grid units per sample
+    float eta;                      // basis function (component 0)
     float wa, wb;                   // w_p, w_{p+P}
     float ex_f, ey_f;               // e_par in FP32
-    int32_t l_lo, l_hi, lat0, pad;  // lattice lines l_lo..l_hi; their BackLine records from lat0
-    float eta_c[4], w_eta_c[4];     // per order-parameter component: eta, (w_p + w_{p+P}) eta
+    float eta_c[4];                 // per order-parameter component: eta_c
 };
+static_assert(offsetof(PairF32, l_lo) == 48 && offsetof(PairF32, w_eta) == 64 && offsetof(PairF32, w_eta_c) == 80 &&
+                  alignof(PairF32) == 16,
+              "the rotate-back loads PairF32 as 16-byte groups");
 
 // Everything the sweep needs of one grain (one context, or one member of a batch).
 struct GrainSweep {

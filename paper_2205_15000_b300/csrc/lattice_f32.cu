@@ -231,14 +231,18 @@ __device__ __forceinline__ void rotate_back_f32_block(const PairF32 *__restrict_
             float ac[2 * NC] = {};
             const int pe = min(p0 + 16, n_pairs);
             for (int p = p0; p < pe; ++p) {
-                const PairF32 &pp = pairs[p];
+                // the pair's rotate-back fields as five 16-byte loads
+                const longlong2 *pv = (const longlong2 *)(pairs + p);
+                const longlong2 q0 = pv[0], q1 = pv[1], q2 = pv[2];  // (ui, uj), (u0, vi), (vj, v0)
+                const int4 lr = *(const int4 *)(pv + 3);             // l_lo, l_hi, lat0
+                const float4 wt = *(const float4 *)(pv + 4);         // w_eta, w_ex, w_ey, w_sum
                 int iu, iv;
                 float wu, wv;
-                split_fixed(i * pp.ui + j * pp.uj + pp.u0, iu, wu);
-                split_fixed(i * pp.vi + j * pp.vj + pp.v0, iv, wv);
-                const int la = min(max(iu, pp.l_lo), pp.l_hi), lb = min(max(iu + 1, pp.l_lo), pp.l_hi);
-                const BackLine La = back_chord_at(bl, grid.n_back, pp.lat0 + (la - pp.l_lo), iv, wv);
-                const BackLine Lb = back_chord_at(bl, grid.n_back, pp.lat0 + (lb - pp.l_lo), iv, wv);
+                split_fixed(i * q0.x + j * q0.y + q1.x, iu, wu);
+                split_fixed(i * q1.y + j * q2.x + q2.y, iv, wv);
+                const int la = min(max(iu, lr.x), lr.y), lb = min(max(iu + 1, lr.x), lr.y);
+                const BackLine La = back_chord_at(bl, grid.n_back, lr.z + (la - lr.x), iv, wv);
+                const BackLine Lb = back_chord_at(bl, grid.n_back, lr.z + (lb - lr.x), iv, wv);
                 const int ma0 = min(max(iv, La.m0), La.m0 + La.ns - 1);
                 const int ma1 = min(max(iv + 1, La.m0), La.m0 + La.ns - 1);
                 const int mb0 = min(max(iv, Lb.m0), Lb.m0 + Lb.ns - 1);
@@ -254,15 +258,19 @@ __device__ __forceinline__ void rotate_back_f32_block(const PairF32 *__restrict_
                 const float x2 = wa0 * sa0.z + wa1 * sa1.z + wb0 * sb0.z + wb1 * sb1.z;
                 const float x3 = wa0 * sa0.w + wa1 * sa1.w + wb0 * sb0.w + wb1 * sb1.w;
                 // S_f, S_F are equal at phi and phi + pi; S_g and v change sign together
-                a0 += pp.w_eta * x0;
-                a1 += pp.w_eta * x1;
-                a2 += pp.w_ex * x2;
-                a3 += pp.w_ey * x2;
-                a4 += pp.w_sum * x3;
+                a0 += wt.x * x0;
+                a1 += wt.x * x1;
+                a2 += wt.y * x2;
+                a3 += wt.z * x2;
+                a4 += wt.w * x3;
+                if constexpr (NC > 1) {
+                    const float4 wc4 = *(const float4 *)(pv + 5);  // w_eta_c
+                    const float wc[4] = {wc4.x, wc4.y, wc4.z, wc4.w};
 #pragma unroll
-                for (int c = 1; c < NC; ++c) {
-                    ac[2 * c] += pp.w_eta_c[c] * x0;
-                    ac[2 * c + 1] += pp.w_eta_c[c] * x1;
+                    for (int c = 1; c < NC; ++c) {
+                        ac[2 * c] += wc[c] * x0;
+                        ac[2 * c + 1] += wc[c] * x1;
+                    }
                 }
             }
             A[0] += a0;
