@@ -21,20 +21,24 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def test_checked_build_counts_no_violation_and_matches(tmp_path):
-    import _bounds_run as R
     from paper_2205_15000_b300 import build
     assert os.path.exists(build.LIB_CHECKED), "build the checked library first (build(checked=True))"
-    out = tmp_path / "checked.npz"
-    env = dict(os.environ, SC_LIBRARY="checked")
-    r = subprocess.run([sys.executable, os.path.join(HERE, "_bounds_run.py"), str(out)], env=env,
-                       capture_output=True, text=True, timeout=900)
-    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
-    chk = np.load(out)
-    assert int(chk["checked"]) == 1
-    assert int(chk["violations"]) == 0
-    reg, v, checked = R.run()
-    assert not checked and v == 0
-    assert set(reg) == set(chk.files) - {"violations", "checked"}
+
+    def run(checked_lib):
+        # each library in its own process, whatever the test run itself loaded
+        out = tmp_path / ("checked.npz" if checked_lib else "regular.npz")
+        env = {k: v for k, v in os.environ.items() if k != "SC_LIBRARY"}
+        if checked_lib:
+            env["SC_LIBRARY"] = "checked"
+        r = subprocess.run([sys.executable, os.path.join(HERE, "_bounds_run.py"), str(out)], env=env,
+                           capture_output=True, text=True, timeout=900)
+        assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+        return np.load(out)
+    chk, regf = run(True), run(False)
+    assert int(chk["checked"]) == 1 and int(chk["violations"]) == 0
+    assert int(regf["checked"]) == 0 and int(regf["violations"]) == 0
+    assert set(regf.files) == set(chk.files)
+    reg = {k: regf[k] for k in regf.files if k not in ("violations", "checked")}
     for k, a in reg.items():
         b = chk[k]
         if k.startswith("adj_"):
