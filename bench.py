@@ -213,17 +213,20 @@ def _measured_fma_peak():
         return None
 
 
-def _profiled_traffic(workload, precision):
+def _profiled_traffic(workload, precision, fused=False):
     """DRAM bytes (read + write) of the dominant kernel per sweep from the ncu
-    capture recorded in profiles/sweep_traffic.json for this workload and
-    precision, or None when no capture of the current build is recorded."""
+    capture recorded in profiles/sweep_traffic.json for this workload,
+    precision and batch layout (sweep launches with or without the lattice
+    transfers as work items), or None when no capture of the current build is
+    recorded."""
     try:
         with open(os.path.join(ROOT, "profiles", "sweep_traffic.json")) as f:
             entries = json.load(f)
     except Exception:
         return None
     for tr in entries if isinstance(entries, list) else [entries]:
-        if tr.get("precision") == precision and tr.get("workload") == workload:
+        if tr.get("precision") == precision and tr.get("workload") == workload and \
+                bool(tr.get("fused_transfers", False)) == bool(fused):
             return tr.get("dram_bytes_per_sweep", tr.get("dram_bytes_per_launch"))
     return None
 
@@ -812,7 +815,7 @@ def run_batch(args):
     achieved = pse * ALG_OPS_PER_PSE[args.stepper] / (sweep_ms * 1e-3) / 1e9
     lanes = FP32_LANES_PER_SM if args.precision == "fp32" else FP64_LANES_PER_SM
     peak_gops = SM_COUNT_B300 * lanes * ((clocks or {}).get("sm_max_mhz") or 2032.0) * 1e6 / 1e9
-    traffic = _profiled_traffic(workload, args.precision)
+    traffic = _profiled_traffic(workload, args.precision, last.fused_transfers)
     pm = _measured_fma_peak() if args.precision == "fp32" else None
     line = {
         "metric": METRIC, "value": value, "unit": "trajectory-steps/s", "n_gpus": world,
@@ -826,13 +829,18 @@ def run_batch(args):
                    "sweep_launches": fp32_launches, "sweep_classes": classes,
                    "two_part_members": last.split_members,
                    "autotune_split_ms": {"with_parts": last.split_ms_on, "without": last.split_ms_off},
+                   "fused_transfers": bool(last.fused_transfers), "transfer_items": last.transfer_items,
+                   "autotune_fuse_ms": {"with_transfer_items": last.fuse_ms_on, "without": last.fuse_ms_off},
                    "min_lanes_per_line": last.min_lanes_per_line,
                    "step": "one batch iteration: every member's rotate, the sweep, rotate-back and outputs",
+                   "ms_iteration": last.ms_iteration,
                    "l2": "flushed between timed steps", "parallelism": f"replicas{world}",
                    "cuda_graph": "one graph per iteration parity"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": traffic,
-                     "kernel": f"sweep_kernel ({fp32_launches} launches back to back per sweep)",
+                     "kernel": f"sweep_kernel ({fp32_launches} launches back to back per sweep)"
+                     + (", which also run most members' rotations and rotate-backs as work items"
+                        if last.fused_transfers else ""),
                      "ms_per_sweep": sweep_ms,
                      "ops_per_unit": f"{ALG_OPS_PER_PSE[args.stepper]} FP32 lane-operations per (angle pair, "
                                      "sample, energy): the optimised closed-form formulation, terms that depend "

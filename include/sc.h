@@ -365,8 +365,13 @@ typedef struct {
     int32_t launches_per_iteration; /* kernel launches of one batch iteration with outputs
                                        (sc_batch_run with with_outputs = 1) */
     int32_t split_members;      /* members whose energies run as two parts in their own layouts */
-    double split_ms_on, split_ms_off; /* sc_batch_autotune's sweep times with and without two-part
-                                         members (0 before it runs) */
+    double split_ms_on, split_ms_off; /* sc_batch_autotune's iteration times with and without
+                                         two-part members (0 before it runs) */
+    int32_t fused_transfers;    /* 1: the class launches also run the members' rotations and
+                                   rotate-backs as work items (sc_batch_set_fused_transfers) */
+    int64_t transfer_items;     /* those work items (4 lines, or a tile of 8 x 4 grid points, each) */
+    double fuse_ms_on, fuse_ms_off; /* sc_batch_autotune's iteration times with and without them */
+    double ms_iteration;        /* last batch sweep from its rotation to its rotate-back (CUDA events) */
 } sc_batch_info;
 
 /* Create n member contexts (params[0..n-1], same precision; each validated as
@@ -405,16 +410,31 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
    out again (captured graphs are dropped).  SC_EINVAL for an FP64 batch with
    on = 1. */
 sc_status sc_batch_set_energy_parts(sc_batch *b, int32_t on);
+/* FP32 batches: on = 1 runs the members' lattice transfers (Sec. 3.1) inside the
+   sweep's class launches: each one-part member's rotation as work items (four
+   lines each) of a launch before its own class and its rotate-back (one
+   component; tiles of 8 x 4 grid points) of a launch after it, spread evenly
+   among that launch's sweep items, so that these gathers, bound by the L1 data
+   pipe, share the SMs with the sweep, bound by FP32 arithmetic and its
+   latency.  Transfers go to the eligible launch with the least transfer work
+   relative to its sweep work, largest first, and never more than that launch's
+   sweep work; the rest (and every transfer while some member has energy blocks)
+   run in their own launches before and after the sweep.  Results are bit for
+   bit those of on = 0 (the same arithmetic in the same order).  The work list
+   is laid out again (captured graphs are dropped).  SC_EINVAL for an FP64 batch
+   with on = 1. */
+sc_status sc_batch_set_fused_transfers(sc_batch *b, int32_t on);
 /* Forget every member's boundary coherence functions: the next batch sweep
    starts every trajectory from the local homogeneous solution, as the first
    sweep after sc_batch_create does.  The layout (energies per lane, lanes per
    line, blocks per SM) is kept. */
 sc_status sc_batch_reset_boundary(sc_batch *b);
-/* Time one sweep per candidate bound on energies per lane (2..8; FP32 2..10) and
-   keep the fastest; then the fewest lanes per line a member may take (2, 4, 8, 16:
+/* Time one batch sweep (rotation to rotate-back) per candidate bound on
+   energies per lane (2..8; FP32 2..10) and keep the fastest; then the fewest lanes per line a member may take (2, 4, 8, 16:
    at most 16, 8, 4, 2 lines per warp, which a warp steps as long as its longest);
    then (FP32) the members in two energy parts where that is more than 1 %
-   faster, else all in one;
+   faster, else all in one; then (FP32) the lattice transfers inside the class
+   launches (sc_batch_set_fused_transfers) where that is more than 1 % faster;
    then, for that layout, size every class launch's persistent
    grid for each of its occupancy, occupancy - 1 and occupancy - 2 resident blocks
    per SM and keep, per class, the fastest (each class launch timed by its own

@@ -14,10 +14,10 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libsc.so")
 # the same sources with every table index checked in the kernels (-DSC_DEBUG_BOUNDS)
 LIB_CHECKED = os.path.join(LIBDIR, "libsc_checked.so")
-SOURCES = ["kernels.cu", "sweep_f32.cu", "sweep_f64.cu", "lattice_f32.cu", "adjoint.cu", "adjoint_f32.cu",
+SOURCES = ["kernels.cu", "sweep_f32.cu", "sweep_side_f32.cu", "sweep_f64.cu", "lattice_f32.cu", "adjoint.cu", "adjoint_f32.cu",
            "adjoint_f64.cu", "api.cpp", "batch.cpp", "geometry.cpp", "noalloc.cu", "accel.cu", "accel_api.cpp", "ozaki.cpp", "vecpot.cu"]
 HEADERS = ["bounds.cuh", "kernels.cuh", "sweep_kernel.cuh", "geometry.hpp", "riccati_step.cuh", "context.hpp", "adjoint.cuh",
-           "adjoint_kernel.cuh", "adjoint_x2.cuh", "accel.cuh", "vecpot.cuh", "sweep_x2.cuh"]
+           "adjoint_kernel.cuh", "adjoint_x2.cuh", "accel.cuh", "vecpot.cuh", "sweep_x2.cuh", "lattice_f32.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

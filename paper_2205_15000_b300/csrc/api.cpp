@@ -1541,7 +1541,7 @@ sc_status sc_debug_bounds(uint64_t *violations, int32_t *checked_build, int32_t 
     *checked_build = 0;
 #endif
     cudaError_t (*const units[])(unsigned long long *, bool) = {
-        scd::bounds_sweep_f32, scd::bounds_sweep_f64, scd::bounds_adjoint_f32, scd::bounds_adjoint_f64,
+        scd::bounds_sweep_f32, scd::bounds_sweep_side_f32, scd::bounds_sweep_f64, scd::bounds_adjoint_f32, scd::bounds_adjoint_f64,
         scd::bounds_adjoint_transposes, scd::bounds_lattice_f32, scd::bounds_kernels};
     unsigned long long total = 0;
     cudaError_t e = cudaDeviceSynchronize();

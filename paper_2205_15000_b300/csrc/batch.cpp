@@ -41,6 +41,7 @@ struct sc_batch {
     struct Class {
         int ept, first, n, grid_blocks;
         int occ, bps;  // occupancy (blocks per SM) and the blocks per SM the grid is sized for
+        int64_t side_first, side_n;  // its lattice-transfer items: d_side[side_first, + side_n)
     };
     std::vector<Class> classes;
     void *d_scratch = nullptr;
@@ -63,6 +64,18 @@ struct sc_batch {
     bool have_boundary = false;
     int64_t steps_per_sweep = 0;
     int64_t lane_steps_per_sweep = 0;  // with padded energy slots, for the current layout
+    // FP32: the members' rotations and rotate-backs as work items of the class
+    // launches (sc_batch_set_fused_transfers; chosen by sc_batch_autotune)
+    bool fuse = false;   // wanted
+    bool fused = false;  // the current layout carries transfer items
+    float fuse_ms[2] = {0.f, 0.f};  // the autotune's iteration times with and without
+    int2 *d_side = nullptr;
+    int64_t n_side = 0;
+    // [2][n + 1] prefixes: blocks of 16 lines rotated before the first class launch,
+    // tiles (one-component members) rotated back after the last
+    int64_t *d_solo = nullptr;
+    int64_t tot_solo_rot = 0, tot_solo_back = 0;
+    cudaEvent_t iev[2] = {nullptr, nullptr};  // around a whole batch sweep (rotation to rotate-back)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t cev[kMaxClasses + 1] = {};  // around each class launch of the last sweep
     std::vector<int> bps_choice;  // autotuned blocks per SM of each class (empty: occupancy)
@@ -112,8 +125,13 @@ void free_graphs(sc_batch *b) {
 void free_plan_buffers(sc_batch *b) {
     cudaFree(b->d_grains);
     cudaFree(b->d_items);
+    cudaFree(b->d_side);
+    cudaFree(b->d_solo);
     b->d_grains = nullptr;
     b->d_items = nullptr;
+    b->d_side = nullptr;
+    b->d_solo = nullptr;
+    b->n_side = 0;
 }
 
 // Energy layout of one member with at most `ept_max` energies per lane: the
@@ -186,6 +204,112 @@ std::vector<Part> member_parts(int n_e, int ept_max, int min_lanes, bool split) 
     return res;
 }
 
+// Cost of the lattice transfers in sweep lane-steps (one energy slot of one lane
+// over one segment), from the B300 rates of the transfer kernels and of the
+// FP32 sweep on the 256^2 grain with 128 angles: about 3.4e11 lane-steps, 6.6e10
+// rotated slots and 1.1e11 rotated-back (grid point, pair) terms per second.
+constexpr double kRotLaneSteps = 5.3;   // per image slot
+constexpr double kBackLaneSteps = 3.3;  // per grid point and angle pair
+
+// Where the members' lattice transfers run when the class launches carry them.
+// A one-part member of class k is rotated during one of the launches before k
+// and rotated back during one after k; each transfer goes, largest first, to
+// the eligible launch whose transfer load relative to its own sweep work stays
+// lowest, and runs in the separate launches (solo) when none is eligible or it
+// would exceed that launch's sweep work.  The launch order puts the class with
+// the least rotation work first and, of the others, the one with the least
+// rotate-back work last.  Members in two energy parts, and the rotate-back of
+// members with several order-parameter components, stay solo.
+void plan_transfers(sc_batch *b, const std::vector<scd::GrainSweep> &gs, const std::vector<int> &member_gi,
+                    std::vector<sc_batch::Class> &classes, std::vector<double> &class_cost, std::vector<int2> &side,
+                    std::vector<int64_t> &solo) {
+    const size_t n = b->members.size(), K = classes.size();
+    std::vector<int> kc(n, -1);
+    std::vector<double> rot(n, 0.0), back(n, 0.0), crot(K, 0.0), cback(K, 0.0);
+    for (size_t g = 0; g < n; ++g) {
+        const sc_ctx *c = b->members[g];
+        rot[g] = kRotLaneSteps * (double)c->geo.n_slots;
+        if (c->geo.n_comp == 1) back[g] = kBackLaneSteps * (double)c->geo.nx * c->geo.ny * c->geo.n_pairs;
+        if (member_gi[g] < 0) continue;
+        for (size_t k = 0; k < K; ++k)
+            if (classes[k].ept == gs[member_gi[g]].ept) kc[g] = (int)k;
+        if (kc[g] >= 0) {
+            crot[kc[g]] += rot[g];
+            cback[kc[g]] += back[g];
+        }
+    }
+    // launch order: position -> class
+    size_t f = 0;
+    for (size_t k = 1; k < K; ++k)
+        if (crot[k] < crot[f]) f = k;
+    size_t l = f == 0 ? 1 : 0;
+    for (size_t k = 0; k < K; ++k)
+        if (k != f && cback[k] < cback[l]) l = k;
+    std::vector<size_t> order{f};
+    for (size_t k = 0; k < K; ++k)
+        if (k != f && k != l) order.push_back(k);
+    order.push_back(l);
+    std::vector<int> pos_of(K);
+    std::vector<sc_batch::Class> cl(K);
+    std::vector<double> cc(K);
+    for (size_t q = 0; q < K; ++q) {
+        cl[q] = classes[order[q]];
+        cc[q] = class_cost[order[q]];
+        pos_of[order[q]] = (int)q;
+    }
+    classes = cl;
+    class_cost = cc;
+    for (size_t g = 0; g < n; ++g)
+        if (kc[g] >= 0) kc[g] = pos_of[kc[g]];
+    // transfers (member, kind 0 rotation / 1 rotate-back), largest first
+    struct Job {
+        double cost;
+        int g, kind;
+    };
+    std::vector<Job> jobs;
+    for (size_t g = 0; g < n; ++g) {
+        if (kc[g] < 0) continue;
+        if (kc[g] > 0) jobs.push_back({rot[g], (int)g, 0});
+        if (kc[g] < (int)K - 1 && back[g] > 0.0) jobs.push_back({back[g], (int)g, 1});
+    }
+    std::stable_sort(jobs.begin(), jobs.end(), [](const Job &x, const Job &y) { return x.cost > y.cost; });
+    std::vector<double> load(K, 0.0);
+    std::vector<std::vector<Job>> at(K);
+    std::vector<char> rot_fused(n, 0), back_fused(n, 0);
+    for (const Job &j : jobs) {
+        const int lo = j.kind == 0 ? 0 : kc[j.g] + 1, hi = j.kind == 0 ? kc[j.g] : (int)K;
+        int best = -1;
+        double best_r = 1.0;  // at most the launch's own sweep work
+        for (int q = lo; q < hi; ++q) {
+            const double r = (load[q] + j.cost) / std::max(class_cost[q], 1.0);
+            if (r <= best_r) {
+                best_r = r;
+                best = q;
+            }
+        }
+        if (best < 0) continue;
+        load[best] += j.cost;
+        at[best].push_back(j);
+        (j.kind == 0 ? rot_fused : back_fused)[j.g] = 1;
+    }
+    side.clear();
+    for (size_t q = 0; q < K; ++q) {
+        classes[q].side_first = (int64_t)side.size();
+        for (const Job &j : at[q]) {
+            const sc_ctx *c = b->members[j.g];
+            const int64_t cnt = j.kind == 0 ? ((int64_t)c->geo.lines.size() + 3) / 4 : scd::back_tiles(c->geo.nx, c->geo.ny);
+            for (int64_t i = 0; i < cnt; ++i) side.push_back(make_int2(2 * j.g + j.kind, (int)i));
+        }
+        classes[q].side_n = (int64_t)side.size() - classes[q].side_first;
+    }
+    solo.assign(2 * (n + 1), 0);
+    for (size_t g = 0; g < n; ++g) {
+        const sc_ctx *c = b->members[g];
+        solo[g + 1] = solo[g] + (rot_fused[g] ? 0 : ((int64_t)c->geo.lines.size() + 15) / 16);
+        solo[n + 1 + g + 1] = solo[n + 1 + g] + (back_fused[g] || c->geo.n_comp != 1 ? 0 : scd::back_tiles(c->geo.nx, c->geo.ny));
+    }
+}
+
 // Lay out the work list for at most `ept` energies per lane.
 sc_status build(sc_batch *b, int ept) {
     free_graphs(b);  // captured graphs refer to the buffers rebuilt here
@@ -200,10 +324,12 @@ sc_status build(sc_batch *b, int ept) {
     std::vector<It> items;
     int64_t stride = 0;
     int64_t lane_steps = 0;
+    std::vector<int> member_gi(b->members.size(), -1);  // sweep descriptor of a one-part member
     for (size_t g = 0; g < b->members.size(); ++g) {
         sc_ctx *c = b->members[g];
         const std::vector<Part> parts = member_parts(c->n_e, ept, b->min_lanes, b->split && !b->fp64);
         const bool two = parts.size() > 1;
+        if (!two) member_gi[g] = (int)gs.size();
         b->member_parts[g] = (int)parts.size();
         if (two && !b->part_img[g]) {  // zeroed once: slots no sample writes stay zero
             BCK(cudaMalloc(&b->part_img[g], 2 * (size_t)c->geo.n_slots * sizeof(float4)));
@@ -264,22 +390,47 @@ sc_status build(sc_batch *b, int ept) {
     std::vector<int2> flat(items.size());
     for (size_t i = 0; i < items.size(); ++i) flat[i] = make_int2(items[i].grain, items[i].group);
     std::vector<sc_batch::Class> classes;
+    std::vector<double> class_cost;  // lane-steps of each class's items
     for (size_t i = 0; i < items.size(); ++i) {
         const int e = gs[items[i].grain].ept;
-        if (classes.empty() || classes.back().ept != e) classes.push_back({e, (int)i, 0, 0});
+        if (classes.empty() || classes.back().ept != e) {
+            classes.push_back({e, (int)i, 0, 0, 0, 0, 0, 0});
+            class_cost.push_back(0.0);
+        }
         ++classes.back().n;
+        class_cost.back() += 64.0 * items[i].cost;  // both directions, 32 lanes
     }
+    bool any_blocks = false;
+    for (int nbk : b->member_blocks) any_blocks = any_blocks || nbk > 1;
+    std::vector<int2> side;
+    std::vector<int64_t> solo;
+    if (b->fuse && !b->fp64 && !any_blocks && classes.size() >= 2)
+        plan_transfers(b, gs, member_gi, classes, class_cost, side, solo);
+    const bool fused = !side.empty();
     int max_blocks = 1;
     for (size_t k = 0; k < classes.size(); ++k) {
         auto &c = classes[k];
-        int occ = scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper, b->weighted);
+        if (!fused) c.side_first = c.side_n = 0;
+        int occ = c.side_n > 0 ? scd::sweep_side_occupancy_f32(c.ept, 128, b->stepper, b->weighted)
+                               : scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper, b->weighted);
         if (occ < 1) occ = 1;
         c.occ = occ;
         c.bps = k < b->bps_choice.size() && b->bps_choice[k] > 0 ? std::min(b->bps_choice[k], occ) : occ;
-        c.grid_blocks = std::max(1, std::min(b->sm_count * c.bps, (c.n + 3) / 4));
+        c.grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->sm_count * c.bps, (c.n + c.side_n + 3) / 4));
         max_blocks = std::max(max_blocks, c.grid_blocks);
     }
     free_plan_buffers(b);
+    b->fused = fused;
+    if (fused) {
+        BCK(cudaMalloc(&b->d_side, side.size() * sizeof(int2)));
+        BCK(cudaMemcpy(b->d_side, side.data(), side.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        BCK(cudaMalloc(&b->d_solo, solo.size() * sizeof(int64_t)));
+        BCK(cudaMemcpy(b->d_solo, solo.data(), solo.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        b->n_side = (int64_t)side.size();
+        const size_t n = b->members.size();
+        b->tot_solo_rot = solo[n];
+        b->tot_solo_back = solo[2 * n + 1];
+    }
     BCK(cudaMalloc(&b->d_grains, gs.size() * sizeof(scd::GrainSweep)));
     BCK(cudaMemcpy(b->d_grains, gs.data(), gs.size() * sizeof(scd::GrainSweep), cudaMemcpyHostToDevice));
     BCK(cudaMalloc(&b->d_items, flat.size() * sizeof(int2)));
@@ -404,6 +555,8 @@ sc_status sc_batch_destroy(sc_batch *b) {
     for (void *q : b->part_img) cudaFree(q);
     for (cudaEvent_t e : b->ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->iev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : b->cev)
         if (e) cudaEventDestroy(e);
     free_graphs(b);
@@ -472,6 +625,8 @@ sc_status sc_batch_create(const sc_params *params, int32_t n, int32_t energies_p
     cudaError_t e = cudaMalloc(&b->d_counter, sc_batch::kMaxClasses * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->iev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->iev[1]);
     for (int k = 0; k <= sc_batch::kMaxClasses && e == cudaSuccess; ++k) e = cudaEventCreate(&b->cev[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
     for (int k = 0; k < sc_batch::kAux && e == cudaSuccess; ++k) {
@@ -508,10 +663,18 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     for (sc_ctx *c : b->members)
         if (c->failed) return berr(b, SC_ESTATE, "a member context failed");
     sc_status fs = SC_OK;
+    // while a graph is being captured the timing events become external event
+    // nodes, so that every replay records them
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    BCK(cudaStreamIsCapturing(st, &cap));
+    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    BCK(cudaEventRecordWithFlags(b->iev[0], st, ev_flags));
     if (!b->fp64) {
-        // every member's fields onto its lattices: two launches over all members
-        BCK(scd::launch_batch_fields_rotate_f32(b->d_members, member_off(b, 0), b->tot_pad, member_off(b, 1),
-                                                b->tot_slots, n, st));
+        // every member's fields onto its lattices: two launches over all members (with
+        // transfer items, the rotation only of the members no class launch rotates)
+        BCK(scd::launch_batch_fields_rotate_f32(b->d_members, member_off(b, 0), b->tot_pad,
+                                                b->fused ? b->d_solo : member_off(b, 1),
+                                                b->fused ? b->tot_solo_rot : b->tot_slots, n, st));
     } else {
         fs = fork(b, st);
         if (fs != SC_OK) return fs;
@@ -526,11 +689,6 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     if (b->classes.size() > (size_t)sc_batch::kMaxClasses)
         return berr(b, SC_ESTATE, "more energies-per-lane classes than work counters");
     BCK(cudaMemsetAsync(b->d_counter, 0, sc_batch::kMaxClasses * sizeof(int32_t), st));
-    // while a graph is being captured the timing events become external event
-    // nodes, so that every replay records them
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    BCK(cudaStreamIsCapturing(st, &cap));
-    const unsigned ev_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
     BCK(cudaEventRecordWithFlags(b->ev[0], st, ev_flags));
     for (size_t k = 0; k < b->classes.size(); ++k) {
         const sc_batch::Class &c = b->classes[k];
@@ -553,7 +711,15 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.stepper = b->stepper;
         a.weighted = b->weighted ? 1 : 0;
         a.blocked = b->blocked;
-        BCK(scd::launch_sweep(b->fp64, a, st));
+        if (c.side_n > 0) {  // with the lattice transfers of other members as work items
+            a.side_members = b->d_members;
+            a.side = b->d_side + c.side_first;
+            a.n_side = (int32_t)c.side_n;
+            a.n_side_members = n;
+            BCK(scd::launch_sweep_side_f32(a, st));
+        } else {
+            BCK(scd::launch_sweep(b->fp64, a, st));
+        }
     }
     BCK(cudaEventRecordWithFlags(b->cev[b->classes.size()], st, ev_flags));
     for (size_t g = 0; g < b->members.size(); ++g) {
@@ -569,8 +735,12 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
     b->timed = true;
     if (!b->fp64) {
         // the Fermi-surface averages of every member: one launch per component count
-        for (int k = 0; k < 4; ++k)
-            BCK(scd::launch_batch_rotate_back_f32(b->d_members, member_off(b, 2 + k), b->tot_back[k], k + 1, n, st));
+        // (with transfer items, of the one-component members no class launch rotates back)
+        for (int k = 0; k < 4; ++k) {
+            const bool solo = b->fused && k == 0;
+            BCK(scd::launch_batch_rotate_back_f32(b->d_members, solo ? b->d_solo + (n + 1) : member_off(b, 2 + k),
+                                                  solo ? b->tot_solo_back : b->tot_back[k], k + 1, n, st));
+        }
     } else {
         fs = fork(b, st);
         if (fs != SC_OK) return fs;
@@ -581,6 +751,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         fs = join(b, st);
         if (fs != SC_OK) return fs;
     }
+    BCK(cudaEventRecordWithFlags(b->iev[1], st, ev_flags));
     for (sc_ctx *c : b->members) {
         c->cur = b->parity ^ 1;
         c->have_boundary = true;
@@ -610,6 +781,15 @@ sc_status sc_batch_set_energy_parts(sc_batch *b, int32_t on) {
     if (on && b->fp64) return berr(b, SC_EINVAL, "energy parts are an FP32 layout");
     BCK(cudaSetDevice(b->device));
     b->split = on != 0;
+    return build(b, b->ept);
+}
+
+sc_status sc_batch_set_fused_transfers(sc_batch *b, int32_t on) {
+    if (!b) return SC_EINVAL;
+    if (b->failed) return SC_ESTATE;
+    if (on && b->fp64) return berr(b, SC_EINVAL, "transfer items are an FP32 layout");
+    BCK(cudaSetDevice(b->device));
+    b->fuse = on != 0;
     return build(b, b->ept);
 }
 
@@ -695,8 +875,8 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
         for (int rep = 0; rep < 2; ++rep) {  // the second sweep is the one timed
             s = sc_batch_sweep(b, stream);
             if (s != SC_OK) return s;
-            BCK(cudaEventSynchronize(b->ev[1]));
-            BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+            BCK(cudaEventSynchronize(b->iev[1]));
+            BCK(cudaEventElapsedTime(&ms, b->iev[0], b->iev[1]));
         }
         if (ms < best_ms) {
             best_ms = ms;
@@ -715,8 +895,8 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
         for (int rep = 0; rep < 2; ++rep) {
             s = sc_batch_sweep(b, stream);
             if (s != SC_OK) return s;
-            BCK(cudaEventSynchronize(b->ev[1]));
-            BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+            BCK(cudaEventSynchronize(b->iev[1]));
+            BCK(cudaEventElapsedTime(&ms, b->iev[0], b->iev[1]));
         }
         if (ms < best_ms) {
             best_ms = ms;
@@ -734,9 +914,9 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
             for (int rep = 0; rep < 3; ++rep) {  // the second and third sweeps are timed
                 s = sc_batch_sweep(b, stream);
                 if (s != SC_OK) return s;
-                BCK(cudaEventSynchronize(b->ev[1]));
+                BCK(cudaEventSynchronize(b->iev[1]));
                 float ms = 0.f;
-                BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+                BCK(cudaEventElapsedTime(&ms, b->iev[0], b->iev[1]));
                 if (rep > 0) t[v] += ms;
             }
         }
@@ -744,6 +924,25 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
         b->split = ms_on < 0.99f * ms_off;  // parts only where they are clearly faster
         b->split_ms[0] = ms_on;
         b->split_ms[1] = ms_off;
+        // the members' lattice transfers as work items of the class launches, or
+        // in their own launches
+        float u[2] = {0.f, 0.f};  // with, without
+        for (int v = 0; v < 2; ++v) {
+            b->fuse = v == 0;
+            sc_status s = build(b, best);
+            if (s != SC_OK) return s;
+            for (int rep = 0; rep < 3; ++rep) {  // the second and third sweeps are timed
+                s = sc_batch_sweep(b, stream);
+                if (s != SC_OK) return s;
+                BCK(cudaEventSynchronize(b->iev[1]));
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, b->iev[0], b->iev[1]));
+                if (rep > 0) u[v] += ms;
+            }
+        }
+        b->fuse_ms[0] = 0.5f * u[0];
+        b->fuse_ms[1] = 0.5f * u[1];
+        b->fuse = b->fuse_ms[0] < 0.99f * b->fuse_ms[1];
     }
     b->bps_choice.clear();
     sc_status s = build(b, best);
@@ -851,14 +1050,18 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
     for (int nbk : b->member_blocks) nl += nbk > 1 ? 1 : 0;  // energy-block sums
     for (int np : b->member_parts) nl += np > 1 ? 1 : 0;     // sums of two energy parts
     if (!b->fp64) {
-        nl += (b->tot_pad > 0) + (b->tot_slots > 0);
-        for (int k = 0; k < 4; ++k) nl += b->tot_back[k] > 0;
+        nl += (b->tot_pad > 0) + ((b->fused ? b->tot_solo_rot : b->tot_slots) > 0);
+        for (int k = 0; k < 4; ++k) nl += (b->fused && k == 0 ? b->tot_solo_back : b->tot_back[k]) > 0;
     } else {
         nl += 2 * (int32_t)b->members.size();  // rotate and rotate-back per member
     }
     info->launches_per_iteration = nl;
     info->split_ms_on = b->split_ms[0];
     info->split_ms_off = b->split_ms[1];
+    info->fused_transfers = b->fused ? 1 : 0;
+    info->transfer_items = b->n_side;
+    info->fuse_ms_on = b->fuse_ms[0];
+    info->fuse_ms_off = b->fuse_ms[1];
     info->split_members = 0;
     for (int np : b->member_parts) info->split_members += np > 1 ? 1 : 0;
     static_assert(sc_batch::kMaxClasses <= 16, "sc_batch_info holds 16 classes");
@@ -881,6 +1084,11 @@ sc_status sc_batch_get_info(const sc_batch *b, sc_batch_info *info) {
             info->ms_sweep = ms;
         else
             (void)cudaGetLastError();  // a failed query must not linger as the thread's last error
+        if (cudaEventSynchronize(b->iev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, b->iev[0], b->iev[1]) == cudaSuccess)
+            info->ms_iteration = ms;
+        else
+            (void)cudaGetLastError();
     }
     return SC_OK;
 }

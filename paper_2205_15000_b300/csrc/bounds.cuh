@@ -46,9 +46,10 @@ __device__ __forceinline__ T ld_chk(const T *t, int64_t i, int64_t n) {
     return in_bounds(i, n) ? t[i] : T{};
 }
 
-// the per-unit accessors (sweep_f32.cu, sweep_f64.cu, adjoint_f32.cu,
+// the per-unit accessors (sweep_f32.cu, sweep_side_f32.cu, sweep_f64.cu, adjoint_f32.cu,
 // adjoint_f64.cu, adjoint.cu, lattice_f32.cu, kernels.cu)
 cudaError_t bounds_sweep_f32(unsigned long long *v, bool reset);
+cudaError_t bounds_sweep_side_f32(unsigned long long *v, bool reset);
 cudaError_t bounds_sweep_f64(unsigned long long *v, bool reset);
 cudaError_t bounds_adjoint_f32(unsigned long long *v, bool reset);
 cudaError_t bounds_adjoint_f64(unsigned long long *v, bool reset);

@@ -170,6 +170,8 @@ struct GrainSweep {
                                // in its own layout and image (e_count 0: all n_e energies)
 };
 
+struct MemberDev;
+
 // One persistent launch over the work items (grain, line group) of any number
 // of grains; items are taken from an atomic counter, longest first.
 struct SweepLaunch {
@@ -190,6 +192,15 @@ struct SweepLaunch {
     int32_t weighted;          // Matsubara mode: weighted energy sums (grains carry mats_w)
     int32_t blocked;           // some grain splits its energies into blocks (each block writes its
                                // own partial image; launch_block_sum adds them in block order)
+    // FP32 batch (launch_sweep_side_f32 only): lattice transfers of other members
+    // as work items of the launch, spread evenly among the sweep items.  side[s] =
+    // (2 member + kind, index): kind 0 rotates lines 4 index .. 4 index + 3 of the
+    // member, kind 1 rotates back its tile `index` of 8 x 4 grid points (members of
+    // one order-parameter component).
+    const MemberDev *side_members;
+    const int2 *side;
+    int32_t n_side;
+    int32_t n_side_members;
 };
 
 // launchers (return cudaError_t)
@@ -222,6 +233,10 @@ cudaError_t launch_rotate_back_f32(const PairF32 *pairs, int32_t n_pairs, const 
 int sweep_occupancy(bool fp64, int ept, int block_threads, int stepper, bool weighted);
 // per-precision instantiations (sweep_f32.cu, sweep_f64.cu)
 cudaError_t launch_sweep_f32(const SweepLaunch &a, cudaStream_t s);
+// the FP32 batch sweep with lattice transfers as work items (a.n_side > 0;
+// Matsubara or Ozaki sums, no energy blocks, not retarded)
+cudaError_t launch_sweep_side_f32(const SweepLaunch &a, cudaStream_t s);
+int sweep_side_occupancy_f32(int ept, int block_threads, int stepper, bool weighted);
 cudaError_t launch_sweep_f64(const SweepLaunch &a, cudaStream_t s);
 int sweep_occupancy_f32(int ept, int block_threads, int stepper, bool weighted);
 int sweep_occupancy_f64(int ept, int block_threads, int stepper, bool weighted);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "kernels.cuh"
+#include "lattice_f32.cuh"
 #include "riccati_step.cuh"
 #include "sweep_x2.cuh"
 
@@ -307,19 +308,57 @@ __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, 
 #define SC_SWEEP_MIN_BLOCKS_WIDE 4
 #endif
 
-template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK = false>
+// A lattice transfer of another batch member as a work item of a sweep launch:
+// the rotation of four of its lines, or the rotate-back of one of its tiles (the
+// same arithmetic as the transfer kernels, so the same values).  A call, not
+// inlined, so that the sweep's register allocation is its own.
+static __device__ __noinline__ void side_item(const SweepLaunch &a, int64_t s, const int lane) {
+    const int2 v = a.side[s];
+    const int m = v.x >> 1;
+    if (!in_bounds(m, a.n_side_members)) return;
+    const MemberDev &M = a.side_members[m];
+    if ((v.x & 1) == 0) {
+        const int64_t L0 = 4 * (int64_t)v.y;
+        if (L0 >= M.grid.n_lines) return;
+        switch (M.grid.gauge) {
+            case 2: rotate_f32_quad<2>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+            case 1: rotate_f32_quad<1>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane); break;
+            default: rotate_f32_quad<0>(M.lines, L0, M.grid.n_lines, M.pairs, M.grid, M.ghost, M.pad0, M.padc, M.image_in, lane);
+        }
+    } else {
+        rotate_back_f32_warp<1>(M.pairs, M.n_pairs, M.back, M.grid, M.mask, M.image_out, M.acc, v.y, lane);
+    }
+}
+
+// SIDE: the launch also carries a.n_side lattice transfers (FP32 batch sweeps):
+// counter value c is transfer s(c) when s(c + 1) > s(c), s(c) = floor(c n_side /
+// (n_items + n_side)), else sweep item c - s(c), so the transfers are spread
+// evenly over the sweep items, which keep their longest-first order.
+template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK = false, bool SIDE = false>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (EPT > 8 ? SC_SWEEP_MIN_BLOCKS_WIDE
                                                                  : (STEP ? SC_SWEEP_MIN_BLOCKS_MID : SC_SWEEP_MIN_BLOCKS))
                                                       : 1)
     sweep_kernel(SweepLaunch a) {
+    static_assert(!SIDE || (sizeof(T) == 4 && !RET && !BLK), "transfer items run in FP32 batch sweeps only");
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     Cx<T> *const warp_slab = (Cx<T> *)a.scratch + wid * a.scratch_stride;
+    const int64_t n_side = SIDE ? (int64_t)a.n_side : 0;
+    const int64_t total = (int64_t)a.n_items + n_side;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = atomicAdd(a.counter, 1);
-        item = __shfl_sync(FULL_MASK, item, 0);
-        if (item >= a.n_items) break;
+        int c = 0;
+        if (lane == 0) c = atomicAdd(a.counter, 1);
+        c = __shfl_sync(FULL_MASK, c, 0);
+        if (c >= total) break;
+        int item = c;
+        if constexpr (SIDE) {
+            const int64_t s0 = (int64_t)c * n_side / total, s1 = ((int64_t)c + 1) * n_side / total;
+            if (s1 > s0) {
+                side_item(a, s0, lane);
+                continue;
+            }
+            item = c - (int)s0;
+        }
         const int2 it = a.items[item];
         if (!in_bounds(it.x, a.n_grains)) continue;
         if constexpr (sizeof(T) == 4)  // FP32: packed energy pairs
@@ -329,19 +368,19 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? (EPT > 8 ? SC_SWEEP_MIN_
     }
 }
 
-template <typename T, bool RET, int STEP, bool WGT, bool BLK = false>
+template <typename T, bool RET, int STEP, bool WGT, bool BLK = false, bool SIDE = false>
 static cudaError_t sweep_dispatch(const SweepLaunch &a, cudaStream_t st) {
     dim3 grid(a.grid_blocks), block(a.block_threads);
     switch (a.energies_per_lane) {
 #define SC_CASE(E) \
-    case E: sweep_kernel<T, E, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a); break;
+    case E: sweep_kernel<T, E, RET, STEP, WGT, BLK, SIDE><<<grid, block, 0, st>>>(a); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
         case 9:
         case 10:
             // the wide layouts exist for the FP32 sweep without energy blocks only
             if constexpr (sizeof(T) == 4 && !RET && !BLK) {
-                if (a.energies_per_lane == 9) sweep_kernel<T, 9, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a);
-                else sweep_kernel<T, 10, RET, STEP, WGT, BLK><<<grid, block, 0, st>>>(a);
+                if (a.energies_per_lane == 9) sweep_kernel<T, 9, RET, STEP, WGT, BLK, SIDE><<<grid, block, 0, st>>>(a);
+                else sweep_kernel<T, 10, RET, STEP, WGT, BLK, SIDE><<<grid, block, 0, st>>>(a);
                 break;
             } else {
                 return cudaErrorInvalidValue;
@@ -368,19 +407,19 @@ static cudaError_t sweep_launch_t(const SweepLaunch &a, cudaStream_t st) {
     return sweep_launch_s<T, 0>(a, st);
 }
 
-template <typename T, bool RET, int STEP, bool WGT>
+template <typename T, bool RET, int STEP, bool WGT, bool SIDE = false>
 static int occ_dispatch(int ept, int bs) {
     int n = 0;
     switch (ept) {
 #define SC_CASE(E) \
-    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET, STEP, WGT>, bs, 0); break;
+    case E: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, E, RET, STEP, WGT, false, SIDE>, bs, 0); break;
         SC_CASE(1) SC_CASE(2) SC_CASE(3) SC_CASE(4) SC_CASE(5) SC_CASE(6) SC_CASE(7) SC_CASE(8)
 #undef SC_CASE
         case 9:
         case 10:
             if constexpr (sizeof(T) == 4 && !RET) {
-                if (ept == 9) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 9, RET, STEP, WGT>, bs, 0);
-                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 10, RET, STEP, WGT>, bs, 0);
+                if (ept == 9) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 9, RET, STEP, WGT, false, SIDE>, bs, 0);
+                else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_kernel<T, 10, RET, STEP, WGT, false, SIDE>, bs, 0);
             } else {
                 n = 0;
             }

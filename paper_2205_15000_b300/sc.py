@@ -82,6 +82,9 @@ class sc_batch_info(ctypes.Structure):
         ("class_ms", ctypes.c_double * 16), ("min_lanes_per_line", ctypes.c_int32),
         ("launches_per_iteration", ctypes.c_int32), ("split_members", ctypes.c_int32),
         ("split_ms_on", ctypes.c_double), ("split_ms_off", ctypes.c_double),
+        ("fused_transfers", ctypes.c_int32), ("transfer_items", ctypes.c_int64),
+        ("fuse_ms_on", ctypes.c_double), ("fuse_ms_off", ctypes.c_double),
+        ("ms_iteration", ctypes.c_double),
     ]
 
 
@@ -122,7 +125,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_reset_boundary",
-            "sc_batch_set_energy_parts",
+            "sc_batch_set_energy_parts", "sc_batch_set_fused_transfers",
             "sc_batch_autotune",
             "sc_batch_get_info", "sc_batch_set_fields", "sc_batch_get_outputs", "sc_last_error", "sc_version"]
 
@@ -179,6 +182,7 @@ def _load():
         "sc_batch_run": [vp, i32, i32, vp],
         "sc_batch_reset_boundary": [vp],
         "sc_batch_set_energy_parts": [vp, i32],
+        "sc_batch_set_fused_transfers": [vp, i32],
         "sc_batch_autotune": [vp, P(i32), vp],
         "sc_batch_get_info": [vp, P(sc_batch_info)],
         "sc_batch_set_fields": [vp, vp, ctypes.c_int, vp],
@@ -499,6 +503,12 @@ def sc_batch_set_energy_parts(b, on):
     _check(lib.sc_batch_set_energy_parts(b, int(bool(on))))
 
 
+def sc_batch_set_fused_transfers(b, on):
+    """FP32: run the members' rotations and rotate-backs as work items of the
+    sweep's class launches (layout rebuilt)."""
+    _check(lib.sc_batch_set_fused_transfers(b, int(bool(on))))
+
+
 def sc_batch_reset_boundary(b):
     """The next batch sweep starts from fresh boundary values (layout kept)."""
     _check(lib.sc_batch_reset_boundary(b))
@@ -556,6 +566,9 @@ class Batch:
 
     def reset_boundary(self):
         sc_batch_reset_boundary(self.h)
+
+    def set_fused_transfers(self, on):
+        sc_batch_set_fused_transfers(self.h, on)
 
     def info(self):
         return sc_batch_get_info(self.h)
