@@ -668,6 +668,8 @@ def run_batch(args):
     msteps = [m.info.steps_per_sweep for m in b.members]
     check = _c3_members_for_errors(grains, msteps)
     ept = b.autotune(stream) if not args.ept else args.ept
+    if args.transfers != "auto":
+        b.set_fused_transfers(args.transfers == "fused")
     # outputs of the checked members after two sweeps from fresh boundary values,
     # in the layout that is timed
     got = {}
@@ -768,6 +770,21 @@ def run_batch(args):
     last = b.info()
     classes = [{"energies_per_lane": last.class_ept[k], "blocks_per_sm": last.class_blocks_per_sm[k],
                 "ms": last.class_ms[k]} for k in range(last.sweep_launches)]
+    # with the transfers inside the sweep launches, the sweep kernel alone is also
+    # timed in the separate layout (same classes and blocks per SM), after the
+    # timed steps, so that its own roofline fraction is reported beside the
+    # fused launches'
+    separate = None
+    if last.fused_transfers:
+        b.set_fused_transfers(False)
+        b.run(2, True, stream)
+        ms_sep = []
+        for i in range(5):
+            b.run(1, True, stream)
+            flush.fill_(float(i))
+            ms_sep.append(b.info().ms_sweep)
+        torch.cuda.synchronize()
+        separate = {"ms_per_sweep": statistics.mean(ms_sep), "steps": 5}
     b.close()
     del b
 
@@ -848,6 +865,11 @@ def run_batch(args):
                      "peak_note": ("FP32" if args.precision == "fp32" else "FP64")
                      + " lane issue 148 SM x lanes/cycle x max SM clock (derived)",
                      "peak_measured": pm, "frac_of_measured": (achieved / pm) if pm else None,
+                     "sweep_kernel_alone": None if separate is None else dict(
+                         separate, frac=pse * ALG_OPS_PER_PSE[args.stepper] / (separate["ms_per_sweep"] * 1e-3)
+                         / 1e9 / peak_gops,
+                         note="the same class launches without the transfer work items (transfers in launches "
+                              "of their own), 5 steps after the timed ones"),
                      "peak_measured_note": "sc_debug_fma_rate after the timed steps: 8 blocks of 256 threads per SM, "
                                            "8 independent FMA chains per thread"},
         "fp64_plain": fp64,
@@ -1145,6 +1167,9 @@ def main():
     ap.add_argument("--ept", type=int, default=0,
                     help="batch bound on energies per lane (0: chosen by sc_batch_autotune)")
     ap.add_argument("--no-fp64", action="store_true", help="batch: skip the plain FP64 comparison arm")
+    ap.add_argument("--transfers", default="auto", choices=["auto", "fused", "separate"],
+                    help="batch: members' rotations and rotate-backs as work items of the sweep launches "
+                         "(fused), in launches of their own (separate), or as sc_batch_autotune chooses (auto)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="batch: timed steps of the plain FP64 arm")
     ap.add_argument("--ldos", action="store_true", help="time the LDOS sweeps on the c4 grain (64 energies)")
     ap.add_argument("--accel-table", action="store_true",

@@ -78,7 +78,8 @@ struct sc_batch {
     cudaEvent_t iev[2] = {nullptr, nullptr};  // around a whole batch sweep (rotation to rotate-back)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t cev[kMaxClasses + 1] = {};  // around each class launch of the last sweep
-    std::vector<int> bps_choice;  // autotuned blocks per SM of each class (empty: occupancy)
+    std::vector<int> bps_choice;  // autotuned blocks per SM of the class of each energies-per-lane
+                                  // count (index; empty or 0: occupancy)
     bool timed = false;
     // captured iterations: graph[p] = one sweep starting from parity p (+ outputs)
     cudaStream_t gstream = nullptr;
@@ -415,7 +416,8 @@ sc_status build(sc_batch *b, int ept) {
                                : scd::sweep_occupancy(b->fp64, c.ept, 128, b->stepper, b->weighted);
         if (occ < 1) occ = 1;
         c.occ = occ;
-        c.bps = k < b->bps_choice.size() && b->bps_choice[k] > 0 ? std::min(b->bps_choice[k], occ) : occ;
+        const size_t e = (size_t)c.ept;
+        c.bps = e < b->bps_choice.size() && b->bps_choice[e] > 0 ? std::min(b->bps_choice[e], occ) : occ;
         c.grid_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->sm_count * c.bps, (c.n + c.side_n + 3) / 4));
         max_blocks = std::max(max_blocks, c.grid_blocks);
     }
@@ -950,14 +952,15 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
     // per class: the persistent grid sized for occupancy, occupancy - 1, occupancy - 2
     // resident blocks per SM; each class keeps its fastest
     const size_t nc = b->classes.size();
-    std::vector<int> pick(nc, 0);
-    std::vector<float> pick_ms(nc, 1e30f);
+    constexpr size_t kE = 11;  // energies per lane 1..10
+    std::vector<int> pick(kE, 0);
+    std::vector<float> pick_ms(kE, 1e30f);
     for (int d = 0; d <= 2; ++d) {
-        b->bps_choice.assign(nc, 0);
+        b->bps_choice.assign(kE, 0);
         bool any = false;
         for (size_t k = 0; k < nc; ++k) {
             const int occ = b->classes[k].occ;
-            b->bps_choice[k] = std::max(1, occ - d);
+            b->bps_choice[b->classes[k].ept] = std::max(1, occ - d);
             any = any || occ - d >= 1;
         }
         if (!any) break;
@@ -971,9 +974,10 @@ sc_status sc_batch_autotune(sc_batch *b, int32_t *energies_per_lane, void *strea
         for (size_t k = 0; k < nc; ++k) {
             float ms = 0.f;
             BCK(cudaEventElapsedTime(&ms, b->cev[k], b->cev[k + 1]));
-            if (ms < pick_ms[k]) {
-                pick_ms[k] = ms;
-                pick[k] = b->bps_choice[k];
+            const int e = b->classes[k].ept;
+            if (ms < pick_ms[e]) {
+                pick_ms[e] = ms;
+                pick[e] = b->bps_choice[e];
             }
         }
     }

@@ -86,3 +86,27 @@ def test_fused_transfers_bitwise_equal(stepper, energy_sum, split):
             for k in ("images", "delta_new", "j", "F"):
                 assert np.array_equal(ra[k], rc[k]), (it, g, k)
             assert np.isfinite(ra["delta_new"]).all()
+
+
+def test_autotuned_blocks_per_sm_follow_their_class():
+    """The autotune's blocks per SM belong to an energies-per-lane class, not to a
+    launch position: switching the transfer layout afterwards (which reorders the
+    launches) keeps each class's choice."""
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    b = sc.Batch([p for p, _ in grains], precision="fp32")
+    for m, (_, d) in zip(b.members, grains):
+        m.set_fields(d)
+    b.autotune()
+
+    def per_class(i):
+        return {i.class_ept[k]: i.class_blocks_per_sm[k] for k in range(i.sweep_launches)}
+
+    ref = per_class(b.info())
+    for fused in (True, False, True):
+        b.set_fused_transfers(fused)
+        got = per_class(b.info())
+        assert got == ref, (fused, got, ref)
+    b.sweep()
+    assert np.isfinite(b.members[0].outputs()["delta_new"].cpu().numpy()).all()
+    b.close()
