@@ -241,6 +241,17 @@ sc_status sc_burnin(sc_ctx *ctx, int32_t max_sweeps, double tol, void *stream);
    synchronises the stream.  Requires a preceding sc_riccati_sweep. */
 sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_device,
                         void *stream);
+/* Residual history (the per-iteration record of the self-consistency loop,
+   Algorithm 1): one record per residual eps_G (Eq. global_error) that
+   sc_gap_update computed -- every residual check of sc_self_consistency
+   included -- oldest first, each with the number of sweeps the context (or its
+   batch) had run at that point; the newest 65536 are kept.  *n: in, the
+   capacity of `sweeps` and `eps_G` (0 with NULL arrays to ask for the count);
+   out, the number of records held (the first min(capacity, count) are
+   written).  SC_EINVAL for a NULL context or n, a negative capacity, or a
+   positive capacity with a NULL array.  sc_clear_history forgets them. */
+sc_status sc_get_history(const sc_ctx *ctx, int32_t *n, int64_t *sweeps, double *eps_G);
+sc_status sc_clear_history(sc_ctx *ctx);
 /* Charge-current density j(R) = 2 e N_F T sum_n <v_F g> (Eq. current_density),
    vector nx*ny in units of j0. */
 sc_status sc_current(sc_ctx *ctx, double *j_out, int on_device, void *stream);

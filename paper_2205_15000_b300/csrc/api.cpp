@@ -948,6 +948,7 @@ sc_status sc_riccati_sweep(sc_ctx *ctx, void *stream) {
     ctx->have_boundary = true;
     ctx->have_sweep = true;
     ctx->have_outputs = false;
+    ++ctx->sweeps;
     return SC_OK;
 }
 
@@ -979,7 +980,32 @@ sc_status sc_gap_update(sc_ctx *ctx, double *delta_out, double *eps_G, int on_de
         CK(cudaStreamSynchronize(st));
         if (s[3] != 0.0) return set_err(ctx, SC_ENUMERIC, "non-finite values in the sweep outputs");
         *eps_G = s[1] > 0.0 ? std::sqrt(s[0] / s[1]) : 0.0;
+        if (ctx->history.size() == sc_ctx::kHistory) ctx->history.pop_front();
+        ctx->history.emplace_back(ctx->sweeps, *eps_G);
     }
+    return SC_OK;
+}
+
+sc_status sc_get_history(const sc_ctx *ctx, int32_t *n, int64_t *sweeps, double *eps_G) {
+    if (!ctx || !n || *n < 0 || (*n > 0 && (!sweeps || !eps_G))) {
+        sc_internal::set_thread_error("sc_get_history needs a context, n >= 0 and, for n > 0, both arrays");
+        return SC_EINVAL;
+    }
+    const size_t cap = (size_t)*n;
+    size_t k = 0;
+    for (const auto &r : ctx->history) {
+        if (k == cap) break;
+        sweeps[k] = r.first;
+        eps_G[k] = r.second;
+        ++k;
+    }
+    *n = (int32_t)ctx->history.size();
+    return SC_OK;
+}
+
+sc_status sc_clear_history(sc_ctx *ctx) {
+    if (!ctx) return SC_EINVAL;
+    ctx->history.clear();
     return SC_OK;
 }
 

@@ -759,6 +759,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         c->have_boundary = true;
         c->have_sweep = true;
         c->have_outputs = false;
+        ++c->sweeps;
     }
     b->parity ^= 1;
     b->have_boundary = true;
@@ -825,7 +826,10 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
     if (done < n_sweeps && (b->graph_outputs != (with_outputs ? 1 : 0) || b->graph_ept != b->ept || !b->graph[0])) {
         free_graphs(b);
         // capture one iteration per parity; the host state advances as if they ran,
-        // so after capturing both it is back where it started
+        // so after capturing both it is back where it started (the members' sweep
+        // counts, which only advance, are put back)
+        std::vector<int64_t> swept(b->members.size());
+        for (size_t g = 0; g < b->members.size(); ++g) swept[g] = b->members[g]->sweeps;
         for (int k = 0; k < 2; ++k) {
             const int par = b->parity;
             cudaGraph_t g = nullptr;
@@ -843,6 +847,7 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
         }
         b->graph_outputs = with_outputs ? 1 : 0;
         b->graph_ept = b->ept;
+        for (size_t g = 0; g < b->members.size(); ++g) b->members[g]->sweeps = swept[g];
     }
     for (; done < n_sweeps; ++done) {
         BCK(cudaGraphLaunch(b->graph[b->parity], b->gstream));
@@ -852,6 +857,7 @@ sc_status sc_batch_run(sc_batch *b, int32_t n_sweeps, int32_t with_outputs, void
             c->have_boundary = true;
             c->have_sweep = true;
             c->have_outputs = with_outputs != 0;
+            ++c->sweeps;
         }
         b->parity ^= 1;
     }

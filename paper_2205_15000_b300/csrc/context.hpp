@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <deque>
 #include <map>
 #include <string>
 #include <vector>
@@ -85,6 +86,11 @@ struct sc_ctx {
     bool failed = false;
     bool host_only = false;
     bool batch_member = false;  // swept only through its batch
+    // residual history (sc_get_history): sweeps run so far, and per residual that
+    // sc_gap_update computed, the sweep count then and eps_G (the newest kHistory)
+    int64_t sweeps = 0;
+    static constexpr size_t kHistory = 65536;
+    std::deque<std::pair<int64_t, double>> history;
     // failure injection for tests: the fail_alloc_at-th device allocation of this
     // context reports cudaErrorMemoryAllocation without touching the device (-1 = off)
     long fail_alloc_at = -1;

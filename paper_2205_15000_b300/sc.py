@@ -122,7 +122,7 @@ EXPORTED = ["sc_params_default", "sc_create", "sc_destroy", "sc_get_info", "sc_g
             "sc_debug_exits", "sc_debug_images", "sc_debug_fp64_math", "sc_debug_fma_rate", "sc_debug_validate_tables",
             "sc_debug_corrupt_table", "sc_debug_bounds", "sc_sweep_lines_noalloc", "sc_sweep_adjoint",
             "sc_ldos_adjoint", "sc_accel_params_default", "sc_accelerate", "sc_accel_reset",
-            "sc_accel_get_state", "sc_self_consistency", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
+            "sc_accel_get_state", "sc_self_consistency", "sc_get_history", "sc_clear_history", "sc_ozaki_poles", "sc_ozaki_poles_for_cutoff", "sc_energy_grid",
             "sc_batch_create",
             "sc_batch_destroy", "sc_batch_member", "sc_batch_sweep", "sc_batch_run", "sc_batch_reset_boundary",
             "sc_batch_set_energy_parts", "sc_batch_set_fused_transfers",
@@ -169,6 +169,8 @@ def _load():
         "sc_ldos_adjoint": [vp, vp, i32, f64, i32, vp, vp, vp, ctypes.c_int, vp],
         "sc_ozaki_poles": [i32, vp, vp],
         "sc_self_consistency": [vp, P(sc_accel_params), i32, f64, i32, P(i32), P(f64), vp],
+        "sc_get_history": [vp, P(i32), vp, vp],
+        "sc_clear_history": [vp],
         "sc_ozaki_poles_for_cutoff": [f64, f64],
         "sc_energy_grid": [vp, vp, vp],
         "sc_accel_params_default": [i32, P(sc_accel_params)],
@@ -432,6 +434,24 @@ def sc_accelerate(ctx, params, stream=None):
 
 def sc_accel_reset(ctx):
     _check(lib.sc_accel_reset(ctx), ctx)
+
+
+def sc_get_history(ctx):
+    """The context's residual records, oldest first: (sweeps run, eps_G) as two
+    numpy arrays."""
+    n = ctypes.c_int32(0)
+    _check(lib.sc_get_history(ctx, ctypes.byref(n), None, None))
+    cap = n.value
+    sw = np.zeros(cap, dtype=np.int64)
+    eps = np.zeros(cap, dtype=np.float64)
+    if cap:
+        n = ctypes.c_int32(cap)
+        _check(lib.sc_get_history(ctx, ctypes.byref(n), sw.ctypes.data, eps.ctypes.data))
+    return sw, eps
+
+
+def sc_clear_history(ctx):
+    _check(lib.sc_clear_history(ctx))
 
 
 def sc_accel_get_state(ctx):
@@ -735,6 +755,13 @@ class Context:
         if st not in (SC_OK, SC_ENOTCONV):
             _check(st, self.h)
         return st == SC_OK, it.value, eps.value
+
+    def history(self):
+        """Residual records of this context, oldest first: (sweeps, eps_G)."""
+        return sc_get_history(self.h)
+
+    def clear_history(self):
+        sc_clear_history(self.h)
 
     def ldos(self, energies, broadening, n_burnin=20, stream=None):
         import torch

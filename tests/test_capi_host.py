@@ -253,3 +253,19 @@ def test_checked_library_exports_the_same_symbols():
     L = ctypes.CDLL(build.LIB_CHECKED)
     for n in _declared():
         assert hasattr(L, n), n
+
+
+def test_residual_history_arguments():
+    """sc_get_history on a context with no residual computed yet: no records;
+    a negative capacity, or a positive one without arrays, is refused."""
+    import ctypes
+    p = W.disc(5.0, 32, n_angles=8, n_energies=6, t=0.4)
+    ctx = sc.Context(p, host_only=True)
+    sw, eps = sc.sc_get_history(ctx.h)
+    assert sw.size == 0 and eps.size == 0
+    n = ctypes.c_int32(-1)
+    assert sc.lib.sc_get_history(ctx.h, ctypes.byref(n), None, None) == sc.SC_EINVAL
+    n = ctypes.c_int32(2)
+    assert sc.lib.sc_get_history(ctx.h, ctypes.byref(n), None, None) == sc.SC_EINVAL
+    assert sc.lib.sc_get_history(None, ctypes.byref(n), None, None) == sc.SC_EINVAL
+    sc.sc_clear_history(ctx.h)

@@ -166,3 +166,34 @@ def test_native_loop_equals_python_loop(kind):
     assert conv and eps < 1e-3 and it > 1
     _, hist = _gpu_loop(q, d0, kind, it)
     assert np.all(hist[:-1] >= 1e-3) and hist[-1] < 1e-3
+
+
+def test_residual_history_records_every_check():
+    """The native loop's residual checks and every sc_gap_update residual are
+    recorded with the sweep count: the records equal the residuals of the same
+    iterations driven from Python; a batch member counts its batch's sweeps,
+    graph replays included."""
+    from paper_2205_15000_b300 import sc
+    p, d0 = _grain()
+    prm = sc.accel_params("barzilai-borwein")
+    a = sc.Context(p, precision="fp64")
+    a.set_fields(d0)
+    conv, it, eps = a.self_consistency(prm, max_iter=10, tol=0.0, check_every=3)
+    assert not conv and it == 10
+    sw, ev = a.history()
+    assert sw.tolist() == [3, 6, 9, 10] and ev[-1] == eps
+    b, hist = _gpu_loop(p, d0, "barzilai-borwein", 10)
+    sb, eb = b.history()
+    assert sb.tolist() == list(range(1, 11))
+    assert np.array_equal(eb, hist)
+    assert np.array_equal(ev, hist[[2, 5, 8, 9]])
+    a.clear_history()
+    assert a.history()[0].size == 0
+    bt = sc.Batch([p], precision="fp32")
+    bt.members[0].set_fields(d0)
+    bt.run(2, with_outputs=True)
+    bt.sweep()
+    e3 = ctypes_eps(sc, bt.members[0])
+    sw, ev = bt.members[0].history()
+    assert sw.tolist() == [3] and ev[0] == e3
+    bt.close()
