@@ -5,6 +5,7 @@ an independent integrator, brute force on tiny inputs and invariances.
 Each test names the passage of the paper that fixes the checked fact.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -14,6 +15,39 @@ import oracle
 from paper_2205_15000_b300 import workloads as W
 
 EULER_GAMMA = 0.5772156649015329
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    """Rows of a fixture under tests/golden ('|'-separated, '#' comments)."""
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [[c.strip() for c in ln.split("|")] for ln in f if ln.strip() and not ln.startswith("#")]
+
+
+def _printed_eta(expr, phi):
+    """Evaluate a basis function as printed in the paper's table: 1, or
+    sqrt(2)*sin(m*phi) / sqrt(2)*cos(m*phi)."""
+    import re
+    if expr == "1":
+        return np.ones_like(phi)
+    m = re.fullmatch(r"sqrt\(2\)\*(sin|cos)\((\d+)\*phi\)", expr)
+    assert m, expr
+    f = np.sin if m.group(1) == "sin" else np.cos
+    return math.sqrt(2.0) * f(int(m.group(2)) * phi)
+
+
+@pytest.mark.parametrize("row", _golden_rows("basis_functions.txt"), ids=lambda r: r[1])
+def test_basis_functions_match_printed_table(row):
+    """eta(phi) of every pairing symmetry at the Fermi angles phi_k = 2 pi k / N
+    equals the printed table of basis functions (Table basis_functions;
+    fixture tests/golden/basis_functions.txt)."""
+    pairing, _, expr = int(row[0]), row[1], row[2]
+    p = W.disc(5.0, 24, pairing=pairing, n_angles=64, n_energies=4, t=0.5)
+    _, _, eta = oracle.OracleGeom(p).quadrature()
+    phi = 2.0 * np.pi * np.arange(64) / 64
+    np.testing.assert_allclose(eta, _printed_eta(expr, phi), rtol=0, atol=1e-14)
 
 
 # ---------------------------------------------------------------------------
