@@ -42,6 +42,7 @@ struct sc_batch {
         int ept, first, n, grid_blocks;
         int occ, bps;  // occupancy (blocks per SM) and the blocks per SM the grid is sized for
         int64_t side_first, side_n;  // its lattice-transfer items: d_side[side_first, + side_n)
+        int blocked;                 // it holds a member whose energies are split into blocks
     };
     std::vector<Class> classes;
     void *d_scratch = nullptr;
@@ -395,10 +396,13 @@ sc_status build(sc_batch *b, int ept) {
     for (size_t i = 0; i < items.size(); ++i) {
         const int e = gs[items[i].grain].ept;
         if (classes.empty() || classes.back().ept != e) {
-            classes.push_back({e, (int)i, 0, 0, 0, 0, 0, 0});
+            classes.push_back({e, (int)i, 0, 0, 0, 0, 0, 0, 0});
             class_cost.push_back(0.0);
         }
         ++classes.back().n;
+        // the block-aware kernels (at most 8 energies per lane, as every blocked
+        // member's layout) only where a member of the class is blocked
+        if (gs[items[i].grain].n_blocks > 1) classes.back().blocked = 1;
         class_cost.back() += 64.0 * items[i].cost;  // both directions, 32 lanes
     }
     bool any_blocks = false;
@@ -712,7 +716,7 @@ sc_status sc_batch_sweep(sc_batch *b, void *stream) {
         a.block_threads = 128;
         a.stepper = b->stepper;
         a.weighted = b->weighted ? 1 : 0;
-        a.blocked = b->blocked;
+        a.blocked = c.blocked;
         if (c.side_n > 0) {  // with the lattice transfers of other members as work items
             a.side_members = b->d_members;
             a.side = b->d_side + c.side_first;

@@ -37,8 +37,9 @@ namespace scd {
 // One work item: the G lines of group it.y of grain gs, EPT energies per lane;
 // STEP 0 = closed-form step, 1 = implicit midpoint rule; WGT: weighted energy
 // sums (Ozaki's poles) in the Matsubara mode; BLK: the launch holds a grain whose
-// energies are split into blocks (every image of the launch is zeroed first and
-// the sample sums are added into it).
+// energies are split into blocks (item y of a grain is line group y / n_blocks
+// with energy block y % n_blocks, whose sample sums go to that block's own image;
+// a grain of one block is swept as without BLK).
 template <typename T, int EPT, bool RET, int STEP, bool WGT, bool BLK>
 __device__ __forceinline__ void sweep_item(const SweepLaunch &a, const int2 it, const GrainSweep &gs,
                                            Cx<T> *const warp_slab, const int lane) {

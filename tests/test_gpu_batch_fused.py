@@ -110,3 +110,41 @@ def test_autotuned_blocks_per_sm_follow_their_class():
     b.sweep()
     assert np.isfinite(b.members[0].outputs()["delta_new"].cpu().numpy()).all()
     b.close()
+
+
+def test_transfer_items_only_where_the_layout_allows():
+    """The fused layout needs two or more launch classes and no member in energy
+    blocks; otherwise the transfers stay in launches of their own (and the
+    results equal the separate layout's).  FP64 batches refuse it."""
+    from paper_2205_15000_b300 import sc
+    grains = _grains()
+    # one class: two members with the same energies-per-lane count
+    one = [grains[0], (dict(grains[0][0]), W.noisy_delta(grains[0][0], 0.26, 0.1, seed=47))]
+    b = sc.Batch([p for p, _ in one], precision="fp32", energies_per_lane=10)
+    b.set_fused_transfers(True)
+    i = b.info()
+    assert i.sweep_launches == 1 and i.fused_transfers == 0 and i.transfer_items == 0
+    b.close()
+    # a member whose 700 energies exceed one layout (three energy blocks)
+    p = W.disc(3.0, 24, pairing=1, t=0.02, n_angles=8, n_energies=700, flux_quanta=0.4)
+    blk = [grains[0], grains[1], (p, W.vortex_delta(p, 0.24, [(0.5, -0.3)], [-1], seed=48, rel_noise=0.05))]
+    res = []
+    for fused in (True, False):
+        b = sc.Batch([q for q, _ in blk], precision="fp32", energies_per_lane=10)
+        b.set_fused_transfers(fused)
+        i = b.info()
+        assert i.sweep_launches >= 2 and i.fused_transfers == 0
+        for m, (_, d) in zip(b.members, blk):
+            m.set_fields(d)
+        b.sweep()
+        b.sweep()
+        res.append(_state(b))
+        b.close()
+    for ra, rc in zip(*res):
+        for k in ("images", "delta_new", "j", "F"):
+            assert np.array_equal(ra[k], rc[k]), k
+    b = sc.Batch([q for q, _ in grains[:2]], precision="fp64")
+    with pytest.raises(sc.ScError) as ei:
+        b.set_fused_transfers(True)
+    assert ei.value.status == sc.SC_EINVAL
+    b.close()
